@@ -1,0 +1,218 @@
+/*
+ * ewave.h -- C ABI of the GB300 (sm_103a) library for the 2D acoustic PML wave operator of
+ * Ravelo, Schreiber & Peixoto, "High-order exponential integration for seismic wave
+ * modeling" (arXiv 2401.16322), and of the time integrators the paper compares.
+ *
+ * Problem statement (Sec. 3, Eq. 1st_ord): dU/dt = H U + f(t), U = (u, v, w_x, w_y), with H
+ * the semi-discrete operator of Eq. (1) (Sec. 2): PML damping beta (Sec. 2), 8th-order (or
+ * 4th-order) staggered finite differences (Sec. 2.1, Eqs. spatial_8th_1/2), zero extension
+ * on the sides and bottom, and the free-surface rows of Sec. 2.2 / Appendix A on top.
+ * f is a Ricker point source in the v-row.
+ *
+ * Conventions
+ *  - Plain C, no exceptions.  Every function returns an int status (EWV_OK = 0, negative on
+ *    error); ewv_last_error() gives a one-line message for the last failing call on a handle.
+ *  - Memory ownership: the caller owns every grid-sized device buffer (state, model
+ *    parameters, integrator workspace, seismograms) and passes raw device pointers plus byte
+ *    sizes; sizes come from ewv_layout() / ewv_workspace_bytes().  The library owns only
+ *    small device metadata (descriptors, per-step scalars, reduction partials, Hessenberg
+ *    matrices, coefficients).  Host arrays passed in are copied and never kept.
+ *  - Device pointers must be 256-byte aligned (torch allocations are); sizes are checked.
+ *  - Threading: calls on one handle are serialised on its stream (ewv_set_stream); distinct
+ *    handles are independent.  Calls return after enqueueing work unless stated otherwise.
+ *  - Grid: nodes (i, j), i = 0..nx-1 left to right, j = 0..ny-1 top to bottom (j = 0 is the
+ *    free surface when enabled).  w_x lives at (i+1/2, j), i = 0..nx-2; w_y at (i, j+1/2),
+ *    j = 0..ny-2; w_y is the paper's w_y for its upward y axis.
+ *  - Device state layout ("padded"): one state vector = 4 fields (u, v, w_x, w_y), each
+ *    [ny][pitch] of the model's precision, field-major; w_x column nx-1, w_y row ny-1 and
+ *    columns nx..pitch-1 are padding and hold zeros.  A model with nshots shots stores
+ *    nshots such vectors back to back (the "state" buffer).
+ *  - Compact host layout (ewv_set_state / ewv_get_state): float64, u [ny][nx], v [ny][nx],
+ *    w_x [ny][nx-1], w_y [ny-1][nx], concatenated (n = 2 nx ny + (nx-1) ny + nx (ny-1)).
+ */
+#ifndef EWAVE_H
+#define EWAVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------ */
+#define EWV_OK 0
+#define EWV_ERR_INVALID_ARG -1
+#define EWV_ERR_BAD_SIZE_OR_ALIGNMENT -2
+#define EWV_ERR_WORKSPACE_TOO_SMALL -3
+#define EWV_ERR_CUDA -4
+#define EWV_ERR_NONFINITE -5
+#define EWV_ERR_TIMEOUT -6
+#define EWV_ERR_UNSUPPORTED -7
+#define EWV_ERR_NOT_BOUND -8
+
+/* ---- enums ------------------------------------------------------------------------- */
+#define EWV_F32 0
+#define EWV_F64 1
+
+#define EWV_METHOD_APPLY 0    /* plain H x (no integrator)                               */
+#define EWV_METHOD_FABER 1    /* Sec. 3.2 Faber three-term recurrence                    */
+#define EWV_METHOD_KRYLOV 2   /* Sec. 3.2 Arnoldi (modified Gram-Schmidt) + Pade exp     */
+#define EWV_METHOD_HORK 3     /* Sec. 3.2 high-order (SSP) Runge-Kutta                   */
+#define EWV_METHOD_RK32 4     /* Sec. 3.1 RK3-2                                          */
+#define EWV_METHOD_RK44 5     /* Sec. 3.1 classical RK4-4                                */
+#define EWV_METHOD_LEAPFROG 6 /* Sec. 3.1 two-step leap-frog                             */
+
+#define EWV_LEAPFROG_AVERAGED 0 /* time-averaged PML damping of w (stable reading)       */
+#define EWV_LEAPFROG_LITERAL 1  /* explicit -beta w^n damping, as the formula reads      */
+
+/* Largest Krylov dimension and Faber degree the library accepts. */
+#define EWV_MAX_KRYLOV_M 48
+#define EWV_MAX_FABER_DEGREE 128
+#define EWV_MAX_TAIL_P 24
+
+/* ---- model description ------------------------------------------------------------- */
+typedef struct ewv_model_desc {
+    int dims;            /* 2 (the paper's case)                                          */
+    int nx, ny;          /* grid nodes; nx, ny >= 2                                       */
+    double dx;           /* grid spacing (m), dx = dy (Sec. 2.1)                          */
+    int fd_order;        /* 8 (paper, Sec. 2.1) or 4 (no free surface only)               */
+    int pml_width;       /* PML thickness delta in grid points (0 = no damping)           */
+    double beta0;        /* damping magnitude beta0 of Sec. 2's profile (1/s)             */
+    int free_surface;    /* 1: Sec. 2.2 free surface on top; 0: PML + zero extension      */
+    int precision;       /* EWV_F32 or EWV_F64                                            */
+    int nshots;          /* independent shots (states) sharing this velocity model        */
+    int src_taylor_p;    /* p of the augmented matrix H~ (Eq. matrix_ampli), 1..24        */
+    int max_receivers;   /* receivers per shot (seismogram row width)                     */
+} ewv_model_desc;
+
+typedef struct ewv_layout_info {
+    int pitch;                 /* elements per padded row (multiple of 128 bytes)          */
+    int elem_bytes;            /* 4 or 8                                                   */
+    size_t field_elems;        /* ny * pitch                                               */
+    size_t vector_bytes;       /* 4 * field_elems * elem_bytes: one state vector           */
+    size_t state_bytes;        /* nshots * vector_bytes                                    */
+    size_t params_bytes;       /* c^2 on the padded grid: field_elems * elem_bytes         */
+    size_t compact_n;          /* length of the compact host state vector                  */
+} ewv_layout_info;
+
+typedef struct ewv_model* ewv_model_t;
+typedef struct ewv_batch* ewv_batch_t;
+
+/* ---- lifetime and binding ---------------------------------------------------------- */
+
+/* Create a model from desc (copied).  Uses the current CUDA device.  Errors:
+ * INVALID_ARG (bad field, e.g. fd_order 4 with a free surface, p out of range). */
+int ewv_create_model(const ewv_model_desc* desc, ewv_model_t* out);
+int ewv_destroy_model(ewv_model_t model);
+
+/* Stream (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream) for all work. */
+int ewv_set_stream(ewv_model_t model, void* cuda_stream);
+
+/* Padded layout and buffer sizes of this model. */
+int ewv_layout(ewv_model_t model, ewv_layout_info* out);
+
+/* Device workspace bytes that `method` needs at Krylov dimension / Faber degree / HORK
+ * stages m (ignored by the others), for all shots. */
+int ewv_workspace_bytes(ewv_model_t model, int method, int m, size_t* bytes);
+
+/* Bind caller-owned device buffers.  state: state_bytes; params: params_bytes (c^2);
+ * work: workspace (may be NULL with work_bytes 0 until a method needs it).  Binding zeroes
+ * state and work on the stream.  Errors: BAD_SIZE_OR_ALIGNMENT. */
+int ewv_bind_buffers(ewv_model_t model, void* state, size_t state_bytes, void* params,
+                     size_t params_bytes, void* work, size_t work_bytes);
+
+/* Rebind only the workspace (zeroed on the stream); state and params are left untouched. */
+int ewv_bind_workspace(ewv_model_t model, void* work, size_t work_bytes);
+
+/* Seismogram buffer: [nshots][capacity][max_receivers] of the model's precision.  Sample s
+ * holds u at the receivers after the s-th step since the last ewv_reset_recording(). */
+int ewv_bind_seismogram(ewv_model_t model, void* seismo, size_t bytes, int capacity);
+int ewv_reset_recording(ewv_model_t model);
+
+/* ---- model inputs ------------------------------------------------------------------ */
+
+/* Velocity c (m/s) at the nodes, host float64 [ny][nx] (count = nx*ny); stores c^2 in the
+ * params buffer and records c_max (used by the Faber ellipse).  Synchronous. */
+int ewv_set_velocity(ewv_model_t model, const double* c_host, size_t count);
+
+/* Ricker source of shot `shot` at (sx, depth sy) metres, peak frequency f_peak, delay t0,
+ * amplitude amp: f = amp r(t)/dx^2 added to the v-row at the nearest node (index
+ * floor(pos/dx + 1/2), Sec. 4.1's Ricker wavelet).  Receivers: nrec (x, depth) pairs in
+ * rxy (metres).  The node indices are echoed (src_idx_out[2] = {i, j}; rec_idx_out[2*nrec])
+ * when the pointers are non-NULL.  Errors: INVALID_ARG for positions off the grid or
+ * nrec > max_receivers. */
+int ewv_set_source_receivers(ewv_model_t model, int shot, double sx, double sy, double f_peak,
+                             double t0, double amp, int nrec, const double* rxy,
+                             int32_t* src_idx_out, int32_t* rec_idx_out);
+
+/* Override the Faber ellipse (gamma, c0, c1) of Sec. 3.2's recurrence; by default it is
+ * derived from c_max, beta0, dx and the stencil (see the library's design notes). */
+int ewv_set_faber_ellipse(ewv_model_t model, double gamma, double c0, double c1);
+int ewv_get_faber_ellipse(ewv_model_t model, double* gamma, double* c0, double* c1);
+
+/* ---- state transfer (synchronous) --------------------------------------------------- */
+
+/* Compact float64 host state of one shot <-> the padded device state. */
+int ewv_set_state(ewv_model_t model, int shot, const double* host, size_t n);
+int ewv_get_state(ewv_model_t model, int shot, double* host, size_t n);
+/* Compact host vector <-> one padded device vector at `dev` (vector_bytes). */
+int ewv_pack_vector(ewv_model_t model, const double* host, size_t n, void* dev);
+int ewv_unpack_vector(ewv_model_t model, const void* dev, double* host, size_t n);
+
+/* ---- operator (Eq. 1, Secs. 2.1-2.2) ------------------------------------------------- */
+
+/* y = H x (transpose = 0) or y = H^T x (transpose = 1) for padded device vectors x, y of
+ * this model (no source term).  x and y must not overlap. */
+int ewv_apply_operator(ewv_model_t model, int transpose, const void* x, void* y);
+
+/* ---- time integrators: advance every shot by nsteps steps of dt from time t --------- */
+
+/* Sec. 3.2 Faber: u^{n+1} = sum_{j=0}^{degree} a_j F_j(H~) [u^n; e_p]. */
+int ewv_step_faber(ewv_model_t model, double t, double dt, int degree, int nsteps);
+
+/* Sec. 3.2 Krylov: Arnoldi (MGS) on dt H~ with m matrix-vector products, exp of the m x m
+ * Hessenberg by [13/13] Pade with scaling and squaring.  *info (may be NULL) receives the
+ * smallest effective dimension over shots and steps (< m after a happy breakdown). */
+int ewv_step_krylov(ewv_model_t model, double t, double dt, int m, int nsteps, int* info);
+
+/* Sec. 3.2 HORK (scheme EWV_METHOD_HORK, `stages` = m) or Sec. 3.1 RK3-2 / RK4-4
+ * (EWV_METHOD_RK32 / EWV_METHOD_RK44; stages ignored). */
+int ewv_step_rk(ewv_model_t model, double t, double dt, int scheme, int stages, int nsteps);
+
+/* Sec. 3.1 leap-frog.  The state's u, w_x, w_y hold time level n; the previous level lives
+ * in the workspace and is initialised from the state on the first call after a state
+ * change (u^{-1} = u^0, w^{-1} = w^0).  The v field is not advanced. */
+int ewv_step_leapfrog(ewv_model_t model, double t, double dt, int nsteps);
+int ewv_set_leapfrog_variant(ewv_model_t model, int variant);
+
+/* ---- batches: many models (of uneven sizes) stepped together ----------------------- */
+
+/* A batch steps every shot of every listed model in the same kernel launches (one tile
+ * work list across all grids).  Models keep their own buffers; they must share the
+ * precision, fd order and free-surface setting.  The batch uses the first model's stream
+ * unless ewv_batch_set_stream is called. */
+int ewv_create_batch(const ewv_model_t* models, int nmodels, ewv_batch_t* out);
+int ewv_destroy_batch(ewv_batch_t batch);
+int ewv_batch_set_stream(ewv_batch_t batch, void* cuda_stream);
+int ewv_batch_step_faber(ewv_batch_t batch, double t, double dt, int degree, int nsteps);
+int ewv_batch_step_krylov(ewv_batch_t batch, double t, double dt, int m, int nsteps,
+                          int* info);
+int ewv_batch_step_rk(ewv_batch_t batch, double t, double dt, int scheme, int stages,
+                      int nsteps);
+int ewv_batch_step_leapfrog(ewv_batch_t batch, double t, double dt, int nsteps);
+
+/* ---- diagnostics -------------------------------------------------------------------- */
+
+/* Last error message on this handle ("" if none); valid until the next call on it. */
+const char* ewv_last_error(ewv_model_t model);
+const char* ewv_batch_last_error(ewv_batch_t batch);
+/* Library version string. */
+const char* ewv_version(void);
+/* Number of kernel launches this handle has enqueued since creation (for reporting). */
+int ewv_launch_count(ewv_model_t model, long long* count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EWAVE_H */

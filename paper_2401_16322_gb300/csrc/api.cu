@@ -1,0 +1,1174 @@
+// Host implementation of the C ABI declared in include/ewave.h.
+//
+// Each model owns small device metadata (per-shot source scalars, Krylov scalar blocks,
+// step clocks, receiver offsets); the caller owns the grid-sized buffers.  Stepping goes
+// through an Engine: the list of problems (model, shot) of one model or of a batch, the
+// tile work list across all of their grids, and the per-method launch plan.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/ewave.h"
+#include "ewave_internal.cuh"
+
+
+using namespace ewv;
+
+namespace {
+
+const char* kVersion = "ewave-gb300 0.1 (sm_103a)";
+
+enum { PRO_FABER = 1, PRO_KRYLOV = 2, PRO_HORK = 3, PRO_RK32 = 4, PRO_RK44 = 5, PRO_LEAPFROG = 6 };
+enum { FIN_NONE = 0, FIN_NORM0 = 1, FIN_MATVEC = 2, FIN_MGS = 3 };
+
+// ---------------------------------------------------------------- stencil tables
+// Appendix A free-surface rows (physical y, u_i = u(x, -i dx)), the library's own copy.
+const double kFsUyy[4][9] = {
+    {-3144919.0 / 352800.0, 16.0, -14.0, 112.0 / 9.0, -35.0 / 4.0, 112.0 / 25.0, -14.0 / 9.0,
+     16.0 / 49.0, -1.0 / 32.0},
+    {271343.0 / 156800.0, -1991.0 / 630.0, 57.0 / 40.0, 13.0 / 60.0, -109.0 / 288.0, 6.0 / 25.0,
+     -11.0 / 120.0, 179.0 / 8820.0, -9.0 / 4480.0},
+    {-18519.0 / 78400.0, 58.0 / 35.0, -251.0 / 90.0, 22.0 / 15.0, -1.0 / 16.0, -14.0 / 225.0,
+     1.0 / 30.0, -2.0 / 245.0, 17.0 / 20160.0},
+    {74801.0 / 1411200.0, -37.0 / 140.0, 67.0 / 40.0, -263.0 / 90.0, 53.0 / 32.0, -23.0 / 100.0,
+     13.0 / 360.0, -1.0 / 245.0, 1.0 / 4480.0}};
+const double kFsUy[3][8] = {
+    {5034629.0 / 3763200.0, -23533.0 / 15360.0, 4259.0 / 15360.0, -1103.0 / 9216.0,
+     151.0 / 3072.0, -1171.0 / 76800.0, 139.0 / 46080.0, -211.0 / 752640.0},
+    {-363509.0 / 3763200.0, 6297.0 / 5120.0, -6147.0 / 5120.0, 211.0 / 3072.0, 3.0 / 1024.0,
+     -153.0 / 25600.0, 29.0 / 15360.0, -57.0 / 250880.0},
+    {4631.0 / 250880.0, -305.0 / 3072.0, 1245.0 / 1024.0, -3725.0 / 3072.0, 275.0 / 3072.0,
+     -69.0 / 5120.0, 5.0 / 3072.0, -5.0 / 50176.0}};
+
+// Finite-difference weights of the first derivative at z from values at points xs
+// (Fornberg 1988: weights grow one point at a time; double precision).
+void fd_weights_first(double z, const double* xs, int n, double* w_out) {
+    // c[k][j]: weight of point j for derivative k (k = 0, 1)
+    std::vector<double> c0(n, 0.0), c1(n, 0.0);
+    double cprod = 1.0;
+    double dprev = xs[0] - z;
+    c0[0] = 1.0;
+    for (int i = 1; i < n; ++i) {
+        double prod = 1.0;
+        const double dcur = xs[i] - z;
+        for (int j = 0; j < i; ++j) {
+            const double diff = xs[i] - xs[j];
+            prod *= diff;
+            if (j == i - 1) {
+                c1[i] = cprod * (c0[i - 1] - dprev * c1[i - 1]) / prod;
+                c0[i] = -cprod * dprev * c0[i - 1] / prod;
+            }
+            c1[j] = (dcur * c1[j] - c0[j]) / diff;
+            c0[j] = dcur * c0[j] / diff;
+        }
+        cprod = prod;
+        dprev = dcur;
+    }
+    for (int j = 0; j < n; ++j) w_out[j] = c1[j];
+}
+
+// d(w_y)/dy rows at y = -j (j = 0..3) from w_y(0) = 0 and w_y at y = -(q + 1/2), q = 0..7.
+void fs_dwy_table(double out[4][8]) {
+    double xs[9];
+    xs[0] = 0.0;
+    for (int q = 0; q < 8; ++q) xs[q + 1] = -(q + 0.5);
+    for (int j = 0; j < 4; ++j) {
+        double w[9];
+        fd_weights_first(-(double)j, xs, 9, w);
+        for (int q = 0; q < 8; ++q) out[j][q] = w[q + 1];
+    }
+}
+
+int g_tables_device = -1;
+
+int ensure_tables() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+    if (g_tables_device == dev) return 0;
+    double dwy[4][8];
+    fs_dwy_table(dwy);
+    if (upload_stencil_tables(8, &kFsUyy[0][0], &kFsUy[0][0], &dwy[0][0]) != 0) return -1;
+    g_tables_device = dev;
+    return 0;
+}
+
+// Minimum over theta of the centred second-derivative symbol.
+double symbol_min(int order) {
+    const double c8[5] = {-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0, -1.0 / 560.0};
+    const double c4[3] = {-5.0 / 2.0, 4.0 / 3.0, -1.0 / 12.0};
+    const double* c = order == 8 ? c8 : c4;
+    const int R = order / 2;
+    double best = 1e300;
+    for (int s = 0; s <= 20000; ++s) {
+        const double th = M_PI * s / 20000.0;
+        double v = c[0];
+        for (int k = 1; k <= R; ++k) v += 2.0 * c[k] * std::cos(k * th);
+        best = std::min(best, v);
+    }
+    return best;
+}
+
+struct Shot {
+    bool has_src = false;
+    int si = 0, sj = 0;
+    double f_peak = 10.0, t0 = 0.27, amp = 1.0;
+    std::vector<int> rec_off;
+};
+
+}  // namespace
+
+struct ewv_model {
+    ewv_model_desc d{};
+    int R = 4, pitch = 0, elem = 4;
+    size_t field_elems = 0, vec_elems = 0;
+    cudaStream_t stream = nullptr;
+    void* state = nullptr;
+    size_t state_bytes = 0;
+    void* params = nullptr;
+    size_t params_bytes = 0;
+    void* work = nullptr;
+    size_t work_bytes = 0;
+    void* seismo = nullptr;
+    size_t seismo_bytes = 0;
+    int capacity = 0;
+    double c_max = 0.0;
+    bool velocity_set = false;
+    std::vector<Shot> shots;
+    bool ellipse_override = false;
+    double eg = 0, ec0 = 0, ec1 = 0;
+    int lf_variant = EWV_LEAPFROG_AVERAGED;
+    bool lf_history_valid = false;
+    // device metadata
+    int* d_rec = nullptr;
+    double* d_sigma = nullptr;
+    double* d_kry = nullptr;
+    long long* d_clk = nullptr;
+    double* d_tclk = nullptr;
+    long long version = 0;
+    std::string err;
+    long long launches = 0;
+    struct Engine* engine = nullptr;
+};
+
+struct Engine {
+    std::vector<ewv_model*> models;
+    std::vector<long long> versions;
+    std::vector<ProblemDev> probs;
+    int nprob = 0, ntiles = 0, precision = 0, R = 4;
+    ProblemDev* d_probs = nullptr;
+    int* d_tile_prob = nullptr;
+    double* d_partials = nullptr;
+    unsigned int* d_counters = nullptr;
+    double* d_coef = nullptr;
+    ProblemDev* d_apply = nullptr;
+    std::map<std::tuple<double, int, double, double, double>, std::vector<double>> faber_cache;
+    ~Engine() {
+        cudaFree(d_probs);
+        cudaFree(d_tile_prob);
+        cudaFree(d_partials);
+        cudaFree(d_counters);
+        cudaFree(d_coef);
+        cudaFree(d_apply);
+    }
+};
+
+struct ewv_batch {
+    std::vector<ewv_model*> models;
+    cudaStream_t stream = nullptr;
+    bool stream_set = false;
+    Engine* engine = nullptr;
+    std::string err;
+};
+
+namespace {
+
+int fail(std::string& err, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    err = buf;
+    return code;
+}
+
+#define CUDA_OR_FAIL(err, call)                                                              \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(err, EWV_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));        \
+    } while (0)
+
+bool aligned(const void* p) { return ((uintptr_t)p & 255u) == 0; }
+
+size_t compact_n(const ewv_model* m) {
+    const size_t nx = m->d.nx, ny = m->d.ny;
+    return 2 * nx * ny + (nx - 1) * ny + nx * (ny - 1);
+}
+
+void default_ellipse(const ewv_model* m, double* g, double* c0, double* c1) {
+    const double kappa = m->d.free_surface ? 1.30 : 1.05;
+    const double dims = (double)m->d.dims;
+    const double omega = kappa * m->c_max * std::sqrt(dims * std::fabs(symbol_min(m->d.fd_order))) / m->d.dx;
+    const double bsum = dims * m->d.beta0;
+    const double ar = std::sqrt(2.0) * 0.5 * bsum;
+    const double ai = std::sqrt(2.0) * omega;
+    const double centre = -0.5 * bsum;
+    *g = 0.5 * (ar + ai);
+    *c0 = centre / *g;
+    *c1 = (ar - ai) / (ar + ai);
+}
+
+void ellipse_of(const ewv_model* m, double* g, double* c0, double* c1) {
+    if (m->ellipse_override) {
+        *g = m->eg;
+        *c0 = m->ec0;
+        *c1 = m->ec1;
+    } else {
+        default_ellipse(m, g, c0, c1);
+    }
+}
+
+int vectors_needed(int method, int m) {
+    switch (method) {
+        case EWV_METHOD_APPLY: return 0;
+        case EWV_METHOD_FABER: return 2;
+        case EWV_METHOD_KRYLOV: return m;
+        case EWV_METHOD_HORK: return 2;
+        case EWV_METHOD_RK32: return 2;
+        case EWV_METHOD_RK44: return 3;
+        case EWV_METHOD_LEAPFROG: return 1;
+        default: return -1;
+    }
+}
+
+ProblemDev make_problem(ewv_model* m, int shot, int tile_base) {
+    ProblemDev P{};
+    const ewv_model_desc& d = m->d;
+    P.nx = d.nx;
+    P.ny = d.ny;
+    P.pitch = m->pitch;
+    P.fs = d.free_surface;
+    P.pml = d.pml_width;
+    P.tiles_x = (d.nx + BX - 1) / BX;
+    P.tiles_y = (d.ny + BY - 1) / BY;
+    P.ntiles = P.tiles_x * P.tiles_y;
+    P.tile_base = tile_base;
+    const Shot& s = m->shots[shot];
+    P.has_src = s.has_src ? 1 : 0;
+    P.src_i = s.has_src ? s.si : -1;
+    P.src_j = s.has_src ? s.sj : -1;
+    P.f_peak = s.f_peak;
+    P.t0 = s.t0;
+    P.amp = s.amp;
+    P.nrec = (int)s.rec_off.size();
+    P.rec_stride = d.max_receivers;
+    P.capacity = m->seismo ? m->capacity : 0;
+    P.p = d.src_taylor_p;
+    P.beta0 = d.beta0;
+    P.inv_dx = 1.0 / d.dx;
+    P.inv_dx2 = 1.0 / (d.dx * d.dx);
+    P.inv_pml = d.pml_width > 0 ? 1.0 / d.pml_width : 0.0;
+    P.field_stride = (long long)m->field_elems;
+    P.vec_stride = (long long)m->vec_elems;
+    P.state = (char*)m->state + (size_t)shot * m->vec_elems * m->elem;
+    P.work = m->work;
+    P.c2 = m->params;
+    P.sigma = m->d_sigma + (size_t)shot * MAX_SIGMA;
+    P.rec_off = m->d_rec + (size_t)shot * (d.max_receivers > 0 ? d.max_receivers : 1);
+    P.seismo = m->seismo ? (char*)m->seismo + (size_t)shot * m->capacity * d.max_receivers * m->elem
+                         : nullptr;
+    P.kry = m->d_kry + (size_t)shot * KRY_STRIDE;
+    P.clk = m->d_clk + (size_t)shot * 4;
+    P.tclk = m->d_tclk + (size_t)shot * 2;
+    return P;
+}
+
+// Workspace per shot: `nvec` vectors; shots' workspaces are laid out back to back with a
+// per-shot stride of (work_bytes / nshots) rounded down to whole vectors.
+int build_engine(Engine* E, std::string& err) {
+    E->probs.clear();
+    int tb = 0;
+    for (ewv_model* m : E->models) {
+        const size_t per_shot = m->work ? (m->work_bytes / m->d.nshots) / (m->vec_elems * m->elem) : 0;
+        for (int s = 0; s < m->d.nshots; ++s) {
+            ProblemDev P = make_problem(m, s, tb);
+            P.work = (m->work && per_shot > 0)
+                         ? (char*)m->work + (size_t)s * per_shot * m->vec_elems * m->elem
+                         : nullptr;
+            tb += P.ntiles;
+            E->probs.push_back(P);
+        }
+    }
+    E->nprob = (int)E->probs.size();
+    E->ntiles = tb;
+    std::vector<int> tp(tb);
+    for (int p = 0; p < E->nprob; ++p)
+        for (int t = 0; t < E->probs[p].ntiles; ++t) tp[E->probs[p].tile_base + t] = p;
+    cudaFree(E->d_probs);
+    cudaFree(E->d_tile_prob);
+    cudaFree(E->d_partials);
+    cudaFree(E->d_counters);
+    E->d_probs = nullptr;
+    E->d_tile_prob = nullptr;
+    E->d_partials = nullptr;
+    E->d_counters = nullptr;
+    CUDA_OR_FAIL(err, cudaMalloc(&E->d_probs, sizeof(ProblemDev) * E->nprob));
+    CUDA_OR_FAIL(err, cudaMalloc(&E->d_tile_prob, sizeof(int) * (size_t)tb));
+    CUDA_OR_FAIL(err, cudaMalloc(&E->d_partials, sizeof(double) * (size_t)tb));
+    CUDA_OR_FAIL(err, cudaMalloc(&E->d_counters, sizeof(unsigned int) * E->nprob));
+    CUDA_OR_FAIL(err, cudaMemcpy(E->d_probs, E->probs.data(), sizeof(ProblemDev) * E->nprob,
+                                 cudaMemcpyHostToDevice));
+    CUDA_OR_FAIL(err, cudaMemcpy(E->d_tile_prob, tp.data(), sizeof(int) * (size_t)tb,
+                                 cudaMemcpyHostToDevice));
+    CUDA_OR_FAIL(err, cudaMemset(E->d_counters, 0, sizeof(unsigned int) * E->nprob));
+    if (!E->d_coef) CUDA_OR_FAIL(err, cudaMalloc(&E->d_coef, sizeof(double) * (MAX_DEG + 1)));
+    E->versions.clear();
+    for (ewv_model* m : E->models) E->versions.push_back(m->version);
+    return EWV_OK;
+}
+
+int engine_ready(Engine* E, std::string& err) {
+    bool stale = E->probs.empty();
+    for (size_t i = 0; i < E->models.size() && !stale; ++i)
+        stale = E->versions[i] != E->models[i]->version;
+    if (!stale) return EWV_OK;
+    return build_engine(E, err);
+}
+
+int check_bound(ewv_model* m, int method, int mm, std::string& err) {
+    if (!m->state || !m->params)
+        return fail(err, EWV_ERR_NOT_BOUND, "state/params buffers are not bound");
+    if (!m->velocity_set) return fail(err, EWV_ERR_NOT_BOUND, "velocity not set");
+    const int nv = vectors_needed(method, mm);
+    const size_t need = (size_t)nv * m->vec_elems * m->elem * m->d.nshots;
+    if (m->work_bytes < need)
+        return fail(err, EWV_ERR_WORKSPACE_TOO_SMALL, "workspace %zu bytes < %zu needed", m->work_bytes,
+                    need);
+    return EWV_OK;
+}
+
+StageArgs stage_defaults() {
+    StageArgs a{};
+    a.x = 0;
+    a.u = a.a = a.y_out = a.acc_out = a.d = -1;
+    a.src_slot = -1;
+    a.x_scale_slot = -1;
+    a.fin_mode = FIN_NONE;
+    a.transpose = 0;
+    return a;
+}
+
+struct Ctx {
+    Engine* E;
+    cudaStream_t s;
+    long long* launches;
+    std::string* err;
+    void stage(const StageArgs& a) {
+        launch_stage(E->precision, E->R, E->ntiles, E->d_probs, E->d_tile_prob, a, s);
+        ++*launches;
+    }
+    void point(const PointArgs& pa) {
+        launch_point(E->precision, E->ntiles, E->d_probs, E->d_tile_prob, pa, s);
+        ++*launches;
+    }
+    void copy(int src, int dst, int fmask, bool swap) {
+        PointArgs pa{};
+        pa.mode = swap ? 4 : 3;
+        pa.src = src;
+        pa.dst = dst;
+        pa.fmask = fmask;
+        point(pa);
+    }
+    void prologue(int kind, int m, double g = 0, double c0 = 0, double c1 = 0) {
+        launch_prologue(E->d_probs, E->nprob, kind, m, g, c0, c1, s);
+        ++*launches;
+    }
+    void record(int vec = 0) {
+        launch_record(E->precision, E->d_probs, E->nprob, vec, s);
+        ++*launches;
+    }
+};
+
+int check_launch(std::string& err) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(err, EWV_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
+    return EWV_OK;
+}
+
+// ---------------------------------------------------------------- step plans
+int run_faber(Ctx& C, double t, double dt, int m, int nsteps, double g, double c0, double c1) {
+    std::string& err = *C.err;
+    if (m < 1 || m > MAX_DEG) return fail(err, EWV_ERR_INVALID_ARG, "Faber degree must be 1..%d", MAX_DEG);
+    auto key = std::make_tuple(dt, m, g, c0, c1);
+    auto it = C.E->faber_cache.find(key);
+    if (it == C.E->faber_cache.end()) {
+        launch_faber_coeffs(dt, g, c0, c1, m, C.E->d_coef, C.s);
+        ++*C.launches;
+        std::vector<double> a(m + 1);
+        CUDA_OR_FAIL(err, cudaMemcpyAsync(a.data(), C.E->d_coef, sizeof(double) * (m + 1),
+                                          cudaMemcpyDeviceToHost, C.s));
+        CUDA_OR_FAIL(err, cudaStreamSynchronize(C.s));
+        it = C.E->faber_cache.emplace(key, a).first;
+    }
+    const std::vector<double>& a = it->second;
+    launch_set_clock(C.E->d_probs, C.E->nprob, t, dt, C.s);
+    ++*C.launches;
+    for (int n = 0; n < nsteps; ++n) {
+        C.prologue(PRO_FABER, m, g, c0, c1);
+        StageArgs s1 = stage_defaults();
+        s1.x = 0;
+        s1.y_out = 1;
+        s1.acc_out = 2;
+        s1.src_slot = 0;
+        s1.cx = -c0;
+        s1.ch = 1.0 / g;
+        s1.ck = 1.0;
+        s1.cay = a[1];
+        s1.cax = a[0];
+        C.stage(s1);
+        if (m == 1) {
+            C.copy(2, 0, 0xF, false);
+        } else {
+            StageArgs s2 = stage_defaults();
+            s2.x = 1;
+            s2.u = 0;
+            s2.a = 2;
+            s2.y_out = 2;
+            s2.acc_out = 0;
+            s2.src_slot = 1;
+            s2.cx = -c0;
+            s2.ch = 1.0 / g;
+            s2.cu = -2.0 * c1;
+            s2.ck = 1.0;
+            s2.ca = 1.0;
+            s2.cay = a[2];
+            C.stage(s2);
+            for (int j = 3; j <= m; ++j) {
+                StageArgs sj = stage_defaults();
+                const int in = (j & 1) ? 2 : 1;
+                const int out = (j & 1) ? 1 : 2;
+                sj.x = in;
+                sj.u = out;
+                sj.a = 0;
+                sj.y_out = out;
+                sj.acc_out = 0;
+                sj.src_slot = j - 1;
+                sj.cx = -c0;
+                sj.ch = 1.0 / g;
+                sj.cu = -c1;
+                sj.ck = 1.0;
+                sj.ca = 1.0;
+                sj.cay = a[j];
+                C.stage(sj);
+            }
+        }
+        C.record();
+    }
+    return check_launch(err);
+}
+
+std::vector<double> hork_lambdas(int m) {
+    // lambda^(1) = [1]; lambda^(q)_k = lambda^(q-1)_{k-1}/k (k = 1..q-2),
+    // lambda^(q)_{q-1} = 1/q!, lambda^(q)_0 = 1 - sum of the others.
+    std::vector<double> lam(1, 1.0);
+    double fact = 1.0;
+    for (int q = 2; q <= m; ++q) {
+        fact *= q;
+        std::vector<double> nl(q, 0.0);
+        for (int k = 1; k <= q - 2; ++k) nl[k] = lam[k - 1] / k;
+        nl[q - 1] = 1.0 / fact;
+        double s = 0.0;
+        for (int k = 1; k < q; ++k) s += nl[k];
+        nl[0] = 1.0 - s;
+        lam = nl;
+    }
+    return lam;
+}
+
+int run_hork(Ctx& C, double t, double dt, int m, int nsteps) {
+    std::string& err = *C.err;
+    if (m < 1 || m > MAX_SIGMA) return fail(err, EWV_ERR_INVALID_ARG, "HORK stages must be 1..%d", MAX_SIGMA);
+    const std::vector<double> lam = hork_lambdas(m);
+    auto wgt = [&](int i) { return i <= m - 2 ? lam[i] : (i == m - 1 ? 0.0 : lam[m - 1]); };
+    launch_set_clock(C.E->d_probs, C.E->nprob, t, dt, C.s);
+    ++*C.launches;
+    for (int n = 0; n < nsteps; ++n) {
+        C.prologue(PRO_HORK, m);
+        if (m == 1) {
+            StageArgs s1 = stage_defaults();
+            s1.x = 0;
+            s1.acc_out = 1;
+            s1.src_slot = 0;
+            s1.cx = 1.0;
+            s1.ch = dt;
+            s1.ck = 1.0;
+            s1.cay = lam[0];
+            C.stage(s1);
+            C.copy(1, 0, 0xF, false);
+            C.record();
+            continue;
+        }
+        for (int i = 1; i <= m; ++i) {
+            StageArgs si = stage_defaults();
+            si.cx = 1.0;
+            si.ch = dt;
+            si.ck = 1.0;
+            si.src_slot = i - 1;
+            if (i == 1) {
+                si.x = 0;
+                si.y_out = 1;
+                si.acc_out = 2;
+                si.cax = lam[0];
+                si.cay = wgt(1);
+            } else if (i == 2) {
+                si.x = 1;
+                si.y_out = (m > 2) ? 2 : -1;
+                si.a = 2;
+                si.acc_out = 0;
+                si.ca = 1.0;
+                si.cay = wgt(2);
+            } else {
+                si.x = ((i - 1) & 1) ? 1 : 2;
+                si.y_out = (i < m) ? ((i & 1) ? 1 : 2) : -1;
+                si.a = 0;
+                si.acc_out = 0;
+                si.ca = 1.0;
+                si.cay = wgt(i);
+            }
+            C.stage(si);
+        }
+        C.record();
+    }
+    return check_launch(err);
+}
+
+int run_rk(Ctx& C, double t, double dt, int scheme, int nsteps) {
+    launch_set_clock(C.E->d_probs, C.E->nprob, t, dt, C.s);
+    ++*C.launches;
+    for (int n = 0; n < nsteps; ++n) {
+        if (scheme == EWV_METHOD_RK32) {
+            C.prologue(PRO_RK32, 3);
+            const int xs[3] = {0, 1, 2}, ys[3] = {1, 2, 0};
+            const double al[3] = {0.5 * dt, 0.5 * dt, dt};
+            for (int q = 0; q < 3; ++q) {
+                StageArgs a = stage_defaults();
+                a.x = xs[q];
+                a.u = 0;
+                a.y_out = ys[q];
+                a.src_slot = q;
+                a.ch = 1.0;
+                a.cu = 1.0;
+                a.ck = al[q];
+                C.stage(a);
+            }
+        } else {
+            C.prologue(PRO_RK44, 4);
+            StageArgs a = stage_defaults();
+            a.x = 0; a.u = 0; a.y_out = 1; a.acc_out = 3; a.src_slot = 0;
+            a.ch = 1.0; a.cu = 1.0; a.ck = 0.5 * dt; a.cau = 1.0; a.cak = dt / 6.0;
+            C.stage(a);
+            a = stage_defaults();
+            a.x = 1; a.u = 0; a.a = 3; a.y_out = 2; a.acc_out = 3; a.src_slot = 1;
+            a.ch = 1.0; a.cu = 1.0; a.ck = 0.5 * dt; a.ca = 1.0; a.cak = dt / 3.0;
+            C.stage(a);
+            a = stage_defaults();
+            a.x = 2; a.u = 0; a.a = 3; a.y_out = 1; a.acc_out = 3; a.src_slot = 2;
+            a.ch = 1.0; a.cu = 1.0; a.ck = dt; a.ca = 1.0; a.cak = dt / 3.0;
+            C.stage(a);
+            a = stage_defaults();
+            a.x = 1; a.a = 3; a.acc_out = 0; a.src_slot = 3;
+            a.ch = 1.0; a.ca = 1.0; a.cak = dt / 6.0;
+            C.stage(a);
+        }
+        C.record();
+    }
+    return check_launch(*C.err);
+}
+
+int run_krylov(Ctx& C, double t, double dt, int m, int nsteps, int* info) {
+    std::string& err = *C.err;
+    if (m < 1 || m > MAX_M) return fail(err, EWV_ERR_INVALID_ARG, "Krylov m must be 1..%d", MAX_M);
+    const double tol = C.E->precision == EWV_F64 ? 1e-14 : 1e-6;
+    launch_set_clock(C.E->d_probs, C.E->nprob, t, dt, C.s);
+    ++*C.launches;
+    for (int n = 0; n < nsteps; ++n) {
+        C.prologue(PRO_KRYLOV, m);
+        PointArgs pn{};
+        pn.mode = 0;
+        pn.m = m;
+        pn.tol = tol;
+        pn.partials = C.E->d_partials;
+        pn.counters = C.E->d_counters;
+        C.point(pn);
+        for (int j = 1; j <= m; ++j) {
+            StageArgs a = stage_defaults();
+            a.x = j - 1;
+            a.y_out = j;
+            a.d = 0;
+            a.src_slot = j;
+            a.x_scale_slot = KRY_S + j;
+            a.ch = dt;
+            a.ck = 1.0;
+            a.fin_mode = FIN_MATVEC;
+            a.fin_j = j;
+            a.fin_k = 0;
+            a.m = m;
+            a.tol = tol;
+            a.partials = C.E->d_partials;
+            a.counters = C.E->d_counters;
+            C.stage(a);
+            // at j = m the pass k = m only feeds h_{m+1,m}, which the result does not use
+            const int kmax = (j == m) ? j - 1 : j;
+            for (int k = 1; k <= kmax; ++k) {
+                PointArgs pm{};
+                pm.mode = 1;
+                pm.j = j;
+                pm.k = k;
+                pm.m = m;
+                pm.tol = tol;
+                pm.partials = C.E->d_partials;
+                pm.counters = C.E->d_counters;
+                C.point(pm);
+            }
+        }
+        if (launch_expm(C.E->d_probs, C.E->nprob, m, C.s) != 0)
+            return fail(err, EWV_ERR_CUDA, "expm shared-memory configuration failed");
+        ++*C.launches;
+        PointArgs pc{};
+        pc.mode = 2;
+        pc.m = m;
+        C.point(pc);
+        C.record();
+    }
+    int rc = check_launch(err);
+    if (rc != EWV_OK) return rc;
+    // read back the effective dimensions and the non-finite flags
+    int meff_min = m;
+    bool nonfinite = false;
+    for (ewv_model* md : C.E->models) {
+        std::vector<double> kb((size_t)md->d.nshots * KRY_STRIDE);
+        CUDA_OR_FAIL(err, cudaMemcpyAsync(kb.data(), md->d_kry, kb.size() * sizeof(double),
+                                          cudaMemcpyDeviceToHost, C.s));
+        CUDA_OR_FAIL(err, cudaStreamSynchronize(C.s));
+        for (int s = 0; s < md->d.nshots; ++s) {
+            const double* k = kb.data() + (size_t)s * KRY_STRIDE;
+            meff_min = std::min(meff_min, (int)k[KRY_MEFF]);
+            if (k[KRY_NONFINITE] != 0.0) nonfinite = true;
+        }
+    }
+    if (info) *info = meff_min;
+    if (nonfinite) return fail(err, EWV_ERR_NONFINITE, "non-finite value in the Arnoldi process");
+    return EWV_OK;
+}
+
+int run_leapfrog(Ctx& C, std::vector<ewv_model*>& models, double t, double dt, int nsteps, int variant) {
+    bool need_init = false;
+    for (ewv_model* m : models) need_init = need_init || !m->lf_history_valid;
+    if (need_init) {
+        C.copy(0, 1, 0xD, false);   // u, w_x, w_y of level n -> history (level n-1)
+        for (ewv_model* m : models) m->lf_history_valid = true;
+    }
+    launch_set_clock(C.E->d_probs, C.E->nprob, t, dt, C.s);
+    ++*C.launches;
+    int cur = 0, prev = 1;
+    for (int n = 0; n < nsteps; ++n) {
+        C.prologue(PRO_LEAPFROG, 1);
+        launch_leapfrog(C.E->precision, C.E->R, C.E->ntiles, C.E->d_probs, C.E->d_tile_prob,
+                        cur, prev, variant, dt, C.s);
+        ++*C.launches;
+        std::swap(cur, prev);
+        C.record(cur);
+    }
+    if (cur != 0) C.copy(1, 0, 0xD, true);   // level n back into the state, n-1 into history
+    return check_launch(*C.err);
+}
+
+int precheck_engine_models(std::vector<ewv_model*>& models, int method, int mm, std::string& err) {
+    for (ewv_model* m : models) {
+        int rc = check_bound(m, method, mm, err);
+        if (rc != EWV_OK) return rc;
+        if (m->d.precision != models[0]->d.precision || m->d.fd_order != models[0]->d.fd_order)
+            return fail(err, EWV_ERR_INVALID_ARG, "batched models must share precision and fd order");
+    }
+    return EWV_OK;
+}
+
+Engine* ensure_model_engine(ewv_model* m) {
+    if (!m->engine) {
+        m->engine = new Engine();
+        m->engine->models.push_back(m);
+        m->engine->precision = m->d.precision;
+        m->engine->R = m->R;
+    }
+    return m->engine;
+}
+
+int dispatch(std::vector<ewv_model*>& models, Engine* E, cudaStream_t s, long long* launches,
+             std::string& err, int method, double t, double dt, int mm, int nsteps, int* info) {
+    if (nsteps < 0) return fail(err, EWV_ERR_INVALID_ARG, "nsteps < 0");
+    if (!(dt > 0.0) || !std::isfinite(dt) || !std::isfinite(t))
+        return fail(err, EWV_ERR_INVALID_ARG, "dt must be positive and finite");
+    int rc = precheck_engine_models(models, method, mm, err);
+    if (rc != EWV_OK) return rc;
+    rc = engine_ready(E, err);
+    if (rc != EWV_OK) return rc;
+    Ctx C{E, s, launches, &err};
+    switch (method) {
+        case EWV_METHOD_FABER: {
+            double g, c0, c1;
+            ellipse_of(models[0], &g, &c0, &c1);
+            if (models.size() > 1 && !models[0]->ellipse_override) {
+                // one ellipse enclosing every model's spectrum: the widest
+                double gb = 0, c0b = 0, c1b = 0, best = -1;
+                for (ewv_model* m : models) {
+                    double gg, a0, a1;
+                    ellipse_of(m, &gg, &a0, &a1);
+                    const double ai = gg * (1 - a1);
+                    if (ai > best) {
+                        best = ai;
+                        gb = gg;
+                        c0b = a0;
+                        c1b = a1;
+                    }
+                }
+                g = gb;
+                c0 = c0b;
+                c1 = c1b;
+            }
+            return run_faber(C, t, dt, mm, nsteps, g, c0, c1);
+        }
+        case EWV_METHOD_KRYLOV: return run_krylov(C, t, dt, mm, nsteps, info);
+        case EWV_METHOD_HORK: return run_hork(C, t, dt, mm, nsteps);
+        case EWV_METHOD_RK32:
+        case EWV_METHOD_RK44: return run_rk(C, t, dt, method, nsteps);
+        case EWV_METHOD_LEAPFROG: return run_leapfrog(C, models, t, dt, nsteps, models[0]->lf_variant);
+        default: return fail(err, EWV_ERR_INVALID_ARG, "unknown method %d", method);
+    }
+}
+
+}  // namespace
+
+// ======================================================================== C ABI
+extern "C" {
+
+const char* ewv_version(void) { return kVersion; }
+
+int ewv_create_model(const ewv_model_desc* desc, ewv_model_t* out) {
+    if (!desc || !out) return EWV_ERR_INVALID_ARG;
+    *out = nullptr;
+    const ewv_model_desc& d = *desc;
+    if (d.dims != 2 || d.nx < 2 || d.ny < 2 || !(d.dx > 0) || (d.fd_order != 4 && d.fd_order != 8) ||
+        d.pml_width < 0 || d.beta0 < 0 || (d.precision != EWV_F32 && d.precision != EWV_F64) ||
+        d.nshots < 1 || d.src_taylor_p < 1 || d.src_taylor_p > MAX_P || d.max_receivers < 0)
+        return EWV_ERR_INVALID_ARG;
+    if (d.free_surface && d.fd_order != 8) return EWV_ERR_UNSUPPORTED;
+    if (ensure_tables() != 0) return EWV_ERR_CUDA;
+    ewv_model* m = new ewv_model();
+    m->d = d;
+    m->R = d.fd_order / 2;
+    m->elem = d.precision == EWV_F64 ? 8 : 4;
+    const int per128 = 128 / m->elem;
+    m->pitch = ((d.nx + per128 - 1) / per128) * per128;
+    m->field_elems = (size_t)d.ny * m->pitch;
+    m->vec_elems = 4 * m->field_elems;
+    m->shots.resize(d.nshots);
+    const int nr = d.max_receivers > 0 ? d.max_receivers : 1;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_rec, sizeof(int) * (size_t)nr * d.nshots);
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_sigma, sizeof(double) * (size_t)MAX_SIGMA * d.nshots);
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_kry, sizeof(double) * (size_t)KRY_STRIDE * d.nshots);
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_clk, sizeof(long long) * 4 * (size_t)d.nshots);
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_tclk, sizeof(double) * 2 * (size_t)d.nshots);
+    if (e == cudaSuccess) e = cudaMemset(m->d_sigma, 0, sizeof(double) * (size_t)MAX_SIGMA * d.nshots);
+    if (e == cudaSuccess) e = cudaMemset(m->d_kry, 0, sizeof(double) * (size_t)KRY_STRIDE * d.nshots);
+    if (e == cudaSuccess) e = cudaMemset(m->d_clk, 0, sizeof(long long) * 4 * (size_t)d.nshots);
+    if (e == cudaSuccess) e = cudaMemset(m->d_tclk, 0, sizeof(double) * 2 * (size_t)d.nshots);
+    if (e != cudaSuccess) {
+        ewv_destroy_model(m);
+        return EWV_ERR_CUDA;
+    }
+    *out = m;
+    return EWV_OK;
+}
+
+int ewv_destroy_model(ewv_model_t m) {
+    if (!m) return EWV_ERR_INVALID_ARG;
+    delete m->engine;
+    cudaFree(m->d_rec);
+    cudaFree(m->d_sigma);
+    cudaFree(m->d_kry);
+    cudaFree(m->d_clk);
+    cudaFree(m->d_tclk);
+    delete m;
+    return EWV_OK;
+}
+
+int ewv_set_stream(ewv_model_t m, void* stream) {
+    if (!m) return EWV_ERR_INVALID_ARG;
+    m->stream = (cudaStream_t)stream;
+    return EWV_OK;
+}
+
+int ewv_layout(ewv_model_t m, ewv_layout_info* out) {
+    if (!m || !out) return EWV_ERR_INVALID_ARG;
+    out->pitch = m->pitch;
+    out->elem_bytes = m->elem;
+    out->field_elems = m->field_elems;
+    out->vector_bytes = m->vec_elems * m->elem;
+    out->state_bytes = out->vector_bytes * m->d.nshots;
+    out->params_bytes = m->field_elems * m->elem;
+    out->compact_n = compact_n(m);
+    return EWV_OK;
+}
+
+int ewv_workspace_bytes(ewv_model_t m, int method, int mm, size_t* bytes) {
+    if (!m || !bytes) return EWV_ERR_INVALID_ARG;
+    const int nv = vectors_needed(method, mm);
+    if (nv < 0) return fail(m->err, EWV_ERR_INVALID_ARG, "unknown method %d", method);
+    if (method == EWV_METHOD_KRYLOV && (mm < 1 || mm > MAX_M))
+        return fail(m->err, EWV_ERR_INVALID_ARG, "Krylov m must be 1..%d", MAX_M);
+    *bytes = (size_t)nv * m->vec_elems * m->elem * m->d.nshots;
+    return EWV_OK;
+}
+
+int ewv_bind_buffers(ewv_model_t m, void* state, size_t state_bytes, void* params,
+                     size_t params_bytes, void* work, size_t work_bytes) {
+    if (!m) return EWV_ERR_INVALID_ARG;
+    const size_t sb = m->vec_elems * m->elem * m->d.nshots;
+    if (!state || state_bytes < sb || !aligned(state))
+        return fail(m->err, EWV_ERR_BAD_SIZE_OR_ALIGNMENT, "state needs %zu bytes, 256-B aligned", sb);
+    if (!params || params_bytes < m->field_elems * m->elem || !aligned(params))
+        return fail(m->err, EWV_ERR_BAD_SIZE_OR_ALIGNMENT, "params needs %zu bytes, 256-B aligned",
+                    m->field_elems * m->elem);
+    if (work && !aligned(work))
+        return fail(m->err, EWV_ERR_BAD_SIZE_OR_ALIGNMENT, "work must be 256-B aligned");
+    const bool params_changed = params != m->params;
+    m->state = state;
+    m->state_bytes = state_bytes;
+    m->params = params;
+    m->params_bytes = params_bytes;
+    m->work = work_bytes ? work : nullptr;
+    m->work_bytes = work ? work_bytes : 0;
+    CUDA_OR_FAIL(m->err, cudaMemsetAsync(state, 0, sb, m->stream));
+    if (m->work) CUDA_OR_FAIL(m->err, cudaMemsetAsync(m->work, 0, m->work_bytes, m->stream));
+    if (params_changed) m->velocity_set = false;
+    m->lf_history_valid = false;
+    ++m->version;
+    return EWV_OK;
+}
+
+int ewv_bind_workspace(ewv_model_t m, void* work, size_t work_bytes) {
+    if (!m) return EWV_ERR_INVALID_ARG;
+    if (work && !aligned(work))
+        return fail(m->err, EWV_ERR_BAD_SIZE_OR_ALIGNMENT, "work must be 256-B aligned");
+    m->work = work_bytes ? work : nullptr;
+    m->work_bytes = work ? work_bytes : 0;
+    if (m->work) CUDA_OR_FAIL(m->err, cudaMemsetAsync(m->work, 0, m->work_bytes, m->stream));
+    m->lf_history_valid = false;
+    ++m->version;
+    return EWV_OK;
+}
+
+int ewv_bind_seismogram(ewv_model_t m, void* seismo, size_t bytes, int capacity) {
+    if (!m || capacity < 0) return EWV_ERR_INVALID_ARG;
+    const size_t need = (size_t)capacity * m->d.max_receivers * m->elem * m->d.nshots;
+    if (seismo && (bytes < need || !aligned(seismo)))
+        return fail(m->err, EWV_ERR_BAD_SIZE_OR_ALIGNMENT, "seismogram needs %zu bytes", need);
+    m->seismo = seismo;
+    m->seismo_bytes = bytes;
+    m->capacity = seismo ? capacity : 0;
+    ++m->version;
+    return ewv_reset_recording(m);
+}
+
+int ewv_reset_recording(ewv_model_t m) {
+    if (!m) return EWV_ERR_INVALID_ARG;
+    for (int s = 0; s < m->d.nshots; ++s)
+        CUDA_OR_FAIL(m->err, cudaMemsetAsync(m->d_clk + 4 * s + 1, 0, sizeof(long long), m->stream));
+    return EWV_OK;
+}
+
+int ewv_set_velocity(ewv_model_t m, const double* c, size_t count) {
+    if (!m || !c) return EWV_ERR_INVALID_ARG;
+    const int nx = m->d.nx, ny = m->d.ny;
+    if (count != (size_t)nx * ny) return fail(m->err, EWV_ERR_BAD_SIZE_OR_ALIGNMENT, "velocity count %zu != nx*ny", count);
+    if (!m->params) return fail(m->err, EWV_ERR_NOT_BOUND, "params buffer not bound");
+    double cmax = 0.0;
+    for (size_t i = 0; i < count; ++i) {
+        if (!(c[i] > 0.0) || !std::isfinite(c[i]))
+            return fail(m->err, EWV_ERR_INVALID_ARG, "velocity must be positive and finite");
+        cmax = std::max(cmax, c[i]);
+    }
+    std::vector<char> buf(m->field_elems * m->elem, 0);
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            const double v = c[(size_t)j * nx + i] * c[(size_t)j * nx + i];
+            if (m->elem == 8) ((double*)buf.data())[(size_t)j * m->pitch + i] = v;
+            else ((float*)buf.data())[(size_t)j * m->pitch + i] = (float)v;
+        }
+    CUDA_OR_FAIL(m->err, cudaMemcpyAsync(m->params, buf.data(), buf.size(), cudaMemcpyHostToDevice, m->stream));
+    CUDA_OR_FAIL(m->err, cudaStreamSynchronize(m->stream));
+    m->c_max = cmax;
+    m->velocity_set = true;
+    return EWV_OK;
+}
+
+int ewv_set_source_receivers(ewv_model_t m, int shot, double sx, double sy, double f_peak,
+                             double t0, double amp, int nrec, const double* rxy,
+                             int32_t* src_idx_out, int32_t* rec_idx_out) {
+    if (!m || shot < 0 || shot >= m->d.nshots) return EWV_ERR_INVALID_ARG;
+    if (nrec < 0 || nrec > m->d.max_receivers || (nrec > 0 && !rxy))
+        return fail(m->err, EWV_ERR_INVALID_ARG, "nrec must be 0..max_receivers");
+    if (!(f_peak > 0) || !std::isfinite(t0) || !std::isfinite(amp))
+        return fail(m->err, EWV_ERR_INVALID_ARG, "bad wavelet parameters");
+    auto node = [&](double pos) { return (long long)std::floor(pos / m->d.dx + 0.5); };
+    const long long si = node(sx), sj = node(sy);
+    if (!std::isfinite(sx) || !std::isfinite(sy) || si < 0 || si >= m->d.nx || sj < 0 || sj >= m->d.ny)
+        return fail(m->err, EWV_ERR_INVALID_ARG, "source outside the grid");
+    std::vector<int> off(nrec);
+    std::vector<int32_t> ij(2 * (size_t)nrec);
+    for (int r = 0; r < nrec; ++r) {
+        const double x = rxy[2 * r], y = rxy[2 * r + 1];
+        const long long ri = node(x), rj = node(y);
+        if (!std::isfinite(x) || !std::isfinite(y) || ri < 0 || ri >= m->d.nx || rj < 0 || rj >= m->d.ny)
+            return fail(m->err, EWV_ERR_INVALID_ARG, "receiver %d outside the grid", r);
+        off[r] = (int)(rj * m->pitch + ri);
+        ij[2 * r] = (int32_t)ri;
+        ij[2 * r + 1] = (int32_t)rj;
+    }
+    Shot& s = m->shots[shot];
+    s.has_src = true;
+    s.si = (int)si;
+    s.sj = (int)sj;
+    s.f_peak = f_peak;
+    s.t0 = t0;
+    s.amp = amp;
+    s.rec_off = off;
+    if (nrec > 0)
+        CUDA_OR_FAIL(m->err, cudaMemcpy(m->d_rec + (size_t)shot * m->d.max_receivers, off.data(),
+                                        sizeof(int) * nrec, cudaMemcpyHostToDevice));
+    if (src_idx_out) {
+        src_idx_out[0] = (int32_t)si;
+        src_idx_out[1] = (int32_t)sj;
+    }
+    if (rec_idx_out && nrec > 0) std::memcpy(rec_idx_out, ij.data(), sizeof(int32_t) * 2 * nrec);
+    ++m->version;
+    return EWV_OK;
+}
+
+int ewv_set_faber_ellipse(ewv_model_t m, double g, double c0, double c1) {
+    if (!m || !(g > 0) || !std::isfinite(c0) || !std::isfinite(c1)) return EWV_ERR_INVALID_ARG;
+    m->ellipse_override = true;
+    m->eg = g;
+    m->ec0 = c0;
+    m->ec1 = c1;
+    return EWV_OK;
+}
+
+int ewv_get_faber_ellipse(ewv_model_t m, double* g, double* c0, double* c1) {
+    if (!m || !g || !c0 || !c1) return EWV_ERR_INVALID_ARG;
+    if (!m->velocity_set && !m->ellipse_override) return fail(m->err, EWV_ERR_NOT_BOUND, "velocity not set");
+    ellipse_of(m, g, c0, c1);
+    return EWV_OK;
+}
+
+// ---- state transfer
+static int pack_host(ewv_model* m, const double* h, std::vector<char>& buf) {
+    const int nx = m->d.nx, ny = m->d.ny, P = m->pitch;
+    buf.assign(m->vec_elems * m->elem, 0);
+    size_t o = 0;
+    const int fw[4] = {nx, nx, nx - 1, nx};
+    const int fh[4] = {ny, ny, ny, ny - 1};
+    for (int f = 0; f < 4; ++f)
+        for (int j = 0; j < fh[f]; ++j)
+            for (int i = 0; i < fw[f]; ++i) {
+                const size_t idx = (size_t)f * m->field_elems + (size_t)j * P + i;
+                if (m->elem == 8) ((double*)buf.data())[idx] = h[o];
+                else ((float*)buf.data())[idx] = (float)h[o];
+                ++o;
+            }
+    return EWV_OK;
+}
+
+static void unpack_host(ewv_model* m, const std::vector<char>& buf, double* h) {
+    const int nx = m->d.nx, ny = m->d.ny, P = m->pitch;
+    size_t o = 0;
+    const int fw[4] = {nx, nx, nx - 1, nx};
+    const int fh[4] = {ny, ny, ny, ny - 1};
+    for (int f = 0; f < 4; ++f)
+        for (int j = 0; j < fh[f]; ++j)
+            for (int i = 0; i < fw[f]; ++i) {
+                const size_t idx = (size_t)f * m->field_elems + (size_t)j * P + i;
+                h[o++] = m->elem == 8 ? ((const double*)buf.data())[idx] : (double)((const float*)buf.data())[idx];
+            }
+}
+
+int ewv_pack_vector(ewv_model_t m, const double* host, size_t n, void* dev) {
+    if (!m || !host || !dev) return EWV_ERR_INVALID_ARG;
+    if (n != compact_n(m)) return fail(m->err, EWV_ERR_BAD_SIZE_OR_ALIGNMENT, "compact length %zu != %zu", n, compact_n(m));
+    std::vector<char> buf;
+    pack_host(m, host, buf);
+    CUDA_OR_FAIL(m->err, cudaMemcpyAsync(dev, buf.data(), buf.size(), cudaMemcpyHostToDevice, m->stream));
+    CUDA_OR_FAIL(m->err, cudaStreamSynchronize(m->stream));
+    return EWV_OK;
+}
+
+int ewv_unpack_vector(ewv_model_t m, const void* dev, double* host, size_t n) {
+    if (!m || !host || !dev) return EWV_ERR_INVALID_ARG;
+    if (n != compact_n(m)) return fail(m->err, EWV_ERR_BAD_SIZE_OR_ALIGNMENT, "compact length %zu != %zu", n, compact_n(m));
+    std::vector<char> buf(m->vec_elems * m->elem);
+    CUDA_OR_FAIL(m->err, cudaMemcpyAsync(buf.data(), dev, buf.size(), cudaMemcpyDeviceToHost, m->stream));
+    CUDA_OR_FAIL(m->err, cudaStreamSynchronize(m->stream));
+    unpack_host(m, buf, host);
+    return EWV_OK;
+}
+
+int ewv_set_state(ewv_model_t m, int shot, const double* host, size_t n) {
+    if (!m || shot < 0 || shot >= m->d.nshots) return EWV_ERR_INVALID_ARG;
+    if (!m->state) return fail(m->err, EWV_ERR_NOT_BOUND, "state not bound");
+    m->lf_history_valid = false;
+    return ewv_pack_vector(m, host, n, (char*)m->state + (size_t)shot * m->vec_elems * m->elem);
+}
+
+int ewv_get_state(ewv_model_t m, int shot, double* host, size_t n) {
+    if (!m || shot < 0 || shot >= m->d.nshots) return EWV_ERR_INVALID_ARG;
+    if (!m->state) return fail(m->err, EWV_ERR_NOT_BOUND, "state not bound");
+    return ewv_unpack_vector(m, (const char*)m->state + (size_t)shot * m->vec_elems * m->elem, host, n);
+}
+
+int ewv_apply_operator(ewv_model_t m, int transpose, const void* x, void* y) {
+    if (!m || !x || !y || x == y) return EWV_ERR_INVALID_ARG;
+    if (!aligned(x) || !aligned(y)) return fail(m->err, EWV_ERR_BAD_SIZE_OR_ALIGNMENT, "x, y must be 256-B aligned");
+    if (!m->params || !m->velocity_set) return fail(m->err, EWV_ERR_NOT_BOUND, "velocity not set");
+    Engine* E = ensure_model_engine(m);
+    ProblemDev P = make_problem(m, 0, 0);
+    P.has_src = 0;
+    P.state = const_cast<void*>(x);
+    P.work = y;
+    cudaFree(E->d_apply);
+    E->d_apply = nullptr;
+    CUDA_OR_FAIL(m->err, cudaMalloc(&E->d_apply, sizeof(ProblemDev) + sizeof(int) * P.ntiles));
+    std::vector<int> tp(P.ntiles, 0);
+    int* d_tp = (int*)((char*)E->d_apply + sizeof(ProblemDev));
+    CUDA_OR_FAIL(m->err, cudaMemcpyAsync(E->d_apply, &P, sizeof(ProblemDev), cudaMemcpyHostToDevice, m->stream));
+    CUDA_OR_FAIL(m->err, cudaMemcpyAsync(d_tp, tp.data(), sizeof(int) * P.ntiles, cudaMemcpyHostToDevice, m->stream));
+    StageArgs a = stage_defaults();
+    a.x = 0;
+    a.y_out = 1;
+    a.ch = 1.0;
+    a.ck = 1.0;
+    a.transpose = transpose ? 1 : 0;
+    launch_stage(m->d.precision, m->R, P.ntiles, E->d_apply, d_tp, a, m->stream);
+    ++m->launches;
+    // keep the host copies alive until the copies complete
+    CUDA_OR_FAIL(m->err, cudaStreamSynchronize(m->stream));
+    return check_launch(m->err);
+}
+
+// ---- stepping (single model)
+static int step_model(ewv_model_t m, int method, double t, double dt, int mm, int nsteps, int* info) {
+    if (!m) return EWV_ERR_INVALID_ARG;
+    std::vector<ewv_model*> models{m};
+    Engine* E = ensure_model_engine(m);
+    return dispatch(models, E, m->stream, &m->launches, m->err, method, t, dt, mm, nsteps, info);
+}
+
+int ewv_step_faber(ewv_model_t m, double t, double dt, int degree, int nsteps) {
+    return step_model(m, EWV_METHOD_FABER, t, dt, degree, nsteps, nullptr);
+}
+int ewv_step_krylov(ewv_model_t m, double t, double dt, int mm, int nsteps, int* info) {
+    return step_model(m, EWV_METHOD_KRYLOV, t, dt, mm, nsteps, info);
+}
+int ewv_step_rk(ewv_model_t m, double t, double dt, int scheme, int stages, int nsteps) {
+    if (scheme != EWV_METHOD_HORK && scheme != EWV_METHOD_RK32 && scheme != EWV_METHOD_RK44)
+        return m ? fail(m->err, EWV_ERR_INVALID_ARG, "scheme must be HORK, RK32 or RK44") : EWV_ERR_INVALID_ARG;
+    return step_model(m, scheme, t, dt, stages, nsteps, nullptr);
+}
+int ewv_step_leapfrog(ewv_model_t m, double t, double dt, int nsteps) {
+    return step_model(m, EWV_METHOD_LEAPFROG, t, dt, 1, nsteps, nullptr);
+}
+int ewv_set_leapfrog_variant(ewv_model_t m, int variant) {
+    if (!m || (variant != EWV_LEAPFROG_AVERAGED && variant != EWV_LEAPFROG_LITERAL)) return EWV_ERR_INVALID_ARG;
+    m->lf_variant = variant;
+    return EWV_OK;
+}
+
+// ---- batches
+int ewv_create_batch(const ewv_model_t* models, int n, ewv_batch_t* out) {
+    if (!models || n < 1 || !out) return EWV_ERR_INVALID_ARG;
+    ewv_batch* b = new ewv_batch();
+    for (int i = 0; i < n; ++i) {
+        if (!models[i]) {
+            delete b;
+            return EWV_ERR_INVALID_ARG;
+        }
+        b->models.push_back(models[i]);
+    }
+    for (int i = 1; i < n; ++i)
+        if (models[i]->d.precision != models[0]->d.precision || models[i]->d.fd_order != models[0]->d.fd_order ||
+            models[i]->d.free_surface != models[0]->d.free_surface) {
+            delete b;
+            return EWV_ERR_INVALID_ARG;
+        }
+    b->engine = new Engine();
+    b->engine->models = b->models;
+    b->engine->precision = models[0]->d.precision;
+    b->engine->R = models[0]->R;
+    *out = b;
+    return EWV_OK;
+}
+
+int ewv_destroy_batch(ewv_batch_t b) {
+    if (!b) return EWV_ERR_INVALID_ARG;
+    delete b->engine;
+    delete b;
+    return EWV_OK;
+}
+
+int ewv_batch_set_stream(ewv_batch_t b, void* s) {
+    if (!b) return EWV_ERR_INVALID_ARG;
+    b->stream = (cudaStream_t)s;
+    b->stream_set = true;
+    return EWV_OK;
+}
+
+static int step_batch(ewv_batch_t b, int method, double t, double dt, int mm, int nsteps, int* info) {
+    if (!b) return EWV_ERR_INVALID_ARG;
+    cudaStream_t s = b->stream_set ? b->stream : b->models[0]->stream;
+    long long dummy = 0;
+    int rc = dispatch(b->models, b->engine, s, &dummy, b->err, method, t, dt, mm, nsteps, info);
+    b->models[0]->launches += dummy;
+    return rc;
+}
+
+int ewv_batch_step_faber(ewv_batch_t b, double t, double dt, int degree, int nsteps) {
+    return step_batch(b, EWV_METHOD_FABER, t, dt, degree, nsteps, nullptr);
+}
+int ewv_batch_step_krylov(ewv_batch_t b, double t, double dt, int mm, int nsteps, int* info) {
+    return step_batch(b, EWV_METHOD_KRYLOV, t, dt, mm, nsteps, info);
+}
+int ewv_batch_step_rk(ewv_batch_t b, double t, double dt, int scheme, int stages, int nsteps) {
+    if (scheme != EWV_METHOD_HORK && scheme != EWV_METHOD_RK32 && scheme != EWV_METHOD_RK44) return EWV_ERR_INVALID_ARG;
+    return step_batch(b, scheme, t, dt, stages, nsteps, nullptr);
+}
+int ewv_batch_step_leapfrog(ewv_batch_t b, double t, double dt, int nsteps) {
+    return step_batch(b, EWV_METHOD_LEAPFROG, t, dt, 1, nsteps, nullptr);
+}
+
+const char* ewv_last_error(ewv_model_t m) { return m ? m->err.c_str() : "null handle"; }
+const char* ewv_batch_last_error(ewv_batch_t b) { return b ? b->err.c_str() : "null handle"; }
+
+int ewv_launch_count(ewv_model_t m, long long* count) {
+    if (!m || !count) return EWV_ERR_INVALID_ARG;
+    *count = m->launches;
+    return EWV_OK;
+}
+
+}  // extern "C"

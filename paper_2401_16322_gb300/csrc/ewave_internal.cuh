@@ -1,0 +1,109 @@
+// Internal declarations shared by the library's translation units (not part of the ABI).
+//
+// Data model.  A "problem" is one shot of one velocity model: its own state vector(s) on
+// the padded grid plus a pointer to the model's c^2.  Every launch of a grid-sized kernel
+// covers all problems of an engine (one model's shots, or a batch of models of uneven
+// sizes) through a tile work list: block b handles tile (b - tile_base[p]) of problem
+// p = tile_problem[b].  Per-problem scalars that kernels produce and consume (source
+// scalars of each pass, Krylov/Hessenberg data, reduction partials, step clocks) live in
+// small library-owned device arrays.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ewv {
+
+// Tile of outputs per block (x contiguous) and block shape.
+constexpr int BX = 64;
+constexpr int BY = 16;
+constexpr int TPX = 32;   // threads in x
+constexpr int TPY = 8;    // threads in y
+constexpr int NTHREADS = TPX * TPY;
+constexpr int VX = BX / TPX;   // outputs per thread in x
+constexpr int VY = BY / TPY;   // outputs per thread in y
+
+constexpr int MAX_M = 48;        // Krylov dimension limit (EWV_MAX_KRYLOV_M)
+constexpr int MAX_DEG = 128;     // Faber degree limit
+constexpr int MAX_P = 24;        // augmented tail length limit
+constexpr int MAX_SIGMA = 160;   // per-step source-scalar slots
+
+// Per-problem Krylov scalar block (doubles), offsets.
+constexpr int KRY_H = 0;                                  // (MAX_M+1) x MAX_M Hessenberg
+constexpr int KRY_S = KRY_H + (MAX_M + 1) * MAX_M;        // slot scales s_k, k = 1..MAX_M+1
+constexpr int KRY_T = KRY_S + (MAX_M + 2);                // tails Vt[k][MAX_P], k = 1..MAX_M+1
+constexpr int KRY_W = KRY_T + (MAX_M + 2) * MAX_P;        // W scalars (source column values)
+constexpr int KRY_E = KRY_W + MAX_P;                      // exp(H_m) e_1
+constexpr int KRY_BETA = KRY_E + MAX_M;                   // |x|
+constexpr int KRY_MEFF = KRY_BETA + 1;                    // effective dimension (as double)
+constexpr int KRY_ACTIVE = KRY_MEFF + 1;                  // 1 while Arnoldi continues
+constexpr int KRY_NONFINITE = KRY_ACTIVE + 1;             // 1 if a NaN/Inf was seen
+constexpr int KRY_STRIDE = ((KRY_NONFINITE + 1 + 31) / 32) * 32;
+
+struct ProblemDev {
+    int nx, ny, pitch, fs;
+    int pml, src_i, src_j, nrec;
+    int tiles_x, tiles_y, tile_base, ntiles;
+    int rec_stride, capacity, p, has_src;
+    double beta0, inv_dx, inv_dx2, inv_pml;
+    double f_peak, t0, amp;
+    long long field_stride, vec_stride;
+    void* state;          // vector 0 (this shot)
+    void* work;           // vector 1 (vectors 1.. are consecutive)
+    const void* c2;
+    double* sigma;        // [MAX_SIGMA] source scalars of the current step's passes
+    const int* rec_off;   // [nrec] j*pitch + i
+    void* seismo;         // [capacity][rec_stride] of this shot
+    double* kry;          // [KRY_STRIDE]
+    long long* clk;       // [4]: step within call, recording cursor, (unused), (unused)
+    double* tclk;         // [2]: t_start, dt of the current call
+};
+
+// Arguments of the fused stencil-stage kernel (see kernels_stencil.cu).
+struct StageArgs {
+    int x, u, a, y_out, acc_out;     // vector indices (-1 = none)
+    int d;                           // dot partner vector (-1 = none)
+    int src_slot;                    // sigma slot added at the source node (-1 = none)
+    int x_scale_slot;                // -1 or KRY_S index + k: X multiplied by kry[slot]
+    int fin_mode, fin_j, fin_k;      // last-block finalisation (Krylov), see kernels_aux
+    int transpose;                   // 0: H, 1: H^T
+    double cx, ch, cu, ck, ca, cau, cak, cay, cax;
+    double* partials;                // per-block partial dot products (global index)
+    unsigned int* counters;          // per-problem arrival counters
+    double tol;                      // breakdown tolerance (Krylov)
+    int m;                           // Krylov dimension of this step
+    double dt;
+};
+
+// Arguments of the pointwise kernel (kernels_aux.cu).
+struct PointArgs {
+    int mode;        // 0: |q1|^2 (norm); 1: MGS pass; 2: Krylov combine; 3: copy; 4: swap
+    int j, k, m;
+    int src, dst;    // copy / swap vectors
+    int fmask;       // fields for copy / swap (bit f)
+    double tol;
+    double* partials;
+    unsigned int* counters;
+};
+
+// Host-side launchers (defined in kernels_stencil.cu / kernels_aux.cu).
+int upload_stencil_tables(int order, const double* fs_uyy, const double* fs_uy,
+                          const double* fs_dwy);
+void launch_stage(int precision, int R, int nblocks, const ProblemDev* probs,
+                  const int* tile_prob, const StageArgs& a, cudaStream_t s);
+void launch_leapfrog(int precision, int R, int nblocks, const ProblemDev* probs,
+                     const int* tile_prob, int cur, int prev, int variant, double dt,
+                     cudaStream_t s);
+
+void launch_set_clock(const ProblemDev* probs, int nprob, double t, double dt, cudaStream_t s);
+void launch_reset_cursor(const ProblemDev* probs, int nprob, cudaStream_t s);
+void launch_prologue(const ProblemDev* probs, int nprob, int kind, int m, double gamma,
+                     double c0, double c1, cudaStream_t s);
+void launch_record(int precision, const ProblemDev* probs, int nprob, int vec, cudaStream_t s);
+void launch_point(int precision, int nblocks, const ProblemDev* probs, const int* tile_prob,
+                  const PointArgs& pa, cudaStream_t s);
+int launch_expm(const ProblemDev* probs, int nprob, int mmax, cudaStream_t s);
+void launch_faber_coeffs(double dt, double gamma, double c0, double c1, int m, double* out,
+                         cudaStream_t s);
+
+}  // namespace ewv

@@ -1,0 +1,500 @@
+// Small and pointwise kernels around the fused stencil passes:
+//  - step clock and per-step source scalars (Ricker derivatives, augmented tail recurrence)
+//  - receiver recording (seismogram, Sec. 5.1)
+//  - Krylov passes: |x|^2, modified Gram-Schmidt axpy + next dot (Sec. 3.2 listing), the
+//    final combination, and the [13/13] Pade exponential of the Hessenberg matrix
+//  - Faber coefficients by the trapezoid rule on the unit circle (FP64)
+//  - vector copy / swap helpers
+#include <math.h>
+
+#include "ewave_internal.cuh"
+#include "krylov_finalize.cuh"
+
+namespace ewv {
+
+template <typename T>
+__device__ __forceinline__ T* vptr(const ProblemDev* P, int k) {
+    return k == 0 ? (T*)P->state : (T*)P->work + (long long)(k - 1) * P->vec_stride;
+}
+
+// ---------------------------------------------------------------- clock
+__global__ void set_clock_kernel(const ProblemDev* probs, int nprob, double t, double dt) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nprob) return;
+    const ProblemDev* P = probs + p;
+    P->clk[0] = 0;
+    P->tclk[0] = t;
+    P->tclk[1] = dt;
+}
+
+__global__ void reset_cursor_kernel(const ProblemDev* probs, int nprob) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nprob) return;
+    probs[p].clk[1] = 0;
+}
+
+// ---------------------------------------------------------------- source scalars
+// Ricker r(tau) = (1 - 2 a tau^2) exp(-a tau^2), a = (pi f)^2 (Sec. 4.1); derivatives
+// r^(k) = -g^(k+2) / (2a) with g = exp(-a tau^2) and the Hermite recurrence
+// g^(k) = -2 a tau g^(k-1) - 2 a (k-1) g^(k-2).
+__device__ void ricker_derivs(double t, double f, double t0, int p, double* out) {
+    const double a = (M_PI * f) * (M_PI * f);
+    const double tau = t - t0;
+    double gm2 = exp(-a * tau * tau);       // g^(k-2)
+    double gm1 = -2.0 * a * tau * gm2;      // g^(k-1)
+    for (int k = 2; k < p + 2; ++k) {
+        const double g = -2.0 * a * tau * gm1 - 2.0 * a * (double)(k - 1) * gm2;
+        out[k - 2] = -g / (2.0 * a);
+        gm2 = gm1;
+        gm1 = g;
+    }
+}
+
+__device__ __forceinline__ double ricker(double t, double f, double t0) {
+    const double a = (M_PI * f) * (M_PI * f);
+    const double tau = t - t0;
+    return (1.0 - 2.0 * a * tau * tau) * exp(-a * tau * tau);
+}
+
+enum { PRO_FABER = 1, PRO_KRYLOV = 2, PRO_HORK = 3, PRO_RK32 = 4, PRO_RK44 = 5, PRO_LEAPFROG = 6 };
+
+// One thread per problem.  Fills sigma[] (the value added at the source node's v entry in
+// each pass of this step) from t_n = t_start + step * dt:
+//   Faber: sigma_j = W . y_j, y_0 = e_p, y_1 = F1 y_0, y_2 = F1 y_1 - 2 c1 y_0,
+//          y_j = F1 y_{j-1} - c1 y_{j-2}, F1 = (J/dt)/gamma - c0 (tail of Eq. matrix_ampli)
+//   HORK:  sigma_i = W . (I + J)^i e_p
+//   RK3-2 / RK4-4 / leap-frog: f at the stage times
+//   Krylov: W stored for the Arnoldi passes
+// W[p-1-k] = dt^k r^(k)(t_n) amp / dx^2 (tail scaled by dt).
+__global__ void prologue_kernel(const ProblemDev* probs, int nprob, int kind, int m,
+                                double gamma, double c0, double c1) {
+    const int pid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pid >= nprob) return;
+    const ProblemDev* P = probs + pid;
+    const double dt = P->tclk[1];
+    const double tn = P->tclk[0] + (double)P->clk[0] * dt;
+    double* sg = P->sigma;
+    if (!P->has_src) {
+        for (int s = 0; s < MAX_SIGMA; ++s) sg[s] = 0.0;
+        if (kind == PRO_KRYLOV)
+            for (int q = 0; q < MAX_P; ++q) P->kry[KRY_W + q] = 0.0;
+        return;
+    }
+    const double scale = P->amp * P->inv_dx2;
+    if (kind == PRO_RK32) {
+        sg[0] = scale * ricker(tn, P->f_peak, P->t0);
+        sg[1] = sg[2] = scale * ricker(tn + 0.5 * dt, P->f_peak, P->t0);
+        return;
+    }
+    if (kind == PRO_RK44) {
+        sg[0] = scale * ricker(tn, P->f_peak, P->t0);
+        sg[1] = sg[2] = scale * ricker(tn + 0.5 * dt, P->f_peak, P->t0);
+        sg[3] = scale * ricker(tn + dt, P->f_peak, P->t0);
+        return;
+    }
+    if (kind == PRO_LEAPFROG) {
+        sg[0] = scale * ricker(tn, P->f_peak, P->t0);
+        return;
+    }
+    const int p = P->p;
+    double r[MAX_P], W[MAX_P];
+    ricker_derivs(tn, P->f_peak, P->t0, p, r);
+    double dk = 1.0;
+    for (int k = 0; k < p; ++k) {
+        W[p - 1 - k] = dk * r[k] * scale;
+        dk *= dt;
+    }
+    if (kind == PRO_KRYLOV) {
+        for (int q = 0; q < MAX_P; ++q) P->kry[KRY_W + q] = q < p ? W[q] : 0.0;
+        return;
+    }
+    double y0[MAX_P], y1[MAX_P], y2[MAX_P];
+    for (int q = 0; q < p; ++q) y0[q] = 0.0;
+    y0[p - 1] = 1.0;
+    auto dotW = [&](const double* y) {
+        double s = 0.0;
+        for (int q = 0; q < p; ++q) s += W[q] * y[q];
+        return s;
+    };
+    if (kind == PRO_HORK) {
+        // y_i = (I + J) y_{i-1}
+        for (int i = 0; i < m && i < MAX_SIGMA; ++i) {
+            sg[i] = dotW(y0);
+            for (int q = 0; q < p; ++q) y1[q] = y0[q] + (q + 1 < p ? y0[q + 1] : 0.0);
+            for (int q = 0; q < p; ++q) y0[q] = y1[q];
+        }
+        return;
+    }
+    // Faber
+    const double ig = 1.0 / gamma;
+    sg[0] = dotW(y0);
+    for (int q = 0; q < p; ++q) y1[q] = ig * (q + 1 < p ? y0[q + 1] : 0.0) / dt - c0 * y0[q];
+    if (m >= 2) sg[1] = dotW(y1);
+    for (int j = 2; j < m && j < MAX_SIGMA; ++j) {
+        const double cj = (j == 2) ? 2.0 * c1 : c1;
+        for (int q = 0; q < p; ++q)
+            y2[q] = ig * (q + 1 < p ? y1[q + 1] : 0.0) / dt - c0 * y1[q] - cj * y0[q];
+        sg[j] = dotW(y2);
+        for (int q = 0; q < p; ++q) {
+            y0[q] = y1[q];
+            y1[q] = y2[q];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- recording
+template <typename T>
+__global__ void record_kernel(const ProblemDev* probs, int nprob, int vec) {
+    const ProblemDev* P = probs + blockIdx.x;
+    const long long cur = P->clk[1];
+    if (P->seismo && cur < P->capacity) {
+        const T* u = vptr<T>(P, vec);
+        T* out = (T*)P->seismo + cur * P->rec_stride;
+        for (int r = threadIdx.x; r < P->nrec; r += blockDim.x) out[r] = u[P->rec_off[r]];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        P->clk[1] = cur + 1;
+        P->clk[0] += 1;
+    }
+}
+
+// ---------------------------------------------------------------- pointwise Krylov passes
+// Each uses the stencil kernels' tile decomposition so that partial index == block index.
+
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+point_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ tile_prob,
+             PointArgs pa) {
+    __shared__ double red[NTHREADS / 32];
+    __shared__ int s_last;
+    const int pid = tile_prob[blockIdx.x];
+    const ProblemDev* P = probs + pid;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int nx = P->nx, ny = P->ny, pitch = P->pitch;
+    const int lt = blockIdx.x - P->tile_base;
+    const int x0 = (lt % P->tiles_x) * BX, y0 = (lt / P->tiles_x) * BY;
+    const long long fstr = P->field_stride;
+    double* kry = P->kry;
+
+    if (pa.mode == 1 && kry[KRY_ACTIVE] == 0.0) return;
+    if (pa.mode == 3 || pa.mode == 4) {
+        T* S = vptr<T>(P, pa.src);
+        T* Dd = vptr<T>(P, pa.dst);
+        for (int b = 0; b < VY; ++b)
+            for (int c = 0; c < VX; ++c) {
+                const int i = x0 + tx + c * TPX, j = y0 + ty + b * TPY;
+                if (i >= nx || j >= ny) continue;
+                const long long o = (long long)j * pitch + i;
+                for (int f = 0; f < 4; ++f) {
+                    if (!((pa.fmask >> f) & 1)) continue;
+                    const T s = S[f * fstr + o];
+                    if (pa.mode == 4) S[f * fstr + o] = Dd[f * fstr + o];
+                    Dd[f * fstr + o] = s;
+                }
+            }
+        return;
+    }
+    if (pa.mode == 2) {
+        // u^{n+1} = beta sum_{k=1}^{meff} e_k s_k q_k  (q_1 is the state itself)
+        if (kry[KRY_NONFINITE] != 0.0) return;
+        const int meff = (int)kry[KRY_MEFF];
+        const double beta = kry[KRY_BETA];
+        T coef[MAX_M];
+        for (int k = 1; k <= meff; ++k) coef[k - 1] = (T)(beta * kry[KRY_E + k - 1] * kry[KRY_S + k]);
+        T* St = vptr<T>(P, 0);
+        for (int b = 0; b < VY; ++b)
+            for (int c = 0; c < VX; ++c) {
+                const int i = x0 + tx + c * TPX, j = y0 + ty + b * TPY;
+                if (i >= nx || j >= ny) continue;
+                const long long o = (long long)j * pitch + i;
+                for (int f = 0; f < 4; ++f) {
+                    T acc = T(0);
+                    for (int k = 1; k <= meff; ++k) acc += coef[k - 1] * vptr<T>(P, k - 1)[f * fstr + o];
+                    St[f * fstr + o] = acc;
+                }
+            }
+        return;
+    }
+    // mode 0 (norm of the state) or 1 (MGS pass k of Arnoldi step j):
+    // q_{j+1} -= h_{k,j} s_k q_k, then partial <q_{j+1}, q_{k+1}> (k < j) or |q_{j+1}|^2.
+    float accf = 0.f;
+    double accd = 0.0;
+    T* W = nullptr;
+    const T* Qk = nullptr;
+    const T* Qn = nullptr;
+    T coef = T(0);
+    if (pa.mode == 0) {
+        Qn = vptr<T>(P, 0);
+    } else {
+        W = vptr<T>(P, pa.j);                  // slot j+1
+        Qk = vptr<T>(P, pa.k - 1);             // slot k
+        coef = (T)(kry[KRY_H + (pa.k - 1) * MAX_M + (pa.j - 1)] * kry[KRY_S + pa.k]);
+        Qn = pa.k < pa.j ? vptr<T>(P, pa.k) : nullptr;   // slot k+1 (or w itself)
+    }
+    for (int b = 0; b < VY; ++b)
+        for (int c = 0; c < VX; ++c) {
+            const int i = x0 + tx + c * TPX, j = y0 + ty + b * TPY;
+            if (i >= nx || j >= ny) continue;
+            const long long o = (long long)j * pitch + i;
+            for (int f = 0; f < 4; ++f) {
+                if ((f == 2 && i >= nx - 1) || (f == 3 && j >= ny - 1)) continue;
+                T val;
+                T other;
+                if (pa.mode == 0) {
+                    val = Qn[f * fstr + o];
+                    other = val;
+                } else {
+                    val = W[f * fstr + o] - coef * Qk[f * fstr + o];
+                    W[f * fstr + o] = val;
+                    other = Qn ? Qn[f * fstr + o] : val;
+                }
+                if (sizeof(T) == 4) accf = fmaf((float)val, (float)other, accf);
+                else accd = fma((double)val, (double)other, accd);
+            }
+        }
+    if (pa.mode == 1 && pa.k == pa.j && pa.j == pa.m) return;   // h_{m+1,m} unused
+    const double bsum = block_sum_fixed((double)accf + accd, red);
+    StageArgs a{};
+    a.fin_mode = pa.mode == 0 ? FIN_NORM0 : FIN_MGS;
+    a.fin_j = pa.j;
+    a.fin_k = pa.k;
+    a.m = pa.m;
+    a.tol = pa.tol;
+    a.partials = pa.partials;
+    a.counters = pa.counters;
+    partial_and_finalize(P, pid, a, bsum, red, &s_last);
+}
+
+// ---------------------------------------------------------------- Hessenberg exponential
+// [13/13] Pade approximant with scaling and squaring (Higham 2005), FP64, one block per
+// problem; writes exp(H_meff) e_1 to kry[KRY_E..].  Shared memory: 7 matrices of meff^2.
+__device__ void mat_mul(const double* A, const double* B, double* C, int n) {
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int r = e / n, c = e - r * n;
+        double s = 0.0;
+        for (int k = 0; k < n; ++k) s = fma(A[r * n + k], B[k * n + c], s);
+        C[e] = s;
+    }
+    __syncthreads();
+}
+
+__global__ void expm_kernel(const ProblemDev* probs, int nprob) {
+    extern __shared__ double sm[];
+    __shared__ double b[14];
+    __shared__ double colmax[MAX_M];
+    __shared__ int s_scale, s_piv;
+    const ProblemDev* P = probs + blockIdx.x;
+    double* kry = P->kry;
+    const int n = (int)kry[KRY_MEFF];
+    if (n <= 0 || kry[KRY_NONFINITE] != 0.0) return;
+    const int nn = n * n;
+    double* A = sm;
+    double* A2 = A + nn;
+    double* A4 = A2 + nn;
+    double* A6 = A4 + nn;
+    double* Um = A6 + nn;
+    double* Vm = Um + nn;
+    double* Tm = Vm + nn;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        // b_k = (26-k)! 13! / (26! k! (13-k)!)
+        double f[27];
+        f[0] = 1.0;
+        for (int i = 1; i <= 26; ++i) f[i] = f[i - 1] * (double)i;
+        for (int k = 0; k <= 13; ++k) b[k] = f[26 - k] * f[13] / (f[26] * f[k] * f[13 - k]);
+    }
+    for (int e = tid; e < nn; e += blockDim.x) {
+        const int r = e / n, c = e - r * n;
+        A[e] = kry[KRY_H + r * MAX_M + c];
+    }
+    __syncthreads();
+    for (int c = tid; c < n; c += blockDim.x) {
+        double s = 0.0;
+        for (int r = 0; r < n; ++r) s += fabs(A[r * n + c]);
+        colmax[c] = s;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double nrm = 0.0;
+        for (int c = 0; c < n; ++c) nrm = fmax(nrm, colmax[c]);
+        const double theta13 = 5.371920351148152;
+        int s = 0;
+        if (nrm > theta13) s = (int)ceil(log2(nrm / theta13));
+        s_scale = s;
+    }
+    __syncthreads();
+    const int s = s_scale;
+    const double sc = ldexp(1.0, -s);
+    for (int e = tid; e < nn; e += blockDim.x) A[e] *= sc;
+    __syncthreads();
+    mat_mul(A, A, A2, n);
+    mat_mul(A2, A2, A4, n);
+    mat_mul(A4, A2, A6, n);
+    for (int e = tid; e < nn; e += blockDim.x) Tm[e] = b[13] * A6[e] + b[11] * A4[e] + b[9] * A2[e];
+    __syncthreads();
+    mat_mul(A6, Tm, Um, n);   // Um = A6 (b13 A6 + b11 A4 + b9 A2)
+    for (int e = tid; e < nn; e += blockDim.x) {
+        const int r = e / n, c = e - r * n;
+        Tm[e] = Um[e] + b[7] * A6[e] + b[5] * A4[e] + b[3] * A2[e] + (r == c ? b[1] : 0.0);
+    }
+    __syncthreads();
+    mat_mul(A, Tm, Um, n);    // U = A (...)
+    for (int e = tid; e < nn; e += blockDim.x) Tm[e] = b[12] * A6[e] + b[10] * A4[e] + b[8] * A2[e];
+    __syncthreads();
+    mat_mul(A6, Tm, Vm, n);
+    for (int e = tid; e < nn; e += blockDim.x) {
+        const int r = e / n, c = e - r * n;
+        Vm[e] += b[6] * A6[e] + b[4] * A4[e] + b[2] * A2[e] + (r == c ? b[0] : 0.0);
+    }
+    __syncthreads();
+    // Solve (V - U) Rm = (V + U): LU with partial pivoting; P_ in A, RHS in A2.
+    double* Pm = A;
+    double* Q = A2;
+    for (int e = tid; e < nn; e += blockDim.x) {
+        Pm[e] = Vm[e] - Um[e];
+        Q[e] = Vm[e] + Um[e];
+    }
+    __syncthreads();
+    for (int c = 0; c < n; ++c) {
+        if (tid == 0) {
+            int piv = c;
+            double best = fabs(Pm[c * n + c]);
+            for (int r = c + 1; r < n; ++r)
+                if (fabs(Pm[r * n + c]) > best) {
+                    best = fabs(Pm[r * n + c]);
+                    piv = r;
+                }
+            s_piv = piv;
+        }
+        __syncthreads();
+        const int piv = s_piv;
+        if (piv != c) {
+            for (int e = tid; e < n; e += blockDim.x) {
+                double t = Pm[c * n + e];
+                Pm[c * n + e] = Pm[piv * n + e];
+                Pm[piv * n + e] = t;
+                t = Q[c * n + e];
+                Q[c * n + e] = Q[piv * n + e];
+                Q[piv * n + e] = t;
+            }
+        }
+        __syncthreads();
+        const double d = Pm[c * n + c];
+        // eliminate rows below
+        for (int e = tid; e < (n - c - 1) * n; e += blockDim.x) {
+            const int r = c + 1 + e / n, col = e % n;
+            const double l = Pm[r * n + c] / d;
+            if (col > c) Pm[r * n + col] -= l * Pm[c * n + col];
+            Q[r * n + col] -= l * Q[c * n + col];
+        }
+        __syncthreads();
+        for (int r = c + 1 + tid; r < n; r += blockDim.x) Pm[r * n + c] = 0.0;
+        __syncthreads();
+    }
+    // back substitution, column-parallel over the RHS
+    for (int col = tid; col < n; col += blockDim.x) {
+        for (int r = n - 1; r >= 0; --r) {
+            double v = Q[r * n + col];
+            for (int k = r + 1; k < n; ++k) v -= Pm[r * n + k] * Q[k * n + col];
+            Q[r * n + col] = v / Pm[r * n + r];
+        }
+    }
+    __syncthreads();
+    // Rm = Q.  Undo the scaling: Rm^(2^s) e_1 by squarings or repeated products.
+    double* Rm = Q;
+    const long long nmv = 1LL << s;
+    if ((double)nmv <= (double)s * n) {
+        double* x = A4;
+        double* y = A6;
+        for (int r = tid; r < n; r += blockDim.x) x[r] = (r == 0) ? 1.0 : 0.0;
+        __syncthreads();
+        for (long long it = 0; it < nmv; ++it) {
+            for (int r = tid; r < n; r += blockDim.x) {
+                double v = 0.0;
+                for (int k = 0; k < n; ++k) v = fma(Rm[r * n + k], x[k], v);
+                y[r] = v;
+            }
+            __syncthreads();
+            for (int r = tid; r < n; r += blockDim.x) x[r] = y[r];
+            __syncthreads();
+        }
+        for (int r = tid; r < n; r += blockDim.x) kry[KRY_E + r] = x[r];
+    } else {
+        double* cur = Rm;
+        double* nxt = Um;
+        for (int it = 0; it < s; ++it) {
+            mat_mul(cur, cur, nxt, n);
+            double* t = cur;
+            cur = nxt;
+            nxt = t;
+        }
+        for (int r = tid; r < n; r += blockDim.x) kry[KRY_E + r] = cur[r * n + 0];
+    }
+}
+
+// ---------------------------------------------------------------- Faber coefficients
+// a_j = (1/N) sum_k exp(dt psi(w_k)) w_k^-j on w_k = exp(2 pi i k / N),
+// psi(w) = gamma (w + c0 + c1 / w); real part:
+// exp(dt gamma (c0 + (1 + c1) cos th)) cos(dt gamma (1 - c1) sin th - j th).
+__global__ void faber_coeff_kernel(double dt, double gamma, double c0, double c1, int m,
+                                   int N, double* out) {
+    __shared__ double red[8];
+    const int j = blockIdx.x;
+    if (j > m) return;
+    double s = 0.0;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        const double th = 2.0 * M_PI * (double)k / (double)N;
+        double sn, cs;
+        sincos(th, &sn, &cs);
+        const double mag = exp(dt * gamma * (c0 + (1.0 + c1) * cs));
+        s += mag * cos(dt * gamma * (1.0 - c1) * sn - (double)j * th);
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) t += red[w];
+        out[j] = t / (double)N;
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+void launch_set_clock(const ProblemDev* probs, int nprob, double t, double dt, cudaStream_t s) {
+    set_clock_kernel<<<(nprob + 127) / 128, 128, 0, s>>>(probs, nprob, t, dt);
+}
+void launch_reset_cursor(const ProblemDev* probs, int nprob, cudaStream_t s) {
+    reset_cursor_kernel<<<(nprob + 127) / 128, 128, 0, s>>>(probs, nprob);
+}
+void launch_prologue(const ProblemDev* probs, int nprob, int kind, int m, double gamma,
+                     double c0, double c1, cudaStream_t s) {
+    prologue_kernel<<<(nprob + 63) / 64, 64, 0, s>>>(probs, nprob, kind, m, gamma, c0, c1);
+}
+void launch_record(int precision, const ProblemDev* probs, int nprob, int vec, cudaStream_t s) {
+    if (precision == 0) record_kernel<float><<<nprob, 128, 0, s>>>(probs, nprob, vec);
+    else record_kernel<double><<<nprob, 128, 0, s>>>(probs, nprob, vec);
+}
+void launch_point(int precision, int nblocks, const ProblemDev* probs, const int* tile_prob,
+                  const PointArgs& pa, cudaStream_t s) {
+    const dim3 block(TPX, TPY);
+    if (precision == 0) point_kernel<float><<<nblocks, block, 0, s>>>(probs, tile_prob, pa);
+    else point_kernel<double><<<nblocks, block, 0, s>>>(probs, tile_prob, pa);
+}
+int launch_expm(const ProblemDev* probs, int nprob, int mmax, cudaStream_t s) {
+    const size_t smem = (size_t)7 * mmax * mmax * sizeof(double);
+    if (smem > 48 * 1024) {
+        if (cudaFuncSetAttribute(expm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess)
+            return -1;
+    }
+    expm_kernel<<<nprob, 256, smem, s>>>(probs, nprob);
+    return 0;
+}
+void launch_faber_coeffs(double dt, double gamma, double c0, double c1, int m, double* out,
+                         cudaStream_t s) {
+    const int N = (4 * m > 64) ? 4 * m : 64;
+    faber_coeff_kernel<<<m + 1, 256, 0, s>>>(dt, gamma, c0, c1, m, N, out);
+}
+
+}  // namespace ewv

@@ -1,0 +1,132 @@
+// Arnoldi bookkeeping done by the last-arriving block of a pass (Sec. 3.2, Krylov listing).
+//
+// Basis vectors are kept unnormalised on the grid: slot k holds q_k and v_k = s_k q_k with
+// the scale s_k = 1 / h_{k,k-1} (s_1 = 1/|x|) stored per problem.  The augmented tail of
+// each slot (p entries, Eq. matrix_ampli) is stored unscaled beside it.  A pass writes one
+// partial dot product per block; the block that arrives last (per-problem atomic counter,
+// no waiting) sums the partials in a fixed order -- deterministic -- and runs the scalar
+// step below on one thread.  Modes:
+//   FIN_NORM0   tot = |u_n|^2      -> beta = sqrt(tot + |e_p|^2), s_1, tail_1 = e_p
+//   FIN_MATVEC  tot = <q_{j+1}, q_1> after q_{j+1} = dt H~ v_j
+//               -> tail_{j+1} = J (s_j tail_j), h_{1,j}
+//   FIN_MGS     pass k of step j: q_{j+1} -= h_{k,j} v_k, tot = <q_{j+1}, q_{k+1}> (k < j)
+//               or |q_{j+1}|^2 (k = j) -> h_{k+1,j} or h_{j+1,j}, s_{j+1}, breakdown test
+// The source contribution of the next matrix-vector product, W . tail_j (unscaled), goes to
+// sigma[j].
+#pragma once
+
+#include <math.h>
+
+#include "ewave_internal.cuh"
+
+namespace ewv {
+
+enum { FIN_NONE = 0, FIN_NORM0 = 1, FIN_MATVEC = 2, FIN_MGS = 3 };
+
+__device__ __forceinline__ double* kry_tail(double* kry, int k) {  // k = 1..MAX_M+1
+    return kry + KRY_T + (k - 1) * MAX_P;
+}
+
+__device__ inline void krylov_finalize(const ProblemDev* P, int mode, int j, int k, int m,
+                                       double tol, double tot) {
+    double* kry = P->kry;
+    const int p = P->p;
+    if (!isfinite(tot)) {
+        kry[KRY_NONFINITE] = 1.0;
+        kry[KRY_ACTIVE] = 0.0;
+        return;
+    }
+    if (mode == FIN_NORM0) {
+        double* t1 = kry_tail(kry, 1);
+        for (int q = 0; q < MAX_P; ++q) t1[q] = 0.0;
+        t1[p - 1] = 1.0;
+        const double beta = sqrt(tot + 1.0);
+        kry[KRY_BETA] = beta;
+        kry[KRY_S + 1] = 1.0 / beta;
+        kry[KRY_ACTIVE] = 1.0;
+        kry[KRY_MEFF] = (double)m;
+        double sg = 0.0;
+        for (int q = 0; q < p; ++q) sg += kry[KRY_W + q] * t1[q];
+        P->sigma[1] = P->has_src ? sg : 0.0;
+        for (int r = 0; r < (MAX_M + 1) * MAX_M; ++r) kry[KRY_H + r] = 0.0;
+    } else if (mode == FIN_MATVEC) {
+        const double sj = kry[KRY_S + j];
+        const double* tj = kry_tail(kry, j);
+        double* tw = kry_tail(kry, j + 1);
+        for (int q = 0; q < p - 1; ++q) tw[q] = sj * tj[q + 1];   // J (s_j tail_j)
+        tw[p - 1] = 0.0;
+        const double* t1 = kry_tail(kry, 1);
+        double d = 0.0;
+        for (int q = 0; q < p; ++q) d += tw[q] * t1[q];
+        kry[KRY_H + 0 * MAX_M + (j - 1)] = kry[KRY_S + 1] * (tot + d);
+    } else if (mode == FIN_MGS) {
+        const double hkj = kry[KRY_H + (k - 1) * MAX_M + (j - 1)];
+        const double sk = kry[KRY_S + k];
+        const double* tk = kry_tail(kry, k);
+        double* tw = kry_tail(kry, j + 1);
+        for (int q = 0; q < p; ++q) tw[q] -= hkj * sk * tk[q];
+        if (k < j) {
+            const double* tn = kry_tail(kry, k + 1);
+            double d = 0.0;
+            for (int q = 0; q < p; ++q) d += tw[q] * tn[q];
+            kry[KRY_H + k * MAX_M + (j - 1)] = kry[KRY_S + k + 1] * (tot + d);
+        } else {
+            double d = 0.0;
+            for (int q = 0; q < p; ++q) d += tw[q] * tw[q];
+            const double h = sqrt(tot + d);
+            if (j < m) {
+                kry[KRY_H + j * MAX_M + (j - 1)] = h;
+                if (!(h > tol)) {
+                    kry[KRY_ACTIVE] = 0.0;
+                    kry[KRY_MEFF] = (double)j;
+                } else {
+                    kry[KRY_S + j + 1] = 1.0 / h;
+                    double sg = 0.0;
+                    for (int q = 0; q < p; ++q) sg += kry[KRY_W + q] * tw[q];
+                    P->sigma[j + 1] = P->has_src ? sg : 0.0;
+                }
+            }
+        }
+    }
+}
+
+// Block-wide fixed-order sum of one double per thread (blockDim.x * blockDim.y == NTHREADS).
+__device__ __forceinline__ double block_sum_fixed(double v, double* red) {
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (tid == 0) {
+        for (int w = 0; w < NTHREADS / 32; ++w) s += red[w];
+    }
+    __syncthreads();
+    return s;   // valid on thread 0
+}
+
+// Write this block's partial; if it is the last block of the problem, sum all partials in
+// a fixed order and finalise.  Must be called by all threads of the block.
+__device__ inline void partial_and_finalize(const ProblemDev* P, int pid, const StageArgs& a,
+                                            double block_partial_on_t0, double* red,
+                                            int* s_last) {
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    if (tid == 0) {
+        a.partials[blockIdx.x] = block_partial_on_t0;
+        __threadfence();
+        const unsigned int prev = atomicAdd(a.counters + pid, 1u);
+        *s_last = (prev == (unsigned int)(P->ntiles - 1));
+    }
+    __syncthreads();
+    if (!*s_last) return;
+    __threadfence();
+    double v = 0.0;
+    for (int t = tid; t < P->ntiles; t += NTHREADS) v += __ldcg(a.partials + P->tile_base + t);
+    const double tot = block_sum_fixed(v, red);
+    if (tid == 0) {
+        krylov_finalize(P, a.fin_mode, a.fin_j, a.fin_k, a.m, a.tol, tot);
+        a.counters[pid] = 0u;
+        __threadfence();
+    }
+}
+
+}  // namespace ewv

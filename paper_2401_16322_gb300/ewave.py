@@ -1,0 +1,345 @@
+"""Thin Python binding of the ``libewave.so`` C ABI (include/ewave.h).
+
+Argument marshalling only: every step of the computation runs in the library's CUDA
+kernels.  PyTorch provides device memory (the caller-owned buffers of the ABI) and the CUDA
+stream.  There is no CPU fallback: if the library is missing or no GPU is present, the
+constructors raise.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libewave.so")
+
+EWV_OK = 0
+ERRORS = {
+    -1: "INVALID_ARG", -2: "BAD_SIZE_OR_ALIGNMENT", -3: "WORKSPACE_TOO_SMALL", -4: "CUDA_ERROR",
+    -5: "NONFINITE", -6: "TIMEOUT", -7: "UNSUPPORTED", -8: "NOT_BOUND",
+}
+F32, F64 = 0, 1
+METHOD = {"apply": 0, "faber": 1, "krylov": 2, "hork": 3, "rk32": 4, "rk44": 5, "leapfrog": 6}
+LEAPFROG_AVERAGED, LEAPFROG_LITERAL = 0, 1
+
+# Every symbol include/ewave.h declares (checked by the tests).
+EXPORTS = [
+    "ewv_create_model", "ewv_destroy_model", "ewv_set_stream", "ewv_layout",
+    "ewv_workspace_bytes", "ewv_bind_buffers", "ewv_bind_workspace", "ewv_bind_seismogram",
+    "ewv_reset_recording", "ewv_set_velocity", "ewv_set_source_receivers",
+    "ewv_set_faber_ellipse", "ewv_get_faber_ellipse", "ewv_set_state", "ewv_get_state",
+    "ewv_pack_vector", "ewv_unpack_vector", "ewv_apply_operator", "ewv_step_faber",
+    "ewv_step_krylov", "ewv_step_rk", "ewv_step_leapfrog", "ewv_set_leapfrog_variant",
+    "ewv_create_batch", "ewv_destroy_batch", "ewv_batch_set_stream", "ewv_batch_step_faber",
+    "ewv_batch_step_krylov", "ewv_batch_step_rk", "ewv_batch_step_leapfrog", "ewv_last_error",
+    "ewv_batch_last_error", "ewv_version", "ewv_launch_count",
+]
+
+
+class EwaveError(RuntimeError):
+    pass
+
+
+class ModelDesc(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("dx", ctypes.c_double), ("fd_order", ctypes.c_int), ("pml_width", ctypes.c_int),
+                ("beta0", ctypes.c_double), ("free_surface", ctypes.c_int),
+                ("precision", ctypes.c_int), ("nshots", ctypes.c_int),
+                ("src_taylor_p", ctypes.c_int), ("max_receivers", ctypes.c_int)]
+
+
+class LayoutInfo(ctypes.Structure):
+    _fields_ = [("pitch", ctypes.c_int), ("elem_bytes", ctypes.c_int),
+                ("field_elems", ctypes.c_size_t), ("vector_bytes", ctypes.c_size_t),
+                ("state_bytes", ctypes.c_size_t), ("params_bytes", ctypes.c_size_t),
+                ("compact_n", ctypes.c_size_t)]
+
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libewave.so (in-tree build).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise EwaveError(f"{path} is missing: build it with `python -m paper_2401_16322_gb300.build`")
+    lib = ctypes.CDLL(path)
+    vp, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    dp = ctypes.POINTER(ctypes.c_double)
+    ip32 = ctypes.POINTER(ctypes.c_int32)
+    sig = {
+        "ewv_create_model": ([ctypes.POINTER(ModelDesc), ctypes.POINTER(vp)], i),
+        "ewv_destroy_model": ([vp], i),
+        "ewv_set_stream": ([vp, vp], i),
+        "ewv_layout": ([vp, ctypes.POINTER(LayoutInfo)], i),
+        "ewv_workspace_bytes": ([vp, i, i, ctypes.POINTER(sz)], i),
+        "ewv_bind_buffers": ([vp, vp, sz, vp, sz, vp, sz], i),
+        "ewv_bind_workspace": ([vp, vp, sz], i),
+        "ewv_bind_seismogram": ([vp, vp, sz, i], i),
+        "ewv_reset_recording": ([vp], i),
+        "ewv_set_velocity": ([vp, dp, sz], i),
+        "ewv_set_source_receivers": ([vp, i, d, d, d, d, d, i, dp, ip32, ip32], i),
+        "ewv_set_faber_ellipse": ([vp, d, d, d], i),
+        "ewv_get_faber_ellipse": ([vp, dp, dp, dp], i),
+        "ewv_set_state": ([vp, i, dp, sz], i),
+        "ewv_get_state": ([vp, i, dp, sz], i),
+        "ewv_pack_vector": ([vp, dp, sz, vp], i),
+        "ewv_unpack_vector": ([vp, vp, dp, sz], i),
+        "ewv_apply_operator": ([vp, i, vp, vp], i),
+        "ewv_step_faber": ([vp, d, d, i, i], i),
+        "ewv_step_krylov": ([vp, d, d, i, i, ctypes.POINTER(i)], i),
+        "ewv_step_rk": ([vp, d, d, i, i, i], i),
+        "ewv_step_leapfrog": ([vp, d, d, i], i),
+        "ewv_set_leapfrog_variant": ([vp, i], i),
+        "ewv_create_batch": ([ctypes.POINTER(vp), i, ctypes.POINTER(vp)], i),
+        "ewv_destroy_batch": ([vp], i),
+        "ewv_batch_set_stream": ([vp, vp], i),
+        "ewv_batch_step_faber": ([vp, d, d, i, i], i),
+        "ewv_batch_step_krylov": ([vp, d, d, i, i, ctypes.POINTER(i)], i),
+        "ewv_batch_step_rk": ([vp, d, d, i, i, i], i),
+        "ewv_batch_step_leapfrog": ([vp, d, d, i], i),
+        "ewv_last_error": ([vp], ctypes.c_char_p),
+        "ewv_batch_last_error": ([vp], ctypes.c_char_p),
+        "ewv_version": ([], ctypes.c_char_p),
+        "ewv_launch_count": ([vp, ctypes.POINTER(ctypes.c_longlong)], i),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class Model:
+    """One velocity model with ``nshots`` shots, its device buffers held as torch tensors."""
+
+    def __init__(self, nx, ny, dx, order=8, pml=40, beta0=0.0, free_surface=True,
+                 precision="f32", nshots=1, p=12, max_receivers=0, device=None, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise EwaveError("a CUDA device is required (the library has no CPU path)")
+        self.torch = torch
+        self.lib = load_library()
+        self.device = torch.device(device or "cuda")
+        self.prec = F64 if precision in ("f64", "float64", F64) else F32
+        self.dtype = torch.float64 if self.prec == F64 else torch.float32
+        self.nx, self.ny, self.dx, self.nshots = nx, ny, dx, nshots
+        self.max_receivers = max_receivers
+        d = ModelDesc(2, nx, ny, dx, order, pml, beta0, int(bool(free_surface)), self.prec, nshots,
+                      p, max_receivers)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            self._check(self.lib.ewv_create_model(ctypes.byref(d), ctypes.byref(h)), "create_model")
+        self.h = h
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._check(self.lib.ewv_set_stream(self.h, ctypes.c_void_p(self.stream.cuda_stream)))
+        lay = LayoutInfo()
+        self._check(self.lib.ewv_layout(self.h, ctypes.byref(lay)))
+        self.layout = lay
+        self.n = lay.compact_n
+        ne = lay.elem_bytes
+        self.state = torch.zeros(lay.state_bytes // ne, dtype=self.dtype, device=self.device)
+        self.params = torch.zeros(lay.params_bytes // ne, dtype=self.dtype, device=self.device)
+        self.work = None
+        self.seismo = None
+        self.capacity = 0
+        self._check(self.lib.ewv_bind_buffers(self.h, ctypes.c_void_p(self.state.data_ptr()),
+                                              lay.state_bytes, ctypes.c_void_p(self.params.data_ptr()),
+                                              lay.params_bytes, None, 0))
+
+    # ---------------------------------------------------------------- helpers
+    def _check(self, rc, what=""):
+        if rc != EWV_OK:
+            msg = ""
+            if getattr(self, "h", None) is not None and self.h.value:
+                msg = self.lib.ewv_last_error(self.h).decode()
+            raise EwaveError(f"{what or 'ewave'}: {ERRORS.get(rc, rc)} {msg}")
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.ewv_destroy_model(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def vector_elems(self):
+        return self.layout.vector_bytes // self.layout.elem_bytes
+
+    def new_vector(self):
+        return self.torch.zeros(self.vector_elems, dtype=self.dtype, device=self.device)
+
+    # ---------------------------------------------------------------- inputs
+    def set_velocity(self, c):
+        c = np.ascontiguousarray(c, dtype=np.float64)
+        self._check(self.lib.ewv_set_velocity(self.h, _dptr(c), c.size), "set_velocity")
+
+    def set_source_receivers(self, shot, sx, sy, f_peak, t0, amp=1.0, rec=None):
+        rec = np.zeros((0, 2)) if rec is None else np.ascontiguousarray(rec, dtype=np.float64)
+        nrec = rec.shape[0]
+        si = np.zeros(2, dtype=np.int32)
+        ri = np.zeros(max(2 * nrec, 1), dtype=np.int32)
+        self._check(self.lib.ewv_set_source_receivers(
+            self.h, shot, sx, sy, f_peak, t0, amp, nrec, _dptr(rec) if nrec else None,
+            si.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+            ri.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))), "set_source_receivers")
+        return si, ri[:2 * nrec].reshape(nrec, 2)
+
+    def set_faber_ellipse(self, gamma, c0, c1):
+        self._check(self.lib.ewv_set_faber_ellipse(self.h, gamma, c0, c1))
+
+    def faber_ellipse(self):
+        g, c0, c1 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        self._check(self.lib.ewv_get_faber_ellipse(self.h, ctypes.byref(g), ctypes.byref(c0),
+                                                   ctypes.byref(c1)))
+        return g.value, c0.value, c1.value
+
+    def ensure_workspace(self, method, m=0):
+        need = ctypes.c_size_t()
+        self._check(self.lib.ewv_workspace_bytes(self.h, METHOD[method], m, ctypes.byref(need)))
+        have = 0 if self.work is None else self.work.numel() * self.layout.elem_bytes
+        if need.value > have:
+            self.work = self.torch.zeros(need.value // self.layout.elem_bytes, dtype=self.dtype,
+                                         device=self.device)
+            self._check(self.lib.ewv_bind_workspace(self.h, ctypes.c_void_p(self.work.data_ptr()),
+                                                    need.value))
+
+    def bind_seismogram(self, capacity):
+        n = max(self.nshots * capacity * self.max_receivers, 1)
+        self.seismo = self.torch.zeros(n, dtype=self.dtype, device=self.device)
+        self.capacity = capacity
+        self._check(self.lib.ewv_bind_seismogram(self.h, ctypes.c_void_p(self.seismo.data_ptr()),
+                                                 n * self.layout.elem_bytes, capacity))
+
+    def reset_recording(self):
+        self._check(self.lib.ewv_reset_recording(self.h))
+
+    def seismogram(self, shot, nrec, nsamples):
+        self.stream.synchronize()
+        s = self.seismo.view(self.nshots, self.capacity, self.max_receivers)
+        return s[shot, :nsamples, :nrec].double().cpu().numpy()
+
+    # ---------------------------------------------------------------- state
+    def set_state(self, shot, compact):
+        x = np.ascontiguousarray(compact, dtype=np.float64)
+        self._check(self.lib.ewv_set_state(self.h, shot, _dptr(x), x.size), "set_state")
+
+    def get_state(self, shot):
+        out = np.zeros(self.n)
+        self._check(self.lib.ewv_get_state(self.h, shot, _dptr(out), out.size), "get_state")
+        return out
+
+    def pack(self, compact, dev):
+        x = np.ascontiguousarray(compact, dtype=np.float64)
+        self._check(self.lib.ewv_pack_vector(self.h, _dptr(x), x.size, ctypes.c_void_p(dev.data_ptr())))
+
+    def unpack(self, dev):
+        out = np.zeros(self.n)
+        self._check(self.lib.ewv_unpack_vector(self.h, ctypes.c_void_p(dev.data_ptr()), _dptr(out),
+                                               out.size))
+        return out
+
+    # ---------------------------------------------------------------- compute
+    def apply_device(self, x, y, transpose=False):
+        self._check(self.lib.ewv_apply_operator(self.h, int(transpose), ctypes.c_void_p(x.data_ptr()),
+                                                ctypes.c_void_p(y.data_ptr())), "apply_operator")
+
+    def apply(self, compact, transpose=False):
+        x, y = self.new_vector(), self.new_vector()
+        self.pack(compact, x)
+        self.apply_device(x, y, transpose)
+        return self.unpack(y)
+
+    def step_faber(self, t, dt, degree, nsteps=1):
+        self.ensure_workspace("faber", degree)
+        self._check(self.lib.ewv_step_faber(self.h, t, dt, degree, nsteps), "step_faber")
+
+    def step_krylov(self, t, dt, m, nsteps=1):
+        self.ensure_workspace("krylov", m)
+        info = ctypes.c_int(0)
+        self._check(self.lib.ewv_step_krylov(self.h, t, dt, m, nsteps, ctypes.byref(info)), "step_krylov")
+        return info.value
+
+    def step_rk(self, t, dt, scheme, stages=0, nsteps=1):
+        self.ensure_workspace(scheme, stages)
+        self._check(self.lib.ewv_step_rk(self.h, t, dt, METHOD[scheme], stages, nsteps), "step_rk")
+
+    def step_leapfrog(self, t, dt, nsteps=1, variant=LEAPFROG_AVERAGED):
+        self.ensure_workspace("leapfrog")
+        self._check(self.lib.ewv_set_leapfrog_variant(self.h, variant))
+        self._check(self.lib.ewv_step_leapfrog(self.h, t, dt, nsteps), "step_leapfrog")
+
+    def step(self, method, t, dt, m=0, nsteps=1):
+        if method == "faber":
+            return self.step_faber(t, dt, m, nsteps)
+        if method == "krylov":
+            return self.step_krylov(t, dt, m, nsteps)
+        if method in ("hork", "rk32", "rk44"):
+            return self.step_rk(t, dt, method, m, nsteps)
+        if method == "leapfrog":
+            return self.step_leapfrog(t, dt, nsteps)
+        raise ValueError(method)
+
+    def launch_count(self):
+        c = ctypes.c_longlong()
+        self._check(self.lib.ewv_launch_count(self.h, ctypes.byref(c)))
+        return c.value
+
+
+class Batch:
+    """Several models (uneven sizes allowed) stepped in the same kernel launches."""
+
+    def __init__(self, models, stream=None):
+        self.lib = load_library()
+        self.models = list(models)
+        arr = (ctypes.c_void_p * len(self.models))(*[m.h.value for m in self.models])
+        h = ctypes.c_void_p()
+        rc = self.lib.ewv_create_batch(arr, len(self.models), ctypes.byref(h))
+        if rc != EWV_OK:
+            raise EwaveError(f"create_batch: {ERRORS.get(rc, rc)}")
+        self.h = h
+        if stream is not None:
+            self.lib.ewv_batch_set_stream(self.h, ctypes.c_void_p(stream.cuda_stream))
+
+    def _check(self, rc, what):
+        if rc != EWV_OK:
+            raise EwaveError(f"{what}: {ERRORS.get(rc, rc)} {self.lib.ewv_batch_last_error(self.h).decode()}")
+
+    def step(self, method, t, dt, m=0, nsteps=1):
+        for md in self.models:
+            md.ensure_workspace(method, m)
+        if method == "faber":
+            self._check(self.lib.ewv_batch_step_faber(self.h, t, dt, m, nsteps), "batch_step_faber")
+        elif method == "krylov":
+            info = ctypes.c_int(0)
+            self._check(self.lib.ewv_batch_step_krylov(self.h, t, dt, m, nsteps, ctypes.byref(info)),
+                        "batch_step_krylov")
+            return info.value
+        elif method in ("hork", "rk32", "rk44"):
+            self._check(self.lib.ewv_batch_step_rk(self.h, t, dt, METHOD[method], m, nsteps), "batch_step_rk")
+        elif method == "leapfrog":
+            self._check(self.lib.ewv_batch_step_leapfrog(self.h, t, dt, nsteps), "batch_step_leapfrog")
+        else:
+            raise ValueError(method)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.ewv_destroy_batch(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,122 @@
+"""GPU parity of every time integrator (Sec. 3) against the oracle, through the C ABI:
+Faber, Krylov, HORK (augmented source, Eq. matrix_ampli), RK3-2, RK4-4 and leap-frog,
+in FP64 (1e-12) and FP32 (1e-5 per step), with the source active and receivers recorded."""
+import numpy as np
+import pytest
+
+from _helpers import TOL, flatten, gpu_model, oracle_ellipse, oracle_model, rel_l2
+from oracle import faber, krylov, leapfrog, rk
+from oracle.simulate import receiver_nodes, run
+from oracle.source import PointSource
+from paper_2401_16322_gb300.workloads import layered, smooth_random_state
+
+pytestmark = pytest.mark.gpu
+
+NX, NY = 83, 37          # 2 x 3 tiles, ragged in both directions
+
+
+def _setup(prec, fs=True, order=8, p=10, seed=4):
+    c = layered(NX, NY, seed)
+    om = oracle_model(NX, NY, c, order=order, pml=10, fs=fs)
+    rec = np.array([[x * om.dx, 0.0 if fs else 5 * om.dx] for x in range(3, NX - 3, 7)])
+    g = gpu_model(om, prec, p=p, max_receivers=len(rec))
+    sx, sy = 41 * om.dx + 3.0, (2 if fs else 18) * om.dx
+    src = PointSource(om, sx, sy, 25.0, 0.05, amp=1e3, p=p)
+    si, ri = g.set_source_receivers(0, sx, sy, 25.0, 0.05, 1e3, rec)
+    assert (si[1], si[0]) == (src.j, src.i)
+    rn = receiver_nodes(om, rec)
+    assert np.array_equal(ri[:, ::-1], rn)          # integer indices: bit-exact
+    U0 = tuple(smooth_random_state([f.shape for f in om.zeros_state()], 9))
+    return om, g, src, rec, rn, U0
+
+
+def _gpu_run(g, U0, method, t, dt, m, nsteps, capacity):
+    g.bind_seismogram(capacity)
+    g.set_state(0, flatten(U0))
+    info = g.step(method, t, dt, m, nsteps)
+    return g.get_state(0), info
+
+
+CASES = [("faber", 12), ("faber", 30), ("krylov", 8), ("krylov", 16), ("hork", 1), ("hork", 2),
+         ("hork", 7), ("rk32", 0), ("rk44", 0), ("faber", 1), ("faber", 2), ("krylov", 1)]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("method,m", CASES)
+def test_integrator_matches_oracle(prec, method, m):
+    om, g, src, rec, rn, U0 = _setup(prec)
+    dt, t, nsteps = 1.2e-3, 0.03, 3
+    if method == "faber":
+        g.set_faber_ellipse(*oracle_ellipse(om))
+    gs, _ = _gpu_run(g, U0, method, t, dt, m, nsteps, nsteps)
+    U, S = run(om, method, dt, nsteps, src=src, rec_nodes=rn, m=m, U0=U0, t0=t)
+    err = rel_l2(gs, flatten(U))
+    assert err < TOL[prec] * (3 if prec == "f32" else 1), (method, m, err)
+    Sg = g.seismogram(0, len(rec), nsteps)
+    assert rel_l2(Sg, S) < (TOL[prec] * 3 if prec == "f32" else TOL[prec])
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("variant", ["averaged", "literal"])
+def test_leapfrog_matches_oracle(prec, variant):
+    from paper_2401_16322_gb300.ewave import LEAPFROG_AVERAGED, LEAPFROG_LITERAL
+    om, g, src, rec, rn, U0 = _setup(prec)
+    U0 = (U0[0], np.zeros_like(U0[1]), U0[2], U0[3])
+    dt, t, nsteps = 4e-4, 0.03, 7                    # odd: exercises the final buffer swap
+    g.bind_seismogram(nsteps)
+    g.set_state(0, flatten(U0))
+    g.step_leapfrog(t, dt, nsteps, LEAPFROG_AVERAGED if variant == "averaged" else LEAPFROG_LITERAL)
+    gs = g.get_state(0)
+    U, S = run(om, "leapfrog", dt, nsteps, src=src, rec_nodes=rn, U0=U0, t0=t, lf_variant=variant)
+    n_u = om.nx * om.ny
+    ref = flatten(U)
+    mask = np.ones(om.n, bool)
+    mask[n_u:2 * n_u] = False                        # v is not advanced by leap-frog
+    assert rel_l2(gs[mask], ref[mask]) < TOL[prec] * (3 if prec == "f32" else 1)
+    assert rel_l2(g.seismogram(0, len(rec), nsteps), S) < TOL[prec] * (3 if prec == "f32" else 1)
+    # continuing from the restored buffers gives the same as one longer call
+    g.step_leapfrog(t + nsteps * dt, dt, 2, LEAPFROG_AVERAGED if variant == "averaged" else LEAPFROG_LITERAL)
+    U2, _ = run(om, "leapfrog", dt, nsteps + 2, src=src, rec_nodes=rn, U0=U0, t0=t, lf_variant=variant)
+    assert rel_l2(g.get_state(0)[mask], flatten(U2)[mask]) < TOL[prec] * (3 if prec == "f32" else 1)
+
+
+@pytest.mark.parametrize("order,fs", [(4, False), (8, False)])
+def test_faber_and_krylov_without_free_surface(order, fs):
+    om, g, src, rec, rn, U0 = _setup("f64", fs=fs, order=order)
+    g.set_faber_ellipse(*oracle_ellipse(om))
+    for method, m in (("faber", 20), ("krylov", 12)):
+        gs, _ = _gpu_run(g, U0, method, 0.02, 1.5e-3, m, 2, 2)
+        U, _ = run(om, method, 1.5e-3, 2, src=src, rec_nodes=rn, m=m, U0=U0, t0=0.02)
+        assert rel_l2(gs, flatten(U)) < TOL["f64"], method
+
+
+def test_default_faber_ellipse_matches_oracle_reading():
+    om, g, *_ = _setup("f64")
+    ge = g.faber_ellipse()
+    oe = oracle_ellipse(om)
+    assert np.allclose(ge, oe, rtol=1e-12, atol=0)
+
+
+def test_krylov_breakdown_reports_dimension():
+    """A zero state with no source: |x| = |e_p| and the augmented tail space is only
+    p-dimensional under J, so Arnoldi breaks down early (happy breakdown)."""
+    nx, ny = 20, 18
+    om = oracle_model(nx, ny, layered(nx, ny, 2), pml=4, fs=True)
+    g = gpu_model(om, "f64", p=3)
+    g.set_state(0, np.zeros(om.n))
+    info = g.step_krylov(0.0, 1e-3, 10, 1)
+    assert info == 3
+    assert np.all(g.get_state(0) == 0.0)
+
+
+def test_seismogram_indices_bit_exact():
+    nx, ny = 50, 30
+    om = oracle_model(nx, ny, layered(nx, ny, 2), pml=4, fs=True)
+    g = gpu_model(om, "f32", max_receivers=6)
+    rec = np.array([[0.0, 0.0], [14.999, 4.999], [15.0, 5.0], [490.0, 290.0], [104.9, 0.0], [255.0, 35.0]])
+    si, ri = g.set_source_receivers(0, 245.0, 15.0, 10.0, 0.27, 1.0, rec)
+    ref = receiver_nodes(om, rec)
+    assert np.array_equal(ri[:, ::-1], ref)
+    assert list(si) == [int(np.floor(245.0 / 10 + 0.5)), int(np.floor(15.0 / 10 + 0.5))]
+    with pytest.raises(Exception):
+        g.set_source_receivers(0, -6.0, 15.0, 10.0, 0.27, 1.0, rec)

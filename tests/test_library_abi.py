@@ -1,0 +1,47 @@
+"""The C-ABI library builds, loads and exports every symbol include/ewave.h declares.
+No compute calls: these run without a GPU."""
+import os
+import re
+import subprocess
+import sys
+
+import pytest
+
+
+def _declared(repo_root):
+    txt = open(os.path.join(repo_root, "include", "ewave.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(ewv_[a-z0-9_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib(repo_root):
+    so = os.path.join(repo_root, "paper_2401_16322_gb300", "libewave.so")
+    if not os.path.exists(so):
+        subprocess.run([sys.executable, "-m", "paper_2401_16322_gb300.build"], cwd=repo_root,
+                       check=True)
+    from paper_2401_16322_gb300 import ewave
+    return ewave.load_library()
+
+
+def test_header_declarations_match_binding(repo_root):
+    from paper_2401_16322_gb300 import ewave
+    assert _declared(repo_root) == sorted(ewave.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib, repo_root):
+    for name in _declared(repo_root):
+        assert hasattr(lib, name), name
+
+
+def test_version_string(lib):
+    assert b"sm_103a" in lib.ewv_version()
+
+
+def test_null_handle_errors_without_gpu(lib):
+    # argument checks happen before any CUDA call
+    import ctypes
+    assert lib.ewv_destroy_model(None) == -1
+    assert lib.ewv_set_stream(None, None) == -1
+    assert lib.ewv_last_error(None) == b"null handle"
+    assert lib.ewv_create_model(None, None) == -1
