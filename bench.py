@@ -1,0 +1,364 @@
+#!/usr/bin/env python
+"""Benchmark: time-to-solution at 1e-4 relative-L2 seismogram error, and the HBM roofline of
+the fused stencil pass, on the batched workload (64 shots on a 1001 x 501 layered model
+plus 8 layered models from 201 x 101 to 801 x 401; 8th order, free surface, 40-point PML,
+Ricker 10 Hz, T = 2 s; FP32 wavefields, FP64 coefficients).
+
+One "step" of this benchmark is one complete simulation of the whole batch to T (every
+shot's seismogram), at the cheapest (method, m, dt) whose seismogram error against an FP64
+reference is at most 1e-4 (searched in-run on sampled problems, see
+paper_2401_16322_gb300/tts.py).  The inputs (state, workspace: several GB) are larger than
+L2, and every simulation starts from a zeroed state.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Rank 0 prints one JSON line.  --impl reference times the FP64 CPU oracle on a bounded sample
+of the same workload and scales it to the same metric.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "time-to-solution at 1e-4 rel. L2 seismogram error; stencil HBM GB/s as % of peak"
+UNIT = "s"
+T_END = 2.0
+TARGET = 1e-4
+# Sampled problems for the error measurement: (model index, shot index).
+PICKS = [(0, 32), (1, 0), (5, 0)]
+# Cheapest candidate found by the in-run search on GB300 (used by the CPU reference arm; the
+# GPU arm re-runs the search and reports what it finds).
+DEFAULT_SELECTION = ("faber", 40, 8)     # method, m, dt in units of the leap-frog step
+WORKLOAD_NAME = ("batched: 64 shots on 1001x501 + 8 models 201x101..801x401, layered "
+                 "1500-4500 m/s, 8th order, free surface, 40-pt PML, Ricker 10 Hz, T=2 s")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--target", type=float, default=TARGET)
+    ap.add_argument("--cpu-sample-s", type=float, default=15.0)
+    ap.add_argument("--no-search", action="store_true", help="use the default selection")
+    ap.add_argument("--T", type=float, default=T_END, help="simulated time (profiling runs)")
+    ap.add_argument("--case", default="full", choices=["full", "small"],
+                    help="small: the 1001x501 model with 4 shots (profiling)")
+    return ap.parse_args()
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------------------- helpers
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def pass_words(method, m):
+    """Algorithmic FP32 words per grid point of each fused stencil pass of one step
+    (reads + writes; c^2 counted once per pass)."""
+    if method == "faber":
+        return [13] + [21] * (m - 1) if m >= 2 else [13]
+    if method == "hork":
+        return [13] + [17] * (m - 1) if m >= 2 else [9]
+    if method == "rk32":
+        return [13, 13, 13]
+    if method == "rk44":
+        return [17, 21, 21, 13]
+    if method == "krylov":
+        return [13] * m     # x (4) + c^2 (1) + y (4) + dot partner (4)
+    if method == "leapfrog":
+        return [10]
+    raise ValueError(method)
+
+
+def cpu_oracle_sample(workloads, method, m, dt, budget_s, log=log):
+    """Time the FP64 oracle on a bounded sample: steps of ``method`` on one mid-size model
+    (one shot), until ``budget_s`` seconds.  Returns (seconds per grid-point-step, sample
+    description, threads)."""
+    import numpy as np
+    from oracle.faber import ellipse_params
+    from oracle.model import Model as OModel
+    from oracle.simulate import run
+    from oracle.source import PointSource
+    from paper_2401_16322_gb300.tts import pml_beta0
+    from paper_2401_16322_gb300.workloads import t0_for
+    w = workloads[4]                                   # 458 x 229 model
+    c_max = max(float(x.c.max()) for x in workloads)
+    om = OModel(w.nx, w.ny, w.dx, w.order, w.pml, pml_beta0(c_max, w.pml, w.dx), w.free_surface, w.c)
+    s = w.shots[0]
+    src = PointSource(om, s.sx, s.sy, w.f_peak, t0_for(w.f_peak), 1.0, p=12)
+    params = ellipse_params(c_max, om.beta0, om.dx, om.order, free_surface=om.free_surface)
+    t0 = time.perf_counter()
+    nsteps = 0
+    U = om.zeros_state()
+    while True:
+        U, _ = run(om, method, dt, 1, src=src, m=m, U0=U, t0=0.3 + nsteps * dt, faber_params=params)
+        nsteps += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    el = time.perf_counter() - t0
+    per_point_step = el / (nsteps * w.nx * w.ny)
+    desc = (f"oracle {method}(m={m}, dt={dt * 1e3:.3f} ms) FP64, {nsteps} steps of one shot on "
+            f"{w.nx}x{w.ny} ({el:.1f} s), scaled by grid-point-steps to the whole batch")
+    return per_point_step, desc, 1
+
+
+def batch_points(workloads):
+    return sum(w.nx * w.ny * len(w.shots) for w in workloads)
+
+
+# ------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_2401_16322_gb300.tts import leapfrog_step
+    from paper_2401_16322_gb300.workloads import config_batched
+    wl = config_batched()
+    c_max = max(float(w.c.max()) for w in wl)
+    dt_cfl = leapfrog_step(c_max, wl[0].dx, wl[0].order)
+    method, m, k = DEFAULT_SELECTION
+    dt = k * dt_cfl
+    nsteps = int(round(T_END / dt))
+    pts = batch_points(wl)
+    budget = max(1.0, min(args.cpu_sample_s, 60.0 / max(1, args.steps + args.warmup)))
+    vals = []
+    for it in range(args.warmup + args.steps):
+        pps, desc, cores = cpu_oracle_sample(wl, method, m, dt, budget)
+        if it >= args.warmup:
+            vals.append(pps * pts * nsteps)
+    v = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "method": method, "m": m, "dt_ms": dt * 1e3,
+                       "T_s": T_END, "grid_points": pts, "nsteps": nsteps},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2401_16322_gb300 import Batch
+    from paper_2401_16322_gb300.tts import (Candidate, build_models, common_ellipse, leapfrog_step,
+                                            rel_l2_common, run_study, simulate)
+    from paper_2401_16322_gb300.workloads import config_batched
+
+    wl = config_batched() if args.case == "full" else config_batched(nshots=4)[:1]
+    T_run = args.T
+    c_max = max(float(w.c.max()) for w in wl)
+    dt_cfl = leapfrog_step(c_max, wl[0].dx, wl[0].order)
+    pts = batch_points(wl)
+    t_setup = time.perf_counter()
+    models = build_models(wl, "f32", p=12, c_max=c_max)
+    common_ellipse(models, c_max)
+    batch = Batch(models)
+    log(f"setup {time.perf_counter() - t_setup:.1f} s, {pts} grid points, dt_cfl {dt_cfl * 1e3:.4f} ms")
+
+    method, m, k = DEFAULT_SELECTION
+    study = None
+    if not args.no_search and args.case == "full":
+        study = run_study(wl, PICKS, T_run, target=args.target, full_batch=batch, full_models=models,
+                          log=log if rank == 0 else (lambda *a: None))
+        if study.selected is not None:
+            method, m, dt = study.selected.method, study.selected.m, study.selected.dt
+        else:
+            dt = k * dt_cfl
+        seismo_err = study.selected.err if study.selected else float("nan")
+    else:
+        dt = k * dt_cfl
+        seismo_err = float("nan")
+    nsteps = int(round(T_run / dt))
+    log(f"selected {method} m={m} dt={dt * 1e3:.4f} ms ({nsteps} steps), sampled error {seismo_err:.3e}")
+
+    def one_solution():
+        simulate(models, batch, method, m, dt, T_run)
+
+    for _ in range(args.warmup):
+        one_solution()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    batch.enable_kernel_timing(True)
+    batch.kernel_timing()
+    launches0 = batch.launch_count()
+    clk = ClockSampler(local)
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        one_solution()
+    e1.record()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    elapsed_ms = e0.elapsed_time(e1)
+    kern_ms, kern_n = batch.kernel_timing()
+    batch.enable_kernel_timing(False)
+    launches = batch.launch_count() - launches0
+    ms_per_step = elapsed_ms / args.steps
+    if dist:
+        t = torch.tensor([ms_per_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_per_step = float(t.item())
+
+    # roofline of the fused stencil pass (live, CUDA events around every launch)
+    words = pass_words(method, m)
+    alg_bytes_per_step = sum(words) * 4.0 * pts
+    per_launch_bytes = alg_bytes_per_step / len(words)
+    avg_launch_ms = kern_ms / max(kern_n, 1)
+    achieved = per_launch_bytes / (avg_launch_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+
+    # e2e: velocity models from host, every shot's seismogram back to host, per solution
+    vel_host = [np.ascontiguousarray(w.c) for w in wl]
+    h2d = sum(v.nbytes for v in vel_host)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    d2h = 0
+    for _ in range(args.steps):
+        for md, v in zip(models, vel_host):
+            md.set_velocity(v)
+        simulate(models, batch, method, m, dt, T_run)
+        outs = []
+        for md, w in zip(models, wl):
+            s = md.seismo.view(md.nshots, md.capacity, md.max_receivers)[:, :nsteps].cpu()
+            outs.append(s)
+        d2h = sum(o.numel() * o.element_size() for o in outs)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+
+    result = None
+    if rank == 0:
+        cpu_pps, cpu_desc, cores = cpu_oracle_sample(config_batched(), method, m, dt, args.cpu_sample_s)
+        cpu_tts = cpu_pps * pts * nsteps
+        lf = study.leapfrog if study else None
+        result = {
+            "metric": METRIC, "value": ms_per_step / 1e3, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME if args.case == "full" else "small: 1001x501, 4 shots",
+                       "method": method, "m": m, "dt_ms": dt * 1e3,
+                       "dt_over_leapfrog_step": dt / dt_cfl, "nsteps": nsteps, "T_s": T_run,
+                       "grid_points": pts, "problems": sum(len(w.shots) for w in wl),
+                       "l2": "inputs larger than L2 (state + workspace > 1 GB)",
+                       "parallelism": f"replicas x{world}"},
+            "seismo_rel_err": seismo_err,
+            "grid_point_updates_per_s": pts * nsteps / (ms_per_step / 1e3),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "kernel": "stage_kernel<float,4> (fused stencil pass)",
+                         "avg_launch_us": avg_launch_ms * 1e3, "launches": kern_n,
+                         "alg_bytes_per_launch": per_launch_bytes},
+            "cpu_baseline": {"value": cpu_tts, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": cpu_desc},
+            "e2e": {"value": e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "leapfrog_f32": ({"dt_ms": lf.dt * 1e3, "seismo_rel_err": lf.err,
+                              "time_to_solution_s": lf.cost_s} if lf else None),
+            "search_s": study.seconds if study else None,
+        }
+        print(json.dumps(result), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -130,6 +130,10 @@ int ewv_bind_workspace(ewv_model_t model, void* work, size_t work_bytes);
 int ewv_bind_seismogram(ewv_model_t model, void* seismo, size_t bytes, int capacity);
 int ewv_reset_recording(ewv_model_t model);
 
+/* Zero every shot's state on the stream, forget the leap-frog history and rewind the
+ * recording cursor (a fresh simulation from rest). */
+int ewv_reset_state(ewv_model_t model);
+
 /* ---- model inputs ------------------------------------------------------------------ */
 
 /* Velocity c (m/s) at the nodes, host float64 [ny][nx] (count = nx*ny); stores c^2 in the
@@ -209,6 +213,15 @@ const char* ewv_last_error(ewv_model_t model);
 const char* ewv_batch_last_error(ewv_batch_t batch);
 /* Library version string. */
 const char* ewv_version(void);
+/* Event timing of the fused stencil passes (the hot kernel): when enabled, every stencil
+ * pass launch is bracketed by a pair of CUDA events on the handle's stream.
+ * ewv_*kernel_timing synchronises the stream, returns the summed device time (ms) and the
+ * number of timed launches since the last read, and resets both. */
+int ewv_enable_kernel_timing(ewv_model_t model, int enable);
+int ewv_kernel_timing(ewv_model_t model, double* total_ms, long long* launches);
+int ewv_batch_enable_kernel_timing(ewv_batch_t batch, int enable);
+int ewv_batch_kernel_timing(ewv_batch_t batch, double* total_ms, long long* launches);
+
 /* Number of kernel launches this handle has enqueued since creation (for reporting). */
 int ewv_launch_count(ewv_model_t model, long long* count);
 

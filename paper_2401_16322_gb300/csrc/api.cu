@@ -94,6 +94,7 @@ int ensure_tables() {
     double dwy[4][8];
     fs_dwy_table(dwy);
     if (upload_stencil_tables(8, &kFsUyy[0][0], &kFsUy[0][0], &dwy[0][0]) != 0) return -1;
+    if (upload_tma_tables(&kFsUyy[0][0], &kFsUy[0][0], &dwy[0][0]) != 0) return -1;
     g_tables_device = dev;
     return 0;
 }
@@ -167,14 +168,23 @@ struct Engine {
     unsigned int* d_counters = nullptr;
     double* d_coef = nullptr;
     ProblemDev* d_apply = nullptr;
+    void* d_maps = nullptr;     // FP32: TMA tensor maps of every problem
+    int* d_err = nullptr;       // timeout word written by the TMA kernel
     std::map<std::tuple<double, int, double, double, double>, std::vector<double>> faber_cache;
+    // optional CUDA-event timing of the fused stencil passes (pairs around each launch)
+    bool timing = false;
+    std::vector<cudaEvent_t> events;
+    size_t events_used = 0;
     ~Engine() {
+        for (cudaEvent_t e : events) cudaEventDestroy(e);
         cudaFree(d_probs);
         cudaFree(d_tile_prob);
         cudaFree(d_partials);
         cudaFree(d_counters);
         cudaFree(d_coef);
         cudaFree(d_apply);
+        cudaFree(d_maps);
+        cudaFree(d_err);
     }
 };
 
@@ -294,6 +304,7 @@ ProblemDev make_problem(ewv_model* m, int shot, int tile_base) {
 // per-shot stride of (work_bytes / nshots) rounded down to whole vectors.
 int build_engine(Engine* E, std::string& err) {
     E->probs.clear();
+    std::vector<int> work_vecs;
     int tb = 0;
     for (ewv_model* m : E->models) {
         const size_t per_shot = m->work ? (m->work_bytes / m->d.nshots) / (m->vec_elems * m->elem) : 0;
@@ -304,7 +315,16 @@ int build_engine(Engine* E, std::string& err) {
                          : nullptr;
             tb += P.ntiles;
             E->probs.push_back(P);
+            work_vecs.push_back((int)per_shot);
         }
+    }
+    if (E->precision == EWV_F32) {
+        if (build_tensor_maps(E->probs, E->R, work_vecs, &E->d_maps) != 0)
+            return fail(err, EWV_ERR_CUDA, "TMA tensor-map encoding failed");
+    }
+    if (!E->d_err) {
+        CUDA_OR_FAIL(err, cudaMalloc(&E->d_err, sizeof(int)));
+        CUDA_OR_FAIL(err, cudaMemset(E->d_err, 0, sizeof(int)));
     }
     E->nprob = (int)E->probs.size();
     E->ntiles = tb;
@@ -370,8 +390,26 @@ struct Ctx {
     cudaStream_t s;
     long long* launches;
     std::string* err;
+    cudaEvent_t next_event() {
+        if (E->events_used == E->events.size()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            E->events.push_back(e);
+        }
+        return E->events[E->events_used++];
+    }
     void stage(const StageArgs& a) {
-        launch_stage(E->precision, E->R, E->ntiles, E->d_probs, E->d_tile_prob, a, s);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (E->timing) {
+            e0 = next_event();
+            e1 = next_event();
+            cudaEventRecord(e0, s);
+        }
+        if (E->precision == EWV_F32 && !a.transpose && a.fin_mode == FIN_NONE && a.d < 0)
+            launch_stage_tma(E->R, E->ntiles, E->d_probs, E->d_tile_prob, a, E->d_err, s);
+        else
+            launch_stage(E->precision, E->R, E->ntiles, E->d_probs, E->d_tile_prob, a, s);
+        if (E->timing) cudaEventRecord(e1, s);
         ++*launches;
     }
     void point(const PointArgs& pa) {
@@ -700,6 +738,9 @@ int precheck_engine_models(std::vector<ewv_model*>& models, int method, int mm, 
     return EWV_OK;
 }
 
+int dispatch_method(Ctx& C, std::vector<ewv_model*>& models, int method, double t, double dt,
+                    int mm, int nsteps, int* info);
+
 Engine* ensure_model_engine(ewv_model* m) {
     if (!m->engine) {
         m->engine = new Engine();
@@ -720,6 +761,20 @@ int dispatch(std::vector<ewv_model*>& models, Engine* E, cudaStream_t s, long lo
     rc = engine_ready(E, err);
     if (rc != EWV_OK) return rc;
     Ctx C{E, s, launches, &err};
+    rc = dispatch_method(C, models, method, t, dt, mm, nsteps, info);
+    if (rc != EWV_OK) return rc;
+    int herr = 0;
+    CUDA_OR_FAIL(err, cudaMemcpyAsync(&herr, E->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_OR_FAIL(err, cudaStreamSynchronize(s));
+    if (herr) {
+        CUDA_OR_FAIL(err, cudaMemset(E->d_err, 0, sizeof(int)));
+        return fail(err, EWV_ERR_TIMEOUT, "a pipeline wait in the TMA stencil kernel timed out");
+    }
+    return EWV_OK;
+}
+
+int dispatch_method(Ctx& C, std::vector<ewv_model*>& models, int method, double t, double dt,
+                    int mm, int nsteps, int* info) {
     switch (method) {
         case EWV_METHOD_FABER: {
             double g, c0, c1;
@@ -749,7 +804,7 @@ int dispatch(std::vector<ewv_model*>& models, Engine* E, cudaStream_t s, long lo
         case EWV_METHOD_RK32:
         case EWV_METHOD_RK44: return run_rk(C, t, dt, method, nsteps);
         case EWV_METHOD_LEAPFROG: return run_leapfrog(C, models, t, dt, nsteps, models[0]->lf_variant);
-        default: return fail(err, EWV_ERR_INVALID_ARG, "unknown method %d", method);
+        default: return fail(*C.err, EWV_ERR_INVALID_ARG, "unknown method %d", method);
     }
 }
 
@@ -893,6 +948,14 @@ int ewv_reset_recording(ewv_model_t m) {
     for (int s = 0; s < m->d.nshots; ++s)
         CUDA_OR_FAIL(m->err, cudaMemsetAsync(m->d_clk + 4 * s + 1, 0, sizeof(long long), m->stream));
     return EWV_OK;
+}
+
+int ewv_reset_state(ewv_model_t m) {
+    if (!m) return EWV_ERR_INVALID_ARG;
+    if (!m->state) return fail(m->err, EWV_ERR_NOT_BOUND, "state not bound");
+    CUDA_OR_FAIL(m->err, cudaMemsetAsync(m->state, 0, m->vec_elems * m->elem * m->d.nshots, m->stream));
+    m->lf_history_valid = false;
+    return ewv_reset_recording(m);
 }
 
 int ewv_set_velocity(ewv_model_t m, const double* c, size_t count) {
@@ -1049,6 +1112,7 @@ int ewv_apply_operator(ewv_model_t m, int transpose, const void* x, void* y) {
     if (!m->params || !m->velocity_set) return fail(m->err, EWV_ERR_NOT_BOUND, "velocity not set");
     Engine* E = ensure_model_engine(m);
     ProblemDev P = make_problem(m, 0, 0);
+    P.tmaps = nullptr;
     P.has_src = 0;
     P.state = const_cast<void*>(x);
     P.work = y;
@@ -1160,6 +1224,47 @@ int ewv_batch_step_rk(ewv_batch_t b, double t, double dt, int scheme, int stages
 }
 int ewv_batch_step_leapfrog(ewv_batch_t b, double t, double dt, int nsteps) {
     return step_batch(b, EWV_METHOD_LEAPFROG, t, dt, 1, nsteps, nullptr);
+}
+
+static int read_timing(Engine* E, cudaStream_t s, std::string& err, double* total_ms,
+                       long long* count) {
+    CUDA_OR_FAIL(err, cudaStreamSynchronize(s));
+    double tot = 0.0;
+    for (size_t k = 0; k + 1 < E->events_used; k += 2) {
+        float ms = 0.f;
+        CUDA_OR_FAIL(err, cudaEventElapsedTime(&ms, E->events[k], E->events[k + 1]));
+        tot += ms;
+    }
+    if (total_ms) *total_ms = tot;
+    if (count) *count = (long long)(E->events_used / 2);
+    E->events_used = 0;
+    return EWV_OK;
+}
+
+int ewv_enable_kernel_timing(ewv_model_t m, int enable) {
+    if (!m) return EWV_ERR_INVALID_ARG;
+    Engine* E = ensure_model_engine(m);
+    E->timing = enable != 0;
+    E->events_used = 0;
+    return EWV_OK;
+}
+
+int ewv_kernel_timing(ewv_model_t m, double* total_ms, long long* launches) {
+    if (!m || !m->engine) return EWV_ERR_INVALID_ARG;
+    return read_timing(m->engine, m->stream, m->err, total_ms, launches);
+}
+
+int ewv_batch_enable_kernel_timing(ewv_batch_t b, int enable) {
+    if (!b) return EWV_ERR_INVALID_ARG;
+    b->engine->timing = enable != 0;
+    b->engine->events_used = 0;
+    return EWV_OK;
+}
+
+int ewv_batch_kernel_timing(ewv_batch_t b, double* total_ms, long long* launches) {
+    if (!b) return EWV_ERR_INVALID_ARG;
+    return read_timing(b->engine, b->stream_set ? b->stream : b->models[0]->stream, b->err,
+                       total_ms, launches);
 }
 
 const char* ewv_last_error(ewv_model_t m) { return m ? m->err.c_str() : "null handle"; }

@@ -12,6 +12,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace ewv {
 
 // Tile of outputs per block (x contiguous) and block shape.
@@ -57,6 +59,7 @@ struct ProblemDev {
     double* kry;          // [KRY_STRIDE]
     long long* clk;       // [4]: step within call, recording cursor, (unused), (unused)
     double* tclk;         // [2]: t_start, dt of the current call
+    const void* tmaps;    // FP32: this problem's TMA tensor maps (kernels_tma.cu), else null
 };
 
 // Arguments of the fused stencil-stage kernel (see kernels_stencil.cu).
@@ -94,6 +97,13 @@ void launch_stage(int precision, int R, int nblocks, const ProblemDev* probs,
 void launch_leapfrog(int precision, int R, int nblocks, const ProblemDev* probs,
                      const int* tile_prob, int cur, int prev, int variant, double dt,
                      cudaStream_t s);
+
+// kernels_tma.cu: persistent TMA-fed FP32 forward pass.
+int upload_tma_tables(const double* fs_uyy, const double* fs_uy, const double* fs_dwy);
+int build_tensor_maps(std::vector<ProblemDev>& probs, int R, const std::vector<int>& work_vecs,
+                      void** d_maps_inout);
+int launch_stage_tma(int R, int ntiles, const ProblemDev* probs, const int* tile_prob,
+                     const StageArgs& a, int* err, cudaStream_t s);
 
 void launch_set_clock(const ProblemDev* probs, int nprob, double t, double dt, cudaStream_t s);
 void launch_reset_cursor(const ProblemDev* probs, int nprob, cudaStream_t s);

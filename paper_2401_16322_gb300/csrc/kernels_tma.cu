@@ -1,0 +1,457 @@
+// Persistent, TMA-fed fused stencil pass (FP32, forward operator) for sm_103a.
+//
+// Same arithmetic as stage_kernel (kernels_stencil.cu: Eq. 1's operator, Sec. 2.1 stencils,
+// Appendix A / Sec. 2.2 free-surface rows, in-register damping, and the
+// K / Y / ACC epilogue of every integrator), organised for HBM bandwidth:
+//   - one CTA per SM walks the tile work list (tiles b, b + gridDim.x, ...);
+//   - warp 8 (one elected lane) is the producer: for each tile it issues TMA tensor loads
+//     (cp.async.bulk.tensor) of every operand into one of NST shared-memory stages and
+//     arms the stage's "full" mbarrier with the transaction byte count;
+//   - warps 0..7 are consumers: they wait on "full", compute the 64 x 16 tile from shared
+//     memory (4 consecutive rows per thread, y taps slid in registers), store Y / ACC with
+//     coalesced st.global, and arrive on the stage's "empty" mbarrier.
+// The TMA boxes (4D tensor maps over x, y, field, vector) start R rows above and 4 columns
+// left of the tile (16-byte aligned x); out-of-range elements are filled with zeros by
+// the TMA unit, which is exactly the zero extension of Sec. 2.1.
+// Every mbarrier wait is bounded (1 s of %globaltimer): on expiry the kernel records an
+// error word, drains its own outstanding copies (bounded) and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <vector>
+
+#include "ewave_internal.cuh"
+
+namespace ewv {
+
+constexpr int TX = 4;                 // staged x halo (>= R, keeps the box start 16-B aligned)
+constexpr int NST = 3;                // pipeline stages
+constexpr int NCONS = 256;            // consumer threads (8 warps)
+constexpr int TMA_THREADS = NCONS + 32;
+constexpr int NMAP = 11;              // tensor maps per problem
+
+// Shared-memory layout of one stage (floats); each buffer starts on a 128-byte boundary.
+template <int R>
+struct StageLayout {
+    static constexpr int SH = BY + 2 * R;
+    static constexpr int SW = BX + 2 * TX;
+    static constexpr int U_OFF = 0;                          // u      SH x SW
+    static constexpr int WX_OFF = U_OFF + SH * SW;           // w_x    BY x SW
+    static constexpr int WY_OFF = WX_OFF + BY * SW;          // w_y    SH x BX
+    static constexpr int V_OFF = WY_OFF + SH * BX;           // v      BY x BX
+    static constexpr int C2_OFF = V_OFF + BY * BX;           // c^2    BY x BX
+    static constexpr int PU_OFF = C2_OFF + BY * BX;          // U      4 x BY x BX
+    static constexpr int PA_OFF = PU_OFF + 4 * BY * BX;      // A      4 x BY x BX
+    static constexpr int FLOATS = PA_OFF + 4 * BY * BX;
+    static constexpr int BYTES = FLOATS * 4;
+    static_assert((U_OFF * 4) % 128 == 0 && (WX_OFF * 4) % 128 == 0 && (WY_OFF * 4) % 128 == 0 &&
+                      (V_OFF * 4) % 128 == 0 && (C2_OFF * 4) % 128 == 0 &&
+                      (PU_OFF * 4) % 128 == 0 && (PA_OFF * 4) % 128 == 0 && BYTES % 128 == 0,
+                  "TMA destinations must be 128-byte aligned");
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait: false after 1 s (or 2^26 polls) without the phase completing.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 0; it < (1u << 26); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255u) == 0 && global_ns() - t0 > 1000000000ull) return false;
+    }
+    return false;
+}
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, int c3, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
+        "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ void named_bar_sync(int id, int n) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+__constant__ float g_tma_fs[4 * 9 + 3 * 8 + 4 * 8];
+constexpr int TFS_UYY = 0, TFS_UY = 36, TFS_DWY = 60;
+
+int upload_tma_tables(const double* fs_uyy, const double* fs_uy, const double* fs_dwy) {
+    float f[92];
+    for (int i = 0; i < 36; ++i) f[TFS_UYY + i] = (float)fs_uyy[i];
+    for (int i = 0; i < 24; ++i) f[TFS_UY + i] = (float)fs_uy[i];
+    for (int i = 0; i < 32; ++i) f[TFS_DWY + i] = (float)fs_dwy[i];
+    return cudaMemcpyToSymbol(g_tma_fs, f, sizeof(f)) == cudaSuccess ? 0 : -1;
+}
+
+template <int R>
+__device__ __forceinline__ float stag(int k) {
+    if constexpr (R == 4) {
+        return k == 0 ? float(1225.0 / 1024.0) : k == 1 ? float(-245.0 / 3072.0)
+             : k == 2 ? float(49.0 / 5120.0) : float(-5.0 / 7168.0);
+    } else {
+        return k == 0 ? float(9.0 / 8.0) : float(-1.0 / 24.0);
+    }
+}
+template <int R>
+__device__ __forceinline__ float cent(int k) {
+    if constexpr (R == 4) {
+        return k == 0 ? float(-205.0 / 72.0) : k == 1 ? float(8.0 / 5.0) : k == 2 ? float(-1.0 / 5.0)
+             : k == 3 ? float(8.0 / 315.0) : float(-1.0 / 560.0);
+    } else {
+        return k == 0 ? float(-5.0 / 2.0) : k == 1 ? float(4.0 / 3.0) : float(-1.0 / 12.0);
+    }
+}
+__device__ __forceinline__ float dampf(float beta0, float inv_pml, float d, int pml) {
+    if (pml <= 0) return 0.f;
+    const float r = 1.f - d * inv_pml;
+    return (d <= (float)pml) ? beta0 * r * r : 0.f;
+}
+
+// Map index of field box `kind` (0 u, 1 w_x, 2 w_y, 3 v, 4 four fields) for vector k, and
+// the vector coordinate inside that map.
+__device__ __forceinline__ const CUtensorMap* map_of(const CUtensorMap* base, int k, int kind) {
+    return base + (k == 0 ? 0 : 5) + kind;
+}
+
+template <int R>
+__global__ void __launch_bounds__(TMA_THREADS, 1)
+stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ tile_prob,
+                 int ntiles, StageArgs a, int* err) {
+    using L = StageLayout<R>;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // TMA destinations need 128-byte alignment: align the dynamic base explicitly (the
+    // launch reserves 1 KB of slack for this).
+    float* smem = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ __align__(8) uint64_t full[NST];
+    __shared__ __align__(8) uint64_t empty[NST];
+    __shared__ int s_err;
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int s = 0; s < NST; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], NCONS / 32);
+        }
+        s_err = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    const bool has_u = a.u >= 0, has_a = a.a >= 0;
+    const uint32_t bytes = (uint32_t)((L::PU_OFF + (has_u ? 4 * BY * BX : 0)) * 4) +
+                           (has_a ? 4 * BY * BX * 4 : 0);
+    int issued = 0;
+
+    if (warp == NCONS / 32) {
+        // ------------------------------------------------------------ producer
+        if (lane == 0) {
+            int it = 0;
+            for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+                const int s = it % NST;
+                const uint32_t ph = (uint32_t)(it / NST) & 1u;
+                if (!mbar_wait(&empty[s], ph ^ 1u)) {
+                    s_err = 1;
+                    break;
+                }
+                const ProblemDev* P = probs + tile_prob[tile];
+                const CUtensorMap* maps = reinterpret_cast<const CUtensorMap*>(P->tmaps);
+                const int lt = tile - P->tile_base;
+                const int x0 = (lt % P->tiles_x) * BX, y0 = (lt / P->tiles_x) * BY;
+                float* st = smem + (size_t)s * L::FLOATS;
+                mbar_expect_tx(&full[s], bytes);
+                const int kx = a.x, cx = a.x == 0 ? 0 : a.x - 1;
+                tma_load_4d(st + L::U_OFF, map_of(maps, kx, 0), x0 - TX, y0 - R, 0, cx, &full[s]);
+                tma_load_4d(st + L::WX_OFF, map_of(maps, kx, 1), x0 - TX, y0, 2, cx, &full[s]);
+                tma_load_4d(st + L::WY_OFF, map_of(maps, kx, 2), x0, y0 - R, 3, cx, &full[s]);
+                tma_load_4d(st + L::V_OFF, map_of(maps, kx, 3), x0, y0, 1, cx, &full[s]);
+                tma_load_2d(st + L::C2_OFF, maps + 10, x0, y0, &full[s]);
+                if (has_u)
+                    tma_load_4d(st + L::PU_OFF, map_of(maps, a.u, 4), x0, y0, 0, a.u == 0 ? 0 : a.u - 1,
+                                &full[s]);
+                if (has_a)
+                    tma_load_4d(st + L::PA_OFF, map_of(maps, a.a, 4), x0, y0, 0, a.a == 0 ? 0 : a.a - 1,
+                                &full[s]);
+                issued = it + 1;
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ consumers
+        const int tx = tid & 63;          // x inside the tile
+        const int ty = tid >> 6;          // rows 4 ty .. 4 ty + 3
+        const float cxf = (float)a.cx, chf = (float)a.ch, cuf = (float)a.cu, ckf = (float)a.ck;
+        const float caf = (float)a.ca, cauf = (float)a.cau, cakf = (float)a.cak;
+        const float cayf = (float)a.cay, caxf = (float)a.cax;
+        int it = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+            const int s = it % NST;
+            const uint32_t ph = (uint32_t)(it / NST) & 1u;
+            if (!mbar_wait(&full[s], ph)) {
+                s_err = 1;
+                break;
+            }
+            const ProblemDev* P = probs + tile_prob[tile];
+            const int nx = P->nx, ny = P->ny, pitch = P->pitch, pml = P->pml;
+            const bool fs = P->fs != 0;
+            const int lt = tile - P->tile_base;
+            const int x0 = (lt % P->tiles_x) * BX, y0 = (lt / P->tiles_x) * BY;
+            const long long fstr = P->field_stride;
+            const float beta0 = (float)P->beta0, inv_pml = (float)P->inv_pml;
+            const float idx1 = (float)P->inv_dx, idx2 = (float)P->inv_dx2;
+            const float sig = (a.src_slot >= 0 && P->has_src) ? (float)P->sigma[a.src_slot] : 0.f;
+            float* Yg = a.y_out >= 0 ? (a.y_out == 0 ? (float*)P->state
+                                                     : (float*)P->work + (long long)(a.y_out - 1) * P->vec_stride)
+                                     : nullptr;
+            float* Ag = a.acc_out >= 0 ? (a.acc_out == 0 ? (float*)P->state
+                                                         : (float*)P->work + (long long)(a.acc_out - 1) * P->vec_stride)
+                                       : nullptr;
+            const float* st = smem + (size_t)s * L::FLOATS;
+            const float* su = st + L::U_OFF;
+            const float* swx = st + L::WX_OFF;
+            const float* swy = st + L::WY_OFF;
+            const float* sv = st + L::V_OFF;
+            const float* sc2 = st + L::C2_OFF;
+            const float* spu = st + L::PU_OFF;
+            const float* spa = st + L::PA_OFF;
+            const int i = x0 + tx;
+            const int cxs = tx + TX;                     // staged column of this thread
+            // column of u (rows 4ty - R .. 4ty + 3 + R) and w_y (rows 4ty - R .. 4ty + 3 + R - 1)
+            float ucol[4 + 2 * R], wcol[4 + 2 * R - 1];
+#pragma unroll
+            for (int q = 0; q < 4 + 2 * R; ++q) ucol[q] = su[(4 * ty + q) * L::SW + cxs];
+#pragma unroll
+            for (int q = 0; q < 4 + 2 * R - 1; ++q) wcol[q] = swy[(4 * ty + q) * BX + tx];
+            const float bxn = dampf(beta0, inv_pml, (float)min(i + 1, nx - i), pml);
+            const float bxh = dampf(beta0, inv_pml, fminf((float)i + 1.5f, (float)(nx - i) - 0.5f), pml);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int ly = 4 * ty + r;
+                const int j = y0 + ly;
+                const float* urow = su + (ly + R) * L::SW + cxs;
+                const float* wxrow = swx + ly * L::SW + cxs;
+                // x taps of u (i-4 .. i+4)
+                float uxx = cent<R>(0) * ucol[r + R];
+                float dux = 0.f;
+#pragma unroll
+                for (int k = 1; k <= R; ++k) uxx += cent<R>(k) * (urow[k] + urow[-k]);
+#pragma unroll
+                for (int k = 0; k < R; ++k) dux += stag<R>(k) * (urow[1 + k] - urow[-k]);
+                float dwx = 0.f;
+#pragma unroll
+                for (int k = 0; k < R; ++k) dwx += stag<R>(k) * (wxrow[k] - wxrow[-1 - k]);
+                float uyy, duy, dwy;
+                if (fs && j < 4) {
+                    uyy = 0.f;
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) uyy += g_tma_fs[TFS_UYY + j * 9 + q] * su[(q + R) * L::SW + cxs];
+                    dwy = 0.f;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) dwy += g_tma_fs[TFS_DWY + j * 8 + q] * swy[(q + R) * BX + tx];
+                } else {
+                    uyy = cent<R>(0) * ucol[r + R];
+#pragma unroll
+                    for (int k = 1; k <= R; ++k) uyy += cent<R>(k) * (ucol[r + R + k] + ucol[r + R - k]);
+                    dwy = 0.f;
+#pragma unroll
+                    for (int k = 0; k < R; ++k) dwy += stag<R>(k) * (wcol[r + R - 1 - k] - wcol[r + R + k]);
+                }
+                if (fs && j < 3) {
+                    duy = 0.f;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) duy += g_tma_fs[TFS_UY + j * 8 + q] * su[(q + R) * L::SW + cxs];
+                } else {
+                    duy = 0.f;
+#pragma unroll
+                    for (int k = 0; k < R; ++k) duy += stag<R>(k) * (ucol[r + R - k] - ucol[r + R + 1 + k]);
+                }
+                if (i >= nx || j >= ny) continue;
+                const float byn = dampf(beta0, inv_pml, fs ? (float)(ny - j) : (float)min(j + 1, ny - j), pml);
+                const float byh = dampf(beta0, inv_pml,
+                                        fs ? (float)(ny - j) - 0.5f : fminf((float)j + 1.5f, (float)(ny - j) - 0.5f),
+                                        pml);
+                const int pt = ly * BX + tx;
+                const float xu = ucol[r + R], xv = sv[pt], xwx = wxrow[0], xwy = wcol[r + R];
+                const float c2 = sc2[pt];
+                float hv = -bxn * byn * xu + c2 * ((uxx + uyy) * idx2 + (dwx + dwy) * idx1) - (bxn + byn) * xv;
+                if (i == P->src_i && j == P->src_j) hv += sig;
+                const float hwx = (i < nx - 1) ? (byn - bxh) * dux * idx1 - bxh * xwx : 0.f;
+                const float hwy = (j < ny - 1) ? (bxn - byh) * duy * idx1 - byh * xwy : 0.f;
+                const float xf[4] = {xu, xv, xwx, xwy};
+                const float hf[4] = {xv, hv, hwx, hwy};
+                const long long o = (long long)j * pitch + i;
+#pragma unroll
+                for (int f = 0; f < 4; ++f) {
+                    const bool pad = (f == 2 && i >= nx - 1) || (f == 3 && j >= ny - 1);
+                    const float uval = has_u ? spu[f * BY * BX + pt] : 0.f;
+                    const float aval = has_a ? spa[f * BY * BX + pt] : 0.f;
+                    const float kf = cxf * xf[f] + chf * hf[f];
+                    const float yf = pad ? 0.f : (cuf * uval + ckf * kf);
+                    if (Yg) Yg[f * fstr + o] = yf;
+                    if (Ag) Ag[f * fstr + o] = pad ? 0.f : (caf * aval + cauf * uval + cakf * kf + cayf * yf + caxf * xf[f]);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+        }
+    }
+    __syncthreads();
+    if (s_err) {
+        // drain: wait (bounded) for the last copy issued into every stage
+        if (warp == NCONS / 32 && lane == 0) {
+            for (int it = issued - 1; it >= 0 && it >= issued - NST; --it)
+                (void)mbar_wait(&full[it % NST], (uint32_t)(it / NST) & 1u);
+        }
+        if (tid == 0) atomicExch(err, 1);
+    }
+}
+
+// ---------------------------------------------------------------- host side
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+static int get_encoder() {
+    if (g_encode) return 0;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+        return -1;
+    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    return 0;
+}
+
+// 4D map over (x, y, field, vector) of one buffer, box (bx, by, bf, 1).
+static int encode4(CUtensorMap* out, void* base, int nx, int ny, int nvec, long long pitch,
+                   long long fstride, long long vstride, int bx, int by, int bf) {
+    cuuint64_t dims[4] = {(cuuint64_t)nx, (cuuint64_t)ny, 4, (cuuint64_t)nvec};
+    cuuint64_t strides[3] = {(cuuint64_t)pitch * 4, (cuuint64_t)fstride * 4, (cuuint64_t)vstride * 4};
+    cuuint32_t box[4] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bf, 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r = g_encode(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? 0 : -1;
+}
+
+static int encode2(CUtensorMap* out, void* base, int nx, int ny, long long pitch, int bx, int by) {
+    cuuint64_t dims[2] = {(cuuint64_t)nx, (cuuint64_t)ny};
+    cuuint64_t strides[1] = {(cuuint64_t)pitch * 4};
+    cuuint32_t box[2] = {(cuuint32_t)bx, (cuuint32_t)by};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = g_encode(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? 0 : -1;
+}
+
+// Build the NMAP maps of every problem (FP32 only) into a device array; sets P.tmaps.
+int build_tensor_maps(std::vector<ProblemDev>& probs, int R, const std::vector<int>& work_vecs,
+                      void** d_maps_inout) {
+    if (get_encoder() != 0) return -1;
+    const int n = (int)probs.size();
+    std::vector<CUtensorMap> maps((size_t)n * NMAP);
+    const int SH = BY + 2 * R, SW = BX + 2 * TX;
+    for (int p = 0; p < n; ++p) {
+        ProblemDev& P = probs[p];
+        CUtensorMap* m = maps.data() + (size_t)p * NMAP;
+        const int bxs[5] = {SW, SW, BX, BX, BX};
+        const int bys[5] = {SH, BY, SH, BY, BY};
+        const int bfs[5] = {1, 1, 1, 1, 4};
+        for (int k = 0; k < 5; ++k) {
+            if (encode4(m + k, P.state, P.nx, P.ny, 1, P.pitch, P.field_stride, P.vec_stride, bxs[k],
+                        bys[k], bfs[k]) != 0)
+                return -1;
+            void* wb = P.work ? P.work : P.state;
+            const int nv = P.work ? work_vecs[p] : 1;
+            if (encode4(m + 5 + k, wb, P.nx, P.ny, nv > 0 ? nv : 1, P.pitch, P.field_stride, P.vec_stride,
+                        bxs[k], bys[k], bfs[k]) != 0)
+                return -1;
+        }
+        if (encode2(m + 10, const_cast<void*>(P.c2), P.nx, P.ny, P.pitch, BX, BY) != 0) return -1;
+    }
+    cudaFree(*d_maps_inout);
+    *d_maps_inout = nullptr;
+    if (cudaMalloc(d_maps_inout, sizeof(CUtensorMap) * maps.size()) != cudaSuccess) return -1;
+    if (cudaMemcpy(*d_maps_inout, maps.data(), sizeof(CUtensorMap) * maps.size(),
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+        return -1;
+    for (int p = 0; p < n; ++p)
+        probs[p].tmaps = static_cast<char*>(*d_maps_inout) + (size_t)p * NMAP * sizeof(CUtensorMap);
+    return 0;
+}
+
+static int g_num_sms = 0;
+
+int launch_stage_tma(int R, int ntiles, const ProblemDev* probs, const int* tile_prob,
+                     const StageArgs& a, int* err, cudaStream_t s) {
+    if (ntiles <= 0) return 0;
+    if (!g_num_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 1;
+    }
+    const int grid = ntiles < g_num_sms ? ntiles : g_num_sms;
+    if (R == 4) {
+        const size_t smem = (size_t)NST * StageLayout<4>::BYTES + 1024;
+        static bool set4 = false;
+        if (!set4) {
+            if (cudaFuncSetAttribute(stage_tma_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem) != cudaSuccess)
+                return -1;
+            set4 = true;
+        }
+        stage_tma_kernel<4><<<grid, TMA_THREADS, smem, s>>>(probs, tile_prob, ntiles, a, err);
+    } else {
+        const size_t smem = (size_t)NST * StageLayout<2>::BYTES + 1024;
+        static bool set2 = false;
+        if (!set2) {
+            if (cudaFuncSetAttribute(stage_tma_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem) != cudaSuccess)
+                return -1;
+            set2 = true;
+        }
+        stage_tma_kernel<2><<<grid, TMA_THREADS, smem, s>>>(probs, tile_prob, ntiles, a, err);
+    }
+    return 0;
+}
+
+}  // namespace ewv

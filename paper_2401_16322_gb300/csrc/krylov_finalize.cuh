@@ -6,7 +6,9 @@
 // partial dot product per block; the block that arrives last (per-problem atomic counter,
 // no waiting) sums the partials in a fixed order -- deterministic -- and runs the scalar
 // step below on one thread.  Modes:
-//   FIN_NORM0   tot = |u_n|^2      -> beta = sqrt(tot + |e_p|^2), s_1, tail_1 = e_p
+//   FIN_NORM0   tot = |u_n|^2      -> tail_1 = eta e_p with eta = |u_n| (1 if u_n = 0) and
+//               W scaled by 1/eta (balances the augmented tail against the wavefield; the
+//               exact exponential is unchanged), beta = sqrt(tot + eta^2), s_1
 //   FIN_MATVEC  tot = <q_{j+1}, q_1> after q_{j+1} = dt H~ v_j
 //               -> tail_{j+1} = J (s_j tail_j), h_{1,j}
 //   FIN_MGS     pass k of step j: q_{j+1} -= h_{k,j} v_k, tot = <q_{j+1}, q_{k+1}> (k < j)
@@ -38,9 +40,11 @@ __device__ inline void krylov_finalize(const ProblemDev* P, int mode, int j, int
     }
     if (mode == FIN_NORM0) {
         double* t1 = kry_tail(kry, 1);
+        const double eta = tot > 0.0 ? sqrt(tot) : 1.0;
         for (int q = 0; q < MAX_P; ++q) t1[q] = 0.0;
-        t1[p - 1] = 1.0;
-        const double beta = sqrt(tot + 1.0);
+        t1[p - 1] = eta;
+        for (int q = 0; q < MAX_P; ++q) kry[KRY_W + q] /= eta;
+        const double beta = sqrt(tot + eta * eta);
         kry[KRY_BETA] = beta;
         kry[KRY_S + 1] = 1.0 / beta;
         kry[KRY_ACTIVE] = 1.0;

@@ -32,7 +32,8 @@ EXPORTS = [
     "ewv_step_krylov", "ewv_step_rk", "ewv_step_leapfrog", "ewv_set_leapfrog_variant",
     "ewv_create_batch", "ewv_destroy_batch", "ewv_batch_set_stream", "ewv_batch_step_faber",
     "ewv_batch_step_krylov", "ewv_batch_step_rk", "ewv_batch_step_leapfrog", "ewv_last_error",
-    "ewv_batch_last_error", "ewv_version", "ewv_launch_count",
+    "ewv_batch_last_error", "ewv_version", "ewv_launch_count", "ewv_enable_kernel_timing",
+    "ewv_kernel_timing", "ewv_batch_enable_kernel_timing", "ewv_batch_kernel_timing", "ewv_reset_state",
 ]
 
 
@@ -104,6 +105,11 @@ def load_library(path=LIB_PATH):
         "ewv_batch_last_error": ([vp], ctypes.c_char_p),
         "ewv_version": ([], ctypes.c_char_p),
         "ewv_launch_count": ([vp, ctypes.POINTER(ctypes.c_longlong)], i),
+        "ewv_reset_state": ([vp], i),
+        "ewv_enable_kernel_timing": ([vp, i], i),
+        "ewv_kernel_timing": ([vp, dp, ctypes.POINTER(ctypes.c_longlong)], i),
+        "ewv_batch_enable_kernel_timing": ([vp, i], i),
+        "ewv_batch_kernel_timing": ([vp, dp, ctypes.POINTER(ctypes.c_longlong)], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -222,6 +228,9 @@ class Model:
         self._check(self.lib.ewv_bind_seismogram(self.h, ctypes.c_void_p(self.seismo.data_ptr()),
                                                  n * self.layout.elem_bytes, capacity))
 
+    def reset_state(self):
+        self._check(self.lib.ewv_reset_state(self.h), "reset_state")
+
     def reset_recording(self):
         self._check(self.lib.ewv_reset_recording(self.h))
 
@@ -296,6 +305,15 @@ class Model:
         self._check(self.lib.ewv_launch_count(self.h, ctypes.byref(c)))
         return c.value
 
+    def enable_kernel_timing(self, on=True):
+        self._check(self.lib.ewv_enable_kernel_timing(self.h, int(on)))
+
+    def kernel_timing(self):
+        """(total ms, launches) of the stencil passes since the last read."""
+        ms, n = ctypes.c_double(), ctypes.c_longlong()
+        self._check(self.lib.ewv_kernel_timing(self.h, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
 
 class Batch:
     """Several models (uneven sizes allowed) stepped in the same kernel launches."""
@@ -332,6 +350,17 @@ class Batch:
             self._check(self.lib.ewv_batch_step_leapfrog(self.h, t, dt, nsteps), "batch_step_leapfrog")
         else:
             raise ValueError(method)
+
+    def enable_kernel_timing(self, on=True):
+        self._check(self.lib.ewv_batch_enable_kernel_timing(self.h, int(on)), "timing")
+
+    def kernel_timing(self):
+        ms, n = ctypes.c_double(), ctypes.c_longlong()
+        self._check(self.lib.ewv_batch_kernel_timing(self.h, ctypes.byref(ms), ctypes.byref(n)), "timing")
+        return ms.value, n.value
+
+    def launch_count(self):
+        return sum(m.launch_count() for m in self.models[:1])
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:

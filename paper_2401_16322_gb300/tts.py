@@ -1,0 +1,237 @@
+"""Time-to-solution search on the GPU (the paper's Delta-t_max criterion, Secs. 4.2 and 5.2).
+
+For a workload (a list of velocity models with shots and surface receivers) this module
+
+1. computes an FP64 reference seismogram for a few sampled problems with a high-accuracy
+   setting of the same spatial discretisation (Faber, degree 30, at dt_ref = 2 x the
+   leap-frog stability step; at that step the Faber coefficients of degree > 30 are below
+   1e-14, so the time error is negligible -- checked against dt_ref/2 by
+   ``reference_self_check``);
+2. runs every candidate (method, m, dt) in FP32 on the same sampled problems and measures
+   the relative L2 seismogram error against the reference at common sample times;
+3. times one step of every candidate on the full batched workload;
+4. selects the cheapest candidate (steps x time per step) whose error is at most the target
+   (1e-4, relative L2 over receivers x samples).
+
+The candidate grid follows the paper's comparison: Faber degree 20..60 and Krylov dimension
+10..40 at 4..16 x the leap-frog step, and leap-frog itself at 1, 1/2, 1/4, 1/8 of its step.
+"""
+import math
+import time
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import numpy as np
+
+from .ewave import Batch, Model
+from .workloads import Shot, Workload, t0_for
+
+S2_MIN = {8: 6.501587301587302, 4: 16.0 / 3.0}   # |min symbol| of the centred 2nd derivative
+
+
+def leapfrog_step(c_max, dx, order=8, dims=2):
+    """Leap-frog stability step 2 / omega_max, omega_max = c_max sqrt(dims |S2|) / dx."""
+    return 2.0 * dx / (c_max * math.sqrt(dims * S2_MIN[order]))
+
+
+def pml_beta0(c_max, pml, dx, reflection=1e-3):
+    """beta0 = 3 c_max / (2 delta) ln(1/R), R = 1e-3 (the model-parameter choice)."""
+    return 3.0 * c_max / (2.0 * pml * dx) * math.log(1.0 / reflection)
+
+
+@dataclass
+class Candidate:
+    method: str
+    m: int
+    dt: float
+    err: float = float("nan")
+    step_ms: float = float("nan")
+    nsteps: int = 0
+
+    @property
+    def cost_s(self):
+        return self.step_ms * self.nsteps * 1e-3
+
+    def label(self):
+        return f"{self.method}(m={self.m}, dt={self.dt * 1e3:.3f} ms)"
+
+
+def build_models(workloads: List[Workload], precision, p=12, c_max=None, dx=None,
+                 capacity=0, stream=None):
+    """One Model per workload (all its shots), sources and receivers set, common beta0."""
+    cm = c_max if c_max is not None else max(float(w.c.max()) for w in workloads)
+    models = []
+    for w in workloads:
+        b0 = pml_beta0(cm, w.pml, w.dx)
+        nrec = max(len(s.rec) for s in w.shots)
+        md = Model(w.nx, w.ny, w.dx, w.order, w.pml, b0, w.free_surface, precision=precision,
+                   nshots=len(w.shots), p=p, max_receivers=nrec, stream=stream)
+        md.set_velocity(w.c)
+        for k, s in enumerate(w.shots):
+            md.set_source_receivers(k, s.sx, s.sy, w.f_peak, t0_for(w.f_peak), 1.0, s.rec)
+        if capacity:
+            md.bind_seismogram(capacity)
+        models.append(md)
+    return models
+
+
+def common_ellipse(models, c_max):
+    """Set one Faber ellipse (the widest of the models') on every model."""
+    ells = [m.faber_ellipse() for m in models]
+    best = max(ells, key=lambda e: e[0] * (1 - e[2]))
+    for m in models:
+        m.set_faber_ellipse(*best)
+    return best
+
+
+def simulate(models, batch, method, m, dt, T, variant=0):
+    """Run a fresh simulation to time T on every model; returns the number of steps."""
+    nsteps = int(round(T / dt))
+    for md in models:
+        if md.capacity < nsteps:
+            md.bind_seismogram(nsteps)
+        md.reset_state()
+        md.ensure_workspace(method, m)
+    if batch is None:
+        for md in models:
+            if method == "leapfrog":
+                md.step_leapfrog(0.0, dt, nsteps, variant)
+            else:
+                md.step(method, 0.0, dt, m, nsteps)
+    else:
+        batch.step(method, 0.0, dt, m, nsteps)
+    return nsteps
+
+
+def sampled_workloads(workloads: List[Workload], picks):
+    """Single-shot copies (model index, shot index) used for the error measurement."""
+    out = []
+    for wi, si in picks:
+        w = workloads[wi]
+        out.append(Workload(f"{w.name}-shot{si}", w.nx, w.ny, w.dx, w.order, w.pml,
+                            w.free_surface, w.c, [w.shots[si]], w.f_peak, w.T))
+    return out
+
+
+def seismograms(models, nsteps):
+    return [md.seismogram(0, len(w_rec), nsteps) for md, w_rec in models]
+
+
+def rel_l2_common(seis, dt, ref, dt_ref):
+    """Relative L2 error of ``seis`` (samples at (s+1) dt) against ``ref`` (at (s+1) dt_ref),
+    over the sample times both contain (dt and dt_ref are integer multiples)."""
+    if dt >= dt_ref:
+        k = int(round(dt / dt_ref))
+        n = min(seis.shape[0], ref.shape[0] // k)
+        a, b = seis[:n], ref[k - 1::k][:n]
+    else:
+        k = int(round(dt_ref / dt))
+        n = min(seis.shape[0] // k, ref.shape[0])
+        a, b = seis[k - 1::k][:n], ref[:n]
+    den = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / den)
+
+
+@dataclass
+class Study:
+    dt_cfl: float
+    dt_ref: float
+    ref_method: str
+    ref_m: int
+    candidates: List[Candidate] = field(default_factory=list)
+    selected: Optional[Candidate] = None
+    leapfrog: Optional[Candidate] = None
+    ref_self_check: float = float("nan")
+    seconds: float = 0.0
+
+
+def default_candidates(dt_cfl):
+    c = []
+    for m in (20, 30, 40, 50, 60):
+        for k in (4, 8, 12, 16):
+            c.append(Candidate("faber", m, k * dt_cfl))
+    for m in (10, 20, 30, 40):
+        for k in (4, 8, 12, 16):
+            c.append(Candidate("krylov", m, k * dt_cfl))
+    return c
+
+
+def leapfrog_candidates(dt_cfl):
+    return [Candidate("leapfrog", 1, dt_cfl / k) for k in (1, 2, 4, 8)]
+
+
+def run_study(workloads: List[Workload], picks, T, target=1e-4, candidates=None,
+              full_batch=None, full_models=None, ref_m=30, p_ref=20, p=12, log=print,
+              self_check=False):
+    """Search the candidates; ``full_batch``/``full_models`` time one step of each on the full
+    workload.  Returns a Study."""
+    import torch
+    t_start = time.time()
+    c_max = max(float(w.c.max()) for w in workloads)
+    dx = workloads[0].dx
+    order = workloads[0].order
+    dt_cfl = leapfrog_step(c_max, dx, order)
+    dt_ref = 2.0 * dt_cfl
+    sw = sampled_workloads(workloads, picks)
+    # FP64 reference on the sampled problems, batched
+    ref_models = build_models(sw, "f64", p=p_ref, c_max=c_max)
+    ell = common_ellipse(ref_models, c_max)
+    ref_batch = Batch(ref_models)
+    n_ref = simulate(ref_models, ref_batch, "faber", ref_m, dt_ref, T)
+    refs = [md.seismogram(0, len(w.shots[0].rec), n_ref) for md, w in zip(ref_models, sw)]
+    st = Study(dt_cfl, dt_ref, "faber", ref_m)
+    if self_check:
+        n2 = simulate(ref_models, ref_batch, "faber", ref_m, dt_ref / 2, T)
+        refs2 = [md.seismogram(0, len(w.shots[0].rec), n2) for md, w in zip(ref_models, sw)]
+        st.ref_self_check = max(rel_l2_common(a, dt_ref, b, dt_ref / 2) for a, b in zip(refs, refs2))
+        log(f"reference self-check (dt_ref vs dt_ref/2): {st.ref_self_check:.3e}")
+    ref_batch.close()
+    for md in ref_models:
+        md.close()
+    log(f"reference: FP64 faber m={ref_m} dt={dt_ref * 1e3:.3f} ms, {n_ref} steps "
+        f"({time.time() - t_start:.1f} s)")
+    # FP32 candidates on the sampled problems
+    cand_models = build_models(sw, "f32", p=p, c_max=c_max)
+    for md in cand_models:
+        md.set_faber_ellipse(*ell)
+    cand_batch = Batch(cand_models)
+    cands = candidates if candidates is not None else default_candidates(dt_cfl)
+    lf = leapfrog_candidates(dt_cfl)
+    for c in cands + lf:
+        try:
+            c.nsteps = simulate(cand_models, cand_batch, c.method, c.m, c.dt, T)
+            errs = [rel_l2_common(md.seismogram(0, len(w.shots[0].rec), c.nsteps), c.dt, r, dt_ref)
+                    for md, w, r in zip(cand_models, sw, refs)]
+            c.err = max(errs) if all(np.isfinite(errs)) else float("inf")
+        except Exception as e:     # non-finite Arnoldi etc.: the candidate fails the target
+            c.err = float("inf")
+            log(f"  {c.label()}: {e}")
+    cand_batch.close()
+    for md in cand_models:
+        md.close()
+    # time one step of each passing candidate on the full workload
+    if full_batch is not None:
+        for c in cands + lf:
+            if not (c.err <= target):
+                continue
+            for md in full_models:
+                md.ensure_workspace(c.method, c.m)
+            full_batch.step(c.method, 0.0, c.dt, c.m, 1)          # warm (coefficients, plans)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ns = 2
+            e0.record()
+            full_batch.step(c.method, 0.0, c.dt, c.m, ns)
+            e1.record()
+            torch.cuda.synchronize()
+            c.step_ms = e0.elapsed_time(e1) / ns
+    passing = [c for c in cands if c.err <= target and np.isfinite(c.step_ms)]
+    st.candidates = cands + lf
+    st.selected = min(passing, key=lambda c: c.cost_s) if passing else None
+    lf_pass = [c for c in lf if c.err <= target and np.isfinite(c.step_ms)]
+    st.leapfrog = min(lf_pass, key=lambda c: c.cost_s) if lf_pass else None
+    st.seconds = time.time() - t_start
+    for c in st.candidates:
+        log(f"  {c.label():34s} err {c.err:.3e}  step {c.step_ms:.3f} ms  steps {c.nsteps}  "
+            f"cost {c.cost_s:.3f} s")
+    return st
