@@ -25,6 +25,7 @@ __global__ void set_clock_kernel(const ProblemDev* probs, int nprob, double t, d
     P->clk[0] = 0;
     P->tclk[0] = t;
     P->tclk[1] = dt;
+    P->kry[KRY_NONFINITE] = 0.0;   // the flag reports non-finite values within one call
 }
 
 __global__ void reset_cursor_kernel(const ProblemDev* probs, int nprob) {
@@ -34,22 +35,9 @@ __global__ void reset_cursor_kernel(const ProblemDev* probs, int nprob) {
 }
 
 // ---------------------------------------------------------------- source scalars
-// Ricker r(tau) = (1 - 2 a tau^2) exp(-a tau^2), a = (pi f)^2 (Sec. 4.1); derivatives
-// r^(k) = -g^(k+2) / (2a) with g = exp(-a tau^2) and the Hermite recurrence
-// g^(k) = -2 a tau g^(k-1) - 2 a (k-1) g^(k-2).
-__device__ void ricker_derivs(double t, double f, double t0, int p, double* out) {
-    const double a = (M_PI * f) * (M_PI * f);
-    const double tau = t - t0;
-    double gm2 = exp(-a * tau * tau);       // g^(k-2)
-    double gm1 = -2.0 * a * tau * gm2;      // g^(k-1)
-    for (int k = 2; k < p + 2; ++k) {
-        const double g = -2.0 * a * tau * gm1 - 2.0 * a * (double)(k - 1) * gm2;
-        out[k - 2] = -g / (2.0 * a);
-        gm2 = gm1;
-        gm1 = g;
-    }
-}
-
+// Ricker r(tau) = (1 - 2 a tau^2) exp(-a tau^2), a = (pi f)^2 (Sec. 4.1).  Its derivatives
+// (prologue_kernel) follow r^(k) = -g^(k+2) / (2a), g = exp(-a tau^2), with the Hermite
+// recurrence g^(k) = -2 a tau g^(k-1) - 2 a (k-1) g^(k-2).
 __device__ __forceinline__ double ricker(double t, double f, double t0) {
     const double a = (M_PI * f) * (M_PI * f);
     const double tau = t - t0;
@@ -58,87 +46,99 @@ __device__ __forceinline__ double ricker(double t, double f, double t0) {
 
 enum { PRO_FABER = 1, PRO_KRYLOV = 2, PRO_HORK = 3, PRO_RK32 = 4, PRO_RK44 = 5, PRO_LEAPFROG = 6 };
 
-// One thread per problem.  Fills sigma[] (the value added at the source node's v entry in
+// One warp per problem.  Fills sigma[] (the value added at the source node's v entry in
 // each pass of this step) from t_n = t_start + step * dt:
 //   Faber: sigma_j = W . y_j, y_0 = e_p, y_1 = F1 y_0, y_2 = F1 y_1 - 2 c1 y_0,
 //          y_j = F1 y_{j-1} - c1 y_{j-2}, F1 = (J/dt)/gamma - c0 (tail of Eq. matrix_ampli)
 //   HORK:  sigma_i = W . (I + J)^i e_p
 //   RK3-2 / RK4-4 / leap-frog: f at the stage times
 //   Krylov: W stored for the Arnoldi passes
-// W[p-1-k] = dt^k r^(k)(t_n) amp / dx^2 (tail scaled by dt).
+// W[p-1-k] = dt^k r^(k)(t_n) amp / dx^2 (tail scaled by dt).  Lane q holds tail entry q;
+// the shift J (J y)_q = y_{q+1} is a warp shuffle, each W . y a warp reduction.
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 __global__ void prologue_kernel(const ProblemDev* probs, int nprob, int kind, int m,
                                 double gamma, double c0, double c1) {
-    const int pid = blockIdx.x * blockDim.x + threadIdx.x;
-    if (pid >= nprob) return;
+    const int pid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int q = threadIdx.x & 31;
+    if (pid >= nprob) return;           // whole warps exit together
     const ProblemDev* P = probs + pid;
     const double dt = P->tclk[1];
     const double tn = P->tclk[0] + (double)P->clk[0] * dt;
     double* sg = P->sigma;
     if (!P->has_src) {
-        for (int s = 0; s < MAX_SIGMA; ++s) sg[s] = 0.0;
-        if (kind == PRO_KRYLOV)
-            for (int q = 0; q < MAX_P; ++q) P->kry[KRY_W + q] = 0.0;
+        for (int s = q; s < MAX_SIGMA; s += 32) sg[s] = 0.0;
+        if (kind == PRO_KRYLOV && q < MAX_P) P->kry[KRY_W + q] = 0.0;
         return;
     }
     const double scale = P->amp * P->inv_dx2;
-    if (kind == PRO_RK32) {
-        sg[0] = scale * ricker(tn, P->f_peak, P->t0);
-        sg[1] = sg[2] = scale * ricker(tn + 0.5 * dt, P->f_peak, P->t0);
-        return;
-    }
-    if (kind == PRO_RK44) {
-        sg[0] = scale * ricker(tn, P->f_peak, P->t0);
-        sg[1] = sg[2] = scale * ricker(tn + 0.5 * dt, P->f_peak, P->t0);
-        sg[3] = scale * ricker(tn + dt, P->f_peak, P->t0);
-        return;
-    }
-    if (kind == PRO_LEAPFROG) {
-        sg[0] = scale * ricker(tn, P->f_peak, P->t0);
+    if (kind == PRO_RK32 || kind == PRO_RK44 || kind == PRO_LEAPFROG) {
+        if (q == 0) {
+            if (kind == PRO_LEAPFROG) {
+                sg[0] = scale * ricker(tn, P->f_peak, P->t0);
+            } else {
+                sg[0] = scale * ricker(tn, P->f_peak, P->t0);
+                sg[1] = sg[2] = scale * ricker(tn + 0.5 * dt, P->f_peak, P->t0);
+                if (kind == PRO_RK44) sg[3] = scale * ricker(tn + dt, P->f_peak, P->t0);
+            }
+        }
         return;
     }
     const int p = P->p;
-    double r[MAX_P], W[MAX_P];
-    ricker_derivs(tn, P->f_peak, P->t0, p, r);
-    double dk = 1.0;
-    for (int k = 0; k < p; ++k) {
-        W[p - 1 - k] = dk * r[k] * scale;
-        dk *= dt;
+    // W_q = dt^k r^(k)(t_n) scale with k = p-1-q: every lane runs the Hermite recurrence
+    // g^(k) = -2 a tau g^(k-1) - 2 a (k-1) g^(k-2) and keeps its own term.
+    const int kq = p - 1 - q;
+    const double a = (M_PI * P->f_peak) * (M_PI * P->f_peak);
+    const double tau = tn - P->t0;
+    double gm2 = exp(-a * tau * tau), gm1 = -2.0 * a * tau * gm2, rk = 0.0, dk = 1.0;
+    for (int k = 2; k < p + 2; ++k) {
+        const double g = -2.0 * a * tau * gm1 - 2.0 * a * (double)(k - 1) * gm2;
+        if (k - 2 == kq) rk = -g / (2.0 * a);
+        gm2 = gm1;
+        gm1 = g;
     }
+    for (int k = 0; k < kq && kq >= 0; ++k) dk *= dt;
+    const double W = (q < p) ? dk * rk * scale : 0.0;
     if (kind == PRO_KRYLOV) {
-        for (int q = 0; q < MAX_P; ++q) P->kry[KRY_W + q] = q < p ? W[q] : 0.0;
+        if (q < MAX_P) P->kry[KRY_W + q] = W;
         return;
     }
-    double y0[MAX_P], y1[MAX_P], y2[MAX_P];
-    for (int q = 0; q < p; ++q) y0[q] = 0.0;
-    y0[p - 1] = 1.0;
-    auto dotW = [&](const double* y) {
-        double s = 0.0;
-        for (int q = 0; q < p; ++q) s += W[q] * y[q];
-        return s;
-    };
+    double y0 = (q == p - 1) ? 1.0 : 0.0;
     if (kind == PRO_HORK) {
         // y_i = (I + J) y_{i-1}
         for (int i = 0; i < m && i < MAX_SIGMA; ++i) {
-            sg[i] = dotW(y0);
-            for (int q = 0; q < p; ++q) y1[q] = y0[q] + (q + 1 < p ? y0[q + 1] : 0.0);
-            for (int q = 0; q < p; ++q) y0[q] = y1[q];
+            const double s = warp_sum(W * y0);
+            if (q == 0) sg[i] = s;
+            double up = __shfl_down_sync(0xffffffffu, y0, 1);
+            if (q + 1 >= p) up = 0.0;
+            y0 = y0 + up;
         }
         return;
     }
     // Faber
     const double ig = 1.0 / gamma;
-    sg[0] = dotW(y0);
-    for (int q = 0; q < p; ++q) y1[q] = ig * (q + 1 < p ? y0[q + 1] : 0.0) / dt - c0 * y0[q];
-    if (m >= 2) sg[1] = dotW(y1);
+    auto F1 = [&](double y) {
+        double up = __shfl_down_sync(0xffffffffu, y, 1);
+        if (q + 1 >= p) up = 0.0;
+        return ig * up / dt - c0 * y;
+    };
+    double s0 = warp_sum(W * y0);
+    if (q == 0) sg[0] = s0;
+    double y1 = F1(y0);
+    if (m >= 2) {
+        const double s1 = warp_sum(W * y1);
+        if (q == 0) sg[1] = s1;
+    }
     for (int j = 2; j < m && j < MAX_SIGMA; ++j) {
         const double cj = (j == 2) ? 2.0 * c1 : c1;
-        for (int q = 0; q < p; ++q)
-            y2[q] = ig * (q + 1 < p ? y1[q + 1] : 0.0) / dt - c0 * y1[q] - cj * y0[q];
-        sg[j] = dotW(y2);
-        for (int q = 0; q < p; ++q) {
-            y0[q] = y1[q];
-            y1[q] = y2[q];
-        }
+        const double y2 = F1(y1) - cj * y0;
+        const double sj = warp_sum(W * y2);
+        if (q == 0) sg[j] = sj;
+        y0 = y1;
+        y1 = y2;
     }
 }
 
@@ -469,7 +469,7 @@ void launch_reset_cursor(const ProblemDev* probs, int nprob, cudaStream_t s) {
 }
 void launch_prologue(const ProblemDev* probs, int nprob, int kind, int m, double gamma,
                      double c0, double c1, cudaStream_t s) {
-    prologue_kernel<<<(nprob + 63) / 64, 64, 0, s>>>(probs, nprob, kind, m, gamma, c0, c1);
+    prologue_kernel<<<(nprob + 3) / 4, 128, 0, s>>>(probs, nprob, kind, m, gamma, c0, c1);
 }
 void launch_record(int precision, const ProblemDev* probs, int nprob, int vec, cudaStream_t s) {
     if (precision == 0) record_kernel<float><<<nprob, 128, 0, s>>>(probs, nprob, vec);

@@ -7,8 +7,8 @@
 //   - warp 8 (one elected lane) is the producer: for each tile it issues TMA tensor loads
 //     (cp.async.bulk.tensor) of every operand into one of NST shared-memory stages and
 //     arms the stage's "full" mbarrier with the transaction byte count;
-//   - warps 0..7 are consumers: they wait on "full", compute the 64 x 16 tile from shared
-//     memory (4 consecutive rows per thread, y taps slid in registers), store Y / ACC with
+//   - warps 0..15 are consumers: they wait on "full", compute the 64 x 16 tile from shared
+//     memory (2 consecutive rows per thread, y taps slid in registers), store Y / ACC with
 //     coalesced st.global, and arrive on the stage's "empty" mbarrier.
 // The TMA boxes (4D tensor maps over x, y, field, vector) start R rows above and 4 columns
 // left of the tile (16-byte aligned x); out-of-range elements are filled with zeros by
@@ -26,7 +26,8 @@ namespace ewv {
 
 constexpr int TX = 4;                 // staged x halo (>= R, keeps the box start 16-B aligned)
 constexpr int NST = 3;                // pipeline stages
-constexpr int NCONS = 256;            // consumer threads (8 warps)
+constexpr int NCONS = 512;            // consumer threads (16 warps)
+constexpr int NR = BY / (NCONS / BX); // consecutive rows per consumer thread (2)
 constexpr int TMA_THREADS = NCONS + 32;
 constexpr int NMAP = 11;              // tensor maps per problem
 
@@ -216,8 +217,8 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
         }
     } else {
         // ------------------------------------------------------------ consumers
-        const int tx = tid & 63;          // x inside the tile
-        const int ty = tid >> 6;          // rows 4 ty .. 4 ty + 3
+        const int tx = tid & (BX - 1);    // x inside the tile
+        const int ty = tid / BX;          // rows NR ty .. NR ty + NR - 1
         const float cxf = (float)a.cx, chf = (float)a.ch, cuf = (float)a.cu, ckf = (float)a.ck;
         const float caf = (float)a.ca, cauf = (float)a.cau, cakf = (float)a.cak;
         const float cayf = (float)a.cay, caxf = (float)a.cax;
@@ -238,6 +239,7 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
             const float beta0 = (float)P->beta0, inv_pml = (float)P->inv_pml;
             const float idx1 = (float)P->inv_dx, idx2 = (float)P->inv_dx2;
             const float sig = (a.src_slot >= 0 && P->has_src) ? (float)P->sigma[a.src_slot] : 0.f;
+            const int src_i = P->src_i, src_j = P->src_j;
             float* Yg = a.y_out >= 0 ? (a.y_out == 0 ? (float*)P->state
                                                      : (float*)P->work + (long long)(a.y_out - 1) * P->vec_stride)
                                      : nullptr;
@@ -254,21 +256,21 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
             const float* spa = st + L::PA_OFF;
             const int i = x0 + tx;
             const int cxs = tx + TX;                     // staged column of this thread
-            // column of u (rows 4ty - R .. 4ty + 3 + R) and w_y (rows 4ty - R .. 4ty + 3 + R - 1)
-            float ucol[4 + 2 * R], wcol[4 + 2 * R - 1];
+            // column of u (staged rows NR ty .. NR ty + NR - 1 + 2R) and of w_y (one fewer)
+            float ucol[NR + 2 * R], wcol[NR + 2 * R - 1];
 #pragma unroll
-            for (int q = 0; q < 4 + 2 * R; ++q) ucol[q] = su[(4 * ty + q) * L::SW + cxs];
+            for (int q = 0; q < NR + 2 * R; ++q) ucol[q] = su[(NR * ty + q) * L::SW + cxs];
 #pragma unroll
-            for (int q = 0; q < 4 + 2 * R - 1; ++q) wcol[q] = swy[(4 * ty + q) * BX + tx];
+            for (int q = 0; q < NR + 2 * R - 1; ++q) wcol[q] = swy[(NR * ty + q) * BX + tx];
             const float bxn = dampf(beta0, inv_pml, (float)min(i + 1, nx - i), pml);
             const float bxh = dampf(beta0, inv_pml, fminf((float)i + 1.5f, (float)(nx - i) - 0.5f), pml);
+            const bool in_x = i < nx;
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int ly = 4 * ty + r;
+            for (int r = 0; r < NR; ++r) {
+                const int ly = NR * ty + r;
                 const int j = y0 + ly;
                 const float* urow = su + (ly + R) * L::SW + cxs;
                 const float* wxrow = swx + ly * L::SW + cxs;
-                // x taps of u (i-4 .. i+4)
                 float uxx = cent<R>(0) * ucol[r + R];
                 float dux = 0.f;
 #pragma unroll
@@ -303,7 +305,7 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
 #pragma unroll
                     for (int k = 0; k < R; ++k) duy += stag<R>(k) * (ucol[r + R - k] - ucol[r + R + 1 + k]);
                 }
-                if (i >= nx || j >= ny) continue;
+                if (!in_x || j >= ny) continue;
                 const float byn = dampf(beta0, inv_pml, fs ? (float)(ny - j) : (float)min(j + 1, ny - j), pml);
                 const float byh = dampf(beta0, inv_pml,
                                         fs ? (float)(ny - j) - 0.5f : fminf((float)j + 1.5f, (float)(ny - j) - 0.5f),
@@ -312,12 +314,14 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
                 const float xu = ucol[r + R], xv = sv[pt], xwx = wxrow[0], xwy = wcol[r + R];
                 const float c2 = sc2[pt];
                 float hv = -bxn * byn * xu + c2 * ((uxx + uyy) * idx2 + (dwx + dwy) * idx1) - (bxn + byn) * xv;
-                if (i == P->src_i && j == P->src_j) hv += sig;
+                if (i == src_i && j == src_j) hv += sig;
                 const float hwx = (i < nx - 1) ? (byn - bxh) * dux * idx1 - bxh * xwx : 0.f;
                 const float hwy = (j < ny - 1) ? (bxn - byh) * duy * idx1 - byh * xwy : 0.f;
                 const float xf[4] = {xu, xv, xwx, xwy};
                 const float hf[4] = {xv, hv, hwx, hwy};
                 const long long o = (long long)j * pitch + i;
+                float* yrow = Yg ? Yg + o : nullptr;
+                float* arow = Ag ? Ag + o : nullptr;
 #pragma unroll
                 for (int f = 0; f < 4; ++f) {
                     const bool pad = (f == 2 && i >= nx - 1) || (f == 3 && j >= ny - 1);
@@ -325,8 +329,8 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
                     const float aval = has_a ? spa[f * BY * BX + pt] : 0.f;
                     const float kf = cxf * xf[f] + chf * hf[f];
                     const float yf = pad ? 0.f : (cuf * uval + ckf * kf);
-                    if (Yg) Yg[f * fstr + o] = yf;
-                    if (Ag) Ag[f * fstr + o] = pad ? 0.f : (caf * aval + cauf * uval + cakf * kf + cayf * yf + caxf * xf[f]);
+                    if (yrow) yrow[f * fstr] = yf;
+                    if (arow) arow[f * fstr] = pad ? 0.f : (caf * aval + cauf * uval + cakf * kf + cayf * yf + caxf * xf[f]);
                 }
             }
             __syncwarp();
