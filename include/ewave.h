@@ -206,6 +206,43 @@ int ewv_batch_step_rk(ewv_batch_t batch, double t, double dt, int scheme, int st
                       int nsteps);
 int ewv_batch_step_leapfrog(ewv_batch_t batch, double t, double dt, int nsteps);
 
+/* ---- allocation-free Faber step ------------------------------------------------------ */
+
+/* The paper has no counterpart to this entry point; it serves callers that cannot call
+ * cudaMalloc (code running inside someone else's memory pool, environments that forbid
+ * run-time device allocation, or a process that must not grow the device heap while other
+ * work holds the GPU).  It advances one FP32 state by nsteps Faber steps exactly like
+ * ewv_step_faber, but needs no model handle and allocates nothing: the two Faber work
+ * vectors and all per-step metadata live in one fixed file-scope device array of the
+ * library (16 MB + 256 KB, held by every GPU that loads the library until the process
+ * exits), so grids are limited to ny * pitch <= EWV_NOALLOC_MAX_FIELD_ELEMS.
+ *  - state: padded FP32 state vector (4 fields of [ny][pitch], see the layout above),
+ *    advanced in place; c2: c^2 on the padded grid; both 16-byte aligned, caller-owned.
+ *  - args: grid, stencil, damping, optional source and the Faber ellipse (gamma, c0, c1).
+ *  - stream: cudaStream_t (NULL = default stream).
+ * Errors: INVALID_ARG for bad arguments, BAD_SIZE_OR_ALIGNMENT when ny * pitch exceeds
+ * EWV_NOALLOC_MAX_FIELD_ELEMS (nothing is launched) or a pointer is misaligned, CUDA.
+ * The first call on each device (with that device current) looks up the array's device
+ * address; make that first call before any stream capture.  Calls share the array:
+ * calls whose GPU work overlaps race.  The call reads the Faber coefficients back from the
+ * GPU once, so it synchronises the stream before launching the steps. */
+#define EWV_NOALLOC_MAX_FIELD_ELEMS (1 << 19)
+typedef struct ewv_noalloc_faber_args {
+    int nx, ny, pitch;     /* grid nodes; pitch: elements per row, >= nx, multiple of 32 */
+    double dx;
+    int fd_order;          /* 8 or 4 (4 without free surface)                            */
+    int pml_width;
+    double beta0;
+    int free_surface;
+    int has_source;        /* 0: no source term                                         */
+    int src_i, src_j;      /* source node                                                */
+    int src_taylor_p;      /* p of the augmented block, 1..24                            */
+    double f_peak, t0, amp;
+    double gamma, c0, c1;  /* Faber ellipse                                              */
+} ewv_noalloc_faber_args;
+int ewv_faber_step_noalloc(const ewv_noalloc_faber_args* args, float* state, const float* c2,
+                           double t, double dt, int degree, int nsteps, void* stream);
+
 /* ---- diagnostics -------------------------------------------------------------------- */
 
 /* Last error message on this handle ("" if none); valid until the next call on it. */

@@ -21,6 +21,14 @@
 using namespace ewv;
 
 namespace {
+int ensure_tables();
+}
+
+namespace ewv {
+int ensure_tables_current_device() { return ensure_tables(); }
+}  // namespace ewv
+
+namespace {
 
 const char* kVersion = "ewave-gb300 0.1 (sm_103a)";
 

@@ -34,6 +34,7 @@ EXPORTS = [
     "ewv_batch_step_krylov", "ewv_batch_step_rk", "ewv_batch_step_leapfrog", "ewv_last_error",
     "ewv_batch_last_error", "ewv_version", "ewv_launch_count", "ewv_enable_kernel_timing",
     "ewv_kernel_timing", "ewv_batch_enable_kernel_timing", "ewv_batch_kernel_timing", "ewv_reset_state",
+    "ewv_faber_step_noalloc",
 ]
 
 
@@ -47,6 +48,19 @@ class ModelDesc(ctypes.Structure):
                 ("beta0", ctypes.c_double), ("free_surface", ctypes.c_int),
                 ("precision", ctypes.c_int), ("nshots", ctypes.c_int),
                 ("src_taylor_p", ctypes.c_int), ("max_receivers", ctypes.c_int)]
+
+
+class NoallocFaberArgs(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("pitch", ctypes.c_int),
+                ("dx", ctypes.c_double), ("fd_order", ctypes.c_int), ("pml_width", ctypes.c_int),
+                ("beta0", ctypes.c_double), ("free_surface", ctypes.c_int),
+                ("has_source", ctypes.c_int), ("src_i", ctypes.c_int), ("src_j", ctypes.c_int),
+                ("src_taylor_p", ctypes.c_int), ("f_peak", ctypes.c_double), ("t0", ctypes.c_double),
+                ("amp", ctypes.c_double), ("gamma", ctypes.c_double), ("c0", ctypes.c_double),
+                ("c1", ctypes.c_double)]
+
+
+NOALLOC_MAX_FIELD_ELEMS = 1 << 19
 
 
 class LayoutInfo(ctypes.Structure):
@@ -106,6 +120,7 @@ def load_library(path=LIB_PATH):
         "ewv_version": ([], ctypes.c_char_p),
         "ewv_launch_count": ([vp, ctypes.POINTER(ctypes.c_longlong)], i),
         "ewv_reset_state": ([vp], i),
+        "ewv_faber_step_noalloc": ([ctypes.POINTER(NoallocFaberArgs), vp, vp, d, d, i, i, vp], i),
         "ewv_enable_kernel_timing": ([vp, i], i),
         "ewv_kernel_timing": ([vp, dp, ctypes.POINTER(ctypes.c_longlong)], i),
         "ewv_batch_enable_kernel_timing": ([vp, i], i),
@@ -313,6 +328,20 @@ class Model:
         ms, n = ctypes.c_double(), ctypes.c_longlong()
         self._check(self.lib.ewv_kernel_timing(self.h, ctypes.byref(ms), ctypes.byref(n)))
         return ms.value, n.value
+
+
+def faber_step_noalloc(args, state, c2, t, dt, degree, nsteps=1, stream=None):
+    """Allocation-free Faber step (``ewv_faber_step_noalloc``) on caller-owned FP32 device
+    tensors ``state`` (padded state vector) and ``c2``; returns the status code.
+
+    For callers that cannot allocate device memory: the library keeps the work vectors in
+    a fixed device array (grids up to ny * pitch = NOALLOC_MAX_FIELD_ELEMS)."""
+    import torch
+    lib = load_library()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return lib.ewv_faber_step_noalloc(ctypes.byref(args), ctypes.c_void_p(state.data_ptr()),
+                                      ctypes.c_void_p(c2.data_ptr()), t, dt, degree, nsteps,
+                                      ctypes.c_void_p(s.cuda_stream))
 
 
 class Batch:
