@@ -52,8 +52,8 @@ def parse():
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
     ap.add_argument("--no-search", action="store_true", help="use the default selection")
     ap.add_argument("--T", type=float, default=T_END, help="simulated time (profiling runs)")
-    ap.add_argument("--case", default="full", choices=["full", "small"],
-                    help="small: the 1001x501 model with 4 shots (profiling)")
+    ap.add_argument("--case", default="full", choices=["full", "small", "medium"],
+                    help="small / medium: the 1001x501 model with 4 / 16 shots (profiling)")
     return ap.parse_args()
 
 
@@ -118,6 +118,30 @@ def measured_peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "stage_tma_kernel_faber_1001x501x16.md")
+TMA_SOURCE = os.path.join(ROOT, "paper_2401_16322_gb300", "csrc", "kernels_tma.cu")
+
+
+def ncu_traffic_per_point():
+    """DRAM bytes per grid point of one Faber degree pass (j >= 2) from the committed ncu
+    summary, or None when the TMA kernel source changed since the capture."""
+    import hashlib
+    try:
+        with open(TMA_SOURCE, "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+        vals = {}
+        with open(TRAFFIC_SUMMARY) as f:
+            for line in f:
+                if ":" in line and line.startswith("- "):
+                    k, v = line[2:].split(":", 1)
+                    vals[k.strip()] = v.strip().strip("`")
+        if vals.get("kernels_tma.cu sha256") != sha:
+            return None
+        return float(vals["dram bytes per grid point per pass"])
+    except Exception:
+        return None
 
 
 def pass_words(method, m):
@@ -226,7 +250,10 @@ def run_ours(args):
                                             rel_l2_common, run_study, simulate)
     from paper_2401_16322_gb300.workloads import config_batched
 
-    wl = config_batched() if args.case == "full" else config_batched(nshots=4)[:1]
+    if args.case == "full":
+        wl = config_batched()
+    else:
+        wl = config_batched(nshots=4 if args.case == "small" else 16)[:1]
     T_run = args.T
     c_max = max(float(w.c.max()) for w in wl)
     dt_cfl = leapfrog_step(c_max, wl[0].dx, wl[0].order)
@@ -241,7 +268,7 @@ def run_ours(args):
     study = None
     if not args.no_search and args.case == "full":
         study = run_study(wl, PICKS, T_run, target=args.target, full_batch=batch, full_models=models,
-                          log=log if rank == 0 else (lambda *a: None))
+                          log=log if rank == 0 else (lambda *a: None), self_check=True)
         if study.selected is not None:
             method, m, dt = study.selected.method, study.selected.m, study.selected.dt
         else:
@@ -323,7 +350,7 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME if args.case == "full" else "small: 1001x501, 4 shots",
+            "config": {"workload": WORKLOAD_NAME if args.case == "full" else f"{args.case}: 1001x501, {wl[0].shots.__len__()} shots",
                        "method": method, "m": m, "dt_ms": dt * 1e3,
                        "dt_over_leapfrog_step": dt / dt_cfl, "nsteps": nsteps, "T_s": T_run,
                        "grid_points": pts, "problems": sum(len(w.shots) for w in wl),
@@ -332,8 +359,11 @@ def run_ours(args):
             "seismo_rel_err": seismo_err,
             "grid_point_updates_per_s": pts * nsteps / (ms_per_step / 1e3),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                         "kernel": "stage_kernel<float,4> (fused stencil pass)",
+                         "frac": achieved / peak,
+                         "traffic": (tpp * pts if (tpp := ncu_traffic_per_point()) and method == "faber"
+                                     else None),
+                         "peak_kind": peak_kind,
+                         "kernel": "stage_tma_kernel<4> (persistent TMA fused stencil pass, FP32)",
                          "avg_launch_us": avg_launch_ms * 1e3, "launches": kern_n,
                          "alg_bytes_per_launch": per_launch_bytes},
             "cpu_baseline": {"value": cpu_tts, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -345,6 +375,10 @@ def run_ours(args):
             "leapfrog_f32": ({"dt_ms": lf.dt * 1e3, "seismo_rel_err": lf.err,
                               "time_to_solution_s": lf.cost_s} if lf else None),
             "search_s": study.seconds if study else None,
+            "reference_self_check": study.ref_self_check if study else None,
+            "candidates": ([{"method": c.method, "m": c.m, "dt_ms": round(c.dt * 1e3, 4),
+                             "seismo_rel_err": c.err, "time_to_solution_s": c.cost_s}
+                            for c in study.candidates if c.err <= args.target] if study else None),
         }
         print(json.dumps(result), flush=True)
     if dist:
