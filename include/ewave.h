@@ -62,6 +62,7 @@ extern "C" {
 #define EWV_METHOD_RK32 4     /* Sec. 3.1 RK3-2                                          */
 #define EWV_METHOD_RK44 5     /* Sec. 3.1 classical RK4-4                                */
 #define EWV_METHOD_LEAPFROG 6 /* Sec. 3.1 two-step leap-frog                             */
+#define EWV_METHOD_ADJOINT_FABER 7 /* discrete adjoint of the Faber step (workspace query) */
 
 #define EWV_LEAPFROG_AVERAGED 0 /* time-averaged PML damping of w (stable reading)       */
 #define EWV_LEAPFROG_LITERAL 1  /* explicit -beta w^n damping, as the formula reads      */
@@ -189,6 +190,34 @@ int ewv_step_rk(ewv_model_t model, double t, double dt, int scheme, int stages, 
  * change (u^{-1} = u^0, w^{-1} = w^0).  The v field is not advanced. */
 int ewv_step_leapfrog(ewv_model_t model, double t, double dt, int nsteps);
 int ewv_set_leapfrog_variant(ewv_model_t model, int variant);
+
+/* ---- discrete adjoint: FWI gradient with respect to m = c^2 ------------------------------
+ * Misfit J = 1/2 sum_n |R U^n - d^n|^2 over the recorded samples; U^n = Phi_n(U^{n-1}) is one
+ * Faber step (Sec. 3.2).  The inverse problem stores one state per step (Secs. 3.3, 6:
+ * N_mem = T/dt); these calls run the exact discrete adjoint of the recurrence.
+ *
+ * ewv_adjoint_step: for every shot, given the checkpoint U^{n-1} (nshots padded state
+ * vectors) and the cotangent lambda = dJ/dU^n (nshots padded vectors, in/out), replaces
+ * lambda by (dPhi_n/dU)^T lambda and accumulates grad += (dPhi_n/dm)^T lambda into grad
+ * (nshots padded fields [ny][pitch] of the model's precision, one per shot; sum them for
+ * the model gradient).  t = t_{n-1}, dt, m as in the forward ewv_step_faber call (same
+ * ellipse).  Needs ewv_workspace_bytes(EWV_METHOD_ADJOINT_FABER, m) of workspace (the step
+ * is recomputed from the checkpoint: m tape vectors + 3 cotangents).  method must be
+ * EWV_METHOD_FABER (UNSUPPORTED otherwise).  Buffers 256-B aligned, caller-owned.
+ *
+ * ewv_adjoint_inject: lambda_u += R^T values at the receivers, values [nshots][max_receivers]
+ * of the model's precision (the seismogram cotangent of one sample).
+ *
+ * ewv_checkpoint_stride: checkpoint every stride-th step so that at most `budget` states
+ * are stored: stride = 1 if nsteps <= budget, else ceil(nsteps / budget); the states of a
+ * segment are recomputed from its checkpoint during the backward pass. */
+int ewv_adjoint_step(ewv_model_t model, int method, double t, double dt, int m,
+                     const void* checkpoint, void* adj_state, void* grad);
+int ewv_adjoint_inject(ewv_model_t model, void* adj_state, const void* values);
+int ewv_checkpoint_stride(int nsteps, int budget, int* stride);
+/* out[o] = sum over shots of per_shot[shot][o] (fields [ny][pitch]), shots summed in order:
+ * the model gradient from the per-shot gradients of ewv_adjoint_step. */
+int ewv_sum_shot_fields(ewv_model_t model, const void* per_shot, void* out);
 
 /* ---- batches: many models (of uneven sizes) stepped together ----------------------- */
 

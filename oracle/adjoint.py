@@ -1,0 +1,141 @@
+"""Discrete adjoint of the Faber time stepping and the FWI gradient (oracle).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
+
+Not in the paper (its Secs. 3.3 and 6 motivate it: the inverse problem stores one state per
+time step, N_mem = T/dt).  Misfit J(m) = 1/2 sum_n |R U^n - d^n|^2 over the seismogram
+samples n = 1..N (R picks u at the receivers), m = c^2 at the nodes.  U^n = Phi_n(U^{n-1})
+is one Faber step (oracle.faber): p_0 = [U^{n-1}; e_p], p_1 = B p_0, p_2 = B p_1 - 2 c1 p_0,
+p_j = B p_{j-1} - c1 p_{j-2}, U^n = sum_j a_j p_j (U part), B = H~/gamma - c0 I.
+
+Reverse recurrence for a cotangent ybar of U^n (q_j = dJ/dp_j, U parts only -- the tail's
+cotangent never feeds back into U because H~ is block upper triangular):
+    q_m = a_m ybar,  q_{j-1} = a_{j-1} ybar + B^T q_j - c'_{j+1} q_{j+1}
+with c'_2 = 2 c1, c'_k = c1 (k >= 3), q_{m+1} = 0; the cotangent of U^{n-1} is q_0.
+m enters only the v-row of H (Eq. 1): d(H x)_v / dm = L x_u + D x_w (the Laplacian and the
+divergence of w), so dJ/dm += (1/gamma) sum_{j=1..m} q_{j,v} * G(p_{j-1}), G(x) = L x_u + D x_w.
+Time loop: lambda^N = R^T r^N, lambda^{n-1} = q_0(lambda^n) + R^T r^{n-1}.
+
+This route is independent of the CUDA path: B^T uses the transposed sparse matrix of
+``oracle.operator.assemble_H``.  Pins: tests/test_oracle_adjoint.py (dot-product identity
+of one adjoint step; central finite differences of J along seeded directions).
+"""
+import numpy as np
+
+from .faber import faber_coefficients
+from .model import flatten, unflatten
+from .operator import apply_H, assemble_H, dx_node, dxx, dy_node, dyy
+from .source import tail_apply
+
+
+def G_of(model, x_flat):
+    """G(x) = L x_u + D x_w at the nodes (flattened [ny*nx])."""
+    u, _v, wx, wy = unflatten(model, x_flat)
+    g = dxx(model, u) + dyy(model, u) + dx_node(model, wx) + dy_node(model, wy)
+    return g.ravel()
+
+
+def faber_tape(model, U_flat, src, t_n, dt, m, params):
+    """Forward Faber step keeping p_0..p_m (U parts).  Returns (tape list, U^{n+1})."""
+    gamma, c0, c1 = params
+    a = faber_coefficients(dt, gamma, c0, c1, m)
+    p = src.p if src is not None else 1
+    w = src.W(t_n, dt) if src is not None else np.zeros(p)
+    nU = model.n
+
+    def B(x, y):
+        val = float(np.dot(w, y))
+        HU = apply_H(model, unflatten(model, x), None if src is None else (src.j, src.i, val))
+        return flatten(HU) / gamma - c0 * x, tail_apply(y, dt) / gamma - c0 * y
+
+    y0 = np.zeros(p)
+    y0[-1] = 1.0
+    tape = [U_flat.copy()]
+    tails = [y0]
+    if m >= 1:
+        x1, y1 = B(U_flat, y0)
+        tape.append(x1)
+        tails.append(y1)
+    for j in range(2, m + 1):
+        cj = 2.0 * c1 if j == 2 else c1
+        bx, by = B(tape[-1], tails[-1])
+        tape.append(bx - cj * tape[-2])
+        tails.append(by - cj * tails[-2])
+    out = sum(a[j] * tape[j] for j in range(m + 1))
+    return tape, out
+
+
+def faber_adjoint_step(model, U_prev_flat, ybar, src, t_n, dt, m, params, HT=None):
+    """Cotangent of U^{n-1} and the gradient contribution of one Faber step.
+
+    ``ybar``: dJ/dU^n (flat).  Returns (q_0, grad_m [ny*nx])."""
+    gamma, c0, c1 = params
+    a = faber_coefficients(dt, gamma, c0, c1, m)
+    tape, _ = faber_tape(model, U_prev_flat, src, t_n, dt, m, params)
+    if HT is None:
+        HT = assemble_H(model).T.tocsr()
+    nu = model.nx * model.ny
+
+    def BT(q):
+        return (HT @ q) / gamma - c0 * q
+
+    def cprime(k):
+        return 0.0 if k <= 1 else (2.0 * c1 if k == 2 else c1)
+
+    grad = np.zeros(nu)
+    q_next = np.zeros_like(ybar)                  # q_{j+1}
+    q_cur = a[m] * ybar                           # q_m
+    for j in range(m, 0, -1):
+        grad += (1.0 / gamma) * q_cur[nu:2 * nu] * G_of(model, tape[j - 1])
+        q_prev = a[j - 1] * ybar + BT(q_cur) - cprime(j + 1) * q_next
+        q_next, q_cur = q_cur, q_prev
+    return q_cur, grad
+
+
+def faber_forward(model, shots, dt, nsteps, m, params, U0=None):
+    """Forward simulation of every shot; returns (states per shot [N+1 flat], seismograms)."""
+    states, seis = [], []
+    for src, rec_nodes in shots:
+        U = np.zeros(model.n) if U0 is None else U0.copy()
+        Us = [U]
+        S = []
+        for n in range(nsteps):
+            _, U = faber_tape(model, U, src, n * dt, dt, m, params)
+            Us.append(U)
+            S.append(unflatten(model, U)[0][rec_nodes[:, 0], rec_nodes[:, 1]].copy())
+        states.append(Us)
+        seis.append(np.array(S))
+    return states, seis
+
+
+def misfit(seis, d_obs):
+    return 0.5 * sum(float(np.sum((s - d) ** 2)) for s, d in zip(seis, d_obs))
+
+
+def fwi_gradient(model, shots, d_obs, dt, nsteps, m, params):
+    """dJ/dm (m = c^2 at the nodes, [ny, nx]) by the discrete adjoint; returns (J, grad)."""
+    states, seis = faber_forward(model, shots, dt, nsteps, m, params)
+    HT = assemble_H(model).T.tocsr()
+    nu = model.nx * model.ny
+    grad = np.zeros(nu)
+    for (src, rec_nodes), Us, S, D in zip(shots, states, seis, d_obs):
+        r = S - D                                   # residuals [N, nrec]
+        lam = np.zeros(model.n)
+        ridx = rec_nodes[:, 0] * model.nx + rec_nodes[:, 1]
+        np.add.at(lam, ridx, r[nsteps - 1])
+        for n in range(nsteps, 0, -1):
+            q0, g = faber_adjoint_step(model, Us[n - 1], lam, src, (n - 1) * dt, dt, m, params, HT)
+            grad += g
+            lam = q0
+            if n - 1 >= 1:
+                np.add.at(lam, ridx, r[n - 2])
+    return misfit(seis, d_obs), grad.reshape(model.ny, model.nx)
+
+
+def checkpoint_stride(nsteps, budget):
+    """Store every stride-th state so that at most ``budget`` are kept (checkpoint-schedule
+    reading; the paper only counts stored states, N_mem = T/dt): stride 1 when
+    nsteps <= budget, else ceil(nsteps / budget)."""
+    if nsteps <= budget:
+        return 1
+    return -(-nsteps // budget)

@@ -155,6 +155,7 @@ struct ewv_model {
     bool lf_history_valid = false;
     // device metadata
     int* d_rec = nullptr;
+    int* d_nrec = nullptr;      // receivers per shot
     double* d_sigma = nullptr;
     double* d_kry = nullptr;
     long long* d_clk = nullptr;
@@ -177,6 +178,8 @@ struct Engine {
     double* d_coef = nullptr;
     ProblemDev* d_apply = nullptr;
     void* d_maps = nullptr;     // FP32: TMA tensor maps of every problem
+    ProblemDev* d_adj = nullptr;  // adjoint call: descriptors (state = cotangent) + tile map
+    size_t d_adj_bytes = 0;
     int* d_err = nullptr;       // timeout word written by the TMA kernel
     std::map<std::tuple<double, int, double, double, double>, std::vector<double>> faber_cache;
     // optional CUDA-event timing of the fused stencil passes (pairs around each launch)
@@ -193,6 +196,7 @@ struct Engine {
         cudaFree(d_apply);
         cudaFree(d_maps);
         cudaFree(d_err);
+        cudaFree(d_adj);
     }
 };
 
@@ -262,6 +266,7 @@ int vectors_needed(int method, int m) {
         case EWV_METHOD_RK32: return 2;
         case EWV_METHOD_RK44: return 3;
         case EWV_METHOD_LEAPFROG: return 1;
+        case EWV_METHOD_ADJOINT_FABER: return m + 3;   // tape p_0..p_{m-1} + 3 cotangents
         default: return -1;
     }
 }
@@ -279,6 +284,7 @@ ProblemDev make_problem(ewv_model* m, int shot, int tile_base) {
     P.ntiles = P.tiles_x * P.tiles_y;
     P.tile_base = tile_base;
     const Shot& s = m->shots[shot];
+    P.shot = shot;
     P.has_src = s.has_src ? 1 : 0;
     P.src_i = s.has_src ? s.si : -1;
     P.src_j = s.has_src ? s.sj : -1;
@@ -845,6 +851,8 @@ int ewv_create_model(const ewv_model_desc* desc, ewv_model_t* out) {
     const int nr = d.max_receivers > 0 ? d.max_receivers : 1;
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaMalloc(&m->d_rec, sizeof(int) * (size_t)nr * d.nshots);
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_nrec, sizeof(int) * (size_t)d.nshots);
+    if (e == cudaSuccess) e = cudaMemset(m->d_nrec, 0, sizeof(int) * (size_t)d.nshots);
     if (e == cudaSuccess) e = cudaMalloc(&m->d_sigma, sizeof(double) * (size_t)MAX_SIGMA * d.nshots);
     if (e == cudaSuccess) e = cudaMalloc(&m->d_kry, sizeof(double) * (size_t)KRY_STRIDE * d.nshots);
     if (e == cudaSuccess) e = cudaMalloc(&m->d_clk, sizeof(long long) * 4 * (size_t)d.nshots);
@@ -865,6 +873,7 @@ int ewv_destroy_model(ewv_model_t m) {
     if (!m) return EWV_ERR_INVALID_ARG;
     delete m->engine;
     cudaFree(m->d_rec);
+    cudaFree(m->d_nrec);
     cudaFree(m->d_sigma);
     cudaFree(m->d_kry);
     cudaFree(m->d_clk);
@@ -1025,6 +1034,7 @@ int ewv_set_source_receivers(ewv_model_t m, int shot, double sx, double sy, doub
     if (nrec > 0)
         CUDA_OR_FAIL(m->err, cudaMemcpy(m->d_rec + (size_t)shot * m->d.max_receivers, off.data(),
                                         sizeof(int) * nrec, cudaMemcpyHostToDevice));
+    CUDA_OR_FAIL(m->err, cudaMemcpy(m->d_nrec + shot, &nrec, sizeof(int), cudaMemcpyHostToDevice));
     if (src_idx_out) {
         src_idx_out[0] = (int32_t)si;
         src_idx_out[1] = (int32_t)sj;
@@ -1273,6 +1283,166 @@ int ewv_batch_kernel_timing(ewv_batch_t b, double* total_ms, long long* launches
     if (!b) return EWV_ERR_INVALID_ARG;
     return read_timing(b->engine, b->stream_set ? b->stream : b->models[0]->stream, b->err,
                        total_ms, launches);
+}
+
+// ---- discrete adjoint (FWI gradient) -------------------------------------------------
+int ewv_adjoint_step(ewv_model_t m, int method, double t, double dt, int deg,
+                     const void* checkpoint, void* adj_state, void* grad) {
+    if (!m || !checkpoint || !adj_state || !grad) return EWV_ERR_INVALID_ARG;
+    if (method != EWV_METHOD_FABER)
+        return fail(m->err, EWV_ERR_UNSUPPORTED, "adjoint implemented for the Faber step only");
+    if (deg < 1 || deg > MAX_DEG || !(dt > 0.0))
+        return fail(m->err, EWV_ERR_INVALID_ARG, "degree must be 1..%d and dt > 0", MAX_DEG);
+    if (!aligned(checkpoint) || !aligned(adj_state) || !aligned(grad))
+        return fail(m->err, EWV_ERR_BAD_SIZE_OR_ALIGNMENT, "adjoint buffers must be 256-B aligned");
+    int rc = check_bound(m, EWV_METHOD_ADJOINT_FABER, deg, m->err);
+    if (rc != EWV_OK) return rc;
+    Engine* E = ensure_model_engine(m);
+    rc = engine_ready(E, m->err);
+    if (rc != EWV_OK) return rc;
+    cudaStream_t s = m->stream;
+    const int ns = m->d.nshots;
+    const size_t vb = m->vec_elems * m->elem;
+    const size_t per_shot = (m->work_bytes / ns) / vb;        // workspace vectors per shot
+    // descriptors: vector 0 = the cotangent (adj_state), work = this model's workspace
+    std::vector<ProblemDev> probs;
+    int tb = 0;
+    for (int sh = 0; sh < ns; ++sh) {
+        ProblemDev P = make_problem(m, sh, tb);
+        P.state = (char*)adj_state + (size_t)sh * vb;
+        P.work = (char*)m->work + (size_t)sh * per_shot * vb;
+        P.tmaps = nullptr;
+        tb += P.ntiles;
+        probs.push_back(P);
+    }
+    std::vector<int> tp(tb);
+    for (int p = 0; p < ns; ++p)
+        for (int k = 0; k < probs[p].ntiles; ++k) tp[probs[p].tile_base + k] = p;
+    const size_t adj_bytes = sizeof(ProblemDev) * ns + sizeof(int) * (size_t)tb;
+    if (adj_bytes > E->d_adj_bytes) {
+        cudaFree(E->d_adj);
+        E->d_adj = nullptr;
+        E->d_adj_bytes = 0;
+        CUDA_OR_FAIL(m->err, cudaMalloc(&E->d_adj, adj_bytes));
+        E->d_adj_bytes = adj_bytes;
+    }
+    int* d_tp = (int*)((char*)E->d_adj + sizeof(ProblemDev) * ns);
+    CUDA_OR_FAIL(m->err, cudaMemcpyAsync(E->d_adj, probs.data(), sizeof(ProblemDev) * ns,
+                                         cudaMemcpyHostToDevice, s));
+    CUDA_OR_FAIL(m->err, cudaMemcpyAsync(d_tp, tp.data(), sizeof(int) * (size_t)tb,
+                                         cudaMemcpyHostToDevice, s));
+    // checkpoint U^{n-1} -> tape slot T_0 (workspace vector 1) of every shot
+    CUDA_OR_FAIL(m->err, cudaMemcpy2DAsync(m->work, per_shot * vb, checkpoint, vb, vb, ns,
+                                           cudaMemcpyDeviceToDevice, s));
+    double g, c0, c1;
+    ellipse_of(m, &g, &c0, &c1);
+    auto key = std::make_tuple(dt, deg, g, c0, c1);
+    auto it = E->faber_cache.find(key);
+    if (it == E->faber_cache.end()) {
+        launch_faber_coeffs(dt, g, c0, c1, deg, E->d_coef, s);
+        ++m->launches;
+        std::vector<double> a(deg + 1);
+        CUDA_OR_FAIL(m->err, cudaMemcpyAsync(a.data(), E->d_coef, sizeof(double) * (deg + 1),
+                                             cudaMemcpyDeviceToHost, s));
+        CUDA_OR_FAIL(m->err, cudaStreamSynchronize(s));
+        it = E->faber_cache.emplace(key, a).first;
+    }
+    const std::vector<double>& a = it->second;
+    const int R = m->R, prec = m->d.precision;
+    auto cprime = [&](int k) { return k <= 1 ? 0.0 : (k == 2 ? 2.0 * c1 : c1); };
+    auto stage = [&](const StageArgs& sa) {
+        launch_stage(prec, R, tb, E->d_adj, d_tp, sa, s);
+        ++m->launches;
+    };
+    launch_set_clock(E->d_adj, ns, t, dt, s);
+    launch_prologue(E->d_adj, ns, 1 /* Faber */, deg, g, c0, c1, s);
+    m->launches += 2;
+    // recompute the forward vectors p_1..p_{m-1} of this step into the tape (T_k = vector k+1)
+    for (int j = 1; j <= deg - 1; ++j) {
+        StageArgs sa = stage_defaults();
+        sa.x = j;
+        sa.u = j >= 2 ? j - 1 : -1;
+        sa.y_out = j + 1;
+        sa.src_slot = j - 1;
+        sa.cx = -c0;
+        sa.ch = 1.0 / g;
+        sa.cu = -cprime(j);
+        sa.ck = 1.0;
+        stage(sa);
+    }
+    // reverse recurrence; ybar is vector 0, q_{m-k} lives in Q[(k-1) % 3] (vectors m+1..m+3)
+    auto qbuf = [&](int jj) { return jj == 0 ? 0 : deg + 1 + ((deg - jj - 1) % 3); };
+    for (int j = deg; j >= 1; --j) {
+        // gradient: (1/gamma) q_{j,v} G(p_{j-1}); q_m = a_m ybar is not stored
+        StageArgs gr = stage_defaults();
+        gr.x = j;                              // T_{j-1}
+        gr.grad = grad;
+        gr.gq = (j == deg) ? 0 : qbuf(j);
+        gr.gscale = (j == deg) ? a[deg] / g : 1.0 / g;
+        stage(gr);
+        // q_{j-1} = a_{j-1} ybar + B^T q_j - c'_{j+1} q_{j+1}
+        StageArgs tr = stage_defaults();
+        tr.transpose = 1;
+        tr.a = 0;
+        tr.cak = 1.0;
+        if (j == deg) {
+            tr.x = 0;
+            tr.cx = -c0 * a[deg];
+            tr.ch = a[deg] / g;
+            tr.ca = a[deg - 1];
+        } else if (j == deg - 1) {
+            tr.x = qbuf(j);
+            tr.cx = -c0;
+            tr.ch = 1.0 / g;
+            tr.ca = a[j - 1] - cprime(j + 1) * a[deg];
+        } else {
+            tr.x = qbuf(j);
+            tr.u = qbuf(j + 1);
+            tr.cau = -cprime(j + 1);
+            tr.cx = -c0;
+            tr.ch = 1.0 / g;
+            tr.ca = a[j - 1];
+        }
+        // degree 1: q_0 cannot overwrite ybar while ybar is read with a halo
+        tr.acc_out = (j == 1 && deg == 1) ? deg + 1 : qbuf(j - 1);
+        stage(tr);
+    }
+    if (deg == 1) {
+        PointArgs pa{};
+        pa.mode = 3;
+        pa.src = deg + 1;
+        pa.dst = 0;
+        pa.fmask = 0xF;
+        launch_point(prec, tb, E->d_adj, d_tp, pa, s);
+        ++m->launches;
+    }
+    return check_launch(m->err);
+}
+
+int ewv_adjoint_inject(ewv_model_t m, void* adj_state, const void* values) {
+    if (!m || !adj_state || !values) return EWV_ERR_INVALID_ARG;
+    const int ns = m->d.nshots, nr = m->d.max_receivers;
+    const size_t vb = m->vec_elems * m->elem;
+    // lambda_u[rec] += values[shot][rec]; receivers of one shot are added in order
+    if (nr == 0) return EWV_OK;
+    if (!aligned(adj_state)) return fail(m->err, EWV_ERR_BAD_SIZE_OR_ALIGNMENT, "adj_state must be 256-B aligned");
+    launch_inject(m->d.precision, adj_state, (long long)m->vec_elems, values, m->d_rec, m->d_nrec, ns,
+                  nr, m->stream);
+    ++m->launches;
+    return check_launch(m->err);
+}
+
+int ewv_sum_shot_fields(ewv_model_t m, const void* per_shot, void* out) {
+    if (!m || !per_shot || !out) return EWV_ERR_INVALID_ARG;
+    launch_sum_shots(m->d.precision, per_shot, out, (long long)m->field_elems, m->d.nshots, m->stream);
+    ++m->launches;
+    return check_launch(m->err);
+}
+
+int ewv_checkpoint_stride(int nsteps, int budget, int* stride) {
+    if (nsteps < 0 || budget < 1 || !stride) return EWV_ERR_INVALID_ARG;
+    *stride = nsteps <= budget ? 1 : (nsteps + budget - 1) / budget;
+    return EWV_OK;
 }
 
 const char* ewv_last_error(ewv_model_t m) { return m ? m->err.c_str() : "null handle"; }

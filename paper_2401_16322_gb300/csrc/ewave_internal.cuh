@@ -47,6 +47,7 @@ struct ProblemDev {
     int pml, src_i, src_j, nrec;
     int tiles_x, tiles_y, tile_base, ntiles;
     int rec_stride, capacity, p, has_src;
+    int shot, pad_;       // shot index inside its model (per-shot caller arrays)
     double beta0, inv_dx, inv_dx2, inv_pml;
     double f_peak, t0, amp;
     long long field_stride, vec_stride;
@@ -76,6 +77,9 @@ struct StageArgs {
     double tol;                      // breakdown tolerance (Krylov)
     int m;                           // Krylov dimension of this step
     double dt;
+    void* grad;                      // gradient mode: grad += gscale q_v G(X), per-shot fields
+    int gq;                          // vector index of q (its v field is read)
+    double gscale;
 };
 
 // Arguments of the pointwise kernel (kernels_aux.cu).
@@ -112,6 +116,10 @@ void launch_prologue(const ProblemDev* probs, int nprob, int kind, int m, double
 void launch_record(int precision, const ProblemDev* probs, int nprob, int vec, cudaStream_t s);
 void launch_point(int precision, int nblocks, const ProblemDev* probs, const int* tile_prob,
                   const PointArgs& pa, cudaStream_t s);
+void launch_inject(int precision, void* adj, long long vec_elems, const void* values,
+                   const int* rec_off, const int* nrec, int nshots, int max_rec, cudaStream_t s);
+void launch_sum_shots(int precision, const void* in, void* out, long long n, int nshots,
+                      cudaStream_t s);
 int launch_expm(const ProblemDev* probs, int nprob, int mmax, cudaStream_t s);
 void launch_faber_coeffs(double dt, double gamma, double c0, double c1, int m, double* out,
                          cudaStream_t s);

@@ -159,6 +159,30 @@ __global__ void record_kernel(const ProblemDev* probs, int nprob, int vec) {
     }
 }
 
+// ---------------------------------------------------------------- adjoint source
+// lambda_u[rec] += values[shot][rec] (the transpose of recording, R^T r); one thread per
+// shot adds its receivers in order, so coincident receivers are summed deterministically.
+template <typename T>
+__global__ void inject_kernel(T* adj, long long vec_elems, const T* values, const int* rec_off,
+                              const int* nrec, int nshots, int max_rec) {
+    const int sh = blockIdx.x * blockDim.x + threadIdx.x;
+    if (sh >= nshots) return;
+    T* lam = adj + (long long)sh * vec_elems;
+    const int n = nrec[sh];
+    for (int r = 0; r < n; ++r) lam[rec_off[sh * max_rec + r]] += values[(long long)sh * max_rec + r];
+}
+
+// out[o] = sum_s in[s][o], shots summed in index order (deterministic).
+template <typename T>
+__global__ void sum_shots_kernel(const T* in, T* out, long long n, int nshots) {
+    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < n;
+         o += (long long)gridDim.x * blockDim.x) {
+        T acc = T(0);
+        for (int s = 0; s < nshots; ++s) acc += in[(long long)s * n + o];
+        out[o] = acc;
+    }
+}
+
 // ---------------------------------------------------------------- pointwise Krylov passes
 // Each uses the stencil kernels' tile decomposition so that partial index == block index.
 
@@ -475,6 +499,24 @@ void launch_record(int precision, const ProblemDev* probs, int nprob, int vec, c
     if (precision == 0) record_kernel<float><<<nprob, 128, 0, s>>>(probs, nprob, vec);
     else record_kernel<double><<<nprob, 128, 0, s>>>(probs, nprob, vec);
 }
+void launch_inject(int precision, void* adj, long long vec_elems, const void* values,
+                   const int* rec_off, const int* nrec, int nshots, int max_rec, cudaStream_t s) {
+    const int blocks = (nshots + 63) / 64;
+    if (precision == 0)
+        inject_kernel<float><<<blocks, 64, 0, s>>>((float*)adj, vec_elems, (const float*)values, rec_off,
+                                                   nrec, nshots, max_rec);
+    else
+        inject_kernel<double><<<blocks, 64, 0, s>>>((double*)adj, vec_elems, (const double*)values,
+                                                    rec_off, nrec, nshots, max_rec);
+}
+
+void launch_sum_shots(int precision, const void* in, void* out, long long n, int nshots,
+                      cudaStream_t s) {
+    const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    if (precision == 0) sum_shots_kernel<float><<<blocks, 256, 0, s>>>((const float*)in, (float*)out, n, nshots);
+    else sum_shots_kernel<double><<<blocks, 256, 0, s>>>((const double*)in, (double*)out, n, nshots);
+}
+
 void launch_point(int precision, int nblocks, const ProblemDev* probs, const int* tile_prob,
                   const PointArgs& pa, cudaStream_t s) {
     const dim3 block(TPX, TPY);

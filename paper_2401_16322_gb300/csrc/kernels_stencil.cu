@@ -294,6 +294,14 @@ stage_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ tile_
                     for (int k = 0; k < R; ++k)
                         duy += STAG<T, R>(k) * (su[ly + R - k][lx + R] - su[ly + R + 1 + k][lx + R]);
                 }
+                if (a.grad) {
+                    // FWI gradient w.r.t. m = c^2: d(H X)_v / dm = L X_u + D X_w
+                    T* G = (T*)a.grad + (long long)P->shot * fstr;
+                    const T* Q = vec_ptr<T>(P, a.gq);
+                    const T gval = (uxx + uyy) * idx2 + (dwx + dwy) * idx1;
+                    G[o] += (T)a.gscale * Q[fstr + o] * gval;
+                    continue;
+                }
                 hu = xv;
                 hv = -bxn * byn * xu + c2 * ((uxx + uyy) * idx2 + (dwx + dwy) * idx1)
                      - (bxn + byn) * xv;

@@ -19,7 +19,8 @@ ERRORS = {
     -5: "NONFINITE", -6: "TIMEOUT", -7: "UNSUPPORTED", -8: "NOT_BOUND",
 }
 F32, F64 = 0, 1
-METHOD = {"apply": 0, "faber": 1, "krylov": 2, "hork": 3, "rk32": 4, "rk44": 5, "leapfrog": 6}
+METHOD = {"apply": 0, "faber": 1, "krylov": 2, "hork": 3, "rk32": 4, "rk44": 5, "leapfrog": 6,
+          "adjoint_faber": 7}
 LEAPFROG_AVERAGED, LEAPFROG_LITERAL = 0, 1
 
 # Every symbol include/ewave.h declares (checked by the tests).
@@ -34,7 +35,8 @@ EXPORTS = [
     "ewv_batch_step_krylov", "ewv_batch_step_rk", "ewv_batch_step_leapfrog", "ewv_last_error",
     "ewv_batch_last_error", "ewv_version", "ewv_launch_count", "ewv_enable_kernel_timing",
     "ewv_kernel_timing", "ewv_batch_enable_kernel_timing", "ewv_batch_kernel_timing", "ewv_reset_state",
-    "ewv_faber_step_noalloc",
+    "ewv_faber_step_noalloc", "ewv_adjoint_step", "ewv_adjoint_inject", "ewv_checkpoint_stride",
+    "ewv_sum_shot_fields",
 ]
 
 
@@ -120,6 +122,10 @@ def load_library(path=LIB_PATH):
         "ewv_version": ([], ctypes.c_char_p),
         "ewv_launch_count": ([vp, ctypes.POINTER(ctypes.c_longlong)], i),
         "ewv_reset_state": ([vp], i),
+        "ewv_adjoint_step": ([vp, i, d, d, i, vp, vp, vp], i),
+        "ewv_adjoint_inject": ([vp, vp, vp], i),
+        "ewv_checkpoint_stride": ([i, i, ctypes.POINTER(i)], i),
+        "ewv_sum_shot_fields": ([vp, vp, vp], i),
         "ewv_faber_step_noalloc": ([ctypes.POINTER(NoallocFaberArgs), vp, vp, d, d, i, i, vp], i),
         "ewv_enable_kernel_timing": ([vp, i], i),
         "ewv_kernel_timing": ([vp, dp, ctypes.POINTER(ctypes.c_longlong)], i),
@@ -320,6 +326,23 @@ class Model:
         self._check(self.lib.ewv_launch_count(self.h, ctypes.byref(c)))
         return c.value
 
+    # ---------------------------------------------------------------- adjoint
+    def adjoint_step(self, t, dt, degree, checkpoint, adj, grad):
+        """lambda <- (dPhi/dU)^T lambda, grad += (dPhi/dm)^T lambda for one Faber step."""
+        self.ensure_workspace("adjoint_faber", degree)
+        self._check(self.lib.ewv_adjoint_step(self.h, METHOD["faber"], t, dt, degree,
+                                              ctypes.c_void_p(checkpoint.data_ptr()),
+                                              ctypes.c_void_p(adj.data_ptr()),
+                                              ctypes.c_void_p(grad.data_ptr())), "adjoint_step")
+
+    def adjoint_inject(self, adj, values):
+        self._check(self.lib.ewv_adjoint_inject(self.h, ctypes.c_void_p(adj.data_ptr()),
+                                                ctypes.c_void_p(values.data_ptr())), "adjoint_inject")
+
+    def sum_shot_fields(self, per_shot, out):
+        self._check(self.lib.ewv_sum_shot_fields(self.h, ctypes.c_void_p(per_shot.data_ptr()),
+                                                 ctypes.c_void_p(out.data_ptr())), "sum_shot_fields")
+
     def enable_kernel_timing(self, on=True):
         self._check(self.lib.ewv_enable_kernel_timing(self.h, int(on)))
 
@@ -328,6 +351,15 @@ class Model:
         ms, n = ctypes.c_double(), ctypes.c_longlong()
         self._check(self.lib.ewv_kernel_timing(self.h, ctypes.byref(ms), ctypes.byref(n)))
         return ms.value, n.value
+
+
+def checkpoint_stride(nsteps, budget):
+    """Checkpoint every stride-th step so that at most ``budget`` states are stored."""
+    out = ctypes.c_int()
+    rc = load_library().ewv_checkpoint_stride(nsteps, budget, ctypes.byref(out))
+    if rc != EWV_OK:
+        raise EwaveError(f"checkpoint_stride: {ERRORS.get(rc, rc)}")
+    return out.value
 
 
 def faber_step_noalloc(args, state, c2, t, dt, degree, nsteps=1, stream=None):

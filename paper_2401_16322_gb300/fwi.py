@@ -1,0 +1,103 @@
+"""Full-waveform-inversion gradient through the library's discrete adjoint.
+
+The forward map takes m = c^2 (squared velocity at the nodes, [ny, nx]) to every shot's
+seismogram (Faber steps, Sec. 3.2).  The backward pass runs the exact discrete adjoint of
+those steps (``ewv_adjoint_step``), injecting the seismogram cotangent at the receivers
+(``ewv_adjoint_inject``), and returns dL/dm.  Forward states are checkpointed every
+``stride`` steps (``ewv_checkpoint_stride``): with stride 1 every state is stored, which is
+the memory N_mem = T/dt that the paper's large exponential steps reduce (Secs. 3.3, 6);
+with stride k the states inside a segment are recomputed from its checkpoint.
+
+All arithmetic runs in the library's kernels; this module allocates device buffers (torch)
+and sequences the calls.
+"""
+import numpy as np
+
+from .ewave import Model, checkpoint_stride
+
+
+class FaberFWI:
+    """Forward simulation with checkpoints and the adjoint gradient for one model."""
+
+    def __init__(self, model: Model, dt, degree, nsteps, nrec, budget=None, t0=0.0):
+        self.model = model
+        self.dt, self.degree, self.nsteps, self.nrec, self.t0 = dt, degree, nsteps, nrec, t0
+        self.stride = checkpoint_stride(nsteps, budget if budget else max(nsteps, 1))
+        torch = model.torch
+        nv = model.vector_elems
+        self.nck = (nsteps + self.stride - 1) // self.stride
+        self.ckpt = torch.zeros(self.nck, model.nshots * nv, dtype=model.dtype, device=model.device)
+        self.seg = torch.zeros(self.stride, model.nshots * nv, dtype=model.dtype, device=model.device)
+
+    def _set_m(self, m_c2):
+        c = np.sqrt(np.asarray(m_c2.detach().double().cpu().numpy() if hasattr(m_c2, "detach") else m_c2,
+                               dtype=np.float64))
+        self.model.set_velocity(c)
+
+    def forward(self, m_c2):
+        """Seismograms [nshots, nsteps, nrec] (a copy) for squared velocity m_c2 [ny, nx]."""
+        md = self.model
+        self._set_m(m_c2)
+        if md.capacity < self.nsteps:
+            md.bind_seismogram(self.nsteps)
+        md.reset_state()
+        md.ensure_workspace("faber", self.degree)
+        for n in range(self.nsteps):
+            if n % self.stride == 0:
+                self.ckpt[n // self.stride].copy_(md.state)
+            md.step_faber(self.t0 + n * self.dt, self.dt, self.degree, 1)
+        s = md.seismo.view(md.nshots, md.capacity, md.max_receivers)[:, :self.nsteps, :self.nrec]
+        return s.clone()
+
+    def backward(self, grad_seis):
+        """dL/dm [ny, nx] from the seismogram cotangent grad_seis [nshots, nsteps, nrec]."""
+        md = self.model
+        torch = md.torch
+        nv, ns = md.vector_elems, md.nshots
+        fe = md.layout.field_elems
+        g = torch.zeros(ns, md.max_receivers * self.nsteps, dtype=md.dtype, device=md.device)
+        g = g.view(ns, self.nsteps, md.max_receivers)
+        g[:, :, :self.nrec] = grad_seis.to(md.dtype)
+        lam = torch.zeros(ns * nv, dtype=md.dtype, device=md.device)
+        grad = torch.zeros(ns * fe, dtype=md.dtype, device=md.device)
+        md.ensure_workspace("adjoint_faber", self.degree)
+        md.adjoint_inject(lam, g[:, self.nsteps - 1, :].contiguous())
+        for k in range(self.nck - 1, -1, -1):
+            n0 = k * self.stride
+            n1 = min(n0 + self.stride, self.nsteps)
+            # recompute the states U^{n0} .. U^{n1-1} of this segment from its checkpoint
+            if self.stride > 1:
+                md.state.copy_(self.ckpt[k])
+                md.ensure_workspace("faber", self.degree)
+                for n in range(n0, n1):
+                    self.seg[n - n0].copy_(md.state)
+                    if n + 1 < n1:
+                        md.step_faber(self.t0 + n * self.dt, self.dt, self.degree, 1)
+                md.ensure_workspace("adjoint_faber", self.degree)
+            for n in range(n1, n0, -1):          # adjoint of step n: U^{n-1} -> U^n
+                ck = self.seg[n - 1 - n0] if self.stride > 1 else self.ckpt[n - 1]
+                md.adjoint_step(self.t0 + (n - 1) * self.dt, self.dt, self.degree, ck, lam, grad)
+                if n - 1 >= 1:
+                    md.adjoint_inject(lam, g[:, n - 2, :].contiguous())
+        out = torch.zeros(fe, dtype=md.dtype, device=md.device)
+        md.sum_shot_fields(grad, out)
+        return out.view(md.ny, md.layout.pitch)[:, :md.nx]
+
+
+def seismogram_fn():
+    """torch.autograd.Function: m_c2 [ny, nx] -> seismograms, backward by the adjoint."""
+    import torch
+
+    class FaberSeismogram(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, m_c2, fwi):
+            ctx.fwi = fwi
+            ctx.device, ctx.dtype = m_c2.device, m_c2.dtype
+            return fwi.forward(m_c2)
+
+        @staticmethod
+        def backward(ctx, grad_seis):
+            g = ctx.fwi.backward(grad_seis)
+            return g.to(device=ctx.device, dtype=ctx.dtype), None
+
+    return FaberSeismogram

@@ -1,0 +1,151 @@
+"""GPU FWI gradient (m = c^2) through the discrete adjoint of the Faber step: the adjoint
+dot-product identity on the GPU, the oracle's gradient, central finite differences,
+checkpointing, FP32, and the torch.autograd path."""
+import numpy as np
+import pytest
+
+from oracle.adjoint import checkpoint_stride as o_stride
+from oracle.adjoint import faber_forward, fwi_gradient, misfit
+from oracle.faber import ellipse_params
+from oracle.model import Model as OModel
+from oracle.model import default_beta0
+from oracle.simulate import receiver_nodes, rel_l2
+from oracle.source import PointSource
+from paper_2401_16322_gb300.workloads import layered, random_state, smooth_random_state
+
+pytestmark = pytest.mark.gpu
+
+NX, NY, DX, PML = 30, 20, 10.0, 5
+DT, NSTEPS, DEG = 2e-3, 14, 12
+SX = (8 * DX, 21 * DX)
+REC = np.array([[x * DX, 0.0] for x in range(3, NX - 3, 4)])
+
+
+def _setup():
+    c_true = layered(NX, NY, 31, vmin=1500, vmax=3000)
+    c0 = np.full((NY, NX), float(c_true.mean()))
+    beta0 = default_beta0(3000.0, PML, DX)
+    ell = ellipse_params(3000.0, beta0, DX, 8, free_surface=True)
+    return c_true, c0, beta0, ell
+
+
+def _oshots(om):
+    return [(PointSource(om, sx, 2 * DX, 30.0, 0.04, amp=1e3, p=10), receiver_nodes(om, REC)) for sx in SX]
+
+
+def _gpu(c, beta0, ell, prec, sources=True):
+    from paper_2401_16322_gb300 import Model
+    g = Model(NX, NY, DX, 8, PML, beta0, True, precision=prec, nshots=2, p=10, max_receivers=len(REC))
+    g.set_velocity(c)
+    if sources:
+        for k, sx in enumerate(SX):
+            g.set_source_receivers(k, sx, 2 * DX, 30.0, 0.04, 1e3, REC)
+    g.set_faber_ellipse(*ell)
+    return g
+
+
+def _d_obs():
+    c_true, c0, beta0, ell = _setup()
+    om = OModel(NX, NY, DX, 8, PML, beta0, True, c_true)
+    return faber_forward(om, _oshots(om), DT, NSTEPS, DEG, ell)[1]
+
+
+def _gpu_grad(prec, budget=None):
+    import torch
+    from paper_2401_16322_gb300.fwi import FaberFWI
+    c_true, c0, beta0, ell = _setup()
+    g = _gpu(c0, beta0, ell, prec)
+    fwi = FaberFWI(g, DT, DEG, NSTEPS, len(REC), budget=budget)
+    seis = fwi.forward(c0 ** 2)
+    d = torch.tensor(np.array(_d_obs()), dtype=seis.dtype, device=seis.device)
+    grad = fwi.backward(seis - d)
+    J = 0.5 * float(((seis - d) ** 2).sum())
+    return J, grad.double().cpu().numpy(), fwi
+
+
+def test_adjoint_step_dot_product_identity_gpu():
+    """<A dU, ybar> = <dU, A^T ybar> for one Faber step's linear part (no source)."""
+    import torch
+    c_true, c0, beta0, ell = _setup()
+    g = _gpu(c_true, beta0, ell, "f64", sources=False)
+    om = OModel(NX, NY, DX, 8, PML, beta0, True, c_true)
+    dU, yb = (random_state([(om.n,)], s)[0] for s in (3, 4))
+    g.set_state(0, dU)
+    g.set_state(1, dU)
+    g.step_faber(0.0, DT, DEG, 1)
+    AdU = g.get_state(0)
+    ck = torch.zeros_like(g.state)
+    lam = g.new_vector().repeat(2)
+    nv = g.vector_elems
+    g.pack(yb, lam[:nv])
+    grad = torch.zeros(2 * g.layout.field_elems, dtype=torch.float64, device="cuda")
+    g.adjoint_step(0.0, DT, DEG, ck, lam, grad)
+    q0 = g.unpack(lam[:nv])
+    lhs, rhs = float(np.dot(AdU, yb)), float(np.dot(dU, q0))
+    assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), abs(rhs))
+
+
+def test_gpu_gradient_matches_oracle_fp64():
+    c_true, c0, beta0, ell = _setup()
+    om = OModel(NX, NY, DX, 8, PML, beta0, True, c0)
+    J_o, g_o = fwi_gradient(om, _oshots(om), _d_obs(), DT, NSTEPS, DEG, ell)
+    J_g, g_g, _ = _gpu_grad("f64")
+    assert abs(J_g - J_o) <= 1e-11 * J_o
+    assert rel_l2(g_g, g_o) < 1e-10
+
+
+def test_gpu_gradient_central_differences_fp64():
+    """Directional derivative of the GPU misfit by central differences, relative 1e-3."""
+    import torch
+    from paper_2401_16322_gb300.fwi import FaberFWI
+    c_true, c0, beta0, ell = _setup()
+    J0, grad, fwi = _gpu_grad("f64")
+    d = torch.tensor(np.array(_d_obs()), dtype=torch.float64, device="cuda")
+    c2 = c0 ** 2
+    for seed in (5, 6, 7):
+        dm = smooth_random_state([(NY, NX)], seed, sigma_cells=2.0)[0] * 0.01 * c2
+        eps = 1e-4
+        Jp = 0.5 * float(((fwi.forward(c2 + eps * dm) - d) ** 2).sum())
+        Jm = 0.5 * float(((fwi.forward(c2 - eps * dm) - d) ** 2).sum())
+        fd = (Jp - Jm) / (2 * eps)
+        an = float(np.sum(grad * dm))
+        assert abs(fd - an) <= 1e-3 * abs(fd), (seed, fd, an)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_checkpointing_reproduces_full_storage(prec):
+    """Storing every 4th state (segments recomputed) gives the same gradient bit for bit."""
+    _, g_full, fwi1 = _gpu_grad(prec)
+    _, g_ck, fwi4 = _gpu_grad(prec, budget=4)
+    assert fwi1.stride == 1 and fwi4.stride == o_stride(NSTEPS, 4) == 4
+    assert np.array_equal(g_full, g_ck)
+
+
+def test_fp32_gradient_against_fp64_oracle():
+    c_true, c0, beta0, ell = _setup()
+    om = OModel(NX, NY, DX, 8, PML, beta0, True, c0)
+    _, g_o = fwi_gradient(om, _oshots(om), _d_obs(), DT, NSTEPS, DEG, ell)
+    _, g32, _ = _gpu_grad("f32")
+    assert rel_l2(g32, g_o) < 1e-3
+
+
+def test_autograd_function_gives_the_adjoint_gradient():
+    import torch
+    from paper_2401_16322_gb300.fwi import FaberFWI, seismogram_fn
+    c_true, c0, beta0, ell = _setup()
+    g = _gpu(c0, beta0, ell, "f64")
+    fwi = FaberFWI(g, DT, DEG, NSTEPS, len(REC))
+    m = torch.tensor(c0 ** 2, dtype=torch.float64, requires_grad=True)
+    d = torch.tensor(np.array(_d_obs()), dtype=torch.float64, device="cuda")
+    seis = seismogram_fn().apply(m, fwi)
+    loss = 0.5 * ((seis - d) ** 2).sum()
+    loss.backward()
+    _, g_ref, _ = _gpu_grad("f64")
+    assert np.allclose(m.grad.cpu().numpy(), g_ref, rtol=1e-12, atol=0)
+
+
+def test_checkpoint_stride_bit_exact():
+    from paper_2401_16322_gb300.ewave import checkpoint_stride
+    for n in range(0, 60):
+        for b in range(1, 25):
+            assert checkpoint_stride(n, b) == o_stride(n, b)
