@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
     ap.add_argument("--no-search", action="store_true", help="use the default selection")
     ap.add_argument("--T", type=float, default=T_END, help="simulated time (profiling runs)")
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP64 and FWI side runs")
     ap.add_argument("--case", default="full", choices=["full", "small", "medium"],
                     help="small / medium: the 1001x501 model with 4 / 16 shots (profiling)")
     return ap.parse_args()
@@ -198,6 +199,67 @@ def batch_points(workloads):
     return sum(w.nx * w.ny * len(w.shots) for w in workloads)
 
 
+def fp64_single_shot_estimate(wl, method, m, dt, nsteps, c_max, steps_sample=3):
+    """The plain FP64 single-shot form of the selected method: every model alone, one shot,
+    timed for a few steps and scaled to all shots and steps (seconds)."""
+    import torch
+    from paper_2401_16322_gb300.tts import build_models, common_ellipse
+    from paper_2401_16322_gb300.workloads import Workload
+    total = 0.0
+    for w in wl:
+        one = Workload(w.name, w.nx, w.ny, w.dx, w.order, w.pml, w.free_surface, w.c, w.shots[:1],
+                       w.f_peak, w.T)
+        md = build_models([one], "f64", p=12, c_max=c_max)[0]
+        common_ellipse([md], c_max)
+        md.ensure_workspace(method, m)
+        md.step(method, 0.25, dt, m, 1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        md.step(method, 0.25, dt, m, steps_sample)
+        e1.record()
+        torch.cuda.synchronize()
+        total += e0.elapsed_time(e1) / steps_sample * nsteps * len(w.shots) * 1e-3
+        md.close()
+    return {"time_to_solution_s": total, "sample": f"{steps_sample} FP64 steps of one shot per "
+            "model, scaled to every shot and step, one shot per launch"}
+
+
+def fwi_gradient_step(method, m, dt_over_cfl):
+    """FWI gradient (forward + adjoint) on the 401 x 201, 16-shot, 200-receiver workload,
+    FP32, Faber at the selected degree and step ratio; every state checkpointed."""
+    import numpy as np
+    import torch
+    from paper_2401_16322_gb300.fwi import FaberFWI
+    from paper_2401_16322_gb300.tts import build_models, common_ellipse, leapfrog_step
+    from paper_2401_16322_gb300.workloads import config_fwi, smooth_gradient_with_anomalies
+    if method != "faber":
+        return None
+    w = config_fwi()
+    c_max = float(w.c.max()) * 1.05
+    dt = dt_over_cfl * leapfrog_step(c_max, w.dx, w.order)
+    nsteps = int(round(w.T / dt))
+    md = build_models([w], "f32", p=12, c_max=c_max)[0]
+    common_ellipse([md], c_max)
+    fwi = FaberFWI(md, dt, m, nsteps, len(w.shots[0].rec))
+    d_obs = fwi.forward(w.c ** 2)
+    c_init = smooth_gradient_with_anomalies(w.nx, w.ny, 0, dx=w.dx, amps=())
+    fwi.forward(c_init ** 2)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    seis = fwi.forward(c_init ** 2)
+    grad = fwi.backward(seis - d_obs)
+    e1.record()
+    torch.cuda.synchronize()
+    ok = bool(torch.isfinite(grad).all())
+    mem = fwi.ckpt.numel() * fwi.ckpt.element_size()
+    md.close()
+    return {"seconds": e0.elapsed_time(e1) * 1e-3, "nsteps": nsteps, "dt_ms": dt * 1e3, "m": m,
+            "shots": len(w.shots), "grid": f"{w.nx}x{w.ny}", "checkpoint_bytes": mem,
+            "gradient_finite": ok}
+
+
 # ------------------------------------------------------------------------- reference arm
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -340,6 +402,10 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / args.steps
 
+    extras = {}
+    if rank == 0 and args.case == "full" and not args.no_extras:
+        extras["fp64_single_shot"] = fp64_single_shot_estimate(wl, method, m, dt, nsteps, c_max)
+        extras["fwi_gradient"] = fwi_gradient_step(method, m, dt / dt_cfl)
     result = None
     if rank == 0:
         cpu_pps, cpu_desc, cores = cpu_oracle_sample(config_batched(), method, m, dt, args.cpu_sample_s)
@@ -374,6 +440,8 @@ def run_ours(args):
             "clocks": clocks,
             "leapfrog_f32": ({"dt_ms": lf.dt * 1e3, "seismo_rel_err": lf.err,
                               "time_to_solution_s": lf.cost_s} if lf else None),
+            "fp64_single_shot": extras.get("fp64_single_shot"),
+            "fwi_gradient": extras.get("fwi_gradient"),
             "search_s": study.seconds if study else None,
             "reference_self_check": study.ref_self_check if study else None,
             "candidates": ([{"method": c.method, "m": c.m, "dt_ms": round(c.dt * 1e3, 4),

@@ -279,6 +279,14 @@ const char* ewv_last_error(ewv_model_t model);
 const char* ewv_batch_last_error(ewv_batch_t batch);
 /* Library version string. */
 const char* ewv_version(void);
+/* CUDA graphs (default on): a step call launches its first step directly, captures the
+ * launch sequence of one step into a CUDA graph (once per method, m, dt and Faber ellipse)
+ * and replays it for the remaining steps; steps read their time from a device-side clock,
+ * so the graph has no per-step parameters.  Off: every kernel is launched directly.
+ * Capture is skipped while kernel timing is enabled. */
+int ewv_enable_graphs(ewv_model_t model, int enable);
+int ewv_batch_enable_graphs(ewv_batch_t batch, int enable);
+
 /* Event timing of the fused stencil passes (the hot kernel): when enabled, every stencil
  * pass launch is bracketed by a pair of CUDA events on the handle's stream.
  * ewv_*kernel_timing synchronises the stream, returns the summed device time (ms) and the

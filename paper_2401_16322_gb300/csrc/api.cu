@@ -182,11 +182,26 @@ struct Engine {
     size_t d_adj_bytes = 0;
     int* d_err = nullptr;       // timeout word written by the TMA kernel
     std::map<std::tuple<double, int, double, double, double>, std::vector<double>> faber_cache;
+    // CUDA graphs of one step's launch sequence, keyed by (method, m, dt, g, c0, c1, parity)
+    std::map<std::tuple<int, int, double, double, double, double, int>,
+             std::pair<cudaGraphExec_t, long long>> graphs;
+    bool graphs_enabled = true;
+    bool graphs_broken = false;
+    cudaStream_t cap = nullptr;              // capturable stream used while graphs are on
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    void drop_graphs() {
+        for (auto& kv : graphs) cudaGraphExecDestroy(kv.second.first);
+        graphs.clear();
+    }
     // optional CUDA-event timing of the fused stencil passes (pairs around each launch)
     bool timing = false;
     std::vector<cudaEvent_t> events;
     size_t events_used = 0;
     ~Engine() {
+        drop_graphs();
+        if (cap) cudaStreamDestroy(cap);
+        if (ev_in) cudaEventDestroy(ev_in);
+        if (ev_out) cudaEventDestroy(ev_out);
         for (cudaEvent_t e : events) cudaEventDestroy(e);
         cudaFree(d_probs);
         cudaFree(d_tile_prob);
@@ -317,6 +332,7 @@ ProblemDev make_problem(ewv_model* m, int shot, int tile_base) {
 // Workspace per shot: `nvec` vectors; shots' workspaces are laid out back to back with a
 // per-shot stride of (work_bytes / nshots) rounded down to whole vectors.
 int build_engine(Engine* E, std::string& err) {
+    E->drop_graphs();
     E->probs.clear();
     std::vector<int> work_vecs;
     int tb = 0;
@@ -446,6 +462,53 @@ struct Ctx {
         launch_record(E->precision, E->d_probs, E->nprob, vec, s);
         ++*launches;
     }
+    // Run nsteps steps.  Steps are parameter-free (time comes from the device clock), so
+    // after the first step(s) the launch sequence of one step is captured once into a CUDA
+    // graph and replayed; `nparity` distinct sequences alternate (leap-frog buffer swap).
+    // Capture is skipped while kernel timing is on; a failed capture falls back to direct
+    // launches for this engine.
+    template <class F>
+    int step_loop(int nsteps, int method, int m, double dt, double g, double c0, double c1,
+                  int nparity, F&& one_step) {
+        for (int n = 0; n < nsteps; ++n) {
+            const int par = n % nparity;
+            const bool use_graph = E->graphs_enabled && !E->timing && !E->graphs_broken && n >= nparity;
+            if (!use_graph) {
+                one_step(n);
+                continue;
+            }
+            auto key = std::make_tuple(method, m, dt, g, c0, c1, par);
+            auto it = E->graphs.find(key);
+            if (it == E->graphs.end()) {
+                const long long L0 = *launches;
+                cudaGraph_t gr = nullptr;
+                cudaGraphExec_t ex = nullptr;
+                if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+                    cudaGetLastError();
+                    E->graphs_broken = true;
+                    one_step(n);
+                    continue;
+                }
+                one_step(n);
+                const cudaError_t e1 = cudaStreamEndCapture(s, &gr);
+                const long long nodes = *launches - L0;
+                *launches = L0;
+                if (e1 != cudaSuccess || cudaGraphInstantiate(&ex, gr, 0) != cudaSuccess) {
+                    if (gr) cudaGraphDestroy(gr);
+                    cudaGetLastError();
+                    E->graphs_broken = true;
+                    one_step(n);
+                    continue;
+                }
+                cudaGraphDestroy(gr);
+                it = E->graphs.emplace(key, std::make_pair(ex, nodes)).first;
+            }
+            const cudaError_t e = cudaGraphLaunch(it->second.first, s);
+            if (e != cudaSuccess) return fail(*err, EWV_ERR_CUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
+            *launches += it->second.second;
+        }
+        return EWV_OK;
+    }
 };
 
 int check_launch(std::string& err) {
@@ -472,7 +535,7 @@ int run_faber(Ctx& C, double t, double dt, int m, int nsteps, double g, double c
     const std::vector<double>& a = it->second;
     launch_set_clock(C.E->d_probs, C.E->nprob, t, dt, C.s);
     ++*C.launches;
-    for (int n = 0; n < nsteps; ++n) {
+    int rc = C.step_loop(nsteps, EWV_METHOD_FABER, m, dt, g, c0, c1, 1, [&](int) {
         C.prologue(PRO_FABER, m, g, c0, c1);
         StageArgs s1 = stage_defaults();
         s1.x = 0;
@@ -522,7 +585,8 @@ int run_faber(Ctx& C, double t, double dt, int m, int nsteps, double g, double c
             }
         }
         C.record();
-    }
+    });
+    if (rc != EWV_OK) return rc;
     return check_launch(err);
 }
 
@@ -551,7 +615,7 @@ int run_hork(Ctx& C, double t, double dt, int m, int nsteps) {
     auto wgt = [&](int i) { return i <= m - 2 ? lam[i] : (i == m - 1 ? 0.0 : lam[m - 1]); };
     launch_set_clock(C.E->d_probs, C.E->nprob, t, dt, C.s);
     ++*C.launches;
-    for (int n = 0; n < nsteps; ++n) {
+    int rc = C.step_loop(nsteps, EWV_METHOD_HORK, m, dt, 0, 0, 0, 1, [&](int) {
         C.prologue(PRO_HORK, m);
         if (m == 1) {
             StageArgs s1 = stage_defaults();
@@ -565,7 +629,7 @@ int run_hork(Ctx& C, double t, double dt, int m, int nsteps) {
             C.stage(s1);
             C.copy(1, 0, 0xF, false);
             C.record();
-            continue;
+            return;
         }
         for (int i = 1; i <= m; ++i) {
             StageArgs si = stage_defaults();
@@ -597,14 +661,15 @@ int run_hork(Ctx& C, double t, double dt, int m, int nsteps) {
             C.stage(si);
         }
         C.record();
-    }
+    });
+    if (rc != EWV_OK) return rc;
     return check_launch(err);
 }
 
 int run_rk(Ctx& C, double t, double dt, int scheme, int nsteps) {
     launch_set_clock(C.E->d_probs, C.E->nprob, t, dt, C.s);
     ++*C.launches;
-    for (int n = 0; n < nsteps; ++n) {
+    int rc = C.step_loop(nsteps, scheme, 0, dt, 0, 0, 0, 1, [&](int) {
         if (scheme == EWV_METHOD_RK32) {
             C.prologue(PRO_RK32, 3);
             const int xs[3] = {0, 1, 2}, ys[3] = {1, 2, 0};
@@ -640,7 +705,8 @@ int run_rk(Ctx& C, double t, double dt, int scheme, int nsteps) {
             C.stage(a);
         }
         C.record();
-    }
+    });
+    if (rc != EWV_OK) return rc;
     return check_launch(*C.err);
 }
 
@@ -650,7 +716,8 @@ int run_krylov(Ctx& C, double t, double dt, int m, int nsteps, int* info) {
     const double tol = C.E->precision == EWV_F64 ? 1e-14 : 1e-6;
     launch_set_clock(C.E->d_probs, C.E->nprob, t, dt, C.s);
     ++*C.launches;
-    for (int n = 0; n < nsteps; ++n) {
+    bool expm_ok = true;
+    int rc0 = C.step_loop(nsteps, EWV_METHOD_KRYLOV, m, dt, tol, 0, 0, 1, [&](int) {
         C.prologue(PRO_KRYLOV, m);
         PointArgs pn{};
         pn.mode = 0;
@@ -690,15 +757,16 @@ int run_krylov(Ctx& C, double t, double dt, int m, int nsteps, int* info) {
                 C.point(pm);
             }
         }
-        if (launch_expm(C.E->d_probs, C.E->nprob, m, C.s) != 0)
-            return fail(err, EWV_ERR_CUDA, "expm shared-memory configuration failed");
+        if (launch_expm(C.E->d_probs, C.E->nprob, m, C.s) != 0) expm_ok = false;
         ++*C.launches;
         PointArgs pc{};
         pc.mode = 2;
         pc.m = m;
         C.point(pc);
         C.record();
-    }
+    });
+    if (rc0 != EWV_OK) return rc0;
+    if (!expm_ok) return fail(err, EWV_ERR_CUDA, "expm shared-memory configuration failed");
     int rc = check_launch(err);
     if (rc != EWV_OK) return rc;
     // read back the effective dimensions and the non-finite flags
@@ -729,16 +797,17 @@ int run_leapfrog(Ctx& C, std::vector<ewv_model*>& models, double t, double dt, i
     }
     launch_set_clock(C.E->d_probs, C.E->nprob, t, dt, C.s);
     ++*C.launches;
-    int cur = 0, prev = 1;
-    for (int n = 0; n < nsteps; ++n) {
+    // step n reads level n from vector (n even ? 0 : 1) and writes level n+1 over the other
+    int rc = C.step_loop(nsteps, EWV_METHOD_LEAPFROG, variant, dt, 0, 0, 0, 2, [&](int n) {
+        const int cur = (n & 1) ? 1 : 0, prev = 1 - cur;
         C.prologue(PRO_LEAPFROG, 1);
         launch_leapfrog(C.E->precision, C.E->R, C.E->ntiles, C.E->d_probs, C.E->d_tile_prob,
                         cur, prev, variant, dt, C.s);
         ++*C.launches;
-        std::swap(cur, prev);
-        C.record(cur);
-    }
-    if (cur != 0) C.copy(1, 0, 0xD, true);   // level n back into the state, n-1 into history
+        C.record(prev);
+    });
+    if (rc != EWV_OK) return rc;
+    if (nsteps & 1) C.copy(1, 0, 0xD, true);   // level n back into the state, n-1 into history
     return check_launch(*C.err);
 }
 
@@ -774,9 +843,28 @@ int dispatch(std::vector<ewv_model*>& models, Engine* E, cudaStream_t s, long lo
     if (rc != EWV_OK) return rc;
     rc = engine_ready(E, err);
     if (rc != EWV_OK) return rc;
-    Ctx C{E, s, launches, &err};
+    // With graphs on, run the call on the engine's own (capturable, non-blocking) stream,
+    // ordered after the caller's stream and before whatever the caller enqueues next.
+    cudaStream_t run_s = s;
+    const bool own = E->graphs_enabled && !E->timing && !E->graphs_broken;
+    if (own) {
+        if (!E->cap) {
+            CUDA_OR_FAIL(err, cudaStreamCreateWithFlags(&E->cap, cudaStreamNonBlocking));
+            CUDA_OR_FAIL(err, cudaEventCreateWithFlags(&E->ev_in, cudaEventDisableTiming));
+            CUDA_OR_FAIL(err, cudaEventCreateWithFlags(&E->ev_out, cudaEventDisableTiming));
+        }
+        CUDA_OR_FAIL(err, cudaEventRecord(E->ev_in, s));
+        CUDA_OR_FAIL(err, cudaStreamWaitEvent(E->cap, E->ev_in, 0));
+        run_s = E->cap;
+    }
+    Ctx C{E, run_s, launches, &err};
     rc = dispatch_method(C, models, method, t, dt, mm, nsteps, info);
+    if (own) {
+        cudaEventRecord(E->ev_out, run_s);
+        cudaStreamWaitEvent(s, E->ev_out, 0);
+    }
     if (rc != EWV_OK) return rc;
+    s = run_s;
     int herr = 0;
     CUDA_OR_FAIL(err, cudaMemcpyAsync(&herr, E->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     CUDA_OR_FAIL(err, cudaStreamSynchronize(s));
@@ -1256,6 +1344,19 @@ static int read_timing(Engine* E, cudaStream_t s, std::string& err, double* tota
     if (total_ms) *total_ms = tot;
     if (count) *count = (long long)(E->events_used / 2);
     E->events_used = 0;
+    return EWV_OK;
+}
+
+int ewv_enable_graphs(ewv_model_t m, int enable) {
+    if (!m) return EWV_ERR_INVALID_ARG;
+    Engine* E = ensure_model_engine(m);
+    E->graphs_enabled = enable != 0;
+    return EWV_OK;
+}
+
+int ewv_batch_enable_graphs(ewv_batch_t b, int enable) {
+    if (!b) return EWV_ERR_INVALID_ARG;
+    b->engine->graphs_enabled = enable != 0;
     return EWV_OK;
 }
 

@@ -36,7 +36,7 @@ EXPORTS = [
     "ewv_batch_last_error", "ewv_version", "ewv_launch_count", "ewv_enable_kernel_timing",
     "ewv_kernel_timing", "ewv_batch_enable_kernel_timing", "ewv_batch_kernel_timing", "ewv_reset_state",
     "ewv_faber_step_noalloc", "ewv_adjoint_step", "ewv_adjoint_inject", "ewv_checkpoint_stride",
-    "ewv_sum_shot_fields",
+    "ewv_sum_shot_fields", "ewv_enable_graphs", "ewv_batch_enable_graphs",
 ]
 
 
@@ -126,6 +126,8 @@ def load_library(path=LIB_PATH):
         "ewv_adjoint_inject": ([vp, vp, vp], i),
         "ewv_checkpoint_stride": ([i, i, ctypes.POINTER(i)], i),
         "ewv_sum_shot_fields": ([vp, vp, vp], i),
+        "ewv_enable_graphs": ([vp, i], i),
+        "ewv_batch_enable_graphs": ([vp, i], i),
         "ewv_faber_step_noalloc": ([ctypes.POINTER(NoallocFaberArgs), vp, vp, d, d, i, i, vp], i),
         "ewv_enable_kernel_timing": ([vp, i], i),
         "ewv_kernel_timing": ([vp, dp, ctypes.POINTER(ctypes.c_longlong)], i),
@@ -343,6 +345,9 @@ class Model:
         self._check(self.lib.ewv_sum_shot_fields(self.h, ctypes.c_void_p(per_shot.data_ptr()),
                                                  ctypes.c_void_p(out.data_ptr())), "sum_shot_fields")
 
+    def enable_graphs(self, on=True):
+        self._check(self.lib.ewv_enable_graphs(self.h, int(on)))
+
     def enable_kernel_timing(self, on=True):
         self._check(self.lib.ewv_enable_kernel_timing(self.h, int(on)))
 
@@ -411,6 +416,9 @@ class Batch:
             self._check(self.lib.ewv_batch_step_leapfrog(self.h, t, dt, nsteps), "batch_step_leapfrog")
         else:
             raise ValueError(method)
+
+    def enable_graphs(self, on=True):
+        self._check(self.lib.ewv_batch_enable_graphs(self.h, int(on)), "graphs")
 
     def enable_kernel_timing(self, on=True):
         self._check(self.lib.ewv_batch_enable_kernel_timing(self.h, int(on)), "timing")
