@@ -201,9 +201,11 @@ int ewv_set_leapfrog_variant(ewv_model_t model, int variant);
  * lambda by (dPhi_n/dU)^T lambda and accumulates grad += (dPhi_n/dm)^T lambda into grad
  * (nshots padded fields [ny][pitch] of the model's precision, one per shot; sum them for
  * the model gradient).  t = t_{n-1}, dt, m as in the forward ewv_step_faber call (same
- * ellipse).  Needs ewv_workspace_bytes(EWV_METHOD_ADJOINT_FABER, m) of workspace (the step
- * is recomputed from the checkpoint: m tape vectors + 3 cotangents).  method must be
- * EWV_METHOD_FABER (UNSUPPORTED otherwise).  Buffers 256-B aligned, caller-owned.
+ * ellipse).  method EWV_METHOD_FABER (reverse three-term recurrence) or EWV_METHOD_HORK
+ * (m = stages; reverse of the (I + dt H~) chain); UNSUPPORTED otherwise.  Needs
+ * ewv_workspace_bytes(EWV_METHOD_ADJOINT_FABER, m) of workspace (the step is recomputed
+ * from the checkpoint: m tape vectors + 3 cotangents).  Buffers 256-B aligned,
+ * caller-owned.
  *
  * ewv_adjoint_inject: lambda_u += R^T values at the receivers, values [nshots][max_receivers]
  * of the model's precision (the seismogram cotangent of one sample).
@@ -286,6 +288,20 @@ const char* ewv_version(void);
  * Capture is skipped while kernel timing is enabled. */
 int ewv_enable_graphs(ewv_model_t model, int enable);
 int ewv_batch_enable_graphs(ewv_batch_t batch, int enable);
+
+/* Tile-shape autotuner of the FP32 persistent TMA pass.  Variants (tile height, consumer
+ * warps, pipeline stages): 0 = (16, 16, 3), 1 = (16, 8, 3), 2 = (8, 8, 5), 3 = (8, 16, 5);
+ * tiles are 64 columns wide with a 4-column / R-row halo.  With v = -1 (default) the first
+ * FP32 step call times every variant on a probe pass over the engine's own problems and
+ * keeps the fastest; ewv_*kernel_variant reports the choice, its shape and the probe times
+ * (us[4], -1 where a variant could not launch). */
+#define EWV_NUM_KERNEL_VARIANTS 4
+int ewv_set_kernel_variant(ewv_model_t model, int variant);
+int ewv_kernel_variant(ewv_model_t model, int* variant, int* tile_height, int* warps,
+                       int* stages, double* probe_us);
+int ewv_batch_set_kernel_variant(ewv_batch_t batch, int variant);
+int ewv_batch_kernel_variant(ewv_batch_t batch, int* variant, int* tile_height, int* warps,
+                             int* stages, double* probe_us);
 
 /* Event timing of the fused stencil passes (the hot kernel): when enabled, every stencil
  * pass launch is bracketed by a pair of CUDA events on the handle's stream.

@@ -16,6 +16,10 @@ m enters only the v-row of H (Eq. 1): d(H x)_v / dm = L x_u + D x_w (the Laplaci
 divergence of w), so dJ/dm += (1/gamma) sum_{j=1..m} q_{j,v} * G(p_{j-1}), G(x) = L x_u + D x_w.
 Time loop: lambda^N = R^T r^N, lambda^{n-1} = q_0(lambda^n) + R^T r^{n-1}.
 
+HORK (Sec. 3.2) is handled the same way: u^{n+1} = sum_i w_i k_i, k_i = (I + dt H~) k_{i-1}
+with w_i the lambda weights; r_m = w_m ybar, r_{i-1} = w_{i-1} ybar + (I + dt H)^T r_i and
+dJ/dm += dt sum_i r_{i,v} G(k_{i-1}).
+
 This route is independent of the CUDA path: B^T uses the transposed sparse matrix of
 ``oracle.operator.assemble_H``.  Pins: tests/test_oracle_adjoint.py (dot-product identity
 of one adjoint step; central finite differences of J along seeded directions).
@@ -92,7 +96,52 @@ def faber_adjoint_step(model, U_prev_flat, ybar, src, t_n, dt, m, params, HT=Non
     return q_cur, grad
 
 
-def faber_forward(model, shots, dt, nsteps, m, params, U0=None):
+def hork_weights(m):
+    """Weights w_i of u^{n+1} = sum_{i=0}^{m} w_i k_i for HORK (Sec. 3.2): w_i = lambda_i
+    (i <= m-2), w_{m-1} = 0, w_m = lambda_{m-1}."""
+    from .rk import hork_lambdas
+    lam = hork_lambdas(m)
+    w = [0.0] * (m + 1)
+    for i in range(m + 1):
+        w[i] = lam[i] if i <= m - 2 else (0.0 if i == m - 1 else lam[m - 1])
+    return w
+
+
+def hork_tape(model, U_flat, src, t_n, dt, m):
+    """k_0 = [U; e_p], k_i = (I + dt H~) k_{i-1}; returns (k_0..k_m U parts, U^{n+1})."""
+    p = src.p if src is not None else 1
+    w = src.W(t_n, dt) if src is not None else np.zeros(p)
+    y = np.zeros(p)
+    y[-1] = 1.0
+    ks = [U_flat.copy()]
+    x = U_flat.copy()
+    for _ in range(m):
+        val = float(np.dot(w, y))
+        HU = apply_H(model, unflatten(model, x), None if src is None else (src.j, src.i, val))
+        x = x + dt * flatten(HU)
+        y = y + dt * tail_apply(y, dt)
+        ks.append(x)
+    wt = hork_weights(m)
+    return ks, sum(wt[i] * ks[i] for i in range(m + 1))
+
+
+def hork_adjoint_step(model, U_prev_flat, ybar, src, t_n, dt, m, HT=None):
+    """Cotangent of U^{n-1} and the gradient contribution of one HORK step:
+    r_m = w_m ybar, r_{i-1} = w_{i-1} ybar + (I + dt H)^T r_i, grad += dt r_{i,v} G(k_{i-1})."""
+    ks, _ = hork_tape(model, U_prev_flat, src, t_n, dt, m)
+    if HT is None:
+        HT = assemble_H(model).T.tocsr()
+    wt = hork_weights(m)
+    nu = model.nx * model.ny
+    grad = np.zeros(nu)
+    r = wt[m] * ybar
+    for i in range(m, 0, -1):
+        grad += dt * r[nu:2 * nu] * G_of(model, ks[i - 1])
+        r = wt[i - 1] * ybar + r + dt * (HT @ r)
+    return r, grad
+
+
+def faber_forward(model, shots, dt, nsteps, m, params, U0=None, method="faber"):
     """Forward simulation of every shot; returns (states per shot [N+1 flat], seismograms)."""
     states, seis = [], []
     for src, rec_nodes in shots:
@@ -100,7 +149,10 @@ def faber_forward(model, shots, dt, nsteps, m, params, U0=None):
         Us = [U]
         S = []
         for n in range(nsteps):
-            _, U = faber_tape(model, U, src, n * dt, dt, m, params)
+            if method == "faber":
+                _, U = faber_tape(model, U, src, n * dt, dt, m, params)
+            else:
+                _, U = hork_tape(model, U, src, n * dt, dt, m)
             Us.append(U)
             S.append(unflatten(model, U)[0][rec_nodes[:, 0], rec_nodes[:, 1]].copy())
         states.append(Us)
@@ -112,9 +164,9 @@ def misfit(seis, d_obs):
     return 0.5 * sum(float(np.sum((s - d) ** 2)) for s, d in zip(seis, d_obs))
 
 
-def fwi_gradient(model, shots, d_obs, dt, nsteps, m, params):
+def fwi_gradient(model, shots, d_obs, dt, nsteps, m, params, method="faber"):
     """dJ/dm (m = c^2 at the nodes, [ny, nx]) by the discrete adjoint; returns (J, grad)."""
-    states, seis = faber_forward(model, shots, dt, nsteps, m, params)
+    states, seis = faber_forward(model, shots, dt, nsteps, m, params, method=method)
     HT = assemble_H(model).T.tocsr()
     nu = model.nx * model.ny
     grad = np.zeros(nu)
@@ -124,7 +176,10 @@ def fwi_gradient(model, shots, d_obs, dt, nsteps, m, params):
         ridx = rec_nodes[:, 0] * model.nx + rec_nodes[:, 1]
         np.add.at(lam, ridx, r[nsteps - 1])
         for n in range(nsteps, 0, -1):
-            q0, g = faber_adjoint_step(model, Us[n - 1], lam, src, (n - 1) * dt, dt, m, params, HT)
+            if method == "faber":
+                q0, g = faber_adjoint_step(model, Us[n - 1], lam, src, (n - 1) * dt, dt, m, params, HT)
+            else:
+                q0, g = hork_adjoint_step(model, Us[n - 1], lam, src, (n - 1) * dt, dt, m, HT)
             grad += g
             lam = q0
             if n - 1 >= 1:

@@ -178,6 +178,10 @@ struct Engine {
     double* d_coef = nullptr;
     ProblemDev* d_apply = nullptr;
     void* d_maps = nullptr;     // FP32: TMA tensor maps of every problem
+    int* d_tbase = nullptr;     // per tile height (16, 8): nprob + 1 tile prefix sums
+    int ntiles_by[2] = {0, 0};
+    int tma_variant = -1;       // -1: choose by timing at first use
+    double tma_variant_us[TMA_NUM_VARIANTS] = {0, 0, 0, 0};
     ProblemDev* d_adj = nullptr;  // adjoint call: descriptors (state = cotangent) + tile map
     size_t d_adj_bytes = 0;
     int* d_err = nullptr;       // timeout word written by the TMA kernel
@@ -210,6 +214,7 @@ struct Engine {
         cudaFree(d_coef);
         cudaFree(d_apply);
         cudaFree(d_maps);
+        cudaFree(d_tbase);
         cudaFree(d_err);
         cudaFree(d_adj);
     }
@@ -314,6 +319,10 @@ ProblemDev make_problem(ewv_model* m, int shot, int tile_base) {
     P.inv_dx = 1.0 / d.dx;
     P.inv_dx2 = 1.0 / (d.dx * d.dx);
     P.inv_pml = d.pml_width > 0 ? 1.0 / d.pml_width : 0.0;
+    P.fbeta0 = (float)P.beta0;
+    P.finv_pml = (float)P.inv_pml;
+    P.finv_dx = (float)P.inv_dx;
+    P.finv_dx2 = (float)P.inv_dx2;
     P.field_stride = (long long)m->field_elems;
     P.vec_stride = (long long)m->vec_elems;
     P.state = (char*)m->state + (size_t)shot * m->vec_elems * m->elem;
@@ -348,16 +357,32 @@ int build_engine(Engine* E, std::string& err) {
             work_vecs.push_back((int)per_shot);
         }
     }
+    E->nprob = (int)E->probs.size();
+    E->ntiles = tb;
     if (E->precision == EWV_F32) {
         if (build_tensor_maps(E->probs, E->R, work_vecs, &E->d_maps) != 0)
             return fail(err, EWV_ERR_CUDA, "TMA tensor-map encoding failed");
+        std::vector<int> pre(2 * (size_t)(E->nprob + 1), 0);
+        const int heights[2] = {16, 8};
+        for (int set = 0; set < 2; ++set) {
+            int acc = 0;
+            for (int p = 0; p < E->nprob; ++p) {
+                pre[(size_t)set * (E->nprob + 1) + p] = acc;
+                const ProblemDev& P = E->probs[p];
+                acc += ((P.nx + BX - 1) / BX) * ((P.ny + heights[set] - 1) / heights[set]);
+            }
+            pre[(size_t)set * (E->nprob + 1) + E->nprob] = acc;
+            E->ntiles_by[set] = acc;
+        }
+        cudaFree(E->d_tbase);
+        E->d_tbase = nullptr;
+        CUDA_OR_FAIL(err, cudaMalloc(&E->d_tbase, sizeof(int) * pre.size()));
+        CUDA_OR_FAIL(err, cudaMemcpy(E->d_tbase, pre.data(), sizeof(int) * pre.size(), cudaMemcpyHostToDevice));
     }
     if (!E->d_err) {
         CUDA_OR_FAIL(err, cudaMalloc(&E->d_err, sizeof(int)));
         CUDA_OR_FAIL(err, cudaMemset(E->d_err, 0, sizeof(int)));
     }
-    E->nprob = (int)E->probs.size();
-    E->ntiles = tb;
     std::vector<int> tp(tb);
     for (int p = 0; p < E->nprob; ++p)
         for (int t = 0; t < E->probs[p].ntiles; ++t) tp[E->probs[p].tile_base + t] = p;
@@ -420,6 +445,7 @@ struct Ctx {
     cudaStream_t s;
     long long* launches;
     std::string* err;
+    int launch_failed = 0;      // a TMA pass could not be configured or launched
     cudaEvent_t next_event() {
         if (E->events_used == E->events.size()) {
             cudaEvent_t e;
@@ -435,9 +461,17 @@ struct Ctx {
             e1 = next_event();
             cudaEventRecord(e0, s);
         }
-        if (E->precision == EWV_F32 && !a.transpose && a.fin_mode == FIN_NONE && a.d < 0)
-            launch_stage_tma(E->R, E->ntiles, E->d_probs, E->d_tile_prob, a, E->d_err, s);
-        else
+        if (E->precision == EWV_F32 && !a.transpose && a.fin_mode == FIN_NONE && a.d < 0 && !a.grad) {
+            if (E->tma_variant < 0) autotune();
+            if (E->tma_variant < 0) {
+                launch_failed = 1;
+            } else {
+                const int set = tma_variant_tile_height(E->tma_variant) == 16 ? 0 : 1;
+                if (launch_stage_tma(E->tma_variant, E->R, E->d_probs, E->d_tbase + (size_t)set * (E->nprob + 1),
+                                     E->nprob, E->ntiles_by[set], a, E->d_err, s) != 0)
+                    launch_failed = 1;
+            }
+        } else
             launch_stage(E->precision, E->R, E->ntiles, E->d_probs, E->d_tile_prob, a, s);
         if (E->timing) cudaEventRecord(e1, s);
         ++*launches;
@@ -445,6 +479,56 @@ struct Ctx {
     void point(const PointArgs& pa) {
         launch_point(E->precision, E->ntiles, E->d_probs, E->d_tile_prob, pa, s);
         ++*launches;
+    }
+    // Tile-shape autotuner: time every persistent-kernel variant on an idempotent probe pass
+    // (reads the state, writes workspace vectors 1 and 2, which every FP32 method overwrites
+    // before reading) and keep the fastest.  Runs once per engine, outside graph capture.
+    void autotune() {
+        StageArgs p = stage_defaults();
+        p.x = 0;
+        p.u = 0;
+        p.a = 0;
+        p.y_out = 1;
+        p.acc_out = 2;
+        p.cx = 1.0;
+        p.ch = 1e-3;
+        p.cu = 1.0;
+        p.ck = 1.0;
+        p.ca = 1.0;
+        p.cay = 1.0;
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        int best = -1;
+        double best_us = 1e300;
+        for (int v = 0; v < TMA_NUM_VARIANTS; ++v) {
+            const int set = tma_variant_tile_height(v) == 16 ? 0 : 1;
+            const int* tb = E->d_tbase + (size_t)set * (E->nprob + 1);
+            if (launch_stage_tma(v, E->R, E->d_probs, tb, E->nprob, E->ntiles_by[set], p, E->d_err, s) != 0 ||
+                cudaGetLastError() != cudaSuccess) {
+                E->tma_variant_us[v] = -1.0;
+                continue;
+            }
+            double best_v = 1e300;
+            for (int rep = 0; rep < 3; ++rep) {
+                cudaEventRecord(e0, s);
+                launch_stage_tma(v, E->R, E->d_probs, tb, E->nprob, E->ntiles_by[set], p, E->d_err, s);
+                cudaEventRecord(e1, s);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                best_v = std::min(best_v, 1e3 * (double)ms);
+            }
+            E->tma_variant_us[v] = best_v;
+            if (best_v < best_us) {
+                best_us = best_v;
+                best = v;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        E->tma_variant = best;
+        *launches += 4 * TMA_NUM_VARIANTS;
     }
     void copy(int src, int dst, int fmask, bool swap) {
         PointArgs pa{};
@@ -859,6 +943,8 @@ int dispatch(std::vector<ewv_model*>& models, Engine* E, cudaStream_t s, long lo
     }
     Ctx C{E, run_s, launches, &err};
     rc = dispatch_method(C, models, method, t, dt, mm, nsteps, info);
+    if (rc == EWV_OK && C.launch_failed)
+        rc = fail(err, EWV_ERR_CUDA, "no persistent TMA stencil variant could be launched");
     if (own) {
         cudaEventRecord(E->ev_out, run_s);
         cudaStreamWaitEvent(s, E->ev_out, 0);
@@ -1347,6 +1433,42 @@ static int read_timing(Engine* E, cudaStream_t s, std::string& err, double* tota
     return EWV_OK;
 }
 
+static int set_variant(Engine* E, int v) {
+    if (v < -1 || v >= TMA_NUM_VARIANTS) return EWV_ERR_INVALID_ARG;
+    E->tma_variant = v;
+    return EWV_OK;
+}
+
+static int get_variant(Engine* E, int* v, int* by, int* nw, int* nst, double* us) {
+    if (!v) return EWV_ERR_INVALID_ARG;
+    *v = E->tma_variant;
+    int b = 0, w = 0, n = 0;
+    if (E->tma_variant >= 0) tma_variant_describe(E->tma_variant, &b, &w, &n);
+    if (by) *by = b;
+    if (nw) *nw = w;
+    if (nst) *nst = n;
+    if (us)
+        for (int k = 0; k < TMA_NUM_VARIANTS; ++k) us[k] = E->tma_variant_us[k];
+    return EWV_OK;
+}
+
+int ewv_set_kernel_variant(ewv_model_t m, int v) {
+    if (!m) return EWV_ERR_INVALID_ARG;
+    return set_variant(ensure_model_engine(m), v);
+}
+int ewv_kernel_variant(ewv_model_t m, int* v, int* by, int* nw, int* nst, double* us) {
+    if (!m) return EWV_ERR_INVALID_ARG;
+    return get_variant(ensure_model_engine(m), v, by, nw, nst, us);
+}
+int ewv_batch_set_kernel_variant(ewv_batch_t b, int v) {
+    if (!b) return EWV_ERR_INVALID_ARG;
+    return set_variant(b->engine, v);
+}
+int ewv_batch_kernel_variant(ewv_batch_t b, int* v, int* by, int* nw, int* nst, double* us) {
+    if (!b) return EWV_ERR_INVALID_ARG;
+    return get_variant(b->engine, v, by, nw, nst, us);
+}
+
 int ewv_enable_graphs(ewv_model_t m, int enable) {
     if (!m) return EWV_ERR_INVALID_ARG;
     Engine* E = ensure_model_engine(m);
@@ -1390,8 +1512,8 @@ int ewv_batch_kernel_timing(ewv_batch_t b, double* total_ms, long long* launches
 int ewv_adjoint_step(ewv_model_t m, int method, double t, double dt, int deg,
                      const void* checkpoint, void* adj_state, void* grad) {
     if (!m || !checkpoint || !adj_state || !grad) return EWV_ERR_INVALID_ARG;
-    if (method != EWV_METHOD_FABER)
-        return fail(m->err, EWV_ERR_UNSUPPORTED, "adjoint implemented for the Faber step only");
+    if (method != EWV_METHOD_FABER && method != EWV_METHOD_HORK)
+        return fail(m->err, EWV_ERR_UNSUPPORTED, "adjoint implemented for the Faber and HORK steps");
     if (deg < 1 || deg > MAX_DEG || !(dt > 0.0))
         return fail(m->err, EWV_ERR_INVALID_ARG, "degree must be 1..%d and dt > 0", MAX_DEG);
     if (!aligned(checkpoint) || !aligned(adj_state) || !aligned(grad))
@@ -1435,6 +1557,60 @@ int ewv_adjoint_step(ewv_model_t m, int method, double t, double dt, int deg,
     // checkpoint U^{n-1} -> tape slot T_0 (workspace vector 1) of every shot
     CUDA_OR_FAIL(m->err, cudaMemcpy2DAsync(m->work, per_shot * vb, checkpoint, vb, vb, ns,
                                            cudaMemcpyDeviceToDevice, s));
+    const int R = m->R, prec = m->d.precision;
+    auto stage = [&](const StageArgs& sa) {
+        launch_stage(prec, R, tb, E->d_adj, d_tp, sa, s);
+        ++m->launches;
+    };
+    if (method == EWV_METHOD_HORK) {
+        // u^{n+1} = sum_i w_i k_i, k_i = (I + dt H~) k_{i-1}; tape T_k = k_k = vector k+1
+        const std::vector<double> lam = hork_lambdas(deg);
+        auto w = [&](int i) { return i <= deg - 2 ? lam[i] : (i == deg - 1 ? 0.0 : lam[deg - 1]); };
+        launch_set_clock(E->d_adj, ns, t, dt, s);
+        launch_prologue(E->d_adj, ns, 3 /* HORK */, deg, 0.0, 0.0, 0.0, s);
+        m->launches += 2;
+        for (int j = 1; j <= deg - 1; ++j) {
+            StageArgs sa = stage_defaults();
+            sa.x = j;
+            sa.y_out = j + 1;
+            sa.src_slot = j - 1;
+            sa.cx = 1.0;
+            sa.ch = dt;
+            sa.ck = 1.0;
+            stage(sa);
+        }
+        // r_m = w_m ybar (not stored); r_{i-1} = w_{i-1} ybar + (I + dt H)^T r_i
+        auto rbuf = [&](int k) { return k == 0 ? 0 : deg + 1 + ((deg - 1 - k) % 2); };
+        for (int i = deg; i >= 1; --i) {
+            const double sc = (i == deg) ? w(deg) : 1.0;
+            StageArgs gr = stage_defaults();
+            gr.x = i;                              // k_{i-1}
+            gr.grad = grad;
+            gr.gq = (i == deg) ? 0 : rbuf(i);
+            gr.gscale = dt * sc;
+            stage(gr);
+            StageArgs tr = stage_defaults();
+            tr.transpose = 1;
+            tr.x = (i == deg) ? 0 : rbuf(i);
+            tr.cx = sc;
+            tr.ch = dt * sc;
+            tr.a = 0;
+            tr.ca = w(i - 1);
+            tr.cak = 1.0;
+            tr.acc_out = (i == 1 && deg == 1) ? deg + 1 : rbuf(i - 1);
+            stage(tr);
+        }
+        if (deg == 1) {
+            PointArgs pa{};
+            pa.mode = 3;
+            pa.src = deg + 1;
+            pa.dst = 0;
+            pa.fmask = 0xF;
+            launch_point(prec, tb, E->d_adj, d_tp, pa, s);
+            ++m->launches;
+        }
+        return check_launch(m->err);
+    }
     double g, c0, c1;
     ellipse_of(m, &g, &c0, &c1);
     auto key = std::make_tuple(dt, deg, g, c0, c1);
@@ -1449,12 +1625,7 @@ int ewv_adjoint_step(ewv_model_t m, int method, double t, double dt, int deg,
         it = E->faber_cache.emplace(key, a).first;
     }
     const std::vector<double>& a = it->second;
-    const int R = m->R, prec = m->d.precision;
     auto cprime = [&](int k) { return k <= 1 ? 0.0 : (k == 2 ? 2.0 * c1 : c1); };
-    auto stage = [&](const StageArgs& sa) {
-        launch_stage(prec, R, tb, E->d_adj, d_tp, sa, s);
-        ++m->launches;
-    };
     launch_set_clock(E->d_adj, ns, t, dt, s);
     launch_prologue(E->d_adj, ns, 1 /* Faber */, deg, g, c0, c1, s);
     m->launches += 2;

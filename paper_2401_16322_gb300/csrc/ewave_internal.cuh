@@ -61,6 +61,7 @@ struct ProblemDev {
     long long* clk;       // [4]: step within call, recording cursor, (unused), (unused)
     double* tclk;         // [2]: t_start, dt of the current call
     const void* tmaps;    // FP32: this problem's TMA tensor maps (kernels_tma.cu), else null
+    float fbeta0, finv_pml, finv_dx, finv_dx2;   // FP32 copies of the damping / grid constants
 };
 
 // Arguments of the fused stencil-stage kernel (see kernels_stencil.cu).
@@ -106,8 +107,11 @@ void launch_leapfrog(int precision, int R, int nblocks, const ProblemDev* probs,
 int upload_tma_tables(const double* fs_uyy, const double* fs_uy, const double* fs_dwy);
 int build_tensor_maps(std::vector<ProblemDev>& probs, int R, const std::vector<int>& work_vecs,
                       void** d_maps_inout);
-int launch_stage_tma(int R, int ntiles, const ProblemDev* probs, const int* tile_prob,
-                     const StageArgs& a, int* err, cudaStream_t s);
+constexpr int TMA_NUM_VARIANTS = 4;
+int launch_stage_tma(int variant, int R, const ProblemDev* probs, const int* tbase, int nprob,
+                     int ntiles, const StageArgs& a, int* err, cudaStream_t s);
+int tma_variant_tile_height(int v);
+void tma_variant_describe(int v, int* by, int* nw, int* nst);
 
 void launch_set_clock(const ProblemDev* probs, int nprob, double t, double dt, cudaStream_t s);
 void launch_reset_cursor(const ProblemDev* probs, int nprob, cudaStream_t s);

@@ -25,30 +25,37 @@
 namespace ewv {
 
 constexpr int TX = 4;                 // staged x halo (>= R, keeps the box start 16-B aligned)
-constexpr int NST = 3;                // pipeline stages
-constexpr int NCONS = 512;            // consumer threads (16 warps)
-constexpr int NR = BY / (NCONS / BX); // consecutive rows per consumer thread (2)
-constexpr int TMA_THREADS = NCONS + 32;
-constexpr int NMAP = 11;              // tensor maps per problem
+constexpr int NMAP = 11;              // tensor maps per problem and tile height
+constexpr int MAX_NST = 5;
 
-// Shared-memory layout of one stage (floats); each buffer starts on a 128-byte boundary.
-template <int R>
+// Shared-memory layout of one stage (floats) for tile height BYv; every buffer starts on a
+// 128-byte boundary.
+template <int R, int BYv>
 struct StageLayout {
-    static constexpr int SH = BY + 2 * R;
+    static constexpr int SH = BYv + 2 * R;
     static constexpr int SW = BX + 2 * TX;
     static constexpr int U_OFF = 0;                          // u      SH x SW
-    static constexpr int WX_OFF = U_OFF + SH * SW;           // w_x    BY x SW
-    static constexpr int WY_OFF = WX_OFF + BY * SW;          // w_y    SH x BX
-    static constexpr int V_OFF = WY_OFF + SH * BX;           // v      BY x BX
-    static constexpr int C2_OFF = V_OFF + BY * BX;           // c^2    BY x BX
-    static constexpr int PU_OFF = C2_OFF + BY * BX;          // U      4 x BY x BX
-    static constexpr int PA_OFF = PU_OFF + 4 * BY * BX;      // A      4 x BY x BX
-    static constexpr int FLOATS = PA_OFF + 4 * BY * BX;
+    static constexpr int WX_OFF = U_OFF + SH * SW;           // w_x    BYv x SW
+    static constexpr int WY_OFF = WX_OFF + BYv * SW;         // w_y    SH x BX
+    static constexpr int V_OFF = WY_OFF + SH * BX;           // v      BYv x BX
+    static constexpr int C2_OFF = V_OFF + BYv * BX;          // c^2    BYv x BX
+    static constexpr int PU_OFF = C2_OFF + BYv * BX;         // U      4 x BYv x BX
+    static constexpr int PA_OFF = PU_OFF + 4 * BYv * BX;     // A      4 x BYv x BX
+    static constexpr int FLOATS = PA_OFF + 4 * BYv * BX;
     static constexpr int BYTES = FLOATS * 4;
     static_assert((U_OFF * 4) % 128 == 0 && (WX_OFF * 4) % 128 == 0 && (WY_OFF * 4) % 128 == 0 &&
                       (V_OFF * 4) % 128 == 0 && (C2_OFF * 4) % 128 == 0 &&
                       (PU_OFF * 4) % 128 == 0 && (PA_OFF * 4) % 128 == 0 && BYTES % 128 == 0,
                   "TMA destinations must be 128-byte aligned");
+};
+
+// What the producer resolves once per tile and hands to the consumers with the stage.
+struct TileInfo {
+    float* Y;
+    float* A;
+    long long fstr;
+    int x0, y0, nx, ny, pitch, pml, fs, src_i, src_j, pad0;
+    float beta0, inv_pml, idx1, idx2, sig, pad1;
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -108,9 +115,6 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
         "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_addr(bar))
         : "memory");
 }
-__device__ __forceinline__ void named_bar_sync(int id, int n) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
-}
 
 __constant__ float g_tma_fs[4 * 9 + 3 * 8 + 4 * 8];
 constexpr int TFS_UYY = 0, TFS_UY = 36, TFS_DWY = 60;
@@ -147,31 +151,46 @@ __device__ __forceinline__ float dampf(float beta0, float inv_pml, float d, int 
     return (d <= (float)pml) ? beta0 * r * r : 0.f;
 }
 
-// Map index of field box `kind` (0 u, 1 w_x, 2 w_y, 3 v, 4 four fields) for vector k, and
-// the vector coordinate inside that map.
+// Map of field box `kind` (0 u, 1 w_x, 2 w_y, 3 v, 4 four fields) for vector k.
 __device__ __forceinline__ const CUtensorMap* map_of(const CUtensorMap* base, int k, int kind) {
     return base + (k == 0 ? 0 : 5) + kind;
 }
 
-template <int R>
-__global__ void __launch_bounds__(TMA_THREADS, 1)
-stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ tile_prob,
-                 int ntiles, StageArgs a, int* err) {
-    using L = StageLayout<R>;
+// Problem of tile t: the last p with base[p] <= t (base: nprob + 1 prefix sums).
+__device__ __forceinline__ int find_problem(const int* __restrict__ base, int nprob, int t) {
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(base + mid) <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int R, int BYv, int NW, int NSTv>
+__global__ void __launch_bounds__(NW * 32 + 32, 1)
+stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ tbase, int nprob,
+                 int ntiles, int mapset, StageArgs a, int* err) {
+    using L = StageLayout<R, BYv>;
+    constexpr int NCONS = NW * 32;
+    constexpr int TPR = NCONS / BX;             // consumer thread rows
+    constexpr int NR = BYv / TPR;               // consecutive rows per consumer thread
+    static_assert(NR * TPR == BYv && NR >= 1, "tile rows must split evenly over threads");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // TMA destinations need 128-byte alignment: align the dynamic base explicitly (the
     // launch reserves 1 KB of slack for this).
     float* smem = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    __shared__ __align__(8) uint64_t full[NST];
-    __shared__ __align__(8) uint64_t empty[NST];
+    __shared__ __align__(8) uint64_t full[NSTv];
+    __shared__ __align__(8) uint64_t empty[NSTv];
+    __shared__ TileInfo info[NSTv];
     __shared__ int s_err;
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
-        for (int s = 0; s < NST; ++s) {
+        for (int s = 0; s < NSTv; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], NCONS / 32);
+            mbar_init(&empty[s], NW);
         }
         s_err = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -179,26 +198,51 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
     __syncthreads();
 
     const bool has_u = a.u >= 0, has_a = a.a >= 0;
-    const uint32_t bytes = (uint32_t)((L::PU_OFF + (has_u ? 4 * BY * BX : 0)) * 4) +
-                           (has_a ? 4 * BY * BX * 4 : 0);
+    const uint32_t bytes = (uint32_t)((L::PU_OFF + (has_u ? 4 * BYv * BX : 0)) * 4) +
+                           (has_a ? 4 * BYv * BX * 4 : 0);
     int issued = 0;
 
-    if (warp == NCONS / 32) {
+    if (warp == NW) {
         // ------------------------------------------------------------ producer
         if (lane == 0) {
             int it = 0;
             for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-                const int s = it % NST;
-                const uint32_t ph = (uint32_t)(it / NST) & 1u;
+                const int s = it % NSTv;
+                const uint32_t ph = (uint32_t)(it / NSTv) & 1u;
                 if (!mbar_wait(&empty[s], ph ^ 1u)) {
                     s_err = 1;
                     break;
                 }
-                const ProblemDev* P = probs + tile_prob[tile];
-                const CUtensorMap* maps = reinterpret_cast<const CUtensorMap*>(P->tmaps);
-                const int lt = tile - P->tile_base;
-                const int x0 = (lt % P->tiles_x) * BX, y0 = (lt / P->tiles_x) * BY;
+                const int pid = find_problem(tbase, nprob, tile);
+                const ProblemDev* P = probs + pid;
+                const CUtensorMap* maps = reinterpret_cast<const CUtensorMap*>(P->tmaps) + mapset * NMAP;
+                const int tiles_x = (P->nx + BX - 1) / BX;
+                const int lt = tile - __ldg(tbase + pid);
+                const int x0 = (lt % tiles_x) * BX, y0 = (lt / tiles_x) * BYv;
+                TileInfo& ti = info[s];
+                ti.Y = a.y_out >= 0 ? (a.y_out == 0 ? (float*)P->state
+                                                    : (float*)P->work + (long long)(a.y_out - 1) * P->vec_stride)
+                                    : nullptr;
+                ti.A = a.acc_out >= 0 ? (a.acc_out == 0 ? (float*)P->state
+                                                        : (float*)P->work + (long long)(a.acc_out - 1) * P->vec_stride)
+                                      : nullptr;
+                ti.fstr = P->field_stride;
+                ti.x0 = x0;
+                ti.y0 = y0;
+                ti.nx = P->nx;
+                ti.ny = P->ny;
+                ti.pitch = P->pitch;
+                ti.pml = P->pml;
+                ti.fs = P->fs;
+                ti.src_i = P->src_i;
+                ti.src_j = P->src_j;
+                ti.beta0 = P->fbeta0;
+                ti.inv_pml = P->finv_pml;
+                ti.idx1 = P->finv_dx;
+                ti.idx2 = P->finv_dx2;
+                ti.sig = (a.src_slot >= 0 && P->has_src) ? (float)P->sigma[a.src_slot] : 0.f;
                 float* st = smem + (size_t)s * L::FLOATS;
+                // the arrive below releases the tile info together with the copies
                 mbar_expect_tx(&full[s], bytes);
                 const int kx = a.x, cx = a.x == 0 ? 0 : a.x - 1;
                 tma_load_4d(st + L::U_OFF, map_of(maps, kx, 0), x0 - TX, y0 - R, 0, cx, &full[s]);
@@ -224,28 +268,20 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
         const float cayf = (float)a.cay, caxf = (float)a.cax;
         int it = 0;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-            const int s = it % NST;
-            const uint32_t ph = (uint32_t)(it / NST) & 1u;
+            const int s = it % NSTv;
+            const uint32_t ph = (uint32_t)(it / NSTv) & 1u;
             if (!mbar_wait(&full[s], ph)) {
                 s_err = 1;
                 break;
             }
-            const ProblemDev* P = probs + tile_prob[tile];
-            const int nx = P->nx, ny = P->ny, pitch = P->pitch, pml = P->pml;
-            const bool fs = P->fs != 0;
-            const int lt = tile - P->tile_base;
-            const int x0 = (lt % P->tiles_x) * BX, y0 = (lt / P->tiles_x) * BY;
-            const long long fstr = P->field_stride;
-            const float beta0 = (float)P->beta0, inv_pml = (float)P->inv_pml;
-            const float idx1 = (float)P->inv_dx, idx2 = (float)P->inv_dx2;
-            const float sig = (a.src_slot >= 0 && P->has_src) ? (float)P->sigma[a.src_slot] : 0.f;
-            const int src_i = P->src_i, src_j = P->src_j;
-            float* Yg = a.y_out >= 0 ? (a.y_out == 0 ? (float*)P->state
-                                                     : (float*)P->work + (long long)(a.y_out - 1) * P->vec_stride)
-                                     : nullptr;
-            float* Ag = a.acc_out >= 0 ? (a.acc_out == 0 ? (float*)P->state
-                                                         : (float*)P->work + (long long)(a.acc_out - 1) * P->vec_stride)
-                                       : nullptr;
+            const TileInfo& ti = info[s];
+            const int nx = ti.nx, ny = ti.ny, pml = ti.pml;
+            const bool fs = ti.fs != 0;
+            const int y0 = ti.y0;
+            const long long fstr = ti.fstr;
+            const float beta0 = ti.beta0, inv_pml = ti.inv_pml, idx1 = ti.idx1, idx2 = ti.idx2;
+            float* Yg = ti.Y;
+            float* Ag = ti.A;
             const float* st = smem + (size_t)s * L::FLOATS;
             const float* su = st + L::U_OFF;
             const float* swx = st + L::WX_OFF;
@@ -254,9 +290,8 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
             const float* sc2 = st + L::C2_OFF;
             const float* spu = st + L::PU_OFF;
             const float* spa = st + L::PA_OFF;
-            const int i = x0 + tx;
+            const int i = ti.x0 + tx;
             const int cxs = tx + TX;                     // staged column of this thread
-            // column of u (staged rows NR ty .. NR ty + NR - 1 + 2R) and of w_y (one fewer)
             float ucol[NR + 2 * R], wcol[NR + 2 * R - 1];
 #pragma unroll
             for (int q = 0; q < NR + 2 * R; ++q) ucol[q] = su[(NR * ty + q) * L::SW + cxs];
@@ -314,19 +349,19 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
                 const float xu = ucol[r + R], xv = sv[pt], xwx = wxrow[0], xwy = wcol[r + R];
                 const float c2 = sc2[pt];
                 float hv = -bxn * byn * xu + c2 * ((uxx + uyy) * idx2 + (dwx + dwy) * idx1) - (bxn + byn) * xv;
-                if (i == src_i && j == src_j) hv += sig;
+                if (i == ti.src_i && j == ti.src_j) hv += ti.sig;
                 const float hwx = (i < nx - 1) ? (byn - bxh) * dux * idx1 - bxh * xwx : 0.f;
                 const float hwy = (j < ny - 1) ? (bxn - byh) * duy * idx1 - byh * xwy : 0.f;
                 const float xf[4] = {xu, xv, xwx, xwy};
                 const float hf[4] = {xv, hv, hwx, hwy};
-                const long long o = (long long)j * pitch + i;
+                const long long o = (long long)j * ti.pitch + i;
                 float* yrow = Yg ? Yg + o : nullptr;
                 float* arow = Ag ? Ag + o : nullptr;
 #pragma unroll
                 for (int f = 0; f < 4; ++f) {
                     const bool pad = (f == 2 && i >= nx - 1) || (f == 3 && j >= ny - 1);
-                    const float uval = has_u ? spu[f * BY * BX + pt] : 0.f;
-                    const float aval = has_a ? spa[f * BY * BX + pt] : 0.f;
+                    const float uval = has_u ? spu[f * BYv * BX + pt] : 0.f;
+                    const float aval = has_a ? spa[f * BYv * BX + pt] : 0.f;
                     const float kf = cxf * xf[f] + chf * hf[f];
                     const float yf = pad ? 0.f : (cuf * uval + ckf * kf);
                     if (yrow) yrow[f * fstr] = yf;
@@ -340,9 +375,9 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
     __syncthreads();
     if (s_err) {
         // drain: wait (bounded) for the last copy issued into every stage
-        if (warp == NCONS / 32 && lane == 0) {
-            for (int it = issued - 1; it >= 0 && it >= issued - NST; --it)
-                (void)mbar_wait(&full[it % NST], (uint32_t)(it / NST) & 1u);
+        if (warp == NW && lane == 0) {
+            for (int it = issued - 1; it >= 0 && it >= issued - NSTv; --it)
+                (void)mbar_wait(&full[it % NSTv], (uint32_t)(it / NSTv) & 1u);
         }
         if (tid == 0) atomicExch(err, 1);
     }
@@ -386,30 +421,36 @@ static int encode2(CUtensorMap* out, void* base, int nx, int ny, long long pitch
     return r == CUDA_SUCCESS ? 0 : -1;
 }
 
-// Build the NMAP maps of every problem (FP32 only) into a device array; sets P.tmaps.
+// Build NMAP maps per problem and tile height (map set 0: BY = 16, set 1: BY = 8) into a
+// device array (FP32 only); sets P.tmaps to the problem's first map.
 int build_tensor_maps(std::vector<ProblemDev>& probs, int R, const std::vector<int>& work_vecs,
                       void** d_maps_inout) {
     if (get_encoder() != 0) return -1;
     const int n = (int)probs.size();
-    std::vector<CUtensorMap> maps((size_t)n * NMAP);
-    const int SH = BY + 2 * R, SW = BX + 2 * TX;
+    constexpr int NSET = 2;
+    const int heights[NSET] = {16, 8};
+    std::vector<CUtensorMap> maps((size_t)n * NSET * NMAP);
+    const int SW = BX + 2 * TX;
     for (int p = 0; p < n; ++p) {
         ProblemDev& P = probs[p];
-        CUtensorMap* m = maps.data() + (size_t)p * NMAP;
-        const int bxs[5] = {SW, SW, BX, BX, BX};
-        const int bys[5] = {SH, BY, SH, BY, BY};
-        const int bfs[5] = {1, 1, 1, 1, 4};
-        for (int k = 0; k < 5; ++k) {
-            if (encode4(m + k, P.state, P.nx, P.ny, 1, P.pitch, P.field_stride, P.vec_stride, bxs[k],
-                        bys[k], bfs[k]) != 0)
-                return -1;
-            void* wb = P.work ? P.work : P.state;
-            const int nv = P.work ? work_vecs[p] : 1;
-            if (encode4(m + 5 + k, wb, P.nx, P.ny, nv > 0 ? nv : 1, P.pitch, P.field_stride, P.vec_stride,
-                        bxs[k], bys[k], bfs[k]) != 0)
-                return -1;
+        for (int set = 0; set < NSET; ++set) {
+            const int by = heights[set], SH = by + 2 * R;
+            CUtensorMap* m = maps.data() + ((size_t)p * NSET + set) * NMAP;
+            const int bxs[5] = {SW, SW, BX, BX, BX};
+            const int bys[5] = {SH, by, SH, by, by};
+            const int bfs[5] = {1, 1, 1, 1, 4};
+            for (int k = 0; k < 5; ++k) {
+                if (encode4(m + k, P.state, P.nx, P.ny, 1, P.pitch, P.field_stride, P.vec_stride,
+                            bxs[k], bys[k], bfs[k]) != 0)
+                    return -1;
+                void* wb = P.work ? P.work : P.state;
+                const int nv = P.work ? work_vecs[p] : 1;
+                if (encode4(m + 5 + k, wb, P.nx, P.ny, nv > 0 ? nv : 1, P.pitch, P.field_stride,
+                            P.vec_stride, bxs[k], bys[k], bfs[k]) != 0)
+                    return -1;
+            }
+            if (encode2(m + 10, const_cast<void*>(P.c2), P.nx, P.ny, P.pitch, BX, by) != 0) return -1;
         }
-        if (encode2(m + 10, const_cast<void*>(P.c2), P.nx, P.ny, P.pitch, BX, BY) != 0) return -1;
     }
     cudaFree(*d_maps_inout);
     *d_maps_inout = nullptr;
@@ -418,44 +459,66 @@ int build_tensor_maps(std::vector<ProblemDev>& probs, int R, const std::vector<i
                    cudaMemcpyHostToDevice) != cudaSuccess)
         return -1;
     for (int p = 0; p < n; ++p)
-        probs[p].tmaps = static_cast<char*>(*d_maps_inout) + (size_t)p * NMAP * sizeof(CUtensorMap);
+        probs[p].tmaps = static_cast<char*>(*d_maps_inout) + (size_t)p * NSET * NMAP * sizeof(CUtensorMap);
     return 0;
+}
+
+// Kernel variants the autotuner chooses from: (tile height, consumer warps, stages).
+struct TmaVariant {
+    int by, nw, nst;
+};
+constexpr TmaVariant kVariants[TMA_NUM_VARIANTS] = {{16, 16, 3}, {16, 8, 3}, {8, 8, 5}, {8, 16, 5}};
+
+int tma_variant_tile_height(int v) { return kVariants[v].by; }
+void tma_variant_describe(int v, int* by, int* nw, int* nst) {
+    *by = kVariants[v].by;
+    *nw = kVariants[v].nw;
+    *nst = kVariants[v].nst;
 }
 
 static int g_num_sms = 0;
 
-int launch_stage_tma(int R, int ntiles, const ProblemDev* probs, const int* tile_prob,
-                     const StageArgs& a, int* err, cudaStream_t s) {
-    if (ntiles <= 0) return 0;
+template <int R, int BYv, int NW, int NSTv>
+static int launch_variant(const ProblemDev* probs, const int* tbase, int nprob, int ntiles,
+                          const StageArgs& a, int* err, cudaStream_t s) {
+    const size_t smem = (size_t)NSTv * StageLayout<R, BYv>::BYTES + 1024;
+    // the shared-memory attribute is set once per instantiation and device
+    static unsigned long long configured = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return -1;
+    if (!(configured >> dev & 1ull)) {
+        if (cudaFuncSetAttribute(stage_tma_kernel<R, BYv, NW, NSTv>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return -1;
+        configured |= 1ull << dev;
+    }
+    const int grid = ntiles < g_num_sms ? ntiles : g_num_sms;
+    stage_tma_kernel<R, BYv, NW, NSTv><<<grid, NW * 32 + 32, smem, s>>>(
+        probs, tbase, nprob, ntiles, BYv == 16 ? 0 : 1, a, err);
+    return 0;
+}
+
+int launch_stage_tma(int variant, int R, const ProblemDev* probs, const int* tbase, int nprob,
+                     int ntiles, const StageArgs& a, int* err, cudaStream_t s) {
+    if (ntiles <= 0) return nprob > 0 ? -1 : 0;   // problems but no tiles: inconsistent lists
     if (!g_num_sms) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
         if (g_num_sms <= 0) g_num_sms = 1;
     }
-    const int grid = ntiles < g_num_sms ? ntiles : g_num_sms;
-    if (R == 4) {
-        const size_t smem = (size_t)NST * StageLayout<4>::BYTES + 1024;
-        static bool set4 = false;
-        if (!set4) {
-            if (cudaFuncSetAttribute(stage_tma_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem) != cudaSuccess)
-                return -1;
-            set4 = true;
-        }
-        stage_tma_kernel<4><<<grid, TMA_THREADS, smem, s>>>(probs, tile_prob, ntiles, a, err);
-    } else {
-        const size_t smem = (size_t)NST * StageLayout<2>::BYTES + 1024;
-        static bool set2 = false;
-        if (!set2) {
-            if (cudaFuncSetAttribute(stage_tma_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem) != cudaSuccess)
-                return -1;
-            set2 = true;
-        }
-        stage_tma_kernel<2><<<grid, TMA_THREADS, smem, s>>>(probs, tile_prob, ntiles, a, err);
-    }
-    return 0;
+#define EWV_TMA_CASE(V, RR, BYV, NWV, NSTV) \
+    if (variant == V && R == RR) return launch_variant<RR, BYV, NWV, NSTV>(probs, tbase, nprob, ntiles, a, err, s);
+    EWV_TMA_CASE(0, 4, 16, 16, 3)
+    EWV_TMA_CASE(1, 4, 16, 8, 3)
+    EWV_TMA_CASE(2, 4, 8, 8, 5)
+    EWV_TMA_CASE(3, 4, 8, 16, 5)
+    EWV_TMA_CASE(0, 2, 16, 16, 3)
+    EWV_TMA_CASE(1, 2, 16, 8, 3)
+    EWV_TMA_CASE(2, 2, 8, 8, 5)
+    EWV_TMA_CASE(3, 2, 8, 16, 5)
+#undef EWV_TMA_CASE
+    return -1;
 }
 
 }  // namespace ewv

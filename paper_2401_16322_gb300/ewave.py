@@ -37,6 +37,8 @@ EXPORTS = [
     "ewv_kernel_timing", "ewv_batch_enable_kernel_timing", "ewv_batch_kernel_timing", "ewv_reset_state",
     "ewv_faber_step_noalloc", "ewv_adjoint_step", "ewv_adjoint_inject", "ewv_checkpoint_stride",
     "ewv_sum_shot_fields", "ewv_enable_graphs", "ewv_batch_enable_graphs",
+    "ewv_set_kernel_variant", "ewv_kernel_variant", "ewv_batch_set_kernel_variant",
+    "ewv_batch_kernel_variant",
 ]
 
 
@@ -127,6 +129,12 @@ def load_library(path=LIB_PATH):
         "ewv_checkpoint_stride": ([i, i, ctypes.POINTER(i)], i),
         "ewv_sum_shot_fields": ([vp, vp, vp], i),
         "ewv_enable_graphs": ([vp, i], i),
+        "ewv_set_kernel_variant": ([vp, i], i),
+        "ewv_kernel_variant": ([vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
+                                ctypes.POINTER(i), dp], i),
+        "ewv_batch_set_kernel_variant": ([vp, i], i),
+        "ewv_batch_kernel_variant": ([vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
+                                      ctypes.POINTER(i), dp], i),
         "ewv_batch_enable_graphs": ([vp, i], i),
         "ewv_faber_step_noalloc": ([ctypes.POINTER(NoallocFaberArgs), vp, vp, d, d, i, i, vp], i),
         "ewv_enable_kernel_timing": ([vp, i], i),
@@ -140,6 +148,14 @@ def load_library(path=LIB_PATH):
         fn.restype = res
     _lib = lib
     return lib
+
+
+def _variant(fn, h, check):
+    v, by, nw, nst = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    us = (ctypes.c_double * 4)()
+    check(fn(h, ctypes.byref(v), ctypes.byref(by), ctypes.byref(nw), ctypes.byref(nst), us))
+    return {"variant": v.value, "tile": [64, by.value], "consumer_warps": nw.value,
+            "stages": nst.value, "probe_us": list(us)}
 
 
 def _dptr(a):
@@ -329,10 +345,10 @@ class Model:
         return c.value
 
     # ---------------------------------------------------------------- adjoint
-    def adjoint_step(self, t, dt, degree, checkpoint, adj, grad):
-        """lambda <- (dPhi/dU)^T lambda, grad += (dPhi/dm)^T lambda for one Faber step."""
+    def adjoint_step(self, t, dt, degree, checkpoint, adj, grad, method="faber"):
+        """lambda <- (dPhi/dU)^T lambda, grad += (dPhi/dm)^T lambda for one Faber / HORK step."""
         self.ensure_workspace("adjoint_faber", degree)
-        self._check(self.lib.ewv_adjoint_step(self.h, METHOD["faber"], t, dt, degree,
+        self._check(self.lib.ewv_adjoint_step(self.h, METHOD[method], t, dt, degree,
                                               ctypes.c_void_p(checkpoint.data_ptr()),
                                               ctypes.c_void_p(adj.data_ptr()),
                                               ctypes.c_void_p(grad.data_ptr())), "adjoint_step")
@@ -347,6 +363,12 @@ class Model:
 
     def enable_graphs(self, on=True):
         self._check(self.lib.ewv_enable_graphs(self.h, int(on)))
+
+    def set_kernel_variant(self, v):
+        self._check(self.lib.ewv_set_kernel_variant(self.h, v))
+
+    def kernel_variant(self):
+        return _variant(self.lib.ewv_kernel_variant, self.h, self._check)
 
     def enable_kernel_timing(self, on=True):
         self._check(self.lib.ewv_enable_kernel_timing(self.h, int(on)))
@@ -419,6 +441,12 @@ class Batch:
 
     def enable_graphs(self, on=True):
         self._check(self.lib.ewv_batch_enable_graphs(self.h, int(on)), "graphs")
+
+    def set_kernel_variant(self, v):
+        self._check(self.lib.ewv_batch_set_kernel_variant(self.h, v), "variant")
+
+    def kernel_variant(self):
+        return _variant(self.lib.ewv_batch_kernel_variant, self.h, lambda rc, w="": self._check(rc, "variant"))
 
     def enable_kernel_timing(self, on=True):
         self._check(self.lib.ewv_batch_enable_kernel_timing(self.h, int(on)), "timing")

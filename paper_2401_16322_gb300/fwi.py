@@ -17,9 +17,13 @@ from .ewave import Model, checkpoint_stride
 
 
 class FaberFWI:
-    """Forward simulation with checkpoints and the adjoint gradient for one model."""
+    """Forward simulation with checkpoints and the adjoint gradient for one model
+    (``method`` "faber": degree m; "hork": m stages)."""
 
-    def __init__(self, model: Model, dt, degree, nsteps, nrec, budget=None, t0=0.0):
+    def __init__(self, model: Model, dt, degree, nsteps, nrec, budget=None, t0=0.0, method="faber"):
+        if method not in ("faber", "hork"):
+            raise ValueError("the adjoint exists for the Faber and HORK steps")
+        self.method = method
         self.model = model
         self.dt, self.degree, self.nsteps, self.nrec, self.t0 = dt, degree, nsteps, nrec, t0
         self.stride = checkpoint_stride(nsteps, budget if budget else max(nsteps, 1))
@@ -41,11 +45,11 @@ class FaberFWI:
         if md.capacity < self.nsteps:
             md.bind_seismogram(self.nsteps)
         md.reset_state()
-        md.ensure_workspace("faber", self.degree)
+        md.ensure_workspace(self.method, self.degree)
         for n in range(self.nsteps):
             if n % self.stride == 0:
                 self.ckpt[n // self.stride].copy_(md.state)
-            md.step_faber(self.t0 + n * self.dt, self.dt, self.degree, 1)
+            md.step(self.method, self.t0 + n * self.dt, self.dt, self.degree, 1)
         s = md.seismo.view(md.nshots, md.capacity, md.max_receivers)[:, :self.nsteps, :self.nrec]
         return s.clone()
 
@@ -68,15 +72,16 @@ class FaberFWI:
             # recompute the states U^{n0} .. U^{n1-1} of this segment from its checkpoint
             if self.stride > 1:
                 md.state.copy_(self.ckpt[k])
-                md.ensure_workspace("faber", self.degree)
+                md.ensure_workspace(self.method, self.degree)
                 for n in range(n0, n1):
                     self.seg[n - n0].copy_(md.state)
                     if n + 1 < n1:
-                        md.step_faber(self.t0 + n * self.dt, self.dt, self.degree, 1)
+                        md.step(self.method, self.t0 + n * self.dt, self.dt, self.degree, 1)
                 md.ensure_workspace("adjoint_faber", self.degree)
             for n in range(n1, n0, -1):          # adjoint of step n: U^{n-1} -> U^n
                 ck = self.seg[n - 1 - n0] if self.stride > 1 else self.ckpt[n - 1]
-                md.adjoint_step(self.t0 + (n - 1) * self.dt, self.dt, self.degree, ck, lam, grad)
+                md.adjoint_step(self.t0 + (n - 1) * self.dt, self.dt, self.degree, ck, lam, grad,
+                                self.method)
                 if n - 1 >= 1:
                     md.adjoint_inject(lam, g[:, n - 2, :].contiguous())
         out = torch.zeros(fe, dtype=md.dtype, device=md.device)

@@ -93,3 +93,42 @@ def test_batch_bitwise_equals_single_models():
     for q, g in enumerate(gms):
         for s in range(nshots):
             assert np.array_equal(batched[q][s], g.get_state(s))
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_every_kernel_variant_matches_oracle(variant):
+    """Each persistent-kernel variant the autotuner may pick (tile height 16 or 8, 8 or 16
+    consumer warps, 3 or 5 stages) gives the oracle's result on uneven batched grids."""
+    from paper_2401_16322_gb300 import Batch
+    nshots, dt, t, nsteps, m = 2, 1.1e-3, 0.04, 2, 14
+    oms, gms, shots = _models("f32", nshots)
+    ell = oracle_ellipse(oms[0])
+    for g in gms:
+        g.set_faber_ellipse(*ell)
+        g.bind_seismogram(nsteps)
+    U0 = _init(oms, gms, nshots)
+    B = Batch(gms)
+    B.set_kernel_variant(variant)
+    B.step("faber", t, dt, m, nsteps)
+    assert B.kernel_variant()["variant"] == variant
+    for q, (om, g) in enumerate(zip(oms, gms)):
+        for s in range(nshots):
+            sx, rec = shots[q][s]
+            src = PointSource(om, sx, 2 * om.dx, 20.0, 0.06, amp=1e3, p=8)
+            U, S = run(om, "faber", dt, nsteps, src=src, rec_nodes=receiver_nodes(om, rec), m=m,
+                       U0=U0[q, s], t0=t, faber_params=ell)
+            assert rel_l2(g.get_state(s), flatten(U)) < 3 * TOL["f32"], (variant, q, s)
+
+
+def test_autotuner_picks_a_timed_variant():
+    from paper_2401_16322_gb300 import Batch
+    oms, gms, _ = _models("f32", 1)
+    for g in gms:
+        g.set_faber_ellipse(*oracle_ellipse(oms[0]))
+    B = Batch(gms)
+    B.step("faber", 0.04, 1.1e-3, 8, 1)
+    info = B.kernel_variant()
+    assert 0 <= info["variant"] < 4
+    times = info["probe_us"]
+    assert all(t > 0 for t in times)
+    assert times[info["variant"]] == min(times)

@@ -144,6 +144,31 @@ def test_autograd_function_gives_the_adjoint_gradient():
     assert np.allclose(m.grad.cpu().numpy(), g_ref, rtol=1e-12, atol=0)
 
 
+def test_hork_gradient_matches_oracle_and_differences():
+    """HORK (8 stages, dt 0.5 ms): GPU adjoint gradient = oracle (FP64), and central
+    differences of the GPU misfit along a seeded direction."""
+    import torch
+    from paper_2401_16322_gb300.fwi import FaberFWI
+    c_true, c0, beta0, ell = _setup()
+    dt, deg = 5e-4, 8
+    om_t = OModel(NX, NY, DX, 8, PML, beta0, True, c_true)
+    d_obs = faber_forward(om_t, _oshots(om_t), dt, NSTEPS, deg, ell, method="hork")[1]
+    om = OModel(NX, NY, DX, 8, PML, beta0, True, c0)
+    J_o, g_o = fwi_gradient(om, _oshots(om), d_obs, dt, NSTEPS, deg, ell, method="hork")
+    g = _gpu(c0, beta0, ell, "f64")
+    fwi = FaberFWI(g, dt, deg, NSTEPS, len(REC), method="hork")
+    d = torch.tensor(np.array(d_obs), dtype=torch.float64, device="cuda")
+    seis = fwi.forward(c0 ** 2)
+    grad = fwi.backward(seis - d).double().cpu().numpy()
+    assert rel_l2(grad, g_o) < 1e-10
+    dm = smooth_random_state([(NY, NX)], 9, sigma_cells=2.0)[0] * 0.01 * c0 ** 2
+    eps = 1e-4
+    Jp = 0.5 * float(((fwi.forward(c0 ** 2 + eps * dm) - d) ** 2).sum())
+    Jm = 0.5 * float(((fwi.forward(c0 ** 2 - eps * dm) - d) ** 2).sum())
+    fd = (Jp - Jm) / (2 * eps)
+    assert abs(fd - float(np.sum(grad * dm))) <= 1e-3 * abs(fd)
+
+
 def test_checkpoint_stride_bit_exact():
     from paper_2401_16322_gb300.ewave import checkpoint_stride
     for n in range(0, 60):

@@ -1,5 +1,6 @@
 """CUDA-graph replay of the step loop gives bit-identical states and seismograms to direct
-launches, for every integrator (leap-frog alternates two captured sequences)."""
+launches, for every integrator (leap-frog alternates two captured sequences).  Both runs use
+the same FP32 pass variant: the variants' unrolled loops agree to rounding, not bitwise."""
 import numpy as np
 import pytest
 
@@ -25,6 +26,8 @@ def test_graph_replay_is_bitwise_identical(prec, method, m):
         g.set_source_receivers(0, 41 * om.dx, 2 * om.dx, 25.0, 0.05, 1e3, rec)
         g.set_faber_ellipse(*oracle_ellipse(om))
         g.enable_graphs(graphs)
+        if prec == "f32":
+            g.set_kernel_variant(0)
         g.bind_seismogram(7)
         g.set_state(0, flatten(U0))
         dt = 4e-4 if method == "leapfrog" else 1.1e-3
