@@ -37,7 +37,7 @@ TARGET = 1e-4
 PICKS = [(0, 32), (1, 0), (5, 0)]
 # Cheapest candidate found by the in-run search on GB300 (used by the CPU reference arm; the
 # GPU arm re-runs the search and reports what it finds).
-DEFAULT_SELECTION = ("faber", 40, 8)     # method, m, dt in units of the leap-frog step
+DEFAULT_SELECTION = ("hork", 24, 5)     # method, m, dt in units of the leap-frog step
 WORKLOAD_NAME = ("batched: 64 shots on 1001x501 + 8 models 201x101..801x401, layered "
                  "1500-4500 m/s, 8th order, free surface, 40-pt PML, Ricker 10 Hz, T=2 s")
 
@@ -53,6 +53,11 @@ def parse():
     ap.add_argument("--no-search", action="store_true", help="use the default selection")
     ap.add_argument("--T", type=float, default=T_END, help="simulated time (profiling runs)")
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 and FWI side runs")
+    ap.add_argument("--select", default=None, metavar="METHOD,M,K",
+                    help="with --no-search: integrator, m and step in leap-frog steps "
+                         f"(default {','.join(map(str, DEFAULT_SELECTION))})")
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="FP32 stencil-pass variant (0..3; -1: autotune at first use)")
     ap.add_argument("--case", default="full", choices=["full", "small", "medium"],
                     help="small / medium: the 1001x501 model with 4 / 16 shots (profiling)")
     return ap.parse_args()
@@ -121,19 +126,20 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "stage_tma_kernel_faber_1001x501x16.md")
 TMA_SOURCE = os.path.join(ROOT, "paper_2401_16322_gb300", "csrc", "kernels_tma.cu")
 
 
-def ncu_traffic_per_point():
-    """DRAM bytes per grid point of one Faber degree pass (j >= 2) from the committed ncu
-    summary, or None when the TMA kernel source changed since the capture."""
+def ncu_traffic_per_point(method):
+    """DRAM bytes per grid point of one steady-state stencil pass of ``method`` (a Faber
+    degree j >= 2 or a HORK stage i >= 2) from the committed ncu summary, or None when there
+    is none or the TMA kernel source changed since the capture."""
     import hashlib
+    summary = os.path.join(ROOT, "profiles", f"stage_tma_kernel_{method}_1001x501x16.md")
     try:
         with open(TMA_SOURCE, "rb") as f:
             sha = hashlib.sha256(f.read()).hexdigest()
         vals = {}
-        with open(TRAFFIC_SUMMARY) as f:
+        with open(summary) as f:
             for line in f:
                 if ":" in line and line.startswith("- "):
                     k, v = line[2:].split(":", 1)
@@ -227,13 +233,14 @@ def fp64_single_shot_estimate(wl, method, m, dt, nsteps, c_max, steps_sample=3):
 
 def fwi_gradient_step(method, m, dt_over_cfl):
     """FWI gradient (forward + adjoint) on the 401 x 201, 16-shot, 200-receiver workload,
-    FP32, Faber at the selected degree and step ratio; every state checkpointed."""
+    FP32, with the selected integrator (Faber or HORK: the two with a discrete adjoint) at its
+    m and step ratio; every state checkpointed."""
     import numpy as np
     import torch
     from paper_2401_16322_gb300.fwi import FaberFWI
     from paper_2401_16322_gb300.tts import build_models, common_ellipse, leapfrog_step
     from paper_2401_16322_gb300.workloads import config_fwi, smooth_gradient_with_anomalies
-    if method != "faber":
+    if method not in ("faber", "hork"):
         return None
     w = config_fwi()
     c_max = float(w.c.max()) * 1.05
@@ -241,7 +248,7 @@ def fwi_gradient_step(method, m, dt_over_cfl):
     nsteps = int(round(w.T / dt))
     md = build_models([w], "f32", p=12, c_max=c_max)[0]
     common_ellipse([md], c_max)
-    fwi = FaberFWI(md, dt, m, nsteps, len(w.shots[0].rec))
+    fwi = FaberFWI(md, dt, m, nsteps, len(w.shots[0].rec), method=method)
     d_obs = fwi.forward(w.c ** 2)
     c_init = smooth_gradient_with_anomalies(w.nx, w.ny, 0, dx=w.dx, amps=())
     fwi.forward(c_init ** 2)
@@ -255,7 +262,8 @@ def fwi_gradient_step(method, m, dt_over_cfl):
     ok = bool(torch.isfinite(grad).all())
     mem = fwi.ckpt.numel() * fwi.ckpt.element_size()
     md.close()
-    return {"seconds": e0.elapsed_time(e1) * 1e-3, "nsteps": nsteps, "dt_ms": dt * 1e3, "m": m,
+    return {"seconds": e0.elapsed_time(e1) * 1e-3, "method": method, "nsteps": nsteps,
+            "dt_ms": dt * 1e3, "m": m,
             "shots": len(w.shots), "grid": f"{w.nx}x{w.ny}", "checkpoint_bytes": mem,
             "gradient_finite": ok}
 
@@ -324,13 +332,23 @@ def run_ours(args):
     models = build_models(wl, "f32", p=12, c_max=c_max)
     common_ellipse(models, c_max)
     batch = Batch(models)
+    if args.variant >= 0:
+        batch.set_kernel_variant(args.variant)
     log(f"setup {time.perf_counter() - t_setup:.1f} s, {pts} grid points, dt_cfl {dt_cfl * 1e3:.4f} ms")
 
     method, m, k = DEFAULT_SELECTION
+    if args.select:
+        sm, sk, skk = args.select.split(",")
+        method, m, k = sm, int(sk), float(skk)
     study = None
     if not args.no_search and args.case == "full":
+        models64 = build_models(wl, "f64", p=12, c_max=c_max)   # FP64 leap-frog timing
         study = run_study(wl, PICKS, T_run, target=args.target, full_batch=batch, full_models=models,
-                          log=log if rank == 0 else (lambda *a: None), self_check=True)
+                          full_models_f64=models64, log=log if rank == 0 else (lambda *a: None),
+                          self_check=True)
+        for md in models64:
+            md.close()
+        del models64
         if study.selected is not None:
             method, m, dt = study.selected.method, study.selected.m, study.selected.dt
         else:
@@ -367,6 +385,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks = clk.stop()
     elapsed_ms = e0.elapsed_time(e1)
+    # every problem's seismogram of the last timed simulation is finite (the error target is
+    # measured on sampled problems only)
+    all_finite = all(bool(torch.isfinite(md.seismo).all()) for md in models)
     kern_ms, kern_n = batch.kernel_timing()
     batch.enable_kernel_timing(False)
     launches = batch.launch_count() - launches0
@@ -411,6 +432,7 @@ def run_ours(args):
         cpu_pps, cpu_desc, cores = cpu_oracle_sample(config_batched(), method, m, dt, args.cpu_sample_s)
         cpu_tts = cpu_pps * pts * nsteps
         lf = study.leapfrog if study else None
+        lf64 = study.leapfrog_f64 if study else None
         result = {
             "metric": METRIC, "value": ms_per_step / 1e3, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -423,13 +445,14 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (state + workspace > 1 GB)",
                        "parallelism": f"replicas x{world}"},
             "seismo_rel_err": seismo_err,
+            "all_seismograms_finite": all_finite,
             "grid_point_updates_per_s": pts * nsteps / (ms_per_step / 1e3),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
-                         "traffic": (tpp * pts if (tpp := ncu_traffic_per_point()) and method == "faber"
-                                     else None),
+                         "traffic": (tpp * pts if (tpp := ncu_traffic_per_point(method)) else None),
                          "peak_kind": peak_kind,
-                         "kernel": "stage_tma_kernel<4> (persistent TMA fused stencil pass, FP32)",
+                         "kernel": "stage_tma_kernel (persistent TMA fused stencil pass, FP32)",
+                         "variant": batch.kernel_variant(),
                          "avg_launch_us": avg_launch_ms * 1e3, "launches": kern_n,
                          "alg_bytes_per_launch": per_launch_bytes},
             "cpu_baseline": {"value": cpu_tts, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -439,7 +462,11 @@ def run_ours(args):
             "gpu_launches": launches,
             "clocks": clocks,
             "leapfrog_f32": ({"dt_ms": lf.dt * 1e3, "seismo_rel_err": lf.err,
-                              "time_to_solution_s": lf.cost_s} if lf else None),
+                              "time_to_solution_s": lf.cost_s} if lf else
+                             ("no leap-frog step down to 1/32 of the stability step reaches the "
+                              "target in FP32" if study else None)),
+            "leapfrog_f64": ({"dt_ms": lf64.dt * 1e3, "seismo_rel_err": lf64.err,
+                              "time_to_solution_s": lf64.cost_s} if lf64 else None),
             "fp64_single_shot": extras.get("fp64_single_shot"),
             "fwi_gradient": extras.get("fwi_gradient"),
             "search_s": study.seconds if study else None,

@@ -285,7 +285,8 @@ const char* ewv_version(void);
  * launch sequence of one step into a CUDA graph (once per method, m, dt and Faber ellipse)
  * and replays it for the remaining steps; steps read their time from a device-side clock,
  * so the graph has no per-step parameters.  Off: every kernel is launched directly.
- * Capture is skipped while kernel timing is enabled. */
+ * With kernel timing enabled, the captured step carries its own event pairs and every
+ * replay waits on the host for them (one wait per step). */
 int ewv_enable_graphs(ewv_model_t model, int enable);
 int ewv_batch_enable_graphs(ewv_batch_t batch, int enable);
 
@@ -304,7 +305,7 @@ int ewv_batch_kernel_variant(ewv_batch_t batch, int* variant, int* tile_height, 
                              int* stages, double* probe_us);
 
 /* Event timing of the fused stencil passes (the hot kernel): when enabled, every stencil
- * pass launch is bracketed by a pair of CUDA events on the handle's stream.
+ * pass launch is bracketed by a pair of CUDA events on the stream the pass runs on.
  * ewv_*kernel_timing synchronises the stream, returns the summed device time (ms) and the
  * number of timed launches since the last read, and resets both. */
 int ewv_enable_kernel_timing(ewv_model_t model, int enable);

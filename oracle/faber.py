@@ -88,7 +88,7 @@ def faber_step(model, U, src, t_n, dt, m, params, p=None):
     def B(Ux, y):
         """F_1(H~) = H~/gamma - c0 I on [Ux; y]."""
         val = float(np.dot(w, y))
-        HU = apply_H(model, Ux, None if src is None else (src.j, src.i, val))
+        HU = apply_H(model, Ux, None if src is None else (*src.node, val))
         Ty = tail_apply(y, dt)
         return (tuple(h / gamma - c0 * x for h, x in zip(HU, Ux)), Ty / gamma - c0 * y)
 

@@ -103,7 +103,7 @@ def krylov_step(model, U, src, t_n, dt, m, p=None, breakdown_tol=1e-14, return_i
         Ux = unflatten(model, x[:nU])
         y = x[nU:]
         val = float(np.dot(w, y))
-        HU = apply_H(model, Ux, None if src is None else (src.j, src.i, val))
+        HU = apply_H(model, Ux, None if src is None else (*src.node, val))
         Ty = tail_apply(y, dt)
         return dt * np.concatenate([flatten(HU), Ty])
 

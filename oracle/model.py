@@ -95,9 +95,12 @@ class Model:
         """Length of the state vector (u, v, w_x, w_y)."""
         return 2 * self.nx * self.ny + (self.nx - 1) * self.ny + self.nx * (self.ny - 1)
 
+    def field_shapes(self):
+        nx, ny = self.nx, self.ny
+        return [(ny, nx), (ny, nx), (ny, nx - 1), (ny - 1, nx)]
+
     def zeros_state(self):
-        return (np.zeros((self.ny, self.nx)), np.zeros((self.ny, self.nx)),
-                np.zeros((self.ny, self.nx - 1)), np.zeros((self.ny - 1, self.nx)))
+        return tuple(np.zeros(s) for s in self.field_shapes())
 
 
 def flatten(state):
@@ -106,11 +109,10 @@ def flatten(state):
 
 
 def unflatten(model, x):
-    nx, ny = model.nx, model.ny
-    sizes = [ny * nx, ny * nx, ny * (nx - 1), (ny - 1) * nx]
-    shapes = [(ny, nx), (ny, nx), (ny, nx - 1), (ny - 1, nx)]
+    """Inverse of ``flatten`` for the model's field shapes (2D: u, v, w_x, w_y; 3D adds w_z)."""
     out, o = [], 0
-    for s, sh in zip(sizes, shapes):
+    for sh in model.field_shapes():
+        s = int(np.prod(sh))
         out.append(np.asarray(x[o:o + s], dtype=np.float64).reshape(sh))
         o += s
     return tuple(out)

@@ -139,8 +139,12 @@ def apply_H(m: Model, state, src=None):
     """H U (Eq. 1) plus an optional point source term.
 
     ``src`` is ``None`` or ``(j, i, value)``: ``value`` is added to the v-row at node (i, j)
-    (the f entry of Eq. 1 / the W y term of the augmented matrix).
+    (the f entry of Eq. 1 / the W y term of the augmented matrix).  A three-dimensional
+    model goes to ``oracle.wave3d.apply_H3`` (src ``(k, j, i, value)``).
     """
+    if getattr(m, "dims", 2) == 3:
+        from .wave3d import apply_H3
+        return apply_H3(m, state, src)
     u, v, wx, wy = state
     bxn = m.beta_x_node()[None, :]
     byn = m.beta_y_node()[:, None]

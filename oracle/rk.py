@@ -55,7 +55,7 @@ def hork_step(model, U, src, t_n, dt, m, p=None):
     def step(Ux, y):
         """(I + dt H~) [Ux; y]."""
         val = float(np.dot(w, y))
-        HU = apply_H(model, Ux, None if src is None else (src.j, src.i, val))
+        HU = apply_H(model, Ux, None if src is None else (*src.node, val))
         return _axpy(1.0, Ux, dt, HU), y + dt * tail_apply(y, dt)
 
     y = np.zeros(p)
@@ -73,7 +73,7 @@ def hork_step(model, U, src, t_n, dt, m, p=None):
 
 
 def _Hf(model, X, src, t):
-    return apply_H(model, X, None if src is None else (src.j, src.i, src.f(t)))
+    return apply_H(model, X, None if src is None else (*src.node, src.f(t)))
 
 
 def rk32_step(model, U, src, t_n, dt):

@@ -82,6 +82,11 @@ class PointSource:
         self.f_peak, self.t0, self.amp, self.p = f_peak, t0, amp, p
         self.dx = model.dx
 
+    @property
+    def node(self):
+        """Grid indices of the source node, slowest axis first."""
+        return (self.j, self.i)
+
     def f(self, t):
         """f(t) value added at the source node's v entry (Eq. 1)."""
         return self.amp * ricker(t, self.f_peak, self.t0) / (self.dx * self.dx)
@@ -93,5 +98,5 @@ class PointSource:
 def apply_Htilde(model, U, y, src, w, dt, apply_H):
     """Augmented operator H~ [U; y] = [H U + e_src (w . y); (J/dt) y] (Eq. matrix_ampli)."""
     val = float(np.dot(w, y)) if src is not None else 0.0
-    HU = apply_H(model, U, None if src is None else (src.j, src.i, val))
+    HU = apply_H(model, U, None if src is None else (*src.node, val))
     return HU, tail_apply(y, dt)

@@ -186,21 +186,43 @@ struct Engine {
     size_t d_adj_bytes = 0;
     int* d_err = nullptr;       // timeout word written by the TMA kernel
     std::map<std::tuple<double, int, double, double, double>, std::vector<double>> faber_cache;
-    // CUDA graphs of one step's launch sequence, keyed by (method, m, dt, g, c0, c1, parity)
-    std::map<std::tuple<int, int, double, double, double, double, int>,
-             std::pair<cudaGraphExec_t, long long>> graphs;
+    // CUDA graphs of one step's launch sequence, keyed by (method, m, dt, g, c0, c1, parity
+    // + 2 x timing); a graph captured with timing on owns the event pairs around its passes
+    struct StepGraph {
+        cudaGraphExec_t exec = nullptr;
+        long long nodes = 0;
+        std::vector<cudaEvent_t> ev;
+        bool pending = false;   // launched with timing; event pairs not read yet
+    };
+    std::map<std::tuple<int, int, double, double, double, double, int>, StepGraph> graphs;
     bool graphs_enabled = true;
     bool graphs_broken = false;
     cudaStream_t cap = nullptr;              // capturable stream used while graphs are on
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     void drop_graphs() {
-        for (auto& kv : graphs) cudaGraphExecDestroy(kv.second.first);
+        for (auto& kv : graphs) {
+            StepGraph& sg = kv.second;
+            if (sg.pending && cudaEventSynchronize(sg.ev.back()) == cudaSuccess) {
+                for (size_t k = 0; k + 1 < sg.ev.size(); k += 2) {
+                    float ms = 0.f;
+                    if (cudaEventElapsedTime(&ms, sg.ev[k], sg.ev[k + 1]) == cudaSuccess) {
+                        timing_acc_ms += ms;
+                        ++timing_acc_n;
+                    }
+                }
+            }
+            cudaGraphExecDestroy(kv.second.exec);
+            for (cudaEvent_t e : kv.second.ev) cudaEventDestroy(e);
+        }
         graphs.clear();
     }
-    // optional CUDA-event timing of the fused stencil passes (pairs around each launch)
+    // optional CUDA-event timing of the fused stencil passes (pairs around each launch);
+    // replayed graphs add their pairs' times to timing_acc_* when they are read back
     bool timing = false;
     std::vector<cudaEvent_t> events;
     size_t events_used = 0;
+    double timing_acc_ms = 0.0;
+    long long timing_acc_n = 0;
     ~Engine() {
         drop_graphs();
         if (cap) cudaStreamDestroy(cap);
@@ -440,13 +462,34 @@ StageArgs stage_defaults() {
     return a;
 }
 
+// Add the pass times of a timed graph's last replay (if not read yet) to the accumulator.
+int harvest_graph_timing(Engine* E, Engine::StepGraph& sg, std::string& err) {
+    if (!sg.pending) return EWV_OK;
+    sg.pending = false;
+    CUDA_OR_FAIL(err, cudaEventSynchronize(sg.ev.back()));
+    for (size_t k = 0; k + 1 < sg.ev.size(); k += 2) {
+        float ms = 0.f;
+        CUDA_OR_FAIL(err, cudaEventElapsedTime(&ms, sg.ev[k], sg.ev[k + 1]));
+        E->timing_acc_ms += ms;
+        ++E->timing_acc_n;
+    }
+    return EWV_OK;
+}
+
 struct Ctx {
     Engine* E;
     cudaStream_t s;
     long long* launches;
     std::string* err;
     int launch_failed = 0;      // a TMA pass could not be configured or launched
+    std::vector<cudaEvent_t>* capture_ev = nullptr;   // set while a timed step is captured
     cudaEvent_t next_event() {
+        if (capture_ev) {
+            cudaEvent_t e = nullptr;
+            cudaEventCreate(&e);
+            capture_ev->push_back(e);
+            return e;
+        }
         if (E->events_used == E->events.size()) {
             cudaEvent_t e;
             cudaEventCreate(&e);
@@ -456,10 +499,11 @@ struct Ctx {
     }
     void stage(const StageArgs& a) {
         cudaEvent_t e0 = nullptr, e1 = nullptr;
+        const unsigned rec_flags = capture_ev ? cudaEventRecordExternal : cudaEventRecordDefault;
         if (E->timing) {
             e0 = next_event();
             e1 = next_event();
-            cudaEventRecord(e0, s);
+            cudaEventRecordWithFlags(e0, s, rec_flags);
         }
         if (E->precision == EWV_F32 && !a.transpose && a.fin_mode == FIN_NONE && a.d < 0 && !a.grad) {
             if (E->tma_variant < 0) autotune();
@@ -473,7 +517,7 @@ struct Ctx {
             }
         } else
             launch_stage(E->precision, E->R, E->ntiles, E->d_probs, E->d_tile_prob, a, s);
-        if (E->timing) cudaEventRecord(e1, s);
+        if (E->timing) cudaEventRecordWithFlags(e1, s, rec_flags);
         ++*launches;
     }
     void point(const PointArgs& pa) {
@@ -549,47 +593,56 @@ struct Ctx {
     // Run nsteps steps.  Steps are parameter-free (time comes from the device clock), so
     // after the first step(s) the launch sequence of one step is captured once into a CUDA
     // graph and replayed; `nparity` distinct sequences alternate (leap-frog buffer swap).
-    // Capture is skipped while kernel timing is on; a failed capture falls back to direct
-    // launches for this engine.
+    // With kernel timing on, the captured step records its own event pairs (external event
+    // nodes); two copies of each graph alternate, and a copy's pairs are read back just
+    // before its next replay, while the other copy keeps the GPU busy.  A failed capture
+    // falls back to direct launches for this engine.
     template <class F>
     int step_loop(int nsteps, int method, int m, double dt, double g, double c0, double c1,
                   int nparity, F&& one_step) {
         for (int n = 0; n < nsteps; ++n) {
             const int par = n % nparity;
-            const bool use_graph = E->graphs_enabled && !E->timing && !E->graphs_broken && n >= nparity;
+            const bool use_graph = E->graphs_enabled && !E->graphs_broken && n >= nparity;
             if (!use_graph) {
                 one_step(n);
                 continue;
             }
-            auto key = std::make_tuple(method, m, dt, g, c0, c1, par);
+            const int slot = E->timing ? 2 + 2 * ((n / nparity) & 1) : 0;
+            auto key = std::make_tuple(method, m, dt, g, c0, c1, par + slot);
             auto it = E->graphs.find(key);
             if (it == E->graphs.end()) {
                 const long long L0 = *launches;
+                Engine::StepGraph sg;
                 cudaGraph_t gr = nullptr;
-                cudaGraphExec_t ex = nullptr;
                 if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
                     cudaGetLastError();
                     E->graphs_broken = true;
                     one_step(n);
                     continue;
                 }
+                if (E->timing) capture_ev = &sg.ev;
                 one_step(n);
+                capture_ev = nullptr;
                 const cudaError_t e1 = cudaStreamEndCapture(s, &gr);
-                const long long nodes = *launches - L0;
+                sg.nodes = *launches - L0;
                 *launches = L0;
-                if (e1 != cudaSuccess || cudaGraphInstantiate(&ex, gr, 0) != cudaSuccess) {
+                if (e1 != cudaSuccess || cudaGraphInstantiate(&sg.exec, gr, 0) != cudaSuccess) {
                     if (gr) cudaGraphDestroy(gr);
+                    for (cudaEvent_t ev : sg.ev) cudaEventDestroy(ev);
                     cudaGetLastError();
                     E->graphs_broken = true;
                     one_step(n);
                     continue;
                 }
                 cudaGraphDestroy(gr);
-                it = E->graphs.emplace(key, std::make_pair(ex, nodes)).first;
+                it = E->graphs.emplace(key, std::move(sg)).first;
             }
-            const cudaError_t e = cudaGraphLaunch(it->second.first, s);
+            Engine::StepGraph& sg = it->second;
+            if (harvest_graph_timing(E, sg, *err) != EWV_OK) return EWV_ERR_CUDA;
+            const cudaError_t e = cudaGraphLaunch(sg.exec, s);
             if (e != cudaSuccess) return fail(*err, EWV_ERR_CUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
-            *launches += it->second.second;
+            *launches += sg.nodes;
+            sg.pending = !sg.ev.empty();
         }
         return EWV_OK;
     }
@@ -930,7 +983,7 @@ int dispatch(std::vector<ewv_model*>& models, Engine* E, cudaStream_t s, long lo
     // With graphs on, run the call on the engine's own (capturable, non-blocking) stream,
     // ordered after the caller's stream and before whatever the caller enqueues next.
     cudaStream_t run_s = s;
-    const bool own = E->graphs_enabled && !E->timing && !E->graphs_broken;
+    const bool own = E->graphs_enabled && !E->graphs_broken;
     if (own) {
         if (!E->cap) {
             CUDA_OR_FAIL(err, cudaStreamCreateWithFlags(&E->cap, cudaStreamNonBlocking));
@@ -1421,15 +1474,19 @@ int ewv_batch_step_leapfrog(ewv_batch_t b, double t, double dt, int nsteps) {
 static int read_timing(Engine* E, cudaStream_t s, std::string& err, double* total_ms,
                        long long* count) {
     CUDA_OR_FAIL(err, cudaStreamSynchronize(s));
-    double tot = 0.0;
+    for (auto& kv : E->graphs)
+        if (harvest_graph_timing(E, kv.second, err) != EWV_OK) return EWV_ERR_CUDA;
+    double tot = E->timing_acc_ms;
     for (size_t k = 0; k + 1 < E->events_used; k += 2) {
         float ms = 0.f;
         CUDA_OR_FAIL(err, cudaEventElapsedTime(&ms, E->events[k], E->events[k + 1]));
         tot += ms;
     }
     if (total_ms) *total_ms = tot;
-    if (count) *count = (long long)(E->events_used / 2);
+    if (count) *count = (long long)(E->events_used / 2) + E->timing_acc_n;
     E->events_used = 0;
+    E->timing_acc_ms = 0.0;
+    E->timing_acc_n = 0;
     return EWV_OK;
 }
 
@@ -1487,6 +1544,8 @@ int ewv_enable_kernel_timing(ewv_model_t m, int enable) {
     Engine* E = ensure_model_engine(m);
     E->timing = enable != 0;
     E->events_used = 0;
+    E->timing_acc_ms = 0.0;
+    E->timing_acc_n = 0;
     return EWV_OK;
 }
 
@@ -1499,6 +1558,8 @@ int ewv_batch_enable_kernel_timing(ewv_batch_t b, int enable) {
     if (!b) return EWV_ERR_INVALID_ARG;
     b->engine->timing = enable != 0;
     b->engine->events_used = 0;
+    b->engine->timing_acc_ms = 0.0;
+    b->engine->timing_acc_n = 0;
     return EWV_OK;
 }
 

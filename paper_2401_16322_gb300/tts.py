@@ -3,18 +3,19 @@
 For a workload (a list of velocity models with shots and surface receivers) this module
 
 1. computes an FP64 reference seismogram for a few sampled problems with a high-accuracy
-   setting of the same spatial discretisation (Faber, degree 30, at dt_ref = 2 x the
-   leap-frog stability step; at that step the Faber coefficients of degree > 30 are below
-   1e-14, so the time error is negligible -- checked against dt_ref/2 by
-   ``reference_self_check``);
-2. runs every candidate (method, m, dt) in FP32 on the same sampled problems and measures
-   the relative L2 seismogram error against the reference at common sample times;
-3. times one step of every candidate on the full batched workload;
-4. selects the cheapest candidate (steps x time per step) whose error is at most the target
-   (1e-4, relative L2 over receivers x samples).
+   setting of the same spatial discretisation (Faber, degree 30, at dt_ref = the leap-frog
+   stability step, where the Faber coefficients beyond degree 30 are far below 1e-14; checked
+   against dt_ref/2 by the reference self-check);
+2. for every method and m, finds Delta-t_max: the largest step, an integer multiple k of the
+   leap-frog step, whose FP32 seismograms on the sampled problems are within the target
+   (1e-4 relative L2 over receivers x samples) of the reference at common sample times.  The
+   multiples are scanned from the largest down and the scan stops at the first pass;
+3. times one step of every (method, m) that has a Delta-t_max on the full batched workload;
+4. selects the cheapest (steps x time per step).
 
-The candidate grid follows the paper's comparison: Faber degree 20..60 and Krylov dimension
-10..40 at 4..16 x the leap-frog step, and leap-frog itself at 1 .. 1/16 of its step.
+Faber degree 20..80 and Krylov dimension 10..40 are scanned up to 24 x the leap-frog step
+(the paper's grid is 4..16 x), HORK 8..24 up to 12 x; leap-frog itself, in FP32 and in FP64,
+at 1 .. 1/32 of its step (largest passing step).
 """
 import math
 import time
@@ -23,7 +24,7 @@ from typing import List, Optional
 
 import numpy as np
 
-from .ewave import Batch, Model
+from .ewave import Batch, EwaveError, Model
 from .workloads import Shot, Workload, t0_for
 
 S2_MIN = {8: 6.501587301587302, 4: 16.0 / 3.0}   # |min symbol| of the centred 2nd derivative
@@ -140,38 +141,77 @@ class Study:
     ref_m: int
     candidates: List[Candidate] = field(default_factory=list)
     selected: Optional[Candidate] = None
-    leapfrog: Optional[Candidate] = None
+    leapfrog: Optional[Candidate] = None          # FP32 leap-frog (None: never reaches target)
+    leapfrog_f64: Optional[Candidate] = None
     ref_self_check: float = float("nan")
     seconds: float = 0.0
 
 
-def default_candidates(dt_cfl):
-    c = []
-    for m in (20, 30, 40, 50, 60):
-        for k in (4, 8, 12, 16):
-            c.append(Candidate("faber", m, k * dt_cfl))
-    for m in (10, 20, 30, 40):
-        for k in (4, 8, 12, 16):
-            c.append(Candidate("krylov", m, k * dt_cfl))
-    return c
+# (method, m values, step multiples k of the leap-frog step, scanned from the largest down)
+SCAN_PLAN = (
+    ("faber", (20, 25, 30, 35, 40, 45, 50, 55, 60, 70, 80), tuple(range(24, 1, -1))),
+    ("krylov", (10, 15, 20, 25, 30, 35, 40), tuple(range(24, 1, -1))),
+    ("hork", (8, 12, 16, 20, 24), tuple(range(12, 0, -1))),
+)
+LEAPFROG_DIVISORS = (1, 2, 3, 4, 6, 8, 12, 16, 24, 32)
 
 
-def leapfrog_candidates(dt_cfl):
-    return [Candidate("leapfrog", 1, dt_cfl / k) for k in (1, 2, 4, 8, 12, 16)]
+def dt_max_scan(ks, evaluate, target):
+    """Delta-t_max search for one (method, m) (Secs. 4.2, 5.2): evaluate the candidates in
+    the given order (largest step first) and stop at the first whose error meets the target.
+    ``evaluate(k)`` returns the error (inf for a failed run).  Returns (k or None, [(k, err)])."""
+    seen = []
+    for k in ks:
+        e = float(evaluate(k))
+        seen.append((k, e))
+        if e <= target:
+            return k, seen
+    return None, seen
 
 
-def run_study(workloads: List[Workload], picks, T, target=1e-4, candidates=None,
-              full_batch=None, full_models=None, ref_m=30, p_ref=20, p=12, log=print,
-              self_check=False):
-    """Search the candidates; ``full_batch``/``full_models`` time one step of each on the full
-    workload.  Returns a Study."""
+def _eval_candidate(models, batch, refs, sw, c, T, dt_ref, log):
+    try:
+        c.nsteps = simulate(models, batch, c.method, c.m, c.dt, T)
+        errs = [rel_l2_common(md.seismogram(0, len(w.shots[0].rec), c.nsteps), c.dt, r, dt_ref)
+                for md, w, r in zip(models, sw, refs)]
+        c.err = max(errs) if all(np.isfinite(errs)) else float("inf")
+    except Exception as e:     # non-finite Arnoldi etc.: the candidate fails the target
+        c.err = float("inf")
+        log(f"  {c.label()}: {e}")
+    return c.err
+
+
+def _time_step(full_batch, full_models, method, m, dt, t_live):
+    """ms per step of (method, m, dt) on the full workload, on a developed wavefield: from
+    rest the Arnoldi process breaks down after p vectors (only the source tail spans the
+    space), which would make Krylov steps look cheaper than they are."""
     import torch
+    for md in full_models:
+        md.ensure_workspace(method, m)
+        md.reset_state()
+    full_batch.step(method, t_live - 2 * dt, dt, m, 2)   # inject the source, warm the graph
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ns = 2
+    e0.record()
+    full_batch.step(method, t_live, dt, m, ns)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / ns
+
+
+def run_study(workloads: List[Workload], picks, T, target=1e-4, plan=SCAN_PLAN,
+              full_batch=None, full_models=None, full_models_f64=None, ref_m=30, p_ref=20,
+              p=12, log=print, self_check=False):
+    """Delta-t_max search for every (method, m) of ``plan`` on the sampled problems, then the
+    step time of each (method, m) on the full workload (``full_batch``/``full_models``; FP64
+    leap-frog on ``full_models_f64`` when given).  Returns a Study."""
     t_start = time.time()
     c_max = max(float(w.c.max()) for w in workloads)
     dx = workloads[0].dx
     order = workloads[0].order
     dt_cfl = leapfrog_step(c_max, dx, order)
-    dt_ref = 2.0 * dt_cfl
+    dt_ref = dt_cfl
     sw = sampled_workloads(workloads, picks)
     # FP64 reference on the sampled problems, batched
     ref_models = build_models(sw, "f64", p=p_ref, c_max=c_max)
@@ -185,55 +225,71 @@ def run_study(workloads: List[Workload], picks, T, target=1e-4, candidates=None,
         refs2 = [md.seismogram(0, len(w.shots[0].rec), n2) for md, w in zip(ref_models, sw)]
         st.ref_self_check = max(rel_l2_common(a, dt_ref, b, dt_ref / 2) for a, b in zip(refs, refs2))
         log(f"reference self-check (dt_ref vs dt_ref/2): {st.ref_self_check:.3e}")
+    log(f"reference: FP64 faber m={ref_m} dt={dt_ref * 1e3:.3f} ms, {n_ref} steps "
+        f"({time.time() - t_start:.1f} s)")
+    def scan(models, batch, method, m, ks, to_dt, out):
+        def ev(k):
+            c = Candidate(method, m, to_dt(k))
+            out.append(c)
+            return _eval_candidate(models, batch, refs, sw, c, T, dt_ref, log)
+        return dt_max_scan(ks, ev, target)[0]
+
+    # FP64 leap-frog on the sampled problems (reuses the reference models)
+    lf64 = []
+    scan(ref_models, ref_batch, "leapfrog", 1, LEAPFROG_DIVISORS, lambda k: dt_cfl / k, lf64)
     ref_batch.close()
     for md in ref_models:
         md.close()
-    log(f"reference: FP64 faber m={ref_m} dt={dt_ref * 1e3:.3f} ms, {n_ref} steps "
-        f"({time.time() - t_start:.1f} s)")
     # FP32 candidates on the sampled problems
     cand_models = build_models(sw, "f32", p=p, c_max=c_max)
     for md in cand_models:
         md.set_faber_ellipse(*ell)
     cand_batch = Batch(cand_models)
-    cands = candidates if candidates is not None else default_candidates(dt_cfl)
-    lf = leapfrog_candidates(dt_cfl)
-    for c in cands + lf:
-        try:
-            c.nsteps = simulate(cand_models, cand_batch, c.method, c.m, c.dt, T)
-            errs = [rel_l2_common(md.seismogram(0, len(w.shots[0].rec), c.nsteps), c.dt, r, dt_ref)
-                    for md, w, r in zip(cand_models, sw, refs)]
-            c.err = max(errs) if all(np.isfinite(errs)) else float("inf")
-        except Exception as e:     # non-finite Arnoldi etc.: the candidate fails the target
-            c.err = float("inf")
-            log(f"  {c.label()}: {e}")
+    cands, best_k = [], {}
+    for method, ms, ks in plan:
+        for m in ms:
+            k = scan(cand_models, cand_batch, method, m, ks, lambda k: k * dt_cfl, cands)
+            best_k[method, m] = k
+            log(f"  {method} m={m}: dt_max = " + (f"{k} x leap-frog step" if k else "none in range"))
+    lf = []
+    scan(cand_models, cand_batch, "leapfrog", 1, LEAPFROG_DIVISORS, lambda k: dt_cfl / k, lf)
     cand_batch.close()
     for md in cand_models:
         md.close()
-    # time steps of each passing candidate on the full workload, on a developed wavefield:
-    # from rest the Arnoldi process breaks down after p vectors (only the source tail
-    # spans the space), which would make Krylov steps look cheaper than they are.
+    # step time of every (method, m) with a passing step, on the full workload; the step
+    # time does not depend on dt, so it applies to every passing candidate of that pair
     if full_batch is not None:
         t_live = t0_for(workloads[0].f_peak)
-        for c in cands + lf:
-            if not (c.err <= target):
+        step_ms = {}
+        for (method, m), k in best_k.items():
+            if k is None:
                 continue
-            for md in full_models:
-                md.ensure_workspace(c.method, c.m)
-                md.reset_state()
-            full_batch.step(c.method, t_live - 2 * c.dt, c.dt, c.m, 2)   # inject the source
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            ns = 2
-            e0.record()
-            full_batch.step(c.method, t_live, c.dt, c.m, ns)
-            e1.record()
-            torch.cuda.synchronize()
-            c.step_ms = e0.elapsed_time(e1) / ns
+            try:
+                step_ms[method, m] = _time_step(full_batch, full_models, method, m, k * dt_cfl, t_live)
+            except EwaveError as e:
+                # passed on the sampled problems but not on the whole batch: not a solution
+                log(f"  {method} m={m} at {k} x leap-frog step fails on the full workload: {e}")
+                for c in cands:
+                    if (c.method, c.m) == (method, m) and c.err <= target:
+                        c.err = float("inf")
+        for c in cands:
+            if c.err <= target and (c.method, c.m) in step_ms:
+                c.step_ms = step_ms[c.method, c.m]
+        lf_pass = [c for c in lf if c.err <= target]
+        if lf_pass:
+            lf_pass[0].step_ms = _time_step(full_batch, full_models, "leapfrog", 1, lf_pass[0].dt, t_live)
+        lf64_pass = [c for c in lf64 if c.err <= target]
+        if lf64_pass and full_models_f64 is not None:
+            fb64 = Batch(full_models_f64)
+            lf64_pass[0].step_ms = _time_step(fb64, full_models_f64, "leapfrog", 1, lf64_pass[0].dt, t_live)
+            fb64.close()
     passing = [c for c in cands if c.err <= target and np.isfinite(c.step_ms)]
-    st.candidates = cands + lf
+    st.candidates = cands + lf + lf64
     st.selected = min(passing, key=lambda c: c.cost_s) if passing else None
     lf_pass = [c for c in lf if c.err <= target and np.isfinite(c.step_ms)]
-    st.leapfrog = min(lf_pass, key=lambda c: c.cost_s) if lf_pass else None
+    st.leapfrog = lf_pass[0] if lf_pass else None
+    lf64_pass = [c for c in lf64 if c.err <= target and np.isfinite(c.step_ms)]
+    st.leapfrog_f64 = lf64_pass[0] if lf64_pass else None
     st.seconds = time.time() - t_start
     for c in st.candidates:
         log(f"  {c.label():34s} err {c.err:.3e}  step {c.step_ms:.3f} ms  steps {c.nsteps}  "

@@ -142,6 +142,24 @@ def config_fwi(seed=2402, nshots=16):
     return Workload("fwi-401x201-o8", nx, ny, dx, 8, 40, True, c, shots, f_peak=10.0, T=1.5)
 
 
+def layered3d(nx, ny, nz, seed, vmin=1500.0, vmax=4500.0, n_interfaces=8, jitter=0.05,
+              sigma_cells=8.0, pert=0.05):
+    """The layered model of ``layered`` with the layers along z (depth, the slowest axis):
+    velocity c[k, j, i], interfaces at sorted uniform depths, rising layer velocities with
+    jitter, plus Gaussian-smoothed noise (unit std, x pert) clipped to [vmin, vmax]."""
+    rng = _rng(seed)
+    depths = np.sort(rng.uniform(0.0, nz, size=n_interfaces))
+    nl = n_interfaces + 1
+    base = np.linspace(vmin, vmax, nl) * (1.0 + jitter * rng.uniform(-1.0, 1.0, size=nl))
+    layer = np.searchsorted(depths, np.arange(nz) + 0.5)
+    c = np.broadcast_to(base[layer][:, None, None], (nz, ny, nx)).astype(np.float64)
+    noise = gaussian_filter(rng.standard_normal((nz, ny, nx)).astype(np.float32), sigma_cells,
+                            mode="reflect").astype(np.float64)
+    noise /= max(noise.std(), 1e-30)
+    c = c + pert * c * noise
+    return np.clip(c, vmin, vmax)
+
+
 def random_state(shape_list: List[Tuple[int, ...]], seed, scale=1.0):
     """Seeded N(0, scale^2) arrays of the given shapes (test inputs for operator parity)."""
     rng = _rng(seed)

@@ -35,3 +35,28 @@ def test_graph_replay_is_bitwise_identical(prec, method, m):
         out.append((g.get_state(0), g.seismogram(0, len(rec), 7)))
     assert np.array_equal(out[0][0], out[1][0])
     assert np.array_equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_kernel_timing_inside_replayed_graphs(prec):
+    """With graphs and pass timing both on, every pass of every step is timed (external
+    event nodes in the captured step) and the states equal those of an untimed run."""
+    nx, ny = 83, 37
+    om = oracle_model(nx, ny, layered(nx, ny, 17), pml=10, fs=True)
+    U0 = tuple(smooth_random_state([f.shape for f in om.zeros_state()], 13))
+    out = []
+    for timed in (False, True):
+        g = gpu_model(om, prec, p=8, max_receivers=1)
+        g.set_source_receivers(0, 41 * om.dx, 2 * om.dx, 25.0, 0.05, 1e3, np.array([[0.0, 0.0]]))
+        g.set_faber_ellipse(*oracle_ellipse(om))
+        if prec == "f32":
+            g.set_kernel_variant(0)
+        g.enable_graphs(True)
+        g.set_state(0, flatten(U0))
+        g.enable_kernel_timing(timed)
+        g.step("faber", 0.03, 1.1e-3, 12, 6)
+        if timed:
+            ms, n = g.kernel_timing()
+            assert n == 6 * 12 and ms > 0.0
+        out.append(g.get_state(0))
+    assert np.array_equal(out[0], out[1])
