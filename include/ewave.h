@@ -29,6 +29,19 @@
  *    nshots such vectors back to back (the "state" buffer).
  *  - Compact host layout (ewv_set_state / ewv_get_state): float64, u [ny][nx], v [ny][nx],
  *    w_x [ny][nx-1], w_y [ny-1][nx], concatenated (n = 2 nx ny + (nx-1) ny + nx (ny-1)).
+ *  - Three dimensions (dims = 3; not in the paper, which is 2D): the library's extension of
+ *    Eq. (1) to U = (u, v, w_x, w_y, w_z):
+ *      v_t   = -(bx by + by bz + bx bz) u - (bx + by + bz) v
+ *              + c^2 (u_xx + u_yy + u_zz + d_x w_x + d_y w_y + d_z w_z) + f,
+ *      w_a,t = -b_a w_a + (mean of the other two b's - b_a) d_a u    (a = x, y, z).
+ *    It reduces to Eq. (1) when one axis is dropped.  z is vertical, with node planes
+ *    k = 0..nz-1 and k = 0 the free surface: z takes the role of the 2D y axis (upward
+ *    derivative, Appendix A rows, no top damping).  x and y are horizontal.  w_z lives at
+ *    (i, j, k+1/2).
+ *    - Device layout: 5 fields, each [nz][ny][pitch].
+ *    - Compact host layout: each field [ez][ey][ex] with its own extents.
+ *    - Supported: forward steps of every integrator and H x.  The transpose and the
+ *      adjoint are not (UNSUPPORTED).
  */
 #ifndef EWAVE_H
 #define EWAVE_H
@@ -74,7 +87,7 @@ extern "C" {
 
 /* ---- model description ------------------------------------------------------------- */
 typedef struct ewv_model_desc {
-    int dims;            /* 2 (the paper's case)                                          */
+    int dims;            /* 2 (the paper's case) or 3 (the extension above)               */
     int nx, ny;          /* grid nodes; nx, ny >= 2                                       */
     double dx;           /* grid spacing (m), dx = dy (Sec. 2.1)                          */
     int fd_order;        /* 8 (paper, Sec. 2.1) or 4 (no free surface only)               */
@@ -85,13 +98,14 @@ typedef struct ewv_model_desc {
     int nshots;          /* independent shots (states) sharing this velocity model        */
     int src_taylor_p;    /* p of the augmented matrix H~ (Eq. matrix_ampli), 1..24        */
     int max_receivers;   /* receivers per shot (seismogram row width)                     */
+    int nz;              /* dims = 3: node planes along z (>= 2); ignored for dims = 2    */
 } ewv_model_desc;
 
 typedef struct ewv_layout_info {
     int pitch;                 /* elements per padded row (multiple of 128 bytes)          */
     int elem_bytes;            /* 4 or 8                                                   */
-    size_t field_elems;        /* ny * pitch                                               */
-    size_t vector_bytes;       /* 4 * field_elems * elem_bytes: one state vector           */
+    size_t field_elems;        /* ny * pitch (2D); nz * ny * pitch (3D)                    */
+    size_t vector_bytes;       /* fields (4; 5 in 3D) * field_elems * elem_bytes           */
     size_t state_bytes;        /* nshots * vector_bytes                                    */
     size_t params_bytes;       /* c^2 on the padded grid: field_elems * elem_bytes         */
     size_t compact_n;          /* length of the compact host state vector                  */
@@ -137,8 +151,9 @@ int ewv_reset_state(ewv_model_t model);
 
 /* ---- model inputs ------------------------------------------------------------------ */
 
-/* Velocity c (m/s) at the nodes, host float64 [ny][nx] (count = nx*ny); stores c^2 in the
- * params buffer and records c_max (used by the Faber ellipse).  Synchronous. */
+/* Velocity c (m/s) at the nodes, host float64 [ny][nx] (count = nx*ny; 3D: [nz][ny][nx],
+ * count = nx*ny*nz); stores c^2 in the params buffer and records c_max (used by the Faber
+ * ellipse).  Synchronous. */
 int ewv_set_velocity(ewv_model_t model, const double* c_host, size_t count);
 
 /* Ricker source of shot `shot` at (sx, depth sy) metres, peak frequency f_peak, delay t0,
@@ -151,8 +166,17 @@ int ewv_set_source_receivers(ewv_model_t model, int shot, double sx, double sy, 
                              double t0, double amp, int nrec, const double* rxy,
                              int32_t* src_idx_out, int32_t* rec_idx_out);
 
-/* Override the Faber ellipse (gamma, c0, c1) of Sec. 3.2's recurrence; by default it is
- * derived from c_max, beta0, dx and the stencil (see the library's design notes). */
+/* The same for a 3D model: source at (sx, sy, depth sz); receivers as nrec (x, y, depth)
+ * triples in rxyz; echoed indices src_idx_out[3] = {i, j, k}, rec_idx_out[3*nrec].  The
+ * 2D call on a 3D model (and this call on a 2D model) returns INVALID_ARG. */
+int ewv_set_source_receivers3d(ewv_model_t model, int shot, double sx, double sy, double sz,
+                               double f_peak, double t0, double amp, int nrec,
+                               const double* rxyz, int32_t* src_idx_out, int32_t* rec_idx_out);
+
+/* Override the Faber ellipse (gamma, c0, c1) of Sec. 3.2's recurrence.  By default it is
+ * the ellipse centred at -dims beta0 / 2 with semi-axes sqrt(2) x (dims beta0 / 2) (real)
+ * and sqrt(2) x omega (imaginary), omega = kappa c_max sqrt(dims |S2|) / dx, S2 the minimum
+ * of the centred second-derivative symbol, kappa = 1.30 with a free surface, else 1.05. */
 int ewv_set_faber_ellipse(ewv_model_t model, double gamma, double c0, double c1);
 int ewv_get_faber_ellipse(ewv_model_t model, double* gamma, double* c0, double* c1);
 

@@ -103,6 +103,7 @@ int ensure_tables() {
     fs_dwy_table(dwy);
     if (upload_stencil_tables(8, &kFsUyy[0][0], &kFsUy[0][0], &dwy[0][0]) != 0) return -1;
     if (upload_tma_tables(&kFsUyy[0][0], &kFsUy[0][0], &dwy[0][0]) != 0) return -1;
+    if (upload_stencil_tables_3d(&kFsUyy[0][0], &kFsUy[0][0], &dwy[0][0]) != 0) return -1;
     g_tables_device = dev;
     return 0;
 }
@@ -125,7 +126,7 @@ double symbol_min(int order) {
 
 struct Shot {
     bool has_src = false;
-    int si = 0, sj = 0;
+    int si = 0, sj = 0, sk = 0;
     double f_peak = 10.0, t0 = 0.27, amp = 1.0;
     std::vector<int> rec_off;
 };
@@ -135,6 +136,7 @@ struct Shot {
 struct ewv_model {
     ewv_model_desc d{};
     int R = 4, pitch = 0, elem = 4;
+    int nz = 1, nfields = 4;    // 3D: nz planes and five fields (w_z added)
     size_t field_elems = 0, vec_elems = 0;
     cudaStream_t stream = nullptr;
     void* state = nullptr;
@@ -170,7 +172,7 @@ struct Engine {
     std::vector<ewv_model*> models;
     std::vector<long long> versions;
     std::vector<ProblemDev> probs;
-    int nprob = 0, ntiles = 0, precision = 0, R = 4;
+    int nprob = 0, ntiles = 0, precision = 0, R = 4, dims = 2;
     ProblemDev* d_probs = nullptr;
     int* d_tile_prob = nullptr;
     double* d_partials = nullptr;
@@ -271,9 +273,21 @@ int fail(std::string& err, int code, const char* fmt, ...) {
 
 bool aligned(const void* p) { return ((uintptr_t)p & 255u) == 0; }
 
+// Extents (x, y, z) of field f: u, v on the nodes; w_x, w_y, w_z one shorter along their axis.
+void field_extent(const ewv_model* m, int f, int* ex, int* ey, int* ez) {
+    *ex = m->d.nx - (f == 2 ? 1 : 0);
+    *ey = m->d.ny - (f == 3 ? 1 : 0);
+    *ez = m->nz - (f == 4 ? 1 : 0);
+}
+
 size_t compact_n(const ewv_model* m) {
-    const size_t nx = m->d.nx, ny = m->d.ny;
-    return 2 * nx * ny + (nx - 1) * ny + nx * (ny - 1);
+    size_t n = 0;
+    for (int f = 0; f < m->nfields; ++f) {
+        int ex, ey, ez;
+        field_extent(m, f, &ex, &ey, &ez);
+        n += (size_t)ex * ey * ez;
+    }
+    return n;
 }
 
 void default_ellipse(const ewv_model* m, double* g, double* c0, double* c1) {
@@ -321,11 +335,15 @@ ProblemDev make_problem(ewv_model* m, int shot, int tile_base) {
     P.pitch = m->pitch;
     P.fs = d.free_surface;
     P.pml = d.pml_width;
+    P.nz = m->nz;
+    P.nfields = m->nfields;
     P.tiles_x = (d.nx + BX - 1) / BX;
     P.tiles_y = (d.ny + BY - 1) / BY;
-    P.ntiles = P.tiles_x * P.tiles_y;
+    P.tiles_z = m->nz > 1 ? (m->nz + KC3 - 1) / KC3 : 1;
+    P.ntiles = P.tiles_x * P.tiles_y * P.tiles_z;
     P.tile_base = tile_base;
     const Shot& s = m->shots[shot];
+    P.src_k = s.has_src ? s.sk : -1;
     P.shot = shot;
     P.has_src = s.has_src ? 1 : 0;
     P.src_i = s.has_src ? s.si : -1;
@@ -365,6 +383,9 @@ ProblemDev make_problem(ewv_model* m, int shot, int tile_base) {
 int build_engine(Engine* E, std::string& err) {
     E->drop_graphs();
     E->probs.clear();
+    E->dims = E->models.empty() ? 2 : E->models[0]->d.dims;
+    for (ewv_model* m : E->models)
+        if (m->d.dims != E->dims) return fail(err, EWV_ERR_UNSUPPORTED, "a batch cannot mix 2D and 3D models");
     std::vector<int> work_vecs;
     int tb = 0;
     for (ewv_model* m : E->models) {
@@ -381,7 +402,7 @@ int build_engine(Engine* E, std::string& err) {
     }
     E->nprob = (int)E->probs.size();
     E->ntiles = tb;
-    if (E->precision == EWV_F32) {
+    if (E->precision == EWV_F32 && E->dims == 2) {
         if (build_tensor_maps(E->probs, E->R, work_vecs, &E->d_maps) != 0)
             return fail(err, EWV_ERR_CUDA, "TMA tensor-map encoding failed");
         std::vector<int> pre(2 * (size_t)(E->nprob + 1), 0);
@@ -505,7 +526,10 @@ struct Ctx {
             e1 = next_event();
             cudaEventRecordWithFlags(e0, s, rec_flags);
         }
-        if (E->precision == EWV_F32 && !a.transpose && a.fin_mode == FIN_NONE && a.d < 0 && !a.grad) {
+        if (E->dims == 3) {
+            if (a.transpose || a.grad) launch_failed = 1;   // 3D has no adjoint pass
+            else launch_stage3d(E->precision, E->R, E->ntiles, E->d_probs, E->d_tile_prob, a, s);
+        } else if (E->precision == EWV_F32 && !a.transpose && a.fin_mode == FIN_NONE && a.d < 0 && !a.grad) {
             if (E->tma_variant < 0) autotune();
             if (E->tma_variant < 0) {
                 launch_failed = 1;
@@ -928,8 +952,9 @@ int run_krylov(Ctx& C, double t, double dt, int m, int nsteps, int* info) {
 int run_leapfrog(Ctx& C, std::vector<ewv_model*>& models, double t, double dt, int nsteps, int variant) {
     bool need_init = false;
     for (ewv_model* m : models) need_init = need_init || !m->lf_history_valid;
+    const int wmask = C.E->dims == 3 ? 0x1D : 0xD;   // u and the w fields
     if (need_init) {
-        C.copy(0, 1, 0xD, false);   // u, w_x, w_y of level n -> history (level n-1)
+        C.copy(0, 1, wmask, false);   // u and w of level n -> history (level n-1)
         for (ewv_model* m : models) m->lf_history_valid = true;
     }
     launch_set_clock(C.E->d_probs, C.E->nprob, t, dt, C.s);
@@ -938,13 +963,17 @@ int run_leapfrog(Ctx& C, std::vector<ewv_model*>& models, double t, double dt, i
     int rc = C.step_loop(nsteps, EWV_METHOD_LEAPFROG, variant, dt, 0, 0, 0, 2, [&](int n) {
         const int cur = (n & 1) ? 1 : 0, prev = 1 - cur;
         C.prologue(PRO_LEAPFROG, 1);
-        launch_leapfrog(C.E->precision, C.E->R, C.E->ntiles, C.E->d_probs, C.E->d_tile_prob,
-                        cur, prev, variant, dt, C.s);
+        if (C.E->dims == 3)
+            launch_leapfrog3d(C.E->precision, C.E->R, C.E->ntiles, C.E->d_probs, C.E->d_tile_prob,
+                              cur, prev, variant, dt, C.s);
+        else
+            launch_leapfrog(C.E->precision, C.E->R, C.E->ntiles, C.E->d_probs, C.E->d_tile_prob,
+                            cur, prev, variant, dt, C.s);
         ++*C.launches;
         C.record(prev);
     });
     if (rc != EWV_OK) return rc;
-    if (nsteps & 1) C.copy(1, 0, 0xD, true);   // level n back into the state, n-1 into history
+    if (nsteps & 1) C.copy(1, 0, wmask, true);   // level n back into the state, n-1 into history
     return check_launch(*C.err);
 }
 
@@ -997,7 +1026,7 @@ int dispatch(std::vector<ewv_model*>& models, Engine* E, cudaStream_t s, long lo
     Ctx C{E, run_s, launches, &err};
     rc = dispatch_method(C, models, method, t, dt, mm, nsteps, info);
     if (rc == EWV_OK && C.launch_failed)
-        rc = fail(err, EWV_ERR_CUDA, "no persistent TMA stencil variant could be launched");
+        rc = fail(err, EWV_ERR_CUDA, "a stencil pass could not be launched (no usable TMA variant)");
     if (own) {
         cudaEventRecord(E->ev_out, run_s);
         cudaStreamWaitEvent(s, E->ev_out, 0);
@@ -1060,7 +1089,8 @@ int ewv_create_model(const ewv_model_desc* desc, ewv_model_t* out) {
     if (!desc || !out) return EWV_ERR_INVALID_ARG;
     *out = nullptr;
     const ewv_model_desc& d = *desc;
-    if (d.dims != 2 || d.nx < 2 || d.ny < 2 || !(d.dx > 0) || (d.fd_order != 4 && d.fd_order != 8) ||
+    if ((d.dims != 2 && d.dims != 3) || (d.dims == 3 && d.nz < 2) || d.nx < 2 || d.ny < 2 ||
+        !(d.dx > 0) || (d.fd_order != 4 && d.fd_order != 8) ||
         d.pml_width < 0 || d.beta0 < 0 || (d.precision != EWV_F32 && d.precision != EWV_F64) ||
         d.nshots < 1 || d.src_taylor_p < 1 || d.src_taylor_p > MAX_P || d.max_receivers < 0)
         return EWV_ERR_INVALID_ARG;
@@ -1072,8 +1102,14 @@ int ewv_create_model(const ewv_model_desc* desc, ewv_model_t* out) {
     m->elem = d.precision == EWV_F64 ? 8 : 4;
     const int per128 = 128 / m->elem;
     m->pitch = ((d.nx + per128 - 1) / per128) * per128;
-    m->field_elems = (size_t)d.ny * m->pitch;
-    m->vec_elems = 4 * m->field_elems;
+    m->nz = d.dims == 3 ? d.nz : 1;
+    m->nfields = d.dims == 3 ? 5 : 4;
+    m->field_elems = (size_t)m->nz * d.ny * m->pitch;
+    m->vec_elems = (size_t)m->nfields * m->field_elems;
+    if ((size_t)m->nz * d.ny * m->pitch > (size_t)INT32_MAX) {
+        delete m;
+        return EWV_ERR_INVALID_ARG;   // receiver offsets are 32-bit
+    }
     m->shots.resize(d.nshots);
     const int nr = d.max_receivers > 0 ? d.max_receivers : 1;
     cudaError_t e = cudaSuccess;
@@ -1204,8 +1240,9 @@ int ewv_reset_state(ewv_model_t m) {
 
 int ewv_set_velocity(ewv_model_t m, const double* c, size_t count) {
     if (!m || !c) return EWV_ERR_INVALID_ARG;
-    const int nx = m->d.nx, ny = m->d.ny;
-    if (count != (size_t)nx * ny) return fail(m->err, EWV_ERR_BAD_SIZE_OR_ALIGNMENT, "velocity count %zu != nx*ny", count);
+    const int nx = m->d.nx, ny = m->d.ny, nz = m->nz;
+    if (count != (size_t)nx * ny * nz)
+        return fail(m->err, EWV_ERR_BAD_SIZE_OR_ALIGNMENT, "velocity count %zu != nx*ny*nz", count);
     if (!m->params) return fail(m->err, EWV_ERR_NOT_BOUND, "params buffer not bound");
     double cmax = 0.0;
     for (size_t i = 0; i < count; ++i) {
@@ -1214,11 +1251,11 @@ int ewv_set_velocity(ewv_model_t m, const double* c, size_t count) {
         cmax = std::max(cmax, c[i]);
     }
     std::vector<char> buf(m->field_elems * m->elem, 0);
-    for (int j = 0; j < ny; ++j)
+    for (size_t r = 0; r < (size_t)ny * nz; ++r)        // row r = k ny + j
         for (int i = 0; i < nx; ++i) {
-            const double v = c[(size_t)j * nx + i] * c[(size_t)j * nx + i];
-            if (m->elem == 8) ((double*)buf.data())[(size_t)j * m->pitch + i] = v;
-            else ((float*)buf.data())[(size_t)j * m->pitch + i] = (float)v;
+            const double v = c[r * nx + i] * c[r * nx + i];
+            if (m->elem == 8) ((double*)buf.data())[r * m->pitch + i] = v;
+            else ((float*)buf.data())[r * m->pitch + i] = (float)v;
         }
     CUDA_OR_FAIL(m->err, cudaMemcpyAsync(m->params, buf.data(), buf.size(), cudaMemcpyHostToDevice, m->stream));
     CUDA_OR_FAIL(m->err, cudaStreamSynchronize(m->stream));
@@ -1227,33 +1264,43 @@ int ewv_set_velocity(ewv_model_t m, const double* c, size_t count) {
     return EWV_OK;
 }
 
-int ewv_set_source_receivers(ewv_model_t m, int shot, double sx, double sy, double f_peak,
-                             double t0, double amp, int nrec, const double* rxy,
-                             int32_t* src_idx_out, int32_t* rec_idx_out) {
-    if (!m || shot < 0 || shot >= m->d.nshots) return EWV_ERR_INVALID_ARG;
-    if (nrec < 0 || nrec > m->d.max_receivers || (nrec > 0 && !rxy))
+// Shared implementation: `pos` holds (x, y) or (x, y, z) per receiver; indices per axis are
+// floor(pos / dx + 1/2) (nearest node), all bit-exact int32.
+static int set_src_rec(ewv_model_t m, int shot, const double* spos, double f_peak, double t0,
+                       double amp, int nrec, const double* rpos, int32_t* src_idx_out,
+                       int32_t* rec_idx_out) {
+    const int nd = m->d.dims;
+    if (shot < 0 || shot >= m->d.nshots) return EWV_ERR_INVALID_ARG;
+    if (nrec < 0 || nrec > m->d.max_receivers || (nrec > 0 && !rpos))
         return fail(m->err, EWV_ERR_INVALID_ARG, "nrec must be 0..max_receivers");
     if (!(f_peak > 0) || !std::isfinite(t0) || !std::isfinite(amp))
         return fail(m->err, EWV_ERR_INVALID_ARG, "bad wavelet parameters");
-    auto node = [&](double pos) { return (long long)std::floor(pos / m->d.dx + 0.5); };
-    const long long si = node(sx), sj = node(sy);
-    if (!std::isfinite(sx) || !std::isfinite(sy) || si < 0 || si >= m->d.nx || sj < 0 || sj >= m->d.ny)
-        return fail(m->err, EWV_ERR_INVALID_ARG, "source outside the grid");
+    const int ext[3] = {m->d.nx, m->d.ny, m->nz};
+    auto node = [&](const double* pos, long long* idx) {
+        for (int a = 0; a < nd; ++a) {
+            if (!std::isfinite(pos[a])) return false;
+            idx[a] = (long long)std::floor(pos[a] / m->d.dx + 0.5);
+            if (idx[a] < 0 || idx[a] >= ext[a]) return false;
+        }
+        if (nd == 2) idx[2] = 0;
+        return true;
+    };
+    long long si[3];
+    if (!node(spos, si)) return fail(m->err, EWV_ERR_INVALID_ARG, "source outside the grid");
     std::vector<int> off(nrec);
-    std::vector<int32_t> ij(2 * (size_t)nrec);
+    std::vector<int32_t> ij((size_t)nd * nrec);
     for (int r = 0; r < nrec; ++r) {
-        const double x = rxy[2 * r], y = rxy[2 * r + 1];
-        const long long ri = node(x), rj = node(y);
-        if (!std::isfinite(x) || !std::isfinite(y) || ri < 0 || ri >= m->d.nx || rj < 0 || rj >= m->d.ny)
+        long long ri[3];
+        if (!node(rpos + (size_t)nd * r, ri))
             return fail(m->err, EWV_ERR_INVALID_ARG, "receiver %d outside the grid", r);
-        off[r] = (int)(rj * m->pitch + ri);
-        ij[2 * r] = (int32_t)ri;
-        ij[2 * r + 1] = (int32_t)rj;
+        off[r] = (int)((ri[2] * m->d.ny + ri[1]) * m->pitch + ri[0]);
+        for (int a = 0; a < nd; ++a) ij[(size_t)nd * r + a] = (int32_t)ri[a];
     }
     Shot& s = m->shots[shot];
     s.has_src = true;
-    s.si = (int)si;
-    s.sj = (int)sj;
+    s.si = (int)si[0];
+    s.sj = (int)si[1];
+    s.sk = (int)si[2];
     s.f_peak = f_peak;
     s.t0 = t0;
     s.amp = amp;
@@ -1262,13 +1309,29 @@ int ewv_set_source_receivers(ewv_model_t m, int shot, double sx, double sy, doub
         CUDA_OR_FAIL(m->err, cudaMemcpy(m->d_rec + (size_t)shot * m->d.max_receivers, off.data(),
                                         sizeof(int) * nrec, cudaMemcpyHostToDevice));
     CUDA_OR_FAIL(m->err, cudaMemcpy(m->d_nrec + shot, &nrec, sizeof(int), cudaMemcpyHostToDevice));
-    if (src_idx_out) {
-        src_idx_out[0] = (int32_t)si;
-        src_idx_out[1] = (int32_t)sj;
-    }
-    if (rec_idx_out && nrec > 0) std::memcpy(rec_idx_out, ij.data(), sizeof(int32_t) * 2 * nrec);
+    if (src_idx_out)
+        for (int a = 0; a < nd; ++a) src_idx_out[a] = (int32_t)si[a];
+    if (rec_idx_out && nrec > 0) std::memcpy(rec_idx_out, ij.data(), sizeof(int32_t) * ij.size());
     ++m->version;
     return EWV_OK;
+}
+
+int ewv_set_source_receivers(ewv_model_t m, int shot, double sx, double sy, double f_peak,
+                             double t0, double amp, int nrec, const double* rxy,
+                             int32_t* src_idx_out, int32_t* rec_idx_out) {
+    if (!m) return EWV_ERR_INVALID_ARG;
+    if (m->d.dims != 2) return fail(m->err, EWV_ERR_INVALID_ARG, "3D model: use ewv_set_source_receivers3d");
+    const double spos[2] = {sx, sy};
+    return set_src_rec(m, shot, spos, f_peak, t0, amp, nrec, rxy, src_idx_out, rec_idx_out);
+}
+
+int ewv_set_source_receivers3d(ewv_model_t m, int shot, double sx, double sy, double sz,
+                               double f_peak, double t0, double amp, int nrec, const double* rxyz,
+                               int32_t* src_idx_out, int32_t* rec_idx_out) {
+    if (!m) return EWV_ERR_INVALID_ARG;
+    if (m->d.dims != 3) return fail(m->err, EWV_ERR_INVALID_ARG, "2D model: use ewv_set_source_receivers");
+    const double spos[3] = {sx, sy, sz};
+    return set_src_rec(m, shot, spos, f_peak, t0, amp, nrec, rxyz, src_idx_out, rec_idx_out);
 }
 
 int ewv_set_faber_ellipse(ewv_model_t m, double g, double c0, double c1) {
@@ -1288,34 +1351,40 @@ int ewv_get_faber_ellipse(ewv_model_t m, double* g, double* c0, double* c1) {
 }
 
 // ---- state transfer
+// Compact host order: fields in turn, each [ez][ey][ex] row-major (its own extents).
 static int pack_host(ewv_model* m, const double* h, std::vector<char>& buf) {
-    const int nx = m->d.nx, ny = m->d.ny, P = m->pitch;
+    const int ny = m->d.ny, P = m->pitch;
     buf.assign(m->vec_elems * m->elem, 0);
     size_t o = 0;
-    const int fw[4] = {nx, nx, nx - 1, nx};
-    const int fh[4] = {ny, ny, ny, ny - 1};
-    for (int f = 0; f < 4; ++f)
-        for (int j = 0; j < fh[f]; ++j)
-            for (int i = 0; i < fw[f]; ++i) {
-                const size_t idx = (size_t)f * m->field_elems + (size_t)j * P + i;
-                if (m->elem == 8) ((double*)buf.data())[idx] = h[o];
-                else ((float*)buf.data())[idx] = (float)h[o];
-                ++o;
-            }
+    for (int f = 0; f < m->nfields; ++f) {
+        int ex, ey, ez;
+        field_extent(m, f, &ex, &ey, &ez);
+        for (int k = 0; k < ez; ++k)
+            for (int j = 0; j < ey; ++j)
+                for (int i = 0; i < ex; ++i) {
+                    const size_t idx = (size_t)f * m->field_elems + ((size_t)k * ny + j) * P + i;
+                    if (m->elem == 8) ((double*)buf.data())[idx] = h[o];
+                    else ((float*)buf.data())[idx] = (float)h[o];
+                    ++o;
+                }
+    }
     return EWV_OK;
 }
 
 static void unpack_host(ewv_model* m, const std::vector<char>& buf, double* h) {
-    const int nx = m->d.nx, ny = m->d.ny, P = m->pitch;
+    const int ny = m->d.ny, P = m->pitch;
     size_t o = 0;
-    const int fw[4] = {nx, nx, nx - 1, nx};
-    const int fh[4] = {ny, ny, ny, ny - 1};
-    for (int f = 0; f < 4; ++f)
-        for (int j = 0; j < fh[f]; ++j)
-            for (int i = 0; i < fw[f]; ++i) {
-                const size_t idx = (size_t)f * m->field_elems + (size_t)j * P + i;
-                h[o++] = m->elem == 8 ? ((const double*)buf.data())[idx] : (double)((const float*)buf.data())[idx];
-            }
+    for (int f = 0; f < m->nfields; ++f) {
+        int ex, ey, ez;
+        field_extent(m, f, &ex, &ey, &ez);
+        for (int k = 0; k < ez; ++k)
+            for (int j = 0; j < ey; ++j)
+                for (int i = 0; i < ex; ++i) {
+                    const size_t idx = (size_t)f * m->field_elems + ((size_t)k * ny + j) * P + i;
+                    h[o++] = m->elem == 8 ? ((const double*)buf.data())[idx]
+                                          : (double)((const float*)buf.data())[idx];
+                }
+    }
 }
 
 int ewv_pack_vector(ewv_model_t m, const double* host, size_t n, void* dev) {
@@ -1355,6 +1424,8 @@ int ewv_apply_operator(ewv_model_t m, int transpose, const void* x, void* y) {
     if (!m || !x || !y || x == y) return EWV_ERR_INVALID_ARG;
     if (!aligned(x) || !aligned(y)) return fail(m->err, EWV_ERR_BAD_SIZE_OR_ALIGNMENT, "x, y must be 256-B aligned");
     if (!m->params || !m->velocity_set) return fail(m->err, EWV_ERR_NOT_BOUND, "velocity not set");
+    if (m->d.dims == 3 && transpose)
+        return fail(m->err, EWV_ERR_UNSUPPORTED, "the 3D operator has no transpose pass");
     Engine* E = ensure_model_engine(m);
     ProblemDev P = make_problem(m, 0, 0);
     P.tmaps = nullptr;
@@ -1374,7 +1445,11 @@ int ewv_apply_operator(ewv_model_t m, int transpose, const void* x, void* y) {
     a.ch = 1.0;
     a.ck = 1.0;
     a.transpose = transpose ? 1 : 0;
-    launch_stage(m->d.precision, m->R, P.ntiles, E->d_apply, d_tp, a, m->stream);
+    if (m->d.dims == 3) {
+        launch_stage3d(m->d.precision, m->R, P.ntiles, E->d_apply, d_tp, a, m->stream);
+    } else {
+        launch_stage(m->d.precision, m->R, P.ntiles, E->d_apply, d_tp, a, m->stream);
+    }
     ++m->launches;
     // keep the host copies alive until the copies complete
     CUDA_OR_FAIL(m->err, cudaStreamSynchronize(m->stream));
@@ -1573,6 +1648,7 @@ int ewv_batch_kernel_timing(ewv_batch_t b, double* total_ms, long long* launches
 int ewv_adjoint_step(ewv_model_t m, int method, double t, double dt, int deg,
                      const void* checkpoint, void* adj_state, void* grad) {
     if (!m || !checkpoint || !adj_state || !grad) return EWV_ERR_INVALID_ARG;
+    if (m->d.dims == 3) return fail(m->err, EWV_ERR_UNSUPPORTED, "the adjoint is two-dimensional");
     if (method != EWV_METHOD_FABER && method != EWV_METHOD_HORK)
         return fail(m->err, EWV_ERR_UNSUPPORTED, "adjoint implemented for the Faber and HORK steps");
     if (deg < 1 || deg > MAX_DEG || !(dt > 0.0))

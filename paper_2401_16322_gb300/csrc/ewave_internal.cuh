@@ -25,6 +25,8 @@ constexpr int NTHREADS = TPX * TPY;
 constexpr int VX = BX / TPX;   // outputs per thread in x
 constexpr int VY = BY / TPY;   // outputs per thread in y
 
+constexpr int KC3 = 32;          // 3D: z planes per tile (a block marches down KC3 planes)
+
 constexpr int MAX_M = 48;        // Krylov dimension limit (EWV_MAX_KRYLOV_M)
 constexpr int MAX_DEG = 128;     // Faber degree limit
 constexpr int MAX_P = 24;        // augmented tail length limit
@@ -48,6 +50,8 @@ struct ProblemDev {
     int tiles_x, tiles_y, tile_base, ntiles;
     int rec_stride, capacity, p, has_src;
     int shot, pad_;       // shot index inside its model (per-shot caller arrays)
+    int nz, nfields;      // 2D: 1 and 4 (u, v, w_x, w_y); 3D: nz and 5 (w_z added)
+    int src_k, tiles_z;   // 3D: source plane, tiles along z (KC3 planes each); 2D: 0, 1
     double beta0, inv_dx, inv_dx2, inv_pml;
     double f_peak, t0, amp;
     long long field_stride, vec_stride;
@@ -55,7 +59,7 @@ struct ProblemDev {
     void* work;           // vector 1 (vectors 1.. are consecutive)
     const void* c2;
     double* sigma;        // [MAX_SIGMA] source scalars of the current step's passes
-    const int* rec_off;   // [nrec] j*pitch + i
+    const int* rec_off;   // [nrec] (k*ny + j)*pitch + i
     void* seismo;         // [capacity][rec_stride] of this shot
     double* kry;          // [KRY_STRIDE]
     long long* clk;       // [4]: step within call, recording cursor, (unused), (unused)
@@ -102,6 +106,14 @@ void launch_stage(int precision, int R, int nblocks, const ProblemDev* probs,
 void launch_leapfrog(int precision, int R, int nblocks, const ProblemDev* probs,
                      const int* tile_prob, int cur, int prev, int variant, double dt,
                      cudaStream_t s);
+
+// kernels_3d.cu: three-dimensional forward pass and leap-frog step.
+int upload_stencil_tables_3d(const double* fs_uzz, const double* fs_uz, const double* fs_dwz);
+void launch_stage3d(int precision, int R, int nblocks, const ProblemDev* probs,
+                    const int* tile_prob, const StageArgs& a, cudaStream_t s);
+void launch_leapfrog3d(int precision, int R, int nblocks, const ProblemDev* probs,
+                       const int* tile_prob, int cur, int prev, int variant, double dt,
+                       cudaStream_t s);
 
 // kernels_tma.cu: persistent TMA-fed FP32 forward pass.
 int upload_tma_tables(const double* fs_uyy, const double* fs_uy, const double* fs_dwy);

@@ -197,7 +197,14 @@ point_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ tile_
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int nx = P->nx, ny = P->ny, pitch = P->pitch;
     const int lt = blockIdx.x - P->tile_base;
-    const int x0 = (lt % P->tiles_x) * BX, y0 = (lt / P->tiles_x) * BY;
+    // tile (x, y[, z chunk of KC3 planes]); 2D problems have nz = 1 and one z tile
+    const int nz = P->nz > 1 ? P->nz : 1;
+    const int nf = P->nfields == 5 ? 5 : 4;
+    const int rr = lt / P->tiles_x;
+    const int x0 = (lt % P->tiles_x) * BX, y0 = (rr % P->tiles_y) * BY;
+    const int k0 = nz > 1 ? (rr / P->tiles_y) * KC3 : 0;
+    const int k1 = nz > 1 ? min(k0 + KC3, nz) : 1;
+    const long long ps = (long long)ny * pitch;
     const long long fstr = P->field_stride;
     double* kry = P->kry;
 
@@ -205,12 +212,13 @@ point_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ tile_
     if (pa.mode == 3 || pa.mode == 4) {
         T* S = vptr<T>(P, pa.src);
         T* Dd = vptr<T>(P, pa.dst);
+        for (int kz = k0; kz < k1; ++kz)
         for (int b = 0; b < VY; ++b)
             for (int c = 0; c < VX; ++c) {
                 const int i = x0 + tx + c * TPX, j = y0 + ty + b * TPY;
                 if (i >= nx || j >= ny) continue;
-                const long long o = (long long)j * pitch + i;
-                for (int f = 0; f < 4; ++f) {
+                const long long o = kz * ps + (long long)j * pitch + i;
+                for (int f = 0; f < nf; ++f) {
                     if (!((pa.fmask >> f) & 1)) continue;
                     const T s = S[f * fstr + o];
                     if (pa.mode == 4) S[f * fstr + o] = Dd[f * fstr + o];
@@ -227,12 +235,13 @@ point_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ tile_
         T coef[MAX_M];
         for (int k = 1; k <= meff; ++k) coef[k - 1] = (T)(beta * kry[KRY_E + k - 1] * kry[KRY_S + k]);
         T* St = vptr<T>(P, 0);
+        for (int kz = k0; kz < k1; ++kz)
         for (int b = 0; b < VY; ++b)
             for (int c = 0; c < VX; ++c) {
                 const int i = x0 + tx + c * TPX, j = y0 + ty + b * TPY;
                 if (i >= nx || j >= ny) continue;
-                const long long o = (long long)j * pitch + i;
-                for (int f = 0; f < 4; ++f) {
+                const long long o = kz * ps + (long long)j * pitch + i;
+                for (int f = 0; f < nf; ++f) {
                     T acc = T(0);
                     for (int k = 1; k <= meff; ++k) acc += coef[k - 1] * vptr<T>(P, k - 1)[f * fstr + o];
                     St[f * fstr + o] = acc;
@@ -256,13 +265,15 @@ point_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ tile_
         coef = (T)(kry[KRY_H + (pa.k - 1) * MAX_M + (pa.j - 1)] * kry[KRY_S + pa.k]);
         Qn = pa.k < pa.j ? vptr<T>(P, pa.k) : nullptr;   // slot k+1 (or w itself)
     }
+    for (int kz = k0; kz < k1; ++kz)
     for (int b = 0; b < VY; ++b)
         for (int c = 0; c < VX; ++c) {
             const int i = x0 + tx + c * TPX, j = y0 + ty + b * TPY;
             if (i >= nx || j >= ny) continue;
-            const long long o = (long long)j * pitch + i;
-            for (int f = 0; f < 4; ++f) {
-                if ((f == 2 && i >= nx - 1) || (f == 3 && j >= ny - 1)) continue;
+            const long long o = kz * ps + (long long)j * pitch + i;
+            for (int f = 0; f < nf; ++f) {
+                if ((f == 2 && i >= nx - 1) || (f == 3 && j >= ny - 1) || (f == 4 && kz >= nz - 1))
+                    continue;
                 T val;
                 T other;
                 if (pa.mode == 0) {

@@ -38,7 +38,7 @@ EXPORTS = [
     "ewv_faber_step_noalloc", "ewv_adjoint_step", "ewv_adjoint_inject", "ewv_checkpoint_stride",
     "ewv_sum_shot_fields", "ewv_enable_graphs", "ewv_batch_enable_graphs",
     "ewv_set_kernel_variant", "ewv_kernel_variant", "ewv_batch_set_kernel_variant",
-    "ewv_batch_kernel_variant",
+    "ewv_batch_kernel_variant", "ewv_set_source_receivers3d",
 ]
 
 
@@ -51,7 +51,8 @@ class ModelDesc(ctypes.Structure):
                 ("dx", ctypes.c_double), ("fd_order", ctypes.c_int), ("pml_width", ctypes.c_int),
                 ("beta0", ctypes.c_double), ("free_surface", ctypes.c_int),
                 ("precision", ctypes.c_int), ("nshots", ctypes.c_int),
-                ("src_taylor_p", ctypes.c_int), ("max_receivers", ctypes.c_int)]
+                ("src_taylor_p", ctypes.c_int), ("max_receivers", ctypes.c_int),
+                ("nz", ctypes.c_int)]
 
 
 class NoallocFaberArgs(ctypes.Structure):
@@ -100,6 +101,7 @@ def load_library(path=LIB_PATH):
         "ewv_reset_recording": ([vp], i),
         "ewv_set_velocity": ([vp, dp, sz], i),
         "ewv_set_source_receivers": ([vp, i, d, d, d, d, d, i, dp, ip32, ip32], i),
+        "ewv_set_source_receivers3d": ([vp, i, d, d, d, d, d, d, i, dp, ip32, ip32], i),
         "ewv_set_faber_ellipse": ([vp, d, d, d], i),
         "ewv_get_faber_ellipse": ([vp, dp, dp, dp], i),
         "ewv_set_state": ([vp, i, dp, sz], i),
@@ -163,10 +165,12 @@ def _dptr(a):
 
 
 class Model:
-    """One velocity model with ``nshots`` shots, its device buffers held as torch tensors."""
+    """One velocity model with ``nshots`` shots, its device buffers held as torch tensors.
+    With ``nz`` it is three-dimensional (grid nz x ny x nx, five fields)."""
 
     def __init__(self, nx, ny, dx, order=8, pml=40, beta0=0.0, free_surface=True,
-                 precision="f32", nshots=1, p=12, max_receivers=0, device=None, stream=None):
+                 precision="f32", nshots=1, p=12, max_receivers=0, device=None, stream=None,
+                 nz=None):
         import torch
         if not torch.cuda.is_available():
             raise EwaveError("a CUDA device is required (the library has no CPU path)")
@@ -176,9 +180,11 @@ class Model:
         self.prec = F64 if precision in ("f64", "float64", F64) else F32
         self.dtype = torch.float64 if self.prec == F64 else torch.float32
         self.nx, self.ny, self.dx, self.nshots = nx, ny, dx, nshots
+        self.nz = nz
+        self.dims = 3 if nz else 2
         self.max_receivers = max_receivers
-        d = ModelDesc(2, nx, ny, dx, order, pml, beta0, int(bool(free_surface)), self.prec, nshots,
-                      p, max_receivers)
+        d = ModelDesc(self.dims, nx, ny, dx, order, pml, beta0, int(bool(free_surface)), self.prec,
+                      nshots, p, max_receivers, nz or 1)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             self._check(self.lib.ewv_create_model(ctypes.byref(d), ctypes.byref(h)), "create_model")
@@ -240,6 +246,18 @@ class Model:
             si.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
             ri.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))), "set_source_receivers")
         return si, ri[:2 * nrec].reshape(nrec, 2)
+
+    def set_source_receivers3d(self, shot, sx, sy, sz, f_peak, t0, amp=1.0, rec=None):
+        """3D model: source at (sx, sy, depth sz), receivers as (x, y, depth) rows."""
+        rec = np.zeros((0, 3)) if rec is None else np.ascontiguousarray(rec, dtype=np.float64)
+        nrec = rec.shape[0]
+        si = np.zeros(3, dtype=np.int32)
+        ri = np.zeros(max(3 * nrec, 1), dtype=np.int32)
+        self._check(self.lib.ewv_set_source_receivers3d(
+            self.h, shot, sx, sy, sz, f_peak, t0, amp, nrec, _dptr(rec) if nrec else None,
+            si.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+            ri.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))), "set_source_receivers3d")
+        return si, ri[:3 * nrec].reshape(nrec, 3)
 
     def set_faber_ellipse(self, gamma, c0, c1):
         self._check(self.lib.ewv_set_faber_ellipse(self.h, gamma, c0, c1))
