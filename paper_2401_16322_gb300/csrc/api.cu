@@ -104,6 +104,7 @@ int ensure_tables() {
     if (upload_stencil_tables(8, &kFsUyy[0][0], &kFsUy[0][0], &dwy[0][0]) != 0) return -1;
     if (upload_tma_tables(&kFsUyy[0][0], &kFsUy[0][0], &dwy[0][0]) != 0) return -1;
     if (upload_stencil_tables_3d(&kFsUyy[0][0], &kFsUy[0][0], &dwy[0][0]) != 0) return -1;
+    if (upload_tma3d_tables(&kFsUyy[0][0], &kFsUy[0][0], &dwy[0][0]) != 0) return -1;
     g_tables_device = dev;
     return 0;
 }
@@ -422,6 +423,22 @@ int build_engine(Engine* E, std::string& err) {
         CUDA_OR_FAIL(err, cudaMalloc(&E->d_tbase, sizeof(int) * pre.size()));
         CUDA_OR_FAIL(err, cudaMemcpy(E->d_tbase, pre.data(), sizeof(int) * pre.size(), cudaMemcpyHostToDevice));
     }
+    if (E->precision == EWV_F32 && E->dims == 3) {
+        if (build_tensor_maps3d(E->probs, E->R, work_vecs, &E->d_maps) != 0)
+            return fail(err, EWV_ERR_CUDA, "TMA tensor-map encoding failed (3D)");
+        std::vector<int> pre((size_t)E->nprob + 1, 0);
+        int acc = 0;
+        for (int p = 0; p < E->nprob; ++p) {
+            pre[p] = acc;
+            acc += tma3d_tasks_of(E->probs[p]);
+        }
+        pre[E->nprob] = acc;
+        E->ntiles_by[0] = acc;
+        cudaFree(E->d_tbase);
+        E->d_tbase = nullptr;
+        CUDA_OR_FAIL(err, cudaMalloc(&E->d_tbase, sizeof(int) * pre.size()));
+        CUDA_OR_FAIL(err, cudaMemcpy(E->d_tbase, pre.data(), sizeof(int) * pre.size(), cudaMemcpyHostToDevice));
+    }
     if (!E->d_err) {
         CUDA_OR_FAIL(err, cudaMalloc(&E->d_err, sizeof(int)));
         CUDA_OR_FAIL(err, cudaMemset(E->d_err, 0, sizeof(int)));
@@ -527,8 +544,16 @@ struct Ctx {
             cudaEventRecordWithFlags(e0, s, rec_flags);
         }
         if (E->dims == 3) {
+            // FP32 passes without a dot product take the TMA pipeline unless variant 1 (the
+            // plain z-marching kernel) is selected
             if (a.transpose || a.grad) launch_failed = 1;   // 3D has no adjoint pass
-            else launch_stage3d(E->precision, E->R, E->ntiles, E->d_probs, E->d_tile_prob, a, s);
+            else if (E->precision == EWV_F32 && a.fin_mode == FIN_NONE && a.d < 0 && E->tma_variant != 1) {
+                if (launch_stage_tma3d(E->R, E->d_probs, E->d_tbase, E->nprob, E->ntiles_by[0], a,
+                                       E->d_err, s) != 0)
+                    launch_failed = 1;
+            } else {
+                launch_stage3d(E->precision, E->R, E->ntiles, E->d_probs, E->d_tile_prob, a, s);
+            }
         } else if (E->precision == EWV_F32 && !a.transpose && a.fin_mode == FIN_NONE && a.d < 0 && !a.grad) {
             if (E->tma_variant < 0) autotune();
             if (E->tma_variant < 0) {

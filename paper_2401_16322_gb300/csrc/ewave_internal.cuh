@@ -115,6 +115,14 @@ void launch_leapfrog3d(int precision, int R, int nblocks, const ProblemDev* prob
                        const int* tile_prob, int cur, int prev, int variant, double dt,
                        cudaStream_t s);
 
+// kernels_tma3d.cu: persistent TMA-fed FP32 forward pass of three-dimensional problems.
+int upload_tma3d_tables(const double* fs_uzz, const double* fs_uz, const double* fs_dwz);
+int tma3d_tasks_of(const ProblemDev& P);
+int build_tensor_maps3d(std::vector<ProblemDev>& probs, int R, const std::vector<int>& work_vecs,
+                        void** d_maps_inout);
+int launch_stage_tma3d(int R, const ProblemDev* probs, const int* tbase, int nprob, int ntasks,
+                       const StageArgs& a, int* err, cudaStream_t s);
+
 // kernels_tma.cu: persistent TMA-fed FP32 forward pass.
 int upload_tma_tables(const double* fs_uyy, const double* fs_uy, const double* fs_dwy);
 int build_tensor_maps(std::vector<ProblemDev>& probs, int R, const std::vector<int>& work_vecs,

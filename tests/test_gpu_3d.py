@@ -122,3 +122,24 @@ def test_default_ellipse_is_the_3d_one():
     want = faber.ellipse_params(om.c_max, om.beta0, om.dx, 8, dims=3, free_surface=True)
     assert np.allclose(g.faber_ellipse(), want, rtol=1e-12)
     g.close()
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("method,m", [("faber", 12), ("hork", 5), ("rk44", 0)])
+def test_fp32_pass_variants_match_oracle_3d(variant, method, m):
+    """FP32 3D passes: variant 0 is the persistent TMA pipeline (64 x 8 column tiles, z chunks
+    of 32 planes, warm-up stages), variant 1 the plain z-marching kernel.  NZ = 38 spans two
+    chunks and the free-surface planes; NX, NY are ragged."""
+    om, g, src, rec, rn, U0 = _setup("f32")
+    g.set_kernel_variant(variant)
+    dt, t, nsteps = 1.0e-3, 0.03, 2
+    if method == "faber":
+        g.set_faber_ellipse(*faber.ellipse_params(om.c_max, om.beta0, om.dx, 8, dims=3,
+                                                  free_surface=True))
+    g.bind_seismogram(nsteps)
+    g.set_state(0, flatten(U0))
+    g.step(method, t, dt, m, nsteps)
+    U, S = _oracle_steps(om, method, U0, src, t, dt, m, nsteps, rn)
+    assert rel_l2(g.get_state(0), flatten(U)) < 3 * TOL["f32"]
+    assert rel_l2(g.seismogram(0, len(rec), nsteps), S) < 3 * TOL["f32"]
+    g.close()
