@@ -53,13 +53,16 @@ def parse():
     ap.add_argument("--no-search", action="store_true", help="use the default selection")
     ap.add_argument("--T", type=float, default=T_END, help="simulated time (profiling runs)")
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 and FWI side runs")
+    ap.add_argument("--n3d", type=int, default=400, help="edge of the 3D cube (side run)")
     ap.add_argument("--select", default=None, metavar="METHOD,M,K",
                     help="with --no-search: integrator, m and step in leap-frog steps "
                          f"(default {','.join(map(str, DEFAULT_SELECTION))})")
     ap.add_argument("--variant", type=int, default=-1,
                     help="FP32 stencil-pass variant (0..3; -1: autotune at first use)")
-    ap.add_argument("--case", default="full", choices=["full", "small", "medium"],
-                    help="small / medium: the 1001x501 model with 4 / 16 shots (profiling)")
+    ap.add_argument("--case", default="full", choices=["full", "small", "medium", "cube"],
+                    help="small / medium: the 1001x501 model with 4 / 16 shots (profiling); "
+                         "cube: only the 3D side run (--n3d, --check3d)")
+    ap.add_argument("--check3d", type=int, default=96, help="edge of the 3D accuracy cube")
     return ap.parse_args()
 
 
@@ -268,6 +271,109 @@ def fwi_gradient_step(method, m, dt_over_cfl):
             "gradient_finite": ok}
 
 
+def config5_3d(n=400, check_n=96):
+    """The three-dimensional workload (n^3 layered cube, 8th order, free surface, 30-point ABC,
+    Ricker 10 Hz, T = 1 s; FP32): per-step time of Faber 40, Krylov 20 and HORK 24 at the
+    steps the 2D search calibrated (multiples of the 3D leap-frog step) and of leap-frog at
+    half its stability step, the time to T, the roofline of the 3D TMA pass, and each
+    candidate's seismogram error against an FP64 reference (Faber 30 at the leap-frog step)
+    on a check_n^3 cube of the same construction over T = 0.5 s."""
+    import numpy as np
+    import torch
+    from paper_2401_16322_gb300 import Model
+    from paper_2401_16322_gb300.tts import leapfrog_step, pml_beta0, rel_l2_common
+    from paper_2401_16322_gb300.workloads import config_3d, t0_for
+    plan = [("faber", 40, 6.0), ("krylov", 20, 8.0), ("hork", 24, 5.0), ("leapfrog", 1, 0.5)]
+    c_max = 4500.0
+
+    def build(w, prec, p=12):
+        b0 = pml_beta0(c_max, w.pml, w.dx)
+        md = Model(w.n, w.n, w.dx, w.order, w.pml, b0, w.free_surface, precision=prec, p=p,
+                   max_receivers=len(w.rec), nz=w.n)
+        md.set_velocity(w.c)
+        md.set_source_receivers3d(0, *w.src, w.f_peak, t0_for(w.f_peak), 1.0, w.rec)
+        return md
+
+    def simulate(md, method, m, dt, T):
+        nsteps = int(round(T / dt))
+        md.bind_seismogram(nsteps)
+        md.reset_state()
+        md.step(method, 0.0, dt, m, nsteps)
+        return md.seismogram(0, md.max_receivers, nsteps)
+
+    out = {"workload": f"{n}^3 layered, dx 10 m, 8th order, free surface, 30-pt ABC, Ricker 10 Hz, "
+                       "T 1 s, FP32", "candidates": []}
+    # accuracy on the small cube (check_n = 0 skips it)
+    errs = {}
+    if check_n > 0:
+        wc = config_3d(check_n, pml=min(20, check_n // 4), T=0.5)
+        dt3 = leapfrog_step(c_max, wc.dx, dims=3)
+        ref_md = build(wc, "f64", p=20)
+        ref = simulate(ref_md, "faber", 30, dt3, wc.T)
+        ref_md.close()
+        cmd = build(wc, "f32")
+        for method, m, k in plan:
+            try:
+                s = simulate(cmd, method, m, k * dt3, wc.T)
+                errs[method] = rel_l2_common(s, k * dt3, ref, dt3)
+            except Exception as e:       # e.g. a non-finite Arnoldi step
+                errs[method] = float("inf")
+                log(f"3D check {method}: {e}")
+        cmd.close()
+    # timing on the full cube
+    w = config_3d(n)
+    dt3 = leapfrog_step(c_max, w.dx, dims=3)
+    md = build(w, "f32")
+    t_live = t0_for(w.f_peak)
+    peak, peak_kind = measured_peaks()
+    for method, m, k in plan:
+        dt = k * dt3
+        md.ensure_workspace(method, m)
+        md.reset_state()
+        md.step(method, t_live - 2 * dt, dt, m, 2)
+        torch.cuda.synchronize()
+        md.enable_kernel_timing(True)
+        md.kernel_timing()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ns = 4
+        e0.record()
+        md.step(method, t_live, dt, m, ns)
+        e1.record()
+        torch.cuda.synchronize()
+        kms, kn = md.kernel_timing()
+        md.enable_kernel_timing(False)
+        step_ms = e0.elapsed_time(e1) / ns
+        nsteps = int(round(w.T / dt))
+        cand = {"method": method, "m": m, "dt_over_leapfrog_step": k, "dt_ms": dt * 1e3,
+                "ms_per_step": step_ms, "nsteps_to_T": nsteps,
+                "time_to_T_s": step_ms * nsteps * 1e-3,
+                "grid_point_updates_per_s": n ** 3 / (step_ms * 1e-3),
+                "seismo_rel_err_vs_fp64": errs.get(method),
+                "error_check": f"{check_n}^3 cube, T 0.5 s, FP64 Faber 30 at the leap-frog step"}
+        if method == "faber" and kn:
+            words = pass_words3d(method, m)
+            per_launch = sum(words) * 4.0 * n ** 3 / len(words)
+            avg = kms / kn * 1e-3
+            cand["roofline"] = {"bound": "hbm", "kernel": "stage_tma3d_kernel (FP32)",
+                                "achieved": per_launch / avg / 1e9, "peak": peak, "unit": "GB/s",
+                                "frac": per_launch / avg / 1e9 / peak, "peak_kind": peak_kind,
+                                "avg_launch_us": avg * 1e6, "alg_bytes_per_launch": per_launch}
+        out["candidates"].append(cand)
+        log(f"3D {method} m={m} at {k} x: {step_ms:.2f} ms/step, {nsteps} steps, "
+            f"err {errs.get(method, float('nan')):.3e}")
+    md.close()
+    return out
+
+
+def pass_words3d(method, m):
+    """Algorithmic FP32 words per point of each 3D stencil pass (five fields)."""
+    if method == "faber":
+        return [16] + [26] * (m - 1) if m >= 2 else [16]
+    if method == "hork":
+        return [16] + [21] * (m - 1) if m >= 2 else [11]
+    raise ValueError(method)
+
+
 # ------------------------------------------------------------------------- reference arm
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -427,6 +533,7 @@ def run_ours(args):
     if rank == 0 and args.case == "full" and not args.no_extras:
         extras["fp64_single_shot"] = fp64_single_shot_estimate(wl, method, m, dt, nsteps, c_max)
         extras["fwi_gradient"] = fwi_gradient_step(method, m, dt / dt_cfl)
+        extras["config5_3d"] = config5_3d(args.n3d, args.check3d)
     result = None
     if rank == 0:
         cpu_pps, cpu_desc, cores = cpu_oracle_sample(config_batched(), method, m, dt, args.cpu_sample_s)
@@ -469,6 +576,7 @@ def run_ours(args):
                               "time_to_solution_s": lf64.cost_s} if lf64 else None),
             "fp64_single_shot": extras.get("fp64_single_shot"),
             "fwi_gradient": extras.get("fwi_gradient"),
+            "config5_3d": extras.get("config5_3d"),
             "search_s": study.seconds if study else None,
             "reference_self_check": study.ref_self_check if study else None,
             "candidates": ([{"method": c.method, "m": c.m, "dt_ms": round(c.dt * 1e3, 4),
@@ -486,6 +594,11 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.case == "cube":
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        print(json.dumps({"config5_3d": config5_3d(args.n3d, args.check3d)}), flush=True)
+        return 0
     return run_ours(args)
 
 

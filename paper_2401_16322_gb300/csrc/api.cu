@@ -500,6 +500,9 @@ StageArgs stage_defaults() {
     return a;
 }
 
+// 3D engines: consumer warps of the TMA pass for the selected variant (2: 8 warps, else 16).
+int tma3d_warps(const Engine* E) { return E->tma_variant == 2 ? 8 : 16; }
+
 // Add the pass times of a timed graph's last replay (if not read yet) to the accumulator.
 int harvest_graph_timing(Engine* E, Engine::StepGraph& sg, std::string& err) {
     if (!sg.pending) return EWV_OK;
@@ -544,12 +547,12 @@ struct Ctx {
             cudaEventRecordWithFlags(e0, s, rec_flags);
         }
         if (E->dims == 3) {
-            // FP32 passes without a dot product take the TMA pipeline unless variant 1 (the
-            // plain z-marching kernel) is selected
+            // FP32 passes without a dot product take the TMA pipeline (variant 0: 16 consumer
+            // warps, 2: 8 warps) unless variant 1 (the plain z-marching kernel) is selected
             if (a.transpose || a.grad) launch_failed = 1;   // 3D has no adjoint pass
             else if (E->precision == EWV_F32 && a.fin_mode == FIN_NONE && a.d < 0 && E->tma_variant != 1) {
-                if (launch_stage_tma3d(E->R, E->d_probs, E->d_tbase, E->nprob, E->ntiles_by[0], a,
-                                       E->d_err, s) != 0)
+                if (launch_stage_tma3d(E->R, tma3d_warps(E), E->d_probs, E->d_tbase, E->nprob,
+                                       E->ntiles_by[0], a, E->d_err, s) != 0)
                     launch_failed = 1;
             } else {
                 launch_stage3d(E->precision, E->R, E->ntiles, E->d_probs, E->d_tile_prob, a, s);
@@ -988,7 +991,11 @@ int run_leapfrog(Ctx& C, std::vector<ewv_model*>& models, double t, double dt, i
     int rc = C.step_loop(nsteps, EWV_METHOD_LEAPFROG, variant, dt, 0, 0, 0, 2, [&](int n) {
         const int cur = (n & 1) ? 1 : 0, prev = 1 - cur;
         C.prologue(PRO_LEAPFROG, 1);
-        if (C.E->dims == 3)
+        if (C.E->dims == 3 && C.E->precision == EWV_F32 && C.E->tma_variant != 1) {
+            if (launch_leapfrog_tma3d(C.E->R, tma3d_warps(C.E), C.E->d_probs, C.E->d_tbase, C.E->nprob,
+                                      C.E->ntiles_by[0], cur, prev, variant, dt, C.E->d_err, C.s) != 0)
+                C.launch_failed = 1;
+        } else if (C.E->dims == 3)
             launch_leapfrog3d(C.E->precision, C.E->R, C.E->ntiles, C.E->d_probs, C.E->d_tile_prob,
                               cur, prev, variant, dt, C.s);
         else

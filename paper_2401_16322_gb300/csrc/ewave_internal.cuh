@@ -120,8 +120,11 @@ int upload_tma3d_tables(const double* fs_uzz, const double* fs_uz, const double*
 int tma3d_tasks_of(const ProblemDev& P);
 int build_tensor_maps3d(std::vector<ProblemDev>& probs, int R, const std::vector<int>& work_vecs,
                         void** d_maps_inout);
-int launch_stage_tma3d(int R, const ProblemDev* probs, const int* tbase, int nprob, int ntasks,
-                       const StageArgs& a, int* err, cudaStream_t s);
+int launch_stage_tma3d(int R, int warps, const ProblemDev* probs, const int* tbase, int nprob,
+                       int ntasks, const StageArgs& a, int* err, cudaStream_t s);
+int launch_leapfrog_tma3d(int R, int warps, const ProblemDev* probs, const int* tbase, int nprob,
+                          int ntasks, int cur, int prev, int variant, double dt, int* err,
+                          cudaStream_t s);
 
 // kernels_tma.cu: persistent TMA-fed FP32 forward pass.
 int upload_tma_tables(const double* fs_uyy, const double* fs_uy, const double* fs_dwy);

@@ -167,7 +167,10 @@ __device__ __forceinline__ int find_task_problem(const int* __restrict__ base, i
     return lo;
 }
 
-template <int R, int NW, int NST>
+// MODE 0: integrator pass (epilogue above).  MODE 1: leap-frog step (Sec. 3.1's scheme on
+// the 3D system): a.x = level n (cur), a.a = level n-1 (prev, overwritten with level n+1 in
+// fields u, w_x, w_y, w_z), a.m = damping variant (0 time-averaged, 1 explicit), a.dt.
+template <int R, int NW, int NST, int MODE>
 __global__ void __launch_bounds__(NW * 32 + 32, 1)
 stage_tma3d_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ tbase, int nprob,
                    int ntasks, StageArgs a, int* err) {
@@ -196,8 +199,9 @@ stage_tma3d_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__
 
     const bool has_u = a.u >= 0, has_a = a.a >= 0;
     const uint32_t bytes_warm = 2u * L::PL * 4u;
-    const uint32_t bytes_full = (uint32_t)(L::PU_OFF * 4) + (has_u ? 5u * L::PL * 4u : 0u) +
-                                (has_a ? 5u * L::PL * 4u : 0u);
+    // the leap-frog step does not read v
+    const uint32_t bytes_full = (uint32_t)(L::PU_OFF * 4) - (MODE == 1 ? L::PL * 4u : 0u) +
+                                (has_u ? 5u * L::PL * 4u : 0u) + (has_a ? 5u * L::PL * 4u : 0u);
     int issued = 0;
 
     if (warp == NW) {
@@ -269,7 +273,7 @@ stage_tma3d_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__
                         tma5(st + L::U_OFF, map3(maps, kx, 0), x0 - TX3, y0 - R, c, 0, vx, &full[s]);
                         tma5(st + L::WX_OFF, map3(maps, kx, 1), x0 - TX3, y0, c, 2, vx, &full[s]);
                         tma5(st + L::WY_OFF, map3(maps, kx, 2), x0, y0 - R, c, 3, vx, &full[s]);
-                        tma5(st + L::V_OFF, map3(maps, kx, 3), x0, y0, c, 1, vx, &full[s]);
+                        if (MODE == 0) tma5(st + L::V_OFF, map3(maps, kx, 3), x0, y0, c, 1, vx, &full[s]);
                         tma3(st + L::C2_OFF, maps + 10, x0, y0, c, &full[s]);
                         if (has_u)
                             tma5(st + L::PU_OFF, map3(maps, a.u, 4), x0, y0, c, 0, a.u == 0 ? 0 : a.u - 1,
@@ -403,32 +407,65 @@ stage_tma3d_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__
                         const float byn = dmp(beta0, inv_pml, (float)min(j + 1, ny - j), pml);
                         const float byh = dmp(beta0, inv_pml, fminf((float)j + 1.5f, (float)(ny - j) - 0.5f), pml);
                         const int pt = ly * BX + tx;
-                        const float xv = st[L::V_OFF + pt];
                         const float xwx = wxrow[0];
                         const float xwy = swy[(ly + R) * BX + tx];
                         const float xwz = wq[r][R];
                         const float c2 = st[L::C2_OFF + pt];
-                        float hv = -(bxn * byn + byn * bzn + bxn * bzn) * u - (bxn + byn + bzn) * xv
-                                   + c2 * ((uxx + uyy + uzz) * idx2 + (dwx + dwy + dwz) * idx1);
-                        if (i == ti.src_i && j == ti.src_j && c == ti.src_k) hv += ti.sig;
-                        const float hwx = (i < nx - 1) ? (0.5f * (byn + bzn) - bxh) * dux * idx1 - bxh * xwx : 0.f;
-                        const float hwy = (j < ny - 1) ? (0.5f * (bxn + bzn) - byh) * duy * idx1 - byh * xwy : 0.f;
-                        const float hwz = (c < nz - 1) ? (0.5f * (bxn + byn) - bzh) * duz * idx1 - bzh * xwz : 0.f;
-                        const float xf[5] = {u, xv, xwx, xwy, xwz};
-                        const float hf[5] = {xv, hv, hwx, hwy, hwz};
+                        const bool at_src = i == ti.src_i && j == ti.src_j && c == ti.src_k;
                         const long long o = (long long)c * ps + oc;
-                        float* yp = ti.Y ? ti.Y + o : nullptr;
-                        float* ap = ti.A ? ti.A + o : nullptr;
+                        if constexpr (MODE == 0) {
+                            const float xv = st[L::V_OFF + pt];
+                            float hv = -(bxn * byn + byn * bzn + bxn * bzn) * u - (bxn + byn + bzn) * xv
+                                       + c2 * ((uxx + uyy + uzz) * idx2 + (dwx + dwy + dwz) * idx1);
+                            if (at_src) hv += ti.sig;
+                            const float hwx = (i < nx - 1) ? (0.5f * (byn + bzn) - bxh) * dux * idx1 - bxh * xwx : 0.f;
+                            const float hwy = (j < ny - 1) ? (0.5f * (bxn + bzn) - byh) * duy * idx1 - byh * xwy : 0.f;
+                            const float hwz = (c < nz - 1) ? (0.5f * (bxn + byn) - bzh) * duz * idx1 - bzh * xwz : 0.f;
+                            const float xf[5] = {u, xv, xwx, xwy, xwz};
+                            const float hf[5] = {xv, hv, hwx, hwy, hwz};
+                            float* yp = ti.Y ? ti.Y + o : nullptr;
+                            float* ap = ti.A ? ti.A + o : nullptr;
 #pragma unroll
-                        for (int fld = 0; fld < 5; ++fld) {
-                            const bool pad = (fld == 2 && i >= nx - 1) || (fld == 3 && j >= ny - 1) ||
-                                             (fld == 4 && c >= nz - 1);
-                            const float uval = has_u ? st[L::PU_OFF + fld * L::PL + pt] : 0.f;
-                            const float aval = has_a ? st[L::PA_OFF + fld * L::PL + pt] : 0.f;
-                            const float kf = cxf * xf[fld] + chf * hf[fld];
-                            const float yf = pad ? 0.f : (cuf * uval + ckf * kf);
-                            if (yp) yp[fld * fstr] = yf;
-                            if (ap) ap[fld * fstr] = pad ? 0.f : (caf * aval + cauf * uval + cakf * kf + cayf * yf + caxf * xf[fld]);
+                            for (int fld = 0; fld < 5; ++fld) {
+                                const bool pad = (fld == 2 && i >= nx - 1) || (fld == 3 && j >= ny - 1) ||
+                                                 (fld == 4 && c >= nz - 1);
+                                const float uval = has_u ? st[L::PU_OFF + fld * L::PL + pt] : 0.f;
+                                const float aval = has_a ? st[L::PA_OFF + fld * L::PL + pt] : 0.f;
+                                const float kf = cxf * xf[fld] + chf * hf[fld];
+                                const float yf = pad ? 0.f : (cuf * uval + ckf * kf);
+                                if (yp) yp[fld * fstr] = yf;
+                                if (ap) ap[fld * fstr] = pad ? 0.f : (caf * aval + cauf * uval + cakf * kf + cayf * yf + caxf * xf[fld]);
+                            }
+                        } else {
+                            const float dt = (float)a.dt;
+                            const float inv_dt2 = 1.f / (dt * dt), inv_2dt = 1.f / (2.f * dt);
+                            const float bsum = bxn + byn + bzn;
+                            float rhs = -(bxn * byn + byn * bzn + bxn * bzn) * u
+                                        + c2 * ((uxx + uyy + uzz) * idx2 + (dwx + dwy + dwz) * idx1);
+                            if (at_src) rhs += ti.sig;
+                            const float* pm = st + L::PA_OFF + pt;   // level n-1, five fields
+                            const float um = pm[0];
+                            const float up = ((2.f * u - um) * inv_dt2 + bsum * um * inv_2dt + rhs)
+                                             / (inv_dt2 + bsum * inv_2dt);
+                            const bool has[3] = {i < nx - 1, j < ny - 1, c < nz - 1};
+                            const float bh[3] = {bxh, byh, bzh};
+                            const float gco[3] = {0.5f * (byn + bzn) - bxh, 0.5f * (bxn + bzn) - byh,
+                                                  0.5f * (bxn + byn) - bzh};
+                            const float du[3] = {dux, duy, duz};
+                            const float wcur[3] = {xwx, xwy, xwz};
+                            float* out = ti.Y + o;
+                            out[0] = up;
+#pragma unroll
+                            for (int a3 = 0; a3 < 3; ++a3) {
+                                float wn = 0.f;
+                                if (has[a3]) {
+                                    const float wm = pm[(2 + a3) * L::PL];
+                                    const float g = gco[a3] * du[a3] * idx1;
+                                    wn = a.m == 0 ? ((1.f - bh[a3] * dt) * wm + 2.f * dt * g) / (1.f + bh[a3] * dt)
+                                                  : wm + 2.f * dt * (-bh[a3] * wcur[a3] + g);
+                                }
+                                out[(2 + a3) * fstr] = wn;
+                            }
                         }
                     }
                 }
@@ -488,7 +525,7 @@ int enc3(CUtensorMap* out, const void* base, const ProblemDev& P, int bx, int by
 
 int g_sms3 = 0;
 
-template <int R, int NW, int NST>
+template <int R, int NW, int NST, int MODE>
 int launch3(const ProblemDev* probs, const int* tbase, int nprob, int ntasks, const StageArgs& a,
             int* err, cudaStream_t s) {
     const size_t smem = (size_t)NST * Stage3<R>::BYTES + 1024;
@@ -496,7 +533,7 @@ int launch3(const ProblemDev* probs, const int* tbase, int nprob, int ntasks, co
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return -1;
     if (!(configured >> dev & 1ull)) {
-        if (cudaFuncSetAttribute(stage_tma3d_kernel<R, NW, NST>,
+        if (cudaFuncSetAttribute(stage_tma3d_kernel<R, NW, NST, MODE>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return -1;
         configured |= 1ull << dev;
@@ -506,7 +543,7 @@ int launch3(const ProblemDev* probs, const int* tbase, int nprob, int ntasks, co
         if (g_sms3 <= 0) g_sms3 = 1;
     }
     const int grid = ntasks < g_sms3 ? ntasks : g_sms3;
-    stage_tma3d_kernel<R, NW, NST><<<grid, NW * 32 + 32, smem, s>>>(probs, tbase, nprob, ntasks, a, err);
+    stage_tma3d_kernel<R, NW, NST, MODE><<<grid, NW * 32 + 32, smem, s>>>(probs, tbase, nprob, ntasks, a, err);
     return 0;
 }
 
@@ -557,11 +594,42 @@ int build_tensor_maps3d(std::vector<ProblemDev>& probs, int R, const std::vector
     return 0;
 }
 
-int launch_stage_tma3d(int R, const ProblemDev* probs, const int* tbase, int nprob, int ntasks,
-                       const StageArgs& a, int* err, cudaStream_t s) {
+// warps: 16 consumer warps (one row per thread) or 8 (two rows per thread).
+int launch_stage_tma3d(int R, int warps, const ProblemDev* probs, const int* tbase, int nprob,
+                       int ntasks, const StageArgs& a, int* err, cudaStream_t s) {
     if (ntasks <= 0) return nprob > 0 ? -1 : 0;
-    if (R == 4) return launch3<4, 8, 4>(probs, tbase, nprob, ntasks, a, err, s);
-    if (R == 2) return launch3<2, 8, 4>(probs, tbase, nprob, ntasks, a, err, s);
+    if (warps == 16) {
+        if (R == 4) return launch3<4, 16, 4, 0>(probs, tbase, nprob, ntasks, a, err, s);
+        if (R == 2) return launch3<2, 16, 4, 0>(probs, tbase, nprob, ntasks, a, err, s);
+    } else {
+        if (R == 4) return launch3<4, 8, 4, 0>(probs, tbase, nprob, ntasks, a, err, s);
+        if (R == 2) return launch3<2, 8, 4, 0>(probs, tbase, nprob, ntasks, a, err, s);
+    }
+    return -1;
+}
+
+int launch_leapfrog_tma3d(int R, int warps, const ProblemDev* probs, const int* tbase, int nprob,
+                          int ntasks, int cur, int prev, int variant, double dt, int* err,
+                          cudaStream_t s) {
+    if (ntasks <= 0) return nprob > 0 ? -1 : 0;
+    StageArgs a{};
+    a.x = cur;
+    a.u = -1;
+    a.a = prev;
+    a.y_out = prev;
+    a.acc_out = -1;
+    a.d = -1;
+    a.src_slot = 0;
+    a.x_scale_slot = -1;
+    a.m = variant;
+    a.dt = dt;
+    if (warps == 16) {
+        if (R == 4) return launch3<4, 16, 4, 1>(probs, tbase, nprob, ntasks, a, err, s);
+        if (R == 2) return launch3<2, 16, 4, 1>(probs, tbase, nprob, ntasks, a, err, s);
+    } else {
+        if (R == 4) return launch3<4, 8, 4, 1>(probs, tbase, nprob, ntasks, a, err, s);
+        if (R == 2) return launch3<2, 8, 4, 1>(probs, tbase, nprob, ntasks, a, err, s);
+    }
     return -1;
 }
 

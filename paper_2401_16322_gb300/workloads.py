@@ -160,6 +160,34 @@ def layered3d(nx, ny, nz, seed, vmin=1500.0, vmax=4500.0, n_interfaces=8, jitter
     return np.clip(c, vmin, vmax)
 
 
+@dataclass
+class Workload3D:
+    """One three-dimensional model with a single shot (positions in metres, z = depth)."""
+    name: str
+    n: int
+    dx: float
+    order: int
+    pml: int
+    free_surface: bool
+    c: np.ndarray            # [nz, ny, nx]
+    src: Tuple[float, float, float]
+    rec: np.ndarray          # [nrec, 3] (x, y, depth)
+    f_peak: float
+    T: float
+
+
+def config_3d(n=400, seed=2403, pml=30, T=1.0):
+    """n^3 layered model (layers along depth, as ``layered``), dx 10 m, 8th order, free
+    surface, ``pml``-point ABC, Ricker 10 Hz at the centre two cells below the surface,
+    receivers every 4th node along the centre line of the surface, T 1 s."""
+    dx = 10.0
+    c = layered3d(n, n, n, seed)
+    mid = (n // 2) * dx
+    rec = np.array([[i * dx, mid, 0.0] for i in range(0, n, 4)])
+    return Workload3D(f"layered3d-{n}^3-o8", n, dx, 8, pml, True, c, (mid, mid, 2 * dx), rec,
+                      10.0, T)
+
+
 def random_state(shape_list: List[Tuple[int, ...]], seed, scale=1.0):
     """Seeded N(0, scale^2) arrays of the given shapes (test inputs for operator parity)."""
     rng = _rng(seed)

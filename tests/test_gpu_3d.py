@@ -124,15 +124,16 @@ def test_default_ellipse_is_the_3d_one():
     g.close()
 
 
-@pytest.mark.parametrize("variant", [0, 1])
-@pytest.mark.parametrize("method,m", [("faber", 12), ("hork", 5), ("rk44", 0)])
+@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("method,m", [("faber", 12), ("hork", 5), ("rk44", 0), ("leapfrog", 0)])
 def test_fp32_pass_variants_match_oracle_3d(variant, method, m):
-    """FP32 3D passes: variant 0 is the persistent TMA pipeline (64 x 8 column tiles, z chunks
-    of 32 planes, warm-up stages), variant 1 the plain z-marching kernel.  NZ = 38 spans two
-    chunks and the free-surface planes; NX, NY are ragged."""
+    """FP32 3D passes: variants 0 and 2 are the persistent TMA pipeline (64 x 8 column tiles,
+    z chunks of 32 planes, warm-up stages) with 16 and 8 consumer warps, variant 1 the plain
+    z-marching kernel.  NZ = 38 spans two chunks and the free-surface planes; NX, NY are
+    ragged."""
     om, g, src, rec, rn, U0 = _setup("f32")
     g.set_kernel_variant(variant)
-    dt, t, nsteps = 1.0e-3, 0.03, 2
+    dt, t, nsteps = (3e-4 if method == "leapfrog" else 1.0e-3), 0.03, 2
     if method == "faber":
         g.set_faber_ellipse(*faber.ellipse_params(om.c_max, om.beta0, om.dx, 8, dims=3,
                                                   free_surface=True))
