@@ -271,19 +271,29 @@ def fwi_gradient_step(method, m, dt_over_cfl):
             "gradient_finite": ok}
 
 
-def config5_3d(n=400, check_n=96):
+# Delta-t_max scan of the 3D side run: (method, m values, step multiples, largest first)
+SCAN3D = (("faber", (30, 40, 50, 60), tuple(range(24, 1, -1))),
+          ("hork", (12, 16, 24), tuple(range(12, 0, -1))),
+          ("krylov", (20,), tuple(range(24, 1, -1))))
+LEAPFROG3D_DIVISORS = (1, 2, 3, 4, 6, 8)
+
+
+def config5_3d(n=400, check_n=96, target=TARGET):
     """The three-dimensional workload (n^3 layered cube, 8th order, free surface, 30-point ABC,
-    Ricker 10 Hz, T = 1 s; FP32): per-step time of Faber 40, Krylov 20 and HORK 24 at the
-    steps the 2D search calibrated (multiples of the 3D leap-frog step) and of leap-frog at
-    half its stability step, the time to T, the roofline of the 3D TMA pass, and each
-    candidate's seismogram error against an FP64 reference (Faber 30 at the leap-frog step)
-    on a check_n^3 cube of the same construction over T = 0.5 s."""
+    Ricker 10 Hz, T = 1 s; FP32).
+
+    1. Delta-t_max search on a check_n^3 cube of the same construction over T = 0.5 s: for
+       every (method, m) the largest multiple of the 3D leap-frog step whose seismogram is
+       within the target of an FP64 reference (Faber 30 at the leap-frog step); leap-frog at
+       1 .. 1/8 of its step.
+    2. Time per step of each passing (method, m) at its Delta-t_max on the n^3 cube, time to
+       T, and the roofline of the 3D TMA pass (Faber).
+    check_n = 0 skips the search and times Faber 40 at 6 x (profiling runs)."""
     import numpy as np
     import torch
     from paper_2401_16322_gb300 import Model
-    from paper_2401_16322_gb300.tts import leapfrog_step, pml_beta0, rel_l2_common
+    from paper_2401_16322_gb300.tts import dt_max_scan, leapfrog_step, pml_beta0, rel_l2_common
     from paper_2401_16322_gb300.workloads import config_3d, t0_for
-    plan = [("faber", 40, 6.0), ("krylov", 20, 8.0), ("hork", 24, 5.0), ("leapfrog", 1, 0.5)]
     c_max = 4500.0
 
     def build(w, prec, p=12):
@@ -302,66 +312,107 @@ def config5_3d(n=400, check_n=96):
         return md.seismogram(0, md.max_receivers, nsteps)
 
     out = {"workload": f"{n}^3 layered, dx 10 m, 8th order, free surface, 30-pt ABC, Ricker 10 Hz, "
-                       "T 1 s, FP32", "candidates": []}
-    # accuracy on the small cube (check_n = 0 skips it)
-    errs = {}
+                       "T 1 s, FP32", "target": target, "candidates": []}
+    found = []          # (method, m, k, err); k < 1: leap-frog divisor 1/k
     if check_n > 0:
+        t_search = time.perf_counter()
         wc = config_3d(check_n, pml=min(20, check_n // 4), T=0.5)
         dt3 = leapfrog_step(c_max, wc.dx, dims=3)
         ref_md = build(wc, "f64", p=20)
         ref = simulate(ref_md, "faber", 30, dt3, wc.T)
-        ref_md.close()
+        log(f"3D reference {time.perf_counter() - t_search:.1f} s")
         cmd = build(wc, "f32")
-        for method, m, k in plan:
+
+        def err_of(md, method, m, dt):
             try:
-                s = simulate(cmd, method, m, k * dt3, wc.T)
-                errs[method] = rel_l2_common(s, k * dt3, ref, dt3)
+                return rel_l2_common(simulate(md, method, m, dt, wc.T), dt, ref, dt3)
             except Exception as e:       # e.g. a non-finite Arnoldi step
-                errs[method] = float("inf")
-                log(f"3D check {method}: {e}")
+                log(f"3D {method} m={m} dt={dt * 1e3:.3f} ms: {e}")
+                return float("inf")
+
+        for method, ms, ks in SCAN3D:
+            for m in ms:
+                errs = {}
+                k, _ = dt_max_scan(ks, lambda k: errs.setdefault(k, err_of(cmd, method, m, k * dt3)),
+                                   target)
+                if k is not None:
+                    found.append((method, m, float(k), errs[k]))
+                log(f"3D {method} m={m}: dt_max = " + (f"{k} x leap-frog step" if k else "none")
+                    + f" ({time.perf_counter() - t_search:.1f} s)")
+        for prec, md in (("f32", cmd), ("f64", ref_md)):
+            errs = {}
+            k, _ = dt_max_scan(LEAPFROG3D_DIVISORS,
+                               lambda k: errs.setdefault(k, err_of(md, "leapfrog", 1, dt3 / k)), target)
+            if k is not None:
+                found.append(("leapfrog" if prec == "f32" else "leapfrog_f64", 1, 1.0 / k, errs[k]))
+        ref_md.close()
         cmd.close()
+        out["search_s"] = time.perf_counter() - t_search
+        out["error_check"] = f"{check_n}^3 cube, T 0.5 s, FP64 Faber 30 at the 3D leap-frog step"
+    else:
+        found.append(("faber", 40, 6.0, float("nan")))
     # timing on the full cube
     w = config_3d(n)
     dt3 = leapfrog_step(c_max, w.dx, dims=3)
-    md = build(w, "f32")
     t_live = t0_for(w.f_peak)
     peak, peak_kind = measured_peaks()
-    for method, m, k in plan:
+    md = build(w, "f32")
+    md64 = None
+    for method, m, k, err in found:
         dt = k * dt3
-        md.ensure_workspace(method, m)
-        md.reset_state()
-        md.step(method, t_live - 2 * dt, dt, m, 2)
-        torch.cuda.synchronize()
-        md.enable_kernel_timing(True)
-        md.kernel_timing()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ns = 4
-        e0.record()
-        md.step(method, t_live, dt, m, ns)
-        e1.record()
-        torch.cuda.synchronize()
-        kms, kn = md.kernel_timing()
-        md.enable_kernel_timing(False)
+        prec = "f32"
+        dev = md
+        if method == "leapfrog_f64":
+            if md64 is None:
+                md.close()
+                md = None
+                md64 = build(w, "f64")
+            dev, prec, method = md64, "f64", "leapfrog"
+        dev.ensure_workspace(method, m)
+        dev.reset_state()
+        try:
+            dev.step(method, t_live - 2 * dt, dt, m, 2)
+            torch.cuda.synchronize()
+            dev.enable_kernel_timing(True)
+            dev.kernel_timing()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ns = 4
+            e0.record()
+            dev.step(method, t_live, dt, m, ns)
+            e1.record()
+            torch.cuda.synchronize()
+            kms, kn = dev.kernel_timing()
+            dev.enable_kernel_timing(False)
+        except Exception as e:
+            log(f"3D {method} m={m} at {k} x fails on the {n}^3 cube: {e}")
+            continue
         step_ms = e0.elapsed_time(e1) / ns
         nsteps = int(round(w.T / dt))
-        cand = {"method": method, "m": m, "dt_over_leapfrog_step": k, "dt_ms": dt * 1e3,
-                "ms_per_step": step_ms, "nsteps_to_T": nsteps,
+        cand = {"method": method, "precision": prec, "m": m, "dt_over_leapfrog_step": k,
+                "dt_ms": dt * 1e3, "ms_per_step": step_ms, "nsteps_to_T": nsteps,
                 "time_to_T_s": step_ms * nsteps * 1e-3,
                 "grid_point_updates_per_s": n ** 3 / (step_ms * 1e-3),
-                "seismo_rel_err_vs_fp64": errs.get(method),
-                "error_check": f"{check_n}^3 cube, T 0.5 s, FP64 Faber 30 at the leap-frog step"}
-        if method == "faber" and kn:
+                "seismo_rel_err_vs_fp64": err}
+        if method == "faber" and kn and prec == "f32":
             words = pass_words3d(method, m)
             per_launch = sum(words) * 4.0 * n ** 3 / len(words)
             avg = kms / kn * 1e-3
-            cand["roofline"] = {"bound": "hbm", "kernel": "stage_tma3d_kernel (FP32)",
+            cand["roofline"] = {"bound": "hbm", "kernel": "stage_tma3d_kernel (FP32, 16 warps)",
                                 "achieved": per_launch / avg / 1e9, "peak": peak, "unit": "GB/s",
                                 "frac": per_launch / avg / 1e9 / peak, "peak_kind": peak_kind,
                                 "avg_launch_us": avg * 1e6, "alg_bytes_per_launch": per_launch}
         out["candidates"].append(cand)
-        log(f"3D {method} m={m} at {k} x: {step_ms:.2f} ms/step, {nsteps} steps, "
-            f"err {errs.get(method, float('nan')):.3e}")
-    md.close()
+        log(f"3D {method} ({prec}) m={m} at {k:.3g} x: {step_ms:.2f} ms/step, {nsteps} steps, "
+            f"{cand['time_to_T_s']:.2f} s, err {err:.3e}")
+    for d in (md, md64):
+        if d is not None:
+            d.close()
+    exp = [c for c in out["candidates"] if c["method"] != "leapfrog"]
+    if exp:
+        out["selected"] = min(exp, key=lambda c: c["time_to_T_s"])
+    lf = [c for c in out["candidates"] if c["method"] == "leapfrog"]
+    if lf:
+        out["leapfrog_best"] = min(lf, key=lambda c: c["time_to_T_s"])
     return out
 
 

@@ -445,8 +445,9 @@ stage_tma3d_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__
                             if (at_src) rhs += ti.sig;
                             const float* pm = st + L::PA_OFF + pt;   // level n-1, five fields
                             const float um = pm[0];
-                            const float up = ((2.f * u - um) * inv_dt2 + bsum * um * inv_2dt + rhs)
-                                             / (inv_dt2 + bsum * inv_2dt);
+                            // fast (2-ulp) division: the step's own error is far larger
+                            const float up = __fdividef((2.f * u - um) * inv_dt2 + bsum * um * inv_2dt + rhs,
+                                                        inv_dt2 + bsum * inv_2dt);
                             const bool has[3] = {i < nx - 1, j < ny - 1, c < nz - 1};
                             const float bh[3] = {bxh, byh, bzh};
                             const float gco[3] = {0.5f * (byn + bzn) - bxh, 0.5f * (bxn + bzn) - byh,
@@ -461,7 +462,7 @@ stage_tma3d_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__
                                 if (has[a3]) {
                                     const float wm = pm[(2 + a3) * L::PL];
                                     const float g = gco[a3] * du[a3] * idx1;
-                                    wn = a.m == 0 ? ((1.f - bh[a3] * dt) * wm + 2.f * dt * g) / (1.f + bh[a3] * dt)
+                                    wn = a.m == 0 ? __fdividef((1.f - bh[a3] * dt) * wm + 2.f * dt * g, 1.f + bh[a3] * dt)
                                                   : wm + 2.f * dt * (-bh[a3] * wcur[a3] + g);
                                 }
                                 out[(2 + a3) * fstr] = wn;
