@@ -182,6 +182,8 @@ struct Engine {
     ProblemDev* d_apply = nullptr;
     void* d_maps = nullptr;     // FP32: TMA tensor maps of every problem
     int* d_tbase = nullptr;     // per tile height (16, 8): nprob + 1 tile prefix sums
+    int* d_pbase = nullptr;     // nprob + 1 prefix sums of the flat pointwise chunks
+    int nchunks = 0;
     int ntiles_by[2] = {0, 0};
     int tma_variant = -1;       // -1: choose by timing at first use
     double tma_variant_us[TMA_NUM_VARIANTS] = {0, 0, 0, 0};
@@ -240,6 +242,7 @@ struct Engine {
         cudaFree(d_apply);
         cudaFree(d_maps);
         cudaFree(d_tbase);
+        cudaFree(d_pbase);
         cudaFree(d_err);
         cudaFree(d_adj);
     }
@@ -403,6 +406,25 @@ int build_engine(Engine* E, std::string& err) {
     }
     E->nprob = (int)E->probs.size();
     E->ntiles = tb;
+    {
+        // flat pointwise passes: PCHUNK elements of a problem's padded vector per block
+        std::vector<int> pb((size_t)E->nprob + 1, 0);
+        int acc = 0;
+        for (int p = 0; p < E->nprob; ++p) {
+            ProblemDev& P = E->probs[p];
+            const long long nel = (long long)P.nfields * P.field_stride;
+            P.pchunks = (int)((nel + PCHUNK - 1) / PCHUNK);
+            P.pchunk_base = acc;
+            pb[p] = acc;
+            acc += P.pchunks;
+        }
+        pb[E->nprob] = acc;
+        E->nchunks = acc;
+        cudaFree(E->d_pbase);
+        E->d_pbase = nullptr;
+        CUDA_OR_FAIL(err, cudaMalloc(&E->d_pbase, sizeof(int) * pb.size()));
+        CUDA_OR_FAIL(err, cudaMemcpy(E->d_pbase, pb.data(), sizeof(int) * pb.size(), cudaMemcpyHostToDevice));
+    }
     if (E->precision == EWV_F32 && E->dims == 2) {
         if (build_tensor_maps(E->probs, E->R, work_vecs, &E->d_maps) != 0)
             return fail(err, EWV_ERR_CUDA, "TMA tensor-map encoding failed");
@@ -456,7 +478,7 @@ int build_engine(Engine* E, std::string& err) {
     E->d_counters = nullptr;
     CUDA_OR_FAIL(err, cudaMalloc(&E->d_probs, sizeof(ProblemDev) * E->nprob));
     CUDA_OR_FAIL(err, cudaMalloc(&E->d_tile_prob, sizeof(int) * (size_t)tb));
-    CUDA_OR_FAIL(err, cudaMalloc(&E->d_partials, sizeof(double) * (size_t)tb));
+    CUDA_OR_FAIL(err, cudaMalloc(&E->d_partials, sizeof(double) * (size_t)std::max(tb, E->nchunks)));
     CUDA_OR_FAIL(err, cudaMalloc(&E->d_counters, sizeof(unsigned int) * E->nprob));
     CUDA_OR_FAIL(err, cudaMemcpy(E->d_probs, E->probs.data(), sizeof(ProblemDev) * E->nprob,
                                  cudaMemcpyHostToDevice));
@@ -573,7 +595,10 @@ struct Ctx {
         ++*launches;
     }
     void point(const PointArgs& pa) {
-        launch_point(E->precision, E->ntiles, E->d_probs, E->d_tile_prob, pa, s);
+        if (pa.mode <= 2)   // norm, MGS pass, combine: flat over the padded vectors
+            launch_point_flat(E->precision, E->nchunks, E->d_probs, E->d_pbase, E->nprob, pa, s);
+        else
+            launch_point(E->precision, E->ntiles, E->d_probs, E->d_tile_prob, pa, s);
         ++*launches;
     }
     // Tile-shape autotuner: time every persistent-kernel variant on an idempotent probe pass

@@ -26,6 +26,7 @@ constexpr int VX = BX / TPX;   // outputs per thread in x
 constexpr int VY = BY / TPY;   // outputs per thread in y
 
 constexpr int KC3 = 32;          // 3D: z planes per tile (a block marches down KC3 planes)
+constexpr int PCHUNK = 8192;     // elements per block of the flat pointwise passes
 
 constexpr int MAX_M = 48;        // Krylov dimension limit (EWV_MAX_KRYLOV_M)
 constexpr int MAX_DEG = 128;     // Faber degree limit
@@ -52,6 +53,7 @@ struct ProblemDev {
     int shot, pad_;       // shot index inside its model (per-shot caller arrays)
     int nz, nfields;      // 2D: 1 and 4 (u, v, w_x, w_y); 3D: nz and 5 (w_z added)
     int src_k, tiles_z;   // 3D: source plane, tiles along z (KC3 planes each); 2D: 0, 1
+    int pchunks, pchunk_base;   // flat pointwise passes: chunks of this problem's vector, first
     double beta0, inv_dx, inv_dx2, inv_pml;
     double f_peak, t0, amp;
     long long field_stride, vec_stride;
@@ -143,6 +145,10 @@ void launch_prologue(const ProblemDev* probs, int nprob, int kind, int m, double
 void launch_record(int precision, const ProblemDev* probs, int nprob, int vec, cudaStream_t s);
 void launch_point(int precision, int nblocks, const ProblemDev* probs, const int* tile_prob,
                   const PointArgs& pa, cudaStream_t s);
+// Flat pointwise passes (modes 0, 1, 2 of PointArgs) over whole padded vectors, PCHUNK
+// elements per block; pbase: nprob + 1 prefix sums of the problems' chunk counts.
+void launch_point_flat(int precision, int nchunks, const ProblemDev* probs, const int* pbase,
+                       int nprob, const PointArgs& pa, cudaStream_t s);
 void launch_inject(int precision, void* adj, long long vec_elems, const void* values,
                    const int* rec_off, const int* nrec, int nshots, int max_rec, cudaStream_t s);
 void launch_sum_shots(int precision, const void* in, void* out, long long n, int nshots,

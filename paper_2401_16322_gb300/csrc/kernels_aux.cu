@@ -301,6 +301,128 @@ point_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ tile_
     partial_and_finalize(P, pid, a, bsum, red, &s_last);
 }
 
+// ---------------------------------------------------------------- flat pointwise passes
+// Modes 0 (|q_1|^2), 1 (MGS pass) and 2 (Krylov combine) over whole padded vectors: every
+// pad element is zero in every vector, so the flat sums and updates equal the masked ones.
+// Block b handles elements [c PCHUNK, (c + 1) PCHUNK) of problem p, c = b - pbase[p], with
+// 16-byte vector loads; its partial dot product goes to slot b, and the problem's last block
+// sums the partials in a fixed order (deterministic, no waiting).
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+    using type = float4;
+    static constexpr int N = 4;
+};
+template <>
+struct Vec16<double> {
+    using type = double2;
+    static constexpr int N = 2;
+};
+
+template <typename V>
+__device__ __forceinline__ float dot16(const float4& a, const float4& b) {
+    return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, a.x * b.x)));
+}
+__device__ __forceinline__ double dot16d(const double2& a, const double2& b) {
+    return fma(a.y, b.y, a.x * b.x);
+}
+__device__ __forceinline__ float4 axpy16(const float4& w, float c, const float4& q) {
+    return make_float4(fmaf(-c, q.x, w.x), fmaf(-c, q.y, w.y), fmaf(-c, q.z, w.z), fmaf(-c, q.w, w.w));
+}
+__device__ __forceinline__ double2 axpy16(const double2& w, double c, const double2& q) {
+    return make_double2(fma(-c, q.x, w.x), fma(-c, q.y, w.y));
+}
+__device__ __forceinline__ void fma16(float4& acc, float c, const float4& q) {
+    acc.x = fmaf(c, q.x, acc.x);
+    acc.y = fmaf(c, q.y, acc.y);
+    acc.z = fmaf(c, q.z, acc.z);
+    acc.w = fmaf(c, q.w, acc.w);
+}
+__device__ __forceinline__ void fma16(double2& acc, double c, const double2& q) {
+    acc.x = fma(c, q.x, acc.x);
+    acc.y = fma(c, q.y, acc.y);
+}
+__device__ __forceinline__ double dotv(const float4& a, const float4& b) {
+    return (double)dot16<float4>(a, b);
+}
+__device__ __forceinline__ double dotv(const double2& a, const double2& b) { return dot16d(a, b); }
+
+__device__ __forceinline__ int flat_problem(const int* __restrict__ base, int nprob, int b) {
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(base + mid) <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+point_flat_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ pbase, int nprob,
+                  PointArgs pa) {
+    using V = typename Vec16<T>::type;
+    constexpr int NV = Vec16<T>::N;
+    __shared__ double red[NTHREADS / 32];
+    __shared__ int s_last;
+    __shared__ T s_coef[MAX_M];
+    const int pid = flat_problem(pbase, nprob, blockIdx.x);
+    const ProblemDev* P = probs + pid;
+    double* kry = P->kry;
+    if (pa.mode == 1 && kry[KRY_ACTIVE] == 0.0) return;
+    if (pa.mode == 2 && kry[KRY_NONFINITE] != 0.0) return;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nf = P->nfields == 5 ? 5 : 4;
+    const long long nelem = (long long)nf * P->field_stride;
+    const long long e0 = (long long)(blockIdx.x - __ldg(pbase + pid)) * PCHUNK;
+    const long long e1 = e0 + PCHUNK < nelem ? e0 + PCHUNK : nelem;
+    const long long q0 = e0 / NV, q1 = e1 / NV;
+    if (pa.mode == 2) {
+        // u^{n+1} = beta sum_{k=1}^{meff} e_k s_k q_k  (q_1 is the state itself)
+        const int meff = (int)kry[KRY_MEFF];
+        const double beta = kry[KRY_BETA];
+        for (int k = tid; k < meff; k += NTHREADS) s_coef[k] = (T)(beta * kry[KRY_E + k] * kry[KRY_S + k + 1]);
+        __syncthreads();
+        V* St = reinterpret_cast<V*>(vptr<T>(P, 0));
+        for (long long q = q0 + tid; q < q1; q += NTHREADS) {
+            V acc = {};
+            for (int k = 1; k <= meff; ++k) fma16(acc, s_coef[k - 1], reinterpret_cast<const V*>(vptr<T>(P, k - 1))[q]);
+            St[q] = acc;
+        }
+        return;
+    }
+    double accd = 0.0;
+    if (pa.mode == 0) {
+        const V* Q = reinterpret_cast<const V*>(vptr<T>(P, 0));
+        for (long long q = q0 + tid; q < q1; q += NTHREADS) {
+            const V a = Q[q];
+            accd += dotv(a, a);
+        }
+    } else {
+        V* W = reinterpret_cast<V*>(vptr<T>(P, pa.j));                  // slot j+1
+        const V* Qk = reinterpret_cast<const V*>(vptr<T>(P, pa.k - 1));   // slot k
+        const V* Qn = pa.k < pa.j ? reinterpret_cast<const V*>(vptr<T>(P, pa.k)) : nullptr;
+        const T coef = (T)(kry[KRY_H + (pa.k - 1) * MAX_M + (pa.j - 1)] * kry[KRY_S + pa.k]);
+        for (long long q = q0 + tid; q < q1; q += NTHREADS) {
+            const V w = axpy16(W[q], coef, Qk[q]);
+            W[q] = w;
+            accd += dotv(w, Qn ? Qn[q] : w);
+        }
+    }
+    if (pa.mode == 1 && pa.k == pa.j && pa.j == pa.m) return;   // h_{m+1,m} unused
+    const double bsum = block_sum_fixed(accd, red);
+    StageArgs a{};
+    a.fin_mode = pa.mode == 0 ? FIN_NORM0 : FIN_MGS;
+    a.fin_j = pa.j;
+    a.fin_k = pa.k;
+    a.m = pa.m;
+    a.tol = pa.tol;
+    a.partials = pa.partials;
+    a.counters = pa.counters;
+    partial_and_finalize_at(P, pid, a, bsum, red, &s_last, blockIdx.x, __ldg(pbase + pid), P->pchunks);
+}
+
 // ---------------------------------------------------------------- Hessenberg exponential
 // [13/13] Pade approximant with scaling and squaring (Higham 2005), FP64, one block per
 // problem; writes exp(H_meff) e_1 to kry[KRY_E..].  Shared memory: 7 matrices of meff^2.
@@ -533,6 +655,13 @@ void launch_point(int precision, int nblocks, const ProblemDev* probs, const int
     const dim3 block(TPX, TPY);
     if (precision == 0) point_kernel<float><<<nblocks, block, 0, s>>>(probs, tile_prob, pa);
     else point_kernel<double><<<nblocks, block, 0, s>>>(probs, tile_prob, pa);
+}
+void launch_point_flat(int precision, int nchunks, const ProblemDev* probs, const int* pbase,
+                       int nprob, const PointArgs& pa, cudaStream_t s) {
+    if (nchunks <= 0) return;
+    const dim3 block(TPX, TPY);
+    if (precision == 0) point_flat_kernel<float><<<nchunks, block, 0, s>>>(probs, pbase, nprob, pa);
+    else point_flat_kernel<double><<<nchunks, block, 0, s>>>(probs, pbase, nprob, pa);
 }
 int launch_expm(const ProblemDev* probs, int nprob, int mmax, cudaStream_t s) {
     const size_t smem = (size_t)7 * mmax * mmax * sizeof(double);

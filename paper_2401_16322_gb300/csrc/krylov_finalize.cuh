@@ -108,29 +108,38 @@ __device__ __forceinline__ double block_sum_fixed(double v, double* red) {
     return s;   // valid on thread 0
 }
 
-// Write this block's partial; if it is the last block of the problem, sum all partials in
-// a fixed order and finalise.  Must be called by all threads of the block.
-__device__ inline void partial_and_finalize(const ProblemDev* P, int pid, const StageArgs& a,
-                                            double block_partial_on_t0, double* red,
-                                            int* s_last) {
+// Write this block's partial into slot `slot`; if it is the last of the problem's `count`
+// blocks (slots base .. base + count - 1), sum all partials in a fixed order and finalise.
+// Must be called by all threads of the block.
+__device__ inline void partial_and_finalize_at(const ProblemDev* P, int pid, const StageArgs& a,
+                                               double block_partial_on_t0, double* red,
+                                               int* s_last, int slot, int base, int count) {
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     if (tid == 0) {
-        a.partials[blockIdx.x] = block_partial_on_t0;
+        a.partials[slot] = block_partial_on_t0;
         __threadfence();
         const unsigned int prev = atomicAdd(a.counters + pid, 1u);
-        *s_last = (prev == (unsigned int)(P->ntiles - 1));
+        *s_last = (prev == (unsigned int)(count - 1));
     }
     __syncthreads();
     if (!*s_last) return;
     __threadfence();
     double v = 0.0;
-    for (int t = tid; t < P->ntiles; t += NTHREADS) v += __ldcg(a.partials + P->tile_base + t);
+    for (int t = tid; t < count; t += NTHREADS) v += __ldcg(a.partials + base + t);
     const double tot = block_sum_fixed(v, red);
     if (tid == 0) {
         krylov_finalize(P, a.fin_mode, a.fin_j, a.fin_k, a.m, a.tol, tot);
         a.counters[pid] = 0u;
         __threadfence();
     }
+}
+
+// The tile-list form: one block per tile, slot = block index.
+__device__ inline void partial_and_finalize(const ProblemDev* P, int pid, const StageArgs& a,
+                                            double block_partial_on_t0, double* red,
+                                            int* s_last) {
+    partial_and_finalize_at(P, pid, a, block_partial_on_t0, red, s_last, blockIdx.x,
+                            P->tile_base, P->ntiles);
 }
 
 }  // namespace ewv
