@@ -628,6 +628,11 @@ def run_ours(args):
             "fp64_single_shot": extras.get("fp64_single_shot"),
             "fwi_gradient": extras.get("fwi_gradient"),
             "config5_3d": extras.get("config5_3d"),
+            "bf16_storage": ({"seismo_rel_err": study.bf16_err,
+                              "note": "every stored integrator vector rounded to bfloat16 "
+                                      "(round to nearest even) on the sampled problems, at the "
+                                      "cheapest FP32 (method, m, dt) by passes per unit time"}
+                             if study else None),
             "search_s": study.seconds if study else None,
             "reference_self_check": study.ref_self_check if study else None,
             "candidates": ([{"method": c.method, "m": c.m, "dt_ms": round(c.dt * 1e3, 4),

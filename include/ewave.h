@@ -189,6 +189,18 @@ int ewv_get_state(ewv_model_t model, int shot, double* host, size_t n);
 int ewv_pack_vector(ewv_model_t model, const double* host, size_t n, void* dev);
 int ewv_unpack_vector(ewv_model_t model, const void* dev, double* host, size_t n);
 
+/* Storage-precision experiment (the paper keeps every vector in its working precision; this
+ * is the library's own probe of bfloat16 storage).  With EWV_STORE_BF16 every value that a
+ * stencil pass stores (the integrator's Y and ACC vectors of Faber, HORK, RK3-2 and RK4-4
+ * steps) is rounded to the nearest bfloat16 (ties to even) and kept in the FP32 buffer, so
+ * the arithmetic sees exactly what a bfloat16 store and load would give.  The FP32 plain
+ * stencil kernel serves these passes (the TMA pipeline is not used), so the experiment
+ * measures accuracy, not speed.  Krylov's final combination and the leap-frog step are not
+ * rounded.  2D FP32 models only (UNSUPPORTED otherwise). */
+#define EWV_STORE_FP32 0
+#define EWV_STORE_BF16 1
+int ewv_set_storage_rounding(ewv_model_t model, int mode);
+
 /* ---- operator (Eq. 1, Secs. 2.1-2.2) ------------------------------------------------- */
 
 /* y = H x (transpose = 0) or y = H^T x (transpose = 1) for padded device vectors x, y of

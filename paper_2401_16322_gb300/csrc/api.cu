@@ -155,6 +155,7 @@ struct ewv_model {
     bool ellipse_override = false;
     double eg = 0, ec0 = 0, ec1 = 0;
     int lf_variant = EWV_LEAPFROG_AVERAGED;
+    int store_bf16 = 0;         // storage-precision experiment (ewv_set_storage_rounding)
     bool lf_history_valid = false;
     // device metadata
     int* d_rec = nullptr;
@@ -174,6 +175,7 @@ struct Engine {
     std::vector<long long> versions;
     std::vector<ProblemDev> probs;
     int nprob = 0, ntiles = 0, precision = 0, R = 4, dims = 2;
+    int store_bf16 = 0;         // any model of the engine asked for bfloat16 storage rounding
     ProblemDev* d_probs = nullptr;
     int* d_tile_prob = nullptr;
     double* d_partials = nullptr;
@@ -388,6 +390,8 @@ int build_engine(Engine* E, std::string& err) {
     E->drop_graphs();
     E->probs.clear();
     E->dims = E->models.empty() ? 2 : E->models[0]->d.dims;
+    E->store_bf16 = 0;
+    for (ewv_model* m : E->models) E->store_bf16 |= m->store_bf16;
     for (ewv_model* m : E->models)
         if (m->d.dims != E->dims) return fail(err, EWV_ERR_UNSUPPORTED, "a batch cannot mix 2D and 3D models");
     std::vector<int> work_vecs;
@@ -560,7 +564,9 @@ struct Ctx {
         }
         return E->events[E->events_used++];
     }
-    void stage(const StageArgs& a) {
+    void stage(const StageArgs& a_in) {
+        StageArgs a = a_in;
+        a.store_bf16 = E->store_bf16;
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         const unsigned rec_flags = capture_ev ? cudaEventRecordExternal : cudaEventRecordDefault;
         if (E->timing) {
@@ -579,7 +585,8 @@ struct Ctx {
             } else {
                 launch_stage3d(E->precision, E->R, E->ntiles, E->d_probs, E->d_tile_prob, a, s);
             }
-        } else if (E->precision == EWV_F32 && !a.transpose && a.fin_mode == FIN_NONE && a.d < 0 && !a.grad) {
+        } else if (E->precision == EWV_F32 && !a.transpose && a.fin_mode == FIN_NONE && a.d < 0 && !a.grad &&
+                   !a.store_bf16) {
             if (E->tma_variant < 0) autotune();
             if (E->tma_variant < 0) {
                 launch_failed = 1;
@@ -1538,6 +1545,15 @@ int ewv_step_leapfrog(ewv_model_t m, double t, double dt, int nsteps) {
 int ewv_set_leapfrog_variant(ewv_model_t m, int variant) {
     if (!m || (variant != EWV_LEAPFROG_AVERAGED && variant != EWV_LEAPFROG_LITERAL)) return EWV_ERR_INVALID_ARG;
     m->lf_variant = variant;
+    return EWV_OK;
+}
+
+int ewv_set_storage_rounding(ewv_model_t m, int mode) {
+    if (!m || (mode != EWV_STORE_FP32 && mode != EWV_STORE_BF16)) return EWV_ERR_INVALID_ARG;
+    if (mode == EWV_STORE_BF16 && (m->d.precision != EWV_F32 || m->d.dims != 2))
+        return fail(m->err, EWV_ERR_UNSUPPORTED, "bfloat16 storage rounding: 2D FP32 models only");
+    m->store_bf16 = mode == EWV_STORE_BF16 ? 1 : 0;
+    ++m->version;   // the engine picks the flag up on its next build
     return EWV_OK;
 }
 

@@ -87,6 +87,7 @@ struct StageArgs {
     void* grad;                      // gradient mode: grad += gscale q_v G(X), per-shot fields
     int gq;                          // vector index of q (its v field is read)
     double gscale;
+    int store_bf16;                  // 1: round every stored Y / ACC value to bfloat16 (RN)
 };
 
 // Arguments of the pointwise kernel (kernels_aux.cu).

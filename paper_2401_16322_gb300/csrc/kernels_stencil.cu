@@ -26,6 +26,8 @@
 //   Y   = cu U + ck K                               -> y_out
 //   ACC = ca A + cau U + cak K + cay Y + cax X      -> acc_out
 // and optionally a partial dot product <Y, D> (Krylov), finalised by the last block.
+#include <cuda_bf16.h>
+
 #include <type_traits>
 
 #include "ewave_internal.cuh"
@@ -84,6 +86,13 @@ __device__ __forceinline__ T damp(T beta0, T inv_pml, T d, int pml) {
     if (pml <= 0) return T(0);
     const T r = T(1) - d * inv_pml;
     return (d <= T(pml)) ? beta0 * r * r : T(0);
+}
+
+// Round to the nearest bfloat16 (ties to even) and widen back: the value that a bfloat16
+// store followed by a load would return.
+template <typename T>
+__device__ __forceinline__ T bf16_round(T v) {
+    return (T)__bfloat162float(__float2bfloat16_rn((float)v));
 }
 
 template <typename T>
@@ -388,11 +397,13 @@ stage_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ tile_
             for (int f = 0; f < 4; ++f) {
                 const bool pad = (f == 2 && i >= nx - 1) || (f == 3 && j >= ny - 1);
                 const T kf = cx * xs * xf[f] + ch * xs * hf[f];
-                const T yf = pad ? T(0) : (cu * pU[f][b][c] + ck * kf);
+                T yf = pad ? T(0) : (cu * pU[f][b][c] + ck * kf);
+                if (a.store_bf16) yf = bf16_round(yf);     // storage-precision experiment
                 if (Y) Y[f * fstr + o] = yf;
                 if (ACC) {
-                    const T af = ca * pA[f][b][c] + cau * pU[f][b][c] + cak * kf + cay * yf
-                                 + cax * xs * xf[f];
+                    T af = ca * pA[f][b][c] + cau * pU[f][b][c] + cak * kf + cay * yf
+                           + cax * xs * xf[f];
+                    if (a.store_bf16) af = bf16_round(af);
                     ACC[f * fstr + o] = pad ? T(0) : af;
                 }
                 if (D && !pad) {

@@ -38,7 +38,7 @@ EXPORTS = [
     "ewv_faber_step_noalloc", "ewv_adjoint_step", "ewv_adjoint_inject", "ewv_checkpoint_stride",
     "ewv_sum_shot_fields", "ewv_enable_graphs", "ewv_batch_enable_graphs",
     "ewv_set_kernel_variant", "ewv_kernel_variant", "ewv_batch_set_kernel_variant",
-    "ewv_batch_kernel_variant", "ewv_set_source_receivers3d",
+    "ewv_batch_kernel_variant", "ewv_set_source_receivers3d", "ewv_set_storage_rounding",
 ]
 
 
@@ -102,6 +102,7 @@ def load_library(path=LIB_PATH):
         "ewv_set_velocity": ([vp, dp, sz], i),
         "ewv_set_source_receivers": ([vp, i, d, d, d, d, d, i, dp, ip32, ip32], i),
         "ewv_set_source_receivers3d": ([vp, i, d, d, d, d, d, d, i, dp, ip32, ip32], i),
+        "ewv_set_storage_rounding": ([vp, i], i),
         "ewv_set_faber_ellipse": ([vp, d, d, d], i),
         "ewv_get_faber_ellipse": ([vp, dp, dp, dp], i),
         "ewv_set_state": ([vp, i, dp, sz], i),
@@ -258,6 +259,10 @@ class Model:
             si.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
             ri.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))), "set_source_receivers3d")
         return si, ri[:3 * nrec].reshape(nrec, 3)
+
+    def set_storage_rounding(self, bf16):
+        """Round every stored integrator vector to bfloat16 (storage-precision experiment)."""
+        self._check(self.lib.ewv_set_storage_rounding(self.h, 1 if bf16 else 0), "storage_rounding")
 
     def set_faber_ellipse(self, gamma, c0, c1):
         self._check(self.lib.ewv_set_faber_ellipse(self.h, gamma, c0, c1))

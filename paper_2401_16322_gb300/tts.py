@@ -144,6 +144,7 @@ class Study:
     leapfrog: Optional[Candidate] = None          # FP32 leap-frog (None: never reaches target)
     leapfrog_f64: Optional[Candidate] = None
     ref_self_check: float = float("nan")
+    bf16_err: float = float("nan")             # selected candidate with bfloat16 storage
     seconds: float = 0.0
 
 
@@ -254,6 +255,18 @@ def run_study(workloads: List[Workload], picks, T, target=1e-4, plan=SCAN_PLAN,
                 + f" ({time.time() - t_start:.1f} s)")
     lf = []
     scan(cand_models, cand_batch, "leapfrog", 1, LEAPFROG_DIVISORS, lambda k: dt_cfl / k, lf)
+    # storage-precision experiment: the best passing FP32 (method, m, dt) on the sampled
+    # problems, with every stored vector rounded to bfloat16
+    passing_s = [c for c in cands if c.err <= target and c.method != "krylov"]
+    if passing_s:
+        best = min(passing_s, key=lambda c: c.m / c.dt)
+        for md in cand_models:
+            md.set_storage_rounding(True)
+        probe = Candidate(best.method, best.m, best.dt)
+        st.bf16_err = _eval_candidate(cand_models, cand_batch, refs, sw, probe, T, dt_ref, log)
+        for md in cand_models:
+            md.set_storage_rounding(False)
+        log(f"  bfloat16 storage, {probe.label()}: error {st.bf16_err:.3e}")
     cand_batch.close()
     for md in cand_models:
         md.close()

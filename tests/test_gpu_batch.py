@@ -135,3 +135,28 @@ def test_autotuner_picks_a_timed_variant():
     times = info["probe_us"]
     assert all(t > 0 for t in times)
     assert times[info["variant"]] == min(times)
+
+
+def test_bf16_storage_rounding_stores_bf16_values():
+    """Storage-precision experiment: after HORK steps with bfloat16 storage rounding every
+    stored value has a zero low half (exactly representable in bfloat16), and the result
+    stays within the bfloat16 error bound of the FP32 run."""
+    from paper_2401_16322_gb300.ewave import EwaveError
+    oms, gms, _ = _models("f32", 1)
+    om, g = oms[0], gms[0]
+    U0 = smooth_random_state([f.shape for f in om.zeros_state()], 31)
+    out = []
+    for bf16 in (False, True):
+        g.set_storage_rounding(bf16)
+        g.set_state(0, flatten(U0))
+        g.step("hork", 0.04, 1.0e-3, 8, 3)
+        out.append(g.get_state(0))
+    bits = out[1].astype(np.float32).view(np.uint32)
+    assert np.all((bits & 0xFFFF) == 0)
+    # 24 rounded passes, unit round-off 2^-8 each: a linear bound
+    assert 1e-5 < rel_l2(out[1], out[0]) < 24 * 2.0 ** -8
+    from paper_2401_16322_gb300 import Model
+    m64 = Model(om.nx, om.ny, om.dx, om.order, om.pml, om.beta0, om.free_surface, precision="f64")
+    with pytest.raises(EwaveError, match="UNSUPPORTED"):
+        m64.set_storage_rounding(True)
+    m64.close()
