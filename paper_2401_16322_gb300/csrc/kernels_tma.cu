@@ -50,13 +50,25 @@ struct StageLayout {
 };
 
 // What the producer resolves once per tile and hands to the consumers with the stage.
-struct TileInfo {
+struct __align__(16) TileInfo {
     float* Y;
     float* A;
     long long fstr;
     int x0, y0, nx, ny, pitch, pml, fs, src_i, src_j, pad0;
     float beta0, inv_pml, idx1, idx2, sig, pad1;
 };
+
+// The consumers read a stage's TileInfo with 16-byte shared loads into registers.
+__device__ __forceinline__ TileInfo load_info(const TileInfo* p) {
+    static_assert(sizeof(TileInfo) % 16 == 0, "TileInfo must be a whole number of 16-byte words");
+    union {
+        TileInfo t;
+        int4 v[sizeof(TileInfo) / 16];
+    } u;
+#pragma unroll
+    for (int q = 0; q < (int)(sizeof(TileInfo) / 16); ++q) u.v[q] = reinterpret_cast<const int4*>(p)[q];
+    return u.t;
+}
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -145,6 +157,25 @@ __device__ __forceinline__ float cent(int k) {
         return k == 0 ? float(-5.0 / 2.0) : k == 1 ? float(4.0 / 3.0) : float(-1.0 / 12.0);
     }
 }
+// Stencil sums as balanced trees (short dependency chains for the issue slots):
+// stag_tree = sum_k s_k d[k] over the R staggered differences, cent_tree = c_0 u +
+// sum_k c_k p[k-1] over the R symmetric pair sums.
+template <int R>
+__device__ __forceinline__ float stag_tree(const float (&d)[R]) {
+    if constexpr (R == 4)
+        return fmaf(stag<4>(0), d[0], stag<4>(1) * d[1]) + fmaf(stag<4>(2), d[2], stag<4>(3) * d[3]);
+    else
+        return fmaf(stag<R>(0), d[0], stag<R>(1) * d[1]);
+}
+template <int R>
+__device__ __forceinline__ float cent_tree(float u, const float (&p)[R]) {
+    if constexpr (R == 4)
+        return (fmaf(cent<4>(1), p[0], cent<4>(0) * u) + fmaf(cent<4>(3), p[2], cent<4>(2) * p[1])) +
+               cent<4>(4) * p[3];
+    else
+        return fmaf(cent<R>(1), p[0], cent<R>(0) * u) + cent<R>(2) * p[1];
+}
+
 __device__ __forceinline__ float dampf(float beta0, float inv_pml, float d, int pml) {
     if (pml <= 0) return 0.f;
     const float r = 1.f - d * inv_pml;
@@ -167,7 +198,9 @@ __device__ __forceinline__ int find_problem(const int* __restrict__ base, int np
     return lo;
 }
 
-template <int R, int BYv, int NW, int NSTv>
+// EPI 0: the general epilogue.  EPI 1: the steady-state form of the Faber and HORK passes,
+// ck = 1 and cau = cak = cax = 0:  Y = cu U + cx X + ch (H X + sigma),  ACC = ca A + cay Y.
+template <int R, int BYv, int NW, int NSTv, int EPI>
 __global__ void __launch_bounds__(NW * 32 + 32, 1)
 stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ tbase, int nprob,
                  int ntiles, int mapset, StageArgs a, int* err) {
@@ -274,7 +307,7 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
                 s_err = 1;
                 break;
             }
-            const TileInfo& ti = info[s];
+            const TileInfo ti = load_info(&info[s]);
             const int nx = ti.nx, ny = ti.ny, pml = ti.pml;
             const bool fs = ti.fs != 0;
             const int y0 = ti.y0;
@@ -306,15 +339,16 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
                 const int j = y0 + ly;
                 const float* urow = su + (ly + R) * L::SW + cxs;
                 const float* wxrow = swx + ly * L::SW + cxs;
-                float uxx = cent<R>(0) * ucol[r + R];
-                float dux = 0.f;
+                float px[R], dx[R], dw[R];
 #pragma unroll
-                for (int k = 1; k <= R; ++k) uxx += cent<R>(k) * (urow[k] + urow[-k]);
-#pragma unroll
-                for (int k = 0; k < R; ++k) dux += stag<R>(k) * (urow[1 + k] - urow[-k]);
-                float dwx = 0.f;
-#pragma unroll
-                for (int k = 0; k < R; ++k) dwx += stag<R>(k) * (wxrow[k] - wxrow[-1 - k]);
+                for (int k = 0; k < R; ++k) {
+                    px[k] = urow[k + 1] + urow[-k - 1];
+                    dx[k] = urow[1 + k] - urow[-k];
+                    dw[k] = wxrow[k] - wxrow[-1 - k];
+                }
+                const float uxx = cent_tree<R>(ucol[r + R], px);
+                const float dux = stag_tree<R>(dx);
+                const float dwx = stag_tree<R>(dw);
                 float uyy, duy, dwy;
                 if (fs && j < 4) {
                     uyy = 0.f;
@@ -324,21 +358,24 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
 #pragma unroll
                     for (int q = 0; q < 8; ++q) dwy += g_tma_fs[TFS_DWY + j * 8 + q] * swy[(q + R) * BX + tx];
                 } else {
-                    uyy = cent<R>(0) * ucol[r + R];
+                    float py[R], dwv[R];
 #pragma unroll
-                    for (int k = 1; k <= R; ++k) uyy += cent<R>(k) * (ucol[r + R + k] + ucol[r + R - k]);
-                    dwy = 0.f;
-#pragma unroll
-                    for (int k = 0; k < R; ++k) dwy += stag<R>(k) * (wcol[r + R - 1 - k] - wcol[r + R + k]);
+                    for (int k = 0; k < R; ++k) {
+                        py[k] = ucol[r + R + k + 1] + ucol[r + R - k - 1];
+                        dwv[k] = wcol[r + R - 1 - k] - wcol[r + R + k];
+                    }
+                    uyy = cent_tree<R>(ucol[r + R], py);
+                    dwy = stag_tree<R>(dwv);
                 }
                 if (fs && j < 3) {
                     duy = 0.f;
 #pragma unroll
                     for (int q = 0; q < 8; ++q) duy += g_tma_fs[TFS_UY + j * 8 + q] * su[(q + R) * L::SW + cxs];
                 } else {
-                    duy = 0.f;
+                    float dy[R];
 #pragma unroll
-                    for (int k = 0; k < R; ++k) duy += stag<R>(k) * (ucol[r + R - k] - ucol[r + R + 1 + k]);
+                    for (int k = 0; k < R; ++k) dy[k] = ucol[r + R - k] - ucol[r + R + 1 + k];
+                    duy = stag_tree<R>(dy);
                 }
                 if (!in_x || j >= ny) continue;
                 const float byn = dampf(beta0, inv_pml, fs ? (float)(ny - j) : (float)min(j + 1, ny - j), pml);
@@ -362,10 +399,16 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
                     const bool pad = (f == 2 && i >= nx - 1) || (f == 3 && j >= ny - 1);
                     const float uval = has_u ? spu[f * BYv * BX + pt] : 0.f;
                     const float aval = has_a ? spa[f * BYv * BX + pt] : 0.f;
-                    const float kf = cxf * xf[f] + chf * hf[f];
-                    const float yf = pad ? 0.f : (cuf * uval + ckf * kf);
-                    if (yrow) yrow[f * fstr] = yf;
-                    if (arow) arow[f * fstr] = pad ? 0.f : (caf * aval + cauf * uval + cakf * kf + cayf * yf + caxf * xf[f]);
+                    const float kf = fmaf(cxf, xf[f], chf * hf[f]);
+                    if constexpr (EPI == 1) {
+                        const float yf = pad ? 0.f : (has_u ? fmaf(cuf, uval, kf) : kf);
+                        if (yrow) yrow[f * fstr] = yf;
+                        if (arow) arow[f * fstr] = has_a ? fmaf(cayf, yf, caf * aval) : cayf * yf;
+                    } else {
+                        const float yf = pad ? 0.f : (cuf * uval + ckf * kf);
+                        if (yrow) yrow[f * fstr] = yf;
+                        if (arow) arow[f * fstr] = pad ? 0.f : (caf * aval + cauf * uval + cakf * kf + cayf * yf + caxf * xf[f]);
+                    }
                 }
             }
             __syncwarp();
@@ -478,7 +521,7 @@ void tma_variant_describe(int v, int* by, int* nw, int* nst) {
 
 static int g_num_sms = 0;
 
-template <int R, int BYv, int NW, int NSTv>
+template <int R, int BYv, int NW, int NSTv, int EPI>
 static int launch_variant(const ProblemDev* probs, const int* tbase, int nprob, int ntiles,
                           const StageArgs& a, int* err, cudaStream_t s) {
     const size_t smem = (size_t)NSTv * StageLayout<R, BYv>::BYTES + 1024;
@@ -487,13 +530,13 @@ static int launch_variant(const ProblemDev* probs, const int* tbase, int nprob, 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return -1;
     if (!(configured >> dev & 1ull)) {
-        if (cudaFuncSetAttribute(stage_tma_kernel<R, BYv, NW, NSTv>,
+        if (cudaFuncSetAttribute(stage_tma_kernel<R, BYv, NW, NSTv, EPI>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return -1;
         configured |= 1ull << dev;
     }
     const int grid = ntiles < g_num_sms ? ntiles : g_num_sms;
-    stage_tma_kernel<R, BYv, NW, NSTv><<<grid, NW * 32 + 32, smem, s>>>(
+    stage_tma_kernel<R, BYv, NW, NSTv, EPI><<<grid, NW * 32 + 32, smem, s>>>(
         probs, tbase, nprob, ntiles, BYv == 16 ? 0 : 1, a, err);
     return 0;
 }
@@ -507,8 +550,12 @@ int launch_stage_tma(int variant, int R, const ProblemDev* probs, const int* tba
         cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
         if (g_num_sms <= 0) g_num_sms = 1;
     }
+    // the steady-state Faber / HORK form: Y = cu U + cx X + ch H, ACC = ca A + cay Y
+    const bool epi = a.ck == 1.0 && a.cau == 0.0 && a.cak == 0.0 && a.cax == 0.0;
 #define EWV_TMA_CASE(V, RR, BYV, NWV, NSTV) \
-    if (variant == V && R == RR) return launch_variant<RR, BYV, NWV, NSTV>(probs, tbase, nprob, ntiles, a, err, s);
+    if (variant == V && R == RR)                                                                \
+        return epi ? launch_variant<RR, BYV, NWV, NSTV, 1>(probs, tbase, nprob, ntiles, a, err, s) \
+                   : launch_variant<RR, BYV, NWV, NSTV, 0>(probs, tbase, nprob, ntiles, a, err, s);
     EWV_TMA_CASE(0, 4, 16, 16, 3)
     EWV_TMA_CASE(1, 4, 16, 8, 3)
     EWV_TMA_CASE(2, 4, 8, 8, 5)

@@ -57,7 +57,7 @@ struct Stage3 {
                   "TMA destinations must be 128-byte aligned");
 };
 
-struct Info3 {
+struct __align__(16) Info3 {
     float* Y;
     float* A;
     const float* X;          // u field of the input vector (free-surface column taps)
@@ -145,6 +145,24 @@ __device__ __forceinline__ float ce3(int k) {
         return k == 0 ? float(-5.0 / 2.0) : k == 1 ? float(4.0 / 3.0) : float(-1.0 / 12.0);
     }
 }
+// Stencil sums as balanced trees (short dependency chains): st_tree = sum_k s_k d[k] over the
+// R staggered differences, ce_tree = c_0 u + sum_k c_k p[k-1] over the R symmetric pair sums.
+template <int R>
+__device__ __forceinline__ float st_tree(const float (&d)[R]) {
+    if constexpr (R == 4)
+        return fmaf(st3<4>(0), d[0], st3<4>(1) * d[1]) + fmaf(st3<4>(2), d[2], st3<4>(3) * d[3]);
+    else
+        return fmaf(st3<R>(0), d[0], st3<R>(1) * d[1]);
+}
+template <int R>
+__device__ __forceinline__ float ce_tree(float u, const float (&p)[R]) {
+    if constexpr (R == 4)
+        return (fmaf(ce3<4>(1), p[0], ce3<4>(0) * u) + fmaf(ce3<4>(3), p[2], ce3<4>(2) * p[1])) +
+               ce3<4>(4) * p[3];
+    else
+        return fmaf(ce3<R>(1), p[0], ce3<R>(0) * u) + ce3<R>(2) * p[1];
+}
+
 __device__ __forceinline__ float dmp(float beta0, float inv_pml, float d, int pml) {
     if (pml <= 0) return 0.f;
     const float r = 1.f - d * inv_pml;
@@ -322,7 +340,7 @@ stage_tma3d_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__
                     stop = true;
                     break;
                 }
-                const Info3& ti = info[s];
+                const Info3& ti = info[s];   // field loads on use (a register copy would spill)
                 const float* st = smem + (size_t)s * L::FLOATS;
                 // push the front values into the queues
 #pragma unroll
@@ -358,20 +376,19 @@ stage_tma3d_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__
                         const float* urow = su + (ly + R) * L::SW + cxs;
                         const float* wxrow = swx + ly * L::SW + cxs;
                         const float u = uq[r][R];
-                        float uxx = ce3<R>(0) * u, uyy = ce3<R>(0) * u;
-                        float dux = 0.f, duy = 0.f, dwx = 0.f, dwy = 0.f;
-#pragma unroll
-                        for (int q = 1; q <= R; ++q) {
-                            uxx += ce3<R>(q) * (urow[q] + urow[-q]);
-                            uyy += ce3<R>(q) * (urow[q * L::SW] + urow[-q * L::SW]);
-                        }
+                        float px[R], py[R], dx[R], dy[R], dwxv[R], dwyv[R];
 #pragma unroll
                         for (int q = 0; q < R; ++q) {
-                            dux += st3<R>(q) * (urow[1 + q] - urow[-q]);
-                            duy += st3<R>(q) * (urow[(1 + q) * L::SW] - urow[-q * L::SW]);
-                            dwx += st3<R>(q) * (wxrow[q] - wxrow[-1 - q]);
-                            dwy += st3<R>(q) * (swy[(ly + R + q) * BX + tx] - swy[(ly + R - 1 - q) * BX + tx]);
+                            px[q] = urow[q + 1] + urow[-q - 1];
+                            py[q] = urow[(q + 1) * L::SW] + urow[-(q + 1) * L::SW];
+                            dx[q] = urow[1 + q] - urow[-q];
+                            dy[q] = urow[(1 + q) * L::SW] - urow[-q * L::SW];
+                            dwxv[q] = wxrow[q] - wxrow[-1 - q];
+                            dwyv[q] = swy[(ly + R + q) * BX + tx] - swy[(ly + R - 1 - q) * BX + tx];
                         }
+                        const float uxx = ce_tree<R>(u, px), uyy = ce_tree<R>(u, py);
+                        const float dux = st_tree<R>(dx), duy = st_tree<R>(dy);
+                        const float dwx = st_tree<R>(dwxv), dwy = st_tree<R>(dwyv);
                         float uzz, dwz, duz;
                         const long long oc = (long long)j * ti.pitch + i;
                         if (fs && c < 4) {
@@ -386,12 +403,14 @@ stage_tma3d_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__
                             for (int q = 0; q < 8; ++q)
                                 dwz += g3t_fs[T3_DWZ + c * 8 + q] * (q < nz - 1 ? __ldg(wcol + q * ps) : 0.f);
                         } else {
-                            uzz = ce3<R>(0) * u;
+                            float pz[R], dwzv[R];
 #pragma unroll
-                            for (int q = 1; q <= R; ++q) uzz += ce3<R>(q) * (uq[r][R + q] + uq[r][R - q]);
-                            dwz = 0.f;
-#pragma unroll
-                            for (int q = 0; q < R; ++q) dwz += st3<R>(q) * (wq[r][R - 1 - q] - wq[r][R + q]);
+                            for (int q = 0; q < R; ++q) {
+                                pz[q] = uq[r][R + q + 1] + uq[r][R - q - 1];
+                                dwzv[q] = wq[r][R - 1 - q] - wq[r][R + q];
+                            }
+                            uzz = ce_tree<R>(u, pz);
+                            dwz = st_tree<R>(dwzv);
                         }
                         if (fs && c < 3) {
                             const float* ucol = ti.X + oc;
@@ -400,9 +419,10 @@ stage_tma3d_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__
                             for (int q = 0; q < 8; ++q)
                                 duz += g3t_fs[T3_UZ + c * 8 + q] * (q < nz ? __ldg(ucol + q * ps) : 0.f);
                         } else {
-                            duz = 0.f;
+                            float dz[R];
 #pragma unroll
-                            for (int q = 0; q < R; ++q) duz += st3<R>(q) * (uq[r][R - q] - uq[r][R + 1 + q]);
+                            for (int q = 0; q < R; ++q) dz[q] = uq[r][R - q] - uq[r][R + 1 + q];
+                            duz = st_tree<R>(dz);
                         }
                         const float byn = dmp(beta0, inv_pml, (float)min(j + 1, ny - j), pml);
                         const float byh = dmp(beta0, inv_pml, fminf((float)j + 1.5f, (float)(ny - j) - 0.5f), pml);
