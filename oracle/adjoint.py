@@ -20,10 +20,20 @@ HORK (Sec. 3.2) is handled the same way: u^{n+1} = sum_i w_i k_i, k_i = (I + dt 
 with w_i the lambda weights; r_m = w_m ybar, r_{i-1} = w_{i-1} ybar + (I + dt H)^T r_i and
 dJ/dm += dt sum_i r_{i,v} G(k_{i-1}).
 
+Krylov (Sec. 3.2) is not linear in u^n (the Arnoldi basis depends on it), so its adjoint is
+the step-level linearisation of U^{n+1} = [I 0] exp(dt H~) [U^n; e_p] (the reading of the
+Krylov row of the FWI gradient): the cotangent of U^n is exp(dt H)^T ybar, computed by
+Arnoldi on dt H^T from ybar; the m-gradient is the Frechet integral
+    dJ/dm += int_0^dt [exp((dt - s) H)^T ybar]_v  G(x(s)) ds,   x(s) = [I 0] exp(s H~)[U^n; e_p],
+evaluated by 4-point Gauss-Legendre on [0, dt], with x(s) and the adjoint states taken as
+dense output of the forward and adjoint Arnoldi bases (exp(tau A) x ~ |x| V exp(tau H_m) e_1).
+
 This route is independent of the CUDA path: B^T uses the transposed sparse matrix of
 ``oracle.operator.assemble_H``.  Pins: tests/test_oracle_adjoint.py (dot-product identity
 of one adjoint step; central finite differences of J along seeded directions).
 """
+import math
+
 import numpy as np
 
 from .faber import faber_coefficients
@@ -141,6 +151,57 @@ def hork_adjoint_step(model, U_prev_flat, ybar, src, t_n, dt, m, HT=None):
     return r, grad
 
 
+def gauss_legendre4():
+    """Nodes and weights of the 4-point Gauss-Legendre rule on [0, 1] (exact for degree 7):
+    nodes (1 +- sqrt(3/7 -+ (2/7) sqrt(6/5))) / 2, weights (18 +- sqrt(30)) / 72."""
+    a = math.sqrt(3.0 / 7.0 - 2.0 / 7.0 * math.sqrt(6.0 / 5.0))
+    b = math.sqrt(3.0 / 7.0 + 2.0 / 7.0 * math.sqrt(6.0 / 5.0))
+    wa, wb = (18.0 + math.sqrt(30.0)) / 36.0, (18.0 - math.sqrt(30.0)) / 36.0
+    x = np.array([-b, -a, a, b])
+    w = np.array([wb, wa, wa, wb])
+    return (1.0 + x) / 2.0, w / 2.0
+
+
+def krylov_adjoint_step(model, U_prev_flat, ybar, src, t_n, dt, m, HT=None):
+    """Cotangent of U^{n-1} and the m-gradient of one Krylov step (linearised, see the module
+    header).  Returns (exp(dt H)^T ybar by Arnoldi, grad [ny*nx])."""
+    from .krylov import arnoldi, expm
+    nU = model.n
+    nu = model.nx * model.ny
+    if HT is None:
+        HT = assemble_H(model).T.tocsr()
+    # forward Arnoldi on dt H~ from [U; eta e_p], W / eta (as krylov_step)
+    p = src.p if src is not None else 1
+    w = src.W(t_n, dt) if src is not None else np.zeros(p)
+    eta = float(np.linalg.norm(U_prev_flat))
+    eta = eta if eta > 0.0 else 1.0
+    w = w / eta
+
+    def matvec(x):
+        Ux = unflatten(model, x[:nU])
+        val = float(np.dot(w, x[nU:]))
+        HU = apply_H(model, Ux, None if src is None else (*src.node, val))
+        return dt * np.concatenate([flatten(HU), tail_apply(x[nU:], dt)])
+
+    y0 = np.zeros(p)
+    y0[-1] = eta
+    beta, V, Hm, _ = arnoldi(matvec, np.concatenate([U_prev_flat, y0]), m)
+    # adjoint Arnoldi on dt H^T from ybar
+    beta_t, Vt, Ht, _ = arnoldi(lambda y: dt * (HT @ y), ybar, m)
+
+    def fwd(tau):
+        return beta * (V[:nU] @ expm(tau * Hm)[:, 0]) if beta > 0.0 else np.zeros(nU)
+
+    def adj(sig):
+        return beta_t * (Vt @ expm(sig * Ht)[:, 0]) if beta_t > 0.0 else np.zeros(nU)
+
+    taus, wts = gauss_legendre4()
+    grad = np.zeros(nu)
+    for tau, wq in zip(taus, wts):
+        grad += dt * wq * adj(1.0 - tau)[nu:2 * nu] * G_of(model, fwd(tau))
+    return adj(1.0), grad
+
+
 def faber_forward(model, shots, dt, nsteps, m, params, U0=None, method="faber"):
     """Forward simulation of every shot; returns (states per shot [N+1 flat], seismograms)."""
     states, seis = [], []
@@ -151,6 +212,9 @@ def faber_forward(model, shots, dt, nsteps, m, params, U0=None, method="faber"):
         for n in range(nsteps):
             if method == "faber":
                 _, U = faber_tape(model, U, src, n * dt, dt, m, params)
+            elif method == "krylov":
+                from .krylov import krylov_step
+                U = flatten(krylov_step(model, unflatten(model, U), src, n * dt, dt, m))
             else:
                 _, U = hork_tape(model, U, src, n * dt, dt, m)
             Us.append(U)
@@ -178,6 +242,8 @@ def fwi_gradient(model, shots, d_obs, dt, nsteps, m, params, method="faber"):
         for n in range(nsteps, 0, -1):
             if method == "faber":
                 q0, g = faber_adjoint_step(model, Us[n - 1], lam, src, (n - 1) * dt, dt, m, params, HT)
+            elif method == "krylov":
+                q0, g = krylov_adjoint_step(model, Us[n - 1], lam, src, (n - 1) * dt, dt, m, HT)
             else:
                 q0, g = hork_adjoint_step(model, Us[n - 1], lam, src, (n - 1) * dt, dt, m, HT)
             grad += g

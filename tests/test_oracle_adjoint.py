@@ -76,3 +76,93 @@ def test_fwi_gradient_matches_central_differences(method, dt, deg):
         fd = (Jp - Jm) / (2 * eps)
         an = float(np.sum(grad * dm))
         assert abs(fd - an) <= 1e-6 * abs(fd), (seed, fd, an)
+
+
+def test_gauss_legendre4_exact_to_degree_7():
+    from oracle.adjoint import gauss_legendre4
+    t, w = gauss_legendre4()
+    for k in range(8):
+        assert abs(float(np.sum(w * t ** k)) - 1.0 / (k + 1)) < 1e-15
+    assert abs(float(np.sum(w * t ** 8)) - 1.0 / 9.0) > 1e-8     # and not beyond
+
+
+def _tiny_krylov_model():
+    nx, ny, pml = 9, 7, 3
+    c = layered(nx, ny, 17, vmin=1500, vmax=3000)
+    return Model(nx, ny, DX, 8, pml, default_beta0(3000.0, pml, DX), True, c), c
+
+
+def test_krylov_adjoint_transport_is_the_exponential_transpose():
+    """With a full-dimension basis the adjoint transport is exp(dt H)^T ybar exactly."""
+    import scipy.linalg as sl
+    from oracle.adjoint import krylov_adjoint_step
+    from oracle.operator import assemble_H
+    m, _ = _tiny_krylov_model()
+    ybar = flatten(smooth_random_state([f.shape for f in m.zeros_state()], 11))
+    U = flatten(smooth_random_state([f.shape for f in m.zeros_state()], 12))
+    dt = 4e-4
+    lam, _ = krylov_adjoint_step(m, U, ybar, None, 0.0, dt, m.n + 1)
+    H = assemble_H(m).toarray()
+    want = sl.expm(dt * H).T @ ybar
+    assert np.linalg.norm(lam - want) <= 1e-10 * np.linalg.norm(want)
+
+
+def test_krylov_gradient_is_the_frechet_derivative():
+    """<grad, dm> equals the exact Frechet derivative of <ybar, [I 0] exp(dt H~(m)) [U; e_p]>
+    along dm (Van Loan's block exponential), to the accuracy of 4-point Gauss-Legendre."""
+    import scipy.linalg as sl
+    from oracle.adjoint import krylov_adjoint_step
+    from oracle.operator import assemble_H
+    m, c = _tiny_krylov_model()
+    src = PointSource(m, 4 * DX, 2 * DX, 40.0, 0.02, amp=1e3, p=6)
+    U = flatten(smooth_random_state([f.shape for f in m.zeros_state()], 13))
+    ybar = flatten(smooth_random_state([f.shape for f in m.zeros_state()], 14))
+    dt, t = 3e-4, 0.01
+    n, p = m.n, src.p
+    _, grad = krylov_adjoint_step(m, U, ybar, src, t, dt, n + p)
+    dm = smooth_random_state([(m.ny, m.nx)], 15, sigma_cells=1.5)[0] * 0.1 * c ** 2
+    m2 = Model(m.nx, m.ny, DX, 8, m.pml, m.beta0, True, np.sqrt(c ** 2 + dm))
+    E = (assemble_H(m2) - assemble_H(m)).toarray()      # H~ is affine in c^2
+
+    def aug(H):
+        A = np.zeros((n + p, n + p))
+        A[:n, :n] = H
+        nxy = m.nx * m.ny
+        A[nxy + src.j * m.nx + src.i, n:] = src.W(t, dt)
+        for k in range(p - 1):
+            A[n + k, n + k + 1] = 1.0 / dt
+        return A
+
+    A = dt * aug(assemble_H(m).toarray())
+    Ed = np.zeros_like(A)
+    Ed[:n, :n] = dt * E
+    big = np.zeros((2 * (n + p), 2 * (n + p)))
+    big[:n + p, :n + p] = A
+    big[:n + p, n + p:] = Ed
+    big[n + p:, n + p:] = A
+    L = sl.expm(big)[:n + p, n + p:]
+    x = np.concatenate([U, np.eye(p)[-1]])
+    exact = float(ybar @ (L @ x)[:n])
+    got = float(np.sum(grad * dm.ravel()))
+    assert abs(got - exact) <= 1e-6 * abs(exact), (got, exact)
+
+
+def test_krylov_fwi_gradient_matches_central_differences():
+    """The linearised Krylov gradient agrees with central differences of the Krylov
+    forward to the step's time accuracy (the acceptance level of the FWI gradient)."""
+    c_true, c0, beta0, params = _setup()
+    dt, deg, nsteps = 1e-3, 14, 10
+    mt = _model(c_true, beta0)
+    _, d_obs = faber_forward(mt, _shots(mt), dt, nsteps, deg, params, method="krylov")
+    m0 = _model(c0, beta0)
+    J0, grad = fwi_gradient(m0, _shots(m0), d_obs, dt, nsteps, deg, params, method="krylov")
+    c2 = c0 ** 2
+    for seed in (5, 6):
+        dm = smooth_random_state([(NY, NX)], seed, sigma_cells=2.0)[0] * 0.01 * c2
+        eps = 1e-3
+        mp, mm = _model(np.sqrt(c2 + eps * dm), beta0), _model(np.sqrt(c2 - eps * dm), beta0)
+        Jp = misfit(faber_forward(mp, _shots(mp), dt, nsteps, deg, params, method="krylov")[1], d_obs)
+        Jm = misfit(faber_forward(mm, _shots(mm), dt, nsteps, deg, params, method="krylov")[1], d_obs)
+        fd = (Jp - Jm) / (2 * eps)
+        an = float(np.sum(grad * dm))
+        assert abs(fd - an) <= 1e-3 * abs(fd), (seed, fd, an)
