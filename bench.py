@@ -236,14 +236,14 @@ def fp64_single_shot_estimate(wl, method, m, dt, nsteps, c_max, steps_sample=3):
 
 def fwi_gradient_step(method, m, dt_over_cfl):
     """FWI gradient (forward + adjoint) on the 401 x 201, 16-shot, 200-receiver workload,
-    FP32, with the selected integrator (Faber or HORK: the two with a discrete adjoint) at its
-    m and step ratio; every state checkpointed."""
+    FP32, with the given integrator (Faber, HORK: exact discrete adjoints; Krylov: adjoint of
+    the step's exponential) at its m and step ratio; every state checkpointed."""
     import numpy as np
     import torch
     from paper_2401_16322_gb300.fwi import FaberFWI
     from paper_2401_16322_gb300.tts import build_models, common_ellipse, leapfrog_step
     from paper_2401_16322_gb300.workloads import config_fwi, smooth_gradient_with_anomalies
-    if method not in ("faber", "hork"):
+    if method not in ("faber", "hork", "krylov"):
         return None
     w = config_fwi()
     c_max = float(w.c.max()) * 1.05
@@ -584,6 +584,7 @@ def run_ours(args):
     if rank == 0 and args.case == "full" and not args.no_extras:
         extras["fp64_single_shot"] = fp64_single_shot_estimate(wl, method, m, dt, nsteps, c_max)
         extras["fwi_gradient"] = fwi_gradient_step(method, m, dt / dt_cfl)
+        extras["fwi_gradient_krylov"] = fwi_gradient_step("krylov", 20, 8.0)
         extras["config5_3d"] = config5_3d(args.n3d, args.check3d)
     result = None
     if rank == 0:
@@ -627,6 +628,7 @@ def run_ours(args):
                               "time_to_solution_s": lf64.cost_s} if lf64 else None),
             "fp64_single_shot": extras.get("fp64_single_shot"),
             "fwi_gradient": extras.get("fwi_gradient"),
+            "fwi_gradient_krylov": extras.get("fwi_gradient_krylov"),
             "config5_3d": extras.get("config5_3d"),
             "bf16_storage": ({"seismo_rel_err": study.bf16_err,
                               "note": "every stored integrator vector rounded to bfloat16 "

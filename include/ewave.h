@@ -76,6 +76,7 @@ extern "C" {
 #define EWV_METHOD_RK44 5     /* Sec. 3.1 classical RK4-4                                */
 #define EWV_METHOD_LEAPFROG 6 /* Sec. 3.1 two-step leap-frog                             */
 #define EWV_METHOD_ADJOINT_FABER 7 /* discrete adjoint of the Faber step (workspace query) */
+#define EWV_METHOD_ADJOINT_KRYLOV 8 /* linearised adjoint of the Krylov step (workspace query) */
 
 #define EWV_LEAPFROG_AVERAGED 0 /* time-averaged PML damping of w (stable reading)       */
 #define EWV_LEAPFROG_LITERAL 1  /* explicit -beta w^n damping, as the formula reads      */
@@ -238,10 +239,17 @@ int ewv_set_leapfrog_variant(ewv_model_t model, int variant);
  * (nshots padded fields [ny][pitch] of the model's precision, one per shot; sum them for
  * the model gradient).  t = t_{n-1}, dt, m as in the forward ewv_step_faber call (same
  * ellipse).  method EWV_METHOD_FABER (reverse three-term recurrence) or EWV_METHOD_HORK
- * (m = stages; reverse of the (I + dt H~) chain); UNSUPPORTED otherwise.  Needs
+ * (m = stages; reverse of the (I + dt H~) chain): exact discrete adjoints, needing
  * ewv_workspace_bytes(EWV_METHOD_ADJOINT_FABER, m) of workspace (the step is recomputed
- * from the checkpoint: m tape vectors + 3 cotangents).  Buffers 256-B aligned,
- * caller-owned.
+ * from the checkpoint: m tape vectors + 3 cotangents).  method EWV_METHOD_KRYLOV (m = Krylov
+ * dimension, <= EWV_MAX_KRYLOV_M): the Krylov step depends nonlinearly on U (its basis does),
+ * so this is the adjoint of the step's exact exponential, U^n = [I 0] exp(dt H~) [U^{n-1}; e_p]:
+ * lambda <- exp(dt H)^T lambda by Arnoldi on dt H^T (m products), and
+ * grad += int_0^dt [exp((dt-s) H)^T lambda]_v (L u + D w)(s) ds by 4-point Gauss-Legendre,
+ * with the states at the nodes from the forward and adjoint Arnoldi bases (dense output).
+ * It agrees with the Krylov forward to that step's time accuracy.  Workspace:
+ * ewv_workspace_bytes(EWV_METHOD_ADJOINT_KRYLOV, m) (2m + 9 vectors).  2D models only.
+ * Buffers 256-B aligned, caller-owned.
  *
  * ewv_adjoint_inject: lambda_u += R^T values at the receivers, values [nshots][max_receivers]
  * of the model's precision (the seismogram cotangent of one sample).

@@ -191,6 +191,8 @@ struct Engine {
     double tma_variant_us[TMA_NUM_VARIANTS] = {0, 0, 0, 0};
     ProblemDev* d_adj = nullptr;  // adjoint call: descriptors (state = cotangent) + tile map
     size_t d_adj_bytes = 0;
+    ProblemDev* d_kadj = nullptr; // Krylov adjoint: three descriptor views of the workspace
+    size_t d_kadj_bytes = 0;
     int* d_err = nullptr;       // timeout word written by the TMA kernel
     std::map<std::tuple<double, int, double, double, double>, std::vector<double>> faber_cache;
     // CUDA graphs of one step's launch sequence, keyed by (method, m, dt, g, c0, c1, parity
@@ -247,6 +249,7 @@ struct Engine {
         cudaFree(d_pbase);
         cudaFree(d_err);
         cudaFree(d_adj);
+        cudaFree(d_kadj);
     }
 };
 
@@ -329,6 +332,7 @@ int vectors_needed(int method, int m) {
         case EWV_METHOD_RK44: return 3;
         case EWV_METHOD_LEAPFROG: return 1;
         case EWV_METHOD_ADJOINT_FABER: return m + 3;   // tape p_0..p_{m-1} + 3 cotangents
+        case EWV_METHOD_ADJOINT_KRYLOV: return 2 * m + 9;  // two bases + 8 dense outputs
         default: return -1;
     }
 }
@@ -1718,17 +1722,145 @@ int ewv_batch_kernel_timing(ewv_batch_t b, double* total_ms, long long* launches
 }
 
 // ---- discrete adjoint (FWI gradient) -------------------------------------------------
+// Krylov step adjoint (the step-level linearisation of the Krylov row of the FWI gradient):
+// cotangent exp(dt H)^T ybar by Arnoldi on dt H^T, and the m-gradient
+//   dt sum_q w_q [exp((1 - tau_q) dt H)^T ybar]_v  G(x(tau_q dt)),  x(s) = [I 0] exp(s H~)[U; e_p],
+// with 4-point Gauss-Legendre nodes tau_q and dense output of both Arnoldi bases.  Three
+// descriptor views of the workspace (per shot, W_k = workspace vector k):
+//   F (state W_0 = checkpoint, work W_1): forward basis q_1 = W_0, q_{k+1} = W_k; x(tau_q) -> W_{m+q}
+//   A (state = cotangent, work W_{m+5}): adjoint basis q'_1 = cotangent, q'_{k+1} = W_{m+4+k};
+//     y(1 - tau_q) -> W_{2m+4+q}; finally y(1) -> the cotangent
+//   G (state = cotangent, work W_0): gradient passes, x(tau_q) = G vector m+q+1, y = 2m+5+q.
+static int adjoint_krylov(ewv_model* m, Engine* E, double t, double dt, int mm, void* adj_state,
+                          void* grad, const std::vector<ProblemDev>& base, const int* d_tp, int tb) {
+    cudaStream_t s = m->stream;
+    const int ns = m->d.nshots, prec = m->d.precision, R = m->R;
+    const size_t vb = m->vec_elems * m->elem;
+    const size_t per_shot = (m->work_bytes / ns) / vb;
+    auto wvec = [&](int sh, int k) { return (char*)m->work + ((size_t)sh * per_shot + (size_t)k) * vb; };
+    std::vector<ProblemDev> views(3 * (size_t)ns);
+    for (int sh = 0; sh < ns; ++sh) {
+        ProblemDev P = base[sh];
+        P.pchunks = E->probs[sh].pchunks;
+        P.pchunk_base = E->probs[sh].pchunk_base;
+        ProblemDev F = P, A = P, G = P;
+        F.state = wvec(sh, 0);
+        F.work = wvec(sh, 1);
+        A.state = (char*)adj_state + (size_t)sh * vb;
+        A.work = wvec(sh, mm + 5);
+        G.state = A.state;
+        G.work = wvec(sh, 0);
+        views[sh] = F;
+        views[ns + sh] = A;
+        views[2 * ns + sh] = G;
+    }
+    const size_t bytes = sizeof(ProblemDev) * views.size();
+    if (!E->d_kadj || E->d_kadj_bytes < bytes) {
+        cudaFree(E->d_kadj);
+        E->d_kadj = nullptr;
+        CUDA_OR_FAIL(m->err, cudaMalloc(&E->d_kadj, bytes));
+        E->d_kadj_bytes = bytes;
+    }
+    CUDA_OR_FAIL(m->err, cudaMemcpyAsync(E->d_kadj, views.data(), bytes, cudaMemcpyHostToDevice, s));
+    const ProblemDev* vF = E->d_kadj;
+    const ProblemDev* vA = E->d_kadj + ns;
+    const ProblemDev* vG = E->d_kadj + 2 * ns;
+    const double tol = prec == EWV_F64 ? 1e-14 : 1e-6;
+    static const double kTau[4] = {0.069431844202973712, 0.33000947820757187,
+                                   0.66999052179242813, 0.93056815579702629};
+    static const double kW[4] = {0.17392742256872693, 0.32607257743127307,
+                                 0.32607257743127307, 0.17392742256872693};
+    auto arnoldi = [&](const ProblemDev* v, bool transpose) {
+        PointArgs pn{};
+        pn.mode = 0;
+        pn.m = mm;
+        pn.tol = tol;
+        pn.notail = transpose ? 1 : 0;
+        pn.partials = E->d_partials;
+        pn.counters = E->d_counters;
+        launch_point_flat(prec, E->nchunks, v, E->d_pbase, ns, pn, s);
+        ++m->launches;
+        for (int j = 1; j <= mm; ++j) {
+            StageArgs a = stage_defaults();
+            a.x = j - 1;
+            a.y_out = j;
+            a.d = 0;
+            a.src_slot = transpose ? -1 : j;
+            a.x_scale_slot = KRY_S + j;
+            a.ch = dt;
+            a.ck = 1.0;
+            a.transpose = transpose ? 1 : 0;
+            a.fin_mode = FIN_MATVEC;
+            a.fin_j = j;
+            a.m = mm;
+            a.tol = tol;
+            a.partials = E->d_partials;
+            a.counters = E->d_counters;
+            launch_stage(prec, R, tb, v, d_tp, a, s);
+            ++m->launches;
+            const int kmax = (j == mm) ? j - 1 : j;
+            for (int k = 1; k <= kmax; ++k) {
+                PointArgs pm{};
+                pm.mode = 1;
+                pm.j = j;
+                pm.k = k;
+                pm.m = mm;
+                pm.tol = tol;
+                pm.partials = E->d_partials;
+                pm.counters = E->d_counters;
+                launch_point_flat(prec, E->nchunks, v, E->d_pbase, ns, pm, s);
+                ++m->launches;
+            }
+        }
+    };
+    auto dense = [&](const ProblemDev* v, double tau, int dst) {
+        if (launch_expm(v, ns, mm, s, tau) != 0) return false;
+        PointArgs pc{};
+        pc.mode = 2;
+        pc.m = mm;
+        pc.dst = dst;
+        launch_point_flat(prec, E->nchunks, v, E->d_pbase, ns, pc, s);
+        m->launches += 2;
+        return true;
+    };
+    // forward Arnoldi from the checkpoint (W_0 holds U^{n-1}), with the source of step n
+    launch_set_clock(vF, ns, t, dt, s);
+    launch_prologue(vF, ns, PRO_KRYLOV, mm, 0.0, 0.0, 0.0, s);
+    m->launches += 2;
+    arnoldi(vF, false);
+    for (int q = 0; q < 4; ++q)
+        if (!dense(vF, kTau[q], mm + 1 + q)) return fail(m->err, EWV_ERR_CUDA, "expm configuration failed");
+    // adjoint Arnoldi on dt H^T from the cotangent (no tail, no source)
+    arnoldi(vA, true);
+    for (int q = 0; q < 4; ++q)
+        if (!dense(vA, 1.0 - kTau[q], mm + 1 + q)) return fail(m->err, EWV_ERR_CUDA, "expm configuration failed");
+    // gradient: dt w_q y_v(1 - tau_q) G(x(tau_q))
+    for (int q = 0; q < 4; ++q) {
+        StageArgs gr = stage_defaults();
+        gr.x = mm + 2 + q;
+        gr.grad = grad;
+        gr.gq = 2 * mm + 6 + q;
+        gr.gscale = dt * kW[q];
+        launch_stage(prec, R, tb, vG, d_tp, gr, s);
+        ++m->launches;
+    }
+    // new cotangent y(1) into the cotangent buffer
+    if (!dense(vA, 1.0, 0)) return fail(m->err, EWV_ERR_CUDA, "expm configuration failed");
+    return check_launch(m->err);
+}
+
 int ewv_adjoint_step(ewv_model_t m, int method, double t, double dt, int deg,
                      const void* checkpoint, void* adj_state, void* grad) {
     if (!m || !checkpoint || !adj_state || !grad) return EWV_ERR_INVALID_ARG;
     if (m->d.dims == 3) return fail(m->err, EWV_ERR_UNSUPPORTED, "the adjoint is two-dimensional");
-    if (method != EWV_METHOD_FABER && method != EWV_METHOD_HORK)
-        return fail(m->err, EWV_ERR_UNSUPPORTED, "adjoint implemented for the Faber and HORK steps");
-    if (deg < 1 || deg > MAX_DEG || !(dt > 0.0))
-        return fail(m->err, EWV_ERR_INVALID_ARG, "degree must be 1..%d and dt > 0", MAX_DEG);
+    if (method != EWV_METHOD_FABER && method != EWV_METHOD_HORK && method != EWV_METHOD_KRYLOV)
+        return fail(m->err, EWV_ERR_UNSUPPORTED, "adjoint implemented for the Faber, HORK and Krylov steps");
+    if (deg < 1 || deg > (method == EWV_METHOD_KRYLOV ? MAX_M : MAX_DEG) || !(dt > 0.0))
+        return fail(m->err, EWV_ERR_INVALID_ARG, "degree / dimension out of range or dt <= 0");
     if (!aligned(checkpoint) || !aligned(adj_state) || !aligned(grad))
         return fail(m->err, EWV_ERR_BAD_SIZE_OR_ALIGNMENT, "adjoint buffers must be 256-B aligned");
-    int rc = check_bound(m, EWV_METHOD_ADJOINT_FABER, deg, m->err);
+    int rc = check_bound(m, method == EWV_METHOD_KRYLOV ? EWV_METHOD_ADJOINT_KRYLOV : EWV_METHOD_ADJOINT_FABER,
+                         deg, m->err);
     if (rc != EWV_OK) return rc;
     Engine* E = ensure_model_engine(m);
     rc = engine_ready(E, m->err);
@@ -1772,6 +1904,8 @@ int ewv_adjoint_step(ewv_model_t m, int method, double t, double dt, int deg,
         launch_stage(prec, R, tb, E->d_adj, d_tp, sa, s);
         ++m->launches;
     };
+    if (method == EWV_METHOD_KRYLOV)
+        return adjoint_krylov(m, E, t, dt, deg, adj_state, grad, probs, d_tp, tb);
     if (method == EWV_METHOD_HORK) {
         // u^{n+1} = sum_i w_i k_i, k_i = (I + dt H~) k_{i-1}; tape T_k = k_k = vector k+1
         const std::vector<double> lam = hork_lambdas(deg);

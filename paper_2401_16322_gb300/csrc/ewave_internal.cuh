@@ -94,7 +94,8 @@ struct StageArgs {
 struct PointArgs {
     int mode;        // 0: |q1|^2 (norm); 1: MGS pass; 2: Krylov combine; 3: copy; 4: swap
     int j, k, m;
-    int src, dst;    // copy / swap vectors
+    int src, dst;    // copy / swap vectors; combine: destination vector (mode 2)
+    int notail;      // mode 0: start an Arnoldi process without the augmented tail
     int fmask;       // fields for copy / swap (bit f)
     double tol;
     double* partials;
@@ -154,7 +155,7 @@ void launch_inject(int precision, void* adj, long long vec_elems, const void* va
                    const int* rec_off, const int* nrec, int nshots, int max_rec, cudaStream_t s);
 void launch_sum_shots(int precision, const void* in, void* out, long long n, int nshots,
                       cudaStream_t s);
-int launch_expm(const ProblemDev* probs, int nprob, int mmax, cudaStream_t s);
+int launch_expm(const ProblemDev* probs, int nprob, int mmax, cudaStream_t s, double hscale = 1.0);
 void launch_faber_coeffs(double dt, double gamma, double c0, double c1, int m, double* out,
                          cudaStream_t s);
 

@@ -384,7 +384,7 @@ point_flat_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ 
         const double beta = kry[KRY_BETA];
         for (int k = tid; k < meff; k += NTHREADS) s_coef[k] = (T)(beta * kry[KRY_E + k] * kry[KRY_S + k + 1]);
         __syncthreads();
-        V* St = reinterpret_cast<V*>(vptr<T>(P, 0));
+        V* St = reinterpret_cast<V*>(vptr<T>(P, pa.dst));
         for (long long q = q0 + tid; q < q1; q += NTHREADS) {
             V acc = {};
             for (int k = 1; k <= meff; ++k) fma16(acc, s_coef[k - 1], reinterpret_cast<const V*>(vptr<T>(P, k - 1))[q]);
@@ -413,7 +413,7 @@ point_flat_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ 
     if (pa.mode == 1 && pa.k == pa.j && pa.j == pa.m) return;   // h_{m+1,m} unused
     const double bsum = block_sum_fixed(accd, red);
     StageArgs a{};
-    a.fin_mode = pa.mode == 0 ? FIN_NORM0 : FIN_MGS;
+    a.fin_mode = pa.mode == 0 ? (pa.notail ? FIN_NORM0_NOTAIL : FIN_NORM0) : FIN_MGS;
     a.fin_j = pa.j;
     a.fin_k = pa.k;
     a.m = pa.m;
@@ -436,7 +436,7 @@ __device__ void mat_mul(const double* A, const double* B, double* C, int n) {
     __syncthreads();
 }
 
-__global__ void expm_kernel(const ProblemDev* probs, int nprob) {
+__global__ void expm_kernel(const ProblemDev* probs, int nprob, double hscale) {
     extern __shared__ double sm[];
     __shared__ double b[14];
     __shared__ double colmax[MAX_M];
@@ -463,7 +463,7 @@ __global__ void expm_kernel(const ProblemDev* probs, int nprob) {
     }
     for (int e = tid; e < nn; e += blockDim.x) {
         const int r = e / n, c = e - r * n;
-        A[e] = kry[KRY_H + r * MAX_M + c];
+        A[e] = hscale * kry[KRY_H + r * MAX_M + c];   // exp(tau H_m): dense output at tau
     }
     __syncthreads();
     for (int c = tid; c < n; c += blockDim.x) {
@@ -663,14 +663,14 @@ void launch_point_flat(int precision, int nchunks, const ProblemDev* probs, cons
     if (precision == 0) point_flat_kernel<float><<<nchunks, block, 0, s>>>(probs, pbase, nprob, pa);
     else point_flat_kernel<double><<<nchunks, block, 0, s>>>(probs, pbase, nprob, pa);
 }
-int launch_expm(const ProblemDev* probs, int nprob, int mmax, cudaStream_t s) {
+int launch_expm(const ProblemDev* probs, int nprob, int mmax, cudaStream_t s, double hscale) {
     const size_t smem = (size_t)7 * mmax * mmax * sizeof(double);
     if (smem > 48 * 1024) {
         if (cudaFuncSetAttribute(expm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem) != cudaSuccess)
             return -1;
     }
-    expm_kernel<<<nprob, 256, smem, s>>>(probs, nprob);
+    expm_kernel<<<nprob, 256, smem, s>>>(probs, nprob, hscale);
     return 0;
 }
 void launch_faber_coeffs(double dt, double gamma, double c0, double c1, int m, double* out,

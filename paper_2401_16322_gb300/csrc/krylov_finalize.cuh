@@ -23,7 +23,7 @@
 
 namespace ewv {
 
-enum { FIN_NONE = 0, FIN_NORM0 = 1, FIN_MATVEC = 2, FIN_MGS = 3 };
+enum { FIN_NONE = 0, FIN_NORM0 = 1, FIN_MATVEC = 2, FIN_MGS = 3, FIN_NORM0_NOTAIL = 4 };
 
 __device__ __forceinline__ double* kry_tail(double* kry, int k) {  // k = 1..MAX_M+1
     return kry + KRY_T + (k - 1) * MAX_P;
@@ -38,7 +38,21 @@ __device__ inline void krylov_finalize(const ProblemDev* P, int mode, int j, int
         kry[KRY_ACTIVE] = 0.0;
         return;
     }
-    if (mode == FIN_NORM0) {
+    if (mode == FIN_NORM0_NOTAIL) {
+        // Arnoldi on a plain (non-augmented) operator, e.g. dt H^T: zero tail, no source
+        const double beta = sqrt(tot);
+        for (int k = 1; k <= MAX_M + 1; ++k) {
+            double* tk = kry_tail(kry, k);
+            for (int q = 0; q < MAX_P; ++q) tk[q] = 0.0;
+        }
+        for (int q = 0; q < MAX_P; ++q) kry[KRY_W + q] = 0.0;
+        kry[KRY_BETA] = beta;
+        kry[KRY_S + 1] = beta > 0.0 ? 1.0 / beta : 0.0;
+        kry[KRY_ACTIVE] = beta > 0.0 ? 1.0 : 0.0;
+        kry[KRY_MEFF] = beta > 0.0 ? (double)m : 0.0;
+        for (int j2 = 0; j2 <= MAX_M; ++j2) P->sigma[j2] = 0.0;
+        for (int r = 0; r < (MAX_M + 1) * MAX_M; ++r) kry[KRY_H + r] = 0.0;
+    } else if (mode == FIN_NORM0) {
         double* t1 = kry_tail(kry, 1);
         const double eta = tot > 0.0 ? sqrt(tot) : 1.0;
         for (int q = 0; q < MAX_P; ++q) t1[q] = 0.0;

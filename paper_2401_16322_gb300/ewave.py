@@ -20,7 +20,7 @@ ERRORS = {
 }
 F32, F64 = 0, 1
 METHOD = {"apply": 0, "faber": 1, "krylov": 2, "hork": 3, "rk32": 4, "rk44": 5, "leapfrog": 6,
-          "adjoint_faber": 7}
+          "adjoint_faber": 7, "adjoint_krylov": 8}
 LEAPFROG_AVERAGED, LEAPFROG_LITERAL = 0, 1
 
 # Every symbol include/ewave.h declares (checked by the tests).
@@ -369,8 +369,9 @@ class Model:
 
     # ---------------------------------------------------------------- adjoint
     def adjoint_step(self, t, dt, degree, checkpoint, adj, grad, method="faber"):
-        """lambda <- (dPhi/dU)^T lambda, grad += (dPhi/dm)^T lambda for one Faber / HORK step."""
-        self.ensure_workspace("adjoint_faber", degree)
+        """lambda <- (dPhi/dU)^T lambda, grad += (dPhi/dm)^T lambda for one Faber / HORK step
+        (Krylov: the adjoint of the step's exponential)."""
+        self.ensure_workspace("adjoint_krylov" if method == "krylov" else "adjoint_faber", degree)
         self._check(self.lib.ewv_adjoint_step(self.h, METHOD[method], t, dt, degree,
                                               ctypes.c_void_p(checkpoint.data_ptr()),
                                               ctypes.c_void_p(adj.data_ptr()),

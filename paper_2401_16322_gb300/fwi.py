@@ -18,11 +18,12 @@ from .ewave import Model, checkpoint_stride
 
 class FaberFWI:
     """Forward simulation with checkpoints and the adjoint gradient for one model
-    (``method`` "faber": degree m; "hork": m stages)."""
+    (``method`` "faber": degree m; "hork": m stages; "krylov": dimension m, adjoint of the
+    step's exponential)."""
 
     def __init__(self, model: Model, dt, degree, nsteps, nrec, budget=None, t0=0.0, method="faber"):
-        if method not in ("faber", "hork"):
-            raise ValueError("the adjoint exists for the Faber and HORK steps")
+        if method not in ("faber", "hork", "krylov"):
+            raise ValueError("the adjoint exists for the Faber, HORK and Krylov steps")
         self.method = method
         self.model = model
         self.dt, self.degree, self.nsteps, self.nrec, self.t0 = dt, degree, nsteps, nrec, t0
@@ -64,7 +65,8 @@ class FaberFWI:
         g[:, :, :self.nrec] = grad_seis.to(md.dtype)
         lam = torch.zeros(ns * nv, dtype=md.dtype, device=md.device)
         grad = torch.zeros(ns * fe, dtype=md.dtype, device=md.device)
-        md.ensure_workspace("adjoint_faber", self.degree)
+        adj_ws = "adjoint_krylov" if self.method == "krylov" else "adjoint_faber"
+        md.ensure_workspace(adj_ws, self.degree)
         md.adjoint_inject(lam, g[:, self.nsteps - 1, :].contiguous())
         for k in range(self.nck - 1, -1, -1):
             n0 = k * self.stride
@@ -77,7 +79,7 @@ class FaberFWI:
                     self.seg[n - n0].copy_(md.state)
                     if n + 1 < n1:
                         md.step(self.method, self.t0 + n * self.dt, self.dt, self.degree, 1)
-                md.ensure_workspace("adjoint_faber", self.degree)
+                md.ensure_workspace(adj_ws, self.degree)
             for n in range(n1, n0, -1):          # adjoint of step n: U^{n-1} -> U^n
                 ck = self.seg[n - 1 - n0] if self.stride > 1 else self.ckpt[n - 1]
                 md.adjoint_step(self.t0 + (n - 1) * self.dt, self.dt, self.degree, ck, lam, grad,

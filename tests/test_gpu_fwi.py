@@ -174,3 +174,31 @@ def test_checkpoint_stride_bit_exact():
     for n in range(0, 60):
         for b in range(1, 25):
             assert checkpoint_stride(n, b) == o_stride(n, b)
+
+
+@pytest.mark.parametrize("budget", [None, 4])
+def test_krylov_gradient_matches_oracle_and_differences(budget):
+    """Krylov (m = 12, dt 1 ms): the linearised adjoint gradient on the GPU equals the oracle's
+    (FP64), with and without checkpoint segments, and agrees with central differences of the
+    GPU Krylov misfit to the step's time accuracy (1e-3)."""
+    import torch
+    from paper_2401_16322_gb300.fwi import FaberFWI
+    c_true, c0, beta0, ell = _setup()
+    dt, m, nsteps = 1e-3, 12, 10
+    om_t = OModel(NX, NY, DX, 8, PML, beta0, True, c_true)
+    d_obs = faber_forward(om_t, _oshots(om_t), dt, nsteps, m, ell, method="krylov")[1]
+    om = OModel(NX, NY, DX, 8, PML, beta0, True, c0)
+    J_o, g_o = fwi_gradient(om, _oshots(om), d_obs, dt, nsteps, m, ell, method="krylov")
+    g = _gpu(c0, beta0, ell, "f64")
+    fwi = FaberFWI(g, dt, m, nsteps, len(REC), budget=budget, method="krylov")
+    d = torch.tensor(np.array(d_obs), dtype=torch.float64, device="cuda")
+    seis = fwi.forward(c0 ** 2)
+    assert abs(0.5 * float(((seis - d) ** 2).sum()) - J_o) <= 1e-9 * J_o
+    grad = fwi.backward(seis - d).double().cpu().numpy()
+    assert rel_l2(grad, g_o) < 1e-9
+    dm = smooth_random_state([(NY, NX)], 9, sigma_cells=2.0)[0] * 0.01 * c0 ** 2
+    eps = 1e-4
+    Jp = 0.5 * float(((fwi.forward(c0 ** 2 + eps * dm) - d) ** 2).sum())
+    Jm = 0.5 * float(((fwi.forward(c0 ** 2 - eps * dm) - d) ** 2).sum())
+    fd = (Jp - Jm) / (2 * eps)
+    assert abs(fd - float(np.sum(grad * dm))) <= 1e-3 * abs(fd)
