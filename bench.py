@@ -425,6 +425,38 @@ def pass_words3d(method, m):
     raise ValueError(method)
 
 
+def config1_fp64_study():
+    """The small homogeneous case (101 x 101, dx 10 m, 2000 m/s, 4th order, 20-point ABC,
+    Ricker 15 Hz at the centre, 50 receivers, T 0.5 s) in FP64: Delta-t_max of Faber, HORK
+    and Krylov against an FP64 reference (Faber 30 at the leap-frog step) and leap-frog at
+    1 .. 1/32 of its step, each candidate's error and its time to T on the GPU.  Every
+    evaluated (method, m, step) is listed, so the error-versus-step curves can be drawn."""
+    from paper_2401_16322_gb300 import Batch
+    from paper_2401_16322_gb300.tts import build_models, run_study
+    from paper_2401_16322_gb300.workloads import config_homogeneous_small
+    wl = [config_homogeneous_small()]
+    plan = (("faber", (10, 20, 30, 40), tuple(range(16, 0, -1))),
+            ("hork", (8, 12, 16), tuple(range(8, 0, -1))),
+            ("krylov", (10, 20), tuple(range(16, 0, -1))))
+    models = build_models(wl, "f64", p=12)
+    batch = Batch(models)
+    st = run_study(wl, [(0, 0)], wl[0].T, plan=plan, full_batch=batch, full_models=models,
+                   precision="f64", log=lambda *a: None)
+    batch.close()
+    for md in models:
+        md.close()
+    cand = [{"method": c.method, "m": c.m, "dt_ms": round(c.dt * 1e3, 5),
+             "seismo_rel_err": c.err, "time_to_T_s": c.cost_s} for c in st.candidates]
+    sel = st.selected
+    return {"workload": "homogeneous 101x101, 4th order, FP64, T 0.5 s",
+            "leapfrog_step_ms": st.dt_cfl * 1e3,
+            "selected": ({"method": sel.method, "m": sel.m, "dt_ms": sel.dt * 1e3,
+                          "seismo_rel_err": sel.err, "time_to_T_s": sel.cost_s} if sel else None),
+            "leapfrog": ({"dt_ms": st.leapfrog.dt * 1e3, "seismo_rel_err": st.leapfrog.err,
+                          "time_to_T_s": st.leapfrog.cost_s} if st.leapfrog else None),
+            "evaluated": cand, "search_s": st.seconds}
+
+
 # ------------------------------------------------------------------------- reference arm
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -586,6 +618,22 @@ def run_ours(args):
         extras["fwi_gradient"] = fwi_gradient_step(method, m, dt / dt_cfl)
         extras["fwi_gradient_krylov"] = fwi_gradient_step("krylov", 20, 8.0)
         extras["config5_3d"] = config5_3d(args.n3d, args.check3d)
+        extras["config1_fp64"] = config1_fp64_study()
+    if rank == 0 and study is not None:
+        # dispersion / dissipation of the fastest passing setting of each method (and of
+        # leap-frog at its passing FP64 step) on the undamped spectrum
+        from paper_2401_16322_gb300.analysis import report
+        best = {}
+        for c in study.candidates:
+            if c.err <= args.target and c.method != "krylov":
+                if c.method not in best or c.cost_s < best[c.method].cost_s or not math.isfinite(best[c.method].cost_s):
+                    best[c.method] = c
+        if study.leapfrog_f64 is not None:
+            best["leapfrog"] = study.leapfrog_f64
+        g_, c0_, c1_ = models[0].faber_ellipse()
+        omega_spec = g_ * (1 - c1_) / math.sqrt(2.0)
+        extras["dispersion"] = report([(c.method, c.m, c.dt) for c in best.values()],
+                                      wl[0].f_peak, omega_spec, (g_, c0_, c1_))
     result = None
     if rank == 0:
         cpu_pps, cpu_desc, cores = cpu_oracle_sample(config_batched(), method, m, dt, args.cpu_sample_s)
@@ -630,10 +678,10 @@ def run_ours(args):
             "fwi_gradient": extras.get("fwi_gradient"),
             "fwi_gradient_krylov": extras.get("fwi_gradient_krylov"),
             "config5_3d": extras.get("config5_3d"),
-            "bf16_storage": ({"seismo_rel_err": study.bf16_err,
-                              "note": "every stored integrator vector rounded to bfloat16 "
-                                      "(round to nearest even) on the sampled problems, at the "
-                                      "cheapest FP32 (method, m, dt) by passes per unit time"}
+            "config1_fp64": extras.get("config1_fp64"),
+            "dispersion": extras.get("dispersion"),
+            "bf16_storage": ([{"method": k, "m": v[0], "dt_ms": v[1] * 1e3, "seismo_rel_err": v[2],
+                               "seismo_rel_err_fp32": v[3]} for k, v in study.bf16.items()]
                              if study else None),
             "search_s": study.seconds if study else None,
             "reference_self_check": study.ref_self_check if study else None,

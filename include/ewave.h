@@ -339,8 +339,11 @@ int ewv_batch_enable_graphs(ewv_batch_t batch, int enable);
  * tiles are 64 columns wide with a 4-column / R-row halo.  With v = -1 (default) the first
  * FP32 step call times every variant on a probe pass over the engine's own problems and
  * keeps the fastest; ewv_*kernel_variant reports the choice, its shape and the probe times
- * (us[4], -1 where a variant could not launch). */
-#define EWV_NUM_KERNEL_VARIANTS 4
+ * (us[EWV_NUM_KERNEL_VARIANTS], -1 where a variant could not launch).  Variant 4 = (16, 16,
+ * 4) without the U stage buffer: passes that read a U vector run variant 0 under it.
+ * 3D models: 0 (default) = TMA pipeline with 16 consumer warps, 2 = 8 warps, 1 = plain
+ * z-marching kernel. */
+#define EWV_NUM_KERNEL_VARIANTS 5
 int ewv_set_kernel_variant(ewv_model_t model, int variant);
 int ewv_kernel_variant(ewv_model_t model, int* variant, int* tile_height, int* warps,
                        int* stages, double* probe_us);

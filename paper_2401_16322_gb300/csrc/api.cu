@@ -188,7 +188,7 @@ struct Engine {
     int nchunks = 0;
     int ntiles_by[2] = {0, 0};
     int tma_variant = -1;       // -1: choose by timing at first use
-    double tma_variant_us[TMA_NUM_VARIANTS] = {0, 0, 0, 0};
+    double tma_variant_us[TMA_NUM_VARIANTS] = {};
     ProblemDev* d_adj = nullptr;  // adjoint call: descriptors (state = cotangent) + tile map
     size_t d_adj_bytes = 0;
     ProblemDev* d_kadj = nullptr; // Krylov adjoint: three descriptor views of the workspace

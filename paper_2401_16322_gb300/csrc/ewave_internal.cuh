@@ -134,7 +134,7 @@ int launch_leapfrog_tma3d(int R, int warps, const ProblemDev* probs, const int* 
 int upload_tma_tables(const double* fs_uyy, const double* fs_uy, const double* fs_dwy);
 int build_tensor_maps(std::vector<ProblemDev>& probs, int R, const std::vector<int>& work_vecs,
                       void** d_maps_inout);
-constexpr int TMA_NUM_VARIANTS = 4;
+constexpr int TMA_NUM_VARIANTS = 5;
 int launch_stage_tma(int variant, int R, const ProblemDev* probs, const int* tbase, int nprob,
                      int ntiles, const StageArgs& a, int* err, cudaStream_t s);
 int tma_variant_tile_height(int v);

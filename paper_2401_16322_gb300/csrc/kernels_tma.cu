@@ -29,8 +29,9 @@ constexpr int NMAP = 11;              // tensor maps per problem and tile height
 constexpr int MAX_NST = 5;
 
 // Shared-memory layout of one stage (floats) for tile height BYv; every buffer starts on a
-// 128-byte boundary.
-template <int R, int BYv>
+// 128-byte boundary.  HASU = false drops the U buffer (passes without a U operand, e.g. the
+// HORK stages), so that more stages fit in shared memory.
+template <int R, int BYv, bool HASU = true>
 struct StageLayout {
     static constexpr int SH = BYv + 2 * R;
     static constexpr int SW = BX + 2 * TX;
@@ -40,7 +41,7 @@ struct StageLayout {
     static constexpr int V_OFF = WY_OFF + SH * BX;           // v      BYv x BX
     static constexpr int C2_OFF = V_OFF + BYv * BX;          // c^2    BYv x BX
     static constexpr int PU_OFF = C2_OFF + BYv * BX;         // U      4 x BYv x BX
-    static constexpr int PA_OFF = PU_OFF + 4 * BYv * BX;     // A      4 x BYv x BX
+    static constexpr int PA_OFF = PU_OFF + (HASU ? 4 * BYv * BX : 0);   // A  4 x BYv x BX
     static constexpr int FLOATS = PA_OFF + 4 * BYv * BX;
     static constexpr int BYTES = FLOATS * 4;
     static_assert((U_OFF * 4) % 128 == 0 && (WX_OFF * 4) % 128 == 0 && (WY_OFF * 4) % 128 == 0 &&
@@ -200,11 +201,11 @@ __device__ __forceinline__ int find_problem(const int* __restrict__ base, int np
 
 // EPI 0: the general epilogue.  EPI 1: the steady-state form of the Faber and HORK passes,
 // ck = 1 and cau = cak = cax = 0:  Y = cu U + cx X + ch (H X + sigma),  ACC = ca A + cay Y.
-template <int R, int BYv, int NW, int NSTv, int EPI>
+template <int R, int BYv, int NW, int NSTv, int EPI, bool HASU>
 __global__ void __launch_bounds__(NW * 32 + 32, 1)
 stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ tbase, int nprob,
                  int ntiles, int mapset, StageArgs a, int* err) {
-    using L = StageLayout<R, BYv>;
+    using L = StageLayout<R, BYv, HASU>;
     constexpr int NCONS = NW * 32;
     constexpr int TPR = NCONS / BX;             // consumer thread rows
     constexpr int NR = BYv / TPR;               // consecutive rows per consumer thread
@@ -230,7 +231,7 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
     }
     __syncthreads();
 
-    const bool has_u = a.u >= 0, has_a = a.a >= 0;
+    const bool has_u = HASU && a.u >= 0, has_a = a.a >= 0;
     const uint32_t bytes = (uint32_t)((L::PU_OFF + (has_u ? 4 * BYv * BX : 0)) * 4) +
                            (has_a ? 4 * BYv * BX * 4 : 0);
     int issued = 0;
@@ -506,11 +507,13 @@ int build_tensor_maps(std::vector<ProblemDev>& probs, int R, const std::vector<i
     return 0;
 }
 
-// Kernel variants the autotuner chooses from: (tile height, consumer warps, stages).
+// Kernel variants the autotuner chooses from: (tile height, consumer warps, stages).  Variant
+// 4 has no U buffer (4 stages of 64 x 16): passes with a U operand run variant 0 instead.
 struct TmaVariant {
     int by, nw, nst;
 };
-constexpr TmaVariant kVariants[TMA_NUM_VARIANTS] = {{16, 16, 3}, {16, 8, 3}, {8, 8, 5}, {8, 16, 5}};
+constexpr TmaVariant kVariants[TMA_NUM_VARIANTS] = {{16, 16, 3}, {16, 8, 3}, {8, 8, 5}, {8, 16, 5},
+                                                    {16, 16, 4}};
 
 int tma_variant_tile_height(int v) { return kVariants[v].by; }
 void tma_variant_describe(int v, int* by, int* nw, int* nst) {
@@ -521,22 +524,22 @@ void tma_variant_describe(int v, int* by, int* nw, int* nst) {
 
 static int g_num_sms = 0;
 
-template <int R, int BYv, int NW, int NSTv, int EPI>
+template <int R, int BYv, int NW, int NSTv, int EPI, bool HASU = true>
 static int launch_variant(const ProblemDev* probs, const int* tbase, int nprob, int ntiles,
                           const StageArgs& a, int* err, cudaStream_t s) {
-    const size_t smem = (size_t)NSTv * StageLayout<R, BYv>::BYTES + 1024;
+    const size_t smem = (size_t)NSTv * StageLayout<R, BYv, HASU>::BYTES + 1024;
     // the shared-memory attribute is set once per instantiation and device
     static unsigned long long configured = 0;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return -1;
     if (!(configured >> dev & 1ull)) {
-        if (cudaFuncSetAttribute(stage_tma_kernel<R, BYv, NW, NSTv, EPI>,
+        if (cudaFuncSetAttribute(stage_tma_kernel<R, BYv, NW, NSTv, EPI, HASU>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return -1;
         configured |= 1ull << dev;
     }
     const int grid = ntiles < g_num_sms ? ntiles : g_num_sms;
-    stage_tma_kernel<R, BYv, NW, NSTv, EPI><<<grid, NW * 32 + 32, smem, s>>>(
+    stage_tma_kernel<R, BYv, NW, NSTv, EPI, HASU><<<grid, NW * 32 + 32, smem, s>>>(
         probs, tbase, nprob, ntiles, BYv == 16 ? 0 : 1, a, err);
     return 0;
 }
@@ -560,6 +563,16 @@ int launch_stage_tma(int variant, int R, const ProblemDev* probs, const int* tba
     EWV_TMA_CASE(1, 4, 16, 8, 3)
     EWV_TMA_CASE(2, 4, 8, 8, 5)
     EWV_TMA_CASE(3, 4, 8, 16, 5)
+    if (variant == 4) {   // no U buffer; a pass with a U operand runs variant 0
+        if (a.u >= 0) variant = 0;
+        else if (R == 4)
+            return epi ? launch_variant<4, 16, 16, 4, 1, false>(probs, tbase, nprob, ntiles, a, err, s)
+                       : launch_variant<4, 16, 16, 4, 0, false>(probs, tbase, nprob, ntiles, a, err, s);
+        else
+            return epi ? launch_variant<2, 16, 16, 4, 1, false>(probs, tbase, nprob, ntiles, a, err, s)
+                       : launch_variant<2, 16, 16, 4, 0, false>(probs, tbase, nprob, ntiles, a, err, s);
+    }
+    EWV_TMA_CASE(0, 4, 16, 16, 3)
     EWV_TMA_CASE(0, 2, 16, 16, 3)
     EWV_TMA_CASE(1, 2, 16, 8, 3)
     EWV_TMA_CASE(2, 2, 8, 8, 5)

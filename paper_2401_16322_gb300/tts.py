@@ -144,7 +144,7 @@ class Study:
     leapfrog: Optional[Candidate] = None          # FP32 leap-frog (None: never reaches target)
     leapfrog_f64: Optional[Candidate] = None
     ref_self_check: float = float("nan")
-    bf16_err: float = float("nan")             # selected candidate with bfloat16 storage
+    bf16: dict = field(default_factory=dict)   # method -> (m, dt, error) with bfloat16 storage
     seconds: float = 0.0
 
 
@@ -203,7 +203,7 @@ def _time_step(full_batch, full_models, method, m, dt, t_live):
 
 def run_study(workloads: List[Workload], picks, T, target=1e-4, plan=SCAN_PLAN,
               full_batch=None, full_models=None, full_models_f64=None, ref_m=30, p_ref=20,
-              p=12, log=print, self_check=False):
+              p=12, log=print, self_check=False, precision="f32"):
     """Delta-t_max search for every (method, m) of ``plan`` on the sampled problems, then the
     step time of each (method, m) on the full workload (``full_batch``/``full_models``; FP64
     leap-frog on ``full_models_f64`` when given).  Returns a Study."""
@@ -242,7 +242,7 @@ def run_study(workloads: List[Workload], picks, T, target=1e-4, plan=SCAN_PLAN,
     for md in ref_models:
         md.close()
     # FP32 candidates on the sampled problems
-    cand_models = build_models(sw, "f32", p=p, c_max=c_max)
+    cand_models = build_models(sw, precision, p=p, c_max=c_max)
     for md in cand_models:
         md.set_faber_ellipse(*ell)
     cand_batch = Batch(cand_models)
@@ -255,18 +255,22 @@ def run_study(workloads: List[Workload], picks, T, target=1e-4, plan=SCAN_PLAN,
                 + f" ({time.time() - t_start:.1f} s)")
     lf = []
     scan(cand_models, cand_batch, "leapfrog", 1, LEAPFROG_DIVISORS, lambda k: dt_cfl / k, lf)
-    # storage-precision experiment: the best passing FP32 (method, m, dt) on the sampled
-    # problems, with every stored vector rounded to bfloat16
-    passing_s = [c for c in cands if c.err <= target and c.method != "krylov"]
-    if passing_s:
+    # storage-precision experiment: for Faber and HORK, the passing FP32 (m, dt) with the
+    # fewest passes per unit time, again on the sampled problems with every stored vector
+    # rounded to bfloat16
+    for method in ("faber", "hork"):
+        passing_s = [c for c in cands if c.err <= target and c.method == method and precision == "f32"]
+        if not passing_s:
+            continue
         best = min(passing_s, key=lambda c: c.m / c.dt)
         for md in cand_models:
             md.set_storage_rounding(True)
         probe = Candidate(best.method, best.m, best.dt)
-        st.bf16_err = _eval_candidate(cand_models, cand_batch, refs, sw, probe, T, dt_ref, log)
+        err = _eval_candidate(cand_models, cand_batch, refs, sw, probe, T, dt_ref, log)
         for md in cand_models:
             md.set_storage_rounding(False)
-        log(f"  bfloat16 storage, {probe.label()}: error {st.bf16_err:.3e}")
+        st.bf16[method] = (best.m, best.dt, err, best.err)
+        log(f"  bfloat16 storage, {probe.label()}: error {err:.3e} (FP32 {best.err:.3e})")
     cand_batch.close()
     for md in cand_models:
         md.close()

@@ -98,7 +98,7 @@ def test_batch_bitwise_equals_single_models():
             assert np.array_equal(batched[q][s], g.get_state(s))
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
 def test_every_kernel_variant_matches_oracle(variant):
     """Each persistent-kernel variant the autotuner may pick (tile height 16 or 8, 8 or 16
     consumer warps, 3 or 5 stages) gives the oracle's result on uneven batched grids."""
