@@ -625,7 +625,7 @@ def run_ours(args):
         from paper_2401_16322_gb300.analysis import report
         best = {}
         for c in study.candidates:
-            if c.err <= args.target and c.method != "krylov":
+            if c.err <= args.target and not c.method.startswith("krylov"):
                 if c.method not in best or c.cost_s < best[c.method].cost_s or not math.isfinite(best[c.method].cost_s):
                     best[c.method] = c
         if study.leapfrog_f64 is not None:

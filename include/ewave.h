@@ -218,6 +218,15 @@ int ewv_step_faber(ewv_model_t model, double t, double dt, int degree, int nstep
  * smallest effective dimension over shots and steps (< m after a happy breakdown). */
 int ewv_step_krylov(ewv_model_t model, double t, double dt, int m, int nsteps, int* info);
 
+/* Incomplete orthogonalisation for the Krylov step (the library's option; the paper names
+ * incomplete or non-orthonormal bases as the way to cut the Arnoldi cost, Secs. 3.2 and 6):
+ * with window q > 0 each new vector is orthogonalised, in modified Gram-Schmidt order, only
+ * against the q most recent basis vectors, so the Hessenberg matrix is banded and a step
+ * costs m + q m Gram-Schmidt passes instead of m (m + 1) / 2; the Arnoldi relation
+ * A V_m = V_{m+1} H still holds, the basis is no longer orthonormal.  q = 0 (default): full
+ * Gram-Schmidt.  A batch uses the window of its first model. */
+int ewv_set_krylov_window(ewv_model_t model, int window);
+
 /* Sec. 3.2 HORK (scheme EWV_METHOD_HORK, `stages` = m) or Sec. 3.1 RK3-2 / RK4-4
  * (EWV_METHOD_RK32 / EWV_METHOD_RK44; stages ignored). */
 int ewv_step_rk(ewv_model_t model, double t, double dt, int scheme, int stages, int nsteps);

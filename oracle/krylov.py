@@ -64,8 +64,11 @@ def expm(A):
     return R
 
 
-def arnoldi(matvec, x, m, breakdown_tol=1e-14):
-    """MGS Arnoldi.  Returns (beta, V (n x m_eff), Hm (m_eff x m_eff), m_eff)."""
+def arnoldi(matvec, x, m, breakdown_tol=1e-14, window=None):
+    """MGS Arnoldi.  Returns (beta, V (n x m_eff), Hm (m_eff x m_eff), m_eff).
+
+    ``window`` = q: incomplete orthogonalisation (each new vector against the q most recent
+    basis vectors only; the library's option for cutting the Gram-Schmidt cost)."""
     beta = float(np.linalg.norm(x))
     n = x.shape[0]
     V = np.zeros((n, m + 1))
@@ -76,7 +79,8 @@ def arnoldi(matvec, x, m, breakdown_tol=1e-14):
     m_eff = m
     for j in range(m):
         w = matvec(V[:, j])
-        for k in range(j + 1):
+        k0 = 0 if not window else max(0, j - window + 1)
+        for k in range(k0, j + 1):
             Hm[k, j] = float(np.dot(w, V[:, k]))
             w = w - Hm[k, j] * V[:, k]
         if j == m - 1:
@@ -89,8 +93,10 @@ def arnoldi(matvec, x, m, breakdown_tol=1e-14):
     return beta, V[:, :m_eff], Hm[:m_eff, :m_eff], m_eff
 
 
-def krylov_step(model, U, src, t_n, dt, m, p=None, breakdown_tol=1e-14, return_info=False):
-    """One Krylov step: [I 0] exp(dt H~) [U; e_p] by Arnoldi with m matvecs."""
+def krylov_step(model, U, src, t_n, dt, m, p=None, breakdown_tol=1e-14, return_info=False,
+                window=None):
+    """One Krylov step: [I 0] exp(dt H~) [U; e_p] by Arnoldi with m matvecs (``window``: the
+    incomplete-orthogonalisation option of ``arnoldi``)."""
     if src is not None:
         p = src.p
         w = src.W(t_n, dt)
@@ -115,7 +121,7 @@ def krylov_step(model, U, src, t_n, dt, m, p=None, breakdown_tol=1e-14, return_i
     y0 = np.zeros(p)
     y0[-1] = eta
     x = np.concatenate([xu, y0])
-    beta, V, Hm, m_eff = arnoldi(matvec, x, m, breakdown_tol)
+    beta, V, Hm, m_eff = arnoldi(matvec, x, m, breakdown_tol, window)
     if m_eff == 0:
         out = unflatten(model, np.zeros(nU))
     else:

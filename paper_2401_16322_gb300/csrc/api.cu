@@ -156,6 +156,7 @@ struct ewv_model {
     double eg = 0, ec0 = 0, ec1 = 0;
     int lf_variant = EWV_LEAPFROG_AVERAGED;
     int store_bf16 = 0;         // storage-precision experiment (ewv_set_storage_rounding)
+    int kry_window = 0;         // Krylov orthogonalisation window (0 = full Gram-Schmidt)
     bool lf_history_valid = false;
     // device metadata
     int* d_rec = nullptr;
@@ -942,7 +943,8 @@ int run_krylov(Ctx& C, double t, double dt, int m, int nsteps, int* info) {
     launch_set_clock(C.E->d_probs, C.E->nprob, t, dt, C.s);
     ++*C.launches;
     bool expm_ok = true;
-    int rc0 = C.step_loop(nsteps, EWV_METHOD_KRYLOV, m, dt, tol, 0, 0, 1, [&](int) {
+    const int window = C.E->models.empty() ? 0 : C.E->models[0]->kry_window;
+    int rc0 = C.step_loop(nsteps, EWV_METHOD_KRYLOV, m, dt, tol, (double)window, 0, 1, [&](int) {
         C.prologue(PRO_KRYLOV, m);
         PointArgs pn{};
         pn.mode = 0;
@@ -952,17 +954,19 @@ int run_krylov(Ctx& C, double t, double dt, int m, int nsteps, int* info) {
         pn.counters = C.E->d_counters;
         C.point(pn);
         for (int j = 1; j <= m; ++j) {
+            // orthogonalise q_{j+1} against q_{k0} .. q_j (all of them without a window)
+            const int k0 = window > 0 ? std::max(1, j - window + 1) : 1;
             StageArgs a = stage_defaults();
             a.x = j - 1;
             a.y_out = j;
-            a.d = 0;
+            a.d = k0 - 1;
             a.src_slot = j;
             a.x_scale_slot = KRY_S + j;
             a.ch = dt;
             a.ck = 1.0;
             a.fin_mode = FIN_MATVEC;
             a.fin_j = j;
-            a.fin_k = 0;
+            a.fin_k = k0;
             a.m = m;
             a.tol = tol;
             a.partials = C.E->d_partials;
@@ -970,7 +974,7 @@ int run_krylov(Ctx& C, double t, double dt, int m, int nsteps, int* info) {
             C.stage(a);
             // at j = m the pass k = m only feeds h_{m+1,m}, which the result does not use
             const int kmax = (j == m) ? j - 1 : j;
-            for (int k = 1; k <= kmax; ++k) {
+            for (int k = k0; k <= kmax; ++k) {
                 PointArgs pm{};
                 pm.mode = 1;
                 pm.j = j;
@@ -1549,6 +1553,15 @@ int ewv_step_leapfrog(ewv_model_t m, double t, double dt, int nsteps) {
 int ewv_set_leapfrog_variant(ewv_model_t m, int variant) {
     if (!m || (variant != EWV_LEAPFROG_AVERAGED && variant != EWV_LEAPFROG_LITERAL)) return EWV_ERR_INVALID_ARG;
     m->lf_variant = variant;
+    return EWV_OK;
+}
+
+int ewv_set_krylov_window(ewv_model_t m, int window) {
+    if (!m || window < 0) return EWV_ERR_INVALID_ARG;
+    if (m->kry_window != window) {
+        m->kry_window = window;
+        ++m->version;   // drops the captured step graphs
+    }
     return EWV_OK;
 }
 

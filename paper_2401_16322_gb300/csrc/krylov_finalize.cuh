@@ -68,15 +68,18 @@ __device__ inline void krylov_finalize(const ProblemDev* P, int mode, int j, int
         P->sigma[1] = P->has_src ? sg : 0.0;
         for (int r = 0; r < (MAX_M + 1) * MAX_M; ++r) kry[KRY_H + r] = 0.0;
     } else if (mode == FIN_MATVEC) {
+        // tot = <q_{j+1}, q_{k0}>, k0 = k (the first vector this step orthogonalises against:
+        // 1 for full Gram-Schmidt, j - q + 1 with an orthogonalisation window of q)
+        const int k0 = k >= 1 ? k : 1;
         const double sj = kry[KRY_S + j];
         const double* tj = kry_tail(kry, j);
         double* tw = kry_tail(kry, j + 1);
         for (int q = 0; q < p - 1; ++q) tw[q] = sj * tj[q + 1];   // J (s_j tail_j)
         tw[p - 1] = 0.0;
-        const double* t1 = kry_tail(kry, 1);
+        const double* tk0 = kry_tail(kry, k0);
         double d = 0.0;
-        for (int q = 0; q < p; ++q) d += tw[q] * t1[q];
-        kry[KRY_H + 0 * MAX_M + (j - 1)] = kry[KRY_S + 1] * (tot + d);
+        for (int q = 0; q < p; ++q) d += tw[q] * tk0[q];
+        kry[KRY_H + (k0 - 1) * MAX_M + (j - 1)] = kry[KRY_S + k0] * (tot + d);
     } else if (mode == FIN_MGS) {
         const double hkj = kry[KRY_H + (k - 1) * MAX_M + (j - 1)];
         const double sk = kry[KRY_S + k];

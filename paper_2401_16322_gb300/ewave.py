@@ -39,6 +39,7 @@ EXPORTS = [
     "ewv_sum_shot_fields", "ewv_enable_graphs", "ewv_batch_enable_graphs",
     "ewv_set_kernel_variant", "ewv_kernel_variant", "ewv_batch_set_kernel_variant",
     "ewv_batch_kernel_variant", "ewv_set_source_receivers3d", "ewv_set_storage_rounding",
+    "ewv_set_krylov_window",
 ]
 
 
@@ -103,6 +104,7 @@ def load_library(path=LIB_PATH):
         "ewv_set_source_receivers": ([vp, i, d, d, d, d, d, i, dp, ip32, ip32], i),
         "ewv_set_source_receivers3d": ([vp, i, d, d, d, d, d, d, i, dp, ip32, ip32], i),
         "ewv_set_storage_rounding": ([vp, i], i),
+        "ewv_set_krylov_window": ([vp, i], i),
         "ewv_set_faber_ellipse": ([vp, d, d, d], i),
         "ewv_get_faber_ellipse": ([vp, dp, dp, dp], i),
         "ewv_set_state": ([vp, i, dp, sz], i),
@@ -259,6 +261,10 @@ class Model:
             si.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
             ri.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))), "set_source_receivers3d")
         return si, ri[:3 * nrec].reshape(nrec, 3)
+
+    def set_krylov_window(self, q):
+        """Orthogonalise each Krylov vector against the q most recent ones only (0: all)."""
+        self._check(self.lib.ewv_set_krylov_window(self.h, int(q)), "krylov_window")
 
     def set_storage_rounding(self, bf16):
         """Round every stored integrator vector to bfloat16 (storage-precision experiment)."""

@@ -125,3 +125,20 @@ def test_seismogram_indices_bit_exact():
     assert list(si) == [int(np.floor(245.0 / 10 + 0.5)), int(np.floor(15.0 / 10 + 0.5))]
     with pytest.raises(Exception):
         g.set_source_receivers(0, -6.0, 15.0, 10.0, 0.27, 1.0, rec)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("m,q", [(12, 2), (16, 3)])
+def test_krylov_with_orthogonalisation_window_matches_oracle(prec, m, q):
+    """Incomplete orthogonalisation (window q): the GPU step equals the oracle's windowed
+    Arnoldi step, with the source active."""
+    om, g, src, rec, rn, U0 = _setup(prec)
+    U0 = (U0[0], 0 * U0[1], 0 * U0[2], 0 * U0[3])
+    dt, t, nsteps = 1.2e-3, 0.03, 3
+    g.set_krylov_window(q)
+    gs, _ = _gpu_run(g, U0, "krylov", t, dt, m, nsteps, nsteps)
+    U = U0
+    for n in range(nsteps):
+        U = krylov.krylov_step(om, U, src, t + n * dt, dt, m, window=q)
+    err = rel_l2(gs, flatten(U))
+    assert err < TOL[prec] * (3 if prec == "f32" else 1), (m, q, err)

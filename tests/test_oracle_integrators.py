@@ -161,6 +161,25 @@ def test_arnoldi_relation_and_orthonormality():
     assert np.allclose(np.tril(Hm, -2), 0.0)
 
 
+def test_incomplete_orthogonalisation_keeps_the_arnoldi_relation():
+    """Window q: H is banded (h_kj = 0 for k < j - q + 1, 0-based), the Arnoldi relation
+    A V_j = V_{j+1} H_j holds for every column, and a window of m is the full process."""
+    rng = np.random.default_rng(2)
+    A = rng.standard_normal((40, 40))
+    x = rng.standard_normal(40)
+    m, q = 10, 2
+    beta, V, Hm, me = krylov.arnoldi(lambda v: A @ v, x, m, window=q)
+    assert me == m and abs(beta - np.linalg.norm(x)) < 1e-13 * beta
+    for j in range(m):
+        for k in range(0, max(0, j - q + 1)):
+            assert Hm[k, j] == 0.0
+    assert np.allclose(A @ V[:, :m - 1], V @ Hm[:, :m - 1], atol=1e-12)
+    assert not np.allclose(V.T @ V, np.eye(m), atol=1e-6)      # not orthonormal any more
+    full = krylov.arnoldi(lambda v: A @ v, x, m)
+    wide = krylov.arnoldi(lambda v: A @ v, x, m, window=m)
+    assert np.array_equal(full[1], wide[1]) and np.array_equal(full[2], wide[2])
+
+
 def test_arnoldi_happy_breakdown():
     A = np.diag(np.arange(1.0, 9.0))
     x = np.zeros(8)
