@@ -323,9 +323,21 @@ def config5_3d(n=400, check_n=96, target=TARGET):
         log(f"3D reference {time.perf_counter() - t_search:.1f} s")
         cmd = build(wc, "f32")
 
+        from paper_2401_16322_gb300 import Batch
+        from paper_2401_16322_gb300.tts import NOISE_GROWTH, POLYNOMIAL, noise_growth
+        cbatch = Batch([cmd])
+        t_quiet = wc.T + 20.0 / wc.f_peak + t0_for(wc.f_peak)
+
         def err_of(md, method, m, dt):
             try:
-                return rel_l2_common(simulate(md, method, m, dt, wc.T), dt, ref, dt3)
+                err = rel_l2_common(simulate(md, method, m, dt, wc.T), dt, ref, dt3)
+                if err <= target and method in POLYNOMIAL and md is cmd:
+                    # the stability check of the 2D search (white noise, source silent)
+                    growth = noise_growth([cmd], cbatch, method, m, dt, t_quiet)
+                    if not growth <= NOISE_GROWTH:
+                        log(f"3D {method} m={m} dt={dt * 1e3:.3f} ms: noise grows {growth:.3g} x")
+                        return float("inf")
+                return err
             except Exception as e:       # e.g. a non-finite Arnoldi step
                 log(f"3D {method} m={m} dt={dt * 1e3:.3f} ms: {e}")
                 return float("inf")
@@ -346,6 +358,7 @@ def config5_3d(n=400, check_n=96, target=TARGET):
             if k is not None:
                 found.append(("leapfrog" if prec == "f32" else "leapfrog_f64", 1, 1.0 / k, errs[k]))
         ref_md.close()
+        cbatch.close()
         cmd.close()
         out["search_s"] = time.perf_counter() - t_search
         out["error_check"] = f"{check_n}^3 cube, T 0.5 s, FP64 Faber 30 at the 3D leap-frog step"

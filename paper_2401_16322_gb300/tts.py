@@ -49,6 +49,7 @@ class Candidate:
     err: float = float("nan")
     step_ms: float = float("nan")
     nsteps: int = 0
+    growth: float = float("nan")     # white-noise norm growth over NOISE_STEPS steps
 
     @property
     def cost_s(self):
@@ -167,6 +168,13 @@ SCAN_PLAN = (
     ("hork", (8, 12, 16, 20, 24, 28, 32), tuple(range(12, 0, -1))),
 )
 LEAPFROG_DIVISORS = (1, 2, 3, 4, 6, 8, 12, 16, 24, 32)
+# Stability check of the polynomial integrators: a setting that meets the error target must
+# also keep seeded white noise (every mode of the discrete operator excited, source off)
+# from growing more than NOISE_GROWTH between step NOISE_STEPS and step 2 NOISE_STEPS on the
+# sampled problems.
+NOISE_STEPS = 100
+NOISE_GROWTH = 10.0
+POLYNOMIAL = ("faber", "hork", "rk32", "rk44")
 
 
 def dt_max_scan(ks, evaluate, target):
@@ -192,6 +200,31 @@ def _eval_candidate(models, batch, refs, sw, c, T, dt_ref, log):
         c.err = float("inf")
         log(f"  {c.label()}: {e}")
     return c.err
+
+
+def noise_growth(models, batch, method, m, dt, t_quiet, nsteps=NOISE_STEPS, seed=97):
+    """Stability of a setting on the actual spectrum of each discrete operator: from seeded
+    white noise in u and v (source silent, t >= t_quiet) take ``nsteps`` steps, then
+    ``nsteps`` more, and return the largest ||U_2N|| / ||U_N|| over the models.  Bounded
+    dynamics give O(1) (the first segment absorbs the transfer between u and v and the PML's
+    transients); a mode with |R| > 1 grows geometrically.  The smooth source of a shot
+    barely excites the top of the spectrum, so the error scan alone cannot see it."""
+    from .workloads import random_state
+    method = base_method(models, method)
+    for q, md in enumerate(models):
+        md.ensure_workspace(method, m)
+        md.reset_state()
+        npts = md.nx * md.ny * (md.nz or 1)
+        u, v = random_state([(npts,), (npts,)], seed + q)
+        md.set_state(0, np.concatenate([u, v, np.zeros(md.n - 2 * npts)]))
+    batch.step(method, t_quiet, dt, m, nsteps)
+    mid = [float(np.linalg.norm(md.get_state(0))) for md in models]
+    batch.step(method, t_quiet + nsteps * dt, dt, m, nsteps)
+    g = 0.0
+    for md, a in zip(models, mid):
+        b = float(np.linalg.norm(md.get_state(0)))
+        g = max(g, b / a if np.isfinite(a) and np.isfinite(b) and a > 0 else float("inf"))
+    return g
 
 
 def _time_step(full_batch, full_models, method, m, dt, t_live):
@@ -241,11 +274,24 @@ def run_study(workloads: List[Workload], picks, T, target=1e-4, plan=SCAN_PLAN,
         log(f"reference self-check (dt_ref vs dt_ref/2): {st.ref_self_check:.3e}")
     log(f"reference: FP64 faber m={ref_m} dt={dt_ref * 1e3:.3f} ms, {n_ref} steps "
         f"({time.time() - t_start:.1f} s)")
+    t_quiet = T + 20.0 / workloads[0].f_peak + t0_for(workloads[0].f_peak)
+
     def scan(models, batch, method, m, ks, to_dt, out):
         def ev(k):
             c = Candidate(method, m, to_dt(k))
             out.append(c)
-            return _eval_candidate(models, batch, refs, sw, c, T, dt_ref, log)
+            err = _eval_candidate(models, batch, refs, sw, c, T, dt_ref, log)
+            if err <= target and method in POLYNOMIAL:
+                try:
+                    c.growth = noise_growth(models, batch, method, m, c.dt, t_quiet)
+                except Exception as e:
+                    c.growth = float("inf")
+                    log(f"  {c.label()} noise test: {e}")
+                if not c.growth <= NOISE_GROWTH:
+                    log(f"  {c.label()}: error {err:.3e} but white noise grows {c.growth:.3g} x "
+                        f"between steps {NOISE_STEPS} and {2 * NOISE_STEPS}: rejected")
+                    c.err = float("inf")
+            return c.err
         return dt_max_scan(ks, ev, target)[0]
 
     # FP64 leap-frog on the sampled problems (reuses the reference models)

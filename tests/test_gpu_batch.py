@@ -160,3 +160,20 @@ def test_bf16_storage_rounding_stores_bf16_values():
     with pytest.raises(EwaveError, match="UNSUPPORTED"):
         m64.set_storage_rounding(True)
     m64.close()
+
+
+def test_white_noise_stability_check():
+    """The search's stability check: from seeded white noise with the source silent, a HORK
+    setting far outside its stability region grows, while a Faber setting whose ellipse
+    encloses the spectrum does not (the PML only removes energy)."""
+    from paper_2401_16322_gb300 import Batch
+    from paper_2401_16322_gb300.tts import leapfrog_step, noise_growth
+    oms, gms, _ = _models("f32", 1)
+    for g, om in zip(gms, oms):
+        g.set_faber_ellipse(*oracle_ellipse(om))
+    B = Batch(gms)
+    dt = 3.0 * leapfrog_step(float(max(om.c_max for om in oms)), oms[0].dx)
+    grow_hork = noise_growth(gms, B, "hork", 6, dt, t_quiet=5.0, nsteps=60)
+    grow_faber = noise_growth(gms, B, "faber", 40, dt, t_quiet=5.0, nsteps=60)
+    assert grow_hork > 10.0
+    assert grow_faber <= 2.0
