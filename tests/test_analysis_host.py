@@ -51,3 +51,23 @@ def test_faber_converges_to_the_exponential_inside_the_ellipse():
 def test_rk44_dissipates_and_lags():
     d, p = dispersion_dissipation("rk44", 0, 0.5, 2.0)        # omega dt up to 1
     assert 1e-4 < d < 2e-2 and 1e-5 < p < 1e-2
+
+
+def test_hork_stability_edge_on_a_dense_spectrum():
+    """The white-noise check of the step search rejects HORK settings whose amplification
+    exceeds 1 on the discrete spectrum.  On the dense spectrum of a small layered PML model
+    (oracle operator, FP64) HORK 16 is stable at 2x the leap-frog step, marginal at 3x and
+    unstable at 4x: its Taylor polynomial leaves the unit disk near omega dt = 6 on the
+    imaginary axis, and the top of the spectrum approaches 2 / leap-frog step."""
+    from oracle.model import Model, default_beta0
+    from oracle.operator import assemble_H
+    from paper_2401_16322_gb300.tts import leapfrog_step
+    from paper_2401_16322_gb300.workloads import layered
+    c = layered(30, 22, 5, vmin=1500, vmax=4500)
+    m = Model(30, 22, 10.0, 8, 5, default_beta0(float(c.max()), 5, 10.0), True, c)
+    ev = np.linalg.eigvals(assemble_H(m).toarray())
+    dt_lf = leapfrog_step(float(c.max()), 10.0)
+    top = np.abs(ev.imag).max() * dt_lf
+    assert 1.8 < top < 2.0
+    grow = [np.abs(amplification("hork", 16, ev / 1j, k * dt_lf)).max() for k in (2, 3, 4)]
+    assert grow[0] < 1.001 and grow[1] < 1.05 and grow[2] > 1.3
