@@ -63,6 +63,8 @@ def parse():
                     help="small / medium: the 1001x501 model with 4 / 16 shots (profiling); "
                          "cube: only the 3D side run (--n3d, --check3d)")
     ap.add_argument("--check3d", type=int, default=96, help="edge of the 3D accuracy cube")
+    ap.add_argument("--hork-form", default="horner", choices=["horner", "low-storage"],
+                    help="evaluation order of the HORK polynomial")
     return ap.parse_args()
 
 
@@ -132,12 +134,13 @@ def measured_peaks():
 TMA_SOURCE = os.path.join(ROOT, "paper_2401_16322_gb300", "csrc", "kernels_tma.cu")
 
 
-def ncu_traffic_per_point(method):
+def ncu_traffic_per_point(method, hork_form="horner"):
     """DRAM bytes per grid point of one steady-state stencil pass of ``method`` (a Faber
-    degree j >= 2 or a HORK stage i >= 2) from the committed ncu summary, or None when there
-    is none or the TMA kernel source changed since the capture."""
+    degree j >= 2 or a HORK pass after the first) from the committed ncu summary, or None
+    when there is none or the TMA kernel source changed since the capture."""
     import hashlib
-    summary = os.path.join(ROOT, "profiles", f"stage_tma_kernel_{method}_1001x501x16.md")
+    name = f"hork_{hork_form.replace('-', '_')}" if method == "hork" else method
+    summary = os.path.join(ROOT, "profiles", f"stage_tma_kernel_{name}_1001x501x16.md")
     try:
         with open(TMA_SOURCE, "rb") as f:
             sha = hashlib.sha256(f.read()).hexdigest()
@@ -154,11 +157,13 @@ def ncu_traffic_per_point(method):
         return None
 
 
-def pass_words(method, m):
+def pass_words(method, m, hork_form="horner"):
     """Algorithmic FP32 words per grid point of each fused stencil pass of one step
     (reads + writes; c^2 counted once per pass)."""
     if method == "faber":
         return [13] + [21] * (m - 1) if m >= 2 else [13]
+    if method == "hork" and hork_form == "horner":
+        return [9] + [13] * (m - 1)      # V_m: X, c^2 -> Y; then V_{j+1}, c^2, V_0 -> V_j
     if method == "hork":
         return [13] + [17] * (m - 1) if m >= 2 else [9]
     if method == "rk32":
@@ -434,7 +439,7 @@ def pass_words3d(method, m):
     if method == "faber":
         return [16] + [26] * (m - 1) if m >= 2 else [16]
     if method == "hork":
-        return [16] + [21] * (m - 1) if m >= 2 else [11]
+        return [11] + [16] * (m - 1)     # Horner form (the default)
     raise ValueError(method)
 
 
@@ -533,6 +538,8 @@ def run_ours(args):
     t_setup = time.perf_counter()
     models = build_models(wl, "f32", p=12, c_max=c_max)
     common_ellipse(models, c_max)
+    for md in models:
+        md.set_hork_form(args.hork_form)
     batch = Batch(models)
     if args.variant >= 0:
         batch.set_kernel_variant(args.variant)
@@ -600,7 +607,7 @@ def run_ours(args):
         ms_per_step = float(t.item())
 
     # roofline of the fused stencil pass (live, CUDA events around every launch)
-    words = pass_words(method, m)
+    words = pass_words(method, m, args.hork_form)
     alg_bytes_per_step = sum(words) * 4.0 * pts
     per_launch_bytes = alg_bytes_per_step / len(words)
     avg_launch_ms = kern_ms / max(kern_n, 1)
@@ -662,6 +669,7 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD_NAME if args.case == "full" else f"{args.case}: 1001x501, {wl[0].shots.__len__()} shots",
                        "method": method, "m": m, "dt_ms": dt * 1e3,
+                       "hork_form": args.hork_form if method == "hork" else None,
                        "dt_over_leapfrog_step": dt / dt_cfl, "nsteps": nsteps, "T_s": T_run,
                        "grid_points": pts, "problems": sum(len(w.shots) for w in wl),
                        "l2": "inputs larger than L2 (state + workspace > 1 GB)",
@@ -671,7 +679,7 @@ def run_ours(args):
             "grid_point_updates_per_s": pts * nsteps / (ms_per_step / 1e3),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
-                         "traffic": (tpp * pts if (tpp := ncu_traffic_per_point(method)) else None),
+                         "traffic": (tpp * pts if (tpp := ncu_traffic_per_point(method, args.hork_form)) else None),
                          "peak_kind": peak_kind,
                          "kernel": "stage_tma_kernel (persistent TMA fused stencil pass, FP32)",
                          "variant": batch.kernel_variant(),

@@ -231,6 +231,21 @@ int ewv_set_krylov_window(ewv_model_t model, int window);
  * (EWV_METHOD_RK32 / EWV_METHOD_RK44; stages ignored). */
 int ewv_step_rk(ewv_model_t model, double t, double dt, int scheme, int stages, int nsteps);
 
+/* Evaluation order of HORK(m) (Sec. 3.2).  For the linear system one HORK step is the
+ * degree-m Taylor polynomial of exp(dt H~) applied to [u^n; e_p]; both forms compute it with
+ * m operator passes and agree up to rounding.
+ *   EWV_HORK_HORNER (default): V_j = V_0 + (dt/j) H~ V_{j+1}, j = m .. 1, V_{m+1} = V_0,
+ *     u^{n+1} = V_1.  A pass reads V_{j+1}, V_0 and c^2 and writes V_j (13 FP32 words per
+ *     grid point).
+ *   EWV_HORK_LOW_STORAGE: the paper's low-storage stages k_i = (I + dt H~) k_{i-1} with the
+ *     accumulator sum_i lambda_i k_i (17 words per point; its large alternating lambda_i
+ *     cancel, which costs accuracy at high m and in reduced storage precision).
+ * The setting drops the model's captured step graphs; a batch uses its first model's form.
+ * Returns EWV_ERR_INVALID_ARG for an unknown form. */
+#define EWV_HORK_HORNER 0
+#define EWV_HORK_LOW_STORAGE 1
+int ewv_set_hork_form(ewv_model_t model, int form);
+
 /* Sec. 3.1 leap-frog.  The state's u, w_x, w_y hold time level n; the previous level lives
  * in the workspace and is initialised from the state on the first call after a state
  * change (u^{-1} = u^0, w^{-1} = w^0).  The v field is not advanced. */

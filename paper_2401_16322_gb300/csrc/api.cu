@@ -32,7 +32,11 @@ namespace {
 
 const char* kVersion = "ewave-gb300 0.1 (sm_103a)";
 
-enum { PRO_FABER = 1, PRO_KRYLOV = 2, PRO_HORK = 3, PRO_RK32 = 4, PRO_RK44 = 5, PRO_LEAPFROG = 6 };
+// Field mask of whole state vectors for the copy pass (bit f = field f; 2D uses bits 0..3).
+constexpr int ALL_FIELDS = 0x1F;
+
+enum { PRO_FABER = 1, PRO_KRYLOV = 2, PRO_HORK = 3, PRO_RK32 = 4, PRO_RK44 = 5, PRO_LEAPFROG = 6,
+       PRO_HORK_HORNER = 7 };
 enum { FIN_NONE = 0, FIN_NORM0 = 1, FIN_MATVEC = 2, FIN_MGS = 3 };
 
 // ---------------------------------------------------------------- stencil tables
@@ -157,6 +161,7 @@ struct ewv_model {
     int lf_variant = EWV_LEAPFROG_AVERAGED;
     int store_bf16 = 0;         // storage-precision experiment (ewv_set_storage_rounding)
     int kry_window = 0;         // Krylov orthogonalisation window (0 = full Gram-Schmidt)
+    int hork_form = EWV_HORK_HORNER;   // evaluation order of the HORK polynomial
     bool lf_history_valid = false;
     // device metadata
     int* d_rec = nullptr;
@@ -775,7 +780,7 @@ int run_faber(Ctx& C, double t, double dt, int m, int nsteps, double g, double c
         s1.cax = a[0];
         C.stage(s1);
         if (m == 1) {
-            C.copy(2, 0, 0xF, false);
+            C.copy(2, 0, ALL_FIELDS, false);
         } else {
             StageArgs s2 = stage_defaults();
             s2.x = 1;
@@ -834,9 +839,48 @@ std::vector<double> hork_lambdas(int m) {
     return lam;
 }
 
+// HORK(m) in Horner form: the same degree-m Taylor polynomial of exp(dt H~) as the
+// low-storage stages below, evaluated as V_{m+1} = V_0, V_j = V_0 + (dt/j) H~ V_{j+1}
+// (j = m .. 1), U^{n+1} = V_1.  Each pass reads V_{j+1} (with halo), V_0 and c^2 and writes
+// V_j: 13 words per point against 17 for a stage with an accumulator, and no cancellation
+// between large coefficients.  Work vectors 1 and 2 alternate; the last pass writes the
+// state in place (V_0 is read only at the point being written).
+int run_hork_horner(Ctx& C, double t, double dt, int m, int nsteps) {
+    launch_set_clock(C.E->d_probs, C.E->nprob, t, dt, C.s);
+    ++*C.launches;
+    int rc = C.step_loop(nsteps, EWV_METHOD_HORK, m, dt, 0, 0, 0, 1, [&](int) {
+        C.prologue(PRO_HORK_HORNER, m);
+        int prev = 0;
+        for (int k = 0; k < m; ++k) {
+            const int j = m - k;
+            StageArgs s = stage_defaults();
+            s.x = prev;
+            s.src_slot = k;
+            s.ch = dt / (double)j;
+            s.ck = 1.0;
+            if (k == 0) {
+                s.cx = 1.0;                     // V_m = V_0 + (dt/m) H~ V_0
+            } else {
+                s.cx = 0.0;
+                s.u = 0;
+                s.cu = 1.0;
+            }
+            s.y_out = (j == 1 && k > 0) ? 0 : (prev == 1 ? 2 : 1);
+            C.stage(s);
+            prev = s.y_out;
+        }
+        if (prev != 0) C.copy(prev, 0, ALL_FIELDS, false);   // m = 1: V_1 is in a work vector
+        C.record();
+    });
+    if (rc != EWV_OK) return rc;
+    return check_launch(*C.err);
+}
+
 int run_hork(Ctx& C, double t, double dt, int m, int nsteps) {
     std::string& err = *C.err;
     if (m < 1 || m > MAX_SIGMA) return fail(err, EWV_ERR_INVALID_ARG, "HORK stages must be 1..%d", MAX_SIGMA);
+    if (!C.E->models.empty() && C.E->models[0]->hork_form == EWV_HORK_HORNER)
+        return run_hork_horner(C, t, dt, m, nsteps);
     const std::vector<double> lam = hork_lambdas(m);
     auto wgt = [&](int i) { return i <= m - 2 ? lam[i] : (i == m - 1 ? 0.0 : lam[m - 1]); };
     launch_set_clock(C.E->d_probs, C.E->nprob, t, dt, C.s);
@@ -853,7 +897,7 @@ int run_hork(Ctx& C, double t, double dt, int m, int nsteps) {
             s1.ck = 1.0;
             s1.cay = lam[0];
             C.stage(s1);
-            C.copy(1, 0, 0xF, false);
+            C.copy(1, 0, ALL_FIELDS, false);
             C.record();
             return;
         }
@@ -1560,6 +1604,15 @@ int ewv_set_krylov_window(ewv_model_t m, int window) {
     if (!m || window < 0) return EWV_ERR_INVALID_ARG;
     if (m->kry_window != window) {
         m->kry_window = window;
+        ++m->version;   // drops the captured step graphs
+    }
+    return EWV_OK;
+}
+
+int ewv_set_hork_form(ewv_model_t m, int form) {
+    if (!m || (form != EWV_HORK_HORNER && form != EWV_HORK_LOW_STORAGE)) return EWV_ERR_INVALID_ARG;
+    if (m->hork_form != form) {
+        m->hork_form = form;
         ++m->version;   // drops the captured step graphs
     }
     return EWV_OK;

@@ -44,13 +44,16 @@ __device__ __forceinline__ double ricker(double t, double f, double t0) {
     return (1.0 - 2.0 * a * tau * tau) * exp(-a * tau * tau);
 }
 
-enum { PRO_FABER = 1, PRO_KRYLOV = 2, PRO_HORK = 3, PRO_RK32 = 4, PRO_RK44 = 5, PRO_LEAPFROG = 6 };
+enum { PRO_FABER = 1, PRO_KRYLOV = 2, PRO_HORK = 3, PRO_RK32 = 4, PRO_RK44 = 5, PRO_LEAPFROG = 6,
+       PRO_HORK_HORNER = 7 };
 
 // One warp per problem.  Fills sigma[] (the value added at the source node's v entry in
 // each pass of this step) from t_n = t_start + step * dt:
 //   Faber: sigma_j = W . y_j, y_0 = e_p, y_1 = F1 y_0, y_2 = F1 y_1 - 2 c1 y_0,
 //          y_j = F1 y_{j-1} - c1 y_{j-2}, F1 = (J/dt)/gamma - c0 (tail of Eq. matrix_ampli)
 //   HORK:  sigma_i = W . (I + J)^i e_p
+//   HORK in Horner form (passes j = m .. 1): sigma_k = W . y_{j+1} with j = m - k,
+//          y_{m+1} = e_p, y_j = e_p + (1/j) J y_{j+1}
 //   RK3-2 / RK4-4 / leap-frog: f at the stage times
 //   Krylov: W stored for the Arnoldi passes
 // W[p-1-k] = dt^k r^(k)(t_n) amp / dx^2 (tail scaled by dt).  Lane q holds tail entry q;
@@ -107,6 +110,17 @@ __global__ void prologue_kernel(const ProblemDev* probs, int nprob, int kind, in
         return;
     }
     double y0 = (q == p - 1) ? 1.0 : 0.0;
+    if (kind == PRO_HORK_HORNER) {
+        double y = y0;
+        for (int k = 0; k < m && k < MAX_SIGMA; ++k) {
+            const double s = warp_sum(W * y);
+            if (q == 0) sg[k] = s;
+            double up = __shfl_down_sync(0xffffffffu, y, 1);
+            if (q + 1 >= p) up = 0.0;
+            y = ((q == p - 1) ? 1.0 : 0.0) + up / (double)(m - k);
+        }
+        return;
+    }
     if (kind == PRO_HORK) {
         // y_i = (I + J) y_{i-1}
         for (int i = 0; i < m && i < MAX_SIGMA; ++i) {

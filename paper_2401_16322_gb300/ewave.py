@@ -40,6 +40,7 @@ EXPORTS = [
     "ewv_set_kernel_variant", "ewv_kernel_variant", "ewv_batch_set_kernel_variant",
     "ewv_batch_kernel_variant", "ewv_set_source_receivers3d", "ewv_set_storage_rounding",
     "ewv_set_krylov_window",
+    "ewv_set_hork_form",
 ]
 
 
@@ -105,6 +106,7 @@ def load_library(path=LIB_PATH):
         "ewv_set_source_receivers3d": ([vp, i, d, d, d, d, d, d, i, dp, ip32, ip32], i),
         "ewv_set_storage_rounding": ([vp, i], i),
         "ewv_set_krylov_window": ([vp, i], i),
+        "ewv_set_hork_form": ([vp, i], i),
         "ewv_set_faber_ellipse": ([vp, d, d, d], i),
         "ewv_get_faber_ellipse": ([vp, dp, dp, dp], i),
         "ewv_set_state": ([vp, i, dp, sz], i),
@@ -261,6 +263,11 @@ class Model:
             si.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
             ri.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))), "set_source_receivers3d")
         return si, ri[:3 * nrec].reshape(nrec, 3)
+
+    def set_hork_form(self, form):
+        """'horner' (default) or 'low-storage' evaluation of the HORK polynomial."""
+        code = {"horner": 0, "low-storage": 1}[form]
+        self._check(self.lib.ewv_set_hork_form(self.h, code), "hork_form")
 
     def set_krylov_window(self, q):
         """Orthogonalise each Krylov vector against the q most recent ones only (0: all)."""

@@ -142,3 +142,32 @@ def test_krylov_with_orthogonalisation_window_matches_oracle(prec, m, q):
         U = krylov.krylov_step(om, U, src, t + n * dt, dt, m, window=q)
     err = rel_l2(gs, flatten(U))
     assert err < TOL[prec] * (3 if prec == "f32" else 1), (m, q, err)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("form", ["horner", "low-storage"])
+@pytest.mark.parametrize("m,k", [(1, 0.3), (2, 0.5), (7, 1.0), (24, 5.0)])
+def test_hork_forms_match_oracle(prec, form, m, k):
+    """Both evaluation orders of HORK(m) (Horner: V_j = V_0 + (dt/j) H~ V_{j+1}; the paper's
+    low-storage stages with lambda_i) equal the oracle's HORK step, with the source active,
+    up to k times the leap-frog step (m = 24 at 5x: the setting the step search selects)."""
+    from paper_2401_16322_gb300.tts import leapfrog_step
+    om, g, src, rec, rn, U0 = _setup(prec)
+    g.set_hork_form(form)
+    dt = k * leapfrog_step(om.c_max, om.dx)
+    t, nsteps = 0.03, 3
+    gs, _ = _gpu_run(g, U0, "hork", t, dt, m, nsteps, nsteps)
+    U, S = run(om, "hork", dt, nsteps, src=src, rec_nodes=rn, m=m, U0=U0, t0=t)
+    err = rel_l2(gs, flatten(U))
+    assert err < TOL[prec] * (3 if prec == "f32" else 1), (form, m, err)
+    assert rel_l2(g.seismogram(0, len(rec), nsteps), S) < TOL[prec] * (3 if prec == "f32" else 1)
+
+
+def test_hork_horner_and_low_storage_agree_fp64():
+    om, g, src, rec, rn, U0 = _setup("f64")
+    out = []
+    for form in ("low-storage", "horner", "low-storage"):
+        g.set_hork_form(form)
+        out.append(_gpu_run(g, U0, "hork", 0.03, 4e-3, 16, 4, 4)[0])
+    assert np.array_equal(out[0], out[2])           # switching back restores the same graph
+    assert rel_l2(out[1], out[0]) < 1e-13
