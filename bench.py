@@ -63,8 +63,6 @@ def parse():
                     help="small / medium: the 1001x501 model with 4 / 16 shots (profiling); "
                          "cube: only the 3D side run (--n3d, --check3d)")
     ap.add_argument("--check3d", type=int, default=96, help="edge of the 3D accuracy cube")
-    ap.add_argument("--hork-form", default="horner", choices=["horner", "low-storage"],
-                    help="evaluation order of the HORK polynomial")
     return ap.parse_args()
 
 
@@ -134,12 +132,12 @@ def measured_peaks():
 TMA_SOURCE = os.path.join(ROOT, "paper_2401_16322_gb300", "csrc", "kernels_tma.cu")
 
 
-def ncu_traffic_per_point(method, hork_form="horner"):
+def ncu_traffic_per_point(method):
     """DRAM bytes per grid point of one steady-state stencil pass of ``method`` (a Faber
     degree j >= 2 or a HORK pass after the first) from the committed ncu summary, or None
     when there is none or the TMA kernel source changed since the capture."""
     import hashlib
-    name = f"hork_{hork_form.replace('-', '_')}" if method == "hork" else method
+    name = {"hork": "hork_low_storage", "hork-horner": "hork_horner"}.get(method, method)
     summary = os.path.join(ROOT, "profiles", f"stage_tma_kernel_{name}_1001x501x16.md")
     try:
         with open(TMA_SOURCE, "rb") as f:
@@ -157,12 +155,12 @@ def ncu_traffic_per_point(method, hork_form="horner"):
         return None
 
 
-def pass_words(method, m, hork_form="horner"):
+def pass_words(method, m):
     """Algorithmic FP32 words per grid point of each fused stencil pass of one step
     (reads + writes; c^2 counted once per pass)."""
     if method == "faber":
         return [13] + [21] * (m - 1) if m >= 2 else [13]
-    if method == "hork" and hork_form == "horner":
+    if method == "hork-horner":
         return [9] + [13] * (m - 1)      # V_m: X, c^2 -> Y; then V_{j+1}, c^2, V_0 -> V_j
     if method == "hork":
         return [13] + [17] * (m - 1) if m >= 2 else [9]
@@ -170,7 +168,7 @@ def pass_words(method, m, hork_form="horner"):
         return [13, 13, 13]
     if method == "rk44":
         return [17, 21, 21, 13]
-    if method == "krylov":
+    if method.startswith("krylov"):
         return [13] * m     # x (4) + c^2 (1) + y (4) + dot partner (4)
     if method == "leapfrog":
         return [10]
@@ -197,14 +195,16 @@ def cpu_oracle_sample(workloads, method, m, dt, budget_s, log=log):
     t0 = time.perf_counter()
     nsteps = 0
     U = om.zeros_state()
+    # the oracle evaluates HORK in the paper's stages and Krylov with full orthogonalisation
+    om_method = "hork" if method == "hork-horner" else ("krylov" if method.startswith("krylov") else method)
     while True:
-        U, _ = run(om, method, dt, 1, src=src, m=m, U0=U, t0=0.3 + nsteps * dt, faber_params=params)
+        U, _ = run(om, om_method, dt, 1, src=src, m=m, U0=U, t0=0.3 + nsteps * dt, faber_params=params)
         nsteps += 1
         if time.perf_counter() - t0 >= budget_s:
             break
     el = time.perf_counter() - t0
     per_point_step = el / (nsteps * w.nx * w.ny)
-    desc = (f"oracle {method}(m={m}, dt={dt * 1e3:.3f} ms) FP64, {nsteps} steps of one shot on "
+    desc = (f"oracle {om_method}(m={m}, dt={dt * 1e3:.3f} ms) FP64, {nsteps} steps of one shot on "
             f"{w.nx}x{w.ny} ({el:.1f} s), scaled by grid-point-steps to the whole batch")
     return per_point_step, desc, 1
 
@@ -217,7 +217,7 @@ def fp64_single_shot_estimate(wl, method, m, dt, nsteps, c_max, steps_sample=3):
     """The plain FP64 single-shot form of the selected method: every model alone, one shot,
     timed for a few steps and scaled to all shots and steps (seconds)."""
     import torch
-    from paper_2401_16322_gb300.tts import build_models, common_ellipse
+    from paper_2401_16322_gb300.tts import base_method, build_models, common_ellipse
     from paper_2401_16322_gb300.workloads import Workload
     total = 0.0
     for w in wl:
@@ -225,6 +225,7 @@ def fp64_single_shot_estimate(wl, method, m, dt, nsteps, c_max, steps_sample=3):
                        w.f_peak, w.T)
         md = build_models([one], "f64", p=12, c_max=c_max)[0]
         common_ellipse([md], c_max)
+        method = base_method([md], method)
         md.ensure_workspace(method, m)
         md.step(method, 0.25, dt, m, 1)
         torch.cuda.synchronize()
@@ -246,9 +247,9 @@ def fwi_gradient_step(method, m, dt_over_cfl):
     import numpy as np
     import torch
     from paper_2401_16322_gb300.fwi import FaberFWI
-    from paper_2401_16322_gb300.tts import build_models, common_ellipse, leapfrog_step
+    from paper_2401_16322_gb300.tts import base_method, build_models, common_ellipse, leapfrog_step
     from paper_2401_16322_gb300.workloads import config_fwi, smooth_gradient_with_anomalies
-    if method not in ("faber", "hork", "krylov"):
+    if method not in ("faber", "hork", "hork-horner", "krylov"):
         return None
     w = config_fwi()
     c_max = float(w.c.max()) * 1.05
@@ -256,7 +257,7 @@ def fwi_gradient_step(method, m, dt_over_cfl):
     nsteps = int(round(w.T / dt))
     md = build_models([w], "f32", p=12, c_max=c_max)[0]
     common_ellipse([md], c_max)
-    fwi = FaberFWI(md, dt, m, nsteps, len(w.shots[0].rec), method=method)
+    fwi = FaberFWI(md, dt, m, nsteps, len(w.shots[0].rec), method=base_method([md], method))
     d_obs = fwi.forward(w.c ** 2)
     c_init = smooth_gradient_with_anomalies(w.nx, w.ny, 0, dx=w.dx, amps=())
     fwi.forward(c_init ** 2)
@@ -279,6 +280,7 @@ def fwi_gradient_step(method, m, dt_over_cfl):
 # Delta-t_max scan of the 3D side run: (method, m values, step multiples, largest first)
 SCAN3D = (("faber", (30, 40, 50, 60), tuple(range(24, 1, -1))),
           ("hork", (12, 16, 24), tuple(range(12, 0, -1))),
+          ("hork-horner", (12, 16, 24), tuple(range(12, 0, -1))),
           ("krylov", (20,), tuple(range(24, 1, -1))))
 LEAPFROG3D_DIVISORS = (1, 2, 3, 4, 6, 8)
 
@@ -297,7 +299,8 @@ def config5_3d(n=400, check_n=96, target=TARGET):
     import numpy as np
     import torch
     from paper_2401_16322_gb300 import Model
-    from paper_2401_16322_gb300.tts import dt_max_scan, leapfrog_step, pml_beta0, rel_l2_common
+    from paper_2401_16322_gb300.tts import (base_method, dt_max_scan, leapfrog_step, pml_beta0,
+                                            rel_l2_common)
     from paper_2401_16322_gb300.workloads import config_3d, t0_for
     c_max = 4500.0
 
@@ -313,7 +316,7 @@ def config5_3d(n=400, check_n=96, target=TARGET):
         nsteps = int(round(T / dt))
         md.bind_seismogram(nsteps)
         md.reset_state()
-        md.step(method, 0.0, dt, m, nsteps)
+        md.step(base_method([md], method), 0.0, dt, m, nsteps)
         return md.seismogram(0, md.max_receivers, nsteps)
 
     out = {"workload": f"{n}^3 layered, dx 10 m, 8th order, free surface, 30-pt ABC, Ricker 10 Hz, "
@@ -386,17 +389,18 @@ def config5_3d(n=400, check_n=96, target=TARGET):
                 md = None
                 md64 = build(w, "f64")
             dev, prec, method = md64, "f64", "leapfrog"
-        dev.ensure_workspace(method, m)
+        bm = base_method([dev], method)
+        dev.ensure_workspace(bm, m)
         dev.reset_state()
         try:
-            dev.step(method, t_live - 2 * dt, dt, m, 2)
+            dev.step(bm, t_live - 2 * dt, dt, m, 2)
             torch.cuda.synchronize()
             dev.enable_kernel_timing(True)
             dev.kernel_timing()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             ns = 4
             e0.record()
-            dev.step(method, t_live, dt, m, ns)
+            dev.step(bm, t_live, dt, m, ns)
             e1.record()
             torch.cuda.synchronize()
             kms, kn = dev.kernel_timing()
@@ -411,11 +415,11 @@ def config5_3d(n=400, check_n=96, target=TARGET):
                 "time_to_T_s": step_ms * nsteps * 1e-3,
                 "grid_point_updates_per_s": n ** 3 / (step_ms * 1e-3),
                 "seismo_rel_err_vs_fp64": err}
-        if method == "faber" and kn and prec == "f32":
+        if method in ("faber", "hork-horner") and kn and prec == "f32":
             words = pass_words3d(method, m)
             per_launch = sum(words) * 4.0 * n ** 3 / len(words)
             avg = kms / kn * 1e-3
-            cand["roofline"] = {"bound": "hbm", "kernel": "stage_tma3d_kernel (FP32, 16 warps)",
+            cand["roofline"] = {"bound": "hbm", "kernel": "stage_tma3d_kernel (FP32)",
                                 "achieved": per_launch / avg / 1e9, "peak": peak, "unit": "GB/s",
                                 "frac": per_launch / avg / 1e9 / peak, "peak_kind": peak_kind,
                                 "avg_launch_us": avg * 1e6, "alg_bytes_per_launch": per_launch}
@@ -438,8 +442,10 @@ def pass_words3d(method, m):
     """Algorithmic FP32 words per point of each 3D stencil pass (five fields)."""
     if method == "faber":
         return [16] + [26] * (m - 1) if m >= 2 else [16]
+    if method == "hork-horner":
+        return [11] + [16] * (m - 1)
     if method == "hork":
-        return [11] + [16] * (m - 1)     # Horner form (the default)
+        return [16] + [21] * (m - 1) if m >= 2 else [11]
     raise ValueError(method)
 
 
@@ -538,8 +544,6 @@ def run_ours(args):
     t_setup = time.perf_counter()
     models = build_models(wl, "f32", p=12, c_max=c_max)
     common_ellipse(models, c_max)
-    for md in models:
-        md.set_hork_form(args.hork_form)
     batch = Batch(models)
     if args.variant >= 0:
         batch.set_kernel_variant(args.variant)
@@ -607,7 +611,7 @@ def run_ours(args):
         ms_per_step = float(t.item())
 
     # roofline of the fused stencil pass (live, CUDA events around every launch)
-    words = pass_words(method, m, args.hork_form)
+    words = pass_words(method, m)
     alg_bytes_per_step = sum(words) * 4.0 * pts
     per_launch_bytes = alg_bytes_per_step / len(words)
     avg_launch_ms = kern_ms / max(kern_n, 1)
@@ -669,7 +673,6 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD_NAME if args.case == "full" else f"{args.case}: 1001x501, {wl[0].shots.__len__()} shots",
                        "method": method, "m": m, "dt_ms": dt * 1e3,
-                       "hork_form": args.hork_form if method == "hork" else None,
                        "dt_over_leapfrog_step": dt / dt_cfl, "nsteps": nsteps, "T_s": T_run,
                        "grid_points": pts, "problems": sum(len(w.shots) for w in wl),
                        "l2": "inputs larger than L2 (state + workspace > 1 GB)",
@@ -679,7 +682,7 @@ def run_ours(args):
             "grid_point_updates_per_s": pts * nsteps / (ms_per_step / 1e3),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
-                         "traffic": (tpp * pts if (tpp := ncu_traffic_per_point(method, args.hork_form)) else None),
+                         "traffic": (tpp * pts if (tpp := ncu_traffic_per_point(method)) else None),
                          "peak_kind": peak_kind,
                          "kernel": "stage_tma_kernel (persistent TMA fused stencil pass, FP32)",
                          "variant": batch.kernel_variant(),

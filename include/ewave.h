@@ -234,12 +234,12 @@ int ewv_step_rk(ewv_model_t model, double t, double dt, int scheme, int stages, 
 /* Evaluation order of HORK(m) (Sec. 3.2).  For the linear system one HORK step is the
  * degree-m Taylor polynomial of exp(dt H~) applied to [u^n; e_p]; both forms compute it with
  * m operator passes and agree up to rounding.
- *   EWV_HORK_HORNER (default): V_j = V_0 + (dt/j) H~ V_{j+1}, j = m .. 1, V_{m+1} = V_0,
- *     u^{n+1} = V_1.  A pass reads V_{j+1}, V_0 and c^2 and writes V_j (13 FP32 words per
- *     grid point).
- *   EWV_HORK_LOW_STORAGE: the paper's low-storage stages k_i = (I + dt H~) k_{i-1} with the
- *     accumulator sum_i lambda_i k_i (17 words per point; its large alternating lambda_i
- *     cancel, which costs accuracy at high m and in reduced storage precision).
+ *   EWV_HORK_LOW_STORAGE (default): the paper's low-storage stages k_i = (I + dt H~) k_{i-1}
+ *     with the accumulator sum_i lambda_i k_i (17 FP32 words per grid point and pass).
+ *   EWV_HORK_HORNER: V_j = V_0 + (dt/j) H~ V_{j+1}, j = m .. 1, V_{m+1} = V_0,
+ *     u^{n+1} = V_1.  A pass reads V_{j+1}, V_0 and c^2 and writes V_j (13 words).  Rounding
+ *     made in pass j reaches the result multiplied by (dt H~)^(j-1)/(j-1)!, so in FP32 at
+ *     large steps (|dt lambda| near 10) it is less accurate than the low-storage form.
  * The setting drops the model's captured step graphs; a batch uses its first model's form.
  * Returns EWV_ERR_INVALID_ARG for an unknown form. */
 #define EWV_HORK_HORNER 0

@@ -36,7 +36,7 @@ def faber_coefficients(dt, gamma, c0, c1, m, nodes=None):
 def amplification(method, m, omega, dt, ellipse=None):
     """R(i omega dt) of ``method`` (faber needs ``ellipse`` = (gamma, c0, c1))."""
     z = 1j * np.asarray(omega, dtype=np.float64) * dt
-    if method == "hork":
+    if method in ("hork", "hork-horner"):      # the same polynomial, either evaluation order
         out, term = np.ones_like(z), np.ones_like(z)
         for k in range(1, m + 1):
             term = term * z / k

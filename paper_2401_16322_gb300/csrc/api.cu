@@ -161,7 +161,7 @@ struct ewv_model {
     int lf_variant = EWV_LEAPFROG_AVERAGED;
     int store_bf16 = 0;         // storage-precision experiment (ewv_set_storage_rounding)
     int kry_window = 0;         // Krylov orthogonalisation window (0 = full Gram-Schmidt)
-    int hork_form = EWV_HORK_HORNER;   // evaluation order of the HORK polynomial
+    int hork_form = EWV_HORK_LOW_STORAGE;   // evaluation order of the HORK polynomial
     bool lf_history_valid = false;
     // device metadata
     int* d_rec = nullptr;
@@ -842,8 +842,9 @@ std::vector<double> hork_lambdas(int m) {
 // HORK(m) in Horner form: the same degree-m Taylor polynomial of exp(dt H~) as the
 // low-storage stages below, evaluated as V_{m+1} = V_0, V_j = V_0 + (dt/j) H~ V_{j+1}
 // (j = m .. 1), U^{n+1} = V_1.  Each pass reads V_{j+1} (with halo), V_0 and c^2 and writes
-// V_j: 13 words per point against 17 for a stage with an accumulator, and no cancellation
-// between large coefficients.  Work vectors 1 and 2 alternate; the last pass writes the
+// V_j: 13 words per point against 17 for a stage with an accumulator.  Rounding made in
+// pass j reaches the result multiplied by (dt H~)^(j-1)/(j-1)!, which is large on the top of
+// the spectrum at large steps.  Work vectors 1 and 2 alternate; the last pass writes the
 // state in place (V_0 is read only at the point being written).
 int run_hork_horner(Ctx& C, double t, double dt, int m, int nsteps) {
     launch_set_clock(C.E->d_probs, C.E->nprob, t, dt, C.s);

@@ -265,7 +265,8 @@ class Model:
         return si, ri[:3 * nrec].reshape(nrec, 3)
 
     def set_hork_form(self, form):
-        """'horner' (default) or 'low-storage' evaluation of the HORK polynomial."""
+        """'low-storage' (default, the paper's stages) or 'horner' evaluation of the HORK
+        polynomial (fewer bytes per pass, less accurate in FP32 at large steps)."""
         code = {"horner": 0, "low-storage": 1}[form]
         self._check(self.lib.ewv_set_hork_form(self.h, code), "hork_form")
 

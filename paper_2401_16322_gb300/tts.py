@@ -15,7 +15,8 @@ For a workload (a list of velocity models with shots and surface receivers) this
 
 Faber degree 20..120 is scanned up to 32 x the leap-frog step, Krylov dimension 10..40 up to
 24 x (the paper's grid is 4..16 x), Krylov 20..40 with an orthogonalisation window of 2
-("krylov-w2"), HORK 8..32 up to 12 x; leap-frog itself, in FP32 and in FP64, at
+("krylov-w2"), HORK 8..32 up to 12 x in its low-storage form and in Horner form
+("hork-horner"); leap-frog itself, in FP32 and in FP64, at
 1 .. 1/32 of its step (largest passing step).
 """
 import math
@@ -89,11 +90,15 @@ def common_ellipse(models, c_max):
 
 def base_method(models, method):
     """Map a candidate method name to the library's: "krylov-wQ" is Krylov with an
-    orthogonalisation window of Q (set on every model; every other name resets it)."""
+    orthogonalisation window of Q, "hork-horner" HORK evaluated in Horner form (both set on
+    every model; every other name resets them)."""
     window = int(method[len("krylov-w"):]) if method.startswith("krylov-w") else 0
     for md in models:
         md.set_krylov_window(window)
-    return "krylov" if window else method
+        md.set_hork_form("horner" if method == "hork-horner" else "low-storage")
+    if window:
+        return "krylov"
+    return "hork" if method == "hork-horner" else method
 
 
 def simulate(models, batch, method, m, dt, T, variant=0):
@@ -166,6 +171,7 @@ SCAN_PLAN = (
     ("krylov", (10, 15, 20, 30, 40), tuple(range(24, 1, -1))),
     ("krylov-w2", (20, 30, 40), tuple(range(24, 1, -1))),
     ("hork", (8, 12, 16, 20, 24, 28, 32), tuple(range(12, 0, -1))),
+    ("hork-horner", (8, 12, 16, 20, 24, 28, 32), tuple(range(12, 0, -1))),
 )
 LEAPFROG_DIVISORS = (1, 2, 3, 4, 6, 8, 12, 16, 24, 32)
 # Stability check of the polynomial integrators: a setting that meets the error target must
@@ -174,7 +180,7 @@ LEAPFROG_DIVISORS = (1, 2, 3, 4, 6, 8, 12, 16, 24, 32)
 # sampled problems.
 NOISE_STEPS = 100
 NOISE_GROWTH = 10.0
-POLYNOMIAL = ("faber", "hork", "rk32", "rk44")
+POLYNOMIAL = ("faber", "hork", "hork-horner", "rk32", "rk44")
 
 
 def dt_max_scan(ks, evaluate, target):
@@ -317,7 +323,7 @@ def run_study(workloads: List[Workload], picks, T, target=1e-4, plan=SCAN_PLAN,
     # storage-precision experiment: for Faber and HORK, the passing FP32 (m, dt) with the
     # fewest passes per unit time, again on the sampled problems with every stored vector
     # rounded to bfloat16
-    for method in ("faber", "hork"):
+    for method in ("faber", "hork", "hork-horner"):
         passing_s = [c for c in cands if c.err <= target and c.method == method and precision == "f32"]
         if not passing_s:
             continue

@@ -88,12 +88,12 @@ def _oracle_steps(om, method, U0, src, t, dt, m, nsteps, rn):
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 @pytest.mark.parametrize("method,m", [("faber", 14), ("krylov", 10), ("hork", 6), ("rk32", 0),
                                       ("rk44", 0), ("leapfrog", 0), ("faber", 1), ("hork", 1),
-                                      ("hork-low-storage", 6), ("hork-low-storage", 1)])
+                                      ("hork-horner", 6), ("hork-horner", 1)])
 def test_integrators_match_oracle_3d(prec, method, m):
     """m = 1 covers the copy of a work vector into the state (all five fields)."""
     om, g, src, rec, rn, U0 = _setup(prec)
-    if method == "hork-low-storage":
-        g.set_hork_form("low-storage")
+    if method == "hork-horner":
+        g.set_hork_form("horner")
         method = "hork"
     if method in ("krylov", "leapfrog"):
         # displacement at rest (Krylov conditioning; leap-frog starts from u^{-1} = u^0)

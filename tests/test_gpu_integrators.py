@@ -145,12 +145,20 @@ def test_krylov_with_orthogonalisation_window_matches_oracle(prec, m, q):
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-@pytest.mark.parametrize("form", ["horner", "low-storage"])
+@pytest.mark.parametrize("form", ["low-storage", "horner"])
 @pytest.mark.parametrize("m,k", [(1, 0.3), (2, 0.5), (7, 1.0), (24, 5.0)])
 def test_hork_forms_match_oracle(prec, form, m, k):
-    """Both evaluation orders of HORK(m) (Horner: V_j = V_0 + (dt/j) H~ V_{j+1}; the paper's
-    low-storage stages with lambda_i) equal the oracle's HORK step, with the source active,
-    up to k times the leap-frog step (m = 24 at 5x: the setting the step search selects)."""
+    """Both evaluation orders of HORK(m) (the paper's low-storage stages with lambda_i;
+    Horner: V_j = V_0 + (dt/j) H~ V_{j+1}) equal the oracle's HORK step, with the source
+    active, up to k times the leap-frog step (m = 24 at 5x: the setting the step search
+    selects).
+
+    FP32 Horner bound: rounding made in pass j reaches the result multiplied by
+    (dt lambda)^(j-1)/(j-1)!, and |dt lambda| <= 2k on this spectrum (the top of the interior
+    spectrum is 2 / leap-frog step), so per step the error is at most about
+    2^-24 max_j (2k)^j / j!; the tolerance is the larger of that over the steps and the usual
+    FP32 one.  At k = 5 that is 5e-4 (measured 6.6e-5; the low-storage form 1.2e-6)."""
+    import math
     from paper_2401_16322_gb300.tts import leapfrog_step
     om, g, src, rec, rn, U0 = _setup(prec)
     g.set_hork_form(form)
@@ -158,9 +166,13 @@ def test_hork_forms_match_oracle(prec, form, m, k):
     t, nsteps = 0.03, 3
     gs, _ = _gpu_run(g, U0, "hork", t, dt, m, nsteps, nsteps)
     U, S = run(om, "hork", dt, nsteps, src=src, rec_nodes=rn, m=m, U0=U0, t0=t)
+    tol = TOL[prec] * (3 if prec == "f32" else 1)
+    if prec == "f32" and form == "horner":
+        gain = max((2 * k) ** j / math.factorial(j) for j in range(m + 1))
+        tol = max(tol, nsteps * 2.0 ** -24 * gain)
     err = rel_l2(gs, flatten(U))
-    assert err < TOL[prec] * (3 if prec == "f32" else 1), (form, m, err)
-    assert rel_l2(g.seismogram(0, len(rec), nsteps), S) < TOL[prec] * (3 if prec == "f32" else 1)
+    assert err < tol, (form, m, err, tol)
+    assert rel_l2(g.seismogram(0, len(rec), nsteps), S) < tol
 
 
 def test_hork_horner_and_low_storage_agree_fp64():
