@@ -262,16 +262,18 @@ def fwi_gradient_step(method, m, dt_over_cfl):
     c_init = smooth_gradient_with_anomalies(w.nx, w.ny, 0, dx=w.dx, amps=())
     fwi.forward(c_init ** 2)
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0, em, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
     e0.record()
     seis = fwi.forward(c_init ** 2)
+    em.record()
     grad = fwi.backward(seis - d_obs)
     e1.record()
     torch.cuda.synchronize()
     ok = bool(torch.isfinite(grad).all())
     mem = fwi.ckpt.numel() * fwi.ckpt.element_size()
     md.close()
-    return {"seconds": e0.elapsed_time(e1) * 1e-3, "method": method, "nsteps": nsteps,
+    return {"seconds": e0.elapsed_time(e1) * 1e-3, "forward_s": e0.elapsed_time(em) * 1e-3,
+            "backward_s": em.elapsed_time(e1) * 1e-3, "method": method, "nsteps": nsteps,
             "dt_ms": dt * 1e3, "m": m,
             "shots": len(w.shots), "grid": f"{w.nx}x{w.ny}", "checkpoint_bytes": mem,
             "gradient_finite": ok}

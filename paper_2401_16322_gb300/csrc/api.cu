@@ -189,10 +189,10 @@ struct Engine {
     double* d_coef = nullptr;
     ProblemDev* d_apply = nullptr;
     void* d_maps = nullptr;     // FP32: TMA tensor maps of every problem
-    int* d_tbase = nullptr;     // per tile height (16, 8): nprob + 1 tile prefix sums
+    int* d_tbase = nullptr;     // per 2D map set (tile heights 16, 8, 20): nprob + 1 tile prefix sums
     int* d_pbase = nullptr;     // nprob + 1 prefix sums of the flat pointwise chunks
     int nchunks = 0;
-    int ntiles_by[2] = {0, 0};
+    int ntiles_by[TMA_NUM_SETS] = {};
     int tma_variant = -1;       // -1: choose by timing at first use
     double tma_variant_us[TMA_NUM_VARIANTS] = {};
     ProblemDev* d_adj = nullptr;  // adjoint call: descriptors (state = cotangent) + tile map
@@ -442,9 +442,9 @@ int build_engine(Engine* E, std::string& err) {
     if (E->precision == EWV_F32 && E->dims == 2) {
         if (build_tensor_maps(E->probs, E->R, work_vecs, &E->d_maps) != 0)
             return fail(err, EWV_ERR_CUDA, "TMA tensor-map encoding failed");
-        std::vector<int> pre(2 * (size_t)(E->nprob + 1), 0);
-        const int heights[2] = {16, 8};
-        for (int set = 0; set < 2; ++set) {
+        std::vector<int> pre(TMA_NUM_SETS * (size_t)(E->nprob + 1), 0);
+        const int* heights = TMA_SET_HEIGHTS;
+        for (int set = 0; set < TMA_NUM_SETS; ++set) {
             int acc = 0;
             for (int p = 0; p < E->nprob; ++p) {
                 pre[(size_t)set * (E->nprob + 1) + p] = acc;
@@ -601,7 +601,7 @@ struct Ctx {
             if (E->tma_variant < 0) {
                 launch_failed = 1;
             } else {
-                const int set = tma_variant_tile_height(E->tma_variant) == 16 ? 0 : 1;
+                const int set = tma_map_set(tma_variant_tile_height(E->tma_variant));
                 if (launch_stage_tma(E->tma_variant, E->R, E->d_probs, E->d_tbase + (size_t)set * (E->nprob + 1),
                                      E->nprob, E->ntiles_by[set], a, E->d_err, s) != 0)
                     launch_failed = 1;
@@ -640,7 +640,7 @@ struct Ctx {
         int best = -1;
         double best_us = 1e300;
         for (int v = 0; v < TMA_NUM_VARIANTS; ++v) {
-            const int set = tma_variant_tile_height(v) == 16 ? 0 : 1;
+            const int set = tma_map_set(tma_variant_tile_height(v));
             const int* tb = E->d_tbase + (size_t)set * (E->nprob + 1);
             if (launch_stage_tma(v, E->R, E->d_probs, tb, E->nprob, E->ntiles_by[set], p, E->d_err, s) != 0 ||
                 cudaGetLastError() != cudaSuccess) {

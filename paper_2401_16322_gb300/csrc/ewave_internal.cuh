@@ -134,10 +134,14 @@ int launch_leapfrog_tma3d(int R, int warps, const ProblemDev* probs, const int* 
 int upload_tma_tables(const double* fs_uyy, const double* fs_uy, const double* fs_dwy);
 int build_tensor_maps(std::vector<ProblemDev>& probs, int R, const std::vector<int>& work_vecs,
                       void** d_maps_inout);
-constexpr int TMA_NUM_VARIANTS = 5;
+constexpr int TMA_NUM_VARIANTS = 6;
 int launch_stage_tma(int variant, int R, const ProblemDev* probs, const int* tbase, int nprob,
                      int ntiles, const StageArgs& a, int* err, cudaStream_t s);
 int tma_variant_tile_height(int v);
+// Tile heights of the 2D TMA map sets (set k has tile height TMA_SET_HEIGHTS[k]).
+constexpr int TMA_NUM_SETS = 3;
+constexpr int TMA_SET_HEIGHTS[TMA_NUM_SETS] = {16, 8, 20};
+int tma_map_set(int tile_height);
 void tma_variant_describe(int v, int* by, int* nw, int* nst);
 
 void launch_set_clock(const ProblemDev* probs, int nprob, double t, double dt, cudaStream_t s);

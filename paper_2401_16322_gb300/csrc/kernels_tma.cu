@@ -465,14 +465,23 @@ static int encode2(CUtensorMap* out, void* base, int nx, int ny, long long pitch
     return r == CUDA_SUCCESS ? 0 : -1;
 }
 
-// Build NMAP maps per problem and tile height (map set 0: BY = 16, set 1: BY = 8) into a
-// device array (FP32 only); sets P.tmaps to the problem's first map.
+int tma_map_set(int tile_height) {
+    for (int k = 0; k < TMA_NUM_SETS; ++k)
+        if (TMA_SET_HEIGHTS[k] == tile_height) return k;
+    return -1;
+}
+constexpr int map_set_of(int by) { return by == 16 ? 0 : (by == 8 ? 1 : 2); }
+static_assert(map_set_of(16) == 0 && map_set_of(8) == 1 && map_set_of(20) == 2 && TMA_SET_HEIGHTS[2] == 20,
+              "map sets and tile heights must agree");
+
+// Build NMAP maps per problem and tile height (one map set per entry of TMA_SET_HEIGHTS)
+// into a device array (FP32 only); sets P.tmaps to the problem's first map.
 int build_tensor_maps(std::vector<ProblemDev>& probs, int R, const std::vector<int>& work_vecs,
                       void** d_maps_inout) {
     if (get_encoder() != 0) return -1;
     const int n = (int)probs.size();
-    constexpr int NSET = 2;
-    const int heights[NSET] = {16, 8};
+    constexpr int NSET = TMA_NUM_SETS;
+    const int* heights = TMA_SET_HEIGHTS;
     std::vector<CUtensorMap> maps((size_t)n * NSET * NMAP);
     const int SW = BX + 2 * TX;
     for (int p = 0; p < n; ++p) {
@@ -509,11 +518,13 @@ int build_tensor_maps(std::vector<ProblemDev>& probs, int R, const std::vector<i
 
 // Kernel variants the autotuner chooses from: (tile height, consumer warps, stages).  Variant
 // 4 has no U buffer (4 stages of 64 x 16): passes with a U operand run variant 0 instead.
+// Variant 5 keeps two rows per consumer thread with 20 warps (64 x 20 tiles): 21 warps per
+// SM at up to 96 registers a thread, for more latency hiding than variant 0's 17.
 struct TmaVariant {
     int by, nw, nst;
 };
 constexpr TmaVariant kVariants[TMA_NUM_VARIANTS] = {{16, 16, 3}, {16, 8, 3}, {8, 8, 5}, {8, 16, 5},
-                                                    {16, 16, 4}};
+                                                    {16, 16, 4}, {20, 20, 3}};
 
 int tma_variant_tile_height(int v) { return kVariants[v].by; }
 void tma_variant_describe(int v, int* by, int* nw, int* nst) {
@@ -540,7 +551,7 @@ static int launch_variant(const ProblemDev* probs, const int* tbase, int nprob, 
     }
     const int grid = ntiles < g_num_sms ? ntiles : g_num_sms;
     stage_tma_kernel<R, BYv, NW, NSTv, EPI, HASU><<<grid, NW * 32 + 32, smem, s>>>(
-        probs, tbase, nprob, ntiles, BYv == 16 ? 0 : 1, a, err);
+        probs, tbase, nprob, ntiles, map_set_of(BYv), a, err);
     return 0;
 }
 
@@ -563,6 +574,7 @@ int launch_stage_tma(int variant, int R, const ProblemDev* probs, const int* tba
     EWV_TMA_CASE(1, 4, 16, 8, 3)
     EWV_TMA_CASE(2, 4, 8, 8, 5)
     EWV_TMA_CASE(3, 4, 8, 16, 5)
+    EWV_TMA_CASE(5, 4, 20, 20, 3)
     if (variant == 4) {   // no U buffer; a pass with a U operand runs variant 0
         if (a.u >= 0) variant = 0;
         else if (R == 4)
@@ -577,6 +589,7 @@ int launch_stage_tma(int variant, int R, const ProblemDev* probs, const int* tba
     EWV_TMA_CASE(1, 2, 16, 8, 3)
     EWV_TMA_CASE(2, 2, 8, 8, 5)
     EWV_TMA_CASE(3, 2, 8, 16, 5)
+    EWV_TMA_CASE(5, 2, 20, 20, 3)
 #undef EWV_TMA_CASE
     return -1;
 }
