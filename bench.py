@@ -260,7 +260,7 @@ def fwi_gradient_step(method, m, dt_over_cfl):
     fwi = FaberFWI(md, dt, m, nsteps, len(w.shots[0].rec), method=base_method([md], method))
     d_obs = fwi.forward(w.c ** 2)
     c_init = smooth_gradient_with_anomalies(w.nx, w.ny, 0, dx=w.dx, amps=())
-    fwi.forward(c_init ** 2)
+    fwi.backward(fwi.forward(c_init ** 2) - d_obs)     # warm-up: workspaces, graphs, tuning
     torch.cuda.synchronize()
     e0, em, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
     e0.record()

@@ -189,7 +189,7 @@ struct Engine {
     double* d_coef = nullptr;
     ProblemDev* d_apply = nullptr;
     void* d_maps = nullptr;     // FP32: TMA tensor maps of every problem
-    int* d_tbase = nullptr;     // per 2D map set (tile heights 16, 8, 20): nprob + 1 tile prefix sums
+    int* d_tbase = nullptr;     // per 2D map set (TMA_SET_HEIGHTS): nprob + 1 tile prefix sums
     int* d_pbase = nullptr;     // nprob + 1 prefix sums of the flat pointwise chunks
     int nchunks = 0;
     int ntiles_by[TMA_NUM_SETS] = {};
@@ -656,6 +656,14 @@ struct Ctx {
                 float ms = 0.f;
                 cudaEventElapsedTime(&ms, e0, e1);
                 best_v = std::min(best_v, 1e3 * (double)ms);
+            }
+            // a variant whose pipeline wait gave up is not a candidate (clear its flag)
+            int flag = 0;
+            if (cudaMemcpyAsync(&flag, E->d_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess || flag != 0) {
+                cudaMemsetAsync(E->d_err, 0, sizeof(int), s);
+                E->tma_variant_us[v] = -1.0;
+                continue;
             }
             E->tma_variant_us[v] = best_v;
             if (best_v < best_us) {

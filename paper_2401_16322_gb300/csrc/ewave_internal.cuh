@@ -88,6 +88,9 @@ struct StageArgs {
     int gq;                          // vector index of q (its v field is read)
     double gscale;
     int store_bf16;                  // 1: round every stored Y / ACC value to bfloat16 (RN)
+    // FP32 copies of cx .. cax, filled by the FP32 TMA launcher (the kernel reads them from
+    // the parameter bank instead of holding converted values in registers)
+    float fcx, fch, fcu, fck, fca, fcau, fcak, fcay, fcax;
 };
 
 // Arguments of the pointwise kernel (kernels_aux.cu).
@@ -134,13 +137,13 @@ int launch_leapfrog_tma3d(int R, int warps, const ProblemDev* probs, const int* 
 int upload_tma_tables(const double* fs_uyy, const double* fs_uy, const double* fs_dwy);
 int build_tensor_maps(std::vector<ProblemDev>& probs, int R, const std::vector<int>& work_vecs,
                       void** d_maps_inout);
-constexpr int TMA_NUM_VARIANTS = 6;
+constexpr int TMA_NUM_VARIANTS = 7;
 int launch_stage_tma(int variant, int R, const ProblemDev* probs, const int* tbase, int nprob,
                      int ntiles, const StageArgs& a, int* err, cudaStream_t s);
 int tma_variant_tile_height(int v);
 // Tile heights of the 2D TMA map sets (set k has tile height TMA_SET_HEIGHTS[k]).
-constexpr int TMA_NUM_SETS = 3;
-constexpr int TMA_SET_HEIGHTS[TMA_NUM_SETS] = {16, 8, 20};
+constexpr int TMA_NUM_SETS = 4;
+constexpr int TMA_SET_HEIGHTS[TMA_NUM_SETS] = {16, 8, 20, 18};
 int tma_map_set(int tile_height);
 void tma_variant_describe(int v, int* by, int* nw, int* nst);
 

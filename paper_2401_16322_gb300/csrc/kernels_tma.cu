@@ -18,6 +18,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <type_traits>
 #include <vector>
 
 #include "ewave_internal.cuh"
@@ -33,16 +34,19 @@ constexpr int MAX_NST = 5;
 // HORK stages), so that more stages fit in shared memory.
 template <int R, int BYv, bool HASU = true>
 struct StageLayout {
+    static constexpr int up32(int v) { return (v + 31) / 32 * 32; }   // 128-byte boundary
     static constexpr int SH = BYv + 2 * R;
     static constexpr int SW = BX + 2 * TX;
-    static constexpr int U_OFF = 0;                          // u      SH x SW
-    static constexpr int WX_OFF = U_OFF + SH * SW;           // w_x    BYv x SW
-    static constexpr int WY_OFF = WX_OFF + BYv * SW;         // w_y    SH x BX
-    static constexpr int V_OFF = WY_OFF + SH * BX;           // v      BYv x BX
-    static constexpr int C2_OFF = V_OFF + BYv * BX;          // c^2    BYv x BX
-    static constexpr int PU_OFF = C2_OFF + BYv * BX;         // U      4 x BYv x BX
+    static constexpr int U_OFF = 0;                                // u      SH x SW
+    static constexpr int WX_OFF = up32(U_OFF + SH * SW);           // w_x    BYv x SW
+    static constexpr int WY_OFF = up32(WX_OFF + BYv * SW);         // w_y    SH x BX
+    static constexpr int V_OFF = WY_OFF + SH * BX;                 // v      BYv x BX
+    static constexpr int C2_OFF = V_OFF + BYv * BX;                // c^2    BYv x BX
+    static constexpr int PU_OFF = C2_OFF + BYv * BX;               // U      4 x BYv x BX
     static constexpr int PA_OFF = PU_OFF + (HASU ? 4 * BYv * BX : 0);   // A  4 x BYv x BX
     static constexpr int FLOATS = PA_OFF + 4 * BYv * BX;
+    // floats the five field boxes deliver (the padding between buffers is not written)
+    static constexpr int BOX_FLOATS = SH * SW + BYv * SW + SH * BX + 2 * BYv * BX;
     static constexpr int BYTES = FLOATS * 4;
     static_assert((U_OFF * 4) % 128 == 0 && (WX_OFF * 4) % 128 == 0 && (WY_OFF * 4) % 128 == 0 &&
                       (V_OFF * 4) % 128 == 0 && (C2_OFF * 4) % 128 == 0 &&
@@ -69,6 +73,13 @@ __device__ __forceinline__ TileInfo load_info(const TileInfo* p) {
 #pragma unroll
     for (int q = 0; q < (int)(sizeof(TileInfo) / 16); ++q) u.v[q] = reinterpret_cast<const int4*>(p)[q];
     return u.t;
+}
+template <bool kRegs>
+__device__ __forceinline__ std::conditional_t<kRegs, TileInfo, const TileInfo&> tile_info(const TileInfo* p) {
+    if constexpr (kRegs)
+        return load_info(p);
+    else
+        return *p;
 }
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -177,6 +188,32 @@ __device__ __forceinline__ float cent_tree(float u, const float (&p)[R]) {
         return fmaf(cent<R>(1), p[0], cent<R>(0) * u) + cent<R>(2) * p[1];
 }
 
+// Two-row arithmetic on packed FP32 pairs (one instruction for both rows of a consumer
+// thread; each component rounds exactly as the scalar operation does).
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 f2s(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2s(-1.f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+template <int R>
+__device__ __forceinline__ float2 stag_tree2(const float2 (&d)[R]) {
+    if constexpr (R == 4)
+        return add2(fma2(f2s(stag<4>(0)), d[0], mul2(f2s(stag<4>(1)), d[1])),
+                    fma2(f2s(stag<4>(2)), d[2], mul2(f2s(stag<4>(3)), d[3])));
+    else
+        return fma2(f2s(stag<R>(0)), d[0], mul2(f2s(stag<R>(1)), d[1]));
+}
+template <int R>
+__device__ __forceinline__ float2 cent_tree2(float2 u, const float2 (&p)[R]) {
+    if constexpr (R == 4)
+        return add2(add2(fma2(f2s(cent<4>(1)), p[0], mul2(f2s(cent<4>(0)), u)),
+                         fma2(f2s(cent<4>(3)), p[2], mul2(f2s(cent<4>(2)), p[1]))),
+                    mul2(f2s(cent<4>(4)), p[3]));
+    else
+        return add2(fma2(f2s(cent<R>(1)), p[0], mul2(f2s(cent<R>(0)), u)), mul2(f2s(cent<R>(2)), p[1]));
+}
+
 __device__ __forceinline__ float dampf(float beta0, float inv_pml, float d, int pml) {
     if (pml <= 0) return 0.f;
     const float r = 1.f - d * inv_pml;
@@ -232,7 +269,7 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
     __syncthreads();
 
     const bool has_u = HASU && a.u >= 0, has_a = a.a >= 0;
-    const uint32_t bytes = (uint32_t)((L::PU_OFF + (has_u ? 4 * BYv * BX : 0)) * 4) +
+    const uint32_t bytes = (uint32_t)((L::BOX_FLOATS + (has_u ? 4 * BYv * BX : 0)) * 4) +
                            (has_a ? 4 * BYv * BX * 4 : 0);
     int issued = 0;
 
@@ -297,9 +334,15 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
         // ------------------------------------------------------------ consumers
         const int tx = tid & (BX - 1);    // x inside the tile
         const int ty = tid / BX;          // rows NR ty .. NR ty + NR - 1
-        const float cxf = (float)a.cx, chf = (float)a.ch, cuf = (float)a.cu, ckf = (float)a.ck;
-        const float caf = (float)a.ca, cauf = (float)a.cau, cakf = (float)a.cak;
-        const float cayf = (float)a.cay, caxf = (float)a.cax;
+#define cxf a.fcx
+#define chf a.fch
+#define cuf a.fcu
+#define ckf a.fck
+#define caf a.fca
+#define cauf a.fcau
+#define cakf a.fcak
+#define cayf a.fcay
+#define caxf a.fcax
         int it = 0;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
             const int s = it % NSTv;
@@ -308,7 +351,10 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
                 s_err = 1;
                 break;
             }
-            const TileInfo ti = load_info(&info[s]);
+            // The tile descriptor: copied into registers where they are plentiful; read from
+            // shared memory field by field by the 20-warp variant (80 registers a thread).
+            using TI = std::conditional_t<(NW < 20), const TileInfo, const TileInfo&>;
+            TI ti = tile_info<(NW < 20)>(&info[s]);
             const int nx = ti.nx, ny = ti.ny, pml = ti.pml;
             const bool fs = ti.fs != 0;
             const int y0 = ti.y0;
@@ -334,8 +380,99 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
             const float bxn = dampf(beta0, inv_pml, (float)min(i + 1, nx - i), pml);
             const float bxh = dampf(beta0, inv_pml, fminf((float)i + 1.5f, (float)(nx - i) - 0.5f), pml);
             const bool in_x = i < nx;
+            bool paired = false;
+            if constexpr (NR == 2 && EPI == 1) {
+                // Both rows of this thread as packed pairs (rows below the free-surface
+                // band: the interior stencils apply to both).
+                const int ly0 = 2 * ty;
+                const int j0 = y0 + ly0, j1 = j0 + 1;
+                paired = !(fs && j0 < 4);
+                if (paired && in_x && j0 < ny) {
+                    const float* urow0 = su + (ly0 + R) * L::SW + cxs;
+                    const float* urow1 = urow0 + L::SW;
+                    const float* wx0 = swx + ly0 * L::SW + cxs;
+                    const float* wx1 = wx0 + L::SW;
+                    const float2 uc = f2(ucol[R], ucol[R + 1]);
+                    // The pair sums and differences of the taps are packed; the products with
+                    // the stencil weights stay scalar (immediate operands, no registers held).
+                    // lap = 2 c_0 u + sum_k c_k (x pair sum + y pair sum); the divergence of w
+                    // and d_x u, d_y u accumulate their staggered differences the same way.
+                    float lap0 = (2.f * cent<R>(0)) * uc.x, lap1 = (2.f * cent<R>(0)) * uc.y;
+                    float dw0 = 0.f, dw1 = 0.f, ux0 = 0.f, ux1 = 0.f, uy0 = 0.f, uy1 = 0.f;
+#pragma unroll
+                    for (int k = 0; k < R; ++k) {
+                        const float2 ap = f2(urow0[k + 1], urow1[k + 1]);
+                        const float2 am = f2(urow0[-k - 1], urow1[-k - 1]);
+                        const float2 a0 = k == 0 ? uc : f2(urow0[-k], urow1[-k]);
+                        const float2 sl = add2(ap, am);
+                        const float2 sx = sub2(ap, a0);
+                        const float2 sw = sub2(f2(wx0[k], wx1[k]), f2(wx0[-1 - k], wx1[-1 - k]));
+                        lap0 = fmaf(cent<R>(k + 1), sl.x + (ucol[R + k + 1] + ucol[R - k - 1]), lap0);
+                        lap1 = fmaf(cent<R>(k + 1), sl.y + (ucol[R + k + 2] + ucol[R - k]), lap1);
+                        ux0 = fmaf(stag<R>(k), sx.x, ux0);
+                        ux1 = fmaf(stag<R>(k), sx.y, ux1);
+                        uy0 = fmaf(stag<R>(k), ucol[R - k] - ucol[R + 1 + k], uy0);
+                        uy1 = fmaf(stag<R>(k), ucol[R - k + 1] - ucol[R + 2 + k], uy1);
+                        dw0 = fmaf(stag<R>(k), sw.x + (wcol[R - 1 - k] - wcol[R + k]), dw0);
+                        dw1 = fmaf(stag<R>(k), sw.y + (wcol[R - k] - wcol[R + k + 1]), dw1);
+                    }
+                    const float byn0 = dampf(beta0, inv_pml, fs ? (float)(ny - j0) : (float)min(j0 + 1, ny - j0), pml);
+                    const float byn1 = dampf(beta0, inv_pml, fs ? (float)(ny - j1) : (float)min(j1 + 1, ny - j1), pml);
+                    const float byh0 = dampf(beta0, inv_pml,
+                                             fs ? (float)(ny - j0) - 0.5f : fminf((float)j0 + 1.5f, (float)(ny - j0) - 0.5f), pml);
+                    const float byh1 = dampf(beta0, inv_pml,
+                                             fs ? (float)(ny - j1) - 0.5f : fminf((float)j1 + 1.5f, (float)(ny - j1) - 0.5f), pml);
+                    const int pt0 = ly0 * BX + tx, pt1 = pt0 + BX;
+                    const float xv0 = sv[pt0], xv1 = sv[pt1];
+                    const float xwx0 = wx0[0], xwx1 = wx1[0];
+                    const float xwy0 = wcol[R], xwy1 = wcol[R + 1];
+                    // H v = -bx by u + c^2 (lap u / dx^2 + div w / dx) - (bx + by) v
+                    float hv0 = -bxn * byn0 * uc.x + sc2[pt0] * (lap0 * idx2 + dw0 * idx1) - (bxn + byn0) * xv0;
+                    float hv1 = -bxn * byn1 * uc.y + sc2[pt1] * (lap1 * idx2 + dw1 * idx1) - (bxn + byn1) * xv1;
+                    if (i == ti.src_i) {
+                        if (j0 == ti.src_j) hv0 += ti.sig;
+                        if (j1 == ti.src_j) hv1 += ti.sig;
+                    }
+                    const bool wxin = i < nx - 1;
+                    const float hwx0 = wxin ? (byn0 - bxh) * ux0 * idx1 - bxh * xwx0 : 0.f;
+                    const float hwx1 = wxin ? (byn1 - bxh) * ux1 * idx1 - bxh * xwx1 : 0.f;
+                    const float hwy0 = (j0 < ny - 1) ? (bxn - byh0) * uy0 * idx1 - byh0 * xwy0 : 0.f;
+                    const float hwy1 = (j1 < ny - 1) ? (bxn - byh1) * uy1 * idx1 - byh1 * xwy1 : 0.f;
+                    const bool row1 = j1 < ny;
+                    const long long o0 = (long long)j0 * ti.pitch + i;
+                    const float xf0[4] = {uc.x, xv0, xwx0, xwy0}, xf1[4] = {uc.y, xv1, xwx1, xwy1};
+                    const float hf0[4] = {xv0, hv0, hwx0, hwy0}, hf1[4] = {xv1, hv1, hwx1, hwy1};
+#pragma unroll
+                    for (int f = 0; f < 4; ++f) {
+                        float y0v = fmaf(cxf, xf0[f], chf * hf0[f]);
+                        float y1v = fmaf(cxf, xf1[f], chf * hf1[f]);
+                        if (has_u) {
+                            y0v = fmaf(cuf, spu[f * BYv * BX + pt0], y0v);
+                            y1v = fmaf(cuf, spu[f * BYv * BX + pt1], y1v);
+                        }
+                        if ((f == 2 && !wxin) || (f == 3 && j0 >= ny - 1)) y0v = 0.f;
+                        if ((f == 2 && !wxin) || (f == 3 && j1 >= ny - 1)) y1v = 0.f;
+                        if (Yg) {
+                            float* yp = Yg + f * fstr + o0;
+                            yp[0] = y0v;
+                            if (row1) yp[ti.pitch] = y1v;
+                        }
+                        if (Ag) {
+                            float a0v = cayf * y0v, a1v = cayf * y1v;
+                            if (has_a) {
+                                a0v = fmaf(cayf, y0v, caf * spa[f * BYv * BX + pt0]);
+                                a1v = fmaf(cayf, y1v, caf * spa[f * BYv * BX + pt1]);
+                            }
+                            float* ap = Ag + f * fstr + o0;
+                            ap[0] = a0v;
+                            if (row1) ap[ti.pitch] = a1v;
+                        }
+                    }
+                }
+            }
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
+                if (paired) break;
                 const int ly = NR * ty + r;
                 const int j = y0 + ly;
                 const float* urow = su + (ly + R) * L::SW + cxs;
@@ -427,6 +564,16 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
     }
 }
 
+#undef cxf
+#undef chf
+#undef cuf
+#undef ckf
+#undef caf
+#undef cauf
+#undef cakf
+#undef cayf
+#undef caxf
+
 // ---------------------------------------------------------------- host side
 static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
@@ -470,8 +617,9 @@ int tma_map_set(int tile_height) {
         if (TMA_SET_HEIGHTS[k] == tile_height) return k;
     return -1;
 }
-constexpr int map_set_of(int by) { return by == 16 ? 0 : (by == 8 ? 1 : 2); }
-static_assert(map_set_of(16) == 0 && map_set_of(8) == 1 && map_set_of(20) == 2 && TMA_SET_HEIGHTS[2] == 20,
+constexpr int map_set_of(int by) { return by == 16 ? 0 : (by == 8 ? 1 : (by == 20 ? 2 : 3)); }
+static_assert(map_set_of(16) == 0 && map_set_of(8) == 1 && map_set_of(20) == 2 && map_set_of(18) == 3 &&
+                  TMA_SET_HEIGHTS[2] == 20 && TMA_SET_HEIGHTS[3] == 18,
               "map sets and tile heights must agree");
 
 // Build NMAP maps per problem and tile height (one map set per entry of TMA_SET_HEIGHTS)
@@ -519,12 +667,13 @@ int build_tensor_maps(std::vector<ProblemDev>& probs, int R, const std::vector<i
 // Kernel variants the autotuner chooses from: (tile height, consumer warps, stages).  Variant
 // 4 has no U buffer (4 stages of 64 x 16): passes with a U operand run variant 0 instead.
 // Variant 5 keeps two rows per consumer thread with 20 warps (64 x 20 tiles): 21 warps per
-// SM at up to 96 registers a thread, for more latency hiding than variant 0's 17.
+// SM, which caps a thread at 80 registers (six warps share one scheduler's register file).
+// Variant 6 uses 18 warps (64 x 18 tiles): 19 warps per SM, still 96 registers a thread.
 struct TmaVariant {
     int by, nw, nst;
 };
 constexpr TmaVariant kVariants[TMA_NUM_VARIANTS] = {{16, 16, 3}, {16, 8, 3}, {8, 8, 5}, {8, 16, 5},
-                                                    {16, 16, 4}, {20, 20, 3}};
+                                                    {16, 16, 4}, {20, 20, 3}, {18, 18, 3}};
 
 int tma_variant_tile_height(int v) { return kVariants[v].by; }
 void tma_variant_describe(int v, int* by, int* nw, int* nst) {
@@ -556,7 +705,17 @@ static int launch_variant(const ProblemDev* probs, const int* tbase, int nprob, 
 }
 
 int launch_stage_tma(int variant, int R, const ProblemDev* probs, const int* tbase, int nprob,
-                     int ntiles, const StageArgs& a, int* err, cudaStream_t s) {
+                     int ntiles, const StageArgs& a_in, int* err, cudaStream_t s) {
+    StageArgs a = a_in;
+    a.fcx = (float)a.cx;
+    a.fch = (float)a.ch;
+    a.fcu = (float)a.cu;
+    a.fck = (float)a.ck;
+    a.fca = (float)a.ca;
+    a.fcau = (float)a.cau;
+    a.fcak = (float)a.cak;
+    a.fcay = (float)a.cay;
+    a.fcax = (float)a.cax;
     if (ntiles <= 0) return nprob > 0 ? -1 : 0;   // problems but no tiles: inconsistent lists
     if (!g_num_sms) {
         int dev = 0;
@@ -575,6 +734,7 @@ int launch_stage_tma(int variant, int R, const ProblemDev* probs, const int* tba
     EWV_TMA_CASE(2, 4, 8, 8, 5)
     EWV_TMA_CASE(3, 4, 8, 16, 5)
     EWV_TMA_CASE(5, 4, 20, 20, 3)
+    EWV_TMA_CASE(6, 4, 18, 18, 3)
     if (variant == 4) {   // no U buffer; a pass with a U operand runs variant 0
         if (a.u >= 0) variant = 0;
         else if (R == 4)
@@ -590,6 +750,7 @@ int launch_stage_tma(int variant, int R, const ProblemDev* probs, const int* tba
     EWV_TMA_CASE(2, 2, 8, 8, 5)
     EWV_TMA_CASE(3, 2, 8, 16, 5)
     EWV_TMA_CASE(5, 2, 20, 20, 3)
+    EWV_TMA_CASE(6, 2, 18, 18, 3)
 #undef EWV_TMA_CASE
     return -1;
 }

@@ -159,7 +159,7 @@ def load_library(path=LIB_PATH):
 
 def _variant(fn, h, check):
     v, by, nw, nst = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    us = (ctypes.c_double * 6)()
+    us = (ctypes.c_double * 7)()
     check(fn(h, ctypes.byref(v), ctypes.byref(by), ctypes.byref(nw), ctypes.byref(nst), us))
     return {"variant": v.value, "tile": [64, by.value], "consumer_warps": nw.value,
             "stages": nst.value, "probe_us": list(us)}

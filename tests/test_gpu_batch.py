@@ -98,10 +98,10 @@ def test_batch_bitwise_equals_single_models():
             assert np.array_equal(batched[q][s], g.get_state(s))
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6])
 def test_every_kernel_variant_matches_oracle(variant):
-    """Each persistent-kernel variant the autotuner may pick (tile height 16, 8 or 20; 8, 16
-    or 20 consumer warps; 3 to 5 stages) gives the oracle's result on uneven batched grids."""
+    """Each persistent-kernel variant the autotuner may pick (tile height 16, 8, 18 or 20;
+    8, 16, 18 or 20 consumer warps; 3 to 5 stages) gives the oracle's result on uneven batched grids."""
     from paper_2401_16322_gb300 import Batch
     nshots, dt, t, nsteps, m = 2, 1.1e-3, 0.04, 2, 14
     oms, gms, shots = _models("f32", nshots)
