@@ -612,7 +612,7 @@ struct Ctx {
         ++*launches;
     }
     void point(const PointArgs& pa) {
-        if (pa.mode <= 2)   // norm, MGS pass, combine: flat over the padded vectors
+        if (pa.mode <= 2 || pa.mode == 5)   // norm, MGS pass, combine, dot: flat over the padded vectors
             launch_point_flat(E->precision, E->nchunks, E->d_probs, E->d_pbase, E->nprob, pa, s);
         else
             launch_point(E->precision, E->ntiles, E->d_probs, E->d_tile_prob, pa, s);
@@ -997,6 +997,10 @@ int run_krylov(Ctx& C, double t, double dt, int m, int nsteps, int* info) {
     ++*C.launches;
     bool expm_ok = true;
     const int window = C.E->models.empty() ? 0 : C.E->models[0]->kry_window;
+    // FP32: the matrix-vector product runs on the TMA stencil pass, which has no dot partner;
+    // a flat pass then forms <q_{j+1}, q_k0> with the same finalisation (FP64 keeps the fused
+    // dot of the plain stencil kernel)
+    const bool split_dot = C.E->precision == EWV_F32;
     int rc0 = C.step_loop(nsteps, EWV_METHOD_KRYLOV, m, dt, tol, (double)window, 0, 1, [&](int) {
         C.prologue(PRO_KRYLOV, m);
         PointArgs pn{};
@@ -1024,7 +1028,22 @@ int run_krylov(Ctx& C, double t, double dt, int m, int nsteps, int* info) {
             a.tol = tol;
             a.partials = C.E->d_partials;
             a.counters = C.E->d_counters;
+            if (split_dot) {
+                a.d = -1;
+                a.fin_mode = FIN_NONE;
+            }
             C.stage(a);
+            if (split_dot) {
+                PointArgs pd{};
+                pd.mode = 5;
+                pd.j = j;
+                pd.k = k0;
+                pd.m = m;
+                pd.tol = tol;
+                pd.partials = C.E->d_partials;
+                pd.counters = C.E->d_counters;
+                C.point(pd);
+            }
             // at j = m the pass k = m only feeds h_{m+1,m}, which the result does not use
             const int kmax = (j == m) ? j - 1 : j;
             for (int k = k0; k <= kmax; ++k) {

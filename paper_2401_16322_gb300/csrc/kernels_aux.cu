@@ -384,7 +384,7 @@ point_flat_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ 
     const int pid = flat_problem(pbase, nprob, blockIdx.x);
     const ProblemDev* P = probs + pid;
     double* kry = P->kry;
-    if (pa.mode == 1 && kry[KRY_ACTIVE] == 0.0) return;
+    if ((pa.mode == 1 || pa.mode == 5) && kry[KRY_ACTIVE] == 0.0) return;
     if (pa.mode == 2 && kry[KRY_NONFINITE] != 0.0) return;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int nf = P->nfields == 5 ? 5 : 4;
@@ -413,6 +413,11 @@ point_flat_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ 
             const V a = Q[q];
             accd += dotv(a, a);
         }
+    } else if (pa.mode == 5) {
+        // <q_{j+1}, q_k> after the matrix-vector product (its finalisation is FIN_MATVEC)
+        const V* W = reinterpret_cast<const V*>(vptr<T>(P, pa.j));      // slot j+1
+        const V* D = reinterpret_cast<const V*>(vptr<T>(P, pa.k - 1));  // slot k
+        for (long long q = q0 + tid; q < q1; q += NTHREADS) accd += dotv(W[q], D[q]);
     } else {
         V* W = reinterpret_cast<V*>(vptr<T>(P, pa.j));                  // slot j+1
         const V* Qk = reinterpret_cast<const V*>(vptr<T>(P, pa.k - 1));   // slot k
@@ -427,7 +432,7 @@ point_flat_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ 
     if (pa.mode == 1 && pa.k == pa.j && pa.j == pa.m) return;   // h_{m+1,m} unused
     const double bsum = block_sum_fixed(accd, red);
     StageArgs a{};
-    a.fin_mode = pa.mode == 0 ? (pa.notail ? FIN_NORM0_NOTAIL : FIN_NORM0) : FIN_MGS;
+    a.fin_mode = pa.mode == 0 ? (pa.notail ? FIN_NORM0_NOTAIL : FIN_NORM0) : (pa.mode == 5 ? FIN_MATVEC : FIN_MGS);
     a.fin_j = pa.j;
     a.fin_k = pa.k;
     a.m = pa.m;

@@ -60,7 +60,7 @@ struct __align__(16) TileInfo {
     float* A;
     long long fstr;
     int x0, y0, nx, ny, pitch, pml, fs, src_i, src_j, pad0;
-    float beta0, inv_pml, idx1, idx2, sig, pad1;
+    float beta0, inv_pml, idx1, idx2, sig, xs;   // xs: per-problem scale of H X (Krylov)
 };
 
 // The consumers read a stage's TileInfo with 16-byte shared loads into registers.
@@ -312,6 +312,7 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
                 ti.idx1 = P->finv_dx;
                 ti.idx2 = P->finv_dx2;
                 ti.sig = (a.src_slot >= 0 && P->has_src) ? (float)P->sigma[a.src_slot] : 0.f;
+                ti.xs = a.x_scale_slot >= 0 ? (float)P->kry[a.x_scale_slot] : 1.f;
                 float* st = smem + (size_t)s * L::FLOATS;
                 // the arrive below releases the tile info together with the copies
                 mbar_expect_tx(&full[s], bytes);
@@ -380,6 +381,7 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
             const float bxn = dampf(beta0, inv_pml, (float)min(i + 1, nx - i), pml);
             const float bxh = dampf(beta0, inv_pml, fminf((float)i + 1.5f, (float)(nx - i) - 0.5f), pml);
             const bool in_x = i < nx;
+            const float chx = chf * ti.xs;     // ch xs: K = cx X + ch xs (H X + sigma)
             bool paired = false;
             if constexpr (NR == 2 && EPI == 1) {
                 // Both rows of this thread as packed pairs (rows below the free-surface
@@ -444,8 +446,8 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
                     const float hf0[4] = {xv0, hv0, hwx0, hwy0}, hf1[4] = {xv1, hv1, hwx1, hwy1};
 #pragma unroll
                     for (int f = 0; f < 4; ++f) {
-                        float y0v = fmaf(cxf, xf0[f], chf * hf0[f]);
-                        float y1v = fmaf(cxf, xf1[f], chf * hf1[f]);
+                        float y0v = fmaf(cxf, xf0[f], chx * hf0[f]);
+                        float y1v = fmaf(cxf, xf1[f], chx * hf1[f]);
                         if (has_u) {
                             y0v = fmaf(cuf, spu[f * BYv * BX + pt0], y0v);
                             y1v = fmaf(cuf, spu[f * BYv * BX + pt1], y1v);
@@ -537,7 +539,7 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
                     const bool pad = (f == 2 && i >= nx - 1) || (f == 3 && j >= ny - 1);
                     const float uval = has_u ? spu[f * BYv * BX + pt] : 0.f;
                     const float aval = has_a ? spa[f * BYv * BX + pt] : 0.f;
-                    const float kf = fmaf(cxf, xf[f], chf * hf[f]);
+                    const float kf = fmaf(cxf, xf[f], chx * hf[f]);
                     if constexpr (EPI == 1) {
                         const float yf = pad ? 0.f : (has_u ? fmaf(cuf, uval, kf) : kf);
                         if (yrow) yrow[f * fstr] = yf;

@@ -64,7 +64,7 @@ struct __align__(16) Info3 {
     long long fstr, ps;
     int x0, y0, c, warm;     // compute plane c; warm = 1: front values only
     int nx, ny, nz, pitch, pml, fs, src_i, src_j, src_k, pad0;
-    float beta0, inv_pml, idx1, idx2, sig, pad1;
+    float beta0, inv_pml, idx1, idx2, sig, xs;   // xs: per-problem scale of H X (Krylov)
 };
 
 __device__ __forceinline__ uint32_t saddr(const void* p) {
@@ -283,6 +283,7 @@ stage_tma3d_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__
                     ti.idx1 = P->finv_dx;
                     ti.idx2 = P->finv_dx2;
                     ti.sig = (a.src_slot >= 0 && P->has_src) ? (float)P->sigma[a.src_slot] : 0.f;
+                    ti.xs = a.x_scale_slot >= 0 ? (float)P->kry[a.x_scale_slot] : 1.f;
                     float* st = smem + (size_t)s * L::FLOATS;
                     bar_expect_tx(&full[s], warm ? bytes_warm : bytes_full);
                     tma5(st + L::UF_OFF, map3(maps, kx, 3), x0, y0, f, 0, vx, &full[s]);
@@ -451,7 +452,7 @@ stage_tma3d_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__
                                                  (fld == 4 && c >= nz - 1);
                                 const float uval = has_u ? st[L::PU_OFF + fld * L::PL + pt] : 0.f;
                                 const float aval = has_a ? st[L::PA_OFF + fld * L::PL + pt] : 0.f;
-                                const float kf = cxf * xf[fld] + chf * hf[fld];
+                                const float kf = cxf * xf[fld] + (chf * ti.xs) * hf[fld];
                                 const float yf = pad ? 0.f : (cuf * uval + ckf * kf);
                                 if (yp) yp[fld * fstr] = yf;
                                 if (ap) ap[fld * fstr] = pad ? 0.f : (caf * aval + cauf * uval + cakf * kf + cayf * yf + caxf * xf[fld]);

@@ -50,11 +50,13 @@ def _d_obs():
     return faber_forward(om, _oshots(om), DT, NSTEPS, DEG, ell)[1]
 
 
-def _gpu_grad(prec, budget=None):
+def _gpu_grad(prec, budget=None, variant=None):
     import torch
     from paper_2401_16322_gb300.fwi import FaberFWI
     c_true, c0, beta0, ell = _setup()
     g = _gpu(c0, beta0, ell, prec)
+    if variant is not None:
+        g.set_kernel_variant(variant)
     fwi = FaberFWI(g, DT, DEG, NSTEPS, len(REC), budget=budget)
     seis = fwi.forward(c0 ** 2)
     d = torch.tensor(np.array(_d_obs()), dtype=seis.dtype, device=seis.device)
@@ -114,9 +116,11 @@ def test_gpu_gradient_central_differences_fp64():
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_checkpointing_reproduces_full_storage(prec):
-    """Storing every 4th state (segments recomputed) gives the same gradient bit for bit."""
-    _, g_full, fwi1 = _gpu_grad(prec)
-    _, g_ck, fwi4 = _gpu_grad(prec, budget=4)
+    """Storing every 4th state (segments recomputed) gives the same gradient bit for bit.  The
+    two models are pinned to one stencil-pass variant: models tuned separately may pick
+    different variants, which agree to rounding only."""
+    _, g_full, fwi1 = _gpu_grad(prec, variant=0)
+    _, g_ck, fwi4 = _gpu_grad(prec, budget=4, variant=0)
     assert fwi1.stride == 1 and fwi4.stride == o_stride(NSTEPS, 4) == 4
     assert np.array_equal(g_full, g_ck)
 
