@@ -297,7 +297,8 @@ def config5_3d(n=400, check_n=96, target=TARGET):
        1 .. 1/8 of its step.
     2. Time per step of each passing (method, m) at its Delta-t_max on the n^3 cube, time to
        T, and the roofline of the 3D TMA pass (Faber).
-    check_n = 0 skips the search and times Faber 40 at 6 x (profiling runs)."""
+    check_n = 0 skips the search and times Faber 40 at 6 x and Horner HORK 16 at 3 x (profiling
+    runs)."""
     import numpy as np
     import torch
     from paper_2401_16322_gb300 import Model
@@ -374,6 +375,7 @@ def config5_3d(n=400, check_n=96, target=TARGET):
         out["error_check"] = f"{check_n}^3 cube, T 0.5 s, FP64 Faber 30 at the 3D leap-frog step"
     else:
         found.append(("faber", 40, 6.0, float("nan")))
+        found.append(("hork-horner", 16, 3.0, float("nan")))
     # timing on the full cube
     w = config_3d(n)
     dt3 = leapfrog_step(c_max, w.dx, dims=3)
