@@ -172,6 +172,8 @@ def pass_words(method, m):
         return [13] * m     # x (4) + c^2 (1) + y (4) + dot partner (4)
     if method == "leapfrog":
         return [10]
+    if method == "leapfrog-difference":
+        return [11]      # u, w_x, w_y (halo), c^2, w^{n-1}, d^n -> u, w_x, w_y, d
     raise ValueError(method)
 
 

@@ -80,6 +80,12 @@ extern "C" {
 
 #define EWV_LEAPFROG_AVERAGED 0 /* time-averaged PML damping of w (stable reading)       */
 #define EWV_LEAPFROG_LITERAL 1  /* explicit -beta w^n damping, as the formula reads      */
+/* The averaged scheme with u advanced in difference form: d^{n+1} = u^{n+1} - u^n follows
+ * from d^n, and u^{n+1} = u^n + d^{n+1} (the same scheme in exact arithmetic).  2u^n - u^{n-1}
+ * is never formed, so FP32 rounding no longer acts as a velocity error every step.  d is
+ * kept in the v field (2D only; the v field then holds no velocity).  Switching to or from
+ * this form restarts the history (u^{-1} = u^0). */
+#define EWV_LEAPFROG_DIFFERENCE 2
 
 /* Largest Krylov dimension and Faber degree the library accepts. */
 #define EWV_MAX_KRYLOV_M 48

@@ -1093,8 +1093,17 @@ int run_leapfrog(Ctx& C, std::vector<ewv_model*>& models, double t, double dt, i
     bool need_init = false;
     for (ewv_model* m : models) need_init = need_init || !m->lf_history_valid;
     const int wmask = C.E->dims == 3 ? 0x1D : 0xD;   // u and the w fields
+    const bool diff = variant == EWV_LEAPFROG_DIFFERENCE;
+    if (diff && C.E->dims != 2) return fail(*C.err, EWV_ERR_UNSUPPORTED, "difference form: 2D only");
     if (need_init) {
         C.copy(0, 1, wmask, false);   // u and w of level n -> history (level n-1)
+        if (diff) {                   // d^0 = u^0 - u^{-1} = 0 in the history's v field
+            PointArgs pz{};
+            pz.mode = 6;
+            pz.dst = 1;
+            pz.fmask = 0x2;
+            C.point(pz);
+        }
         for (ewv_model* m : models) m->lf_history_valid = true;
     }
     launch_set_clock(C.E->d_probs, C.E->nprob, t, dt, C.s);
@@ -1117,7 +1126,8 @@ int run_leapfrog(Ctx& C, std::vector<ewv_model*>& models, double t, double dt, i
         C.record(prev);
     });
     if (rc != EWV_OK) return rc;
-    if (nsteps & 1) C.copy(1, 0, wmask, true);   // level n back into the state, n-1 into history
+    // level n back into the state, n-1 into history (and d^n with it in the difference form)
+    if (nsteps & 1) C.copy(1, 0, wmask | (diff ? 0x2 : 0), true);
     return check_launch(*C.err);
 }
 
@@ -1623,7 +1633,14 @@ int ewv_step_leapfrog(ewv_model_t m, double t, double dt, int nsteps) {
     return step_model(m, EWV_METHOD_LEAPFROG, t, dt, 1, nsteps, nullptr);
 }
 int ewv_set_leapfrog_variant(ewv_model_t m, int variant) {
-    if (!m || (variant != EWV_LEAPFROG_AVERAGED && variant != EWV_LEAPFROG_LITERAL)) return EWV_ERR_INVALID_ARG;
+    if (!m || (variant != EWV_LEAPFROG_AVERAGED && variant != EWV_LEAPFROG_LITERAL &&
+               variant != EWV_LEAPFROG_DIFFERENCE))
+        return EWV_ERR_INVALID_ARG;
+    if (variant == EWV_LEAPFROG_DIFFERENCE && m->d.dims != 2)
+        return fail(m->err, EWV_ERR_UNSUPPORTED, "the difference form of leap-frog is two-dimensional");
+    // the difference form keeps d^n instead of u^{n-1}: a switch restarts the history
+    if ((variant == EWV_LEAPFROG_DIFFERENCE) != (m->lf_variant == EWV_LEAPFROG_DIFFERENCE))
+        m->lf_history_valid = false;
     m->lf_variant = variant;
     return EWV_OK;
 }

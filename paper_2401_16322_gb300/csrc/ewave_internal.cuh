@@ -96,7 +96,8 @@ struct StageArgs {
 // Arguments of the pointwise kernel (kernels_aux.cu).
 struct PointArgs {
     int mode;        // 0: |q1|^2 (norm); 1: MGS pass; 2: Krylov combine; 3: copy; 4: swap;
-                     // 5: <q_{j+1}, q_k> after a matrix-vector product (flat)
+                     // 5: <q_{j+1}, q_k> after a matrix-vector product (flat); 6: zero the
+                     // fields fmask of vector dst
     int j, k, m;
     int src, dst;    // copy / swap vectors; combine: destination vector (mode 2)
     int notail;      // mode 0: start an Arnoldi process without the augmented tail

@@ -223,8 +223,8 @@ point_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ tile_
     double* kry = P->kry;
 
     if (pa.mode == 1 && kry[KRY_ACTIVE] == 0.0) return;
-    if (pa.mode == 3 || pa.mode == 4) {
-        T* S = vptr<T>(P, pa.src);
+    if (pa.mode == 3 || pa.mode == 4 || pa.mode == 6) {
+        T* S = vptr<T>(P, pa.mode == 6 ? pa.dst : pa.src);
         T* Dd = vptr<T>(P, pa.dst);
         for (int kz = k0; kz < k1; ++kz)
         for (int b = 0; b < VY; ++b)
@@ -234,6 +234,10 @@ point_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ tile_
                 const long long o = kz * ps + (long long)j * pitch + i;
                 for (int f = 0; f < nf; ++f) {
                     if (!((pa.fmask >> f) & 1)) continue;
+                    if (pa.mode == 6) {
+                        Dd[f * fstr + o] = T(0);
+                        continue;
+                    }
                     const T s = S[f * fstr + o];
                     if (pa.mode == 4) S[f * fstr + o] = Dd[f * fstr + o];
                     Dd[f * fstr + o] = s;

@@ -423,7 +423,9 @@ stage_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ tile_
 
 // --------------------------------------------------------------------------------------
 // Leap-frog kernel (Sec. 3.1).  Vectors `cur` (u^n, w^n) and `prev` (u^{n-1}, w^{n-1}) use
-// fields 0 (u), 2 (w_x), 3 (w_y); level n+1 overwrites `prev`.
+// fields 0 (u), 2 (w_x), 3 (w_y); level n+1 overwrites `prev`.  Variant 2 (difference form)
+// reads d^n = u^n - u^{n-1} from field 1 of `prev` instead of u^{n-1} and writes d^{n+1} to
+// field 1 of `cur` (read by no other thread of the step), u^{n+1} = u^n + d^{n+1}.
 // --------------------------------------------------------------------------------------
 template <typename T, int R>
 __global__ void __launch_bounds__(NTHREADS)
@@ -456,7 +458,7 @@ leapfrog_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ ti
             const int i = x0 + tx + c * TPX, j = y0 + ty + b * TPY;
             const bool in = (i < nx) && (j < ny);
             const long long o = (long long)j * pitch + i;
-            pum[b][c] = in ? Pn[o] : T(0);
+            pum[b][c] = in ? Pn[(variant == 2 ? fstr : 0) + o] : T(0);
             pwxm[b][c] = in ? Pn[2 * fstr + o] : T(0);
             pwym[b][c] = in ? Pn[3 * fstr + o] : T(0);
             pc2[b][c] = in ? C2[o] : T(0);
@@ -541,18 +543,26 @@ leapfrog_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ ti
             T rhs = -bxn * byn * u + pc2[b][c] * ((uxx + uyy) * idx2 + (dwx + dwy) * idx1);
             if (i == P->src_i && j == P->src_j) rhs += sig;
             const T um = pum[b][c];
-            const T inv_dt2 = T(1) / (dt * dt), inv_2dt = T(1) / (T(2) * dt);
-            const T up = ((T(2) * u - um) * inv_dt2 + bsum * um * inv_2dt + rhs)
-                         / (inv_dt2 + bsum * inv_2dt);
+            T up;
+            if (variant == 2) {
+                // (u^{n+1} - u^n)(1 + b dt/2) = d^n (1 - b dt/2) + dt^2 rhs, with d^n = um
+                const T hb = T(0.5) * bsum * dt;
+                const T dn = (um * (T(1) - hb) + dt * dt * rhs) / (T(1) + hb);
+                Cn[fstr + o] = dn;
+                up = u + dn;
+            } else {
+                const T inv_dt2 = T(1) / (dt * dt), inv_2dt = T(1) / (T(2) * dt);
+                up = ((T(2) * u - um) * inv_dt2 + bsum * um * inv_2dt + rhs) / (inv_dt2 + bsum * inv_2dt);
+            }
             T wxp = T(0), wyp = T(0);
             if (i < nx - 1) {
                 const T gx = (byn - bxh) * dux * idx1;
-                wxp = variant == 0 ? ((T(1) - bxh * dt) * pwxm[b][c] + T(2) * dt * gx) / (T(1) + bxh * dt)
+                wxp = variant != 1 ? ((T(1) - bxh * dt) * pwxm[b][c] + T(2) * dt * gx) / (T(1) + bxh * dt)
                                    : pwxm[b][c] + T(2) * dt * (-bxh * swx[ly][lx + R] + gx);
             }
             if (j < ny - 1) {
                 const T gy = (bxn - byh) * duy * idx1;
-                wyp = variant == 0 ? ((T(1) - byh * dt) * pwym[b][c] + T(2) * dt * gy) / (T(1) + byh * dt)
+                wyp = variant != 1 ? ((T(1) - byh * dt) * pwym[b][c] + T(2) * dt * gy) / (T(1) + byh * dt)
                                    : pwym[b][c] + T(2) * dt * (-byh * swy[ly + R][lx] + gy);
             }
             Pn[o] = up;

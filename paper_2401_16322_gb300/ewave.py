@@ -21,7 +21,7 @@ ERRORS = {
 F32, F64 = 0, 1
 METHOD = {"apply": 0, "faber": 1, "krylov": 2, "hork": 3, "rk32": 4, "rk44": 5, "leapfrog": 6,
           "adjoint_faber": 7, "adjoint_krylov": 8}
-LEAPFROG_AVERAGED, LEAPFROG_LITERAL = 0, 1
+LEAPFROG_AVERAGED, LEAPFROG_LITERAL, LEAPFROG_DIFFERENCE = 0, 1, 2
 
 # Every symbol include/ewave.h declares (checked by the tests).
 EXPORTS = [
@@ -360,9 +360,15 @@ class Model:
         self.ensure_workspace(scheme, stages)
         self._check(self.lib.ewv_step_rk(self.h, t, dt, METHOD[scheme], stages, nsteps), "step_rk")
 
-    def step_leapfrog(self, t, dt, nsteps=1, variant=LEAPFROG_AVERAGED):
+    def set_leapfrog_variant(self, variant):
+        """LEAPFROG_AVERAGED (default), LEAPFROG_LITERAL or LEAPFROG_DIFFERENCE (2D)."""
+        self._check(self.lib.ewv_set_leapfrog_variant(self.h, int(variant)), "leapfrog_variant")
+
+    def step_leapfrog(self, t, dt, nsteps=1, variant=None):
+        """Leap-frog steps; ``variant`` (if given) is set first, else the model's is kept."""
         self.ensure_workspace("leapfrog")
-        self._check(self.lib.ewv_set_leapfrog_variant(self.h, variant))
+        if variant is not None:
+            self.set_leapfrog_variant(variant)
         self._check(self.lib.ewv_step_leapfrog(self.h, t, dt, nsteps), "step_leapfrog")
 
     def step(self, method, t, dt, m=0, nsteps=1):

@@ -60,17 +60,22 @@ def test_integrator_matches_oracle(prec, method, m):
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
-@pytest.mark.parametrize("variant", ["averaged", "literal"])
+@pytest.mark.parametrize("variant", ["averaged", "literal", "difference"])
 def test_leapfrog_matches_oracle(prec, variant):
-    from paper_2401_16322_gb300.ewave import LEAPFROG_AVERAGED, LEAPFROG_LITERAL
+    """Both damping readings, and the averaged one in difference form (the same scheme in
+    exact arithmetic: the oracle's averaged leap-frog is its reference)."""
+    from paper_2401_16322_gb300.ewave import LEAPFROG_AVERAGED, LEAPFROG_DIFFERENCE, LEAPFROG_LITERAL
+    code = {"averaged": LEAPFROG_AVERAGED, "literal": LEAPFROG_LITERAL,
+            "difference": LEAPFROG_DIFFERENCE}[variant]
+    ovar = "literal" if variant == "literal" else "averaged"
     om, g, src, rec, rn, U0 = _setup(prec)
     U0 = (U0[0], np.zeros_like(U0[1]), U0[2], U0[3])
     dt, t, nsteps = 4e-4, 0.03, 7                    # odd: exercises the final buffer swap
     g.bind_seismogram(nsteps)
     g.set_state(0, flatten(U0))
-    g.step_leapfrog(t, dt, nsteps, LEAPFROG_AVERAGED if variant == "averaged" else LEAPFROG_LITERAL)
+    g.step_leapfrog(t, dt, nsteps, code)
     gs = g.get_state(0)
-    U, S = run(om, "leapfrog", dt, nsteps, src=src, rec_nodes=rn, U0=U0, t0=t, lf_variant=variant)
+    U, S = run(om, "leapfrog", dt, nsteps, src=src, rec_nodes=rn, U0=U0, t0=t, lf_variant=ovar)
     n_u = om.nx * om.ny
     ref = flatten(U)
     mask = np.ones(om.n, bool)
@@ -78,8 +83,8 @@ def test_leapfrog_matches_oracle(prec, variant):
     assert rel_l2(gs[mask], ref[mask]) < TOL[prec] * (3 if prec == "f32" else 1)
     assert rel_l2(g.seismogram(0, len(rec), nsteps), S) < TOL[prec] * (3 if prec == "f32" else 1)
     # continuing from the restored buffers gives the same as one longer call
-    g.step_leapfrog(t + nsteps * dt, dt, 2, LEAPFROG_AVERAGED if variant == "averaged" else LEAPFROG_LITERAL)
-    U2, _ = run(om, "leapfrog", dt, nsteps + 2, src=src, rec_nodes=rn, U0=U0, t0=t, lf_variant=variant)
+    g.step_leapfrog(t + nsteps * dt, dt, 2, code)
+    U2, _ = run(om, "leapfrog", dt, nsteps + 2, src=src, rec_nodes=rn, U0=U0, t0=t, lf_variant=ovar)
     assert rel_l2(g.get_state(0)[mask], flatten(U2)[mask]) < TOL[prec] * (3 if prec == "f32" else 1)
 
 
@@ -183,3 +188,25 @@ def test_hork_horner_and_low_storage_agree_fp64():
         out.append(_gpu_run(g, U0, "hork", 0.03, 4e-3, 16, 4, 4)[0])
     assert np.array_equal(out[0], out[2])           # switching back restores the same graph
     assert rel_l2(out[1], out[0]) < 1e-13
+
+
+def test_leapfrog_difference_form_cuts_fp32_rounding():
+    """Many small FP32 steps (1/12 of the stability step): the difference form stays much
+    closer to the FP64 run than the plain form, whose 2u^n - u^{n-1} turns each step's
+    rounding into a velocity error."""
+    from paper_2401_16322_gb300.ewave import LEAPFROG_AVERAGED, LEAPFROG_DIFFERENCE
+    from paper_2401_16322_gb300.tts import leapfrog_step
+    errs = {}
+    for variant in (LEAPFROG_AVERAGED, LEAPFROG_DIFFERENCE):
+        out = {}
+        for prec in ("f64", "f32"):
+            om, g, src, rec, rn, U0 = _setup(prec)
+            dt = leapfrog_step(om.c_max, om.dx) / 12
+            nsteps = 600
+            g.bind_seismogram(nsteps)
+            g.set_state(0, flatten(tuple(0 * f for f in U0)))
+            g.step_leapfrog(0.0, dt, nsteps, variant)
+            out[prec] = g.seismogram(0, len(rec), nsteps)
+            g.close()
+        errs[variant] = rel_l2(out["f32"], out["f64"])
+    assert errs[LEAPFROG_DIFFERENCE] < 0.5 * errs[LEAPFROG_AVERAGED], errs
