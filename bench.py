@@ -198,7 +198,8 @@ def cpu_oracle_sample(workloads, method, m, dt, budget_s, log=log):
     nsteps = 0
     U = om.zeros_state()
     # the oracle evaluates HORK in the paper's stages and Krylov with full orthogonalisation
-    om_method = "hork" if method == "hork-horner" else ("krylov" if method.startswith("krylov") else method)
+    om_method = {"hork-horner": "hork", "leapfrog-difference": "leapfrog"}.get(
+        method, "krylov" if method.startswith("krylov") else method)
     while True:
         U, _ = run(om, om_method, dt, 1, src=src, m=m, U0=U, t0=0.3 + nsteps * dt, faber_params=params)
         nsteps += 1

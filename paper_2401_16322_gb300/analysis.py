@@ -46,7 +46,7 @@ def amplification(method, m, omega, dt, ellipse=None):
         return amplification("hork", 4, omega, dt)
     if method == "rk32":
         return 1 + z + z ** 2 / 2 + z ** 3 / 4
-    if method == "leapfrog":
+    if method in ("leapfrog", "leapfrog-difference"):      # one scheme, two storage forms
         b = 1 + z ** 2 / 2
         root = np.sqrt(b * b - 1 + 0j)
         z1, z2 = b + root, b - root

@@ -574,6 +574,21 @@ struct Ctx {
         }
         return E->events[E->events_used++];
     }
+    // Launch one stencil-type kernel through `launch` with the per-launch timing events that
+    // stage() records (kernel timing on), and count it.
+    template <class F>
+    void timed(F&& launch) {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        const unsigned rec_flags = capture_ev ? cudaEventRecordExternal : cudaEventRecordDefault;
+        if (E->timing) {
+            e0 = next_event();
+            e1 = next_event();
+            cudaEventRecordWithFlags(e0, s, rec_flags);
+        }
+        launch();
+        if (E->timing) cudaEventRecordWithFlags(e1, s, rec_flags);
+        ++*launches;
+    }
     void stage(const StageArgs& a_in) {
         StageArgs a = a_in;
         a.store_bf16 = E->store_bf16;
@@ -1112,17 +1127,25 @@ int run_leapfrog(Ctx& C, std::vector<ewv_model*>& models, double t, double dt, i
     int rc = C.step_loop(nsteps, EWV_METHOD_LEAPFROG, variant, dt, 0, 0, 0, 2, [&](int n) {
         const int cur = (n & 1) ? 1 : 0, prev = 1 - cur;
         C.prologue(PRO_LEAPFROG, 1);
+        C.timed([&] {
         if (C.E->dims == 3 && C.E->precision == EWV_F32 && C.E->tma_variant != 1) {
             if (launch_leapfrog_tma3d(C.E->R, tma3d_warps(C.E), C.E->d_probs, C.E->d_tbase, C.E->nprob,
                                       C.E->ntiles_by[0], cur, prev, variant, dt, C.E->d_err, C.s) != 0)
                 C.launch_failed = 1;
-        } else if (C.E->dims == 3)
+        } else if (C.E->dims == 3) {
             launch_leapfrog3d(C.E->precision, C.E->R, C.E->ntiles, C.E->d_probs, C.E->d_tile_prob,
                               cur, prev, variant, dt, C.s);
-        else
+        } else if (C.E->precision == EWV_F32) {
+            const int set = tma_map_set(18);
+            if (launch_leapfrog_tma(C.E->R, C.E->d_probs, C.E->d_tbase + (size_t)set * (C.E->nprob + 1),
+                                    C.E->nprob, C.E->ntiles_by[set], cur, prev, variant, dt, C.E->d_err,
+                                    C.s) != 0)
+                C.launch_failed = 1;
+        } else {
             launch_leapfrog(C.E->precision, C.E->R, C.E->ntiles, C.E->d_probs, C.E->d_tile_prob,
                             cur, prev, variant, dt, C.s);
-        ++*C.launches;
+        }
+        });
         C.record(prev);
     });
     if (rc != EWV_OK) return rc;

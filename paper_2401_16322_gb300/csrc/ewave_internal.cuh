@@ -140,6 +140,10 @@ int upload_tma_tables(const double* fs_uyy, const double* fs_uy, const double* f
 int build_tensor_maps(std::vector<ProblemDev>& probs, int R, const std::vector<int>& work_vecs,
                       void** d_maps_inout);
 constexpr int TMA_NUM_VARIANTS = 7;
+// One 2D FP32 leap-frog step through the persistent TMA pass (64 x 18 tiles); tbase and
+// ntiles are those of the 18-row map set.
+int launch_leapfrog_tma(int R, const ProblemDev* probs, const int* tbase, int nprob, int ntiles, int cur,
+                        int prev, int variant, double dt, int* err, cudaStream_t s);
 int launch_stage_tma(int variant, int R, const ProblemDev* probs, const int* tbase, int nprob,
                      int ntiles, const StageArgs& a, int* err, cudaStream_t s);
 int tma_variant_tile_height(int v);

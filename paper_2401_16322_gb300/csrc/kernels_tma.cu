@@ -269,7 +269,8 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
     __syncthreads();
 
     const bool has_u = HASU && a.u >= 0, has_a = a.a >= 0;
-    const uint32_t bytes = (uint32_t)((L::BOX_FLOATS + (has_u ? 4 * BYv * BX : 0)) * 4) +
+    // (the leap-frog step, EPI 2, does not read v)
+    const uint32_t bytes = (uint32_t)((L::BOX_FLOATS - (EPI == 2 ? BYv * BX : 0) + (has_u ? 4 * BYv * BX : 0)) * 4) +
                            (has_a ? 4 * BYv * BX * 4 : 0);
     int issued = 0;
 
@@ -320,7 +321,7 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
                 tma_load_4d(st + L::U_OFF, map_of(maps, kx, 0), x0 - TX, y0 - R, 0, cx, &full[s]);
                 tma_load_4d(st + L::WX_OFF, map_of(maps, kx, 1), x0 - TX, y0, 2, cx, &full[s]);
                 tma_load_4d(st + L::WY_OFF, map_of(maps, kx, 2), x0, y0 - R, 3, cx, &full[s]);
-                tma_load_4d(st + L::V_OFF, map_of(maps, kx, 3), x0, y0, 1, cx, &full[s]);
+                if (EPI != 2) tma_load_4d(st + L::V_OFF, map_of(maps, kx, 3), x0, y0, 1, cx, &full[s]);
                 tma_load_2d(st + L::C2_OFF, maps + 10, x0, y0, &full[s]);
                 if (has_u)
                     tma_load_4d(st + L::PU_OFF, map_of(maps, a.u, 4), x0, y0, 0, a.u == 0 ? 0 : a.u - 1,
@@ -382,8 +383,47 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
             const float bxh = dampf(beta0, inv_pml, fminf((float)i + 1.5f, (float)(nx - i) - 0.5f), pml);
             const bool in_x = i < nx;
             const float chx = chf * ti.xs;     // ch xs: K = cx X + ch xs (H X + sigma)
+            // EPI 2: one leap-frog step (Sec. 3.1) at a point.  X = level n; the A box holds
+            // level n - 1 (u^{n-1} or, in difference form, d^n in field 1, and w^{n-1});
+            // level n + 1 goes to Y (u, w_x, w_y) and, in difference form, d^{n+1} to field 1
+            // of level n (acc_out), which no thread of this step reads.
+            auto leapfrog_point = [&](int ii, int jj, int ptv, float uu, float c2v, float lap, float dws,
+                                      float dux, float duy, float bxnv, float bxhv, float bynv, float byhv,
+                                      float xwxv, float xwyv) {
+                const float dt = (float)a.dt, bsum = bxnv + bynv;
+                float rhs = -bxnv * bynv * uu + c2v * (lap * idx2 + dws * idx1);
+                if (ii == ti.src_i && jj == ti.src_j) rhs += ti.sig;
+                const float* pm = spa + ptv;
+                const long long o = (long long)jj * ti.pitch + ii;
+                // fast (2-ulp) divisions, as in the 3D step: the step's own error is far larger
+                float up;
+                if (a.m == 2) {
+                    const float hb = 0.5f * bsum * dt;
+                    const float dn = __fdividef(pm[BYv * BX] * (1.f - hb) + dt * dt * rhs, 1.f + hb);
+                    Ag[fstr + o] = dn;
+                    up = uu + dn;
+                } else {
+                    const float um = pm[0];
+                    const float inv_dt2 = 1.f / (dt * dt), inv_2dt = 1.f / (2.f * dt);
+                    up = __fdividef((2.f * uu - um) * inv_dt2 + bsum * um * inv_2dt + rhs, inv_dt2 + bsum * inv_2dt);
+                }
+                float wxp = 0.f, wyp = 0.f;
+                if (ii < nx - 1) {
+                    const float gx = (bynv - bxhv) * dux * idx1, wm = pm[2 * BYv * BX];
+                    wxp = a.m != 1 ? __fdividef((1.f - bxhv * dt) * wm + 2.f * dt * gx, 1.f + bxhv * dt)
+                                   : wm + 2.f * dt * (-bxhv * xwxv + gx);
+                }
+                if (jj < ny - 1) {
+                    const float gy = (bxnv - byhv) * duy * idx1, wm = pm[3 * BYv * BX];
+                    wyp = a.m != 1 ? __fdividef((1.f - byhv * dt) * wm + 2.f * dt * gy, 1.f + byhv * dt)
+                                   : wm + 2.f * dt * (-byhv * xwyv + gy);
+                }
+                Yg[o] = up;
+                Yg[2 * fstr + o] = wxp;
+                Yg[3 * fstr + o] = wyp;
+            };
             bool paired = false;
-            if constexpr (NR == 2 && EPI == 1) {
+            if constexpr (NR == 2 && (EPI == 1 || EPI == 2)) {
                 // Both rows of this thread as packed pairs (rows below the free-surface
                 // band: the interior stencils apply to both).
                 const int ly0 = 2 * ty;
@@ -425,6 +465,13 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
                     const float byh1 = dampf(beta0, inv_pml,
                                              fs ? (float)(ny - j1) - 0.5f : fminf((float)j1 + 1.5f, (float)(ny - j1) - 0.5f), pml);
                     const int pt0 = ly0 * BX + tx, pt1 = pt0 + BX;
+                    if constexpr (EPI == 2) {
+                        leapfrog_point(i, j0, pt0, uc.x, sc2[pt0], lap0, dw0, ux0, uy0, bxn, bxh, byn0, byh0,
+                                       wx0[0], wcol[R]);
+                        if (j1 < ny)
+                            leapfrog_point(i, j1, pt1, uc.y, sc2[pt1], lap1, dw1, ux1, uy1, bxn, bxh, byn1, byh1,
+                                           wx1[0], wcol[R + 1]);
+                    } else {
                     const float xv0 = sv[pt0], xv1 = sv[pt1];
                     const float xwx0 = wx0[0], xwx1 = wx1[0];
                     const float xwy0 = wcol[R], xwy1 = wcol[R + 1];
@@ -470,6 +517,7 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
                             if (row1) ap[ti.pitch] = a1v;
                         }
                     }
+                    }   // EPI 1
                 }
             }
 #pragma unroll
@@ -523,6 +571,11 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
                                         fs ? (float)(ny - j) - 0.5f : fminf((float)j + 1.5f, (float)(ny - j) - 0.5f),
                                         pml);
                 const int pt = ly * BX + tx;
+                if constexpr (EPI == 2) {
+                    leapfrog_point(i, j, pt, ucol[r + R], sc2[pt], uxx + uyy, dwx + dwy, dux, duy, bxn, bxh,
+                                   byn, byh, wxrow[0], wcol[r + R]);
+                    continue;
+                }
                 const float xu = ucol[r + R], xv = sv[pt], xwx = wxrow[0], xwy = wcol[r + R];
                 const float c2 = sc2[pt];
                 float hv = -bxn * byn * xu + c2 * ((uxx + uyy) * idx2 + (dwx + dwy) * idx1) - (bxn + byn) * xv;
@@ -704,6 +757,33 @@ static int launch_variant(const ProblemDev* probs, const int* tbase, int nprob, 
     stage_tma_kernel<R, BYv, NW, NSTv, EPI, HASU><<<grid, NW * 32 + 32, smem, s>>>(
         probs, tbase, nprob, ntiles, map_set_of(BYv), a, err);
     return 0;
+}
+
+// One leap-frog step (EPI 2) on 64 x 18 tiles with 18 consumer warps and no U buffer
+// (4 stages); tbase is the tile list of the 18-row map set.
+int launch_leapfrog_tma(int R, const ProblemDev* probs, const int* tbase, int nprob, int ntiles, int cur,
+                        int prev, int variant, double dt, int* err, cudaStream_t s) {
+    if (ntiles <= 0) return nprob > 0 ? -1 : 0;
+    if (!g_num_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 1;
+    }
+    StageArgs a{};
+    a.x = cur;
+    a.u = -1;
+    a.a = prev;
+    a.y_out = prev;
+    a.acc_out = cur;
+    a.d = -1;
+    a.src_slot = 0;
+    a.x_scale_slot = -1;
+    a.m = variant;
+    a.dt = dt;
+    if (R == 4) return launch_variant<4, 18, 18, 4, 2, false>(probs, tbase, nprob, ntiles, a, err, s);
+    if (R == 2) return launch_variant<2, 18, 18, 4, 2, false>(probs, tbase, nprob, ntiles, a, err, s);
+    return -1;
 }
 
 int launch_stage_tma(int variant, int R, const ProblemDev* probs, const int* tbase, int nprob,

@@ -16,7 +16,7 @@ For a workload (a list of velocity models with shots and surface receivers) this
 Faber degree 20..120 is scanned up to 32 x the leap-frog step, Krylov dimension 10..40 up to
 24 x (the paper's grid is 4..16 x), Krylov 20..40 with an orthogonalisation window of 2
 ("krylov-w2"), HORK 8..32 up to 12 x in its low-storage form and in Horner form
-("hork-horner"); leap-frog itself, in FP32 and in FP64, at
+("hork-horner"); leap-frog itself, in FP32 (difference form) and in FP64, at
 1 .. 1/32 of its step (largest passing step).
 """
 import math
