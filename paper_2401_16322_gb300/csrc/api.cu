@@ -196,6 +196,11 @@ struct Engine {
     int tma_variant = -1;       // -1: choose by timing at first use
     double tma_variant_us[TMA_NUM_VARIANTS] = {};
     ProblemDev* d_adj = nullptr;  // adjoint call: descriptors (state = cotangent) + tile map
+    void* d_adj_maps = nullptr;   // FP32: TMA tensor maps of the adjoint's buffers
+    const void* adj_key_state = nullptr;     // ... valid for this cotangent buffer,
+    const void* adj_key_work = nullptr;      // workspace
+    size_t adj_key_bytes = 0;                // and workspace size
+    std::vector<const void*> adj_tmaps;      // per-shot map pointers
     size_t d_adj_bytes = 0;
     ProblemDev* d_kadj = nullptr; // Krylov adjoint: three descriptor views of the workspace
     size_t d_kadj_bytes = 0;
@@ -255,6 +260,7 @@ struct Engine {
         cudaFree(d_pbase);
         cudaFree(d_err);
         cudaFree(d_adj);
+        cudaFree(d_adj_maps);
         cudaFree(d_kadj);
     }
 };
@@ -2034,9 +2040,59 @@ int ewv_adjoint_step(ewv_model_t m, int method, double t, double dt, int deg,
     CUDA_OR_FAIL(m->err, cudaMemcpy2DAsync(m->work, per_shot * vb, checkpoint, vb, vb, ns,
                                            cudaMemcpyDeviceToDevice, s));
     const int R = m->R, prec = m->d.precision;
+    // FP32: the forward-recompute passes (no transpose, no gradient) take the persistent TMA
+    // pass, with tensor maps of the adjoint's buffers (rebuilt when the buffers change)
+    bool tma_adj = prec == EWV_F32 && E->tma_variant >= 0 && E->d_tbase && E->nprob == ns;
+    if (tma_adj) {
+        if (E->adj_key_state != adj_state || E->adj_key_work != m->work || E->adj_key_bytes != m->work_bytes) {
+            std::vector<int> wv((size_t)ns, (int)per_shot);
+            E->adj_key_state = nullptr;
+            if (build_tensor_maps(probs, R, wv, &E->d_adj_maps) == 0) {
+                E->adj_key_state = adj_state;
+                E->adj_key_work = m->work;
+                E->adj_key_bytes = m->work_bytes;
+                E->adj_tmaps.assign((size_t)ns, nullptr);
+                for (int p = 0; p < ns; ++p) E->adj_tmaps[p] = probs[p].tmaps;
+            } else {
+                tma_adj = false;
+                for (ProblemDev& P : probs) P.tmaps = nullptr;
+            }
+        } else {
+            for (int p = 0; p < ns; ++p) probs[p].tmaps = E->adj_tmaps[p];
+        }
+        CUDA_OR_FAIL(m->err, cudaMemcpyAsync(E->d_adj, probs.data(), sizeof(ProblemDev) * ns,
+                                             cudaMemcpyHostToDevice, s));
+    }
+    const int tset = tma_adj ? tma_map_set(tma_variant_tile_height(E->tma_variant)) : 0;
+    const int gset = tma_map_set(18);
     auto stage = [&](const StageArgs& sa) {
+        if (tma_adj && !sa.transpose && sa.grad && sa.fin_mode == FIN_NONE && sa.d < 0 &&
+            launch_grad_tma(R, E->d_adj, E->d_tbase + (size_t)gset * (E->nprob + 1), ns, E->ntiles_by[gset], sa,
+                            E->d_err, s) == 0) {
+            ++m->launches;
+            return;
+        }
+        if (tma_adj && !sa.transpose && !sa.grad && sa.fin_mode == FIN_NONE && sa.d < 0 &&
+            launch_stage_tma(E->tma_variant, R, E->d_adj, E->d_tbase + (size_t)tset * (E->nprob + 1), ns,
+                             E->ntiles_by[tset], sa, E->d_err, s) == 0) {
+            ++m->launches;
+            return;
+        }
         launch_stage(prec, R, tb, E->d_adj, d_tp, sa, s);
         ++m->launches;
+    };
+    // launch errors, and the TMA pipeline's timeout flag when it ran
+    auto adj_finish = [&]() {
+        int rc2 = check_launch(m->err);
+        if (rc2 != EWV_OK || !tma_adj) return rc2;
+        int herr = 0;
+        CUDA_OR_FAIL(m->err, cudaMemcpyAsync(&herr, E->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CUDA_OR_FAIL(m->err, cudaStreamSynchronize(s));
+        if (herr) {
+            CUDA_OR_FAIL(m->err, cudaMemset(E->d_err, 0, sizeof(int)));
+            return fail(m->err, EWV_ERR_TIMEOUT, "a pipeline wait in the TMA stencil kernel timed out");
+        }
+        return EWV_OK;
     };
     if (method == EWV_METHOD_KRYLOV)
         return adjoint_krylov(m, E, t, dt, deg, adj_state, grad, probs, d_tp, tb);
@@ -2087,7 +2143,7 @@ int ewv_adjoint_step(ewv_model_t m, int method, double t, double dt, int deg,
             launch_point(prec, tb, E->d_adj, d_tp, pa, s);
             ++m->launches;
         }
-        return check_launch(m->err);
+        return adj_finish();
     }
     double g, c0, c1;
     ellipse_of(m, &g, &c0, &c1);
@@ -2166,7 +2222,7 @@ int ewv_adjoint_step(ewv_model_t m, int method, double t, double dt, int deg,
         launch_point(prec, tb, E->d_adj, d_tp, pa, s);
         ++m->launches;
     }
-    return check_launch(m->err);
+    return adj_finish();
 }
 
 int ewv_adjoint_inject(ewv_model_t m, void* adj_state, const void* values) {

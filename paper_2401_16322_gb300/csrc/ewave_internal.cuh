@@ -144,6 +144,9 @@ constexpr int TMA_NUM_VARIANTS = 7;
 // ntiles are those of the 18-row map set.
 int launch_leapfrog_tma(int R, const ProblemDev* probs, const int* tbase, int nprob, int ntiles, int cur,
                         int prev, int variant, double dt, int* err, cudaStream_t s);
+// The FWI gradient pass through the persistent TMA pass (64 x 18 tiles, 18-row map set).
+int launch_grad_tma(int R, const ProblemDev* probs, const int* tbase, int nprob, int ntiles,
+                    const StageArgs& a, int* err, cudaStream_t s);
 int launch_stage_tma(int variant, int R, const ProblemDev* probs, const int* tbase, int nprob,
                      int ntiles, const StageArgs& a, int* err, cudaStream_t s);
 int tma_variant_tile_height(int v);

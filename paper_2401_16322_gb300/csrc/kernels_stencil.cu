@@ -156,27 +156,38 @@ stage_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ tile_
     }
 
     // ---- stage halo tiles ----------------------------------------------------------------
+    // Row-wise: thread (tx, ty) fills columns tx, tx + TPX, ... of rows ty, ty + TPY, ...; the
+    // row's bounds test and (in the transpose) its damping factor are taken once per row.
     if constexpr (!TRANS) {
         const T* Xu = X;
         const T* Xwx = X + 2 * fstr;
         const T* Xwy = X + 3 * fstr;
-        for (int idx = tid; idx < SH * SW; idx += NTHREADS) {
-            const int r = idx / SW, c = idx - r * SW;
-            const int gx = x0 - R + c, gy = y0 - R + r;
-            su[r][c] = (gx >= 0 && gx < nx && gy >= 0 && gy < ny) ? Xu[(long long)gy * pitch + gx]
-                                                                   : T(0);
+        for (int r = ty; r < SH; r += TPY) {
+            const int gy = y0 - R + r;
+            const bool rok = gy >= 0 && gy < ny;
+            const T* row = Xu + (long long)(rok ? gy : 0) * pitch;
+            for (int c = tx; c < SW; c += TPX) {
+                const int gx = x0 - R + c;
+                su[r][c] = (rok && gx >= 0 && gx < nx) ? row[gx] : T(0);
+            }
         }
-        for (int idx = tid; idx < BY * SW; idx += NTHREADS) {
-            const int r = idx / SW, c = idx - r * SW;
-            const int gx = x0 - R + c, gy = y0 + r;
-            swx[r][c] = (gx >= 0 && gx < nx - 1 && gy < ny) ? Xwx[(long long)gy * pitch + gx]
-                                                            : T(0);
+        for (int r = ty; r < BY; r += TPY) {
+            const int gy = y0 + r;
+            const bool rok = gy < ny;
+            const T* row = Xwx + (long long)(rok ? gy : 0) * pitch;
+            for (int c = tx; c < SW; c += TPX) {
+                const int gx = x0 - R + c;
+                swx[r][c] = (rok && gx >= 0 && gx < nx - 1) ? row[gx] : T(0);
+            }
         }
-        for (int idx = tid; idx < SH * BX; idx += NTHREADS) {
-            const int r = idx / BX, c = idx - r * BX;
-            const int gx = x0 + c, gy = y0 - R + r;
-            swy[r][c] = (gx < nx && gy >= 0 && gy < ny - 1) ? Xwy[(long long)gy * pitch + gx]
-                                                            : T(0);
+        for (int r = ty; r < SH; r += TPY) {
+            const int gy = y0 - R + r;
+            const bool rok = gy >= 0 && gy < ny - 1;
+            const T* row = Xwy + (long long)(rok ? gy : 0) * pitch;
+            for (int c = tx; c < BX; c += TPX) {
+                const int gx = x0 + c;
+                swy[r][c] = (rok && gx < nx) ? row[gx] : T(0);
+            }
         }
     } else {
         // Transpose: stage z_v = c^2 y_v (2D halo), z_x = g_x y_wx (x halo) and
@@ -184,39 +195,43 @@ stage_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ tile_
         const T* Xv = X + fstr;
         const T* Xwx = X + 2 * fstr;
         const T* Xwy = X + 3 * fstr;
-        for (int idx = tid; idx < SH * SW; idx += NTHREADS) {
-            const int r = idx / SW, c = idx - r * SW;
-            const int gx = x0 - R + c, gy = y0 - R + r;
-            T val = T(0);
-            if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) {
-                const long long o = (long long)gy * pitch + gx;
-                val = C2[o] * Xv[o];
+        for (int r = ty; r < SH; r += TPY) {
+            const int gy = y0 - R + r;
+            const bool rok = gy >= 0 && gy < ny;
+            const long long ro = (long long)(rok ? gy : 0) * pitch;
+            for (int c = tx; c < SW; c += TPX) {
+                const int gx = x0 - R + c;
+                su[r][c] = (rok && gx >= 0 && gx < nx) ? C2[ro + gx] * Xv[ro + gx] : T(0);
             }
-            su[r][c] = val;
         }
-        for (int idx = tid; idx < BY * SW; idx += NTHREADS) {
-            const int r = idx / SW, c = idx - r * SW;
-            const int gx = x0 - R + c, gy = y0 + r;
-            T val = T(0);
-            if (gx >= 0 && gx < nx - 1 && gy < ny) {
-                const T dyn = fs ? T(ny - gy) : T(min(gy + 1, ny - gy));
-                const T dxh = min(T(gx) + T(1.5), T(nx - gx) - T(0.5));
-                const T g = damp<T>(beta0, inv_pml, dyn, pml) - damp<T>(beta0, inv_pml, dxh, pml);
-                val = g * Xwx[(long long)gy * pitch + gx];
+        for (int r = ty; r < BY; r += TPY) {
+            const int gy = y0 + r;
+            const bool rok = gy < ny;
+            const T* row = Xwx + (long long)(rok ? gy : 0) * pitch;
+            const T byn = rok ? damp<T>(beta0, inv_pml, fs ? T(ny - gy) : T(min(gy + 1, ny - gy)), pml) : T(0);
+            for (int c = tx; c < SW; c += TPX) {
+                const int gx = x0 - R + c;
+                T val = T(0);
+                if (rok && gx >= 0 && gx < nx - 1) {
+                    const T dxh = min(T(gx) + T(1.5), T(nx - gx) - T(0.5));
+                    val = (byn - damp<T>(beta0, inv_pml, dxh, pml)) * row[gx];
+                }
+                swx[r][c] = val;
             }
-            swx[r][c] = val;
         }
-        for (int idx = tid; idx < SH * BX; idx += NTHREADS) {
-            const int r = idx / BX, c = idx - r * BX;
-            const int gx = x0 + c, gy = y0 - R + r;
-            T val = T(0);
-            if (gx < nx && gy >= 0 && gy < ny - 1) {
-                const T dxn = T(min(gx + 1, nx - gx));
-                const T dyh = fs ? (T(ny - gy) - T(0.5)) : min(T(gy) + T(1.5), T(ny - gy) - T(0.5));
-                const T g = damp<T>(beta0, inv_pml, dxn, pml) - damp<T>(beta0, inv_pml, dyh, pml);
-                val = g * Xwy[(long long)gy * pitch + gx];
+        for (int r = ty; r < SH; r += TPY) {
+            const int gy = y0 - R + r;
+            const bool rok = gy >= 0 && gy < ny - 1;
+            const T* row = Xwy + (long long)(rok ? gy : 0) * pitch;
+            const T byh = rok ? damp<T>(beta0, inv_pml,
+                                        fs ? (T(ny - gy) - T(0.5)) : min(T(gy) + T(1.5), T(ny - gy) - T(0.5)), pml)
+                              : T(0);
+            for (int c = tx; c < BX; c += TPX) {
+                const int gx = x0 + c;
+                T val = T(0);
+                if (rok && gx < nx) val = (damp<T>(beta0, inv_pml, T(min(gx + 1, nx - gx)), pml) - byh) * row[gx];
+                swy[r][c] = val;
             }
-            swy[r][c] = val;
         }
     }
     __syncthreads();
@@ -463,20 +478,32 @@ leapfrog_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ ti
             pwym[b][c] = in ? Pn[3 * fstr + o] : T(0);
             pc2[b][c] = in ? C2[o] : T(0);
         }
-    for (int idx = tid; idx < SH * SW; idx += NTHREADS) {
-        const int r = idx / SW, c = idx - r * SW;
-        const int gx = x0 - R + c, gy = y0 - R + r;
-        su[r][c] = (gx >= 0 && gx < nx && gy >= 0 && gy < ny) ? Cn[(long long)gy * pitch + gx] : T(0);
+    for (int r = ty; r < SH; r += TPY) {
+        const int gy = y0 - R + r;
+        const bool rok = gy >= 0 && gy < ny;
+        const T* row = Cn + (long long)(rok ? gy : 0) * pitch;
+        for (int c = tx; c < SW; c += TPX) {
+            const int gx = x0 - R + c;
+            su[r][c] = (rok && gx >= 0 && gx < nx) ? row[gx] : T(0);
+        }
     }
-    for (int idx = tid; idx < BY * SW; idx += NTHREADS) {
-        const int r = idx / SW, c = idx - r * SW;
-        const int gx = x0 - R + c, gy = y0 + r;
-        swx[r][c] = (gx >= 0 && gx < nx - 1 && gy < ny) ? Cn[2 * fstr + (long long)gy * pitch + gx] : T(0);
+    for (int r = ty; r < BY; r += TPY) {
+        const int gy = y0 + r;
+        const bool rok = gy < ny;
+        const T* row = Cn + 2 * fstr + (long long)(rok ? gy : 0) * pitch;
+        for (int c = tx; c < SW; c += TPX) {
+            const int gx = x0 - R + c;
+            swx[r][c] = (rok && gx >= 0 && gx < nx - 1) ? row[gx] : T(0);
+        }
     }
-    for (int idx = tid; idx < SH * BX; idx += NTHREADS) {
-        const int r = idx / BX, c = idx - r * BX;
-        const int gx = x0 + c, gy = y0 - R + r;
-        swy[r][c] = (gx < nx && gy >= 0 && gy < ny - 1) ? Cn[3 * fstr + (long long)gy * pitch + gx] : T(0);
+    for (int r = ty; r < SH; r += TPY) {
+        const int gy = y0 - R + r;
+        const bool rok = gy >= 0 && gy < ny - 1;
+        const T* row = Cn + 3 * fstr + (long long)(rok ? gy : 0) * pitch;
+        for (int c = tx; c < BX; c += TPX) {
+            const int gx = x0 + c;
+            swy[r][c] = (rok && gx < nx) ? row[gx] : T(0);
+        }
     }
     __syncthreads();
     const T sig = P->has_src ? (T)P->sigma[0] : T(0);

@@ -59,7 +59,7 @@ struct __align__(16) TileInfo {
     float* Y;
     float* A;
     long long fstr;
-    int x0, y0, nx, ny, pitch, pml, fs, src_i, src_j, pad0;
+    int x0, y0, nx, ny, pitch, pml, fs, src_i, src_j, shot;
     float beta0, inv_pml, idx1, idx2, sig, xs;   // xs: per-problem scale of H X (Krylov)
 };
 
@@ -269,8 +269,9 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
     __syncthreads();
 
     const bool has_u = HASU && a.u >= 0, has_a = a.a >= 0;
-    // (the leap-frog step, EPI 2, does not read v)
-    const uint32_t bytes = (uint32_t)((L::BOX_FLOATS - (EPI == 2 ? BYv * BX : 0) + (has_u ? 4 * BYv * BX : 0)) * 4) +
+    // (the leap-frog step, EPI 2, does not read v; the gradient pass, EPI 3, neither v nor c^2)
+    const uint32_t bytes = (uint32_t)((L::BOX_FLOATS - (EPI >= 2 ? BYv * BX : 0) - (EPI == 3 ? BYv * BX : 0) +
+                                       (has_u ? 4 * BYv * BX : 0)) * 4) +
                            (has_a ? 4 * BYv * BX * 4 : 0);
     int issued = 0;
 
@@ -308,6 +309,7 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
                 ti.fs = P->fs;
                 ti.src_i = P->src_i;
                 ti.src_j = P->src_j;
+                ti.shot = P->shot;
                 ti.beta0 = P->fbeta0;
                 ti.inv_pml = P->finv_pml;
                 ti.idx1 = P->finv_dx;
@@ -321,8 +323,8 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
                 tma_load_4d(st + L::U_OFF, map_of(maps, kx, 0), x0 - TX, y0 - R, 0, cx, &full[s]);
                 tma_load_4d(st + L::WX_OFF, map_of(maps, kx, 1), x0 - TX, y0, 2, cx, &full[s]);
                 tma_load_4d(st + L::WY_OFF, map_of(maps, kx, 2), x0, y0 - R, 3, cx, &full[s]);
-                if (EPI != 2) tma_load_4d(st + L::V_OFF, map_of(maps, kx, 3), x0, y0, 1, cx, &full[s]);
-                tma_load_2d(st + L::C2_OFF, maps + 10, x0, y0, &full[s]);
+                if (EPI < 2) tma_load_4d(st + L::V_OFF, map_of(maps, kx, 3), x0, y0, 1, cx, &full[s]);
+                if (EPI != 3) tma_load_2d(st + L::C2_OFF, maps + 10, x0, y0, &full[s]);
                 if (has_u)
                     tma_load_4d(st + L::PU_OFF, map_of(maps, a.u, 4), x0, y0, 0, a.u == 0 ? 0 : a.u - 1,
                                 &full[s]);
@@ -423,7 +425,7 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
                 Yg[3 * fstr + o] = wyp;
             };
             bool paired = false;
-            if constexpr (NR == 2 && (EPI == 1 || EPI == 2)) {
+            if constexpr (NR == 2 && EPI >= 1) {
                 // Both rows of this thread as packed pairs (rows below the free-surface
                 // band: the interior stencils apply to both).
                 const int ly0 = 2 * ty;
@@ -458,6 +460,14 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
                         dw0 = fmaf(stag<R>(k), sw.x + (wcol[R - 1 - k] - wcol[R + k]), dw0);
                         dw1 = fmaf(stag<R>(k), sw.y + (wcol[R - k] - wcol[R + k + 1]), dw1);
                     }
+                    if constexpr (EPI == 3) {
+                        // FWI gradient pass: grad += gscale q_v (L u + D w) of X (m = c^2)
+                        float* G = (float*)a.grad + (long long)ti.shot * fstr;
+                        const long long o0 = (long long)j0 * ti.pitch + i;
+                        const float gs = (float)a.gscale;
+                        G[o0] += gs * spa[BYv * BX + ly0 * BX + tx] * (lap0 * idx2 + dw0 * idx1);
+                        if (j1 < ny) G[o0 + ti.pitch] += gs * spa[BYv * BX + ly0 * BX + BX + tx] * (lap1 * idx2 + dw1 * idx1);
+                    } else {
                     const float byn0 = dampf(beta0, inv_pml, fs ? (float)(ny - j0) : (float)min(j0 + 1, ny - j0), pml);
                     const float byn1 = dampf(beta0, inv_pml, fs ? (float)(ny - j1) : (float)min(j1 + 1, ny - j1), pml);
                     const float byh0 = dampf(beta0, inv_pml,
@@ -518,6 +528,7 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
                         }
                     }
                     }   // EPI 1
+                    }   // EPI 1, 2
                 }
             }
 #pragma unroll
@@ -571,6 +582,12 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
                                         fs ? (float)(ny - j) - 0.5f : fminf((float)j + 1.5f, (float)(ny - j) - 0.5f),
                                         pml);
                 const int pt = ly * BX + tx;
+                if constexpr (EPI == 3) {
+                    float* G = (float*)a.grad + (long long)ti.shot * fstr;
+                    G[(long long)j * ti.pitch + i] += (float)a.gscale * spa[BYv * BX + pt] *
+                                                      ((uxx + uyy) * idx2 + (dwx + dwy) * idx1);
+                    continue;
+                }
                 if constexpr (EPI == 2) {
                     leapfrog_point(i, j, pt, ucol[r + R], sc2[pt], uxx + uyy, dwx + dwy, dux, duy, bxn, bxh,
                                    byn, byh, wxrow[0], wcol[r + R]);
@@ -783,6 +800,27 @@ int launch_leapfrog_tma(int R, const ProblemDev* probs, const int* tbase, int np
     a.dt = dt;
     if (R == 4) return launch_variant<4, 18, 18, 4, 2, false>(probs, tbase, nprob, ntiles, a, err, s);
     if (R == 2) return launch_variant<2, 18, 18, 4, 2, false>(probs, tbase, nprob, ntiles, a, err, s);
+    return -1;
+}
+
+// The FWI gradient pass (EPI 3): grad += gscale q_v (L u + D w) of vector a.x, q = a.gq (its
+// four fields ride in the A box); same tiles as the leap-frog step.
+int launch_grad_tma(int R, const ProblemDev* probs, const int* tbase, int nprob, int ntiles,
+                    const StageArgs& a_in, int* err, cudaStream_t s) {
+    if (ntiles <= 0) return nprob > 0 ? -1 : 0;
+    if (!g_num_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 1;
+    }
+    StageArgs a = a_in;
+    a.u = -1;
+    a.a = a.gq;
+    a.y_out = -1;
+    a.acc_out = -1;
+    if (R == 4) return launch_variant<4, 18, 18, 4, 3, false>(probs, tbase, nprob, ntiles, a, err, s);
+    if (R == 2) return launch_variant<2, 18, 18, 4, 3, false>(probs, tbase, nprob, ntiles, a, err, s);
     return -1;
 }
 

@@ -131,8 +131,8 @@ def test_autotuner_picks_a_timed_variant():
     B = Batch(gms)
     B.step("faber", 0.04, 1.1e-3, 8, 1)
     info = B.kernel_variant()
-    assert 0 <= info["variant"] < 4
     times = info["probe_us"]
+    assert len(times) == 7 and 0 <= info["variant"] < len(times)
     assert all(t > 0 for t in times)
     assert times[info["variant"]] == min(times)
 
