@@ -167,6 +167,8 @@ struct ewv_model {
     int* d_rec = nullptr;
     int* d_nrec = nullptr;      // receivers per shot
     double* d_sigma = nullptr;
+    float* d_btab = nullptr;    // damping profile at half-cell distances (FP32 TMA passes)
+    int nbtab = 0;
     double* d_kry = nullptr;
     long long* d_clk = nullptr;
     double* d_tclk = nullptr;
@@ -382,6 +384,8 @@ ProblemDev make_problem(ewv_model* m, int shot, int tile_base) {
     P.inv_dx2 = 1.0 / (d.dx * d.dx);
     P.inv_pml = d.pml_width > 0 ? 1.0 / d.pml_width : 0.0;
     P.fbeta0 = (float)P.beta0;
+    P.btab = m->d_btab;
+    P.nbtab = m->nbtab;
     P.finv_pml = (float)P.inv_pml;
     P.finv_dx = (float)P.inv_dx;
     P.finv_dx2 = (float)P.inv_dx2;
@@ -1300,6 +1304,17 @@ int ewv_create_model(const ewv_model_desc* desc, ewv_model_t* out) {
     if (e == cudaSuccess) e = cudaMalloc(&m->d_nrec, sizeof(int) * (size_t)d.nshots);
     if (e == cudaSuccess) e = cudaMemset(m->d_nrec, 0, sizeof(int) * (size_t)d.nshots);
     if (e == cudaSuccess) e = cudaMalloc(&m->d_sigma, sizeof(double) * (size_t)MAX_SIGMA * d.nshots);
+    // beta at distance d = k/2 cells from the first ghost line (Sec. 2 profile), k = 0 .. 2 pml
+    m->nbtab = 2 * d.pml_width + 1;
+    {
+        std::vector<float> bt((size_t)m->nbtab, 0.f);
+        for (int k = 0; k < m->nbtab && d.pml_width > 0; ++k) {
+            const double r = 1.0 - (0.5 * k) / d.pml_width;
+            bt[k] = (float)(d.beta0 * r * r);
+        }
+        if (e == cudaSuccess) e = cudaMalloc(&m->d_btab, sizeof(float) * bt.size());
+        if (e == cudaSuccess) e = cudaMemcpy(m->d_btab, bt.data(), sizeof(float) * bt.size(), cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess) e = cudaMalloc(&m->d_kry, sizeof(double) * (size_t)KRY_STRIDE * d.nshots);
     if (e == cudaSuccess) e = cudaMalloc(&m->d_clk, sizeof(long long) * 4 * (size_t)d.nshots);
     if (e == cudaSuccess) e = cudaMalloc(&m->d_tclk, sizeof(double) * 2 * (size_t)d.nshots);
@@ -1321,6 +1336,7 @@ int ewv_destroy_model(ewv_model_t m) {
     cudaFree(m->d_rec);
     cudaFree(m->d_nrec);
     cudaFree(m->d_sigma);
+    cudaFree(m->d_btab);
     cudaFree(m->d_kry);
     cudaFree(m->d_clk);
     cudaFree(m->d_tclk);

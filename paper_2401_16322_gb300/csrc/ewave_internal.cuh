@@ -54,6 +54,7 @@ struct ProblemDev {
     int nz, nfields;      // 2D: 1 and 4 (u, v, w_x, w_y); 3D: nz and 5 (w_z added)
     int src_k, tiles_z;   // 3D: source plane, tiles along z (KC3 planes each); 2D: 0, 1
     int pchunks, pchunk_base;   // flat pointwise passes: chunks of this problem's vector, first
+    int nbtab, pad2;      // entries of btab
     double beta0, inv_dx, inv_dx2, inv_pml;
     double f_peak, t0, amp;
     long long field_stride, vec_stride;
@@ -67,6 +68,7 @@ struct ProblemDev {
     long long* clk;       // [4]: step within call, recording cursor, (unused), (unused)
     double* tclk;         // [2]: t_start, dt of the current call
     const void* tmaps;    // FP32: this problem's TMA tensor maps (kernels_tma.cu), else null
+    const float* btab;    // beta0 (1 - d/delta)^2 at distances d = k/2 cells, k < nbtab (FP32)
     float fbeta0, finv_pml, finv_dx, finv_dx2;   // FP32 copies of the damping / grid constants
 };
 

@@ -61,6 +61,8 @@ struct __align__(16) TileInfo {
     long long fstr;
     int x0, y0, nx, ny, pitch, pml, fs, src_i, src_j, shot;
     float beta0, inv_pml, idx1, idx2, sig, xs;   // xs: per-problem scale of H X (Krylov)
+    const float* btab;       // damping at half-cell distances (ProblemDev::btab)
+    int nbtab, pad3;
 };
 
 // The consumers read a stage's TileInfo with 16-byte shared loads into registers.
@@ -214,6 +216,13 @@ __device__ __forceinline__ float2 cent_tree2(float2 u, const float2 (&p)[R]) {
         return add2(fma2(f2s(cent<R>(1)), p[0], mul2(f2s(cent<R>(0)), u)), mul2(f2s(cent<R>(2)), p[1]));
 }
 
+// beta at 2 d = k half cells from the first ghost line (zero beyond the layer).  Columns and
+// rows past the grid edge (ragged tiles, never stored) give k <= 0; the unsigned test sends
+// negative k to zero as well, so the table is never read outside its n entries.
+__device__ __forceinline__ float btab_at(const float* t, int n, int k) {
+    return (unsigned)k < (unsigned)n ? __ldg(t + k) : 0.f;
+}
+
 __device__ __forceinline__ float dampf(float beta0, float inv_pml, float d, int pml) {
     if (pml <= 0) return 0.f;
     const float r = 1.f - d * inv_pml;
@@ -310,6 +319,8 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
                 ti.src_i = P->src_i;
                 ti.src_j = P->src_j;
                 ti.shot = P->shot;
+                ti.btab = P->btab;
+                ti.nbtab = P->nbtab;
                 ti.beta0 = P->fbeta0;
                 ti.inv_pml = P->finv_pml;
                 ti.idx1 = P->finv_dx;
@@ -381,8 +392,10 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
             for (int q = 0; q < NR + 2 * R; ++q) ucol[q] = su[(NR * ty + q) * L::SW + cxs];
 #pragma unroll
             for (int q = 0; q < NR + 2 * R - 1; ++q) wcol[q] = swy[(NR * ty + q) * BX + tx];
-            const float bxn = dampf(beta0, inv_pml, (float)min(i + 1, nx - i), pml);
-            const float bxh = dampf(beta0, inv_pml, fminf((float)i + 1.5f, (float)(nx - i) - 0.5f), pml);
+            const float* btab = ti.btab;
+            const int nbt = ti.nbtab;
+            const float bxn = btab_at(btab, nbt, 2 * min(i + 1, nx - i));
+            const float bxh = btab_at(btab, nbt, min(2 * i + 3, 2 * (nx - i) - 1));
             const bool in_x = i < nx;
             const float chx = chf * ti.xs;     // ch xs: K = cx X + ch xs (H X + sigma)
             // EPI 2: one leap-frog step (Sec. 3.1) at a point.  X = level n; the A box holds
@@ -468,12 +481,10 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
                         G[o0] += gs * spa[BYv * BX + ly0 * BX + tx] * (lap0 * idx2 + dw0 * idx1);
                         if (j1 < ny) G[o0 + ti.pitch] += gs * spa[BYv * BX + ly0 * BX + BX + tx] * (lap1 * idx2 + dw1 * idx1);
                     } else {
-                    const float byn0 = dampf(beta0, inv_pml, fs ? (float)(ny - j0) : (float)min(j0 + 1, ny - j0), pml);
-                    const float byn1 = dampf(beta0, inv_pml, fs ? (float)(ny - j1) : (float)min(j1 + 1, ny - j1), pml);
-                    const float byh0 = dampf(beta0, inv_pml,
-                                             fs ? (float)(ny - j0) - 0.5f : fminf((float)j0 + 1.5f, (float)(ny - j0) - 0.5f), pml);
-                    const float byh1 = dampf(beta0, inv_pml,
-                                             fs ? (float)(ny - j1) - 0.5f : fminf((float)j1 + 1.5f, (float)(ny - j1) - 0.5f), pml);
+                    const float byn0 = btab_at(btab, nbt, 2 * (fs ? ny - j0 : min(j0 + 1, ny - j0)));
+                    const float byn1 = btab_at(btab, nbt, 2 * (fs ? ny - j1 : min(j1 + 1, ny - j1)));
+                    const float byh0 = btab_at(btab, nbt, fs ? 2 * (ny - j0) - 1 : min(2 * j0 + 3, 2 * (ny - j0) - 1));
+                    const float byh1 = btab_at(btab, nbt, fs ? 2 * (ny - j1) - 1 : min(2 * j1 + 3, 2 * (ny - j1) - 1));
                     const int pt0 = ly0 * BX + tx, pt1 = pt0 + BX;
                     if constexpr (EPI == 2) {
                         leapfrog_point(i, j0, pt0, uc.x, sc2[pt0], lap0, dw0, ux0, uy0, bxn, bxh, byn0, byh0,
@@ -577,10 +588,8 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
                     duy = stag_tree<R>(dy);
                 }
                 if (!in_x || j >= ny) continue;
-                const float byn = dampf(beta0, inv_pml, fs ? (float)(ny - j) : (float)min(j + 1, ny - j), pml);
-                const float byh = dampf(beta0, inv_pml,
-                                        fs ? (float)(ny - j) - 0.5f : fminf((float)j + 1.5f, (float)(ny - j) - 0.5f),
-                                        pml);
+                const float byn = btab_at(btab, nbt, 2 * (fs ? ny - j : min(j + 1, ny - j)));
+                const float byh = btab_at(btab, nbt, fs ? 2 * (ny - j) - 1 : min(2 * j + 3, 2 * (ny - j) - 1));
                 const int pt = ly * BX + tx;
                 if constexpr (EPI == 3) {
                     float* G = (float*)a.grad + (long long)ti.shot * fstr;
