@@ -37,7 +37,7 @@ TARGET = 1e-4
 PICKS = [(0, 32), (1, 0), (5, 0)]
 # Cheapest candidate found by the in-run search on GB300 (used by the CPU reference arm; the
 # GPU arm re-runs the search and reports what it finds).
-DEFAULT_SELECTION = ("hork", 24, 5)     # method, m, dt in units of the leap-frog step
+DEFAULT_SELECTION = ("hork-horner", 24, 5)     # method, m, dt in units of the leap-frog step
 WORKLOAD_NAME = ("batched: 64 shots on 1001x501 + 8 models 201x101..801x401, layered "
                  "1500-4500 m/s, 8th order, free surface, 40-pt PML, Ricker 10 Hz, T=2 s")
 
