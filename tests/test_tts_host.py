@@ -67,3 +67,36 @@ def test_pml_beta0_reflection_choice():
 def test_candidate_cost():
     c = Candidate("faber", 50, 0.01, err=1e-5, step_ms=20.0, nsteps=200)
     assert c.cost_s == pytest.approx(4.0)
+
+
+class _FakeModel:
+    """Records the option calls that tts.base_method makes on a model."""
+
+    def __init__(self):
+        self.window, self.form, self.lf = None, None, None
+
+    def set_krylov_window(self, q):
+        self.window = q
+
+    def set_hork_form(self, form):
+        self.form = form
+
+    def set_leapfrog_variant(self, v):
+        self.lf = v
+
+
+@pytest.mark.parametrize("name,base,window,form,lf", [
+    ("krylov-w2", "krylov", 2, "low-storage", None),
+    ("krylov", "krylov", 0, "low-storage", None),
+    ("hork-horner", "hork", 0, "horner", None),
+    ("hork", "hork", 0, "low-storage", None),
+    ("leapfrog-difference", "leapfrog", 0, "low-storage", 2),
+    ("leapfrog", "leapfrog", 0, "low-storage", 0),
+    ("faber", "faber", 0, "low-storage", None),
+])
+def test_candidate_names_map_to_library_methods_and_options(name, base, window, form, lf):
+    from paper_2401_16322_gb300.tts import base_method
+    mds = [_FakeModel(), _FakeModel()]
+    assert base_method(mds, name) == base
+    for md in mds:
+        assert (md.window, md.form, md.lf) == (window, form, lf)
