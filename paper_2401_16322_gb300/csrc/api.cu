@@ -729,14 +729,16 @@ struct Ctx {
                   int nparity, F&& one_step) {
         for (int n = 0; n < nsteps; ++n) {
             const int par = n % nparity;
-            const bool use_graph = E->graphs_enabled && !E->graphs_broken && n >= nparity;
-            if (!use_graph) {
+            const int slot = E->timing ? 2 + 2 * ((n / nparity) & 1) : 0;
+            auto key = std::make_tuple(method, m, dt, g, c0, c1, par + slot);
+            // the first steps of a call launch directly (one-time work such as the tile-shape
+            // tuning happens there), unless an earlier call already captured this step
+            const bool ok = E->graphs_enabled && !E->graphs_broken;
+            auto it = ok ? E->graphs.find(key) : E->graphs.end();
+            if (!ok || (n < nparity && it == E->graphs.end())) {
                 one_step(n);
                 continue;
             }
-            const int slot = E->timing ? 2 + 2 * ((n / nparity) & 1) : 0;
-            auto key = std::make_tuple(method, m, dt, g, c0, c1, par + slot);
-            auto it = E->graphs.find(key);
             if (it == E->graphs.end()) {
                 const long long L0 = *launches;
                 Engine::StepGraph sg;
@@ -1800,7 +1802,10 @@ static int read_timing(Engine* E, cudaStream_t s, std::string& err, double* tota
 
 static int set_variant(Engine* E, int v) {
     if (v < -1 || v >= TMA_NUM_VARIANTS) return EWV_ERR_INVALID_ARG;
-    E->tma_variant = v;
+    if (E->tma_variant != v) {
+        E->tma_variant = v;
+        E->drop_graphs();   // captured steps hold the previous variant's launches
+    }
     return EWV_OK;
 }
 

@@ -60,3 +60,24 @@ def test_kernel_timing_inside_replayed_graphs(prec):
             assert n == 6 * 12 and ms > 0.0
         out.append(g.get_state(0))
     assert np.array_equal(out[0], out[1])
+
+
+def test_graph_from_an_earlier_call_is_replayed_bit_exactly():
+    """A step graph captured in one call is replayed from the first step of the next call
+    (one-step calls, as the FWI forward makes): the result equals direct launches."""
+    nx, ny = 83, 37
+    om = oracle_model(nx, ny, layered(nx, ny, 17), pml=10, fs=True)
+    rec = np.array([[x * om.dx, 0.0] for x in range(2, nx - 2, 9)])
+    U0 = tuple(smooth_random_state([f.shape for f in om.zeros_state()], 12))
+    out = []
+    for graphs in (True, False):
+        g = gpu_model(om, "f32", p=8, max_receivers=len(rec))
+        g.set_source_receivers(0, 41 * om.dx, 2 * om.dx, 25.0, 0.05, 1e3, rec)
+        g.enable_graphs(graphs)
+        g.set_kernel_variant(0)
+        g.bind_seismogram(1)
+        g.set_state(0, flatten(U0))
+        for n in range(4):
+            g.step("hork", 0.03 + n * 1.1e-3, 1.1e-3, 6, 1)
+        out.append(g.get_state(0))
+    assert np.array_equal(out[0], out[1])
