@@ -1486,12 +1486,12 @@ static int set_src_rec(ewv_model_t m, int shot, const double* spos, double f_pea
         if (nd == 2) idx[2] = 0;
         return true;
     };
-    long long si[3];
+    long long si[3] = {0, 0, 0};
     if (!node(spos, si)) return fail(m->err, EWV_ERR_INVALID_ARG, "source outside the grid");
     std::vector<int> off(nrec);
     std::vector<int32_t> ij((size_t)nd * nrec);
     for (int r = 0; r < nrec; ++r) {
-        long long ri[3];
+        long long ri[3] = {0, 0, 0};
         if (!node(rpos + (size_t)nd * r, ri))
             return fail(m->err, EWV_ERR_INVALID_ARG, "receiver %d outside the grid", r);
         off[r] = (int)((ri[2] * m->d.ny + ri[1]) * m->pitch + ri[0]);
@@ -2249,7 +2249,6 @@ int ewv_adjoint_step(ewv_model_t m, int method, double t, double dt, int deg,
 int ewv_adjoint_inject(ewv_model_t m, void* adj_state, const void* values) {
     if (!m || !adj_state || !values) return EWV_ERR_INVALID_ARG;
     const int ns = m->d.nshots, nr = m->d.max_receivers;
-    const size_t vb = m->vec_elems * m->elem;
     // lambda_u[rec] += values[shot][rec]; receivers of one shot are added in order
     if (nr == 0) return EWV_OK;
     if (!aligned(adj_state)) return fail(m->err, EWV_ERR_BAD_SIZE_OR_ALIGNMENT, "adj_state must be 256-B aligned");

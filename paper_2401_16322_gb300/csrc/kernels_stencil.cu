@@ -120,7 +120,6 @@ stage_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ tile_
     if (a.fin_mode != FIN_NONE && P->kry[KRY_ACTIVE] == 0.0) return;   // Arnoldi stopped
 
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int tid = ty * TPX + tx;
     const int nx = P->nx, ny = P->ny, pitch = P->pitch, pml = P->pml;
     const bool fs = P->fs != 0;
     const int lt = blockIdx.x - P->tile_base;
@@ -453,7 +452,7 @@ leapfrog_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ ti
     __shared__ T swy[SH][BX];
     const int pid = tile_prob[blockIdx.x];
     const ProblemDev* P = probs + pid;
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TPX + tx;
+    const int tx = threadIdx.x, ty = threadIdx.y;
     const int nx = P->nx, ny = P->ny, pitch = P->pitch, pml = P->pml;
     const bool fs = P->fs != 0;
     const int lt = blockIdx.x - P->tile_base;
