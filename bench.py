@@ -488,6 +488,17 @@ def config1_fp64_study():
             "evaluated": cand, "search_s": st.seconds}
 
 
+def max_over_ranks(value, dist=None, device="cuda"):
+    """The largest value over the ranks (the slowest rank sets a step's time); the value itself
+    on a single process."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ------------------------------------------------------------------------- reference arm
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -612,10 +623,7 @@ def run_ours(args):
     batch.enable_kernel_timing(False)
     launches = batch.launch_count() - launches0
     ms_per_step = elapsed_ms / args.steps
-    if dist:
-        t = torch.tensor([ms_per_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_per_step = float(t.item())
+    ms_per_step = max_over_ranks(ms_per_step, dist)
 
     # roofline of the fused stencil pass (live, CUDA events around every launch)
     words = pass_words(method, m)
