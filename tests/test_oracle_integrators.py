@@ -312,3 +312,30 @@ def test_leapfrog_energy_without_damping():
         Es.append(energy(LF[0], LF[1]))
     Es = np.array(Es)
     assert np.max(np.abs(Es - Es[0])) <= 1e-10 * np.max(np.abs(Es))
+
+
+@pytest.mark.parametrize("mm", [1, 3, 8, 16])
+def test_horner_recursion_is_the_hork_polynomial(mm):
+    """The evaluation order the library offers for HORK: V_{m+1} = x, V_j = x + (dt/j) H~ V_{j+1}
+    (j = m .. 1) on the dense augmented operator gives the oracle's HORK step (the paper's
+    low-storage stages), i.e. the same degree-m Taylor polynomial."""
+    m, s, U, Ht, x, exact, dt, t = _setup()
+    V = x.copy()
+    for j in range(mm, 0, -1):
+        V = x + (dt / j) * (Ht @ V)
+    got = flatten(rk.hork_step(m, U, s, t, dt, mm))
+    assert rel_l2(got, V[:m.n]) < 1e-13
+
+
+def test_leapfrog_difference_form_is_the_same_update():
+    """The difference form of the averaged leap-frog update: with d = u^n - u^{n-1},
+    u^{n+1} = u^n + (d (1 - b dt/2) + dt^2 rhs) / (1 + b dt/2) equals
+    ((2u^n - u^{n-1})/dt^2 + b u^{n-1}/(2 dt) + rhs) / (1/dt^2 + b/(2 dt)) for any values."""
+    rng = np.random.default_rng(29)
+    u, um, rhs = rng.standard_normal((3, 1000))
+    b = rng.uniform(0.0, 300.0, 1000)
+    dt = rng.uniform(1e-5, 5e-3, 1000)
+    plain = ((2 * u - um) / dt ** 2 + b * um / (2 * dt) + rhs) / (1 / dt ** 2 + b / (2 * dt))
+    d = u - um
+    diff = u + (d * (1 - b * dt / 2) + dt ** 2 * rhs) / (1 + b * dt / 2)
+    assert np.allclose(diff, plain, rtol=1e-12, atol=1e-12 * np.abs(plain).max())
