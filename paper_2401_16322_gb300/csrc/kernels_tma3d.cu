@@ -163,6 +163,12 @@ __device__ __forceinline__ float ce_tree(float u, const float (&p)[R]) {
         return fmaf(ce3<R>(1), p[0], ce3<R>(0) * u) + ce3<R>(2) * p[1];
 }
 
+// beta at 2 d = k half cells from the first ghost line, from the model's table (zero beyond
+// the layer; negative k, from rows and columns past a ragged grid edge, also gives zero)
+__device__ __forceinline__ float bt3(const float* t, int n, int k) {
+    return (unsigned)k < (unsigned)n ? __ldg(t + k) : 0.f;
+}
+
 __device__ __forceinline__ float dmp(float beta0, float inv_pml, float d, int pml) {
     if (pml <= 0) return 0.f;
     const float r = 1.f - d * inv_pml;
@@ -328,6 +334,8 @@ stage_tma3d_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__
             // the number of stages of this task is known from its geometry: recompute it
             const int pid = find_task_problem(tbase, nprob, task);
             const ProblemDev* P = probs + pid;
+            const float* btab = P->btab;
+            const int nbt = P->nbtab;
             const int tiles_x = (P->nx + BX - 1) / BX;
             const int tiles_y = (P->ny + BY3 - 1) / BY3;
             const int lt = task - __ldg(tbase + pid);
@@ -363,12 +371,10 @@ stage_tma3d_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__
                     const float* su = st + L::U_OFF;
                     const float* swx = st + L::WX_OFF;
                     const float* swy = st + L::WY_OFF;
-                    const float bxn = dmp(beta0, inv_pml, (float)min(i + 1, nx - i), pml);
-                    const float bxh = dmp(beta0, inv_pml, fminf((float)i + 1.5f, (float)(nx - i) - 0.5f), pml);
-                    const float bzn = dmp(beta0, inv_pml, fs ? (float)(nz - c) : (float)min(c + 1, nz - c), pml);
-                    const float bzh = dmp(beta0, inv_pml,
-                                          fs ? (float)(nz - c) - 0.5f : fminf((float)c + 1.5f, (float)(nz - c) - 0.5f),
-                                          pml);
+                    const float bxn = bt3(btab, nbt, 2 * min(i + 1, nx - i));
+                    const float bxh = bt3(btab, nbt, min(2 * i + 3, 2 * (nx - i) - 1));
+                    const float bzn = bt3(btab, nbt, 2 * (fs ? nz - c : min(c + 1, nz - c)));
+                    const float bzh = bt3(btab, nbt, fs ? 2 * (nz - c) - 1 : min(2 * c + 3, 2 * (nz - c) - 1));
 #pragma unroll
                     for (int r = 0; r < NR; ++r) {
                         const int ly = NR * ty + r;
@@ -425,8 +431,8 @@ stage_tma3d_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__
                             for (int q = 0; q < R; ++q) dz[q] = uq[r][R - q] - uq[r][R + 1 + q];
                             duz = st_tree<R>(dz);
                         }
-                        const float byn = dmp(beta0, inv_pml, (float)min(j + 1, ny - j), pml);
-                        const float byh = dmp(beta0, inv_pml, fminf((float)j + 1.5f, (float)(ny - j) - 0.5f), pml);
+                        const float byn = bt3(btab, nbt, 2 * min(j + 1, ny - j));
+                        const float byh = bt3(btab, nbt, min(2 * j + 3, 2 * (ny - j) - 1));
                         const int pt = ly * BX + tx;
                         const float xwx = wxrow[0];
                         const float xwy = swy[(ly + R) * BX + tx];
