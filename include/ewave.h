@@ -383,7 +383,8 @@ int ewv_batch_kernel_variant(ewv_batch_t batch, int* variant, int* tile_height, 
                              int* stages, double* probe_us);
 
 /* Event timing of the fused stencil passes (the hot kernel): when enabled, every stencil
- * pass launch is bracketed by a pair of CUDA events on the stream the pass runs on.
+ * pass launch (each integrator pass and each leap-frog step, inside captured step graphs
+ * too) is bracketed by a pair of CUDA events on the stream the pass runs on.
  * ewv_*kernel_timing synchronises the stream, returns the summed device time (ms) and the
  * number of timed launches since the last read, and resets both. */
 int ewv_enable_kernel_timing(ewv_model_t model, int enable);
