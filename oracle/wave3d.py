@@ -2,8 +2,11 @@
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 
-The paper is two-dimensional (Eq. 1, Sec. 2).  This module is the builder's own extension,
-written so that it reduces to Eq. 1 when one axis is dropped.  State U = (u, v, w_x, w_y, w_z);
+The paper is two-dimensional (Eq. 1, Sec. 2).  This module is the builder's own extension.
+Without damping it reduces to Eq. 1 when one axis is dropped, and with one axis undamped its
+v row does too; its w rows use the mean of the other two damping profiles, so with damping
+they do not (a PML that reduces exactly needs a further auxiliary field).  The damping is
+this extension's own reading.  State U = (u, v, w_x, w_y, w_z);
 x, y horizontal (i, j), z vertical (k = 0 the top, depth grows with k):
 
     (HU)_u   = v
