@@ -55,10 +55,11 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64 and FWI side runs")
     ap.add_argument("--n3d", type=int, default=400, help="edge of the 3D cube (side run)")
     ap.add_argument("--select", default=None, metavar="METHOD,M,K",
-                    help="with --no-search: integrator, m and step in leap-frog steps "
+                    help="with --no-search: integrator (faber, hork, hork-horner, krylov, krylov-wQ, "
+                         "rk32, rk44, leapfrog, leapfrog-difference), m and step in leap-frog steps "
                          f"(default {','.join(map(str, DEFAULT_SELECTION))})")
     ap.add_argument("--variant", type=int, default=-1,
-                    help="FP32 stencil-pass variant (0..3; -1: autotune at first use)")
+                    help="FP32 stencil-pass variant (0..6; -1: autotune at first use)")
     ap.add_argument("--case", default="full", choices=["full", "small", "medium", "cube"],
                     help="small / medium: the 1001x501 model with 4 / 16 shots (profiling); "
                          "cube: only the 3D side run (--n3d, --check3d)")
