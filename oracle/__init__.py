@@ -18,6 +18,10 @@ wave modeling" (arXiv 2401.16322):
 * ``rk``         -- HORK (Sec. 3.2), RK3-2 and RK4-4 (Sec. 3.1).
 * ``leapfrog``   -- the two-step scheme of Sec. 3.1.
 * ``simulate``   -- time loops, receivers and the relative-L2 error measure.
+* ``adjoint``    -- discrete adjoints of the Faber and HORK steps, the Krylov step's
+                    linearisation, and the FWI misfit gradient.
+* ``wave3d``     -- the builder's 3D extension of Eq. (1) used by the 3D GPU passes.
+* ``wave3d_pml`` -- a 3D PML with an auxiliary field that reduces exactly to Eq. (1).
 
 Every floating-point quantity is IEEE double.  The module shares no code with the CUDA
 path; the only module both sides import is the seeded input generator
