@@ -45,3 +45,17 @@ def test_null_handle_errors_without_gpu(lib):
     assert lib.ewv_set_stream(None, None) == -1
     assert lib.ewv_last_error(None) == b"null handle"
     assert lib.ewv_create_model(None, None) == -1
+
+
+def test_checkpoint_stride_host_logic_matches_oracle(lib):
+    # pure host arithmetic in the library: bit-exact against the oracle's schedule
+    import ctypes
+    from oracle.adjoint import checkpoint_stride as o_stride
+    out = ctypes.c_int()
+    for n in range(0, 60):
+        for b in range(1, 25):
+            assert lib.ewv_checkpoint_stride(n, b, ctypes.byref(out)) == 0
+            assert out.value == o_stride(n, b), (n, b)
+    assert lib.ewv_checkpoint_stride(-1, 4, ctypes.byref(out)) == -1
+    assert lib.ewv_checkpoint_stride(10, 0, ctypes.byref(out)) == -1
+    assert lib.ewv_checkpoint_stride(10, 4, None) == -1

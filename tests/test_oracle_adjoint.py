@@ -166,3 +166,18 @@ def test_krylov_fwi_gradient_matches_central_differences():
         fd = (Jp - Jm) / (2 * eps)
         an = float(np.sum(grad * dm))
         assert abs(fd - an) <= 1e-3 * abs(fd), (seed, fd, an)
+
+
+def test_checkpoint_stride_is_the_smallest_stride_within_budget():
+    """Brute force: storing the states at steps 0, s, 2s, ... (those below nsteps) keeps at
+    most ``budget`` of them, and no smaller stride does (stride 1 when everything fits)."""
+    from oracle.adjoint import checkpoint_stride
+
+    def stored(n, s):
+        return len(range(0, n, s))
+
+    for n in range(0, 80):
+        for b in range(1, 30):
+            s = checkpoint_stride(n, b)
+            assert s >= 1 and stored(n, s) <= b, (n, b, s)
+            assert s == 1 or stored(n, s - 1) > b, (n, b, s)
