@@ -20,6 +20,8 @@ wave modeling" (arXiv 2401.16322):
 * ``simulate``   -- time loops, receivers and the relative-L2 error measure.
 * ``adjoint``    -- discrete adjoints of the Faber and HORK steps, the Krylov step's
                     linearisation, and the FWI misfit gradient.
+* ``krylov_adjoint`` -- the exact discrete adjoint of the Krylov step (reverse mode through
+                    Arnoldi and the small exponential) and the FWI gradient through it.
 * ``leapfrog_adjoint`` -- the leap-frog step as a sparse linear map, its discrete adjoint and
                     the FWI gradient through it.
 * ``wave3d``     -- the builder's 3D extension of Eq. (1) used by the 3D GPU passes.
