@@ -20,6 +20,8 @@ wave modeling" (arXiv 2401.16322):
 * ``simulate``   -- time loops, receivers and the relative-L2 error measure.
 * ``adjoint``    -- discrete adjoints of the Faber and HORK steps, the Krylov step's
                     linearisation, and the FWI misfit gradient.
+* ``krylov_adaptive`` -- a KIOPS-style Krylov step with adaptive dimension and substeps
+                    under an a-posteriori error estimate (the improvement Secs. 3.2 and 6 name).
 * ``krylov_adjoint`` -- the exact discrete adjoint of the Krylov step (reverse mode through
                     Arnoldi and the small exponential) and the FWI gradient through it.
 * ``leapfrog_adjoint`` -- the leap-frog step as a sparse linear map, its discrete adjoint and
