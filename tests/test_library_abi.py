@@ -59,3 +59,15 @@ def test_checkpoint_stride_host_logic_matches_oracle(lib):
     assert lib.ewv_checkpoint_stride(-1, 4, ctypes.byref(out)) == -1
     assert lib.ewv_checkpoint_stride(10, 0, ctypes.byref(out)) == -1
     assert lib.ewv_checkpoint_stride(10, 4, None) == -1
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    # the binding has no fallback: without the built library every entry point raises
+    from paper_2401_16322_gb300 import ewave
+    saved = ewave._lib
+    ewave._lib = None
+    try:
+        with pytest.raises(ewave.EwaveError, match="missing"):
+            ewave.load_library(str(tmp_path / "libewave.so"))
+    finally:
+        ewave._lib = saved
