@@ -95,7 +95,7 @@ extern "C" {
 /* ---- model description ------------------------------------------------------------- */
 typedef struct ewv_model_desc {
     int dims;            /* 2 (the paper's case) or 3 (the extension above)               */
-    int nx, ny;          /* grid nodes; nx, ny >= 2                                       */
+    int nx, ny;          /* grid nodes; 2 <= nx, ny <= 2^30                               */
     double dx;           /* grid spacing (m), dx = dy (Sec. 2.1)                          */
     int fd_order;        /* 8 (paper, Sec. 2.1) or 4 (no free surface only)               */
     int pml_width;       /* PML thickness delta in grid points (0 = no damping)           */
@@ -105,7 +105,7 @@ typedef struct ewv_model_desc {
     int nshots;          /* independent shots (states) sharing this velocity model        */
     int src_taylor_p;    /* p of the augmented matrix H~ (Eq. matrix_ampli), 1..24        */
     int max_receivers;   /* receivers per shot (seismogram row width)                     */
-    int nz;              /* dims = 3: node planes along z (>= 2); ignored for dims = 2    */
+    int nz;              /* dims = 3: node planes along z (2..2^30); ignored for dims = 2 */
 } ewv_model_desc;
 
 typedef struct ewv_layout_info {
@@ -124,7 +124,9 @@ typedef struct ewv_batch* ewv_batch_t;
 /* ---- lifetime and binding ---------------------------------------------------------- */
 
 /* Create a model from desc (copied).  Uses the current CUDA device.  Errors:
- * INVALID_ARG (bad field, e.g. fd_order 4 with a free surface, p out of range). */
+ * INVALID_ARG (a field out of range, e.g. p, or a padded grid nz * ny * pitch above
+ * 2^31 - 1 elements: receiver offsets are 32-bit), checked before any CUDA call;
+ * UNSUPPORTED (a free surface with fd_order 4); CUDA (allocation failed). */
 int ewv_create_model(const ewv_model_desc* desc, ewv_model_t* out);
 int ewv_destroy_model(ewv_model_t model);
 

@@ -1278,7 +1278,10 @@ int ewv_create_model(const ewv_model_desc* desc, ewv_model_t* out) {
     if (!desc || !out) return EWV_ERR_INVALID_ARG;
     *out = nullptr;
     const ewv_model_desc& d = *desc;
-    if ((d.dims != 2 && d.dims != 3) || (d.dims == 3 && d.nz < 2) || d.nx < 2 || d.ny < 2 ||
+    // extents up to 2^30 keep the pitch arithmetic below in int range; the 32-bit receiver
+    // offsets bound the padded grid further
+    if ((d.dims != 2 && d.dims != 3) || (d.dims == 3 && (d.nz < 2 || d.nz > (1 << 30))) ||
+        d.nx < 2 || d.ny < 2 || d.nx > (1 << 30) || d.ny > (1 << 30) ||
         !(d.dx > 0) || (d.fd_order != 4 && d.fd_order != 8) ||
         d.pml_width < 0 || d.beta0 < 0 || (d.precision != EWV_F32 && d.precision != EWV_F64) ||
         d.nshots < 1 || d.src_taylor_p < 1 || d.src_taylor_p > MAX_P || d.max_receivers < 0)
@@ -1479,9 +1482,9 @@ static int set_src_rec(ewv_model_t m, int shot, const double* spos, double f_pea
     const int ext[3] = {m->d.nx, m->d.ny, m->nz};
     auto node = [&](const double* pos, long long* idx) {
         for (int a = 0; a < nd; ++a) {
-            if (!std::isfinite(pos[a])) return false;
-            idx[a] = (long long)std::floor(pos[a] / m->d.dx + 0.5);
-            if (idx[a] < 0 || idx[a] >= ext[a]) return false;
+            const double f = std::floor(pos[a] / m->d.dx + 0.5);   // range-checked before the cast
+            if (!(f >= 0.0 && f < (double)ext[a])) return false;
+            idx[a] = (long long)f;
         }
         if (nd == 2) idx[2] = 0;
         return true;

@@ -71,3 +71,18 @@ def test_missing_library_fails_loudly(tmp_path):
             ewave.load_library(str(tmp_path / "libewave.so"))
     finally:
         ewave._lib = saved
+
+
+def test_create_model_rejects_bad_extents_without_gpu(lib):
+    # descriptor checks return before any CUDA call
+    import ctypes
+    from paper_2401_16322_gb300 import ewave
+    base = dict(dims=2, nx=64, ny=32, dx=10.0, fd_order=8, pml_width=4, beta0=10.0,
+                free_surface=1, precision=0, nshots=1, src_taylor_p=8, max_receivers=4, nz=1)
+    out = ctypes.c_void_p()
+    for bad in (dict(nx=1), dict(ny=(1 << 30) + 1), dict(nx=2 ** 31 - 1),
+                dict(dims=3, nz=(1 << 30) + 1), dict(dims=3, nz=1), dict(dims=4),
+                dict(src_taylor_p=0), dict(fd_order=6), dict(dx=0.0), dict(nshots=0)):
+        d = ewave.ModelDesc(**{**base, **bad})
+        assert lib.ewv_create_model(ctypes.byref(d), ctypes.byref(out)) == -1, bad
+        assert not out.value
