@@ -140,8 +140,12 @@ def apply_H(m: Model, state, src=None):
 
     ``src`` is ``None`` or ``(j, i, value)``: ``value`` is added to the v-row at node (i, j)
     (the f entry of Eq. 1 / the W y term of the augmented matrix).  A three-dimensional
-    model goes to ``oracle.wave3d.apply_H3`` (src ``(k, j, i, value)``).
+    model goes to ``oracle.wave3d.apply_H3`` (src ``(k, j, i, value)``), and one with the
+    auxiliary field psi (``oracle.wave3d_pml.Model3DPML``) to ``apply_H3p``.
     """
+    if getattr(m, "aux_psi", False):
+        from .wave3d_pml import apply_H3p
+        return apply_H3p(m, state, src)
     if getattr(m, "dims", 2) == 3:
         from .wave3d import apply_H3
         return apply_H3(m, state, src)

@@ -3,6 +3,7 @@ exact reduction to Eq. 1 with damping on a field that does not vary along an und
 reduction to the 3D operator without damping, and a stable dense spectrum."""
 import numpy as np
 import pytest
+import scipy.linalg as sl
 
 from oracle import operator as O
 from oracle import wave3d as W
@@ -96,3 +97,72 @@ def test_dense_spectrum_is_stable():
     ev = np.linalg.eigvals(P.assemble_H3p(m).toarray())
     assert ev.real.max() < 1e-9 * m.beta0
     assert ev.real.min() < -0.1 * m.beta0
+
+
+def _tiny3p():
+    """A 8 x 7 x 7 cube on the auxiliary-field PML with a source, a smooth random state (psi
+    included) and the dense augmented operator [[H, W], [0, J/dt]] built from assemble_H3p."""
+    from oracle import source as src_mod
+    nx, ny, nz, pml = 8, 7, 7, 2
+    c = layered3d(nx, ny, nz, 5, vmin=1500, vmax=3000)
+    m = P.Model3DPML(nx, ny, nz, 10.0, 8, pml, default_beta0(3000.0, pml, 10.0), True, c)
+    s = W.PointSource3D(m, 40.0, 30.0, 20.0, 40.0, 0.02, amp=1e3, p=8)
+    U = tuple(smooth_random_state(P.field_shapes(m), 8))
+    dt, t = 1e-3, 0.012
+    n, p = m.n, s.p
+    Ht = np.zeros((n + p, n + p))
+    Ht[:n, :n] = P.assemble_H3p(m).toarray()
+    N = nx * ny * nz
+    k, j, i = s.node
+    Ht[N + (k * ny + j) * nx + i, n:] = s.W(t, dt)
+    for q in range(p - 1):
+        Ht[n + q, n + q + 1] = 1.0 / dt
+    x = np.concatenate([flatten(U), src_mod.e_p(p)])
+    exact = (sl.expm(dt * Ht) @ x)[:n]
+    return m, s, U, dt, t, Ht, x, exact
+
+
+def test_integrators_run_on_the_auxiliary_field_pml():
+    """The oracle's integrators reach H through oracle.operator.apply_H, which sends a
+    Model3DPML to apply_H3p: Faber and Krylov converge to the dense exponential, and HORK(m)
+    is the Taylor polynomial of exp(dt H~)."""
+    from oracle import faber, krylov, rk
+    from oracle.simulate import rel_l2
+    m, s, U, dt, t, Ht, x, exact = _tiny3p()
+    assert m.n == sum(int(np.prod(f)) for f in P.field_shapes(m))
+    params = faber.ellipse_params(m.c_max, m.beta0, m.dx, 8, dims=3, free_surface=True)
+    errs = [rel_l2(flatten(faber.faber_step(m, U, s, t, dt, deg, params)), exact)
+            for deg in (10, 40)]
+    assert errs[0] > errs[1] and errs[1] < 1e-11
+    assert rel_l2(flatten(krylov.krylov_step(m, U, s, t, dt, 40)), exact) < 1e-11
+    taylor, term = x.copy(), x.copy()
+    for jj in range(1, 7):
+        term = dt * (Ht @ term) / jj
+        taylor = taylor + term
+    assert rel_l2(flatten(rk.hork_step(m, U, s, t, dt, 6)), taylor[:m.n]) < 1e-13
+
+
+def test_auxiliary_field_pml_absorbs_what_the_mean_reading_reflects():
+    """A Gaussian pulse in a homogeneous 24^3 cube with a 6-point PML on every side (Faber 30,
+    dt 2 ms, to T = 80 ms, when the pulse has entered the layer): the field left in the
+    interior is ~1e-2 of the start with the 3D operator of oracle.wave3d (its w rows take the
+    mean of the other two damping profiles, so where one profile is on they see half of it),
+    and over 20x less with the auxiliary-field PML."""
+    from oracle import faber
+    n, pml, dx, c0 = 24, 6, 10.0, 2000.0
+    c = np.full((n, n, n), c0)
+    b0 = default_beta0(c0, pml, dx)
+    z = (np.arange(n) - (n - 1) / 2) * dx
+    Z, Y, X = np.meshgrid(z, z, z, indexing="ij")
+    u0 = np.exp(-(X ** 2 + Y ** 2 + Z ** 2) / (2 * 15.0 ** 2))
+    inner = (slice(pml, n - pml),) * 3
+    params = faber.ellipse_params(c0, b0, dx, 8, dims=3, free_surface=False)
+    left = {}
+    for name, M in (("mean", W.Model3D), ("aux", P.Model3DPML)):
+        m = M(n, n, n, dx, 8, pml, b0, False, c)
+        U = (u0.copy(),) + tuple(np.zeros(s) for s in m.field_shapes()[1:])
+        for k in range(40):
+            U = faber.faber_step(m, U, None, k * 2e-3, 2e-3, 30, params)
+        left[name] = np.linalg.norm(U[0][inner]) / np.linalg.norm(u0[inner])
+    assert left["mean"] > 5e-3
+    assert left["aux"] < 2e-3 and left["aux"] < left["mean"] / 10.0, left
