@@ -18,6 +18,12 @@ exact on the span of its basis.
 Dissipation is |R| - 1 and dispersion the relative phase error arg(R) / (omega dt) - 1.  Both
 vanish for the exact exponential.  This is host-side analysis of the methods; it is not part
 of the GPU path.
+
+``trace_errors`` is the paper's own measure (Sec. 4.1), taken on recorded traces instead of
+amplification factors: with F_ref and F_appr the discrete Fourier transforms of a reference
+and an approximate receiver trace, F_ref = exp(k + i l) F_appr defines k(omega) (dissipation)
+and l(omega) (dispersion), and the two errors are the means of |k| and |l| over the
+frequencies where |F_ref| or |F_appr| exceeds 1 % of max |F_ref|.
 """
 import math
 
@@ -34,8 +40,11 @@ def faber_coefficients(dt, gamma, c0, c1, m, nodes=None):
 
 
 def amplification(method, m, omega, dt, ellipse=None):
-    """R(i omega dt) of ``method`` (faber needs ``ellipse`` = (gamma, c0, c1))."""
-    z = 1j * np.asarray(omega, dtype=np.float64) * dt
+    """R(i omega dt) of ``method`` (faber needs ``ellipse`` = (gamma, c0, c1)).  A complex
+    omega = lambda / i evaluates R at z = lambda dt for an eigenvalue lambda with damping."""
+    omega = np.asarray(omega)
+    omega = omega.astype(np.complex128 if np.iscomplexobj(omega) else np.float64)
+    z = 1j * omega * dt
     if method in ("hork", "hork-horner"):      # the same polynomial, either evaluation order
         out, term = np.ones_like(z), np.ones_like(z)
         for k in range(1, m + 1):
@@ -94,3 +103,28 @@ def report(candidates, f_peak, omega_spectrum, ellipse):
                     "band_dissipation": db, "band_dispersion": pb,
                     "spectrum_dissipation": ds, "spectrum_dispersion": ps})
     return out
+
+
+def trace_errors(ref, appr, threshold=0.01):
+    """(dissipation, dispersion) of trace ``appr`` against ``ref`` by Sec. 4.1's Fourier measure.
+
+    Readings of what the paper leaves open: the transform is the real DFT of the traces as
+    sampled (same length and spacing; the sample spacing scales omega only and cancels);
+    "reference or approximated" is the union of the two amplitude tests; l is the principal
+    value of arg(F_ref / F_appr), which is the phase error itself while it stays below pi, as
+    it does for the small errors the measure is meant for.  A selected bin with F_appr = 0
+    gives an infinite dissipation error."""
+    ref = np.asarray(ref, dtype=np.float64)
+    appr = np.asarray(appr, dtype=np.float64)
+    if ref.shape != appr.shape or ref.ndim != 1:
+        raise ValueError("traces must be 1-D and of equal length")
+    Fr, Fa = np.fft.rfft(ref), np.fft.rfft(appr)
+    peak = float(np.max(np.abs(Fr)))
+    if peak == 0.0:
+        raise ValueError("the reference trace is zero")
+    sel = (np.abs(Fr) > threshold * peak) | (np.abs(Fa) > threshold * peak)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        ratio = Fr[sel] / Fa[sel]
+        k = np.where(Fa[sel] == 0, np.inf, np.log(np.abs(ratio)))
+        l = np.where(Fa[sel] == 0, 0.0, np.angle(ratio))
+    return float(np.mean(np.abs(k))), float(np.mean(np.abs(l)))
