@@ -128,3 +128,27 @@ def test_trace_errors_select_bins_above_one_percent_of_either_trace():
     assert max(trace_errors(ref, ref + _tone(n, 300, 0.005))) < 1e-14
     diss, _ = trace_errors(ref, ref + _tone(n, 300, 0.02))
     assert diss > 1.0
+
+
+def test_trace_errors_show_leapfrog_second_order():
+    """On traces of the oracle (homogeneous 1.2 x 1 km at 10 m, c = 3 km/s, 15 Hz Ricker, one
+    receiver 300 m from the source, T = 0.3 s, before any boundary reflection arrives), the
+    leap-frog scheme's dispersion and dissipation errors against an HORK 8 reference at 1 ms
+    (whose own errors by this measure against Faber 40 at 1 ms are ~1e-10) fall by 4 when dt
+    halves: second order."""
+    from oracle.model import Model
+    from oracle.simulate import receiver_nodes, run
+    from oracle.source import PointSource
+    from paper_2401_16322_gb300.analysis import trace_errors
+    m = Model(121, 101, 10.0, 8, 0, 0.0, False, np.full((101, 121), 3000.0))
+    src = PointSource(m, 600.0, 700.0, 15.0, 0.08, amp=1e3, p=12)
+    rec = receiver_nodes(m, np.array([[600.0, 400.0]]))
+    _, ref = run(m, "hork", 1e-3, 300, src, rec, m=8)
+    errs = []
+    for dt in (1e-3, 0.5e-3, 0.25e-3):
+        stride = int(round(1e-3 / dt))
+        _, s = run(m, "leapfrog", dt, 300 * stride, src, rec)
+        errs.append(trace_errors(ref[:, 0], s[stride - 1::stride, 0]))
+    assert 0.01 < errs[0][1] < 0.03
+    for a, b in zip(errs, errs[1:]):
+        assert 3.6 < a[0] / b[0] < 4.4 and 3.6 < a[1] / b[1] < 4.4, errs
