@@ -21,7 +21,7 @@ Readings (the paper defers gamma, c0, c1 and a_j to its earlier Faber paper):
 * a_j are the Faber coefficients of z -> exp(dt z): the w^j coefficient of
   exp(dt psi(w)) on |w| = 1, computed by the trapezoid rule on N >= max(4m, 64) nodes.
 
-Pins: tests/test_oracle_faber.py (Bessel J/I closed forms, the Taylor special case, and
+Pins: tests/test_oracle_integrators.py (Bessel J/I closed forms, the Taylor special case, and
 convergence of the step to the dense matrix exponential).
 """
 import math

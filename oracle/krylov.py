@@ -21,7 +21,7 @@ approximant with scaling and squaring (Higham, SIAM J. Matrix Anal. Appl. 26 (20
 written here from the published method: Pade coefficients from their closed form,
 s = max(0, ceil(log2(|A|_1 / theta_13))), theta_13 = 5.371920351148152.
 
-Pins: tests/test_oracle_krylov.py (expm against scipy.linalg.expm and closed forms; with
+Pins: tests/test_oracle_integrators.py (expm against scipy.linalg.expm and closed forms; with
 m = n the step reproduces the dense exponential; orthonormality of the basis).
 """
 import math

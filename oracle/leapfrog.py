@@ -17,7 +17,7 @@ w_t ~ (w^{n+1} - w^{n-1})/(2 dt).  Readings of what Sec. 3.1 leaves open:
 
 The state is (u^n, u^{n-1}, w_x^n, w_x^{n-1}, w_y^n, w_y^{n-1}).
 
-Pins: tests/test_oracle_leapfrog.py (second-order convergence; conservation of the
+Pins: tests/test_oracle_integrators.py (second-order convergence; conservation of the
 discrete leap-frog energy at beta = 0 without free surface).
 """
 import numpy as np

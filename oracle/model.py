@@ -17,7 +17,8 @@ location of the variable being updated.
 
 Parity status: pinned indirectly (energy conservation at beta0 = 0 and the dense
 exponential checks use this module); the profile formula itself is "parity unpinned"
-beyond tests/test_oracle_model.py's closed-form spot values.
+beyond the closed-form spot values of tests/test_oracle_operator.py
+(``test_damping_profile_values``).
 """
 from dataclasses import dataclass, field
 import math

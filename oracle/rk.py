@@ -12,7 +12,7 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 * RK4-4 (Sec. 3.1, classical tableau; not printed in the paper): stages at t_n,
   t_n + dt/2 (twice), t_n + dt with weights 1/6, 1/3, 1/3, 1/6.
 
-Pins: tests/test_oracle_rk.py (HORK equals the degree-m Taylor polynomial of the dense
+Pins: tests/test_oracle_integrators.py (HORK equals the degree-m Taylor polynomial of the dense
 exp(dt H~); RK3-2 and RK4-4 equal their stability polynomials on a dense H and converge
 at orders 2 and 4).
 """

@@ -13,8 +13,9 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
   operator J/dt and W column p-1-k = dt^k r^(k)(t_n) amp/dx^2 -- which is the same
   exponential after the change of variables y_{p-1-k} = (s/dt)^k / k!.
 
-Pins: tests/test_oracle_source.py (derivatives against the closed form and central
-differences; the tail exponential reproduces the Taylor polynomial of f).
+Pins: tests/test_oracle_integrators.py (derivatives against sympy's symbolic derivatives of
+the closed form; the tail exponential reproduces the Taylor polynomial of f; the
+nearest-node rule).
 """
 import math
 
