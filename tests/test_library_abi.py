@@ -86,3 +86,25 @@ def test_create_model_rejects_bad_extents_without_gpu(lib):
         d = ewave.ModelDesc(**{**base, **bad})
         assert lib.ewv_create_model(ctypes.byref(d), ctypes.byref(out)) == -1, bad
         assert not out.value
+
+
+def test_oracle_and_product_share_no_code(repo_root):
+    # the product package never imports the oracle, and the oracle imports nothing of the
+    # product (the seeded input generator is imported by the tests, not by oracle/)
+    import ast
+    import glob
+
+    def imported(path):
+        tree = ast.parse(open(path).read())
+        names = set()
+        for node in ast.walk(tree):
+            if isinstance(node, ast.Import):
+                names.update(a.name.split(".")[0] for a in node.names)
+            elif isinstance(node, ast.ImportFrom) and node.module and node.level == 0:
+                names.add(node.module.split(".")[0])
+        return names
+
+    for p in glob.glob(os.path.join(repo_root, "paper_2401_16322_gb300", "*.py")):
+        assert "oracle" not in imported(p), p
+    for p in glob.glob(os.path.join(repo_root, "oracle", "*.py")):
+        assert "paper_2401_16322_gb300" not in imported(p), p
