@@ -108,3 +108,27 @@ def test_oracle_and_product_share_no_code(repo_root):
         assert "oracle" not in imported(p), p
     for p in glob.glob(os.path.join(repo_root, "oracle", "*.py")):
         assert "paper_2401_16322_gb300" not in imported(p), p
+
+
+def test_oracle_is_used_only_by_smoke_and_the_cpu_baseline(repo_root):
+    # outside tests/, only __graft_entry__.smoke() and bench.py's CPU-baseline sampler (used
+    # by the cpu_baseline figure and the reference arm) import the oracle
+    import ast
+
+    def users(path):
+        tree = ast.parse(open(path).read())
+        out = set()
+        for fn in ast.walk(tree):
+            if isinstance(fn, (ast.FunctionDef, ast.AsyncFunctionDef)):
+                for node in ast.walk(fn):
+                    mod = (node.module if isinstance(node, ast.ImportFrom) else
+                           node.names[0].name if isinstance(node, ast.Import) else None)
+                    if mod and mod.split(".")[0] == "oracle":
+                        out.add(fn.name)
+        top = {n for n in tree.body if isinstance(n, (ast.Import, ast.ImportFrom))}
+        assert not any((getattr(n, "module", None) or n.names[0].name).split(".")[0] == "oracle"
+                       for n in top), path
+        return out
+
+    assert users(os.path.join(repo_root, "__graft_entry__.py")) == {"smoke"}
+    assert users(os.path.join(repo_root, "bench.py")) == {"cpu_oracle_sample"}
