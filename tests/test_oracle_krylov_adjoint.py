@@ -197,3 +197,19 @@ def _forward(model, dt, nsteps, mm, window):
             S.append(U[0][rec[:, 0], rec[:, 1]].copy())
         out.append(np.array(S))
     return out
+
+
+@pytest.mark.parametrize("window", [None, 3])
+def test_gram_schmidt_intermediates_are_rebuilt_from_the_basis(window):
+    """Before the k-th subtraction of column j the tape's vector equals
+    A v_j - sum_{k0 <= i < k} h_ij v_i: the reverse sweep can rebuild it from V, A V and H."""
+    c, beta0 = _base()
+    m = _model(c, beta0)
+    tp = KrylovTape(m, _state(m, 31), _src(m), 0.02, 1.5e-3, 10, window=window)
+    V, H = tp.V_full, tp.H_full
+    for j in range(tp.m_eff):
+        Av = tp.matvec(V[:, j])
+        k0 = tp.k0[j]
+        for idx, k in enumerate(range(k0, j + 1)):
+            rebuilt = Av - sum((H[i, j] * V[:, i] for i in range(k0, k)), np.zeros_like(Av))
+            assert np.linalg.norm(rebuilt - tp.ws[j][idx]) <= 1e-12 * np.linalg.norm(Av)
