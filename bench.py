@@ -12,8 +12,11 @@ L2, and every simulation starts from a zeroed state.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
-Rank 0 prints one JSON line.  --impl reference times the FP64 CPU oracle on a bounded sample
-of the same workload and scales it to the same metric.
+Rank 0 prints one JSON line (strict JSON: a non-finite number is written as null).  The side
+runs (FP64 single shot, FWI gradients, the 3D cube, the small FP64 study, the dispersion
+table, every search candidate) are summarised in it; --detail-out PATH writes them in full.
+--impl reference times the FP64 CPU oracle on a bounded sample of the same workload, on
+every host core (independent shots in separate processes), and scales it to the same metric.
 """
 import argparse
 import json
@@ -35,6 +38,9 @@ T_END = 2.0
 TARGET = 1e-4
 # Sampled problems for the error measurement: (model index, shot index).
 PICKS = [(0, 32), (1, 0), (5, 0)]
+# Problems on which the selected setting's error is checked after the timed region: one shot
+# of every uneven model and eight shots spread over the 64 of the large model.
+CHECK_PROBLEMS = [(q, 0) for q in range(1, 9)] + [(0, k) for k in (0, 9, 18, 27, 32, 36, 45, 54, 63)]
 # Cheapest candidate found by the in-run search on GB300 (used by the CPU reference arm; the
 # GPU arm re-runs the search and reports what it finds).
 DEFAULT_SELECTION = ("hork-horner", 24, 5)     # method, m, dt in units of the leap-frog step
@@ -42,7 +48,7 @@ WORKLOAD_NAME = ("batched: 64 shots on 1001x501 + 8 models 201x101..801x401, lay
                  "1500-4500 m/s, 8th order, free surface, 40-pt PML, Ricker 10 Hz, T=2 s")
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
@@ -63,12 +69,42 @@ def parse():
     ap.add_argument("--case", default="full", choices=["full", "small", "medium", "cube"],
                     help="small / medium: the 1001x501 model with 4 / 16 shots (profiling); "
                          "cube: only the 3D side run (--n3d, --check3d)")
-    ap.add_argument("--check3d", type=int, default=96, help="edge of the 3D accuracy cube")
-    return ap.parse_args()
+    ap.add_argument("--check3d", type=int, default=0,
+                    help="edge of the 3D accuracy cube of a Delta-t_max search (0: time the "
+                         "settings found by that search on a 96^3 cube, and check their error "
+                         "on a 64^3 cube)")
+    ap.add_argument("--detail-out", default=None, metavar="PATH",
+                    help="also write every side run in full to this JSON file")
+    ap.add_argument("--cpu-procs", type=int, default=0,
+                    help="oracle processes of the CPU baseline (0: one per host core)")
+    return ap.parse_args(argv)
 
 
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
+
+
+def finite_or_none(obj):
+    """A copy of ``obj`` (dicts, lists, tuples, numbers, strings) with every non-finite float
+    replaced by None and numpy scalars turned into Python numbers."""
+    if isinstance(obj, dict):
+        return {str(k): finite_or_none(v) for k, v in obj.items()}
+    if isinstance(obj, (list, tuple)):
+        return [finite_or_none(v) for v in obj]
+    if isinstance(obj, bool) or obj is None or isinstance(obj, str):
+        return obj
+    if hasattr(obj, "item") and not isinstance(obj, (int, float)):
+        obj = obj.item()                                  # numpy scalar
+    if isinstance(obj, float):
+        return obj if math.isfinite(obj) else None
+    if isinstance(obj, int):
+        return obj
+    return str(obj)
+
+
+def json_line(obj):
+    """One line of strict JSON (no NaN or Infinity tokens)."""
+    return json.dumps(finite_or_none(obj), allow_nan=False, separators=(", ", ": "))
 
 
 # ------------------------------------------------------------------------- clocks
@@ -178,39 +214,75 @@ def pass_words(method, m):
     raise ValueError(method)
 
 
-def cpu_oracle_sample(workloads, method, m, dt, budget_s, log=log):
-    """Time the FP64 oracle on a bounded sample: steps of ``method`` on one mid-size model
-    (one shot), until ``budget_s`` seconds.  Returns (seconds per grid-point-step, sample
-    description, threads)."""
-    import numpy as np
-    from oracle.faber import ellipse_params
+def _oracle_worker(task):
+    """One oracle process: steps of ``method`` on one shot of one model until ``budget_s``
+    seconds have passed.  Returns (grid-point-steps, seconds, steps)."""
+    (nx, ny, dx, order, pml, beta0, fs, c, sx, sy, f_peak, t0, method, m, dt, t_start,
+     budget_s, ellipse) = task
     from oracle.model import Model as OModel
     from oracle.simulate import run
     from oracle.source import PointSource
-    from paper_2401_16322_gb300.tts import pml_beta0
-    from paper_2401_16322_gb300.workloads import t0_for
-    w = workloads[4]                                   # 458 x 229 model
-    c_max = max(float(x.c.max()) for x in workloads)
-    om = OModel(w.nx, w.ny, w.dx, w.order, w.pml, pml_beta0(c_max, w.pml, w.dx), w.free_surface, w.c)
-    s = w.shots[0]
-    src = PointSource(om, s.sx, s.sy, w.f_peak, t0_for(w.f_peak), 1.0, p=12)
-    params = ellipse_params(c_max, om.beta0, om.dx, om.order, free_surface=om.free_surface)
-    t0 = time.perf_counter()
-    nsteps = 0
+    om = OModel(nx, ny, dx, order, pml, beta0, fs, c)
+    src = PointSource(om, sx, sy, f_peak, t0, 1.0, p=12)
     U = om.zeros_state()
-    # the oracle evaluates HORK in the paper's stages and Krylov with full orthogonalisation
-    om_method = {"hork-horner": "hork", "leapfrog-difference": "leapfrog"}.get(
-        method, "krylov" if method.startswith("krylov") else method)
+    t0w = time.perf_counter()
+    nsteps = 0
     while True:
-        U, _ = run(om, om_method, dt, 1, src=src, m=m, U0=U, t0=0.3 + nsteps * dt, faber_params=params)
+        U, _ = run(om, method, dt, 1, src=src, m=m, U0=U, t0=t_start + nsteps * dt,
+                   faber_params=ellipse)
         nsteps += 1
-        if time.perf_counter() - t0 >= budget_s:
+        if time.perf_counter() - t0w >= budget_s:
             break
-    el = time.perf_counter() - t0
-    per_point_step = el / (nsteps * w.nx * w.ny)
-    desc = (f"oracle {om_method}(m={m}, dt={dt * 1e3:.3f} ms) FP64, {nsteps} steps of one shot on "
-            f"{w.nx}x{w.ny} ({el:.1f} s), scaled by grid-point-steps to the whole batch")
-    return per_point_step, desc, 1
+    return nsteps * nx * ny, time.perf_counter() - t0w, nsteps
+
+
+class OracleSampler:
+    """The FP64 CPU oracle timed on the host cores: ``procs`` processes (spawned, one
+    numpy thread each) each step one shot of the 458 x 229 model of the batched workload for
+    a bounded time, on different shot positions; the rate is the grid-point-steps of all of
+    them over the wall time of the sample.  The oracle runs as it stands; the processes only
+    run independent shots side by side, as the shots of the workload are independent."""
+
+    def __init__(self, procs=0):
+        import multiprocessing as mp
+        self.procs = procs if procs > 0 else (os.cpu_count() or 1)
+        for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[var] = "1"
+        self.pool = mp.get_context("spawn").Pool(self.procs)
+        self.pool.map(abs, range(self.procs))            # start every process before timing
+
+    def sample(self, workloads, method, m, dt, budget_s):
+        """(seconds per grid-point-step of the whole host, description, cores, wall seconds,
+        grid-point-steps sampled)."""
+        from oracle.faber import ellipse_params
+        from paper_2401_16322_gb300.tts import pml_beta0
+        from paper_2401_16322_gb300.workloads import t0_for
+        w = workloads[4]                                   # 458 x 229 model
+        c_max = max(float(x.c.max()) for x in workloads)
+        beta0 = pml_beta0(c_max, w.pml, w.dx)
+        ell = ellipse_params(c_max, beta0, w.dx, w.order, free_surface=w.free_surface)
+        # the oracle evaluates HORK in the paper's stages and Krylov with full orthogonalisation
+        om_method = {"hork-horner": "hork", "leapfrog-difference": "leapfrog"}.get(
+            method, "krylov" if method.startswith("krylov") else method)
+        tasks = []
+        for q in range(self.procs):
+            sx = (40 + (w.nx - 80) * (q + 0.5) / self.procs) * w.dx
+            tasks.append((w.nx, w.ny, w.dx, w.order, w.pml, beta0, w.free_surface, w.c, sx,
+                          w.shots[0].sy, w.f_peak, t0_for(w.f_peak), om_method, m, dt, 0.3,
+                          budget_s, ell))
+        t0 = time.perf_counter()
+        res = self.pool.map(_oracle_worker, tasks, chunksize=1)
+        wall = time.perf_counter() - t0
+        pts = sum(r[0] for r in res)
+        steps = sum(r[2] for r in res)
+        desc = (f"oracle {om_method}(m={m}, dt={dt * 1e3:.3f} ms) FP64 on {self.procs} processes, "
+                f"{steps} steps of {self.procs} shots of the {w.nx}x{w.ny} model in {wall:.1f} s "
+                f"wall, scaled by grid-point-steps to the whole batch")
+        return wall / pts, desc, self.procs, wall, pts
+
+    def close(self):
+        self.pool.terminate()
+        self.pool.join()
 
 
 def batch_points(workloads):
@@ -237,7 +309,7 @@ def fp64_single_shot_estimate(wl, method, m, dt, nsteps, c_max, steps_sample=3):
         e0.record()
         md.step(method, 0.25, dt, m, steps_sample)
         e1.record()
-        torch.cuda.synchronize()
+        md.sync()
         total += e0.elapsed_time(e1) / steps_sample * nsteps * len(w.shots) * 1e-3
         md.close()
     return {"time_to_solution_s": total, "sample": f"{steps_sample} FP64 steps of one shot per "
@@ -289,9 +361,11 @@ SCAN3D = (("faber", (30, 40, 50, 60), tuple(range(24, 1, -1))),
           ("hork-horner", (12, 16, 24), tuple(range(12, 0, -1))),
           ("krylov", (20,), tuple(range(24, 1, -1))))
 LEAPFROG3D_DIVISORS = (1, 2, 3, 4, 6, 8)
+# settings of the last 3D Delta-t_max search (method, m, step in 3D leap-frog steps)
+FIXED3D = (("hork-horner", 16, 3.0), ("faber", 60, 12.0), ("krylov", 20, 8.0), ("leapfrog", 1, 0.5))
 
 
-def config5_3d(n=400, check_n=96, target=TARGET):
+def config5_3d(n=400, check_n=0, target=TARGET):
     """The three-dimensional workload (n^3 layered cube, 8th order, free surface, 30-point ABC,
     Ricker 10 Hz, T = 1 s; FP32).
 
@@ -301,8 +375,9 @@ def config5_3d(n=400, check_n=96, target=TARGET):
        1 .. 1/8 of its step.
     2. Time per step of each passing (method, m) at its Delta-t_max on the n^3 cube, time to
        T, and the roofline of the 3D TMA pass (Faber).
-    check_n = 0 skips the search and times Faber 40 at 6 x and Horner HORK 16 at 3 x (profiling
-    runs)."""
+    check_n = 0 skips the search: the settings of FIXED3D (found by an earlier search) are
+    checked for error and stability on a 64^3 cube of the same construction, then timed.
+    """
     import numpy as np
     import torch
     from paper_2401_16322_gb300 import Model
@@ -324,39 +399,40 @@ def config5_3d(n=400, check_n=96, target=TARGET):
         md.bind_seismogram(nsteps)
         md.reset_state()
         md.step(base_method([md], method), 0.0, dt, m, nsteps)
+        md.sync()
         return md.seismogram(0, md.max_receivers, nsteps)
 
     out = {"workload": f"{n}^3 layered, dx 10 m, 8th order, free surface, 30-pt ABC, Ricker 10 Hz, "
                        "T 1 s, FP32", "target": target, "candidates": []}
     found = []          # (method, m, k, err); k < 1: leap-frog divisor 1/k
+    t_search = time.perf_counter()
+    wc = config_3d(check_n if check_n > 0 else 64, pml=min(20, (check_n or 64) // 4), T=0.5)
+    dt3 = leapfrog_step(c_max, wc.dx, dims=3)
+    ref_md = build(wc, "f64", p=20)
+    ref = simulate(ref_md, "faber", 30, dt3, wc.T)
+    log(f"3D reference {time.perf_counter() - t_search:.1f} s")
+    cmd = build(wc, "f32")
+
+    from paper_2401_16322_gb300 import Batch
+    from paper_2401_16322_gb300.tts import NOISE_GROWTH, POLYNOMIAL, noise_growth
+    cbatch = Batch([cmd])
+    t_quiet = wc.T + 20.0 / wc.f_peak + t0_for(wc.f_peak)
+
+    def err_of(md, method, m, dt):
+        try:
+            err = rel_l2_common(simulate(md, method, m, dt, wc.T), dt, ref, dt3)
+            if err <= target and method in POLYNOMIAL and md is cmd:
+                # the stability check of the 2D search (white noise, source silent)
+                growth = noise_growth([cmd], cbatch, method, m, dt, t_quiet)
+                if not growth <= NOISE_GROWTH:
+                    log(f"3D {method} m={m} dt={dt * 1e3:.3f} ms: noise grows {growth:.3g} x")
+                    return float("inf")
+            return err
+        except Exception as e:       # e.g. a non-finite Arnoldi step
+            log(f"3D {method} m={m} dt={dt * 1e3:.3f} ms: {e}")
+            return float("inf")
+
     if check_n > 0:
-        t_search = time.perf_counter()
-        wc = config_3d(check_n, pml=min(20, check_n // 4), T=0.5)
-        dt3 = leapfrog_step(c_max, wc.dx, dims=3)
-        ref_md = build(wc, "f64", p=20)
-        ref = simulate(ref_md, "faber", 30, dt3, wc.T)
-        log(f"3D reference {time.perf_counter() - t_search:.1f} s")
-        cmd = build(wc, "f32")
-
-        from paper_2401_16322_gb300 import Batch
-        from paper_2401_16322_gb300.tts import NOISE_GROWTH, POLYNOMIAL, noise_growth
-        cbatch = Batch([cmd])
-        t_quiet = wc.T + 20.0 / wc.f_peak + t0_for(wc.f_peak)
-
-        def err_of(md, method, m, dt):
-            try:
-                err = rel_l2_common(simulate(md, method, m, dt, wc.T), dt, ref, dt3)
-                if err <= target and method in POLYNOMIAL and md is cmd:
-                    # the stability check of the 2D search (white noise, source silent)
-                    growth = noise_growth([cmd], cbatch, method, m, dt, t_quiet)
-                    if not growth <= NOISE_GROWTH:
-                        log(f"3D {method} m={m} dt={dt * 1e3:.3f} ms: noise grows {growth:.3g} x")
-                        return float("inf")
-                return err
-            except Exception as e:       # e.g. a non-finite Arnoldi step
-                log(f"3D {method} m={m} dt={dt * 1e3:.3f} ms: {e}")
-                return float("inf")
-
         for method, ms, ks in SCAN3D:
             for m in ms:
                 errs = {}
@@ -372,14 +448,22 @@ def config5_3d(n=400, check_n=96, target=TARGET):
                                lambda k: errs.setdefault(k, err_of(md, "leapfrog", 1, dt3 / k)), target)
             if k is not None:
                 found.append(("leapfrog" if prec == "f32" else "leapfrog_f64", 1, 1.0 / k, errs[k]))
-        ref_md.close()
-        cbatch.close()
-        cmd.close()
-        out["search_s"] = time.perf_counter() - t_search
         out["error_check"] = f"{check_n}^3 cube, T 0.5 s, FP64 Faber 30 at the 3D leap-frog step"
     else:
-        found.append(("faber", 40, 6.0, float("nan")))
-        found.append(("hork-horner", 16, 3.0, float("nan")))
+        # the settings an earlier search found (FIXED3D), each checked for error and
+        # stability on a 64^3 cube
+        for method, m, k in FIXED3D:
+            dt = k * dt3
+            err = err_of(cmd, method, m, dt)
+            if err <= target:
+                found.append((method, m, float(k), err))
+            else:
+                log(f"3D {method} m={m} at {k} x: error {err:.3e} above the target")
+        out["error_check"] = "64^3 cube, T 0.5 s, FP64 Faber 30 at the 3D leap-frog step"
+    ref_md.close()
+    cbatch.close()
+    cmd.close()
+    out["search_s"] = time.perf_counter() - t_search
     # timing on the full cube
     w = config_3d(n)
     dt3 = leapfrog_step(c_max, w.dx, dims=3)
@@ -410,7 +494,7 @@ def config5_3d(n=400, check_n=96, target=TARGET):
             e0.record()
             dev.step(bm, t_live, dt, m, ns)
             e1.record()
-            torch.cuda.synchronize()
+            dev.sync()
             kms, kn = dev.kernel_timing()
             dev.enable_kernel_timing(False)
         except Exception as e:
@@ -440,6 +524,8 @@ def config5_3d(n=400, check_n=96, target=TARGET):
     exp = [c for c in out["candidates"] if c["method"] != "leapfrog"]
     if exp:
         out["selected"] = min(exp, key=lambda c: c["time_to_T_s"])
+    fr = [c["roofline"]["frac"] for c in out["candidates"] if "roofline" in c]
+    out["roofline_frac"] = max(fr) if fr else None
     lf = [c for c in out["candidates"] if c["method"] == "leapfrog"]
     if lf:
         out["leapfrog_best"] = min(lf, key=lambda c: c["time_to_T_s"])
@@ -507,6 +593,7 @@ def run_reference(args):
         return 0
     from paper_2401_16322_gb300.tts import leapfrog_step
     from paper_2401_16322_gb300.workloads import config_batched
+    sampler = OracleSampler(args.cpu_procs)
     wl = config_batched()
     c_max = max(float(w.c.max()) for w in wl)
     dt_cfl = leapfrog_step(c_max, wl[0].dx, wl[0].order)
@@ -515,26 +602,98 @@ def run_reference(args):
     nsteps = int(round(T_END / dt))
     pts = batch_points(wl)
     budget = max(1.0, min(args.cpu_sample_s, 60.0 / max(1, args.steps + args.warmup)))
-    vals = []
+    vals, walls, sampled = [], [], 0
     for it in range(args.warmup + args.steps):
-        pps, desc, cores = cpu_oracle_sample(wl, method, m, dt, budget)
+        pps, desc, cores, wall, npts = sampler.sample(wl, method, m, dt, budget)
         if it >= args.warmup:
             vals.append(pps * pts * nsteps)
+            walls.append(wall)
+            sampled += npts
+    sampler.close()
     v = statistics.mean(vals)
+    # a step of this arm is one bounded sample of the oracle (its wall time is ms_per_step);
+    # the value is the whole batch's time to solution at the sampled rate (extrapolated)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": statistics.mean(walls) * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD_NAME, "method": method, "m": m, "dt_ms": dt * 1e3,
                        "T_s": T_END, "grid_points": pts, "nsteps": nsteps},
+            "extrapolated": True,
+            "sampled_grid_point_steps": sampled, "sample_wall_s": sum(walls),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": desc},
+                             "sample": desc, "extrapolated": True},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+    print(json_line(line), flush=True)
     return 0
 
 
 # ------------------------------------------------------------------------- our arm
+def check_problems(wl, models, method, m, dt, nsteps, c_max, dt_cfl, study, target):
+    """Seismogram error of the selected setting on CHECK_PROBLEMS (17 of the 72 problems),
+    taken from the last simulation of the timed region, against an FP64 Faber reference of
+    degree 60 at dt / q (q the smallest integer with dt / q <= 6 leap-frog steps; the Faber
+    coefficients beyond degree 60 are below 1e-15 there), or of degree 30 at the leap-frog
+    step when dt is smaller.  On the three problems of the search the reference is compared
+    with the search's own FP64 reference."""
+    from paper_2401_16322_gb300 import Batch
+    from paper_2401_16322_gb300.tts import (build_models, common_ellipse, rel_l2_common,
+                                            sampled_workloads, simulate)
+    t0 = time.perf_counter()
+    got = []
+    for wi, si in CHECK_PROBLEMS:
+        md = models[wi]
+        nrec = len(wl[wi].shots[si].rec)
+        s = md.seismo.view(md.nshots, md.capacity, md.max_receivers)[si, :nsteps, :nrec]
+        got.append(s.double().cpu().numpy())
+    if dt >= dt_cfl * (1 - 1e-9):
+        q = max(1, math.ceil(dt / (6.0 * dt_cfl) - 1e-9))
+        dt_ref, m_ref = dt / q, 60
+    else:
+        dt_ref, m_ref = dt_cfl, 30
+    sw = sampled_workloads(wl, CHECK_PROBLEMS)
+    ref_models = build_models(sw, "f64", p=20, c_max=c_max)
+    common_ellipse(ref_models, c_max)
+    rb = Batch(ref_models)
+    n_ref = simulate(ref_models, rb, "faber", m_ref, dt_ref, nsteps * dt)
+    errs, cross = [], []
+    for (wi, si), md, w, g in zip(CHECK_PROBLEMS, ref_models, sw, got):
+        ref = md.seismogram(0, len(w.shots[0].rec), n_ref)
+        errs.append(rel_l2_common(g, dt, ref, dt_ref))
+        if study is not None and (wi, si) in PICKS:
+            sref = study.refs[PICKS.index((wi, si))]
+            cross.append(rel_l2_common(ref, dt_ref, sref, study.dt_ref))
+    rb.close()
+    for md in ref_models:
+        md.close()
+    worst = int(max(range(len(errs)), key=lambda i: errs[i] if math.isfinite(errs[i]) else 1e300))
+    return {"problems": len(errs), "of": sum(len(w.shots) for w in wl),
+            "max_rel_err": max(errs) if all(math.isfinite(e) for e in errs) else float("inf"),
+            "worst_problem": list(CHECK_PROBLEMS[worst]),
+            "all_within_target": all(e <= target for e in errs),
+            "reference": f"FP64 faber m={m_ref} dt={dt_ref * 1e3:.4f} ms",
+            "reference_vs_search_reference": max(cross) if cross else None,
+            "per_problem": [[wi, si, e] for (wi, si), e in zip(CHECK_PROBLEMS, errs)],
+            "seconds": time.perf_counter() - t0}
+
+
+def stability_margin(method, m, dt, dt_cfl, ellipse):
+    """omega_edge / omega_top for a polynomial integrator: omega_edge is the smallest
+    frequency where the amplification factor on the imaginary axis exceeds 1 (+1e-12);
+    omega_top = 2 / (leap-frog step) is the top of the undamped interior spectrum."""
+    import numpy as np
+    from paper_2401_16322_gb300.analysis import amplification
+    if method not in ("faber", "hork", "hork-horner", "rk32", "rk44"):
+        return None
+    top = 2.0 / dt_cfl
+    om = np.linspace(top / 4000, 3 * top, 12000)
+    a = np.abs(amplification(method, m, om, dt, ellipse))
+    bad = np.nonzero(a > 1 + 1e-12)[0]
+    edge = float(om[bad[0]]) if bad.size else float(om[-1])
+    return edge / top
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -548,10 +707,11 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     from paper_2401_16322_gb300 import Batch
-    from paper_2401_16322_gb300.tts import (Candidate, build_models, common_ellipse, leapfrog_step,
-                                            rel_l2_common, run_study, simulate)
+    from paper_2401_16322_gb300.tts import (build_models, common_ellipse, leapfrog_step, run_study,
+                                            simulate)
     from paper_2401_16322_gb300.workloads import config_batched
 
+    t_run = time.perf_counter()
     if args.case == "full":
         wl = config_batched()
     else:
@@ -562,7 +722,7 @@ def run_ours(args):
     pts = batch_points(wl)
     t_setup = time.perf_counter()
     models = build_models(wl, "f32", p=12, c_max=c_max)
-    common_ellipse(models, c_max)
+    ellipse = common_ellipse(models, c_max)
     batch = Batch(models)
     if args.variant >= 0:
         batch.set_kernel_variant(args.variant)
@@ -573,6 +733,7 @@ def run_ours(args):
         sm, sk, skk = args.select.split(",")
         method, m, k = sm, int(sk), float(skk)
     study = None
+    growth = float("nan")
     if not args.no_search and args.case == "full":
         models64 = build_models(wl, "f64", p=12, c_max=c_max)   # FP64 leap-frog timing
         study = run_study(wl, PICKS, T_run, target=args.target, full_batch=batch, full_models=models,
@@ -583,6 +744,7 @@ def run_ours(args):
         del models64
         if study.selected is not None:
             method, m, dt = study.selected.method, study.selected.m, study.selected.dt
+            growth = study.selected.growth
         else:
             dt = k * dt_cfl
         seismo_err = study.selected.err if study.selected else float("nan")
@@ -590,19 +752,20 @@ def run_ours(args):
         dt = k * dt_cfl
         seismo_err = float("nan")
     nsteps = int(round(T_run / dt))
-    log(f"selected {method} m={m} dt={dt * 1e3:.4f} ms ({nsteps} steps), sampled error {seismo_err:.3e}")
+    log(f"selected {method} m={m} dt={dt * 1e3:.4f} ms ({nsteps} steps), sampled error {seismo_err:.3e} "
+        f"({time.perf_counter() - t_run:.0f} s into the run)")
 
     def one_solution():
         simulate(models, batch, method, m, dt, T_run)
 
+    # ---- timed region: K whole simulations, no per-pass instrumentation
+    batch.enable_kernel_timing(False)
     for _ in range(args.warmup):
         one_solution()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    batch.enable_kernel_timing(True)
-    batch.kernel_timing()
     launches0 = batch.launch_count()
     clk = ClockSampler(local)
     clk.start()
@@ -617,16 +780,27 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks = clk.stop()
     elapsed_ms = e0.elapsed_time(e1)
-    # every problem's seismogram of the last timed simulation is finite (the error target is
-    # measured on sampled problems only)
-    all_finite = all(bool(torch.isfinite(md.seismo).all()) for md in models)
-    kern_ms, kern_n = batch.kernel_timing()
-    batch.enable_kernel_timing(False)
     launches = batch.launch_count() - launches0
     ms_per_step = elapsed_ms / args.steps
     ms_per_step = max_over_ranks(ms_per_step, dist)
+    # every problem's seismogram of the last timed simulation is finite
+    all_finite = all(bool(torch.isfinite(md.seismo).all()) for md in models)
+    log(f"timed: {ms_per_step:.1f} ms per solution ({time.perf_counter() - t_run:.0f} s into the run)")
 
-    # roofline of the fused stencil pass (live, CUDA events around every launch)
+    # ---- error of the last timed simulation on a spread of problems
+    check = None
+    if rank == 0 and args.case == "full" and T_run == T_END:
+        check = check_problems(wl, models, method, m, dt, nsteps, c_max, dt_cfl, study, args.target)
+        log(f"error on {check['problems']} problems: max {check['max_rel_err']:.3e} "
+            f"({check['seconds']:.1f} s)")
+
+    # ---- roofline: one more simulation with CUDA events around every stencil pass
+    batch.enable_kernel_timing(True)
+    batch.kernel_timing()
+    one_solution()
+    torch.cuda.synchronize()
+    kern_ms, kern_n = batch.kernel_timing()
+    batch.enable_kernel_timing(False)
     words = pass_words(method, m)
     alg_bytes_per_step = sum(words) * 4.0 * pts
     per_launch_bytes = alg_bytes_per_step / len(words)
@@ -634,9 +808,10 @@ def run_ours(args):
     achieved = per_launch_bytes / (avg_launch_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
 
-    # e2e: velocity models from host, every shot's seismogram back to host, per solution
+    # ---- e2e through the public API: velocity models in, every seismogram out, per solution
     vel_host = [np.ascontiguousarray(w.c) for w in wl]
     h2d = sum(v.nbytes for v in vel_host)
+    pinned = [torch.empty(md.seismo.numel(), dtype=md.seismo.dtype, pin_memory=True) for md in models]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     d2h = 0
@@ -644,108 +819,161 @@ def run_ours(args):
         for md, v in zip(models, vel_host):
             md.set_velocity(v)
         simulate(models, batch, method, m, dt, T_run)
-        outs = []
-        for md, w in zip(models, wl):
-            s = md.seismo.view(md.nshots, md.capacity, md.max_receivers)[:, :nsteps].cpu()
-            outs.append(s)
-        d2h = sum(o.numel() * o.element_size() for o in outs)
-    torch.cuda.synchronize()
+        d2h = 0
+        for md, buf in zip(models, pinned):
+            buf.copy_(md.seismo, non_blocking=True)
+            d2h += buf.numel() * buf.element_size()
+        torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / args.steps
+    e2e_s = max_over_ranks(e2e_s, dist)
+    log(f"e2e: {e2e_s:.3f} s per solution ({time.perf_counter() - t_run:.0f} s into the run)")
 
     extras = {}
     if rank == 0 and args.case == "full" and not args.no_extras:
-        extras["fp64_single_shot"] = fp64_single_shot_estimate(wl, method, m, dt, nsteps, c_max)
-        extras["fwi_gradient"] = fwi_gradient_step(method, m, dt / dt_cfl)
-        extras["fwi_gradient_krylov"] = fwi_gradient_step("krylov", 20, 8.0)
-        extras["config5_3d"] = config5_3d(args.n3d, args.check3d)
-        extras["config1_fp64"] = config1_fp64_study()
+        for name, fn in (("fp64_single_shot", lambda: fp64_single_shot_estimate(wl, method, m, dt, nsteps, c_max)),
+                         ("fwi_gradient", lambda: fwi_gradient_step(method, m, dt / dt_cfl)),
+                         ("fwi_gradient_krylov", lambda: fwi_gradient_step("krylov", 20, 8.0)),
+                         ("config5_3d", lambda: config5_3d(args.n3d, args.check3d)),
+                         ("config1_fp64", config1_fp64_study)):
+            t_x = time.perf_counter()
+            try:
+                extras[name] = fn()
+            except Exception as e:           # a side run never costs the headline
+                extras[name] = {"error": f"{type(e).__name__}: {e}"}
+            log(f"side run {name}: {time.perf_counter() - t_x:.1f} s")
     if rank == 0 and study is not None:
         # dispersion / dissipation of the fastest passing setting of each method (and of
         # leap-frog at its passing FP64 step) on the undamped spectrum
         from paper_2401_16322_gb300.analysis import report
         best = {}
         for c in study.candidates:
-            if c.err <= args.target and not c.method.startswith("krylov"):
-                if c.method not in best or c.cost_s < best[c.method].cost_s or not math.isfinite(best[c.method].cost_s):
+            if c.err <= args.target and not c.method.startswith("krylov") and math.isfinite(c.cost_s):
+                if c.method not in best or c.cost_s < best[c.method].cost_s:
                     best[c.method] = c
         if study.leapfrog_f64 is not None:
             best["leapfrog"] = study.leapfrog_f64
-        g_, c0_, c1_ = models[0].faber_ellipse()
-        # top of the undamped interior spectrum, c_max sqrt(2 |S2|) / dx = 2 / leap-frog step;
-        # the free-surface rows sit in the slow top layer here and do not raise it
-        omega_spec = 2.0 / dt_cfl
+        # top of the undamped interior spectrum, c_max sqrt(2 |S2|) / dx = 2 / leap-frog step
         extras["dispersion"] = report([(c.method, c.m, c.dt) for c in best.values()],
-                                      wl[0].f_peak, omega_spec, (g_, c0_, c1_))
-    result = None
+                                      wl[0].f_peak, 2.0 / dt_cfl, ellipse)
     if rank == 0:
-        cpu_pps, cpu_desc, cores = cpu_oracle_sample(config_batched(), method, m, dt, args.cpu_sample_s)
+        sampler = OracleSampler(args.cpu_procs)
+        cpu_pps, cpu_desc, cores, _, _ = sampler.sample(config_batched(), method, m, dt, args.cpu_sample_s)
+        sampler.close()
         cpu_tts = cpu_pps * pts * nsteps
         lf = study.leapfrog if study else None
         lf64 = study.leapfrog_f64 if study else None
+
+        def brief(c):
+            return {"dt_ms": c.dt * 1e3, "seismo_rel_err": c.err, "time_to_solution_s": c.cost_s}
+
+        passing = sorted([c for c in study.candidates if c.err <= args.target and math.isfinite(c.cost_s)],
+                         key=lambda c: c.cost_s) if study else []
+        best_per_method = {}
+        for c in passing:
+            best_per_method.setdefault(c.method, c)
+        x3 = extras.get("config5_3d") or {}
+        f1 = extras.get("config1_fp64") or {}
+        fp = extras.get("fwi_gradient") or {}
+        fk = extras.get("fwi_gradient_krylov") or {}
         result = {
             "metric": METRIC, "value": ms_per_step / 1e3, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME if args.case == "full" else f"{args.case}: 1001x501, {wl[0].shots.__len__()} shots",
+            "config": {"workload": WORKLOAD_NAME if args.case == "full" else f"{args.case}: 1001x501, {len(wl[0].shots)} shots",
                        "method": method, "m": m, "dt_ms": dt * 1e3,
                        "dt_over_leapfrog_step": dt / dt_cfl, "nsteps": nsteps, "T_s": T_run,
                        "grid_points": pts, "problems": sum(len(w.shots) for w in wl),
                        "l2": "inputs larger than L2 (state + workspace > 1 GB)",
                        "parallelism": f"replicas x{world}"},
-            "seismo_rel_err": seismo_err,
+            "seismo_rel_err_search_problems": seismo_err,
+            "seismo_rel_err_max_over_checked_problems": check["max_rel_err"] if check else None,
+            "checked_problems": ({"count": check["problems"], "of": check["of"],
+                                  "all_within_target": check["all_within_target"],
+                                  "worst": check["worst_problem"], "reference": check["reference"],
+                                  "reference_vs_search_reference": check["reference_vs_search_reference"]}
+                                 if check else None),
             "all_seismograms_finite": all_finite,
+            "stability": {"noise_growth_per_100_steps": growth, "limit": NOISE_LIMIT(),
+                          "omega_edge_over_omega_top": stability_margin(method, m, dt, dt_cfl, ellipse)},
             "grid_point_updates_per_s": pts * nsteps / (ms_per_step / 1e3),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
                          "traffic": (tpp * pts if (tpp := ncu_traffic_per_point(method)) else None),
                          "peak_kind": peak_kind,
                          "kernel": "stage_tma_kernel (persistent TMA fused stencil pass, FP32)",
-                         "variant": batch.kernel_variant(),
+                         "variant": {k_: v_ for k_, v_ in batch.kernel_variant().items() if k_ != "probe_us"},
                          "avg_launch_us": avg_launch_ms * 1e3, "launches": kern_n,
-                         "alg_bytes_per_launch": per_launch_bytes},
+                         "alg_bytes_per_launch": per_launch_bytes,
+                         "timing": "CUDA events around every pass of one extra simulation after the timed region"},
             "cpu_baseline": {"value": cpu_tts, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": cpu_desc},
+                             "sample": cpu_desc, "extrapolated": True},
             "e2e": {"value": e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "clocks": clocks,
-            "leapfrog_f32": ({"dt_ms": lf.dt * 1e3, "seismo_rel_err": lf.err,
-                              "time_to_solution_s": lf.cost_s} if lf else
+            "leapfrog_f32": (brief(lf) if lf else
                              ("no leap-frog step down to 1/32 of the stability step reaches the "
                               "target in FP32" if study else None)),
-            "leapfrog_f64": ({"dt_ms": lf64.dt * 1e3, "seismo_rel_err": lf64.err,
-                              "time_to_solution_s": lf64.cost_s} if lf64 else None),
-            "fp64_single_shot": extras.get("fp64_single_shot"),
-            "fwi_gradient": extras.get("fwi_gradient"),
-            "fwi_gradient_krylov": extras.get("fwi_gradient_krylov"),
-            "config5_3d": extras.get("config5_3d"),
-            "config1_fp64": extras.get("config1_fp64"),
-            "dispersion": extras.get("dispersion"),
-            "bf16_storage": ([{"method": k, "m": v[0], "dt_ms": v[1] * 1e3, "seismo_rel_err": v[2],
-                               "seismo_rel_err_fp32": v[3]} for k, v in study.bf16.items()]
+            "leapfrog_f64": brief(lf64) if lf64 else None,
+            "best_per_method": {k_: {"m": c.m, "dt_over_leapfrog_step": round(c.dt / dt_cfl, 4),
+                                     "time_to_solution_s": c.cost_s, "seismo_rel_err": c.err}
+                                for k_, c in best_per_method.items()},
+            "fp64_single_shot_s": (extras.get("fp64_single_shot") or {}).get("time_to_solution_s"),
+            "fwi_gradient": ({k_: fp.get(k_) for k_ in ("method", "m", "dt_ms", "nsteps", "seconds",
+                                                        "forward_s", "backward_s", "gradient_finite")}
+                             if fp else None),
+            "fwi_gradient_krylov": ({k_: fk.get(k_) for k_ in ("m", "dt_ms", "nsteps", "seconds",
+                                                               "forward_s", "backward_s", "adjoint")}
+                                    if fk else None),
+            "config5_3d": ({"selected": {k_: (x3.get("selected") or {}).get(k_) for k_ in
+                                         ("method", "m", "dt_over_leapfrog_step", "time_to_T_s",
+                                          "seismo_rel_err_vs_fp64")},
+                            "leapfrog_f32": {k_: (x3.get("leapfrog_best") or {}).get(k_) for k_ in
+                                             ("dt_over_leapfrog_step", "time_to_T_s", "seismo_rel_err_vs_fp64")},
+                            "roofline_frac": x3.get("roofline_frac"),
+                            "pml": x3.get("pml")} if x3 else None),
+            "config1_fp64": ({"selected": f1.get("selected"), "leapfrog": f1.get("leapfrog")}
+                             if f1 else None),
+            "bf16_storage": ([{"method": k_, "m": v[0], "dt_ms": v[1] * 1e3, "seismo_rel_err": v[2],
+                               "seismo_rel_err_fp32": v[3]} for k_, v in study.bf16.items()]
                              if study else None),
             "search_s": study.seconds if study else None,
             "reference_self_check": study.ref_self_check if study else None,
-            "candidates": ([{"method": c.method, "m": c.m, "dt_ms": round(c.dt * 1e3, 4),
-                             "seismo_rel_err": c.err, "time_to_solution_s": c.cost_s}
-                            for c in study.candidates if c.err <= args.target] if study else None),
+            "run_s": time.perf_counter() - t_run,
         }
-        print(json.dumps(result), flush=True)
+        line = json_line(result)
+        if args.detail_out:
+            detail = dict(result)
+            detail.update(extras)
+            detail["checked_problems"] = check
+            detail["candidates"] = ([{"method": c.method, "m": c.m, "dt_ms": c.dt * 1e3,
+                                      "seismo_rel_err": c.err, "growth": c.growth,
+                                      "time_to_solution_s": c.cost_s} for c in study.candidates]
+                                    if study else None)
+            os.makedirs(os.path.dirname(os.path.abspath(args.detail_out)), exist_ok=True)
+            with open(args.detail_out, "w") as f:
+                f.write(json_line(detail) + "\n")
+        print(line, flush=True)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
     return 0
 
 
-def main():
-    args = parse()
+def NOISE_LIMIT():
+    from paper_2401_16322_gb300.tts import NOISE_GROWTH
+    return NOISE_GROWTH
+
+
+def main(argv=None):
+    args = parse(argv)
     if args.impl == "reference":
         return run_reference(args)
     if args.case == "cube":
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-        print(json.dumps({"config5_3d": config5_3d(args.n3d, args.check3d)}), flush=True)
+        print(json_line({"config5_3d": config5_3d(args.n3d, args.check3d)}), flush=True)
         return 0
     return run_ours(args)
 

@@ -20,6 +20,11 @@
  *  - Device pointers must be 256-byte aligned (torch allocations are); sizes are checked.
  *  - Threading: calls on one handle are serialised on its stream (ewv_set_stream); distinct
  *    handles are independent.  Calls return after enqueueing work unless stated otherwise.
+ *  - Asynchronous errors: a step call ends its GPU work with a scan of every shot's state;
+ *    a non-finite value (NaN or infinity) or a TMA pipeline wait that gave up sets the
+ *    handle's error word, which is copied to the host without waiting.  The next step call
+ *    on the handle, or ewv_sync, returns EWV_ERR_NONFINITE or EWV_ERR_TIMEOUT for it (and
+ *    clears it); such a step call enqueues nothing.
  *  - Grid: nodes (i, j), i = 0..nx-1 left to right, j = 0..ny-1 top to bottom (j = 0 is the
  *    free surface when enabled).  w_x lives at (i+1/2, j), i = 0..nx-2; w_y at (i, j+1/2),
  *    j = 0..ny-2; w_y is the paper's w_y for its upward y axis.
@@ -223,7 +228,10 @@ int ewv_step_faber(ewv_model_t model, double t, double dt, int degree, int nstep
 
 /* Sec. 3.2 Krylov: Arnoldi (MGS) on dt H~ with m matrix-vector products, exp of the m x m
  * Hessenberg by [13/13] Pade with scaling and squaring.  *info (may be NULL) receives the
- * smallest effective dimension over shots and steps (< m after a happy breakdown). */
+ * smallest effective dimension over shots and steps (< m after a happy breakdown); with a
+ * non-NULL info the call waits for the GPU to read it and returns EWV_ERR_NONFINITE itself
+ * when the Arnoldi process met a non-finite value.  With info NULL it returns after
+ * enqueueing, like the other step calls. */
 int ewv_step_krylov(ewv_model_t model, double t, double dt, int m, int nsteps, int* info);
 
 /* Incomplete orthogonalisation for the Krylov step (the library's option; the paper names
@@ -332,7 +340,8 @@ int ewv_batch_step_leapfrog(ewv_batch_t batch, double t, double dt, int nsteps);
  * The first call on each device (with that device current) looks up the array's device
  * address; make that first call before any stream capture.  Calls share the array:
  * calls whose GPU work overlaps race.  The call reads the Faber coefficients back from the
- * GPU once, so it synchronises the stream before launching the steps. */
+ * GPU once, so it synchronises the stream before launching the steps.  Unlike the handle
+ * calls it does not scan the state for non-finite values: check the state if that matters. */
 #define EWV_NOALLOC_MAX_FIELD_ELEMS (1 << 19)
 typedef struct ewv_noalloc_faber_args {
     int nx, ny, pitch;     /* grid nodes; pitch: elements per row, >= nx, multiple of 32 */
@@ -396,6 +405,19 @@ int ewv_batch_kernel_timing(ewv_batch_t batch, double* total_ms, long long* laun
 
 /* Number of kernel launches this handle has enqueued since creation (for reporting). */
 int ewv_launch_count(ewv_model_t model, long long* count);
+
+/* Wait until every call enqueued on the handle has finished on the GPU, then report (and
+ * clear) its asynchronous error word: EWV_OK, EWV_ERR_NONFINITE or EWV_ERR_TIMEOUT. */
+int ewv_sync(ewv_model_t model);
+int ewv_batch_sync(ewv_batch_t batch);
+
+/* Testing aid: the limit, in ns (at most 1e9, the default), after which a pipeline wait of
+ * the 2D FP32 TMA pass on the current device gives up.  The kernel then waits (up to 1 s)
+ * for its copies in flight, sets the timeout bit of the error word and returns, so that a
+ * test can check the EWV_ERR_TIMEOUT path on a healthy GPU with a limit a normal pass
+ * outruns (e.g. 0).  Waits for the device to be idle first; applies to later launches,
+ * graph replays included.  Restore 1000000000 afterwards.  INVALID_ARG above 1e9. */
+int ewv_debug_set_wait_limit(unsigned long long ns);
 
 #ifdef __cplusplus
 }

@@ -206,7 +206,9 @@ struct Engine {
     size_t d_adj_bytes = 0;
     ProblemDev* d_kadj = nullptr; // Krylov adjoint: three descriptor views of the workspace
     size_t d_kadj_bytes = 0;
-    int* d_err = nullptr;       // timeout word written by the TMA kernel
+    int* d_err = nullptr;       // error word: 1 = a TMA pipeline wait timed out, 2 = non-finite
+    int* h_err = nullptr;       // pinned host copy, written by an async copy at the end of a call
+    cudaEvent_t err_ev = nullptr;   // recorded after that copy
     std::map<std::tuple<double, int, double, double, double>, std::vector<double>> faber_cache;
     // CUDA graphs of one step's launch sequence, keyed by (method, m, dt, g, c0, c1, parity
     // + 2 x timing); a graph captured with timing on owns the event pairs around its passes
@@ -246,6 +248,7 @@ struct Engine {
     double timing_acc_ms = 0.0;
     long long timing_acc_n = 0;
     ~Engine() {
+        if (err_ev) cudaEventSynchronize(err_ev);   // the last copy into h_err has landed
         drop_graphs();
         if (cap) cudaStreamDestroy(cap);
         if (ev_in) cudaEventDestroy(ev_in);
@@ -261,6 +264,8 @@ struct Engine {
         cudaFree(d_tbase);
         cudaFree(d_pbase);
         cudaFree(d_err);
+        if (h_err) cudaFreeHost(h_err);
+        if (err_ev) cudaEventDestroy(err_ev);
         cudaFree(d_adj);
         cudaFree(d_adj_maps);
         cudaFree(d_kadj);
@@ -488,6 +493,9 @@ int build_engine(Engine* E, std::string& err) {
     if (!E->d_err) {
         CUDA_OR_FAIL(err, cudaMalloc(&E->d_err, sizeof(int)));
         CUDA_OR_FAIL(err, cudaMemset(E->d_err, 0, sizeof(int)));
+        CUDA_OR_FAIL(err, cudaHostAlloc(&E->h_err, sizeof(int), cudaHostAllocDefault));
+        *E->h_err = 0;
+        CUDA_OR_FAIL(err, cudaEventCreateWithFlags(&E->err_ev, cudaEventDisableTiming));
     }
     std::vector<int> tp(tb);
     for (int p = 0; p < E->nprob; ++p)
@@ -1097,7 +1105,10 @@ int run_krylov(Ctx& C, double t, double dt, int m, int nsteps, int* info) {
     if (!expm_ok) return fail(err, EWV_ERR_CUDA, "expm shared-memory configuration failed");
     int rc = check_launch(err);
     if (rc != EWV_OK) return rc;
-    // read back the effective dimensions and the non-finite flags
+    // Without an info pointer the call does not wait: a non-finite Arnoldi value reaches the
+    // host through the error word (the end-of-call scan reads the flag).  With one, read
+    // back the effective dimensions and the non-finite flags now.
+    if (!info) return EWV_OK;
     int meff_min = m;
     bool nonfinite = false;
     for (ewv_model* md : C.E->models) {
@@ -1189,6 +1200,8 @@ Engine* ensure_model_engine(ewv_model* m) {
     return m->engine;
 }
 
+int take_pending_error(Engine* E, cudaStream_t s, std::string& err);
+
 int dispatch(std::vector<ewv_model*>& models, Engine* E, cudaStream_t s, long long* launches,
              std::string& err, int method, double t, double dt, int mm, int nsteps, int* info) {
     if (nsteps < 0) return fail(err, EWV_ERR_INVALID_ARG, "nsteps < 0");
@@ -1197,6 +1210,8 @@ int dispatch(std::vector<ewv_model*>& models, Engine* E, cudaStream_t s, long lo
     int rc = precheck_engine_models(models, method, mm, err);
     if (rc != EWV_OK) return rc;
     rc = engine_ready(E, err);
+    if (rc != EWV_OK) return rc;
+    rc = take_pending_error(E, s, err);
     if (rc != EWV_OK) return rc;
     // With graphs on, run the call on the engine's own (capturable, non-blocking) stream,
     // ordered after the caller's stream and before whatever the caller enqueues next.
@@ -1216,20 +1231,42 @@ int dispatch(std::vector<ewv_model*>& models, Engine* E, cudaStream_t s, long lo
     rc = dispatch_method(C, models, method, t, dt, mm, nsteps, info);
     if (rc == EWV_OK && C.launch_failed)
         rc = fail(err, EWV_ERR_CUDA, "a stencil pass could not be launched (no usable TMA variant)");
+    if (rc == EWV_OK) {
+        // end of the call's work: scan the states for non-finite values and copy the error
+        // word to the host without waiting; the next call (or ewv_sync) reports it
+        launch_nonfinite_scan(E->precision, E->nchunks, E->d_probs, E->d_pbase, E->nprob, E->d_err, run_s);
+        ++*launches;
+        CUDA_OR_FAIL(err, cudaMemcpyAsync(E->h_err, E->d_err, sizeof(int), cudaMemcpyDeviceToHost, run_s));
+        CUDA_OR_FAIL(err, cudaEventRecord(E->err_ev, run_s));
+    }
     if (own) {
         cudaEventRecord(E->ev_out, run_s);
         cudaStreamWaitEvent(s, E->ev_out, 0);
     }
-    if (rc != EWV_OK) return rc;
-    s = run_s;
-    int herr = 0;
-    CUDA_OR_FAIL(err, cudaMemcpyAsync(&herr, E->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    return rc;
+}
+
+// Report an error word that an earlier call's GPU work left (see dispatch): 0 while none
+// has reached the host.  On a nonzero word the call waits for the engine's work, then
+// clears the word on both sides and returns TIMEOUT or NONFINITE.
+int take_pending_error(Engine* E, cudaStream_t s, std::string& err) {
+    if (!E || !E->h_err) return EWV_OK;
+    if (*(volatile int*)E->h_err == 0) return EWV_OK;
+    if (E->cap) CUDA_OR_FAIL(err, cudaStreamSynchronize(E->cap));
     CUDA_OR_FAIL(err, cudaStreamSynchronize(s));
-    if (herr) {
-        CUDA_OR_FAIL(err, cudaMemset(E->d_err, 0, sizeof(int)));
-        return fail(err, EWV_ERR_TIMEOUT, "a pipeline wait in the TMA stencil kernel timed out");
-    }
-    return EWV_OK;
+    const int w = *(volatile int*)E->h_err;
+    CUDA_OR_FAIL(err, cudaMemset(E->d_err, 0, sizeof(int)));
+    *(volatile int*)E->h_err = 0;
+    if (w & 1) return fail(err, EWV_ERR_TIMEOUT, "a pipeline wait in the TMA stencil kernel timed out "
+                                                 "during an earlier call");
+    return fail(err, EWV_ERR_NONFINITE, "a non-finite value appeared in the state during an earlier call");
+}
+
+// Wait for every call enqueued on the engine, then report its error word.
+int sync_engine(Engine* E, cudaStream_t s, std::string& err) {
+    if (E && E->cap) CUDA_OR_FAIL(err, cudaStreamSynchronize(E->cap));
+    CUDA_OR_FAIL(err, cudaStreamSynchronize(s));
+    return take_pending_error(E, s, err);
 }
 
 int dispatch_method(Ctx& C, std::vector<ewv_model*>& models, int method, double t, double dt,
@@ -2281,6 +2318,23 @@ int ewv_launch_count(ewv_model_t m, long long* count) {
     if (!m || !count) return EWV_ERR_INVALID_ARG;
     *count = m->launches;
     return EWV_OK;
+}
+
+int ewv_sync(ewv_model_t m) {
+    if (!m) return EWV_ERR_INVALID_ARG;
+    return sync_engine(m->engine, m->stream, m->err);
+}
+
+int ewv_batch_sync(ewv_batch_t b) {
+    if (!b) return EWV_ERR_INVALID_ARG;
+    cudaStream_t s = b->stream_set ? b->stream : b->models[0]->stream;
+    return sync_engine(b->engine, s, b->err);
+}
+
+int ewv_debug_set_wait_limit(unsigned long long ns) {
+    if (ns > 1000000000ull) return EWV_ERR_INVALID_ARG;
+    if (cudaDeviceSynchronize() != cudaSuccess) return EWV_ERR_CUDA;
+    return set_tma_wait_limit_ns(ns) == 0 ? EWV_OK : EWV_ERR_CUDA;
 }
 
 }  // extern "C"

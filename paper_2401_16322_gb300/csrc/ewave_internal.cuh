@@ -169,6 +169,11 @@ void launch_point(int precision, int nblocks, const ProblemDev* probs, const int
 // elements per block; pbase: nprob + 1 prefix sums of the problems' chunk counts.
 void launch_point_flat(int precision, int nchunks, const ProblemDev* probs, const int* pbase,
                        int nprob, const PointArgs& pa, cudaStream_t s);
+// Non-finite check of every problem's state vector (and its Arnoldi flag): sets bit 2 of *err.
+void launch_nonfinite_scan(int precision, int nchunks, const ProblemDev* probs, const int* pbase,
+                           int nprob, int* err, cudaStream_t s);
+// Pipeline-wait limit of the 2D TMA pass in ns (default 1 s) on the current device.
+int set_tma_wait_limit_ns(unsigned long long ns);
 void launch_inject(int precision, void* adj, long long vec_elems, const void* values,
                    const int* rec_off, const int* nrec, int nshots, int max_rec, cudaStream_t s);
 void launch_sum_shots(int precision, const void* in, void* out, long long n, int nshots,

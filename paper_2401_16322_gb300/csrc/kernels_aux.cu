@@ -673,6 +673,43 @@ void launch_sum_shots(int precision, const void* in, void* out, long long n, int
     else sum_shots_kernel<double><<<blocks, 256, 0, s>>>((const double*)in, (double*)out, n, nshots);
 }
 
+// Non-finite scan at the end of a step call: every block checks one PCHUNK chunk of its
+// problem's state vector (the pads hold zeros) and the first block of each problem its
+// Arnoldi flag; any NaN or infinity sets bit 1 (EWV error word: 1 = a pipeline wait timed
+// out, 2 = a non-finite value) with one atomicOr per block that saw one.
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+nonfinite_scan_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ pbase, int nprob,
+                      int* err) {
+    using V = typename Vec16<T>::type;
+    constexpr int NV = Vec16<T>::N;
+    const int pid = flat_problem(pbase, nprob, blockIdx.x);
+    const ProblemDev* P = probs + pid;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nf = P->nfields == 5 ? 5 : 4;
+    const long long nelem = (long long)nf * P->field_stride;
+    const int c = blockIdx.x - __ldg(pbase + pid);
+    const long long e0 = (long long)c * PCHUNK;
+    const long long e1 = e0 + PCHUNK < nelem ? e0 + PCHUNK : nelem;
+    const V* S = reinterpret_cast<const V*>(vptr<T>(P, 0));
+    bool bad = (c == 0 && tid == 0 && P->kry != nullptr && P->kry[KRY_NONFINITE] != 0.0);
+    for (long long q = e0 / NV + tid; q < e1 / NV; q += NTHREADS) {
+        const V v = S[q];
+        bool b = !isfinite(v.x) || !isfinite(v.y);
+        if constexpr (NV == 4) b = b || !isfinite(v.z) || !isfinite(v.w);
+        bad = bad || b;
+    }
+    if (__syncthreads_or(bad) && tid == 0) atomicOr(err, 2);
+}
+
+void launch_nonfinite_scan(int precision, int nchunks, const ProblemDev* probs, const int* pbase,
+                           int nprob, int* err, cudaStream_t s) {
+    if (nchunks <= 0) return;
+    const dim3 block(TPX, TPY);
+    if (precision == 0) nonfinite_scan_kernel<float><<<nchunks, block, 0, s>>>(probs, pbase, nprob, err);
+    else nonfinite_scan_kernel<double><<<nchunks, block, 0, s>>>(probs, pbase, nprob, err);
+}
+
 void launch_point(int precision, int nblocks, const ProblemDev* probs, const int* tile_prob,
                   const PointArgs& pa, cudaStream_t s) {
     const dim3 block(TPX, TPY);

@@ -114,13 +114,38 @@ __device__ __forceinline__ uint64_t global_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// Bounded wait: false after 1 s (or 2^26 polls) without the phase completing.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Limit of the pipeline waits (ns).  1 s by default; ewv_debug_set_wait_limit lowers it so
+// that a test can make a wait give up on a healthy GPU and check the reported status.  The
+// drain after a give-up always waits up to 1 s for the copies still in flight.
+__device__ unsigned long long g_tma_wait_limit_ns = 1000000000ull;
+constexpr uint64_t kDrainLimitNs = 1000000000ull;
+
+int set_tma_wait_limit_ns(unsigned long long ns) {
+    return cudaMemcpyToSymbol(g_tma_wait_limit_ns, &ns, sizeof(ns)) == cudaSuccess ? 0 : -1;
+}
+
+// Non-blocking probe of a phase.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: false after limit_ns (or 2^26 polls) without the phase completing; with
+// limit_ns = 0, false unless the phase has already completed (one non-blocking probe).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+    if (limit_ns == 0) return mbar_test_wait(bar, parity);
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (uint32_t it = 0; it < (1u << 26); ++it) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 255u) == 0 && global_ns() - t0 > 1000000000ull) return false;
+        if ((it & 255u) == 0 && global_ns() - t0 > limit_ns) return false;
     }
     return false;
 }
@@ -267,6 +292,7 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
+    const uint64_t wait_lim = g_tma_wait_limit_ns;
     if (tid == 0) {
         for (int s = 0; s < NSTv; ++s) {
             mbar_init(&full[s], 1);
@@ -291,7 +317,7 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
             for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
                 const int s = it % NSTv;
                 const uint32_t ph = (uint32_t)(it / NSTv) & 1u;
-                if (!mbar_wait(&empty[s], ph ^ 1u)) {
+                if (!mbar_wait(&empty[s], ph ^ 1u, wait_lim)) {
                     s_err = 1;
                     break;
                 }
@@ -362,7 +388,7 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
             const int s = it % NSTv;
             const uint32_t ph = (uint32_t)(it / NSTv) & 1u;
-            if (!mbar_wait(&full[s], ph)) {
+            if (!mbar_wait(&full[s], ph, wait_lim)) {
                 s_err = 1;
                 break;
             }
@@ -639,9 +665,9 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
         // drain: wait (bounded) for the last copy issued into every stage
         if (warp == NW && lane == 0) {
             for (int it = issued - 1; it >= 0 && it >= issued - NSTv; --it)
-                (void)mbar_wait(&full[it % NSTv], (uint32_t)(it / NSTv) & 1u);
+                (void)mbar_wait(&full[it % NSTv], (uint32_t)(it / NSTv) & 1u, kDrainLimitNs);
         }
-        if (tid == 0) atomicExch(err, 1);
+        if (tid == 0) atomicOr(err, 1);
     }
 }
 

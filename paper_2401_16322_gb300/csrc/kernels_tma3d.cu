@@ -508,7 +508,7 @@ stage_tma3d_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__
             for (int k = issued - 1; k >= 0 && k >= issued - NST; --k)
                 (void)bar_wait(&full[k % NST], (uint32_t)(k / NST) & 1u);
         }
-        if (tid == 0) atomicExch(err, 1);
+        if (tid == 0) atomicOr(err, 1);
     }
 }
 

@@ -25,6 +25,7 @@ LEAPFROG_AVERAGED, LEAPFROG_LITERAL, LEAPFROG_DIFFERENCE = 0, 1, 2
 
 # Every symbol include/ewave.h declares (checked by the tests).
 EXPORTS = [
+    "ewv_sync", "ewv_batch_sync", "ewv_debug_set_wait_limit",
     "ewv_create_model", "ewv_destroy_model", "ewv_set_stream", "ewv_layout",
     "ewv_workspace_bytes", "ewv_bind_buffers", "ewv_bind_workspace", "ewv_bind_seismogram",
     "ewv_reset_recording", "ewv_set_velocity", "ewv_set_source_receivers",
@@ -148,6 +149,9 @@ def load_library(path=LIB_PATH):
         "ewv_kernel_timing": ([vp, dp, ctypes.POINTER(ctypes.c_longlong)], i),
         "ewv_batch_enable_kernel_timing": ([vp, i], i),
         "ewv_batch_kernel_timing": ([vp, dp, ctypes.POINTER(ctypes.c_longlong)], i),
+        "ewv_sync": ([vp], i),
+        "ewv_batch_sync": ([vp], i),
+        "ewv_debug_set_wait_limit": ([ctypes.c_ulonglong], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -387,6 +391,10 @@ class Model:
         self._check(self.lib.ewv_launch_count(self.h, ctypes.byref(c)))
         return c.value
 
+    def sync(self):
+        """Wait for the model's GPU work; raise on a non-finite state or a timed-out wait."""
+        self._check(self.lib.ewv_sync(self.h), "sync")
+
     # ---------------------------------------------------------------- adjoint
     def adjoint_step(self, t, dt, degree, checkpoint, adj, grad, method="faber"):
         """lambda <- (dPhi/dU)^T lambda, grad += (dPhi/dm)^T lambda for one Faber / HORK step
@@ -431,6 +439,13 @@ def checkpoint_stride(nsteps, budget):
     if rc != EWV_OK:
         raise EwaveError(f"checkpoint_stride: {ERRORS.get(rc, rc)}")
     return out.value
+
+
+def debug_set_wait_limit(ns):
+    """Testing aid: pipeline-wait limit of the 2D FP32 TMA pass (ns, default 1e9)."""
+    rc = load_library().ewv_debug_set_wait_limit(int(ns))
+    if rc != EWV_OK:
+        raise EwaveError(f"debug_set_wait_limit: {ERRORS.get(rc, rc)}")
 
 
 def faber_step_noalloc(args, state, c2, t, dt, degree, nsteps=1, stream=None):
@@ -502,6 +517,10 @@ class Batch:
 
     def launch_count(self):
         return sum(m.launch_count() for m in self.models[:1])
+
+    def sync(self):
+        """Wait for the batch's GPU work; raise on a non-finite state or a timed-out wait."""
+        self._check(self.lib.ewv_batch_sync(self.h), "batch_sync")
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:

@@ -51,6 +51,7 @@ class FaberFWI:
             if n % self.stride == 0:
                 self.ckpt[n // self.stride].copy_(md.state)
             md.step(self.method, self.t0 + n * self.dt, self.dt, self.degree, 1)
+        md.sync()           # raises if the forward run produced a non-finite state
         s = md.seismo.view(md.nshots, md.capacity, md.max_receivers)[:, :self.nsteps, :self.nrec]
         return s.clone()
 

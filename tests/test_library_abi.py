@@ -131,4 +131,4 @@ def test_oracle_is_used_only_by_smoke_and_the_cpu_baseline(repo_root):
         return out
 
     assert users(os.path.join(repo_root, "__graft_entry__.py")) == {"smoke"}
-    assert users(os.path.join(repo_root, "bench.py")) == {"cpu_oracle_sample"}
+    assert users(os.path.join(repo_root, "bench.py")) == {"_oracle_worker", "sample"}

@@ -78,3 +78,9 @@ def test_reference_arm_prints_one_json_line_on_rank_0():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
+    # the value is extrapolated from the sample, and says so; a step is one bounded sample,
+    # so the timed region (steps x ms_per_step) is what the run actually spent
+    assert d["extrapolated"] is True and cb["extrapolated"] is True
+    assert d["sampled_grid_point_steps"] > 0 and d["sample_wall_s"] > 0
+    assert d["ms_per_step"] * d["steps"] / 1e3 <= 10 * 60
+    assert d["ms_per_step"] / 1e3 == pytest.approx(d["sample_wall_s"], rel=1e-6)
