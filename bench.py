@@ -403,7 +403,8 @@ def config5_3d(n=400, check_n=0, target=TARGET):
         return md.seismogram(0, md.max_receivers, nsteps)
 
     out = {"workload": f"{n}^3 layered, dx 10 m, 8th order, free surface, 30-pt ABC, Ricker 10 Hz, "
-                       "T 1 s, FP32", "target": target, "candidates": []}
+                       "T 1 s, FP32", "target": target, "candidates": [],
+           "pml": "auxiliary-field PML (psi_t = u), exact reduction to Eq. 1"}
     found = []          # (method, m, k, err); k < 1: leap-frog divisor 1/k
     t_search = time.perf_counter()
     wc = config_3d(check_n if check_n > 0 else 64, pml=min(20, (check_n or 64) // 4), T=0.5)
@@ -533,13 +534,14 @@ def config5_3d(n=400, check_n=0, target=TARGET):
 
 
 def pass_words3d(method, m):
-    """Algorithmic FP32 words per point of each 3D stencil pass (five fields)."""
+    """Algorithmic FP32 words per point of each 3D stencil pass (six fields: u, v, w_x, w_y,
+    w_z, psi; c^2 once)."""
     if method == "faber":
-        return [16] + [26] * (m - 1) if m >= 2 else [16]
+        return [19] + [31] * (m - 1) if m >= 2 else [19]
     if method == "hork-horner":
-        return [11] + [16] * (m - 1)
+        return [13] + [19] * (m - 1)
     if method == "hork":
-        return [16] + [21] * (m - 1) if m >= 2 else [11]
+        return [19] + [25] * (m - 1) if m >= 2 else [13]
     raise ValueError(method)
 
 

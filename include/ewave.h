@@ -34,17 +34,21 @@
  *    nshots such vectors back to back (the "state" buffer).
  *  - Compact host layout (ewv_set_state / ewv_get_state): float64, u [ny][nx], v [ny][nx],
  *    w_x [ny][nx-1], w_y [ny-1][nx], concatenated (n = 2 nx ny + (nx-1) ny + nx (ny-1)).
- *  - Three dimensions (dims = 3; not in the paper, which is 2D): the library's extension of
- *    Eq. (1) to U = (u, v, w_x, w_y, w_z):
- *      v_t   = -(bx by + by bz + bx bz) u - (bx + by + bz) v
+ *  - Three dimensions (dims = 3; not in the paper, which is 2D): the PML of Eq. (1) carried
+ *    to three axes with an auxiliary field psi (psi_t = u), U = (u, v, w_x, w_y, w_z, psi):
+ *      v_t   = -(bx by + by bz + bx bz) u - (bx + by + bz) v - bx by bz psi
  *              + c^2 (u_xx + u_yy + u_zz + d_x w_x + d_y w_y + d_z w_z) + f,
- *      w_a,t = -b_a w_a + (mean of the other two b's - b_a) d_a u    (a = x, y, z).
- *    It reduces to Eq. (1) when one axis is dropped.  z is vertical, with node planes
- *    k = 0..nz-1 and k = 0 the free surface: z takes the role of the 2D y axis (upward
- *    derivative, Appendix A rows, no top damping).  x and y are horizontal.  w_z lives at
- *    (i, j, k+1/2).
- *    - Device layout: 5 fields, each [nz][ny][pitch].
+ *      w_a,t = -b_a w_a + (sum of the other two b's - b_a) d_a u
+ *              + (product of the other two b's) d_a psi              (a = x, y, z),
+ *      psi_t = u.
+ *    With one axis undamped and a field constant along it, the u, v and remaining w rows are
+ *    exactly Eq. (1) on the other two axes.  z is vertical, with node planes k = 0..nz-1 and
+ *    k = 0 the free surface: z takes the role of the 2D y axis (upward derivative, Appendix A
+ *    rows, no top damping).  x and y are horizontal.  w_z lives at (i, j, k+1/2), psi at the
+ *    nodes (its half-point derivatives use the stencils of d_a u).
+ *    - Device layout: 6 fields, each [nz][ny][pitch].
  *    - Compact host layout: each field [ez][ey][ex] with its own extents.
+ *    - Leap-frog advances psi by the trapezoid rule, psi^{n+1} = psi^n + dt (u^n + u^{n+1})/2.
  *    - Supported: forward steps of every integrator and H x.  The transpose and the
  *      adjoint are not (UNSUPPORTED).
  */
@@ -82,6 +86,7 @@ extern "C" {
 #define EWV_METHOD_LEAPFROG 6 /* Sec. 3.1 two-step leap-frog                             */
 #define EWV_METHOD_ADJOINT_FABER 7 /* discrete adjoint of the Faber step (workspace query) */
 #define EWV_METHOD_ADJOINT_KRYLOV 8 /* linearised adjoint of the Krylov step (workspace query) */
+#define EWV_METHOD_ADJOINT_LEAPFROG 9 /* discrete adjoint of the leap-frog step (workspace query) */
 
 #define EWV_LEAPFROG_AVERAGED 0 /* time-averaged PML damping of w (stable reading)       */
 #define EWV_LEAPFROG_LITERAL 1  /* explicit -beta w^n damping, as the formula reads      */
@@ -117,7 +122,7 @@ typedef struct ewv_layout_info {
     int pitch;                 /* elements per padded row (multiple of 128 bytes)          */
     int elem_bytes;            /* 4 or 8                                                   */
     size_t field_elems;        /* ny * pitch (2D); nz * ny * pitch (3D)                    */
-    size_t vector_bytes;       /* fields (4; 5 in 3D) * field_elems * elem_bytes           */
+    size_t vector_bytes;       /* fields (4; 6 in 3D) * field_elems * elem_bytes           */
     size_t state_bytes;        /* nshots * vector_bytes                                    */
     size_t params_bytes;       /* c^2 on the padded grid: field_elems * elem_bytes         */
     size_t compact_n;          /* length of the compact host state vector                  */
@@ -288,8 +293,17 @@ int ewv_set_leapfrog_variant(ewv_model_t model, int variant);
  * grad += int_0^dt [exp((dt-s) H)^T lambda]_v (L u + D w)(s) ds by 4-point Gauss-Legendre,
  * with the states at the nodes from the forward and adjoint Arnoldi bases (dense output).
  * It agrees with the Krylov forward to that step's time accuracy.  Workspace:
- * ewv_workspace_bytes(EWV_METHOD_ADJOINT_KRYLOV, m) (2m + 9 vectors).  2D models only.
- * Buffers 256-B aligned, caller-owned.
+ * ewv_workspace_bytes(EWV_METHOD_ADJOINT_KRYLOV, m) (2m + 9 vectors).
+ * method EWV_METHOD_LEAPFROG (m ignored; averaged damping of w, in the plain or the
+ * difference form, which are one scheme): the exact discrete adjoint of one Sec. 3.1 step
+ * z^{n-1} -> z^n, z = (u, u_prev, w, w_prev).  checkpoint: level n-1 in the u, w_x, w_y
+ * fields (the state before the step); adj_state: 2 nshots padded vectors, the first nshots
+ * holding the cotangents of (u, u_prev, w_x, w_y) of level n (u_prev in the v field), the
+ * next nshots those of w_prev in their w fields; both are replaced by the cotangents of
+ * level n-1.  One H^T pass and two pointwise passes; workspace
+ * ewv_workspace_bytes(EWV_METHOD_ADJOINT_LEAPFROG, 0) (3 vectors).  UNSUPPORTED for the
+ * literal damping variant.
+ * 2D models only.  Buffers 256-B aligned, caller-owned.
  *
  * ewv_adjoint_inject: lambda_u += R^T values at the receivers, values [nshots][max_receivers]
  * of the model's precision (the seismogram cotangent of one sample).

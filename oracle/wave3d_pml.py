@@ -27,6 +27,12 @@ pin).
 
 Two routes: ``apply_H3p`` (shifted arrays, reusing the derivative operators of
 ``oracle.wave3d``) and ``assemble_H3p`` (tap-by-tap sparse assembly written out here).
+
+Leap-frog (Sec. 3.1's two-step scheme) on this PML, ``leapfrog3dp_step``: u and the w fields
+as in ``oracle.wave3d.leapfrog3d_step`` (u_t of the damping term centred, the damping of w
+time-averaged) with the psi terms added at level n, and psi advanced by the trapezoid rule,
+psi^{n+1} = psi^n + dt (u^n + u^{n+1}) / 2 (the paper is 2D and has no psi: this is the
+reading of its scheme for the extra field).
 ``Model3DPML`` is a ``Model3D`` whose state carries psi; ``oracle.operator.apply_H`` sends it
 to ``apply_H3p``, so every integrator of the oracle runs on this PML.
 Pins: tests/test_oracle_wave3d_pml.py (also: the integrators against the dense exponential,
@@ -216,3 +222,37 @@ def assemble_H3p(m, undamped=()):
                             put(r, PSI(k + 1 + q, j, i), -gp * s[q])
     n = o_psi + N
     return sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
+
+
+# ------------------------------------------------------------------ leap-frog
+def leapfrog3dp_init(U):
+    """Leap-frog state (u^n, u^{n-1}, w_x^n, w_x^{n-1}, w_y^n, w_y^{n-1}, w_z^n, w_z^{n-1},
+    psi^n) from U = (u, v, w_x, w_y, w_z, psi) with u^{-1} = u^0 and w^{-1} = w^0."""
+    u, _v, wx, wy, wz, psi = U
+    return (u.copy(), u.copy(), wx.copy(), wx.copy(), wy.copy(), wy.copy(), wz.copy(), wz.copy(),
+            psi.copy())
+
+
+def leapfrog3dp_step(m, LF, src, t_n, dt, undamped=()):
+    """One step of the scheme in the module header."""
+    u, um, wx, wxm, wy, wym, wz, wzm, psi = LF
+    p = _profiles(m, undamped)
+    bx, bxh = p["x"][0][None, None, :], p["x"][1][None, None, :]
+    by, byh = p["y"][0][None, :, None], p["y"][1][None, :, None]
+    bz, bzh = p["z"][0][:, None, None], p["z"][1][:, None, None]
+    b = bx + by + bz
+    lap = d_second(m, u, 2) + d_second(m, u, 1) + d_second(m, u, 0)
+    div = d_node(m, wx, 2) + d_node(m, wy, 1) + d_node(m, wz, 0)
+    rhs = -(bx * by + by * bz + bx * bz) * u - bx * by * bz * psi + m.c2 * (lap + div)
+    if src is not None:
+        rhs[src.k, src.j, src.i] += src.f(t_n)
+    up = ((2.0 * u - um) / dt ** 2 + b * um / (2.0 * dt) + rhs) / (1.0 / dt ** 2 + b / (2.0 * dt))
+
+    def wnext(wm, bh, g):
+        return ((1.0 - bh * dt) * wm + 2.0 * dt * g) / (1.0 + bh * dt)
+
+    wxp = wnext(wxm, bxh, (by + bz - bxh) * d_half(m, u, 2) + by * bz * d_half(m, psi, 2))
+    wyp = wnext(wym, byh, (bx + bz - byh) * d_half(m, u, 1) + bx * bz * d_half(m, psi, 1))
+    wzp = wnext(wzm, bzh, (bx + by - bzh) * d_half(m, u, 0) + bx * by * d_half(m, psi, 0))
+    psip = psi + 0.5 * dt * (u + up)
+    return (up, u, wxp, wx, wyp, wy, wzp, wz, psip)

@@ -33,7 +33,7 @@ namespace {
 const char* kVersion = "ewave-gb300 0.1 (sm_103a)";
 
 // Field mask of whole state vectors for the copy pass (bit f = field f; 2D uses bits 0..3).
-constexpr int ALL_FIELDS = 0x1F;
+constexpr int ALL_FIELDS = 0x3F;   // every field of a 2D (4) or 3D (6) vector
 
 enum { PRO_FABER = 1, PRO_KRYLOV = 2, PRO_HORK = 3, PRO_RK32 = 4, PRO_RK44 = 5, PRO_LEAPFROG = 6,
        PRO_HORK_HORNER = 7 };
@@ -141,7 +141,7 @@ struct Shot {
 struct ewv_model {
     ewv_model_desc d{};
     int R = 4, pitch = 0, elem = 4;
-    int nz = 1, nfields = 4;    // 3D: nz planes and five fields (w_z added)
+    int nz = 1, nfields = 4;    // 3D: nz planes and six fields (w_z and psi added)
     size_t field_elems = 0, vec_elems = 0;
     cudaStream_t stream = nullptr;
     void* state = nullptr;
@@ -301,7 +301,8 @@ int fail(std::string& err, int code, const char* fmt, ...) {
 
 bool aligned(const void* p) { return ((uintptr_t)p & 255u) == 0; }
 
-// Extents (x, y, z) of field f: u, v on the nodes; w_x, w_y, w_z one shorter along their axis.
+// Extents (x, y, z) of field f: u, v (and psi in 3D) on the nodes; w_x, w_y, w_z one shorter
+// along their axis.
 void field_extent(const ewv_model* m, int f, int* ex, int* ey, int* ez) {
     *ex = m->d.nx - (f == 2 ? 1 : 0);
     *ey = m->d.ny - (f == 3 ? 1 : 0);
@@ -352,6 +353,7 @@ int vectors_needed(int method, int m) {
         case EWV_METHOD_LEAPFROG: return 1;
         case EWV_METHOD_ADJOINT_FABER: return m + 3;   // tape p_0..p_{m-1} + 3 cotangents
         case EWV_METHOD_ADJOINT_KRYLOV: return 2 * m + 9;  // two bases + 8 dense outputs
+        case EWV_METHOD_ADJOINT_LEAPFROG: return 3;        // level-n tape, q, H^T q
         default: return -1;
     }
 }
@@ -1130,7 +1132,7 @@ int run_krylov(Ctx& C, double t, double dt, int m, int nsteps, int* info) {
 int run_leapfrog(Ctx& C, std::vector<ewv_model*>& models, double t, double dt, int nsteps, int variant) {
     bool need_init = false;
     for (ewv_model* m : models) need_init = need_init || !m->lf_history_valid;
-    const int wmask = C.E->dims == 3 ? 0x1D : 0xD;   // u and the w fields
+    const int wmask = C.E->dims == 3 ? 0x3D : 0xD;   // u, the w fields (and psi in 3D)
     const bool diff = variant == EWV_LEAPFROG_DIFFERENCE;
     if (diff && C.E->dims != 2) return fail(*C.err, EWV_ERR_UNSUPPORTED, "difference form: 2D only");
     if (need_init) {
@@ -1332,7 +1334,7 @@ int ewv_create_model(const ewv_model_desc* desc, ewv_model_t* out) {
     const int per128 = 128 / m->elem;
     m->pitch = ((d.nx + per128 - 1) / per128) * per128;
     m->nz = d.dims == 3 ? d.nz : 1;
-    m->nfields = d.dims == 3 ? 5 : 4;
+    m->nfields = d.dims == 3 ? 6 : 4;
     m->field_elems = (size_t)m->nz * d.ny * m->pitch;
     m->vec_elems = (size_t)m->nfields * m->field_elems;
     if ((size_t)m->nz * d.ny * m->pitch > (size_t)INT32_MAX) {
@@ -2054,13 +2056,20 @@ int ewv_adjoint_step(ewv_model_t m, int method, double t, double dt, int deg,
                      const void* checkpoint, void* adj_state, void* grad) {
     if (!m || !checkpoint || !adj_state || !grad) return EWV_ERR_INVALID_ARG;
     if (m->d.dims == 3) return fail(m->err, EWV_ERR_UNSUPPORTED, "the adjoint is two-dimensional");
-    if (method != EWV_METHOD_FABER && method != EWV_METHOD_HORK && method != EWV_METHOD_KRYLOV)
-        return fail(m->err, EWV_ERR_UNSUPPORTED, "adjoint implemented for the Faber, HORK and Krylov steps");
-    if (deg < 1 || deg > (method == EWV_METHOD_KRYLOV ? MAX_M : MAX_DEG) || !(dt > 0.0))
+    if (method != EWV_METHOD_FABER && method != EWV_METHOD_HORK && method != EWV_METHOD_KRYLOV &&
+        method != EWV_METHOD_LEAPFROG)
+        return fail(m->err, EWV_ERR_UNSUPPORTED,
+                    "adjoint implemented for the Faber, HORK, Krylov and leap-frog steps");
+    const bool lf = method == EWV_METHOD_LEAPFROG;
+    if (lf && m->lf_variant == EWV_LEAPFROG_LITERAL)
+        return fail(m->err, EWV_ERR_UNSUPPORTED, "leap-frog adjoint: averaged damping of w only");
+    if ((!lf && (deg < 1 || deg > (method == EWV_METHOD_KRYLOV ? MAX_M : MAX_DEG))) || !(dt > 0.0))
         return fail(m->err, EWV_ERR_INVALID_ARG, "degree / dimension out of range or dt <= 0");
     if (!aligned(checkpoint) || !aligned(adj_state) || !aligned(grad))
         return fail(m->err, EWV_ERR_BAD_SIZE_OR_ALIGNMENT, "adjoint buffers must be 256-B aligned");
-    int rc = check_bound(m, method == EWV_METHOD_KRYLOV ? EWV_METHOD_ADJOINT_KRYLOV : EWV_METHOD_ADJOINT_FABER,
+    int rc = check_bound(m, method == EWV_METHOD_KRYLOV ? EWV_METHOD_ADJOINT_KRYLOV
+                            : lf                        ? EWV_METHOD_ADJOINT_LEAPFROG
+                                                        : EWV_METHOD_ADJOINT_FABER,
                          deg, m->err);
     if (rc != EWV_OK) return rc;
     Engine* E = ensure_model_engine(m);
@@ -2157,6 +2166,29 @@ int ewv_adjoint_step(ewv_model_t m, int method, double t, double dt, int deg,
     };
     if (method == EWV_METHOD_KRYLOV)
         return adjoint_krylov(m, E, t, dt, deg, adj_state, grad, probs, d_tp, tb);
+    if (lf) {
+        // tape (vector 1) = level n; q in vector 2, H^T q in vector 3; the cotangents of
+        // w^{n-1} live in the second nshots vectors of adj_state
+        void* a1 = (char*)adj_state + (size_t)ns * vb;
+        launch_leapfrog_adjoint(prec, tb, E->d_adj, d_tp, 0, 2, 3, a1, dt, s);
+        ++m->launches;
+        StageArgs gr = stage_defaults();       // grad += (s lam_u) G(u^n, w^n)
+        gr.x = 1;
+        gr.grad = grad;
+        gr.gq = 2;
+        gr.gscale = 1.0;
+        stage(gr);
+        StageArgs tr = stage_defaults();       // H^T q
+        tr.transpose = 1;
+        tr.x = 2;
+        tr.ch = 1.0;
+        tr.ck = 1.0;
+        tr.y_out = 3;
+        stage(tr);
+        launch_leapfrog_adjoint(prec, tb, E->d_adj, d_tp, 1, 2, 3, a1, dt, s);
+        ++m->launches;
+        return adj_finish();
+    }
     if (method == EWV_METHOD_HORK) {
         // u^{n+1} = sum_i w_i k_i, k_i = (I + dt H~) k_{i-1}; tape T_k = k_k = vector k+1
         const std::vector<double> lam = hork_lambdas(deg);

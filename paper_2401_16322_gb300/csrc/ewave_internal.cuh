@@ -51,7 +51,7 @@ struct ProblemDev {
     int tiles_x, tiles_y, tile_base, ntiles;
     int rec_stride, capacity, p, has_src;
     int shot, pad_;       // shot index inside its model (per-shot caller arrays)
-    int nz, nfields;      // 2D: 1 and 4 (u, v, w_x, w_y); 3D: nz and 5 (w_z added)
+    int nz, nfields;      // 2D: 1 and 4 (u, v, w_x, w_y); 3D: nz and 6 (w_z, psi added)
     int src_k, tiles_z;   // 3D: source plane, tiles along z (KC3 planes each); 2D: 0, 1
     int pchunks, pchunk_base;   // flat pointwise passes: chunks of this problem's vector, first
     int nbtab, pad2;      // entries of btab
@@ -117,6 +117,10 @@ void launch_stage(int precision, int R, int nblocks, const ProblemDev* probs,
 void launch_leapfrog(int precision, int R, int nblocks, const ProblemDev* probs,
                      const int* tile_prob, int cur, int prev, int variant, double dt,
                      cudaStream_t s);
+// Pointwise parts of the leap-frog adjoint step (mode 0: q from lambda; mode 1: lambda update
+// from y = H^T q); a1_base: the second cotangent vector of every shot (lam of w^{n-1}).
+void launch_leapfrog_adjoint(int precision, int nblocks, const ProblemDev* probs, const int* tile_prob,
+                             int mode, int qv, int yv, void* a1_base, double dt, cudaStream_t s);
 
 // kernels_3d.cu: three-dimensional forward pass and leap-frog step.
 int upload_stencil_tables_3d(const double* fs_uzz, const double* fs_uz, const double* fs_dwz);

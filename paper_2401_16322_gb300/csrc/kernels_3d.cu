@@ -1,11 +1,18 @@
 // Three-dimensional fused stencil kernels (the 400^3 workload).
 //
-// Operator: the three-dimensional extension of Eq. (1), on U = (u, v, w_x, w_y, w_z):
+// Operator: the three-dimensional PML form of Eq. (1) with an auxiliary field psi (psi_t = u),
+// on U = (u, v, w_x, w_y, w_z, psi):
 //   (HU)_u   = v
-//   (HU)_v   = -(bx by + by bz + bx bz) u - (bx + by + bz) v
+//   (HU)_v   = -(bx by + by bz + bx bz) u - (bx + by + bz) v - bx by bz psi
 //              + c^2 (u_xx + u_yy + u_zz + d_x w_x + d_y w_y + d_z w_z)
-//   (HU)_w_a = (mean of the other two b's - b_a) d_a u - b_a w_a      (a = x, y, z)
-// with w_x at (i+1/2, j, k), w_y at (i, j+1/2, k) and w_z at (i, j, k+1/2).  The stencils are
+//   (HU)_w_a = (sum of the other two b's - b_a) d_a u + (product of the other two b's) d_a psi
+//              - b_a w_a                                            (a = x, y, z)
+//   (HU)_psi = u
+// With one axis undamped and a field constant along it, the u, v and remaining w rows are
+// Eq. (1) on the other two axes.  The products of two b's vanish outside the edges of the
+// layer, so the psi derivatives (same half-point stencils as those of u) are read from
+// global memory only where their coefficient is nonzero.
+// w_x lives at (i+1/2, j, k), w_y at (i, j+1/2, k), w_z at (i, j, k+1/2), psi at the nodes.  The stencils are
 // Sec. 2.1's, with zero extension beyond the grid.  z is the vertical axis, k = 0 the top.
 // With a free surface, z plays the part of the 2D y axis:
 //   - it points upward: d_z u at k+1/2 = sum_q s_q (u_{k-q} - u_{k+1+q}) / dx;
@@ -106,6 +113,46 @@ struct Deriv3 {
 template <typename T>
 __device__ __forceinline__ T colv(const T* base, long long ps, int q, int nmax) {
     return q < nmax ? base[(long long)q * ps] : T(0);
+}
+
+// Half-point first derivative of psi along one axis (not yet scaled by 1/dx), read from
+// global memory: p points at psi of the output's own node, `stride` is the axis stride, idx
+// the node index along the axis and n its extent (zero extension).  up = true: the vertical
+// axis, whose derivative at k+1/2 is sum_q s_q (psi_{k-q} - psi_{k+1+q}).
+template <typename T, int R>
+__device__ __forceinline__ T dpsi_half(const T* p, long long stride, int idx, int n, bool up) {
+    T s = T(0);
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        const T fwd = (idx + 1 + q < n) ? p[(long long)(1 + q) * stride] : T(0);
+        const T bwd = (idx - q >= 0) ? p[-(long long)q * stride] : T(0);
+        s += S3<T, R>(q) * (up ? bwd - fwd : fwd - bwd);
+    }
+    return s;
+}
+// d_z psi at half level k+1/2 near a free surface (k < 3): the Appendix A rows.
+template <typename T>
+__device__ __forceinline__ T dpsi_fs(const T* col, long long ps, int k, int nz) {
+    T s = T(0);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s += fs3<T>(FS3_UZ + k * 8 + q) * colv(col, ps, q, nz);
+    return s;
+}
+
+// The psi terms of one output point: the products of two damping coefficients times the
+// psi derivatives (scaled by 1/dx), zero where the product vanishes.
+template <typename T, int R>
+__device__ __forceinline__ void psi_terms(const T* psi_c, long long pitch, long long ps, int i,
+                                          int j, int k, int nx, int ny, int nz, bool fs,
+                                          T pyz, T pxz, T pxy, T idx1, T& gx, T& gy, T& gz) {
+    gx = (pyz != T(0) && i < nx - 1) ? pyz * dpsi_half<T, R>(psi_c, 1, i, nx, false) * idx1 : T(0);
+    gy = (pxz != T(0) && j < ny - 1) ? pxz * dpsi_half<T, R>(psi_c, pitch, j, ny, false) * idx1 : T(0);
+    gz = T(0);
+    if (pxy != T(0) && k < nz - 1) {
+        const T d = (fs && k < 3) ? dpsi_fs<T>(psi_c - (long long)k * ps, ps, k, nz)
+                                  : dpsi_half<T, R>(psi_c, ps, k, nz, true);
+        gz = pxy * d * idx1;
+    }
 }
 
 template <typename T, int R>
@@ -304,16 +351,20 @@ stage3d_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ til
                 const T xwx = swx[ly][lx + R];
                 const T xwy = swy[ly + R][lx];
                 const T xwz = wq[b][c][R];
+                const T xpsi = X[5 * fstr + o];
+                T gpx, gpy, gpz;
+                psi_terms<T, R>(X + 5 * fstr + o, pitch, ps, i, j, k, nx, ny, nz, fs, byn * bzn,
+                                bxn * bzn, bxn * byn, idx1, gpx, gpy, gpz);
                 T hv = -(bxn * byn + byn * bzn + bxn * bzn) * xu - (bxn + byn + bzn) * xv
-                       + c2 * (dv.lap * idx2 + dv.div * idx1);
+                       - bxn * byn * bzn * xpsi + c2 * (dv.lap * idx2 + dv.div * idx1);
                 if (i == P->src_i && j == P->src_j && k == P->src_k) hv += sig;
-                const T hwx = (i < nx - 1) ? (T(0.5) * (byn + bzn) - bxh) * dv.dux * idx1 - bxh * xwx : T(0);
-                const T hwy = (j < ny - 1) ? (T(0.5) * (bxn + bzn) - byh) * dv.duy * idx1 - byh * xwy : T(0);
-                const T hwz = (k < nz - 1) ? (T(0.5) * (bxn + byn) - bzh) * dv.duz * idx1 - bzh * xwz : T(0);
-                const T xf[5] = {xu, xv, xwx, xwy, xwz};
-                const T hf[5] = {xv, hv, hwx, hwy, hwz};
+                const T hwx = (i < nx - 1) ? (byn + bzn - bxh) * dv.dux * idx1 + gpx - bxh * xwx : T(0);
+                const T hwy = (j < ny - 1) ? (bxn + bzn - byh) * dv.duy * idx1 + gpy - byh * xwy : T(0);
+                const T hwz = (k < nz - 1) ? (bxn + byn - bzh) * dv.duz * idx1 + gpz - bzh * xwz : T(0);
+                const T xf[6] = {xu, xv, xwx, xwy, xwz, xpsi};
+                const T hf[6] = {xv, hv, hwx, hwy, hwz, xu};
 #pragma unroll
-                for (int f = 0; f < 5; ++f) {
+                for (int f = 0; f < 6; ++f) {
                     const bool pad = (f == 2 && i >= nx - 1) || (f == 3 && j >= ny - 1) ||
                                      (f == 4 && k >= nz - 1);
                     const long long of = f * fstr + o;
@@ -342,8 +393,9 @@ stage3d_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ til
 
 // --------------------------------------------------------------------------------------
 // Leap-frog kernel (Sec. 3.1's scheme on the 3D system).  Vectors `cur` (level n) and
-// `prev` (level n-1) use fields 0 (u), 2, 3, 4 (w_x, w_y, w_z); level n+1 overwrites prev.
-// Damping of u_t centred; damping of w time-averaged (variant 0) or explicit (variant 1).
+// `prev` (level n-1) use fields 0 (u), 2, 3, 4 (w_x, w_y, w_z) and 5 (psi); level n+1
+// overwrites prev.  Damping of u_t centred; damping of w time-averaged (variant 0) or
+// explicit (variant 1); psi^{n+1} = psi^n + dt (u^n + u^{n+1}) / 2 (psi^{n-1} is not used).
 // --------------------------------------------------------------------------------------
 template <typename T, int R>
 __global__ void __launch_bounds__(NTHREADS)
@@ -432,7 +484,12 @@ leapfrog3d_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ 
                 const T byh = damp3<T>(beta0, inv_pml, min(T(j) + T(1.5), T(ny - j) - T(0.5)), pml);
                 const T u = uq[b][c][R];
                 const T bsum = bxn + byn + bzn;
-                T rhs = -(bxn * byn + byn * bzn + bxn * bzn) * u + C2[o] * (dv.lap * idx2 + dv.div * idx1);
+                const T psi = Cn[5 * fstr + o];
+                T gp[3];
+                psi_terms<T, R>(Cn + 5 * fstr + o, pitch, ps, i, j, k, nx, ny, nz, fs, byn * bzn,
+                                bxn * bzn, bxn * byn, idx1, gp[0], gp[1], gp[2]);
+                T rhs = -(bxn * byn + byn * bzn + bxn * bzn) * u - bxn * byn * bzn * psi
+                        + C2[o] * (dv.lap * idx2 + dv.div * idx1);
                 if (i == P->src_i && j == P->src_j && k == P->src_k) rhs += sig;
                 const T um = Pn[o];
                 const T up = ((T(2) * u - um) * inv_dt2 + bsum * um * inv_2dt + rhs)
@@ -440,15 +497,14 @@ leapfrog3d_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ 
                 T wn[3] = {T(0), T(0), T(0)};
                 const bool has[3] = {i < nx - 1, j < ny - 1, k < nz - 1};
                 const T bh[3] = {bxh, byh, bzh};
-                const T gcoef[3] = {T(0.5) * (byn + bzn) - bxh, T(0.5) * (bxn + bzn) - byh,
-                                    T(0.5) * (bxn + byn) - bzh};
+                const T gcoef[3] = {byn + bzn - bxh, bxn + bzn - byh, bxn + byn - bzh};
                 const T du[3] = {dv.dux, dv.duy, dv.duz};
                 const T wcur[3] = {swx[ly][lx + R], swy[ly + R][lx], wq[b][c][R]};
 #pragma unroll
                 for (int a3 = 0; a3 < 3; ++a3) {
                     if (!has[a3]) continue;
                     const T wm = Pn[(2 + a3) * fstr + o];
-                    const T g = gcoef[a3] * du[a3] * idx1;
+                    const T g = gcoef[a3] * du[a3] * idx1 + gp[a3];
                     wn[a3] = variant == 0 ? ((T(1) - bh[a3] * dt) * wm + T(2) * dt * g) / (T(1) + bh[a3] * dt)
                                           : wm + T(2) * dt * (-bh[a3] * wcur[a3] + g);
                 }
@@ -456,6 +512,7 @@ leapfrog3d_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ 
                 Pn[2 * fstr + o] = wn[0];
                 Pn[3 * fstr + o] = wn[1];
                 Pn[4 * fstr + o] = wn[2];
+                Pn[5 * fstr + o] = psi + T(0.5) * dt * (u + up);   // trapezoid rule for psi_t = u
             }
     }
 }

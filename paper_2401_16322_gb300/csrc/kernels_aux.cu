@@ -213,7 +213,7 @@ point_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ tile_
     const int lt = blockIdx.x - P->tile_base;
     // tile (x, y[, z chunk of KC3 planes]); 2D problems have nz = 1 and one z tile
     const int nz = P->nz > 1 ? P->nz : 1;
-    const int nf = P->nfields == 5 ? 5 : 4;
+    const int nf = P->nfields;   // 4 (2D) or 6 (3D: w_z and psi added)
     const int rr = lt / P->tiles_x;
     const int x0 = (lt % P->tiles_x) * BX, y0 = (rr % P->tiles_y) * BY;
     const int k0 = nz > 1 ? (rr / P->tiles_y) * KC3 : 0;
@@ -391,7 +391,7 @@ point_flat_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ 
     if ((pa.mode == 1 || pa.mode == 5) && kry[KRY_ACTIVE] == 0.0) return;
     if (pa.mode == 2 && kry[KRY_NONFINITE] != 0.0) return;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    const int nf = P->nfields == 5 ? 5 : 4;
+    const int nf = P->nfields;   // 4 (2D) or 6 (3D: w_z and psi added)
     const long long nelem = (long long)nf * P->field_stride;
     const long long e0 = (long long)(blockIdx.x - __ldg(pbase + pid)) * PCHUNK;
     const long long e1 = e0 + PCHUNK < nelem ? e0 + PCHUNK : nelem;
@@ -686,7 +686,7 @@ nonfinite_scan_kernel(const ProblemDev* __restrict__ probs, const int* __restric
     const int pid = flat_problem(pbase, nprob, blockIdx.x);
     const ProblemDev* P = probs + pid;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    const int nf = P->nfields == 5 ? 5 : 4;
+    const int nf = P->nfields;   // 4 (2D) or 6 (3D: w_z and psi added)
     const long long nelem = (long long)nf * P->field_stride;
     const int c = blockIdx.x - __ldg(pbase + pid);
     const long long e0 = (long long)c * PCHUNK;

@@ -621,6 +621,91 @@ void launch_stage(int precision, int R, int nblocks, const ProblemDev* probs,
     }
 }
 
+// --------------------------------------------------------------------------------------
+// Pointwise parts of the discrete adjoint of the leap-frog step (averaged damping of w).
+// One step maps z^n = (u^n, u^{n-1}, w^n, w^{n-1}) to z^{n+1} with
+//   u^{n+1} = s (2u^n/dt^2 + (b/(2dt) - 1/dt^2) u^{n-1} + H_vu u^n + H_vw w^n + f),
+//   w^{n+1} = ((1 - beta dt) w^{n-1} + 2 dt H_wu u^n) / (1 + beta dt),
+// s = 1 / (1/dt^2 + b/(2dt)), b = b_x + b_y at the node, beta the w row's own damping, and
+// H_vu, H_vw, H_wu blocks of H (Eq. 1).  Its transpose needs one H^T pass on
+// q = (0, s lam_u, 2 dt lam_w / (1 + beta dt)):
+//   lam_u'   = (H^T q)_u + (2/dt^2) s lam_u + lam_um,
+//   lam_um'  = s (b/(2dt) - 1/dt^2) lam_u,
+//   lam_w'   = (H^T q)_w + beta q_w + lam_wm        ((H^T q)_w holds -beta q_w),
+//   lam_wm'  = (1 - beta dt) / (1 + beta dt) lam_w.
+// Layout: vector 0 of a problem holds (lam_u, lam_um, lam_wx, lam_wy) (lam_um in the v field),
+// a1 + shot * vec_stride holds lam_wm in its w fields.  mode 0 writes q into vector `qv`;
+// mode 1 applies the update above with (H^T q) in vector `yv`.
+// --------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+leapfrog_adjoint_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ tile_prob,
+                        int mode, int qv, int yv, void* a1_base, double dt_d) {
+    const int pid = tile_prob[blockIdx.x];
+    const ProblemDev* P = probs + pid;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int nx = P->nx, ny = P->ny, pitch = P->pitch, pml = P->pml;
+    const bool fs = P->fs != 0;
+    const int lt = blockIdx.x - P->tile_base;
+    const int x0 = (lt % P->tiles_x) * BX, y0 = (lt / P->tiles_x) * BY;
+    const long long fstr = P->field_stride;
+    const T beta0 = (T)P->beta0, inv_pml = (T)P->inv_pml;
+    const T dt = (T)dt_d;
+    T* L0 = vec_ptr<T>(P, 0);
+    T* L1 = (T*)a1_base + (long long)P->shot * P->vec_stride;
+#pragma unroll
+    for (int b = 0; b < VY; ++b)
+#pragma unroll
+        for (int c = 0; c < VX; ++c) {
+            const int i = x0 + tx + c * TPX, j = y0 + ty + b * TPY;
+            if (i >= nx || j >= ny) continue;
+            const long long o = (long long)j * pitch + i;
+            const T bxn = damp<T>(beta0, inv_pml, T(min(i + 1, nx - i)), pml);
+            const T byn = damp<T>(beta0, inv_pml, fs ? T(ny - j) : T(min(j + 1, ny - j)), pml);
+            const T bxh = damp<T>(beta0, inv_pml, min(T(i) + T(1.5), T(nx - i) - T(0.5)), pml);
+            const T byh = damp<T>(beta0, inv_pml,
+                                  fs ? (T(ny - j) - T(0.5)) : min(T(j) + T(1.5), T(ny - j) - T(0.5)),
+                                  pml);
+            const T bsum = bxn + byn;
+            const T inv_dt2 = T(1) / (dt * dt), inv_2dt = T(1) / (T(2) * dt);
+            const T sn = T(1) / (inv_dt2 + bsum * inv_2dt);
+            const bool hx = i < nx - 1, hy = j < ny - 1;
+            const T lu = L0[o], lwx = hx ? L0[2 * fstr + o] : T(0), lwy = hy ? L0[3 * fstr + o] : T(0);
+            if (mode == 0) {
+                T* Q = vec_ptr<T>(P, qv);
+                Q[o] = T(0);
+                Q[fstr + o] = sn * lu;
+                Q[2 * fstr + o] = hx ? T(2) * dt * lwx / (T(1) + bxh * dt) : T(0);
+                Q[3 * fstr + o] = hy ? T(2) * dt * lwy / (T(1) + byh * dt) : T(0);
+            } else {
+                const T* Y = vec_ptr<T>(P, yv);
+                const T lum = L0[fstr + o];
+                L0[o] = Y[o] + T(2) * inv_dt2 * sn * lu + lum;
+                L0[fstr + o] = sn * (bsum * inv_2dt - inv_dt2) * lu;
+                if (hx) {
+                    const T qx = T(2) * dt * lwx / (T(1) + bxh * dt);
+                    L0[2 * fstr + o] = Y[2 * fstr + o] + bxh * qx + L1[2 * fstr + o];
+                    L1[2 * fstr + o] = (T(1) - bxh * dt) / (T(1) + bxh * dt) * lwx;
+                }
+                if (hy) {
+                    const T qy = T(2) * dt * lwy / (T(1) + byh * dt);
+                    L0[3 * fstr + o] = Y[3 * fstr + o] + byh * qy + L1[3 * fstr + o];
+                    L1[3 * fstr + o] = (T(1) - byh * dt) / (T(1) + byh * dt) * lwy;
+                }
+            }
+        }
+}
+
+void launch_leapfrog_adjoint(int precision, int nblocks, const ProblemDev* probs, const int* tile_prob,
+                             int mode, int qv, int yv, void* a1_base, double dt, cudaStream_t s) {
+    const dim3 block(TPX, TPY);
+    if (nblocks <= 0) return;
+    if (precision == 0)
+        leapfrog_adjoint_kernel<float><<<nblocks, block, 0, s>>>(probs, tile_prob, mode, qv, yv, a1_base, dt);
+    else
+        leapfrog_adjoint_kernel<double><<<nblocks, block, 0, s>>>(probs, tile_prob, mode, qv, yv, a1_base, dt);
+}
+
 void launch_leapfrog(int precision, int R, int nblocks, const ProblemDev* probs,
                      const int* tile_prob, int cur, int prev, int variant, double dt,
                      cudaStream_t s) {

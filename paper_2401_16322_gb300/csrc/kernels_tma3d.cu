@@ -1,16 +1,19 @@
 // Persistent, TMA-fed fused stencil pass for three-dimensional problems (FP32, forward
 // operator) on sm_103a.
 //
-// Same arithmetic as stage3d_kernel (kernels_3d.cu: the three-dimensional extension of
-// Eq. 1, Sec. 2.1 stencils, Appendix A / Sec. 2.2 rows on the vertical axis, in-register
-// damping, and the integrators' K / Y / ACC epilogue), organised for HBM bandwidth:
+// Same arithmetic as stage3d_kernel (kernels_3d.cu: the three-dimensional PML form of Eq. 1
+// with the auxiliary field psi, Sec. 2.1 stencils, Appendix A / Sec. 2.2 rows on the vertical
+// axis, damping from the per-model table, and the integrators' K / Y / ACC epilogue),
+// organised for HBM bandwidth:
 //   - a task is one 64 x 8 column tile of one problem over a chunk of KC3 planes; one CTA per
 //     SM walks the task list (tasks b, b + gridDim.x, ...);
 //   - the producer lane streams the chunk plane by plane through NST shared-memory stages
 //     (cp.async.bulk.tensor over 5D maps: x, y, z, field, vector).  The stage for compute
 //     plane c holds u(c) with its x / y halo, w_x(c) (x halo), w_y(c) (y halo), v(c), c^2(c),
-//     the pointwise operands U(c) and A(c), and the "front" values u(c + R) and
-//     w_z(c + R - 1);
+//     psi(c), the six-field pointwise operands U(c) and A(c), and the "front" values
+//     u(c + R) and w_z(c + R - 1);
+//   - the psi derivatives are needed only where a product of two damping coefficients is
+//     nonzero (the edges of the layer): there they are read with plain loads;
 //   - 2R warm-up stages before a chunk's first plane carry only front values;
 //   - the consumer warps push the front values into per-thread register queues
 //     (u over c-R .. c+R, w_z over c-R .. c+R-1), which supply every vertical tap.  The
@@ -46,13 +49,14 @@ struct Stage3 {
     static constexpr int WY_OFF = WX_OFF + BY3 * SW;     // w_y(c)    SH x BX
     static constexpr int V_OFF = WY_OFF + SH * BX;       // v(c)      PL
     static constexpr int C2_OFF = V_OFF + PL;            // c^2(c)    PL
-    static constexpr int PU_OFF = C2_OFF + PL;           // U(c)      5 x PL
-    static constexpr int PA_OFF = PU_OFF + 5 * PL;       // A(c)      5 x PL
-    static constexpr int FLOATS = PA_OFF + 5 * PL;
+    static constexpr int PS_OFF = C2_OFF + PL;           // psi(c)    PL
+    static constexpr int PU_OFF = PS_OFF + PL;           // U(c)      6 x PL
+    static constexpr int PA_OFF = PU_OFF + 6 * PL;       // A(c)      6 x PL
+    static constexpr int FLOATS = PA_OFF + 6 * PL;
     static constexpr int BYTES = FLOATS * 4;
     static_assert((UF_OFF * 4) % 128 == 0 && (WZ_OFF * 4) % 128 == 0 && (WX_OFF * 4) % 128 == 0 &&
                       (WY_OFF * 4) % 128 == 0 && (V_OFF * 4) % 128 == 0 &&
-                      (C2_OFF * 4) % 128 == 0 && (PU_OFF * 4) % 128 == 0 &&
+                      (C2_OFF * 4) % 128 == 0 && (PS_OFF * 4) % 128 == 0 && (PU_OFF * 4) % 128 == 0 &&
                       (PA_OFF * 4) % 128 == 0 && BYTES % 128 == 0,
                   "TMA destinations must be 128-byte aligned");
 };
@@ -175,7 +179,22 @@ __device__ __forceinline__ float dmp(float beta0, float inv_pml, float d, int pm
     return (d <= (float)pml) ? beta0 * r * r : 0.f;
 }
 
-// Map `kind` (0 u halo box, 1 w_x box, 2 w_y box, 3 one-field plane, 4 five-field plane) of
+// Half-point derivative of psi along one axis (unscaled), plain loads: p points at psi of the
+// output node, `stride` is the axis stride, idx the node index and n the extent (zero
+// extension); up = true for the vertical axis (sum_q s_q (psi_{k-q} - psi_{k+1+q})).
+template <int R>
+__device__ __forceinline__ float dpsi3(const float* p, long long stride, int idx, int n, bool up) {
+    float d[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        const float fwd = (idx + 1 + q < n) ? __ldg(p + (long long)(1 + q) * stride) : 0.f;
+        const float bwd = (idx - q >= 0) ? __ldg(p - (long long)q * stride) : 0.f;
+        d[q] = up ? bwd - fwd : fwd - bwd;
+    }
+    return st_tree<R>(d);
+}
+
+// Map `kind` (0 u halo box, 1 w_x box, 2 w_y box, 3 one-field plane, 4 six-field plane) of
 // vector k; map 10 is c^2.
 __device__ __forceinline__ const CUtensorMap* map3(const CUtensorMap* base, int k, int kind) {
     return base + (k == 0 ? 0 : 5) + kind;
@@ -193,7 +212,8 @@ __device__ __forceinline__ int find_task_problem(const int* __restrict__ base, i
 
 // MODE 0: integrator pass (epilogue above).  MODE 1: leap-frog step (Sec. 3.1's scheme on
 // the 3D system): a.x = level n (cur), a.a = level n-1 (prev, overwritten with level n+1 in
-// fields u, w_x, w_y, w_z), a.m = damping variant (0 time-averaged, 1 explicit), a.dt.
+// fields u, w_x, w_y, w_z and psi), a.m = damping variant (0 time-averaged, 1 explicit),
+// a.dt; psi^{n+1} = psi^n + dt (u^n + u^{n+1}) / 2.
 template <int R, int NW, int NST, int MODE>
 __global__ void __launch_bounds__(NW * 32 + 32, 1)
 stage_tma3d_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ tbase, int nprob,
@@ -225,7 +245,7 @@ stage_tma3d_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__
     const uint32_t bytes_warm = 2u * L::PL * 4u;
     // the leap-frog step does not read v
     const uint32_t bytes_full = (uint32_t)(L::PU_OFF * 4) - (MODE == 1 ? L::PL * 4u : 0u) +
-                                (has_u ? 5u * L::PL * 4u : 0u) + (has_a ? 5u * L::PL * 4u : 0u);
+                                (has_u ? 6u * L::PL * 4u : 0u) + (has_a ? 6u * L::PL * 4u : 0u);
     int issued = 0;
 
     if (warp == NW) {
@@ -300,6 +320,7 @@ stage_tma3d_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__
                         tma5(st + L::WY_OFF, map3(maps, kx, 2), x0, y0 - R, c, 3, vx, &full[s]);
                         if (MODE == 0) tma5(st + L::V_OFF, map3(maps, kx, 3), x0, y0, c, 1, vx, &full[s]);
                         tma3(st + L::C2_OFF, maps + 10, x0, y0, c, &full[s]);
+                        tma5(st + L::PS_OFF, map3(maps, kx, 3), x0, y0, c, 5, vx, &full[s]);
                         if (has_u)
                             tma5(st + L::PU_OFF, map3(maps, a.u, 4), x0, y0, c, 0, a.u == 0 ? 0 : a.u - 1,
                                  &full[s]);
@@ -438,22 +459,44 @@ stage_tma3d_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__
                         const float xwy = swy[(ly + R) * BX + tx];
                         const float xwz = wq[r][R];
                         const float c2 = st[L::C2_OFF + pt];
+                        const float xpsi = st[L::PS_OFF + pt];
                         const bool at_src = i == ti.src_i && j == ti.src_j && c == ti.src_k;
                         const long long o = (long long)c * ps + oc;
+                        // psi terms: (product of the other two b's) d_a psi, zero off the edges
+                        float gp[3] = {0.f, 0.f, 0.f};
+                        {
+                            const float pyz = byn * bzn, pxz = bxn * bzn, pxy = bxn * byn;
+                            const float* pc = ti.X + 5 * fstr + o;
+                            if (pyz != 0.f && i < nx - 1) gp[0] = pyz * dpsi3<R>(pc, 1, i, nx, false) * idx1;
+                            if (pxz != 0.f && j < ny - 1) gp[1] = pxz * dpsi3<R>(pc, ti.pitch, j, ny, false) * idx1;
+                            if (pxy != 0.f && c < nz - 1) {
+                                float d = 0.f;
+                                if (fs && c < 3) {
+                                    const float* col = ti.X + 5 * fstr + oc;
+#pragma unroll
+                                    for (int q = 0; q < 8; ++q)
+                                        d += g3t_fs[T3_UZ + c * 8 + q] * (q < nz ? __ldg(col + q * ps) : 0.f);
+                                } else {
+                                    d = dpsi3<R>(pc, ps, c, nz, true);
+                                }
+                                gp[2] = pxy * d * idx1;
+                            }
+                        }
                         if constexpr (MODE == 0) {
                             const float xv = st[L::V_OFF + pt];
                             float hv = -(bxn * byn + byn * bzn + bxn * bzn) * u - (bxn + byn + bzn) * xv
+                                       - bxn * byn * bzn * xpsi
                                        + c2 * ((uxx + uyy + uzz) * idx2 + (dwx + dwy + dwz) * idx1);
                             if (at_src) hv += ti.sig;
-                            const float hwx = (i < nx - 1) ? (0.5f * (byn + bzn) - bxh) * dux * idx1 - bxh * xwx : 0.f;
-                            const float hwy = (j < ny - 1) ? (0.5f * (bxn + bzn) - byh) * duy * idx1 - byh * xwy : 0.f;
-                            const float hwz = (c < nz - 1) ? (0.5f * (bxn + byn) - bzh) * duz * idx1 - bzh * xwz : 0.f;
-                            const float xf[5] = {u, xv, xwx, xwy, xwz};
-                            const float hf[5] = {xv, hv, hwx, hwy, hwz};
+                            const float hwx = (i < nx - 1) ? (byn + bzn - bxh) * dux * idx1 + gp[0] - bxh * xwx : 0.f;
+                            const float hwy = (j < ny - 1) ? (bxn + bzn - byh) * duy * idx1 + gp[1] - byh * xwy : 0.f;
+                            const float hwz = (c < nz - 1) ? (bxn + byn - bzh) * duz * idx1 + gp[2] - bzh * xwz : 0.f;
+                            const float xf[6] = {u, xv, xwx, xwy, xwz, xpsi};
+                            const float hf[6] = {xv, hv, hwx, hwy, hwz, u};
                             float* yp = ti.Y ? ti.Y + o : nullptr;
                             float* ap = ti.A ? ti.A + o : nullptr;
 #pragma unroll
-                            for (int fld = 0; fld < 5; ++fld) {
+                            for (int fld = 0; fld < 6; ++fld) {
                                 const bool pad = (fld == 2 && i >= nx - 1) || (fld == 3 && j >= ny - 1) ||
                                                  (fld == 4 && c >= nz - 1);
                                 const float uval = has_u ? st[L::PU_OFF + fld * L::PL + pt] : 0.f;
@@ -467,18 +510,17 @@ stage_tma3d_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__
                             const float dt = (float)a.dt;
                             const float inv_dt2 = 1.f / (dt * dt), inv_2dt = 1.f / (2.f * dt);
                             const float bsum = bxn + byn + bzn;
-                            float rhs = -(bxn * byn + byn * bzn + bxn * bzn) * u
+                            float rhs = -(bxn * byn + byn * bzn + bxn * bzn) * u - bxn * byn * bzn * xpsi
                                         + c2 * ((uxx + uyy + uzz) * idx2 + (dwx + dwy + dwz) * idx1);
                             if (at_src) rhs += ti.sig;
-                            const float* pm = st + L::PA_OFF + pt;   // level n-1, five fields
+                            const float* pm = st + L::PA_OFF + pt;   // level n-1, six fields
                             const float um = pm[0];
                             // fast (2-ulp) division: the step's own error is far larger
                             const float up = __fdividef((2.f * u - um) * inv_dt2 + bsum * um * inv_2dt + rhs,
                                                         inv_dt2 + bsum * inv_2dt);
                             const bool has[3] = {i < nx - 1, j < ny - 1, c < nz - 1};
                             const float bh[3] = {bxh, byh, bzh};
-                            const float gco[3] = {0.5f * (byn + bzn) - bxh, 0.5f * (bxn + bzn) - byh,
-                                                  0.5f * (bxn + byn) - bzh};
+                            const float gco[3] = {byn + bzn - bxh, bxn + bzn - byh, bxn + byn - bzh};
                             const float du[3] = {dux, duy, duz};
                             const float wcur[3] = {xwx, xwy, xwz};
                             float* out = ti.Y + o;
@@ -488,12 +530,13 @@ stage_tma3d_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__
                                 float wn = 0.f;
                                 if (has[a3]) {
                                     const float wm = pm[(2 + a3) * L::PL];
-                                    const float g = gco[a3] * du[a3] * idx1;
+                                    const float g = gco[a3] * du[a3] * idx1 + gp[a3];
                                     wn = a.m == 0 ? __fdividef((1.f - bh[a3] * dt) * wm + 2.f * dt * g, 1.f + bh[a3] * dt)
                                                   : wm + 2.f * dt * (-bh[a3] * wcur[a3] + g);
                                 }
                                 out[(2 + a3) * fstr] = wn;
                             }
+                            out[5 * fstr] = xpsi + 0.5f * dt * (u + up);   // trapezoid rule, psi_t = u
                         }
                     }
                 }
@@ -526,9 +569,9 @@ int encoder3() {
     return 0;
 }
 
-// 5D map over (x, y, z, field, vector) of one buffer, box (bx, by, 1, bf, 1).
+// 5D map over (x, y, z, field, vector) of one buffer (six fields), box (bx, by, 1, bf, 1).
 int enc5(CUtensorMap* out, void* base, const ProblemDev& P, int nvec, int bx, int by, int bf) {
-    cuuint64_t dims[5] = {(cuuint64_t)P.nx, (cuuint64_t)P.ny, (cuuint64_t)P.nz, 5, (cuuint64_t)nvec};
+    cuuint64_t dims[5] = {(cuuint64_t)P.nx, (cuuint64_t)P.ny, (cuuint64_t)P.nz, 6, (cuuint64_t)nvec};
     const cuuint64_t ps = (cuuint64_t)P.ny * P.pitch;
     cuuint64_t strides[4] = {(cuuint64_t)P.pitch * 4, ps * 4, (cuuint64_t)P.field_stride * 4,
                              (cuuint64_t)P.vec_stride * 4};
@@ -590,7 +633,7 @@ int tma3d_tasks_of(const ProblemDev& P) {
 }
 
 // NMAP3 maps per problem: state and workspace, each with the u halo box, the w_x box, the w_y
-// box, a one-field plane and a five-field plane; then c^2 (3D).  Sets P.tmaps.
+// box, a one-field plane and a six-field plane; then c^2 (3D).  Sets P.tmaps.
 int build_tensor_maps3d(std::vector<ProblemDev>& probs, int R, const std::vector<int>& work_vecs,
                         void** d_maps_inout) {
     if (encoder3() != 0) return -1;
@@ -599,7 +642,7 @@ int build_tensor_maps3d(std::vector<ProblemDev>& probs, int R, const std::vector
     const int SW = BX + 2 * TX3, SH = BY3 + 2 * R;
     const int bxs[5] = {SW, SW, BX, BX, BX};
     const int bys[5] = {SH, BY3, SH, BY3, BY3};
-    const int bfs[5] = {1, 1, 1, 1, 5};
+    const int bfs[5] = {1, 1, 1, 1, 6};
     for (int p = 0; p < n; ++p) {
         const ProblemDev& P = probs[p];
         CUtensorMap* m = maps.data() + (size_t)p * NMAP3;

@@ -20,7 +20,7 @@ ERRORS = {
 }
 F32, F64 = 0, 1
 METHOD = {"apply": 0, "faber": 1, "krylov": 2, "hork": 3, "rk32": 4, "rk44": 5, "leapfrog": 6,
-          "adjoint_faber": 7, "adjoint_krylov": 8}
+          "adjoint_faber": 7, "adjoint_krylov": 8, "adjoint_leapfrog": 9}
 LEAPFROG_AVERAGED, LEAPFROG_LITERAL, LEAPFROG_DIFFERENCE = 0, 1, 2
 
 # Every symbol include/ewave.h declares (checked by the tests).
@@ -175,7 +175,7 @@ def _dptr(a):
 
 class Model:
     """One velocity model with ``nshots`` shots, its device buffers held as torch tensors.
-    With ``nz`` it is three-dimensional (grid nz x ny x nx, five fields)."""
+    With ``nz`` it is three-dimensional (grid nz x ny x nx, six fields: psi added)."""
 
     def __init__(self, nx, ny, dx, order=8, pml=40, beta0=0.0, free_surface=True,
                  precision="f32", nshots=1, p=12, max_receivers=0, device=None, stream=None,
@@ -397,9 +397,11 @@ class Model:
 
     # ---------------------------------------------------------------- adjoint
     def adjoint_step(self, t, dt, degree, checkpoint, adj, grad, method="faber"):
-        """lambda <- (dPhi/dU)^T lambda, grad += (dPhi/dm)^T lambda for one Faber / HORK step
-        (Krylov: the adjoint of the step's exponential)."""
-        self.ensure_workspace("adjoint_krylov" if method == "krylov" else "adjoint_faber", degree)
+        """lambda <- (dPhi/dU)^T lambda, grad += (dPhi/dm)^T lambda for one Faber / HORK /
+        leap-frog step (Krylov: the adjoint of the step's exponential).  Leap-frog: ``adj``
+        holds 2 nshots vectors (cotangents of level n, then of w at level n-1)."""
+        self.ensure_workspace({"krylov": "adjoint_krylov", "leapfrog": "adjoint_leapfrog"}.get(
+            method, "adjoint_faber"), degree)
         self._check(self.lib.ewv_adjoint_step(self.h, METHOD[method], t, dt, degree,
                                               ctypes.c_void_p(checkpoint.data_ptr()),
                                               ctypes.c_void_p(adj.data_ptr()),

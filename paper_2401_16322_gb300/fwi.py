@@ -1,7 +1,7 @@
 """Full-waveform-inversion gradient through the library's discrete adjoint.
 
 The forward map takes m = c^2 (squared velocity at the nodes, [ny, nx]) to every shot's
-seismogram (Faber steps, Sec. 3.2).  The backward pass runs the exact discrete adjoint of
+seismogram (Faber, HORK or Krylov steps, Sec. 3.2, or leap-frog steps, Sec. 3.1).  The backward pass runs the exact discrete adjoint of
 those steps (``ewv_adjoint_step``), injecting the seismogram cotangent at the receivers
 (``ewv_adjoint_inject``), and returns dL/dm.  Forward states are checkpointed every
 ``stride`` steps (``ewv_checkpoint_stride``): with stride 1 every state is stored, which is
@@ -19,20 +19,54 @@ from .ewave import Model, checkpoint_stride
 class FaberFWI:
     """Forward simulation with checkpoints and the adjoint gradient for one model
     (``method`` "faber": degree m; "hork": m stages; "krylov": dimension m, adjoint of the
-    step's exponential)."""
+    step's exponential; "leapfrog": the two-step scheme with averaged damping, m ignored).
+
+    Leap-frog carries two time levels: a checkpoint stores the state (level n) and the
+    library's history vector (level n-1, workspace vector 1 of each shot), and the adjoint
+    state has two vectors per shot (``ewv_adjoint_step``)."""
 
     def __init__(self, model: Model, dt, degree, nsteps, nrec, budget=None, t0=0.0, method="faber"):
-        if method not in ("faber", "hork", "krylov"):
-            raise ValueError("the adjoint exists for the Faber, HORK and Krylov steps")
+        if method not in ("faber", "hork", "krylov", "leapfrog"):
+            raise ValueError("the adjoint exists for the Faber, HORK, Krylov and leap-frog steps")
         self.method = method
         self.model = model
         self.dt, self.degree, self.nsteps, self.nrec, self.t0 = dt, degree, nsteps, nrec, t0
         self.stride = checkpoint_stride(nsteps, budget if budget else max(nsteps, 1))
         torch = model.torch
         nv = model.vector_elems
+        self.levels = 2 if method == "leapfrog" else 1
+        if method == "leapfrog":
+            # one workspace for the forward steps and the adjoint: never rebound in between,
+            # so the history vector survives
+            model.ensure_workspace("adjoint_leapfrog", 0)
         self.nck = (nsteps + self.stride - 1) // self.stride
-        self.ckpt = torch.zeros(self.nck, model.nshots * nv, dtype=model.dtype, device=model.device)
+        self.ckpt = torch.zeros(self.nck, self.levels, model.nshots * nv, dtype=model.dtype,
+                                device=model.device)
         self.seg = torch.zeros(self.stride, model.nshots * nv, dtype=model.dtype, device=model.device)
+
+    def _history(self):
+        """Leap-frog: the level n-1 vector of every shot (workspace vector 1), as a view."""
+        md = self.model
+        nv, ns = md.vector_elems, md.nshots
+        per_shot = md.work.numel() // (ns * nv)
+        return md.work.view(ns, per_shot, nv)[:, 0, :]
+
+    def _save(self, k):
+        md = self.model
+        self.ckpt[k, 0].copy_(md.state)
+        if self.levels == 2:
+            nv, ns = md.vector_elems, md.nshots
+            if k == 0:
+                self.ckpt[k, 1].copy_(md.state)          # u^{-1} = u^0, w^{-1} = w^0
+            else:
+                self.ckpt[k, 1].view(ns, nv).copy_(self._history())
+
+    def _restore(self, k):
+        md = self.model
+        md.state.copy_(self.ckpt[k, 0])
+        if self.levels == 2:
+            nv, ns = md.vector_elems, md.nshots
+            self._history().copy_(self.ckpt[k, 1].view(ns, nv))
 
     def _set_m(self, m_c2):
         c = np.sqrt(np.asarray(m_c2.detach().double().cpu().numpy() if hasattr(m_c2, "detach") else m_c2,
@@ -49,7 +83,7 @@ class FaberFWI:
         md.ensure_workspace(self.method, self.degree)
         for n in range(self.nsteps):
             if n % self.stride == 0:
-                self.ckpt[n // self.stride].copy_(md.state)
+                self._save(n // self.stride)
             md.step(self.method, self.t0 + n * self.dt, self.dt, self.degree, 1)
         md.sync()           # raises if the forward run produced a non-finite state
         s = md.seismo.view(md.nshots, md.capacity, md.max_receivers)[:, :self.nsteps, :self.nrec]
@@ -64,9 +98,9 @@ class FaberFWI:
         g = torch.zeros(ns, md.max_receivers * self.nsteps, dtype=md.dtype, device=md.device)
         g = g.view(ns, self.nsteps, md.max_receivers)
         g[:, :, :self.nrec] = grad_seis.to(md.dtype)
-        lam = torch.zeros(ns * nv, dtype=md.dtype, device=md.device)
+        lam = torch.zeros(self.levels * ns * nv, dtype=md.dtype, device=md.device)
         grad = torch.zeros(ns * fe, dtype=md.dtype, device=md.device)
-        adj_ws = "adjoint_krylov" if self.method == "krylov" else "adjoint_faber"
+        adj_ws = {"krylov": "adjoint_krylov", "leapfrog": "adjoint_leapfrog"}.get(self.method, "adjoint_faber")
         md.ensure_workspace(adj_ws, self.degree)
         md.adjoint_inject(lam, g[:, self.nsteps - 1, :].contiguous())
         for k in range(self.nck - 1, -1, -1):
@@ -74,15 +108,15 @@ class FaberFWI:
             n1 = min(n0 + self.stride, self.nsteps)
             # recompute the states U^{n0} .. U^{n1-1} of this segment from its checkpoint
             if self.stride > 1:
-                md.state.copy_(self.ckpt[k])
                 md.ensure_workspace(self.method, self.degree)
+                self._restore(k)
                 for n in range(n0, n1):
                     self.seg[n - n0].copy_(md.state)
                     if n + 1 < n1:
                         md.step(self.method, self.t0 + n * self.dt, self.dt, self.degree, 1)
                 md.ensure_workspace(adj_ws, self.degree)
             for n in range(n1, n0, -1):          # adjoint of step n: U^{n-1} -> U^n
-                ck = self.seg[n - 1 - n0] if self.stride > 1 else self.ckpt[n - 1]
+                ck = self.seg[n - 1 - n0] if self.stride > 1 else self.ckpt[n - 1, 0]
                 md.adjoint_step(self.t0 + (n - 1) * self.dt, self.dt, self.degree, ck, lam, grad,
                                 self.method)
                 if n - 1 >= 1:

@@ -234,11 +234,16 @@ def noise_growth(models, batch, method, m, dt, t_quiet, nsteps=NOISE_STEPS, seed
         npts = md.nx * md.ny * (md.nz or 1)
         u, v = random_state([(npts,), (npts,)], seed + q)
         md.set_state(0, np.concatenate([u, v, np.zeros(md.n - 2 * npts)]))
-    batch.step(method, t_quiet, dt, m, nsteps)
-    batch.sync()
-    mid = [float(np.linalg.norm(md.get_state(0))) for md in models]
-    batch.step(method, t_quiet + nsteps * dt, dt, m, nsteps)
-    batch.sync()
+    try:
+        batch.step(method, t_quiet, dt, m, nsteps)
+        batch.sync()
+        mid = [float(np.linalg.norm(md.get_state(0))) for md in models]
+        batch.step(method, t_quiet + nsteps * dt, dt, m, nsteps)
+        batch.sync()
+    except EwaveError as e:
+        if "NONFINITE" in str(e):       # the noise grew past the floating-point range
+            return float("inf")
+        raise
     g = 0.0
     for md, a in zip(models, mid):
         b = float(np.linalg.norm(md.get_state(0)))

@@ -25,9 +25,23 @@ def gpu_model(om, precision="f64", nshots=1, p=12, max_receivers=0):
     return g
 
 
+def rel_l2_fields(got, ref, shapes, floor=1e-3):
+    """Relative L2 error of every field of two flattened states (fields in ``shapes`` order):
+    |got_f - ref_f| / max(|ref_f|, floor |ref|), so that an error in a field with a small norm
+    does not hide behind the others."""
+    out, o = [], 0
+    total = float(np.linalg.norm(ref))
+    for sh in shapes:
+        n = int(np.prod(sh))
+        g, r = got[o:o + n], ref[o:o + n]
+        out.append(float(np.linalg.norm(g - r) / max(np.linalg.norm(r), floor * total)))
+        o += n
+    return out
+
+
 def oracle_ellipse(om):
     return ellipse_params(om.c_max, om.beta0, om.dx, om.order, free_surface=om.free_surface)
 
 
 __all__ = ["TOL", "TOL_SEISMO_F32", "oracle_model", "gpu_model", "oracle_ellipse", "flatten",
-           "unflatten", "rel_l2"]
+           "unflatten", "rel_l2", "rel_l2_fields"]

@@ -1,12 +1,14 @@
-"""GPU parity of the three-dimensional path (the extension of Eq. 1 used for the 400^3 workload)
-against the oracle, through the C ABI: H x on ragged grids (FP64 1e-12, FP32 1e-5), every
-integrator with the source active and receivers recorded, and bit-exact node indices."""
+"""GPU parity of the three-dimensional path (the auxiliary-field PML form of Eq. 1 used for the
+400^3 workload, oracle/wave3d_pml.py) against the oracle, through the C ABI: H x on ragged grids
+(FP64 1e-12, FP32 1e-5, whole state and every field on its own), every integrator with the
+source active and receivers recorded, and bit-exact node indices."""
 import numpy as np
 import pytest
 
-from _helpers import TOL, flatten, rel_l2
+from _helpers import TOL, flatten, rel_l2, rel_l2_fields
 from oracle import faber, krylov, rk
 from oracle import wave3d as W
+from oracle import wave3d_pml as PML
 from oracle.model import default_beta0, unflatten
 from paper_2401_16322_gb300.workloads import layered3d, smooth_random_state
 
@@ -17,7 +19,7 @@ def _models(nx, ny, nz, prec, fs=True, order=8, pml=6, p=10, max_receivers=0, se
     from paper_2401_16322_gb300 import Model
     c = layered3d(nx, ny, nz, seed)
     b0 = default_beta0(float(c.max()), pml, 10.0)
-    om = W.Model3D(nx, ny, nz, 10.0, order, pml, b0, fs, c)
+    om = PML.Model3DPML(nx, ny, nz, 10.0, order, pml, b0, fs, c)
     g = Model(nx, ny, 10.0, order, pml, b0, fs, precision=prec, p=p, max_receivers=max_receivers,
               nz=nz)
     g.set_velocity(c)
@@ -31,8 +33,10 @@ def test_operator_matches_oracle(prec, shape, fs, order):
     nx, ny, nz = shape          # ragged in every tile direction (64 x 16 x 32 tiles)
     om, g = _models(nx, ny, nz, prec, fs=fs, order=order)
     x = flatten(smooth_random_state(om.field_shapes(), 17))
-    ref = flatten(W.apply_H3(om, unflatten(om, x)))
-    assert rel_l2(g.apply(x), ref) < TOL[prec]
+    ref = flatten(PML.apply_H3p(om, unflatten(om, x)))
+    got = g.apply(x)
+    assert rel_l2(got, ref) < TOL[prec]
+    assert max(rel_l2_fields(got, ref, om.field_shapes())) < TOL[prec], rel_l2_fields(got, ref, om.field_shapes())
     g.close()
 
 
@@ -65,7 +69,7 @@ def _oracle_steps(om, method, U0, src, t, dt, m, nsteps, rn):
                                   free_surface=om.free_surface)
     U, S = U0, []
     if method == "leapfrog":
-        LF = W.leapfrog3d_init(U0)
+        LF = PML.leapfrog3dp_init(U0)
     for n in range(nsteps):
         tn = t + n * dt
         if method == "faber":
@@ -79,8 +83,8 @@ def _oracle_steps(om, method, U0, src, t, dt, m, nsteps, rn):
         elif method == "rk44":
             U = rk.rk44_step(om, U, src, tn, dt)
         elif method == "leapfrog":
-            LF = W.leapfrog3d_step(om, LF, src, tn, dt)
-            U = (LF[0], U[1], LF[2], LF[4], LF[6])
+            LF = PML.leapfrog3dp_step(om, LF, src, tn, dt)
+            U = (LF[0], U[1], LF[2], LF[4], LF[6], LF[8])
         S.append(U[0][rn[:, 0], rn[:, 1], rn[:, 2]].copy())
     return U, np.array(S)
 
@@ -90,7 +94,7 @@ def _oracle_steps(om, method, U0, src, t, dt, m, nsteps, rn):
                                       ("rk44", 0), ("leapfrog", 0), ("faber", 1), ("hork", 1),
                                       ("hork-horner", 6), ("hork-horner", 1)])
 def test_integrators_match_oracle_3d(prec, method, m):
-    """m = 1 covers the copy of a work vector into the state (all five fields)."""
+    """m = 1 covers the copy of a work vector into the state (all six fields)."""
     om, g, src, rec, rn, U0 = _setup(prec)
     if method == "hork-horner":
         g.set_hork_form("horner")
@@ -117,6 +121,11 @@ def test_integrators_match_oracle_3d(prec, method, m):
         ref = flatten(U)
     tol = TOL[prec] * (3 if prec == "f32" else 1)
     assert rel_l2(got, ref) < tol, (method, m, rel_l2(got, ref))
+    shapes = om.field_shapes()
+    if method == "leapfrog":
+        shapes = [shapes[0]] + shapes[2:]
+    per_field = rel_l2_fields(got, ref, shapes)
+    assert max(per_field) < tol, (method, m, per_field)
     Sg = g.seismogram(0, len(rec), nsteps)
     assert rel_l2(Sg, S) < tol
     g.close()
@@ -146,6 +155,8 @@ def test_fp32_pass_variants_match_oracle_3d(variant, method, m):
     g.set_state(0, flatten(U0))
     g.step(method, t, dt, m, nsteps)
     U, S = _oracle_steps(om, method, U0, src, t, dt, m, nsteps, rn)
-    assert rel_l2(g.get_state(0), flatten(U)) < 3 * TOL["f32"]
+    got = g.get_state(0)
+    assert rel_l2(got, flatten(U)) < 3 * TOL["f32"]
+    assert max(rel_l2_fields(got, flatten(U), om.field_shapes())) < 3 * TOL["f32"]
     assert rel_l2(g.seismogram(0, len(rec), nsteps), S) < 3 * TOL["f32"]
     g.close()

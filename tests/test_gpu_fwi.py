@@ -206,3 +206,96 @@ def test_krylov_gradient_matches_oracle_and_differences(budget):
     Jm = 0.5 * float(((fwi.forward(c0 ** 2 - eps * dm) - d) ** 2).sum())
     fd = (Jp - Jm) / (2 * eps)
     assert abs(fd - float(np.sum(grad * dm))) <= 1e-3 * abs(fd)
+
+
+# ---------------------------------------------------------------- leap-frog adjoint
+LF_DT, LF_NSTEPS = 1e-3, 30
+
+
+def test_leapfrog_adjoint_step_is_the_oracle_transpose():
+    """One leap-frog adjoint step on the GPU (FP64) against the transpose of the oracle's
+    assembled step matrix (oracle/leapfrog_adjoint.py) applied to a random cotangent of
+    (u, u_prev, w, w_prev), and the gradient increment s G(u^n, w^n) lambda_u."""
+    import torch
+    from oracle import leapfrog_adjoint as LA
+    c_true, c0, beta0, ell = _setup()
+    om = OModel(NX, NY, DX, 8, PML, beta0, True, c_true)
+    g = _gpu(c_true, beta0, ell, "f64", sources=False)
+    nu = NX * NY
+    nwx, nwy = NY * (NX - 1), (NY - 1) * NX
+    lam_u, lam_um, lam_wx, lam_wy, lam_wmx, lam_wmy = random_state(
+        [(nu,), (nu,), (nwx,), (nwy,), (nwx,), (nwy,)], 13)
+    u, wx, wy = smooth_random_state([(nu,), (nwx,), (nwy,)], 14)
+    nv = g.vector_elems
+    ck = g.new_vector()
+    g.pack(np.concatenate([u, np.zeros(nu), wx, wy]), ck)
+    adj = torch.zeros(2 * nv, dtype=torch.float64, device="cuda")
+    g.pack(np.concatenate([lam_u, lam_um, lam_wx, lam_wy]), adj[:nv])
+    g.pack(np.concatenate([np.zeros(2 * nu), lam_wmx, lam_wmy]), adj[nv:])
+    grad = torch.zeros(g.layout.field_elems, dtype=torch.float64, device="cuda")
+    g.adjoint_step(0.0, LF_DT, 0, ck, adj, grad, method="leapfrog")
+    g.sync()
+    a0, a1 = g.unpack(adj[:nv]), g.unpack(adj[nv:])
+    got = np.concatenate([a0[:nu], a0[nu:2 * nu], a0[2 * nu:], a1[2 * nu:]])
+    A, s = LA.step_matrix(om, LF_DT)
+    lam = np.concatenate([lam_u, lam_um, lam_wx, lam_wy, lam_wmx, lam_wmy])
+    ref = A.T @ lam
+    assert rel_l2(got, ref) < 1e-12
+    G = LA._G(om, u.reshape(NY, NX), wx.reshape(NY, NX - 1), wy.reshape(NY - 1, NX)).ravel()
+    g_ref = (s * G * lam_u).reshape(NY, NX)
+    g_got = grad.view(NY, g.layout.pitch)[:, :NX].cpu().numpy()
+    assert rel_l2(g_got, g_ref) < 1e-12
+
+
+def _lf_shots(om):
+    return [(PointSource(om, sx, 2 * DX, 30.0, 0.04, amp=1e3, p=10), receiver_nodes(om, REC)) for sx in SX]
+
+
+@pytest.mark.parametrize("variant", ["averaged", "difference"])
+def test_leapfrog_gradient_matches_oracle_checkpointing_and_differences(variant):
+    """The FWI gradient through leap-frog steps (two shots, 30 steps of 1 ms, FP64): GPU =
+    oracle's discrete adjoint (1e-10), checkpoints every 4th step (two time levels each,
+    segments recomputed) reproduce full storage bit for bit, and central differences of the
+    GPU misfit agree (1e-3).  The difference form is the same scheme and has the same
+    adjoint."""
+    import torch
+    from oracle import leapfrog_adjoint as LA
+    from paper_2401_16322_gb300.ewave import LEAPFROG_AVERAGED, LEAPFROG_DIFFERENCE
+    from paper_2401_16322_gb300.fwi import FaberFWI
+    c_true, c0, beta0, ell = _setup()
+    om_t = OModel(NX, NY, DX, 8, PML, beta0, True, c_true)
+    d_obs = LA.forward(om_t, _lf_shots(om_t), LF_DT, LF_NSTEPS)[1]
+    om = OModel(NX, NY, DX, 8, PML, beta0, True, c0)
+    J_o, g_o = LA.fwi_gradient(om, _lf_shots(om), d_obs, LF_DT, LF_NSTEPS)
+    d = torch.tensor(np.array(d_obs), dtype=torch.float64, device="cuda")
+    grads = []
+    for budget in (None, 8):
+        g = _gpu(c0, beta0, ell, "f64")
+        g.set_leapfrog_variant(LEAPFROG_DIFFERENCE if variant == "difference" else LEAPFROG_AVERAGED)
+        fwi = FaberFWI(g, LF_DT, 0, LF_NSTEPS, len(REC), budget=budget, method="leapfrog")
+        seis = fwi.forward(c0 ** 2)
+        assert abs(0.5 * float(((seis - d) ** 2).sum()) - J_o) <= 1e-9 * J_o
+        grads.append(fwi.backward(seis - d).double().cpu().numpy())
+    assert fwi.stride == 4
+    assert rel_l2(grads[0], g_o) < 1e-10
+    assert np.array_equal(grads[0], grads[1])
+    dm = smooth_random_state([(NY, NX)], 9, sigma_cells=2.0)[0] * 0.01 * c0 ** 2
+    eps = 1e-4
+    Jp = 0.5 * float(((fwi.forward(c0 ** 2 + eps * dm) - d) ** 2).sum())
+    Jm = 0.5 * float(((fwi.forward(c0 ** 2 - eps * dm) - d) ** 2).sum())
+    fd = (Jp - Jm) / (2 * eps)
+    assert abs(fd - float(np.sum(grads[0] * dm))) <= 1e-3 * abs(fd)
+
+
+def test_leapfrog_adjoint_rejects_the_literal_variant():
+    import torch
+    from paper_2401_16322_gb300.ewave import LEAPFROG_LITERAL, EwaveError
+    c_true, c0, beta0, ell = _setup()
+    g = _gpu(c_true, beta0, ell, "f64", sources=False)
+    g.set_leapfrog_variant(LEAPFROG_LITERAL)
+    nv = g.vector_elems
+    ck = g.new_vector()
+    adj = torch.zeros(2 * nv, dtype=torch.float64, device="cuda")
+    grad = torch.zeros(g.layout.field_elems, dtype=torch.float64, device="cuda")
+    with pytest.raises(EwaveError, match="UNSUPPORTED"):
+        g.adjoint_step(0.0, LF_DT, 0, ck, adj, grad, method="leapfrog")

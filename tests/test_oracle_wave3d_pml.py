@@ -166,3 +166,74 @@ def test_auxiliary_field_pml_absorbs_what_the_mean_reading_reflects():
         left[name] = np.linalg.norm(U[0][inner]) / np.linalg.norm(u0[inner])
     assert left["mean"] > 5e-3
     assert left["aux"] < 2e-3 and left["aux"] < left["mean"] / 10.0, left
+
+
+def test_leapfrog_without_damping_equals_the_3d_leapfrog():
+    """At beta = 0 the psi terms vanish and the w rows coincide with oracle.wave3d's: the
+    auxiliary-field leap-frog advances (u, w) exactly as leapfrog3d_step does."""
+    m = _m3(beta=False)
+    U = tuple(smooth_random_state(P.field_shapes(m), 41))
+    LFp = P.leapfrog3dp_init(U)
+    LF = W.leapfrog3d_init(U[:5])
+    for n in range(4):
+        LFp = P.leapfrog3dp_step(m, LFp, None, n * 4e-4, 4e-4)
+        LF = W.leapfrog3d_step(m, LF, None, n * 4e-4, 4e-4)
+    for a, b in zip(LFp[:8], LF):
+        assert np.allclose(a, b, rtol=1e-13, atol=1e-13 * np.max(np.abs(b)))
+
+
+def test_leapfrog_reduces_to_the_2d_leapfrog_on_a_y_invariant_field():
+    """y undamped, a field constant in y: on the y rows at least R from the y edges the
+    auxiliary-field leap-frog advances u, w_x and w_z exactly as the 2D oracle's leap-frog
+    (averaged damping) advances u, w_x and w_y on the x-z slice, damping and free surface
+    included."""
+    from oracle import leapfrog as L2
+    nx, ny, nz, pml = 13, 41, 12, 3
+    c2d = layered(nx, nz, 7, vmin=1500, vmax=3000)
+    b0 = default_beta0(3000.0, pml, 10.0)
+    m3 = W.Model3D(nx, ny, nz, 10.0, 8, pml, b0, True, np.repeat(c2d[:, None, :], ny, axis=1))
+    m2 = Model(nx, nz, 10.0, 8, pml, b0, True, c2d)
+    u2, v2, wx2, wz2 = smooth_random_state(m2.field_shapes(), 23)
+    rep = lambda a: np.repeat(a[:, None, :], ny, 1)
+    U3 = (rep(u2), rep(v2), rep(wx2), np.zeros((nz, ny - 1, nx)), rep(wz2), np.zeros((nz, ny, nx)))
+    LF3 = P.leapfrog3dp_init(U3)
+    LF2 = L2.leapfrog_init((u2, v2, wx2, wz2))
+    dt = 3e-4
+    for n in range(2):
+        LF3 = P.leapfrog3dp_step(m3, LF3, None, n * dt, dt, undamped=("y",))
+        LF2 = L2.leapfrog_step(m2, LF2, None, n * dt, dt, variant="averaged")
+    # the y edges' zero extension makes w_y nonzero near them; its effect spreads at most
+    # 2 R cells a step, so the middle row (20 cells in) is still exact after 2 steps
+    j = ny // 2
+    for got, ref in ((LF3[0][:, j, :], LF2[0]), (LF3[2][:, j, :], LF2[2]), (LF3[6][:, j, :], LF2[4])):
+        assert np.allclose(got, ref, rtol=1e-12, atol=1e-12 * np.max(np.abs(ref)))
+
+
+def test_leapfrog_converges_at_second_order_to_the_semi_discrete_solution():
+    """With damping, free surface and a source: the auxiliary-field leap-frog converges at
+    order 2 to Faber steps of degree 60 on the same operator (pinned above against the dense
+    exponential), in u and in psi."""
+    import math
+    from oracle import faber
+    from oracle.simulate import rel_l2
+    nx, ny, nz, pml = 8, 7, 7, 2
+    c = layered3d(nx, ny, nz, 5, vmin=1500, vmax=3000)
+    m = P.Model3DPML(nx, ny, nz, 10.0, 8, pml, default_beta0(3000.0, pml, 10.0), True, c)
+    s = W.PointSource3D(m, 40.0, 30.0, 20.0, 40.0, 2.7 / 40.0, amp=1.0, p=16)
+    T = 0.1
+    params = faber.ellipse_params(m.c_max, m.beta0, m.dx, 8, dims=3, free_surface=True)
+    U = m.zeros_state()
+    nref = 16
+    for n in range(nref):
+        U = faber.faber_step(m, U, s, n * T / nref, T / nref, 60, params)
+    errs, perrs = [], []
+    for nst in (160, 320):
+        h = T / nst
+        LF = P.leapfrog3dp_init(m.zeros_state())
+        for n in range(nst):
+            LF = P.leapfrog3dp_step(m, LF, s, n * h, h)
+        errs.append(rel_l2(LF[0], U[0]))
+        perrs.append(rel_l2(LF[8], U[5]))
+    for e in (errs, perrs):
+        rate = math.log2(e[0] / e[1])
+        assert abs(rate - 2.0) < 0.15, (e, rate)
