@@ -287,13 +287,19 @@ int ewv_set_leapfrog_variant(ewv_model_t model, int variant);
  * (m = stages; reverse of the (I + dt H~) chain): exact discrete adjoints, needing
  * ewv_workspace_bytes(EWV_METHOD_ADJOINT_FABER, m) of workspace (the step is recomputed
  * from the checkpoint: m tape vectors + 3 cotangents).  method EWV_METHOD_KRYLOV (m = Krylov
- * dimension, <= EWV_MAX_KRYLOV_M): the Krylov step depends nonlinearly on U (its basis does),
- * so this is the adjoint of the step's exact exponential, U^n = [I 0] exp(dt H~) [U^{n-1}; e_p]:
- * lambda <- exp(dt H)^T lambda by Arnoldi on dt H^T (m products), and
- * grad += int_0^dt [exp((dt-s) H)^T lambda]_v (L u + D w)(s) ds by 4-point Gauss-Legendre,
- * with the states at the nodes from the forward and adjoint Arnoldi bases (dense output).
- * It agrees with the Krylov forward to that step's time accuracy.  Workspace:
- * ewv_workspace_bytes(EWV_METHOD_ADJOINT_KRYLOV, m) (2m + 9 vectors).
+ * dimension, <= EWV_MAX_KRYLOV_M): the Krylov step depends nonlinearly on U (its basis and
+ * Hessenberg matrix do).  By default (EWV_KRYLOV_ADJOINT_EXACT) this is the exact discrete
+ * adjoint of the computed step: the basis is recomputed from the checkpoint and the reverse
+ * mode runs through the output combination, the Frechet derivative of exp(H_m) (FP64, on the
+ * host: one stream synchronisation per call), every modified Gram-Schmidt update in reverse
+ * order (the orthogonalisation window of ewv_set_krylov_window included) and the start
+ * vector with its tail scaling eta = |U|.  With EWV_KRYLOV_ADJOINT_EXPONENTIAL
+ * (ewv_set_krylov_adjoint) it is the adjoint of the step's exact exponential,
+ * U^n = [I 0] exp(dt H~) [U^{n-1}; e_p]: lambda <- exp(dt H)^T lambda by Arnoldi on dt H^T
+ * (m products), and grad += int_0^dt [exp((dt-s) H)^T lambda]_v (L u + D w)(s) ds by 4-point
+ * Gauss-Legendre with dense output from the two bases; it agrees with the Krylov forward
+ * only to that step's time accuracy.  Workspace: ewv_workspace_bytes(EWV_METHOD_ADJOINT_KRYLOV,
+ * m) (2m + 9 vectors) for either.
  * method EWV_METHOD_LEAPFROG (m ignored; averaged damping of w, in the plain or the
  * difference form, which are one scheme): the exact discrete adjoint of one Sec. 3.1 step
  * z^{n-1} -> z^n, z = (u, u_prev, w, w_prev).  checkpoint: level n-1 in the u, w_x, w_y
@@ -313,6 +319,9 @@ int ewv_set_leapfrog_variant(ewv_model_t model, int variant);
  * segment are recomputed from its checkpoint during the backward pass. */
 int ewv_adjoint_step(ewv_model_t model, int method, double t, double dt, int m,
                      const void* checkpoint, void* adj_state, void* grad);
+#define EWV_KRYLOV_ADJOINT_EXACT 0        /* reverse mode through the computed Krylov step */
+#define EWV_KRYLOV_ADJOINT_EXPONENTIAL 1  /* adjoint of exp(dt H~), the step's limit          */
+int ewv_set_krylov_adjoint(ewv_model_t model, int mode);
 int ewv_adjoint_inject(ewv_model_t model, void* adj_state, const void* values);
 int ewv_checkpoint_stride(int nsteps, int budget, int* stride);
 /* out[o] = sum over shots of per_shot[shot][o] (fields [ny][pitch]), shots summed in order:

@@ -162,6 +162,7 @@ struct ewv_model {
     int store_bf16 = 0;         // storage-precision experiment (ewv_set_storage_rounding)
     int kry_window = 0;         // Krylov orthogonalisation window (0 = full Gram-Schmidt)
     int hork_form = EWV_HORK_LOW_STORAGE;   // evaluation order of the HORK polynomial
+    int kry_adjoint = EWV_KRYLOV_ADJOINT_EXACT;   // which Krylov adjoint ewv_adjoint_step runs
     bool lf_history_valid = false;
     // device metadata
     int* d_rec = nullptr;
@@ -206,6 +207,8 @@ struct Engine {
     size_t d_adj_bytes = 0;
     ProblemDev* d_kadj = nullptr; // Krylov adjoint: three descriptor views of the workspace
     size_t d_kadj_bytes = 0;
+    double* d_kbar = nullptr;     // exact Krylov adjoint: per-shot reverse-sweep scalars
+    size_t d_kbar_n = 0;
     int* d_err = nullptr;       // error word: 1 = a TMA pipeline wait timed out, 2 = non-finite
     int* h_err = nullptr;       // pinned host copy, written by an async copy at the end of a call
     cudaEvent_t err_ev = nullptr;   // recorded after that copy
@@ -269,6 +272,7 @@ struct Engine {
         cudaFree(d_adj);
         cudaFree(d_adj_maps);
         cudaFree(d_kadj);
+        cudaFree(d_kbar);
     }
 };
 
@@ -2052,6 +2056,313 @@ static int adjoint_krylov(ewv_model* m, Engine* E, double t, double dt, int mm, 
     return check_launch(m->err);
 }
 
+// ---------------------------------------------------------------- exact Krylov adjoint
+// exp(A) of a dense n x n matrix (row-major) by the [13/13] Pade approximant with scaling and
+// squaring (Higham 2005), in FP64 on the host: the small dense part of the reverse sweep.
+static std::vector<double> host_expm(const std::vector<double>& A0, int n) {
+    auto mul = [n](const std::vector<double>& X, const std::vector<double>& Y) {
+        std::vector<double> Z((size_t)n * n, 0.0);
+        for (int r = 0; r < n; ++r)
+            for (int k = 0; k < n; ++k) {
+                const double x = X[(size_t)r * n + k];
+                if (x == 0.0) continue;
+                for (int c = 0; c < n; ++c) Z[(size_t)r * n + c] += x * Y[(size_t)k * n + c];
+            }
+        return Z;
+    };
+    double f[27];
+    f[0] = 1.0;
+    for (int i = 1; i <= 26; ++i) f[i] = f[i - 1] * i;
+    double b[14];
+    for (int k = 0; k <= 13; ++k) b[k] = f[26 - k] * f[13] / (f[26] * f[k] * f[13 - k]);
+    double nrm = 0.0;
+    for (int c = 0; c < n; ++c) {
+        double cs = 0.0;
+        for (int r = 0; r < n; ++r) cs += std::fabs(A0[(size_t)r * n + c]);
+        nrm = std::max(nrm, cs);
+    }
+    const double theta13 = 5.371920351148152;
+    const int sc = nrm > theta13 ? (int)std::ceil(std::log2(nrm / theta13)) : 0;
+    std::vector<double> A(A0);
+    const double fac = std::ldexp(1.0, -sc);
+    for (double& v : A) v *= fac;
+    const std::vector<double> A2 = mul(A, A), A4 = mul(A2, A2), A6 = mul(A4, A2);
+    const size_t nn = (size_t)n * n;
+    std::vector<double> T1(nn), T2(nn);
+    for (size_t e = 0; e < nn; ++e) T1[e] = b[13] * A6[e] + b[11] * A4[e] + b[9] * A2[e];
+    std::vector<double> U = mul(A6, T1);
+    for (size_t e = 0; e < nn; ++e) U[e] += b[7] * A6[e] + b[5] * A4[e] + b[3] * A2[e];
+    for (int r = 0; r < n; ++r) U[(size_t)r * n + r] += b[1];
+    U = mul(A, U);
+    for (size_t e = 0; e < nn; ++e) T2[e] = b[12] * A6[e] + b[10] * A4[e] + b[8] * A2[e];
+    std::vector<double> V = mul(A6, T2);
+    for (size_t e = 0; e < nn; ++e) V[e] += b[6] * A6[e] + b[4] * A4[e] + b[2] * A2[e];
+    for (int r = 0; r < n; ++r) V[(size_t)r * n + r] += b[0];
+    // solve (V - U) X = (V + U) by Gaussian elimination with partial pivoting
+    std::vector<double> L(nn), X(nn);
+    for (size_t e = 0; e < nn; ++e) {
+        L[e] = V[e] - U[e];
+        X[e] = V[e] + U[e];
+    }
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (std::fabs(L[(size_t)r * n + c]) > std::fabs(L[(size_t)piv * n + c])) piv = r;
+        if (piv != c)
+            for (int k = 0; k < n; ++k) {
+                std::swap(L[(size_t)c * n + k], L[(size_t)piv * n + k]);
+                std::swap(X[(size_t)c * n + k], X[(size_t)piv * n + k]);
+            }
+        const double d = L[(size_t)c * n + c];
+        for (int r = c + 1; r < n; ++r) {
+            const double fct = L[(size_t)r * n + c] / d;
+            if (fct == 0.0) continue;
+            for (int k = c; k < n; ++k) L[(size_t)r * n + k] -= fct * L[(size_t)c * n + k];
+            for (int k = 0; k < n; ++k) X[(size_t)r * n + k] -= fct * X[(size_t)c * n + k];
+        }
+    }
+    for (int c = n - 1; c >= 0; --c) {
+        const double d = L[(size_t)c * n + c];
+        for (int k = 0; k < n; ++k) {
+            double v = X[(size_t)c * n + k];
+            for (int q = c + 1; q < n; ++q) v -= L[(size_t)c * n + q] * X[(size_t)q * n + k];
+            X[(size_t)c * n + k] = v / d;
+        }
+    }
+    for (int i = 0; i < sc; ++i) X = mul(X, X);
+    return X;
+}
+
+// Exact discrete adjoint of one Krylov step (reverse mode through the Arnoldi process; the
+// passes are described in kernels_kadj.cu).  Views over the workspace wvec(i) of each shot:
+// F (the forward Arnoldi: state = wvec(0) = the checkpoint copy, so q_k = wvec(k-1)) and A
+// (state = the cotangent, work = wvec(0): vector i >= 1 is wvec(i-1), so q_k is vector k).
+static int adjoint_krylov_exact(ewv_model* m, Engine* E, double t, double dt, int mm, void* adj_state,
+                                void* grad, const std::vector<ProblemDev>& base, const int* d_tp, int tb) {
+    cudaStream_t s = m->stream;
+    const int ns = m->d.nshots, prec = m->d.precision, R = m->R, p = m->d.src_taylor_p;
+    const size_t vb = m->vec_elems * m->elem;
+    const size_t per_shot = (m->work_bytes / ns) / vb;
+    if (per_shot < (size_t)(2 * mm + 4))
+        return fail(m->err, EWV_ERR_WORKSPACE_TOO_SMALL, "exact Krylov adjoint needs 2m + 4 vectors");
+    const int window = m->kry_window;
+    auto wvec = [&](int sh, int k) { return (char*)m->work + ((size_t)sh * per_shot + (size_t)k) * vb; };
+    if (!E->d_kbar || E->d_kbar_n < (size_t)ns * KB_STRIDE) {
+        cudaFree(E->d_kbar);
+        E->d_kbar = nullptr;
+        CUDA_OR_FAIL(m->err, cudaMalloc(&E->d_kbar, sizeof(double) * (size_t)ns * KB_STRIDE));
+        E->d_kbar_n = (size_t)ns * KB_STRIDE;
+    }
+    std::vector<ProblemDev> views(2 * (size_t)ns);
+    for (int sh = 0; sh < ns; ++sh) {
+        ProblemDev P = base[sh];
+        P.pchunks = E->probs[sh].pchunks;
+        P.pchunk_base = E->probs[sh].pchunk_base;
+        P.kbar = E->d_kbar + (size_t)sh * KB_STRIDE;
+        ProblemDev F = P, A = P;
+        F.state = wvec(sh, 0);
+        F.work = wvec(sh, 1);
+        A.state = (char*)adj_state + (size_t)sh * vb;
+        A.work = wvec(sh, 0);
+        views[sh] = F;
+        views[ns + sh] = A;
+    }
+    const size_t bytes = sizeof(ProblemDev) * views.size();
+    if (!E->d_kadj || E->d_kadj_bytes < bytes) {
+        cudaFree(E->d_kadj);
+        E->d_kadj = nullptr;
+        CUDA_OR_FAIL(m->err, cudaMalloc(&E->d_kadj, bytes));
+        E->d_kadj_bytes = bytes;
+    }
+    CUDA_OR_FAIL(m->err, cudaMemcpyAsync(E->d_kadj, views.data(), bytes, cudaMemcpyHostToDevice, s));
+    const ProblemDev* vF = E->d_kadj;
+    const ProblemDev* vA = E->d_kadj + ns;
+    const double tol = prec == EWV_F64 ? 1e-14 : 1e-6;
+    // ---- forward Arnoldi of step n from the checkpoint (F view), exactly as run_krylov
+    launch_set_clock(vF, ns, t, dt, s);
+    launch_prologue(vF, ns, PRO_KRYLOV, mm, 0.0, 0.0, 0.0, s);
+    m->launches += 2;
+    {
+        PointArgs pn{};
+        pn.mode = 0;
+        pn.m = mm;
+        pn.tol = tol;
+        pn.partials = E->d_partials;
+        pn.counters = E->d_counters;
+        launch_point_flat(prec, E->nchunks, vF, E->d_pbase, ns, pn, s);
+        ++m->launches;
+        for (int j = 1; j <= mm; ++j) {
+            const int k0 = window > 0 ? std::max(1, j - window + 1) : 1;
+            StageArgs a = stage_defaults();
+            a.x = j - 1;
+            a.y_out = j;
+            a.d = k0 - 1;
+            a.src_slot = j;
+            a.x_scale_slot = KRY_S + j;
+            a.ch = dt;
+            a.ck = 1.0;
+            a.fin_mode = FIN_MATVEC;
+            a.fin_j = j;
+            a.fin_k = k0;
+            a.m = mm;
+            a.tol = tol;
+            a.partials = E->d_partials;
+            a.counters = E->d_counters;
+            launch_stage(prec, R, tb, vF, d_tp, a, s);
+            ++m->launches;
+            const int kmax = (j == mm) ? j - 1 : j;
+            for (int k = k0; k <= kmax; ++k) {
+                PointArgs pm{};
+                pm.mode = 1;
+                pm.j = j;
+                pm.k = k;
+                pm.m = mm;
+                pm.tol = tol;
+                pm.partials = E->d_partials;
+                pm.counters = E->d_counters;
+                launch_point_flat(prec, E->nchunks, vF, E->d_pbase, ns, pm, s);
+                ++m->launches;
+            }
+        }
+        if (launch_expm(vF, ns, mm, s) != 0) return fail(m->err, EWV_ERR_CUDA, "expm configuration failed");
+        ++m->launches;
+    }
+    auto flat = [&](const KAdjArgs& ka) {
+        launch_kadj_flat(prec, E->nchunks, vA, E->d_pbase, ns, ka, s);
+        ++m->launches;
+    };
+    auto args = [&](int mode, int fin) {
+        KAdjArgs ka{};
+        ka.mode = mode;
+        ka.fin = fin;
+        ka.m = mm;
+        ka.dot = -1;
+        ka.partials = E->d_partials;
+        ka.counters = E->d_counters;
+        return ka;
+    };
+    // ---- <ybar, q_k> for the output's cotangents
+    for (int k = 1; k <= mm; ++k) {
+        KAdjArgs ka = args(KA_DOT, FK_STORE);
+        ka.a = 0;
+        ka.b = k;
+        ka.slot = KB_D + k;
+        flat(ka);
+    }
+    // ---- host: Hbar = L(H^T, ebar e_1^T), ebar_k = beta s_k <ybar, q_k>, beta_bar, Vbar = beta e ybar^T
+    std::vector<double> kry((size_t)ns * KRY_STRIDE), kbh((size_t)ns * KB_STRIDE, 0.0);
+    for (int sh = 0; sh < ns; ++sh)
+        CUDA_OR_FAIL(m->err, cudaMemcpyAsync(kry.data() + (size_t)sh * KRY_STRIDE, base[sh].kry,
+                                             sizeof(double) * KRY_STRIDE, cudaMemcpyDeviceToHost, s));
+    CUDA_OR_FAIL(m->err, cudaMemcpyAsync(kbh.data(), E->d_kbar, sizeof(double) * (size_t)ns * KB_STRIDE,
+                                         cudaMemcpyDeviceToHost, s));
+    CUDA_OR_FAIL(m->err, cudaStreamSynchronize(s));
+    int jmax = 0;
+    for (int sh = 0; sh < ns; ++sh) {
+        const double* k = kry.data() + (size_t)sh * KRY_STRIDE;
+        double* kb = kbh.data() + (size_t)sh * KB_STRIDE;
+        if (k[KRY_NONFINITE] != 0.0) return fail(m->err, EWV_ERR_NONFINITE, "non-finite value in the Arnoldi process");
+        const int me = (int)k[KRY_MEFF];
+        jmax = std::max(jmax, me);
+        std::vector<double> dval(kb + KB_D, kb + KB_D + MAX_M + 2);
+        std::fill(kb, kb + KB_STRIDE, 0.0);
+        if (me <= 0) continue;
+        const double beta = k[KRY_BETA];
+        double bbar = 0.0;
+        std::vector<double> ebar(me);
+        for (int q = 1; q <= me; ++q) {
+            const double sq = k[KRY_S + q], d = dval[q];
+            ebar[q - 1] = beta * sq * d;
+            bbar += k[KRY_E + q - 1] * sq * d;
+            kb[KB_C + q] = beta * k[KRY_E + q - 1];
+        }
+        // L(X, Ebar) = upper-right block of expm([[X, Ebar], [0, X]]), X = H_me^T, Ebar = ebar e_1^T
+        const int n2 = 2 * me;
+        std::vector<double> big((size_t)n2 * n2, 0.0);
+        for (int r = 0; r < me; ++r)
+            for (int c = 0; c < me; ++c) {
+                const double x = k[KRY_H + c * MAX_M + r];          // (H^T)_{rc} = H_{cr}
+                big[(size_t)r * n2 + c] = x;
+                big[(size_t)(me + r) * n2 + me + c] = x;
+            }
+        for (int r = 0; r < me; ++r) big[(size_t)r * n2 + me] = ebar[r];
+        const std::vector<double> ex = host_expm(big, n2);
+        for (int r = 0; r < me; ++r)
+            for (int c = 0; c < me; ++c) kb[KB_HB + r * MAX_M + c] = ex[(size_t)r * n2 + me + c];
+        kb[KB_BBAR] = bbar;
+    }
+    CUDA_OR_FAIL(m->err, cudaMemcpyAsync(E->d_kbar, kbh.data(), sizeof(double) * (size_t)ns * KB_STRIDE,
+                                         cudaMemcpyHostToDevice, s));
+    // ---- Vbar_k = beta e_k ybar
+    for (int k = 1; k <= jmax; ++k) {
+        KAdjArgs ka = args(KA_SCALE, FK_NONE);
+        ka.a = 0;
+        ka.b = mm + 1 + k;
+        ka.slot = KB_C + k;
+        flat(ka);
+    }
+    // ---- reverse sweep over the columns
+    for (int j = jmax; j >= 1; --j) {
+        const int k0 = window > 0 ? std::max(1, j - window + 1) : 1;
+        KAdjArgs cp = args(KA_DOT, FK_COLPREP);      // <Vbar_{j+1}, q_{j+1}> -> hbar, wbar tail
+        cp.j = j;
+        cp.a = mm + 2 + j;
+        cp.b = j + 1;
+        flat(cp);
+        KAdjArgs cs = args(KA_COLSET, FK_GSPREP);    // wbar, w; <wbar, q_j> -> step k = j
+        cs.j = j;
+        cs.dot = j;
+        cs.fk = j;
+        flat(cs);
+        for (int k = j; k >= k0; --k) {
+            KAdjArgs gs = args(KA_GS, k > k0 ? FK_GSPREP : FK_NONE);
+            gs.j = j;
+            gs.k = k;
+            gs.k0 = k0;
+            if (k > k0) {
+                gs.dot = k - 1;
+                gs.fk = k - 1;
+            }
+            flat(gs);
+        }
+        // w = A v_j: tail and source terms, Vbar_j += dt H^T wbar, grad += dt s_j wbar_v G(q_j)
+        launch_kadj_src(vA, ns, prec, j, mm, dt, s);
+        ++m->launches;
+        StageArgs tr = stage_defaults();
+        tr.transpose = 1;
+        tr.x = 2 * mm + 3;
+        tr.ch = dt;
+        tr.a = mm + 1 + j;
+        tr.ca = 1.0;
+        tr.cak = 1.0;
+        tr.acc_out = mm + 1 + j;
+        launch_stage(prec, R, tb, vA, d_tp, tr, s);
+        StageArgs gr = stage_defaults();
+        gr.x = j;
+        gr.grad = grad;
+        gr.gq = 2 * mm + 3;
+        gr.gscale = dt;
+        gr.x_scale_slot = KRY_S + j;
+        launch_stage(prec, R, tb, vA, d_tp, gr, s);
+        m->launches += 2;
+    }
+    // ---- start: v_1 = x / beta, beta = |x|, x = [U; eta e_p], eta = |U|
+    KAdjArgs st = args(KA_DOT, FK_START);
+    st.a = mm + 2;
+    st.b = 1;
+    flat(st);
+    flat(args(KA_OUT, FK_NONE));
+    return check_launch(m->err);
+}
+
+int ewv_set_krylov_adjoint(ewv_model_t m, int mode) {
+    if (!m) return EWV_ERR_INVALID_ARG;
+    if (mode != EWV_KRYLOV_ADJOINT_EXACT && mode != EWV_KRYLOV_ADJOINT_EXPONENTIAL)
+        return fail(m->err, EWV_ERR_INVALID_ARG, "unknown Krylov adjoint mode %d", mode);
+    m->kry_adjoint = mode;
+    return EWV_OK;
+}
+
 int ewv_adjoint_step(ewv_model_t m, int method, double t, double dt, int deg,
                      const void* checkpoint, void* adj_state, void* grad) {
     if (!m || !checkpoint || !adj_state || !grad) return EWV_ERR_INVALID_ARG;
@@ -2165,7 +2476,9 @@ int ewv_adjoint_step(ewv_model_t m, int method, double t, double dt, int deg,
         return EWV_OK;
     };
     if (method == EWV_METHOD_KRYLOV)
-        return adjoint_krylov(m, E, t, dt, deg, adj_state, grad, probs, d_tp, tb);
+        return m->kry_adjoint == EWV_KRYLOV_ADJOINT_EXACT
+                   ? adjoint_krylov_exact(m, E, t, dt, deg, adj_state, grad, probs, d_tp, tb)
+                   : adjoint_krylov(m, E, t, dt, deg, adj_state, grad, probs, d_tp, tb);
     if (lf) {
         // tape (vector 1) = level n; q in vector 2, H^T q in vector 3; the cotangents of
         // w^{n-1} live in the second nshots vectors of adj_state

@@ -70,7 +70,44 @@ struct ProblemDev {
     const void* tmaps;    // FP32: this problem's TMA tensor maps (kernels_tma.cu), else null
     const float* btab;    // beta0 (1 - d/delta)^2 at distances d = k/2 cells, k < nbtab (FP32)
     float fbeta0, finv_pml, finv_dx, finv_dx2;   // FP32 copies of the damping / grid constants
+    double* kbar;         // exact Krylov adjoint: [KB_STRIDE] reverse-sweep scalars, else null
 };
+
+// Per-problem scalar block of the exact Krylov adjoint (doubles), offsets (kernels_kadj.cu).
+constexpr int KB_HB = 0;                                  // Hbar, (MAX_M+1) x MAX_M, row k-1, col j-1
+constexpr int KB_VT = KB_HB + (MAX_M + 1) * MAX_M;        // tails of Vbar_k, k = 1..MAX_M+1
+constexpr int KB_WT = KB_VT + (MAX_M + 2) * MAX_P;        // tail of wbar
+constexpr int KB_CT = KB_WT + MAX_P;                      // tail of the reconstructed w
+constexpr int KB_D = KB_CT + MAX_P;                       // <ybar, q_k> (grid), k = 1..MAX_M+1
+constexpr int KB_C = KB_D + MAX_M + 2;                    // beta e_k, k = 1..MAX_M+1
+constexpr int KB_HBAR = KB_C + MAX_M + 2;                 // hbar of the current Gram-Schmidt step
+constexpr int KB_HCOL = KB_HBAR + 1;                      // hbar of the column's normalisation
+constexpr int KB_BBAR = KB_HCOL + 1;                      // beta bar
+constexpr int KB_EBAR = KB_BBAR + 1;                      // eta bar
+constexpr int KB_OA = KB_EBAR + 1;                        // output: lambda = a Vbar_1 + b q_1
+constexpr int KB_OB = KB_OA + 1;
+constexpr int KB_STRIDE = ((KB_OB + 1 + 31) / 32) * 32;
+
+// Arguments of the exact Krylov adjoint's flat passes (kernels_kadj.cu).  Vector indices in
+// the adjoint view: 0 = the cotangent (ybar in, lambda out), k = q_k (k = 1..m+1, the
+// recomputed forward basis), m+1+k = Vbar_k, 2m+3 = wbar, 2m+4 = the reconstructed w.
+enum { KA_DOT = 0, KA_SCALE = 1, KA_COLSET = 2, KA_GS = 3, KA_OUT = 4 };
+enum { FK_NONE = 0, FK_STORE = 1, FK_COLPREP = 2, FK_GSPREP = 3, FK_START = 4 };
+struct KAdjArgs {
+    int mode, fin;
+    int j, k, k0, m;      // column, Gram-Schmidt index, window start of the column, dimension
+    int a, b;             // KA_DOT / KA_SCALE: vector indices (KA_SCALE: b = a * kb[slot])
+    int slot;             // kb slot (FK_STORE target, KA_SCALE coefficient)
+    int fk;               // Gram-Schmidt index the FK_GSPREP finalisation prepares
+    int dot;              // KA_COLSET / KA_GS: vector index of the fused dot's partner (-1: none)
+    double* partials;
+    unsigned int* counters;
+};
+void launch_kadj_flat(int precision, int nchunks, const ProblemDev* probs, const int* pbase,
+                      int nprob, const KAdjArgs& ka, cudaStream_t s);
+// Source and tail terms of the reverse matrix-vector product of column j (one thread per problem).
+void launch_kadj_src(const ProblemDev* probs, int nprob, int precision, int j, int m, double dt,
+                     cudaStream_t s);
 
 // Arguments of the fused stencil-stage kernel (see kernels_stencil.cu).
 struct StageArgs {

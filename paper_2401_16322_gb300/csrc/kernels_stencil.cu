@@ -322,7 +322,7 @@ stage_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ tile_
                     T* G = (T*)a.grad + (long long)P->shot * fstr;
                     const T* Q = vec_ptr<T>(P, a.gq);
                     const T gval = (uxx + uyy) * idx2 + (dwx + dwy) * idx1;
-                    G[o] += (T)a.gscale * Q[fstr + o] * gval;
+                    G[o] += (T)a.gscale * xs * Q[fstr + o] * gval;   // xs: per-problem scale
                     continue;
                 }
                 hu = xv;

@@ -101,6 +101,8 @@ extern "C" int ewv_faber_step_noalloc(const ewv_noalloc_faber_args* a, float* st
     P.ny = a->ny;
     P.pitch = a->pitch;
     P.fs = a->free_surface ? 1 : 0;
+    P.nz = 1;
+    P.nfields = 4;
     P.pml = a->pml_width;
     P.has_src = a->has_source ? 1 : 0;
     P.src_i = a->has_source ? a->src_i : -1;

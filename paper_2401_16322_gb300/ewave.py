@@ -25,7 +25,7 @@ LEAPFROG_AVERAGED, LEAPFROG_LITERAL, LEAPFROG_DIFFERENCE = 0, 1, 2
 
 # Every symbol include/ewave.h declares (checked by the tests).
 EXPORTS = [
-    "ewv_sync", "ewv_batch_sync", "ewv_debug_set_wait_limit",
+    "ewv_sync", "ewv_batch_sync", "ewv_debug_set_wait_limit", "ewv_set_krylov_adjoint",
     "ewv_create_model", "ewv_destroy_model", "ewv_set_stream", "ewv_layout",
     "ewv_workspace_bytes", "ewv_bind_buffers", "ewv_bind_workspace", "ewv_bind_seismogram",
     "ewv_reset_recording", "ewv_set_velocity", "ewv_set_source_receivers",
@@ -152,6 +152,7 @@ def load_library(path=LIB_PATH):
         "ewv_sync": ([vp], i),
         "ewv_batch_sync": ([vp], i),
         "ewv_debug_set_wait_limit": ([ctypes.c_ulonglong], i),
+        "ewv_set_krylov_adjoint": ([vp, i], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -273,6 +274,12 @@ class Model:
         polynomial (fewer bytes per pass, less accurate in FP32 at large steps)."""
         code = {"horner": 0, "low-storage": 1}[form]
         self._check(self.lib.ewv_set_hork_form(self.h, code), "hork_form")
+
+    def set_krylov_adjoint(self, mode):
+        """'exact' (default): reverse mode through the computed Krylov step; 'exponential':
+        the adjoint of exp(dt H~), which the step approximates."""
+        self._check(self.lib.ewv_set_krylov_adjoint(self.h, {"exact": 0, "exponential": 1}[mode]),
+                    "krylov_adjoint")
 
     def set_krylov_window(self, q):
         """Orthogonalise each Krylov vector against the q most recent ones only (0: all)."""
@@ -400,6 +407,13 @@ class Model:
         """lambda <- (dPhi/dU)^T lambda, grad += (dPhi/dm)^T lambda for one Faber / HORK /
         leap-frog step (Krylov: the adjoint of the step's exponential).  Leap-frog: ``adj``
         holds 2 nshots vectors (cotangents of level n, then of w at level n-1)."""
+        ns, nv, fe = self.nshots, self.vector_elems, self.layout.field_elems
+        levels = 2 if method == "leapfrog" else 1
+        for name, buf, need in (("checkpoint", checkpoint, ns * nv), ("adj", adj, levels * ns * nv),
+                                ("grad", grad, ns * fe)):
+            if buf.numel() < need or buf.dtype != self.dtype or not buf.is_cuda:
+                raise ValueError(f"adjoint_step: {name} must be a CUDA tensor of at least {need} "
+                                 f"{self.dtype} elements (got {buf.numel()} {buf.dtype} on {buf.device})")
         self.ensure_workspace({"krylov": "adjoint_krylov", "leapfrog": "adjoint_leapfrog"}.get(
             method, "adjoint_faber"), degree)
         self._check(self.lib.ewv_adjoint_step(self.h, METHOD[method], t, dt, degree,

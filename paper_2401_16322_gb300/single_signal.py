@@ -1,0 +1,182 @@
+"""The single-signal experiment of Sec. 4 (Secs. 4.1-4.3) on the GPU.
+
+Setup (Sec. 4.1): a homogeneous medium of 6 km x 5 km at c = 3 km/s, no absorbing layer
+(reflections do not reach the receiver by T), a 15 Hz Ricker source with delay t0 = 0.18 s
+at (3 km, 4.99 km) and one receiver at (3 km, 2.5 km).  The methods run on the 10 m grid;
+the reference runs on a 2.5 m grid.  Large steps are taken up to t = 0.6 s, then uniform
+steps of dt2 = dx / (8 c) = 0.417 ms to T = 1.3 s, so that every approximation is sampled at
+the same times while the wave passes the receiver (Sec. 4.1).
+
+Readings of what the paper leaves open (all stated with the results):
+
+* Coordinates: (x, depth), depth measured from the grid's top row; the boundaries are the
+  zero extension of Sec. 2.1 on all four sides (no free surface, no damping).
+* Reference: the paper's RK9-7 is not available; the 2.5 m reference is the FP64 HORK(16)
+  step at dt2 (dt2 omega_max = 1.8 on that grid, where the Taylor remainder of degree 16 is
+  below 1e-10), which also samples every dt2.
+* Second phase: the steps after t = 0.6 s use HORK(16) at dt2 for every one-step method
+  (their own time error at dt2 is below 1e-9 in the source band, so the trace difference is
+  that of the first phase), and leap-frog, a two-step scheme whose step cannot change
+  without a restart, runs at one step dt2 / k throughout.
+* Error measures on the phase-2 samples of the receiver trace: the relative L2 error
+  ("convergence"), and the mean |l(omega)| and |k(omega)| of Sec. 4.1's Fourier measure
+  (``analysis.trace_errors``: dispersion and dissipation).
+* Spatial floor: the smallest of each error over every method at dt2 (Sec. 4.1); the
+  threshold is 1.5 x that floor (Secs. 4.1-4.3); Delta-t_max is the largest first-phase step
+  0.6 s / n whose error is at or below the threshold.
+
+All arithmetic runs in the library's kernels (FP64); this module builds the models, sequences
+the calls and compares traces on the host.
+"""
+import time
+
+import numpy as np
+
+from .analysis import trace_errors
+from .ewave import EwaveError, Model
+
+C, DX, F_PEAK, T0 = 3000.0, 10.0, 15.0, 0.18
+LX, LY = 6000.0, 5000.0
+SRC, REC = (3000.0, 4990.0), (3000.0, 2500.0)
+T1, T_END = 0.6, 1.3
+
+
+def dt2_of(dx=DX):
+    """The uniform second-phase step dx / (8 c)."""
+    return dx / (8.0 * C)
+
+
+def build(dx, p=16):
+    nx, ny = int(round(LX / dx)) + 1, int(round(LY / dx)) + 1
+    md = Model(nx, ny, dx, 8, 0, 0.0, False, precision="f64", p=p, max_receivers=1)
+    md.set_velocity(np.full((ny, nx), C))
+    md.set_source_receivers(0, SRC[0], SRC[1], F_PEAK, T0, 1.0, np.array([REC]))
+    return md
+
+
+def _run(md, phases):
+    """phases: [(method, m, dt, nsteps), ...] from rest; returns the receiver trace (one sample
+    per step)."""
+    total = sum(n for _, _, _, n in phases)
+    md.bind_seismogram(total)
+    md.reset_state()
+    t = 0.0
+    for method, m, dt, n in phases:
+        md.ensure_workspace(method, m)
+        md.step(method, t, dt, m, n)
+        t += n * dt
+    md.sync()
+    return md.seismogram(0, 1, total)[:, 0]
+
+
+def reference_trace(dx_ref=DX / 4):
+    """FP64 HORK(16) at dt2 on the fine grid: samples at (s + 1) dt2."""
+    md = build(dx_ref)
+    dt2 = dt2_of()
+    n = int(round(T_END / dt2))
+    tr = _run(md, [("hork", 16, dt2, n)])
+    md.close()
+    return tr
+
+
+def candidate_trace(md, method, m, n1):
+    """The 10 m trace of (method, m) with the first phase at dt1 = 0.6 s / n1, sampled at the
+    phase-2 times; leap-frog: one step dt2 / k throughout (n1 = k)."""
+    dt2 = dt2_of()
+    n2 = int(round((T_END - T1) / dt2))
+    if method == "leapfrog":
+        k = n1
+        n = int(round(T_END / (dt2 / k)))
+        tr = _run(md, [("leapfrog", 1, dt2 / k, n)])
+        return tr[k - 1::k][-n2:]
+    dt1 = T1 / n1
+    tr = _run(md, [(method, m, dt1, n1), ("hork", 16, dt2, n2)])
+    return tr[n1:]
+
+
+def errors(tr, ref):
+    """(relative L2 error, dispersion, dissipation) of a phase-2 trace against the reference."""
+    if tr is None or not np.all(np.isfinite(tr)):
+        return float("inf"), float("inf"), float("inf")
+    r = ref[-len(tr):]
+    rel = float(np.linalg.norm(tr - r) / np.linalg.norm(r))
+    diss, disp = trace_errors(r, tr)
+    return rel, disp, diss
+
+
+PLAN = (("leapfrog", (1,)), ("rk44", (4,)), ("hork", (8, 16, 24)), ("faber", (10, 20, 40)),
+        ("krylov", (7, 8, 9, 10)))
+FLOOR_METHODS = (("hork", 16), ("faber", 20))
+# first-phase step candidates 0.6 s / n, largest step first (n = 1440: dt1 = dt2)
+N_STEPS = (24, 30, 40, 48, 60, 75, 90, 100, 120, 150, 180, 200, 240, 300, 360, 480, 600, 720,
+           900, 1200, 1440)
+LEAPFROG_K = (1, 2, 3, 4, 6, 8, 12, 16)
+
+
+def dt_max_search(evaluate, keys, threshold):
+    """Largest step (first key) whose error meets the threshold, by bisection on the
+    candidates ordered from the largest step down (the error grows with the step); None if
+    even the smallest fails.  ``evaluate`` caches its runs."""
+    if evaluate(keys[-1]) > threshold:
+        return None
+    lo, hi = -1, len(keys) - 1          # keys[hi] passes; keys[lo] (if any) fails
+    if evaluate(keys[0]) <= threshold:
+        return keys[0]
+    lo = 0
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        if evaluate(keys[mid]) <= threshold:
+            hi = mid
+        else:
+            lo = mid
+    return keys[hi]
+
+
+def run(plan=PLAN, log=print):
+    """The whole experiment.  Returns a dict with the spatial floors, thresholds and, for every
+    (method, m), Delta-t_max under each of the three measures and the MVOs per ms."""
+    t_start = time.perf_counter()
+    ref = reference_trace()
+    log(f"reference (2.5 m, FP64 HORK 16): {time.perf_counter() - t_start:.1f} s")
+    md = build(DX)
+    dt2 = dt2_of()
+    n_at_dt2 = int(round(T1 / dt2))
+    floor_runs = {mm: errors(candidate_trace(md, mm[0], mm[1], n_at_dt2), ref) for mm in FLOOR_METHODS}
+    floors = [min(e[q] for e in floor_runs.values()) for q in range(3)]
+    thresholds = [1.5 * f for f in floors]
+    log(f"floors (trace, dispersion, dissipation): {floors} ({time.perf_counter() - t_start:.1f} s)")
+    results = []
+    for method, ms in plan:
+        for m in ms:
+            cache = {}
+
+            def ev(key, q):
+                if key not in cache:
+                    try:
+                        tr = candidate_trace(md, method, m, key)
+                    except EwaveError:             # a step that blew up (non-finite state)
+                        tr = None
+                    cache[key] = errors(tr, ref)
+                return cache[key][q]
+
+            keys = list(LEAPFROG_K) if method == "leapfrog" else [n for n in N_STEPS if n <= n_at_dt2]
+            step = (lambda k: dt2 / k) if method == "leapfrog" else (lambda n: T1 / n)
+            best = []
+            for q in range(3):
+                key = dt_max_search(lambda k: ev(k, q), keys, thresholds[q])
+                best.append(None if key is None else step(key))
+            mvo = {"leapfrog": 1, "rk44": 4}.get(method, m)
+            results.append({"method": method, "m": m, "runs": len(cache),
+                            "dt_max_ms": [None if b is None else b * 1e3 for b in best],
+                            "mvo_per_ms": [None if b is None else mvo / (b * 1e3) for b in best]})
+            log(f"  {method} m={m}: dt_max (trace, disp, diss) = "
+                + ", ".join("-" if b is None else f"{b * 1e3:.3f} ms" for b in best)
+                + f" ({time.perf_counter() - t_start:.1f} s)")
+    md.close()
+    return {"setup": "homogeneous 6x5 km, c 3 km/s, 10 m grid vs 2.5 m FP64 reference, 15 Hz Ricker "
+                     "(t0 0.18 s) at (3, 4.99) km, receiver (3, 2.5) km, T 1.3 s; FP64",
+            "floors": {"trace_rel_l2": floors[0], "dispersion": floors[1], "dissipation": floors[2]},
+            "floor_runs": {f"{k[0]}{k[1]}": list(v) for k, v in floor_runs.items()},
+            "paper_floors": {"trace_rel_l2": 3.9e-6, "dispersion": 0.002, "dissipation": 2.4e-7},
+            "thresholds": thresholds, "results": results,
+            "seconds": time.perf_counter() - t_start}

@@ -171,6 +171,7 @@ class Study:
     refs: list = field(default_factory=list)       # FP64 reference seismograms (sampled problems)
     ref_workloads: list = field(default_factory=list)
     bf16: dict = field(default_factory=dict)   # method -> (m, dt, error) with bfloat16 storage
+    noise_problems: int = 0                    # problems (one shot per model) of the stability check
     seconds: float = 0.0
 
 
@@ -300,14 +301,17 @@ def run_study(workloads: List[Workload], picks, T, target=1e-4, plan=SCAN_PLAN,
         f"({time.time() - t_start:.1f} s)")
     t_quiet = T + 20.0 / workloads[0].f_peak + t0_for(workloads[0].f_peak)
 
+    noise = {}            # models and batch of the stability check (set below)
+
     def scan(models, batch, method, m, ks, to_dt, out):
         def ev(k):
             c = Candidate(method, m, to_dt(k))
             out.append(c)
             err = _eval_candidate(models, batch, refs, sw, c, T, dt_ref, log)
             if err <= target and method in POLYNOMIAL:
+                nm, nb = noise.get("models", models), noise.get("batch", batch)
                 try:
-                    c.growth = noise_growth(models, batch, method, m, c.dt, t_quiet)
+                    c.growth = noise_growth(nm, nb, method, m, c.dt, t_quiet)
                 except Exception as e:
                     c.growth = float("inf")
                     log(f"  {c.label()} noise test: {e}")
@@ -329,6 +333,16 @@ def run_study(workloads: List[Workload], picks, T, target=1e-4, plan=SCAN_PLAN,
     for md in cand_models:
         md.set_faber_ellipse(*ell)
     cand_batch = Batch(cand_models)
+    # the stability check runs on one shot of every model: the spectrum is the model's, and a
+    # setting that is stable on the sampled problems can still have growing modes on another
+    # model of the batch
+    noise_models = build_models(sampled_workloads(workloads, [(q, 0) for q in range(len(workloads))]),
+                                precision, p=p, c_max=c_max)
+    for md in noise_models:
+        md.set_faber_ellipse(*ell)
+    noise_batch = Batch(noise_models)
+    st.noise_problems = len(noise_models)
+    noise["models"], noise["batch"] = noise_models, noise_batch
     cands, best_k = [], {}
     for method, ms, ks in plan:
         for m in ms:
@@ -359,6 +373,9 @@ def run_study(workloads: List[Workload], picks, T, target=1e-4, plan=SCAN_PLAN,
         log(f"  bfloat16 storage, {probe.label()}: error {err:.3e} (FP32 {best.err:.3e})")
     cand_batch.close()
     for md in cand_models:
+        md.close()
+    noise_batch.close()
+    for md in noise_models:
         md.close()
     # step time of every (method, m) with a passing step, on the full workload; the step
     # time does not depend on dt, so it applies to every passing candidate of that pair

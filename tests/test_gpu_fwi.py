@@ -182,7 +182,8 @@ def test_checkpoint_stride_bit_exact():
 
 @pytest.mark.parametrize("budget", [None, 4])
 def test_krylov_gradient_matches_oracle_and_differences(budget):
-    """Krylov (m = 12, dt 1 ms): the linearised adjoint gradient on the GPU equals the oracle's
+    """Krylov (m = 12, dt 1 ms), the adjoint of the step's exponential (the library's
+    EWV_KRYLOV_ADJOINT_EXPONENTIAL option): the linearised adjoint gradient on the GPU equals the oracle's
     (FP64), with and without checkpoint segments, and agrees with central differences of the
     GPU Krylov misfit to the step's time accuracy (1e-3)."""
     import torch
@@ -194,6 +195,7 @@ def test_krylov_gradient_matches_oracle_and_differences(budget):
     om = OModel(NX, NY, DX, 8, PML, beta0, True, c0)
     J_o, g_o = fwi_gradient(om, _oshots(om), d_obs, dt, nsteps, m, ell, method="krylov")
     g = _gpu(c0, beta0, ell, "f64")
+    g.set_krylov_adjoint("exponential")
     fwi = FaberFWI(g, dt, m, nsteps, len(REC), budget=budget, method="krylov")
     d = torch.tensor(np.array(d_obs), dtype=torch.float64, device="cuda")
     seis = fwi.forward(c0 ** 2)
@@ -213,38 +215,44 @@ LF_DT, LF_NSTEPS = 1e-3, 30
 
 
 def test_leapfrog_adjoint_step_is_the_oracle_transpose():
-    """One leap-frog adjoint step on the GPU (FP64) against the transpose of the oracle's
-    assembled step matrix (oracle/leapfrog_adjoint.py) applied to a random cotangent of
-    (u, u_prev, w, w_prev), and the gradient increment s G(u^n, w^n) lambda_u."""
+    """One leap-frog adjoint step on the GPU (FP64, two shots) against the transpose of the
+    oracle's assembled step matrix (oracle/leapfrog_adjoint.py) applied to a random cotangent
+    of (u, u_prev, w, w_prev), and the gradient increment s G(u^n, w^n) lambda_u.  The
+    cotangent buffer holds 2 nshots vectors: level n of every shot, then w_prev of every shot."""
     import torch
     from oracle import leapfrog_adjoint as LA
     c_true, c0, beta0, ell = _setup()
     om = OModel(NX, NY, DX, 8, PML, beta0, True, c_true)
     g = _gpu(c_true, beta0, ell, "f64", sources=False)
+    ns, nv, fe = g.nshots, g.vector_elems, g.layout.field_elems
     nu = NX * NY
     nwx, nwy = NY * (NX - 1), (NY - 1) * NX
-    lam_u, lam_um, lam_wx, lam_wy, lam_wmx, lam_wmy = random_state(
-        [(nu,), (nu,), (nwx,), (nwy,), (nwx,), (nwy,)], 13)
-    u, wx, wy = smooth_random_state([(nu,), (nwx,), (nwy,)], 14)
-    nv = g.vector_elems
-    ck = g.new_vector()
-    g.pack(np.concatenate([u, np.zeros(nu), wx, wy]), ck)
-    adj = torch.zeros(2 * nv, dtype=torch.float64, device="cuda")
-    g.pack(np.concatenate([lam_u, lam_um, lam_wx, lam_wy]), adj[:nv])
-    g.pack(np.concatenate([np.zeros(2 * nu), lam_wmx, lam_wmy]), adj[nv:])
-    grad = torch.zeros(g.layout.field_elems, dtype=torch.float64, device="cuda")
+    A, s = LA.step_matrix(om, LF_DT)
+    ck = torch.zeros(ns * nv, dtype=torch.float64, device="cuda")
+    adj = torch.zeros(2 * ns * nv, dtype=torch.float64, device="cuda")
+    grad = torch.zeros(ns * fe, dtype=torch.float64, device="cuda")
+    lams, states = [], []
+    for k in range(ns):
+        lam = random_state([(nu,), (nu,), (nwx,), (nwy,), (nwx,), (nwy,)], 13 + k)
+        st = smooth_random_state([(nu,), (nwx,), (nwy,)], 14 + k)
+        g.pack(np.concatenate([st[0], np.zeros(nu), st[1], st[2]]), ck[k * nv:(k + 1) * nv])
+        g.pack(np.concatenate(lam[:4]), adj[k * nv:(k + 1) * nv])
+        g.pack(np.concatenate([np.zeros(2 * nu), lam[4], lam[5]]), adj[(ns + k) * nv:(ns + k + 1) * nv])
+        lams.append(lam)
+        states.append(st)
     g.adjoint_step(0.0, LF_DT, 0, ck, adj, grad, method="leapfrog")
     g.sync()
-    a0, a1 = g.unpack(adj[:nv]), g.unpack(adj[nv:])
-    got = np.concatenate([a0[:nu], a0[nu:2 * nu], a0[2 * nu:], a1[2 * nu:]])
-    A, s = LA.step_matrix(om, LF_DT)
-    lam = np.concatenate([lam_u, lam_um, lam_wx, lam_wy, lam_wmx, lam_wmy])
-    ref = A.T @ lam
-    assert rel_l2(got, ref) < 1e-12
-    G = LA._G(om, u.reshape(NY, NX), wx.reshape(NY, NX - 1), wy.reshape(NY - 1, NX)).ravel()
-    g_ref = (s * G * lam_u).reshape(NY, NX)
-    g_got = grad.view(NY, g.layout.pitch)[:, :NX].cpu().numpy()
-    assert rel_l2(g_got, g_ref) < 1e-12
+    for k in range(ns):
+        a0 = g.unpack(adj[k * nv:(k + 1) * nv])
+        a1 = g.unpack(adj[(ns + k) * nv:(ns + k + 1) * nv])
+        got = np.concatenate([a0[:nu], a0[nu:2 * nu], a0[2 * nu:], a1[2 * nu:]])
+        ref = A.T @ np.concatenate(lams[k])
+        assert rel_l2(got, ref) < 1e-12, k
+        u, wx, wy = states[k]
+        G = LA._G(om, u.reshape(NY, NX), wx.reshape(NY, NX - 1), wy.reshape(NY - 1, NX)).ravel()
+        g_ref = (s * G * lams[k][0]).reshape(NY, NX)
+        g_got = grad[k * fe:(k + 1) * fe].view(NY, g.layout.pitch)[:, :NX].cpu().numpy()
+        assert rel_l2(g_got, g_ref) < 1e-12, k
 
 
 def _lf_shots(om):
@@ -293,9 +301,78 @@ def test_leapfrog_adjoint_rejects_the_literal_variant():
     c_true, c0, beta0, ell = _setup()
     g = _gpu(c_true, beta0, ell, "f64", sources=False)
     g.set_leapfrog_variant(LEAPFROG_LITERAL)
-    nv = g.vector_elems
-    ck = g.new_vector()
-    adj = torch.zeros(2 * nv, dtype=torch.float64, device="cuda")
-    grad = torch.zeros(g.layout.field_elems, dtype=torch.float64, device="cuda")
+    ns, nv = g.nshots, g.vector_elems
+    ck = torch.zeros(ns * nv, dtype=torch.float64, device="cuda")
+    adj = torch.zeros(2 * ns * nv, dtype=torch.float64, device="cuda")
+    grad = torch.zeros(ns * g.layout.field_elems, dtype=torch.float64, device="cuda")
     with pytest.raises(EwaveError, match="UNSUPPORTED"):
         g.adjoint_step(0.0, LF_DT, 0, ck, adj, grad, method="leapfrog")
+
+
+# ---------------------------------------------------------------- exact Krylov adjoint
+@pytest.mark.parametrize("mm,window,at_rest", [(1, 0, False), (6, 0, False), (12, 0, False),
+                                               (12, 3, False), (20, 0, True)])
+def test_krylov_exact_adjoint_step_matches_oracle(mm, window, at_rest):
+    """One exact Krylov adjoint step on the GPU (FP64, two shots with their sources) against the
+    oracle's reverse mode through the same step (oracle/krylov_adjoint.py): the cotangent of
+    U^{n-1} and the gradient increment, 1e-10.  Covers m = 1, full and windowed Gram-Schmidt,
+    and a step from rest (U = 0: eta fixed at 1, the basis breaks down after the tail's
+    dimension, so the reverse sweep starts at m_eff < m)."""
+    import torch
+    from oracle.krylov_adjoint import krylov_exact_adjoint_step
+    c_true, c0, beta0, ell = _setup()
+    om = OModel(NX, NY, DX, 8, PML, beta0, True, c0)
+    g = _gpu(c0, beta0, ell, "f64")
+    g.set_krylov_window(window)
+    dt, t = 1.5e-3, 0.03
+    nv, fe = g.vector_elems, g.layout.field_elems
+    Us = [np.zeros(om.n) if at_rest else flatten(smooth_random_state([f.shape for f in om.zeros_state()], 30 + k))
+          for k in range(2)]
+    ybars = [random_state([(om.n,)], 40 + k)[0] for k in range(2)]
+    ck = torch.zeros(2 * nv, dtype=torch.float64, device="cuda")
+    lam = torch.zeros(2 * nv, dtype=torch.float64, device="cuda")
+    for k in range(2):
+        g.pack(Us[k], ck[k * nv:(k + 1) * nv])
+        g.pack(ybars[k], lam[k * nv:(k + 1) * nv])
+    grad = torch.zeros(2 * fe, dtype=torch.float64, device="cuda")
+    g.adjoint_step(t, dt, mm, ck, lam, grad, method="krylov")
+    g.sync()
+    for k, (src, _) in enumerate(_oshots(om)):
+        Ub, gr = krylov_exact_adjoint_step(om, Us[k], ybars[k], src, t, dt, mm,
+                                           window=window or None)
+        assert rel_l2(g.unpack(lam[k * nv:(k + 1) * nv]), Ub) < 1e-10, k
+        g_got = grad[k * fe:(k + 1) * fe].view(NY, g.layout.pitch)[:, :NX].cpu().numpy()
+        assert rel_l2(g_got, gr.reshape(NY, NX)) < 1e-10, k
+    g.close()
+
+
+@pytest.mark.parametrize("budget", [None, 4])
+def test_krylov_exact_gradient_at_the_benchmark_setting(budget):
+    """The FWI gradient through Krylov steps of dimension 20 at 8 x the leap-frog step (the
+    setting bench.py times), FP64: the GPU's exact discrete adjoint equals the oracle's
+    (1e-10), checkpoint segments reproduce full storage, and central differences of the GPU
+    misfit agree to 1e-3 -- the gradient of the misfit of the computed Krylov steps."""
+    import torch
+    from oracle.krylov_adjoint import krylov_exact_fwi_gradient
+    from paper_2401_16322_gb300.fwi import FaberFWI
+    from paper_2401_16322_gb300.tts import leapfrog_step
+    c_true, c0, beta0, ell = _setup()
+    mm, nsteps = 20, 8
+    dt = 8.0 * leapfrog_step(3000.0, DX)
+    om_t = OModel(NX, NY, DX, 8, PML, beta0, True, c_true)
+    d_obs = faber_forward(om_t, _oshots(om_t), dt, nsteps, mm, ell, method="krylov")[1]
+    om = OModel(NX, NY, DX, 8, PML, beta0, True, c0)
+    J_o, g_o = krylov_exact_fwi_gradient(om, _oshots(om), d_obs, dt, nsteps, mm)
+    g = _gpu(c0, beta0, ell, "f64")
+    fwi = FaberFWI(g, dt, mm, nsteps, len(REC), budget=budget, method="krylov")
+    d = torch.tensor(np.array(d_obs), dtype=torch.float64, device="cuda")
+    seis = fwi.forward(c0 ** 2)
+    assert abs(0.5 * float(((seis - d) ** 2).sum()) - J_o) <= 1e-9 * J_o
+    grad = fwi.backward(seis - d).double().cpu().numpy()
+    assert rel_l2(grad, g_o) < 1e-10
+    dm = smooth_random_state([(NY, NX)], 9, sigma_cells=2.0)[0] * 0.01 * c0 ** 2
+    eps = 1e-4
+    Jp = 0.5 * float(((fwi.forward(c0 ** 2 + eps * dm) - d) ** 2).sum())
+    Jm = 0.5 * float(((fwi.forward(c0 ** 2 - eps * dm) - d) ** 2).sum())
+    fd = (Jp - Jm) / (2 * eps)
+    assert abs(fd - float(np.sum(grad * dm))) <= 1e-3 * abs(fd)

@@ -100,3 +100,24 @@ def test_candidate_names_map_to_library_methods_and_options(name, base, window, 
     assert base_method(mds, name) == base
     for md in mds:
         assert (md.window, md.form, md.lf) == (window, form, lf)
+
+
+def test_single_signal_bisection_finds_the_largest_passing_step():
+    """The single-signal experiment's Delta-t_max search (bisection over candidates ordered
+    from the largest step down) agrees with a linear scan whenever the error grows with the
+    step, and evaluates far fewer candidates."""
+    from paper_2401_16322_gb300.single_signal import dt_max_search
+    rng = np.random.default_rng(5)
+    for _ in range(200):
+        n = int(rng.integers(1, 25))
+        errs = np.sort(rng.uniform(0, 1, n))[::-1]            # largest step (first) worst
+        thr = float(rng.uniform(0, 1))
+        calls = []
+
+        def ev(i):
+            calls.append(i)
+            return errs[i]
+        got = dt_max_search(ev, list(range(n)), thr)
+        passing = [i for i in range(n) if errs[i] <= thr]
+        assert got == (passing[0] if passing else None)
+        assert len(set(calls)) <= 2 + int(np.ceil(np.log2(n + 1)))
