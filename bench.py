@@ -73,7 +73,7 @@ def parse(argv=None):
     ap.add_argument("--check3d", type=int, default=0,
                     help="edge of the 3D accuracy cube of a Delta-t_max search (0: time the "
                          "settings found by that search on a 96^3 cube, and check their error "
-                         "on a 64^3 cube)")
+                         "on a 64^3 cube; -1: time them without the check, for profiling)")
     ap.add_argument("--detail-out", default=None, metavar="PATH",
                     help="also write every side run in full to this JSON file")
     ap.add_argument("--cpu-procs", type=int, default=0,
@@ -319,8 +319,8 @@ def fp64_single_shot_estimate(wl, method, m, dt, nsteps, c_max, steps_sample=3):
 
 def fwi_gradient_step(method, m, dt_over_cfl):
     """FWI gradient (forward + adjoint) on the 401 x 201, 16-shot, 200-receiver workload,
-    FP32, with the given integrator (Faber, HORK: exact discrete adjoints; Krylov: adjoint of
-    the step's exponential) at its m and step ratio; every state checkpointed."""
+    FP32, with the given integrator (exact discrete adjoints of the computed steps, Krylov
+    included) at its m and step ratio; every state checkpointed."""
     import numpy as np
     import torch
     from paper_2401_16322_gb300.fwi import FaberFWI
@@ -351,6 +351,8 @@ def fwi_gradient_step(method, m, dt_over_cfl):
     md.close()
     return {"seconds": e0.elapsed_time(e1) * 1e-3, "forward_s": e0.elapsed_time(em) * 1e-3,
             "backward_s": em.elapsed_time(e1) * 1e-3, "method": method, "nsteps": nsteps,
+            "adjoint": ("exact discrete adjoint of the computed Krylov steps (reverse mode through "
+                        "Arnoldi)" if method == "krylov" else "exact discrete adjoint"),
             "dt_ms": dt * 1e3, "m": m,
             "shots": len(w.shots), "grid": f"{w.nx}x{w.ny}", "checkpoint_bytes": mem,
             "gradient_finite": ok}
@@ -408,10 +410,11 @@ def config5_3d(n=400, check_n=0, target=TARGET):
            "pml": "auxiliary-field PML (psi_t = u), exact reduction to Eq. 1"}
     found = []          # (method, m, k, err); k < 1: leap-frog divisor 1/k
     t_search = time.perf_counter()
-    wc = config_3d(check_n if check_n > 0 else 64, pml=min(20, (check_n or 64) // 4), T=0.5)
+    n_check = check_n if check_n > 0 else 64
+    wc = config_3d(n_check, pml=min(20, n_check // 4), T=0.5)
     dt3 = leapfrog_step(c_max, wc.dx, dims=3)
-    ref_md = build(wc, "f64", p=20)
-    ref = simulate(ref_md, "faber", 30, dt3, wc.T)
+    ref_md = build(wc, "f64", p=20) if check_n >= 0 else None
+    ref = simulate(ref_md, "faber", 30, dt3, wc.T) if ref_md is not None else None
     log(f"3D reference {time.perf_counter() - t_search:.1f} s")
     cmd = build(wc, "f32")
 
@@ -434,7 +437,11 @@ def config5_3d(n=400, check_n=0, target=TARGET):
             log(f"3D {method} m={m} dt={dt * 1e3:.3f} ms: {e}")
             return float("inf")
 
-    if check_n > 0:
+    if check_n < 0:
+        # profiling runs: time the settings of FIXED3D without the check cube
+        found.extend((method, m, float(k), float("nan")) for method, m, k in FIXED3D)
+        out["error_check"] = None
+    elif check_n > 0:
         for method, ms, ks in SCAN3D:
             for m in ms:
                 errs = {}
@@ -462,7 +469,8 @@ def config5_3d(n=400, check_n=0, target=TARGET):
             else:
                 log(f"3D {method} m={m} at {k} x: error {err:.3e} above the target")
         out["error_check"] = "64^3 cube, T 0.5 s, FP64 Faber 30 at the 3D leap-frog step"
-    ref_md.close()
+    if ref_md is not None:
+        ref_md.close()
     cbatch.close()
     cmd.close()
     out["search_s"] = time.perf_counter() - t_search

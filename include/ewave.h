@@ -87,6 +87,7 @@ extern "C" {
 #define EWV_METHOD_ADJOINT_FABER 7 /* discrete adjoint of the Faber step (workspace query) */
 #define EWV_METHOD_ADJOINT_KRYLOV 8 /* linearised adjoint of the Krylov step (workspace query) */
 #define EWV_METHOD_ADJOINT_LEAPFROG 9 /* discrete adjoint of the leap-frog step (workspace query) */
+#define EWV_METHOD_KRYLOV_ADAPTIVE 10 /* adaptive Krylov step (workspace query, m = m_max)      */
 
 #define EWV_LEAPFROG_AVERAGED 0 /* time-averaged PML damping of w (stable reading)       */
 #define EWV_LEAPFROG_LITERAL 1  /* explicit -beta w^n damping, as the formula reads      */
@@ -239,6 +240,28 @@ int ewv_step_faber(ewv_model_t model, double t, double dt, int degree, int nstep
  * enqueueing, like the other step calls. */
 int ewv_step_krylov(ewv_model_t model, double t, double dt, int m, int nsteps, int* info);
 
+/* Adaptive Krylov step (KIOPS-style; the paper names adaptive dimensions and substeps as the
+ * improvement it leaves out, Secs. 3.2 and 6): advance every shot by nsteps steps of dt of
+ * U^{n+1} = [I 0] exp(dt H~) [U^n; eta e_p] (the balanced start vector of ewv_step_krylov),
+ * each step in substeps tau of the normalised step.  A substep grows its Arnoldi basis one
+ * vector at a time from m_min to m_max and stops at the first dimension j whose estimate
+ *   beta h_{j+1,j} (tau |[phi_1(tau H_j)]_{j,1}| + tau^2 |[phi_2(tau H_j)]_{j,1}| |A v_{j+1}|)
+ * (the first two terms of Saad's error series; A v_{j+1} is the next column's product,
+ * reused when the basis grows) is at most tol tau beta, beta the norm of the substep's
+ * augmented start vector.  At m_max the substep shrinks tau on the same basis (no new
+ * products); after a substep tau grows by at most 2x; a happy breakdown takes the rest of
+ * the step at once.  phi_1, phi_2 and exp come from one exponential of the twice-bordered
+ * Hessenberg matrix, in FP64 on the host, which reads the Krylov scalars after every basis
+ * vector: the call waits for the GPU once per vector and launches directly (no graphs).
+ * Every shot has its own dimensions and substeps.  The orthogonalisation window of
+ * ewv_set_krylov_window applies.  stats (may be NULL) receives {substeps, matrix-vector
+ * products, largest dimension} summed over shots and steps.  Workspace:
+ * ewv_workspace_bytes(EWV_METHOD_KRYLOV_ADAPTIVE, m_max) (m_max + 1 vectors).  Errors:
+ * INVALID_ARG (tol <= 0, 1 <= m_min <= m_max <= EWV_MAX_KRYLOV_M - 1 violated), NONFINITE
+ * (also when a substep cannot meet tol at m_max after 60 shrinks). */
+int ewv_step_krylov_adaptive(ewv_model_t model, double t, double dt, double tol, int m_min,
+                             int m_max, int nsteps, int* stats);
+
 /* Incomplete orthogonalisation for the Krylov step (the library's option; the paper names
  * incomplete or non-orthonormal bases as the way to cut the Arnoldi cost, Secs. 3.2 and 6):
  * with window q > 0 each new vector is orthogonalised, in modified Gram-Schmidt order, only
@@ -342,6 +365,8 @@ int ewv_batch_step_krylov(ewv_batch_t batch, double t, double dt, int m, int nst
                           int* info);
 int ewv_batch_step_rk(ewv_batch_t batch, double t, double dt, int scheme, int stages,
                       int nsteps);
+int ewv_batch_step_krylov_adaptive(ewv_batch_t batch, double t, double dt, double tol, int m_min,
+                                   int m_max, int nsteps, int* stats);
 int ewv_batch_step_leapfrog(ewv_batch_t batch, double t, double dt, int nsteps);
 
 /* ---- allocation-free Faber step ------------------------------------------------------ */

@@ -209,6 +209,10 @@ struct Engine {
     size_t d_kadj_bytes = 0;
     double* d_kbar = nullptr;     // exact Krylov adjoint: per-shot reverse-sweep scalars
     size_t d_kbar_n = 0;
+    // adaptive Krylov step: tolerance, dimension range and statistics of the current call
+    double ad_tol = 0.0;
+    int ad_mmin = 1, ad_mmax = 1;
+    int ad_stats[3] = {0, 0, 0};
     int* d_err = nullptr;       // error word: 1 = a TMA pipeline wait timed out, 2 = non-finite
     int* h_err = nullptr;       // pinned host copy, written by an async copy at the end of a call
     cudaEvent_t err_ev = nullptr;   // recorded after that copy
@@ -358,6 +362,7 @@ int vectors_needed(int method, int m) {
         case EWV_METHOD_ADJOINT_FABER: return m + 3;   // tape p_0..p_{m-1} + 3 cotangents
         case EWV_METHOD_ADJOINT_KRYLOV: return 2 * m + 9;  // two bases + 8 dense outputs
         case EWV_METHOD_ADJOINT_LEAPFROG: return 3;        // level-n tape, q, H^T q
+        case EWV_METHOD_KRYLOV_ADAPTIVE: return m + 1;     // m = m_max: slots up to m_max + 2
         default: return -1;
     }
 }
@@ -651,7 +656,7 @@ struct Ctx {
         ++*launches;
     }
     void point(const PointArgs& pa) {
-        if (pa.mode <= 2 || pa.mode == 5)   // norm, MGS pass, combine, dot: flat over the padded vectors
+        if (pa.mode <= 2 || pa.mode == 5 || pa.mode == 7)   // norm, MGS, combine, dots: flat
             launch_point_flat(E->precision, E->nchunks, E->d_probs, E->d_pbase, E->nprob, pa, s);
         else
             launch_point(E->precision, E->ntiles, E->d_probs, E->d_tile_prob, pa, s);
@@ -1133,6 +1138,314 @@ int run_krylov(Ctx& C, double t, double dt, int m, int nsteps, int* info) {
     return EWV_OK;
 }
 
+// exp(A) of a dense n x n matrix (row-major) by the [13/13] Pade approximant with scaling and
+// squaring (Higham 2005), in FP64 on the host: the small dense part of the reverse sweep.
+std::vector<double> host_expm(const std::vector<double>& A0, int n) {
+    auto mul = [n](const std::vector<double>& X, const std::vector<double>& Y) {
+        std::vector<double> Z((size_t)n * n, 0.0);
+        for (int r = 0; r < n; ++r)
+            for (int k = 0; k < n; ++k) {
+                const double x = X[(size_t)r * n + k];
+                if (x == 0.0) continue;
+                for (int c = 0; c < n; ++c) Z[(size_t)r * n + c] += x * Y[(size_t)k * n + c];
+            }
+        return Z;
+    };
+    double f[27];
+    f[0] = 1.0;
+    for (int i = 1; i <= 26; ++i) f[i] = f[i - 1] * i;
+    double b[14];
+    for (int k = 0; k <= 13; ++k) b[k] = f[26 - k] * f[13] / (f[26] * f[k] * f[13 - k]);
+    double nrm = 0.0;
+    for (int c = 0; c < n; ++c) {
+        double cs = 0.0;
+        for (int r = 0; r < n; ++r) cs += std::fabs(A0[(size_t)r * n + c]);
+        nrm = std::max(nrm, cs);
+    }
+    const double theta13 = 5.371920351148152;
+    const int sc = nrm > theta13 ? (int)std::ceil(std::log2(nrm / theta13)) : 0;
+    std::vector<double> A(A0);
+    const double fac = std::ldexp(1.0, -sc);
+    for (double& v : A) v *= fac;
+    const std::vector<double> A2 = mul(A, A), A4 = mul(A2, A2), A6 = mul(A4, A2);
+    const size_t nn = (size_t)n * n;
+    std::vector<double> T1(nn), T2(nn);
+    for (size_t e = 0; e < nn; ++e) T1[e] = b[13] * A6[e] + b[11] * A4[e] + b[9] * A2[e];
+    std::vector<double> U = mul(A6, T1);
+    for (size_t e = 0; e < nn; ++e) U[e] += b[7] * A6[e] + b[5] * A4[e] + b[3] * A2[e];
+    for (int r = 0; r < n; ++r) U[(size_t)r * n + r] += b[1];
+    U = mul(A, U);
+    for (size_t e = 0; e < nn; ++e) T2[e] = b[12] * A6[e] + b[10] * A4[e] + b[8] * A2[e];
+    std::vector<double> V = mul(A6, T2);
+    for (size_t e = 0; e < nn; ++e) V[e] += b[6] * A6[e] + b[4] * A4[e] + b[2] * A2[e];
+    for (int r = 0; r < n; ++r) V[(size_t)r * n + r] += b[0];
+    // solve (V - U) X = (V + U) by Gaussian elimination with partial pivoting
+    std::vector<double> L(nn), X(nn);
+    for (size_t e = 0; e < nn; ++e) {
+        L[e] = V[e] - U[e];
+        X[e] = V[e] + U[e];
+    }
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (std::fabs(L[(size_t)r * n + c]) > std::fabs(L[(size_t)piv * n + c])) piv = r;
+        if (piv != c)
+            for (int k = 0; k < n; ++k) {
+                std::swap(L[(size_t)c * n + k], L[(size_t)piv * n + k]);
+                std::swap(X[(size_t)c * n + k], X[(size_t)piv * n + k]);
+            }
+        const double d = L[(size_t)c * n + c];
+        for (int r = c + 1; r < n; ++r) {
+            const double fct = L[(size_t)r * n + c] / d;
+            if (fct == 0.0) continue;
+            for (int k = c; k < n; ++k) L[(size_t)r * n + k] -= fct * L[(size_t)c * n + k];
+            for (int k = 0; k < n; ++k) X[(size_t)r * n + k] -= fct * X[(size_t)c * n + k];
+        }
+    }
+    for (int c = n - 1; c >= 0; --c) {
+        const double d = L[(size_t)c * n + c];
+        for (int k = 0; k < n; ++k) {
+            double v = X[(size_t)c * n + k];
+            for (int q = c + 1; q < n; ++q) v -= L[(size_t)c * n + q] * X[(size_t)q * n + k];
+            X[(size_t)c * n + k] = v / d;
+        }
+    }
+    for (int i = 0; i < sc; ++i) X = mul(X, X);
+    return X;
+}
+
+
+// (exp(tau H) e_1, tau phi_1(tau H) e_1, tau^2 phi_2(tau H) e_1) for the j x j Hessenberg H
+// (row-major, stride MAX_M in kry) from one exponential of the twice-bordered matrix
+// [[tau H, tau e_1, 0], [0, 0, tau], [0, 0, 0]].
+void phi_block(const double* kry, int j, double tau, std::vector<double>& e, double& ph1_last,
+               double& ph2_last) {
+    const int n = j + 2;
+    std::vector<double> B((size_t)n * n, 0.0);
+    for (int r = 0; r < j; ++r)
+        for (int c = 0; c < j; ++c) B[(size_t)r * n + c] = tau * kry[KRY_H + r * MAX_M + c];
+    B[(size_t)0 * n + j] = tau;
+    B[(size_t)j * n + j + 1] = tau;
+    const std::vector<double> E = host_expm(B, n);
+    e.assign(j, 0.0);
+    for (int r = 0; r < j; ++r) e[r] = E[(size_t)r * n];
+    ph1_last = E[(size_t)(j - 1) * n + j];
+    ph2_last = E[(size_t)(j - 1) * n + j + 1];
+}
+
+// Adaptive Krylov step (KIOPS-style dimension and substep control; the paper names it as the
+// improvement it leaves out, Secs. 3.2 and 6).  On the augmented A = dt H~_eta each substep
+// grows the basis one vector at a time from m_min to m_max and stops at the first j whose
+// two-term estimate beta h_{j+1,j} (tau |[phi_1(tau H_j)]_{j,1}| + tau^2 |[phi_2(tau H_j)]_{j,1}|
+// |A v_{j+1}|) is at most tol tau beta; A v_{j+1} is the next column's matrix-vector product,
+// computed once and reused.  At m_max without success tau shrinks on the same basis; after
+// a substep tau grows by at most 2x.  A happy breakdown takes the rest of the step at once.
+// Every problem has its own dimensions and substeps: the host reads the Krylov scalars after
+// each column, decides, and marks finished problems inactive (KRY_ACTIVE, KRY_SKIP).
+int run_krylov_adaptive(Ctx& C, double t, double dt, double tol, int mmin, int mmax, int nsteps,
+                        int* stats) {
+    std::string& err = *C.err;
+    Engine* E = C.E;
+    if (mmin < 1 || mmax < mmin || mmax + 1 > MAX_M || !(tol > 0.0))
+        return fail(err, EWV_ERR_INVALID_ARG, "adaptive Krylov: need 1 <= m_min <= m_max <= %d, tol > 0", MAX_M - 1);
+    const int np = E->nprob;
+    const double btol = E->precision == EWV_F64 ? 1e-14 : 1e-6;
+    const int window = E->models.empty() ? 0 : E->models[0]->kry_window;
+    std::vector<std::vector<double>> kb((size_t)np, std::vector<double>(KRY_STRIDE));
+    auto read_all = [&]() -> int {
+        for (int p = 0; p < np; ++p)
+            CUDA_OR_FAIL(err, cudaMemcpyAsync(kb[p].data(), E->probs[p].kry, sizeof(double) * KRY_STRIDE,
+                                              cudaMemcpyDeviceToHost, C.s));
+        CUDA_OR_FAIL(err, cudaStreamSynchronize(C.s));
+        for (int p = 0; p < np; ++p)
+            if (kb[p][KRY_NONFINITE] != 0.0)
+                return fail(err, EWV_ERR_NONFINITE, "non-finite value in the Arnoldi process");
+        return EWV_OK;
+    };
+    auto write = [&](int p) -> int {
+        CUDA_OR_FAIL(err, cudaMemcpyAsync(E->probs[p].kry, kb[p].data(), sizeof(double) * KRY_STRIDE,
+                                          cudaMemcpyHostToDevice, C.s));
+        return EWV_OK;
+    };
+    auto flat = [&](int mode, int j, int k, int notail) {
+        PointArgs pa{};
+        pa.mode = mode;
+        pa.j = j;
+        pa.k = k;
+        pa.m = mmax + 1;           // every column, m_max included, computes h_{j+1,j}
+        pa.tol = btol;
+        pa.notail = notail;
+        pa.partials = E->d_partials;
+        pa.counters = E->d_counters;
+        C.point(pa);
+    };
+    auto matvec = [&](int j) {     // slot j+1 = dt H~ v_j (no fused dot)
+        StageArgs a = stage_defaults();
+        a.x = j - 1;
+        a.y_out = j;
+        a.src_slot = j;
+        a.x_scale_slot = KRY_S + j;
+        a.ch = dt;
+        a.ck = 1.0;
+        C.stage(a);
+    };
+    long long tot_sub = 0, tot_mv = 0;
+    int max_dim = 0;
+    std::vector<double> s(np), tau(np), e;
+    std::vector<int> done(np), acc_j(np);
+    for (int n = 0; n < nsteps; ++n) {
+        launch_set_clock(E->d_probs, np, t + n * dt, dt, C.s);
+        ++*C.launches;
+        C.prologue(PRO_KRYLOV, mmax + 1);
+        std::fill(s.begin(), s.end(), 0.0);
+        std::fill(tau.begin(), tau.end(), 1.0);
+        std::fill(done.begin(), done.end(), 0);
+        for (int sub = 0;; ++sub) {
+            // start vector: [U; eta e_p] on the first substep, [U; y] on later ones
+            flat(0, 0, 0, sub == 0 ? 0 : 2);
+            int rc = read_all();
+            if (rc != EWV_OK) return rc;
+            std::vector<int> grow(np, 0), accepted(np, 0);
+            std::vector<double> acc_err(np, 0.0), anext(np, 0.0);
+            int ngrow = 0;
+            for (int p = 0; p < np; ++p) {
+                if (done[p]) continue;
+                tau[p] = std::min(tau[p], 1.0 - s[p]);
+                if (kb[p][KRY_ACTIVE] == 0.0) {     // a zero start vector stays zero
+                    s[p] = 1.0;
+                    done[p] = 1;
+                    continue;
+                }
+                grow[p] = 1;
+                ++ngrow;
+            }
+            if (ngrow == 0) break;
+            bool have_next = false;
+            for (int j = 1; j <= mmax && ngrow > 0; ++j) {
+                const int k0 = window > 0 ? std::max(1, j - window + 1) : 1;
+                if (!have_next) {
+                    matvec(j);
+                    ++tot_mv;
+                }
+                flat(5, j, k0, 0);                 // <q_{j+1}, q_k0> -> tail_{j+1}, h_{k0,j}
+                for (int k = k0; k <= j; ++k) flat(1, j, k, 0);
+                have_next = false;
+                if (j >= mmin && j < mmax + 1) {
+                    matvec(j + 1);                 // A v_{j+1}: the estimate, reused by column j+1
+                    flat(7, j + 1, 0, 0);          // |q_{j+2}|^2 -> KRY_AN
+                    ++tot_mv;
+                    have_next = true;
+                }
+                rc = read_all();
+                if (rc != EWV_OK) return rc;
+                for (int p = 0; p < np; ++p) {
+                    if (!grow[p]) continue;
+                    std::vector<double>& k = kb[p];
+                    const double beta = k[KRY_BETA];
+                    const double h = k[KRY_H + j * MAX_M + (j - 1)];
+                    double ph1, ph2;
+                    bool take = false;
+                    if (!(h > btol)) {             // happy breakdown: the rest of the step at once
+                        tau[p] = 1.0 - s[p];
+                        phi_block(k.data(), j, tau[p], e, ph1, ph2);
+                        acc_err[p] = 0.0;
+                        take = true;
+                    } else if (j >= mmin) {
+                        // |A v_{j+1}|: grid part from the pass, tail J (s_{j+1} tail_{j+1}) here
+                        const double sn = k[KRY_S + j + 1];
+                        const double* tn = k.data() + KRY_T + j * MAX_P;
+                        const int pp = E->probs[p].p;
+                        double tt = 0.0;
+                        for (int q = 0; q + 1 < pp; ++q) tt += (sn * tn[q + 1]) * (sn * tn[q + 1]);
+                        anext[p] = std::sqrt(k[KRY_AN] + tt);
+                        phi_block(k.data(), j, tau[p], e, ph1, ph2);
+                        double er = beta * h * (std::fabs(ph1) + std::fabs(ph2) * anext[p]);
+                        if (er <= tol * tau[p] * beta) {
+                            acc_err[p] = er;
+                            take = true;
+                        } else if (j == mmax) {
+                            for (int it = 0; it < 60 && !take; ++it) {
+                                tau[p] *= std::max(0.2, 0.9 * std::pow(tol * tau[p] * beta / er, 1.0 / mmax));
+                                phi_block(k.data(), j, tau[p], e, ph1, ph2);
+                                er = beta * h * (std::fabs(ph1) + std::fabs(ph2) * anext[p]);
+                                if (er <= tol * tau[p] * beta) {
+                                    acc_err[p] = er;
+                                    take = true;
+                                }
+                            }
+                            if (!take)
+                                return fail(err, EWV_ERR_NONFINITE, "adaptive Krylov: a substep did not meet the tolerance");
+                        }
+                    }
+                    if (take) {
+                        for (int r = 0; r < j; ++r) k[KRY_E + r] = e[r];
+                        k[KRY_MEFF] = (double)j;
+                        k[KRY_ACTIVE] = 0.0;
+                        acc_j[p] = j;
+                        accepted[p] = 1;
+                        grow[p] = 0;
+                        --ngrow;
+                        rc = write(p);
+                        if (rc != EWV_OK) return rc;
+                    }
+                }
+            }
+            // U <- beta V_j e on the grid (combine), the tail y <- beta sum_k e_k s_k tail_k here
+            for (int p = 0; p < np; ++p)
+                if (!accepted[p]) {
+                    kb[p][KRY_SKIP] = 1.0;
+                    int rc2 = write(p);
+                    if (rc2 != EWV_OK) return rc2;
+                }
+            PointArgs pc{};
+            pc.mode = 2;
+            pc.m = mmax;
+            C.point(pc);
+            for (int p = 0; p < np; ++p) {
+                std::vector<double>& k = kb[p];
+                if (!accepted[p]) continue;
+                const int j = acc_j[p], pp = E->probs[p].p;
+                std::vector<double> y(MAX_P, 0.0);
+                for (int kk = 1; kk <= j; ++kk)
+                    for (int q = 0; q < pp; ++q)
+                        y[q] += k[KRY_BETA] * k[KRY_E + kk - 1] * k[KRY_S + kk] * k[KRY_T + (kk - 1) * MAX_P + q];
+                for (int q = 0; q < MAX_P; ++q) k[KRY_T + q] = y[q];
+                s[p] += tau[p];
+                const double er = acc_err[p];
+                tau[p] *= er == 0.0 ? 2.0 : std::min(2.0, 0.9 * std::pow(tol * tau[p] * k[KRY_BETA] / er, 1.0 / j));
+                max_dim = std::max(max_dim, j);
+                ++tot_sub;
+                if (s[p] >= 1.0) done[p] = 1;
+                k[KRY_SKIP] = done[p] ? 1.0 : 0.0;
+                int rc2 = write(p);
+                if (rc2 != EWV_OK) return rc2;
+            }
+            for (int p = 0; p < np; ++p)
+                if (!accepted[p] && !done[p]) {     // not reached here: every growing problem accepts
+                    kb[p][KRY_SKIP] = 0.0;
+                    int rc2 = write(p);
+                    if (rc2 != EWV_OK) return rc2;
+                }
+            bool all = true;
+            for (int p = 0; p < np; ++p) all = all && done[p];
+            if (all) break;
+        }
+        C.record();
+    }
+    // leave no problem marked for the regular steps
+    for (int p = 0; p < np; ++p) {
+        kb[p][KRY_SKIP] = 0.0;
+        int rc = write(p);
+        if (rc != EWV_OK) return rc;
+    }
+    if (stats) {
+        stats[0] = (int)tot_sub;
+        stats[1] = (int)tot_mv;
+        stats[2] = max_dim;
+    }
+    return check_launch(err);
+}
+
 int run_leapfrog(Ctx& C, std::vector<ewv_model*>& models, double t, double dt, int nsteps, int variant) {
     bool need_init = false;
     for (ewv_model* m : models) need_init = need_init || !m->lf_history_valid;
@@ -1302,6 +1615,9 @@ int dispatch_method(Ctx& C, std::vector<ewv_model*>& models, int method, double 
             return run_faber(C, t, dt, mm, nsteps, g, c0, c1);
         }
         case EWV_METHOD_KRYLOV: return run_krylov(C, t, dt, mm, nsteps, info);
+        case EWV_METHOD_KRYLOV_ADAPTIVE:
+            return run_krylov_adaptive(C, t, dt, C.E->ad_tol, C.E->ad_mmin, C.E->ad_mmax, nsteps,
+                                       C.E->ad_stats);
         case EWV_METHOD_HORK: return run_hork(C, t, dt, mm, nsteps);
         case EWV_METHOD_RK32:
         case EWV_METHOD_RK44: return run_rk(C, t, dt, method, nsteps);
@@ -1717,6 +2033,30 @@ int ewv_step_faber(ewv_model_t m, double t, double dt, int degree, int nsteps) {
 int ewv_step_krylov(ewv_model_t m, double t, double dt, int mm, int nsteps, int* info) {
     return step_model(m, EWV_METHOD_KRYLOV, t, dt, mm, nsteps, info);
 }
+static int adaptive_call(std::vector<ewv_model*>& models, Engine* E, cudaStream_t s, long long* launches,
+                         std::string& err, double t, double dt, double tol, int mmin, int mmax, int nsteps,
+                         int* stats) {
+    if (!(tol > 0.0) || mmin < 1 || mmax < mmin || mmax + 1 > MAX_M)
+        return fail(err, EWV_ERR_INVALID_ARG, "adaptive Krylov: need tol > 0 and 1 <= m_min <= m_max <= %d",
+                    MAX_M - 1);
+    E->ad_tol = tol;
+    E->ad_mmin = mmin;
+    E->ad_mmax = mmax;
+    E->ad_stats[0] = E->ad_stats[1] = E->ad_stats[2] = 0;
+    const int rc = dispatch(models, E, s, launches, err, EWV_METHOD_KRYLOV_ADAPTIVE, t, dt, mmax, nsteps, nullptr);
+    if (stats)
+        for (int q = 0; q < 3; ++q) stats[q] = E->ad_stats[q];
+    return rc;
+}
+
+int ewv_step_krylov_adaptive(ewv_model_t m, double t, double dt, double tol, int mmin, int mmax,
+                             int nsteps, int* stats) {
+    if (!m) return EWV_ERR_INVALID_ARG;
+    std::vector<ewv_model*> models{m};
+    Engine* E = ensure_model_engine(m);
+    return adaptive_call(models, E, m->stream, &m->launches, m->err, t, dt, tol, mmin, mmax, nsteps, stats);
+}
+
 int ewv_step_rk(ewv_model_t m, double t, double dt, int scheme, int stages, int nsteps) {
     if (scheme != EWV_METHOD_HORK && scheme != EWV_METHOD_RK32 && scheme != EWV_METHOD_RK44)
         return m ? fail(m->err, EWV_ERR_INVALID_ARG, "scheme must be HORK, RK32 or RK44") : EWV_ERR_INVALID_ARG;
@@ -1819,6 +2159,16 @@ int ewv_batch_step_faber(ewv_batch_t b, double t, double dt, int degree, int nst
 int ewv_batch_step_krylov(ewv_batch_t b, double t, double dt, int mm, int nsteps, int* info) {
     return step_batch(b, EWV_METHOD_KRYLOV, t, dt, mm, nsteps, info);
 }
+int ewv_batch_step_krylov_adaptive(ewv_batch_t b, double t, double dt, double tol, int mmin, int mmax,
+                                   int nsteps, int* stats) {
+    if (!b) return EWV_ERR_INVALID_ARG;
+    cudaStream_t s = b->stream_set ? b->stream : b->models[0]->stream;
+    long long dummy = 0;
+    const int rc = adaptive_call(b->models, b->engine, s, &dummy, b->err, t, dt, tol, mmin, mmax, nsteps, stats);
+    b->models[0]->launches += dummy;
+    return rc;
+}
+
 int ewv_batch_step_rk(ewv_batch_t b, double t, double dt, int scheme, int stages, int nsteps) {
     if (scheme != EWV_METHOD_HORK && scheme != EWV_METHOD_RK32 && scheme != EWV_METHOD_RK44) return EWV_ERR_INVALID_ARG;
     return step_batch(b, scheme, t, dt, stages, nsteps, nullptr);
@@ -2057,82 +2407,6 @@ static int adjoint_krylov(ewv_model* m, Engine* E, double t, double dt, int mm, 
 }
 
 // ---------------------------------------------------------------- exact Krylov adjoint
-// exp(A) of a dense n x n matrix (row-major) by the [13/13] Pade approximant with scaling and
-// squaring (Higham 2005), in FP64 on the host: the small dense part of the reverse sweep.
-static std::vector<double> host_expm(const std::vector<double>& A0, int n) {
-    auto mul = [n](const std::vector<double>& X, const std::vector<double>& Y) {
-        std::vector<double> Z((size_t)n * n, 0.0);
-        for (int r = 0; r < n; ++r)
-            for (int k = 0; k < n; ++k) {
-                const double x = X[(size_t)r * n + k];
-                if (x == 0.0) continue;
-                for (int c = 0; c < n; ++c) Z[(size_t)r * n + c] += x * Y[(size_t)k * n + c];
-            }
-        return Z;
-    };
-    double f[27];
-    f[0] = 1.0;
-    for (int i = 1; i <= 26; ++i) f[i] = f[i - 1] * i;
-    double b[14];
-    for (int k = 0; k <= 13; ++k) b[k] = f[26 - k] * f[13] / (f[26] * f[k] * f[13 - k]);
-    double nrm = 0.0;
-    for (int c = 0; c < n; ++c) {
-        double cs = 0.0;
-        for (int r = 0; r < n; ++r) cs += std::fabs(A0[(size_t)r * n + c]);
-        nrm = std::max(nrm, cs);
-    }
-    const double theta13 = 5.371920351148152;
-    const int sc = nrm > theta13 ? (int)std::ceil(std::log2(nrm / theta13)) : 0;
-    std::vector<double> A(A0);
-    const double fac = std::ldexp(1.0, -sc);
-    for (double& v : A) v *= fac;
-    const std::vector<double> A2 = mul(A, A), A4 = mul(A2, A2), A6 = mul(A4, A2);
-    const size_t nn = (size_t)n * n;
-    std::vector<double> T1(nn), T2(nn);
-    for (size_t e = 0; e < nn; ++e) T1[e] = b[13] * A6[e] + b[11] * A4[e] + b[9] * A2[e];
-    std::vector<double> U = mul(A6, T1);
-    for (size_t e = 0; e < nn; ++e) U[e] += b[7] * A6[e] + b[5] * A4[e] + b[3] * A2[e];
-    for (int r = 0; r < n; ++r) U[(size_t)r * n + r] += b[1];
-    U = mul(A, U);
-    for (size_t e = 0; e < nn; ++e) T2[e] = b[12] * A6[e] + b[10] * A4[e] + b[8] * A2[e];
-    std::vector<double> V = mul(A6, T2);
-    for (size_t e = 0; e < nn; ++e) V[e] += b[6] * A6[e] + b[4] * A4[e] + b[2] * A2[e];
-    for (int r = 0; r < n; ++r) V[(size_t)r * n + r] += b[0];
-    // solve (V - U) X = (V + U) by Gaussian elimination with partial pivoting
-    std::vector<double> L(nn), X(nn);
-    for (size_t e = 0; e < nn; ++e) {
-        L[e] = V[e] - U[e];
-        X[e] = V[e] + U[e];
-    }
-    for (int c = 0; c < n; ++c) {
-        int piv = c;
-        for (int r = c + 1; r < n; ++r)
-            if (std::fabs(L[(size_t)r * n + c]) > std::fabs(L[(size_t)piv * n + c])) piv = r;
-        if (piv != c)
-            for (int k = 0; k < n; ++k) {
-                std::swap(L[(size_t)c * n + k], L[(size_t)piv * n + k]);
-                std::swap(X[(size_t)c * n + k], X[(size_t)piv * n + k]);
-            }
-        const double d = L[(size_t)c * n + c];
-        for (int r = c + 1; r < n; ++r) {
-            const double fct = L[(size_t)r * n + c] / d;
-            if (fct == 0.0) continue;
-            for (int k = c; k < n; ++k) L[(size_t)r * n + k] -= fct * L[(size_t)c * n + k];
-            for (int k = 0; k < n; ++k) X[(size_t)r * n + k] -= fct * X[(size_t)c * n + k];
-        }
-    }
-    for (int c = n - 1; c >= 0; --c) {
-        const double d = L[(size_t)c * n + c];
-        for (int k = 0; k < n; ++k) {
-            double v = X[(size_t)c * n + k];
-            for (int q = c + 1; q < n; ++q) v -= L[(size_t)c * n + q] * X[(size_t)q * n + k];
-            X[(size_t)c * n + k] = v / d;
-        }
-    }
-    for (int i = 0; i < sc; ++i) X = mul(X, X);
-    return X;
-}
-
 // Exact discrete adjoint of one Krylov step (reverse mode through the Arnoldi process; the
 // passes are described in kernels_kadj.cu).  Views over the workspace wvec(i) of each shot:
 // F (the forward Arnoldi: state = wvec(0) = the checkpoint copy, so q_k = wvec(k-1)) and A

@@ -43,7 +43,9 @@ constexpr int KRY_BETA = KRY_E + MAX_M;                   // |x|
 constexpr int KRY_MEFF = KRY_BETA + 1;                    // effective dimension (as double)
 constexpr int KRY_ACTIVE = KRY_MEFF + 1;                  // 1 while Arnoldi continues
 constexpr int KRY_NONFINITE = KRY_ACTIVE + 1;             // 1 if a NaN/Inf was seen
-constexpr int KRY_STRIDE = ((KRY_NONFINITE + 1 + 31) / 32) * 32;
+constexpr int KRY_SKIP = KRY_NONFINITE + 1;               // adaptive step: 1 = not in this substep
+constexpr int KRY_AN = KRY_SKIP + 1;                      // adaptive step: |q|^2 of a stored slot
+constexpr int KRY_STRIDE = ((KRY_AN + 1 + 31) / 32) * 32;
 
 struct ProblemDev {
     int nx, ny, pitch, fs;
@@ -136,10 +138,11 @@ struct StageArgs {
 struct PointArgs {
     int mode;        // 0: |q1|^2 (norm); 1: MGS pass; 2: Krylov combine; 3: copy; 4: swap;
                      // 5: <q_{j+1}, q_k> after a matrix-vector product (flat); 6: zero the
-                     // fields fmask of vector dst
+                     // fields fmask of vector dst; 7: |slot j+1|^2 into kry[KRY_AN] (flat)
     int j, k, m;
     int src, dst;    // copy / swap vectors; combine: destination vector (mode 2)
-    int notail;      // mode 0: start an Arnoldi process without the augmented tail
+    int notail;      // mode 0: 1 = start an Arnoldi process without the augmented tail;
+                     // 2 = start from the tail already in slot 1 (adaptive substeps)
     int fmask;       // fields for copy / swap (bit f)
     double tol;
     double* partials;

@@ -389,7 +389,7 @@ point_flat_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ 
     const ProblemDev* P = probs + pid;
     double* kry = P->kry;
     if ((pa.mode == 1 || pa.mode == 5) && kry[KRY_ACTIVE] == 0.0) return;
-    if (pa.mode == 2 && kry[KRY_NONFINITE] != 0.0) return;
+    if (pa.mode == 2 && (kry[KRY_NONFINITE] != 0.0 || kry[KRY_SKIP] != 0.0)) return;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int nf = P->nfields;   // 4 (2D) or 6 (3D: w_z and psi added)
     const long long nelem = (long long)nf * P->field_stride;
@@ -417,6 +417,12 @@ point_flat_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ 
             const V a = Q[q];
             accd += dotv(a, a);
         }
+    } else if (pa.mode == 7) {
+        const V* W = reinterpret_cast<const V*>(vptr<T>(P, pa.j));      // slot j+1
+        for (long long q = q0 + tid; q < q1; q += NTHREADS) {
+            const V w = W[q];
+            accd += dotv(w, w);
+        }
     } else if (pa.mode == 5) {
         // <q_{j+1}, q_k> after the matrix-vector product (its finalisation is FIN_MATVEC)
         const V* W = reinterpret_cast<const V*>(vptr<T>(P, pa.j));      // slot j+1
@@ -436,7 +442,9 @@ point_flat_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ 
     if (pa.mode == 1 && pa.k == pa.j && pa.j == pa.m) return;   // h_{m+1,m} unused
     const double bsum = block_sum_fixed(accd, red);
     StageArgs a{};
-    a.fin_mode = pa.mode == 0 ? (pa.notail ? FIN_NORM0_NOTAIL : FIN_NORM0) : (pa.mode == 5 ? FIN_MATVEC : FIN_MGS);
+    a.fin_mode = pa.mode == 0 ? (pa.notail == 2 ? FIN_NORM0_TAIL : pa.notail ? FIN_NORM0_NOTAIL : FIN_NORM0)
+               : pa.mode == 7 ? FIN_STORE_NORM
+               : (pa.mode == 5 ? FIN_MATVEC : FIN_MGS);
     a.fin_j = pa.j;
     a.fin_k = pa.k;
     a.m = pa.m;

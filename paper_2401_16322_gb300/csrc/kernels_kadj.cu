@@ -17,7 +17,7 @@
 //   w_before(k) = w_after(k) + h_{k,j} v_k.
 // Column j of the reverse sweep, with Hbar from the output:
 //   (normalisation, j < m_eff) hbar = Hbar_{j+1,j} - <Vbar_{j+1}, v_{j+1}> / h_{j+1,j},
-//                              wbar = (Vbar_{j+1} + hbar v_{j+1}) / h_{j+1,j};  wbar = 0 for
+//                              wbar = Vbar_{j+1} / h_{j+1,j} + hbar v_{j+1};  wbar = 0 for
 //                              the last column;
 //   (Gram-Schmidt, k = j .. k0) hbar = Hbar_{k,j} - <wbar, v_k>,
 //                              Vbar_k += -h_{k,j} wbar + hbar w_before(k),
@@ -88,7 +88,7 @@ __device__ void kadj_finalize(const ProblemDev* P, const KAdjArgs& ka, double to
                 const double hcol = kb[KB_HB + j * MAX_M + (j - 1)] - s1 * full / h;
                 kb[KB_HCOL] = hcol;
                 for (int q = 0; q < MAX_P; ++q) {
-                    wt[q] = q < p ? (vt[q] + hcol * s1 * tn[q]) / h : 0.0;
+                    wt[q] = q < p ? vt[q] / h + hcol * s1 * tn[q] : 0.0;
                     ct[q] = q < p ? tn[q] : 0.0;
                 }
             } else {
@@ -215,8 +215,8 @@ kadj_flat_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ p
             break;
         }
         case KA_COLSET: {
-            // wbar = (Vbar_{j+1} + hbar s_{j+1} q_{j+1}) / h_{j+1,j} (j < m_eff), else 0;
-            // w = q_{j+1}; fused <wbar, q_j>
+            // wbar = Vbar_{j+1} / h_{j+1,j} + hbar v_{j+1}, v_{j+1} = s_{j+1} q_{j+1} (j < m_eff),
+            // else 0; w = q_{j+1}; fused <wbar, q_j>
             const bool live = j < me;
             const T hinv = live ? (T)(1.0 / kh(kry, j + 1, j)) : T(0);
             const T cq = live ? (T)(kb[KB_HCOL] * kry[KRY_S + j + 1]) : T(0);
@@ -225,7 +225,7 @@ kadj_flat_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ p
             const V* Qd = ka.dot >= 0 && j <= me ? reinterpret_cast<const V*>(kvec<T>(P, ka.dot)) : nullptr;
             for (long long q = q0 + tid; q < q1; q += NTHREADS) {
                 const V qn = Qn[q];
-                const V wb = live ? Ops::scale(hinv, Ops::fma(cq, qn, Vb[q])) : Ops::zero();
+                const V wb = live ? Ops::fma(cq, qn, Ops::scale(hinv, Vb[q])) : Ops::zero();
                 Wb[q] = wb;
                 Wc[q] = qn;
                 if (Qd) acc += Ops::dot(wb, Qd[q]);

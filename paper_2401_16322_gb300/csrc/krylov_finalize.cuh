@@ -13,6 +13,9 @@
 //               -> tail_{j+1} = J (s_j tail_j), h_{1,j}
 //   FIN_MGS     pass k of step j: q_{j+1} -= h_{k,j} v_k, tot = <q_{j+1}, q_{k+1}> (k < j)
 //               or |q_{j+1}|^2 (k = j) -> h_{k+1,j} or h_{j+1,j}, s_{j+1}, breakdown test
+//   FIN_NORM0_TAIL  (adaptive substeps) beta = sqrt(tot + |tail_1|^2) from the tail already
+//               in slot 1; problems marked KRY_SKIP stay inactive
+//   FIN_STORE_NORM  kry[KRY_AN] = tot (the grid part of |A v_{j+1}|^2 for the error estimate)
 // The source contribution of the next matrix-vector product, W . tail_j (unscaled), goes to
 // sigma[j].
 #pragma once
@@ -23,7 +26,8 @@
 
 namespace ewv {
 
-enum { FIN_NONE = 0, FIN_NORM0 = 1, FIN_MATVEC = 2, FIN_MGS = 3, FIN_NORM0_NOTAIL = 4 };
+enum { FIN_NONE = 0, FIN_NORM0 = 1, FIN_MATVEC = 2, FIN_MGS = 3, FIN_NORM0_NOTAIL = 4,
+       FIN_NORM0_TAIL = 5, FIN_STORE_NORM = 6 };
 
 __device__ __forceinline__ double* kry_tail(double* kry, int k) {  // k = 1..MAX_M+1
     return kry + KRY_T + (k - 1) * MAX_P;
@@ -36,6 +40,31 @@ __device__ inline void krylov_finalize(const ProblemDev* P, int mode, int j, int
     if (!isfinite(tot)) {
         kry[KRY_NONFINITE] = 1.0;
         kry[KRY_ACTIVE] = 0.0;
+        return;
+    }
+    if (mode == FIN_STORE_NORM) {
+        kry[KRY_AN] = tot;
+        return;
+    }
+    if (mode == FIN_NORM0_TAIL) {
+        // a later substep of the adaptive step: the tail of slot 1 is the previous substep's
+        // (uploaded by the host) and W is already scaled by this step's eta
+        for (int r = 0; r < (MAX_M + 1) * MAX_M; ++r) kry[KRY_H + r] = 0.0;
+        if (kry[KRY_SKIP] != 0.0) {
+            kry[KRY_ACTIVE] = 0.0;
+            return;
+        }
+        const double* t1 = kry_tail(kry, 1);
+        double tt = 0.0;
+        for (int q = 0; q < p; ++q) tt += t1[q] * t1[q];
+        const double beta = sqrt(tot + tt);
+        kry[KRY_BETA] = beta;
+        kry[KRY_S + 1] = beta > 0.0 ? 1.0 / beta : 0.0;
+        kry[KRY_ACTIVE] = beta > 0.0 ? 1.0 : 0.0;
+        kry[KRY_MEFF] = (double)m;
+        double sg = 0.0;
+        for (int q = 0; q < p; ++q) sg += kry[KRY_W + q] * t1[q];
+        P->sigma[1] = P->has_src ? sg : 0.0;
         return;
     }
     if (mode == FIN_NORM0_NOTAIL) {
@@ -54,6 +83,7 @@ __device__ inline void krylov_finalize(const ProblemDev* P, int mode, int j, int
         for (int r = 0; r < (MAX_M + 1) * MAX_M; ++r) kry[KRY_H + r] = 0.0;
     } else if (mode == FIN_NORM0) {
         double* t1 = kry_tail(kry, 1);
+        kry[KRY_SKIP] = 0.0;
         const double eta = tot > 0.0 ? sqrt(tot) : 1.0;
         for (int q = 0; q < MAX_P; ++q) t1[q] = 0.0;
         t1[p - 1] = eta;

@@ -20,12 +20,13 @@ ERRORS = {
 }
 F32, F64 = 0, 1
 METHOD = {"apply": 0, "faber": 1, "krylov": 2, "hork": 3, "rk32": 4, "rk44": 5, "leapfrog": 6,
-          "adjoint_faber": 7, "adjoint_krylov": 8, "adjoint_leapfrog": 9}
+          "adjoint_faber": 7, "adjoint_krylov": 8, "adjoint_leapfrog": 9, "krylov_adaptive": 10}
 LEAPFROG_AVERAGED, LEAPFROG_LITERAL, LEAPFROG_DIFFERENCE = 0, 1, 2
 
 # Every symbol include/ewave.h declares (checked by the tests).
 EXPORTS = [
     "ewv_sync", "ewv_batch_sync", "ewv_debug_set_wait_limit", "ewv_set_krylov_adjoint",
+    "ewv_step_krylov_adaptive", "ewv_batch_step_krylov_adaptive",
     "ewv_create_model", "ewv_destroy_model", "ewv_set_stream", "ewv_layout",
     "ewv_workspace_bytes", "ewv_bind_buffers", "ewv_bind_workspace", "ewv_bind_seismogram",
     "ewv_reset_recording", "ewv_set_velocity", "ewv_set_source_receivers",
@@ -153,6 +154,8 @@ def load_library(path=LIB_PATH):
         "ewv_batch_sync": ([vp], i),
         "ewv_debug_set_wait_limit": ([ctypes.c_ulonglong], i),
         "ewv_set_krylov_adjoint": ([vp, i], i),
+        "ewv_step_krylov_adaptive": ([vp, d, d, d, i, i, i, ctypes.POINTER(i)], i),
+        "ewv_batch_step_krylov_adaptive": ([vp, d, d, d, i, i, i, ctypes.POINTER(i)], i),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -367,6 +370,15 @@ class Model:
         self._check(self.lib.ewv_step_krylov(self.h, t, dt, m, nsteps, ctypes.byref(info)), "step_krylov")
         return info.value
 
+    def step_krylov_adaptive(self, t, dt, tol, m_min=1, m_max=30, nsteps=1):
+        """Adaptive Krylov steps (dimension and substeps chosen per shot to meet ``tol``);
+        returns {"substeps", "matvecs", "max_dim"} summed over shots and steps."""
+        self.ensure_workspace("krylov_adaptive", m_max)
+        st = (ctypes.c_int * 3)()
+        self._check(self.lib.ewv_step_krylov_adaptive(self.h, t, dt, tol, m_min, m_max, nsteps, st),
+                    "step_krylov_adaptive")
+        return {"substeps": st[0], "matvecs": st[1], "max_dim": st[2]}
+
     def step_rk(self, t, dt, scheme, stages=0, nsteps=1):
         self.ensure_workspace(scheme, stages)
         self._check(self.lib.ewv_step_rk(self.h, t, dt, METHOD[scheme], stages, nsteps), "step_rk")
@@ -513,6 +525,14 @@ class Batch:
             self._check(self.lib.ewv_batch_step_leapfrog(self.h, t, dt, nsteps), "batch_step_leapfrog")
         else:
             raise ValueError(method)
+
+    def step_krylov_adaptive(self, t, dt, tol, m_min=1, m_max=30, nsteps=1):
+        for md in self.models:
+            md.ensure_workspace("krylov_adaptive", m_max)
+        st = (ctypes.c_int * 3)()
+        self._check(self.lib.ewv_batch_step_krylov_adaptive(self.h, t, dt, tol, m_min, m_max, nsteps, st),
+                    "batch_step_krylov_adaptive")
+        return {"substeps": st[0], "matvecs": st[1], "max_dim": st[2]}
 
     def enable_graphs(self, on=True):
         self._check(self.lib.ewv_batch_enable_graphs(self.h, int(on)), "graphs")

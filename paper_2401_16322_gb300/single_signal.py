@@ -9,8 +9,11 @@ the same times while the wave passes the receiver (Sec. 4.1).
 
 Readings of what the paper leaves open (all stated with the results):
 
-* Coordinates: (x, depth), depth measured from the grid's top row; the boundaries are the
-  zero extension of Sec. 2.1 on all four sides (no free surface, no damping).
+* Coordinates: (x, depth) in the 6 km x 5 km domain.  Its four sides are the zero-extension
+  boundary of Sec. 2.1 (no free surface, no damping), which lies on the ghost lines one cell
+  beyond the outermost nodes; so the nodes are the interior points (i + 1) dx, (j + 1) dx of
+  the domain on every grid, and the source 10 m above the bottom sees the same boundary on
+  the 10 m and the 2.5 m grid.
 * Reference: the paper's RK9-7 is not available; the 2.5 m reference is the FP64 HORK(16)
   step at dt2 (dt2 omega_max = 1.8 on that grid, where the Taylor remainder of degree 16 is
   below 1e-10), which also samples every dt2.
@@ -47,10 +50,12 @@ def dt2_of(dx=DX):
 
 
 def build(dx, p=16):
-    nx, ny = int(round(LX / dx)) + 1, int(round(LY / dx)) + 1
+    """The domain's interior nodes; positions are given from node 0 at (dx, dx)."""
+    nx, ny = int(round(LX / dx)) - 1, int(round(LY / dx)) - 1
     md = Model(nx, ny, dx, 8, 0, 0.0, False, precision="f64", p=p, max_receivers=1)
     md.set_velocity(np.full((ny, nx), C))
-    md.set_source_receivers(0, SRC[0], SRC[1], F_PEAK, T0, 1.0, np.array([REC]))
+    md.set_source_receivers(0, SRC[0] - dx, SRC[1] - dx, F_PEAK, T0, 1.0,
+                            np.array([[REC[0] - dx, REC[1] - dx]]))
     return md
 
 

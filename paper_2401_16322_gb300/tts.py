@@ -88,6 +88,19 @@ def common_ellipse(models, c_max):
     return best
 
 
+# local error tolerance of the adaptive Krylov candidate ("krylov-adaptive", m = m_max)
+ADAPTIVE_TOL = 1e-6
+
+
+def batch_step(batch, method, t, dt, m, nsteps):
+    """Advance a batch; "krylov_adaptive" (the search's "krylov-adaptive") runs the adaptive
+    Krylov step (m = m_max)."""
+    if method == "krylov_adaptive":
+        batch.step_krylov_adaptive(t, dt, ADAPTIVE_TOL, 1, m, nsteps)
+    else:
+        batch.step(method, t, dt, m, nsteps)
+
+
 def base_method(models, method):
     """Map a candidate method name to the library's: "krylov-wQ" is Krylov with an
     orthogonalisation window of Q, "hork-horner" HORK evaluated in Horner form and
@@ -103,6 +116,8 @@ def base_method(models, method):
                                     else LEAPFROG_AVERAGED)
     if window:
         return "krylov"
+    if method == "krylov-adaptive":
+        return "krylov_adaptive"
     return {"hork-horner": "hork", "leapfrog-difference": "leapfrog"}.get(method, method)
 
 
@@ -115,6 +130,11 @@ def simulate(models, batch, method, m, dt, T, variant=0):
             md.bind_seismogram(nsteps)
         md.reset_state()
         md.ensure_workspace(method, m)
+    if method == "krylov_adaptive" and batch is None:
+        for md in models:
+            md.step_krylov_adaptive(0.0, dt, ADAPTIVE_TOL, 1, m, nsteps)
+            md.sync()
+        return nsteps
     if batch is None:
         for md in models:
             if method == "leapfrog":
@@ -123,7 +143,7 @@ def simulate(models, batch, method, m, dt, T, variant=0):
                 md.step(method, 0.0, dt, m, nsteps)
             md.sync()
     else:
-        batch.step(method, 0.0, dt, m, nsteps)
+        batch_step(batch, method, 0.0, dt, m, nsteps)
         batch.sync()        # a non-finite result or a timed-out wait belongs to this run
     return nsteps
 
@@ -182,6 +202,7 @@ SCAN_PLAN = (
     ("krylov-w2", (20, 30, 40), tuple(range(24, 1, -1))),
     ("hork", (8, 12, 16, 20, 24, 28, 32), tuple(range(12, 0, -1))),
     ("hork-horner", (8, 12, 16, 20, 24, 28, 32), tuple(range(12, 0, -1))),
+    ("krylov-adaptive", (40,), (24, 16, 12, 8, 6, 4, 3, 2)),
 )
 LEAPFROG_DIVISORS = (1, 2, 3, 4, 6, 8, 12, 16, 24, 32)
 # Stability check of the polynomial integrators: a setting that meets the error target must
@@ -261,12 +282,12 @@ def _time_step(full_batch, full_models, method, m, dt, t_live):
     for md in full_models:
         md.ensure_workspace(method, m)
         md.reset_state()
-    full_batch.step(method, t_live - 2 * dt, dt, m, 2)   # inject the source, warm the graph
+    batch_step(full_batch, method, t_live - 2 * dt, dt, m, 2)   # inject the source, warm the graph
     full_batch.sync()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ns = 2
     e0.record()
-    full_batch.step(method, t_live, dt, m, ns)
+    batch_step(full_batch, method, t_live, dt, m, ns)
     e1.record()
     full_batch.sync()
     return e0.elapsed_time(e1) / ns
