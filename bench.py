@@ -66,10 +66,11 @@ def parse(argv=None):
                          f"(default {','.join(map(str, DEFAULT_SELECTION))})")
     ap.add_argument("--variant", type=int, default=-1,
                     help="FP32 stencil-pass variant (0..6; -1: autotune at first use)")
-    ap.add_argument("--case", default="full", choices=["full", "small", "medium", "cube", "signal"],
+    ap.add_argument("--case", default="full", choices=["full", "small", "medium", "cube", "signal", "oracle"],
                     help="small / medium: the 1001x501 model with 4 / 16 shots (profiling); "
                          "cube: only the 3D side run (--n3d, --check3d); signal: only the "
-                         "single-signal experiment of Sec. 4 (FP64, 10 m against 2.5 m)")
+                         "single-signal experiment of Sec. 4 (FP64, 10 m against 2.5 m); oracle: "
+                         "the FP64 oracle run in full on the host cores (no GPU)")
     ap.add_argument("--check3d", type=int, default=0,
                     help="edge of the 3D accuracy cube of a Delta-t_max search (0: time the "
                          "settings found by that search on a 96^3 cube, and check their error "
@@ -597,6 +598,73 @@ def max_over_ranks(value, dist=None, device="cuda"):
     return float(t.item())
 
 
+# ------------------------------------------------------------------------- full oracle runs
+def _oracle_full_worker(task):
+    """One whole oracle simulation of one shot (no time budget): (seconds, steps, points)."""
+    (nx, ny, dx, order, pml, beta0, fs, c, sx, sy, f_peak, t0, method, m, dt, nsteps, ellipse) = task
+    from oracle.model import Model as OModel
+    from oracle.simulate import run
+    from oracle.source import PointSource
+    om = OModel(nx, ny, dx, order, pml, beta0, fs, c)
+    src = PointSource(om, sx, sy, f_peak, t0, 1.0, p=12)
+    t_start = time.perf_counter()
+    run(om, method, dt, nsteps, src=src, m=m, t0=0.0, faber_params=ellipse)
+    return time.perf_counter() - t_start, nsteps, nx * ny
+
+
+def oracle_full_runs(procs=0):
+    """The FP64 oracle run in full (not sampled) on the small homogeneous case, the 601 x 301
+    model and the 16-shot FWI model, with the settings the GPU runs use: one process for a
+    single shot, and the 16 shots on one process (measured on one shot, times 16) and on every
+    host core (shots in parallel, measured)."""
+    import multiprocessing as mp
+    import platform
+    from oracle.faber import ellipse_params
+    from paper_2401_16322_gb300.tts import leapfrog_step, pml_beta0
+    from paper_2401_16322_gb300.workloads import (config_fwi, config_homogeneous_small,
+                                                  config_layered_601x301, t0_for)
+    procs = procs if procs > 0 else (os.cpu_count() or 1)
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+
+    def tasks(w, method, m, k, shots, beta0=None, dims_c=None):
+        c_max = float(w.c.max())
+        b0 = pml_beta0(c_max, w.pml, w.dx) if beta0 is None else beta0
+        dt = k * leapfrog_step(c_max, w.dx, w.order)
+        nsteps = int(round(w.T / dt))
+        ell = ellipse_params(c_max, b0, w.dx, w.order, free_surface=w.free_surface)
+        return [(w.nx, w.ny, w.dx, w.order, w.pml, b0, w.free_surface, w.c, s.sx, s.sy, w.f_peak,
+                 t0_for(w.f_peak), method, m, dt, nsteps, ell) for s in shots], dt, nsteps
+
+    out = {"cpu": platform.processor() or platform.machine(), "cores": procs, "runs": []}
+    w1 = config_homogeneous_small()
+    w2 = config_layered_601x301()
+    w4 = config_fwi()
+    pool = mp.get_context("spawn").Pool(procs)
+    pool.map(abs, range(procs))
+    for name, w, method, m, k in (("homogeneous 101x101, 4th order", w1, "hork", 12, 2.0),
+                                  ("layered 601x301", w2, "hork", 20, 4.0),
+                                  ("FWI model 401x201, one shot", w4, "krylov", 20, 8.0)):
+        tk, dt, nsteps = tasks(w, method, m, k, w.shots[:1])
+        sec, _, pts = pool.apply(_oracle_full_worker, (tk[0],))
+        out["runs"].append({"workload": name, "method": method, "m": m, "dt_ms": dt * 1e3,
+                            "nsteps": nsteps, "processes": 1, "seconds": sec,
+                            "grid_point_steps_per_s": pts * nsteps / sec})
+        log(f"oracle {name}: {sec:.1f} s")
+    tk, dt, nsteps = tasks(w4, "krylov", 20, 8.0, w4.shots)
+    t_start = time.perf_counter()
+    res = pool.map(_oracle_full_worker, tk, chunksize=1)
+    wall = time.perf_counter() - t_start
+    one = out["runs"][-1]["seconds"]
+    out["runs"].append({"workload": "FWI model 401x201, 16 shots (forward)", "method": "krylov", "m": 20,
+                        "dt_ms": dt * 1e3, "nsteps": nsteps, "processes": procs, "seconds": wall,
+                        "one_process_seconds_est": 16 * one,
+                        "grid_point_steps_per_s": sum(r[2] * r[1] for r in res) / wall})
+    pool.terminate()
+    pool.join()
+    return out
+
+
 # ------------------------------------------------------------------------- reference arm
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -978,6 +1046,9 @@ def main(argv=None):
     args = parse(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.case == "oracle":
+        print(json_line({"oracle_full": oracle_full_runs(args.cpu_procs)}), flush=True)
+        return 0
     if args.case == "cube":
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))

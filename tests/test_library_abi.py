@@ -131,4 +131,5 @@ def test_oracle_is_used_only_by_smoke_and_the_cpu_baseline(repo_root):
         return out
 
     assert users(os.path.join(repo_root, "__graft_entry__.py")) == {"smoke"}
-    assert users(os.path.join(repo_root, "bench.py")) == {"_oracle_worker", "sample"}
+    assert users(os.path.join(repo_root, "bench.py")) == {"_oracle_worker", "sample", "_oracle_full_worker",
+                                                          "oracle_full_runs"}
