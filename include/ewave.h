@@ -425,7 +425,10 @@ int ewv_batch_enable_graphs(ewv_batch_t batch, int enable);
 
 /* Tile-shape autotuner of the FP32 persistent TMA pass.  Variants (tile height, consumer
  * warps, pipeline stages): 0 = (16, 16, 3), 1 = (16, 8, 3), 2 = (8, 8, 5), 3 = (8, 16, 5),
- * 5 = (20, 20, 3), 6 = (18, 18, 3);
+ * 5 = (20, 20, 3), 6 = (18, 18, 3), each consumer thread on one column; 7 = (18, 9, 3),
+ * 8 = (16, 8, 3), 9 = (18, 18, 3), each consumer thread on two adjacent columns (8-byte
+ * shared loads, packed FP32 pair arithmetic); the leap-frog step and the gradient pass
+ * always run the one-column form (18, 18);
  * tiles are 64 columns wide with a 4-column / R-row halo.  With v = -1 (default) the first
  * FP32 step call times every variant on a probe pass over the engine's own problems and
  * keeps the fastest; ewv_*kernel_variant reports the choice, its shape and the probe times
@@ -433,7 +436,7 @@ int ewv_batch_enable_graphs(ewv_batch_t batch, int enable);
  * 4) without the U stage buffer: passes that read a U vector run variant 0 under it.
  * 3D models: 0 (default) = TMA pipeline with 16 consumer warps, 2 = 8 warps, 1 = plain
  * z-marching kernel. */
-#define EWV_NUM_KERNEL_VARIANTS 7
+#define EWV_NUM_KERNEL_VARIANTS 10
 int ewv_set_kernel_variant(ewv_model_t model, int variant);
 int ewv_kernel_variant(ewv_model_t model, int* variant, int* tile_height, int* warps,
                        int* stages, double* probe_us);

@@ -185,7 +185,7 @@ int launch_leapfrog_tma3d(int R, int warps, const ProblemDev* probs, const int* 
 int upload_tma_tables(const double* fs_uyy, const double* fs_uy, const double* fs_dwy);
 int build_tensor_maps(std::vector<ProblemDev>& probs, int R, const std::vector<int>& work_vecs,
                       void** d_maps_inout);
-constexpr int TMA_NUM_VARIANTS = 7;
+constexpr int TMA_NUM_VARIANTS = 10;
 // One 2D FP32 leap-frog step through the persistent TMA pass (64 x 18 tiles); tbase and
 // ntiles are those of the 18-row map set.
 int launch_leapfrog_tma(int R, const ProblemDev* probs, const int* tbase, int nprob, int ntiles, int cur,

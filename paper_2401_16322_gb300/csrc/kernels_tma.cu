@@ -270,6 +270,100 @@ __device__ __forceinline__ int find_problem(const int* __restrict__ base, int np
     return lo;
 }
 
+// The producer (one elected lane of the last warp): for each tile of this CTA, wait until
+// its stage is free, resolve the tile's problem and descriptor, arm the stage's "full"
+// barrier with the byte count and issue the TMA loads.  Returns the number of tiles issued.
+template <int R, int BYv, int NSTv, int EPI, bool HASU>
+__device__ __forceinline__ int tma_produce(const ProblemDev* __restrict__ probs, const int* __restrict__ tbase,
+                                           int nprob, int ntiles, int mapset, const StageArgs& a, float* smem,
+                                           uint64_t* full, uint64_t* empty, TileInfo* info, int* s_err,
+                                           uint32_t bytes, uint64_t wait_lim) {
+    using L = StageLayout<R, BYv, HASU>;
+    const bool has_u = HASU && a.u >= 0, has_a = a.a >= 0;
+    int issued = 0;
+    int it = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const int s = it % NSTv;
+        const uint32_t ph = (uint32_t)(it / NSTv) & 1u;
+        if (!mbar_wait(&empty[s], ph ^ 1u, wait_lim)) {
+            *s_err = 1;
+            break;
+        }
+        const int pid = find_problem(tbase, nprob, tile);
+        const ProblemDev* P = probs + pid;
+        const CUtensorMap* maps = reinterpret_cast<const CUtensorMap*>(P->tmaps) + mapset * NMAP;
+        const int tiles_x = (P->nx + BX - 1) / BX;
+        const int lt = tile - __ldg(tbase + pid);
+        const int x0 = (lt % tiles_x) * BX, y0 = (lt / tiles_x) * BYv;
+        TileInfo& ti = info[s];
+        ti.Y = a.y_out >= 0 ? (a.y_out == 0 ? (float*)P->state
+                                            : (float*)P->work + (long long)(a.y_out - 1) * P->vec_stride)
+                            : nullptr;
+        ti.A = a.acc_out >= 0 ? (a.acc_out == 0 ? (float*)P->state
+                                                : (float*)P->work + (long long)(a.acc_out - 1) * P->vec_stride)
+                              : nullptr;
+        ti.fstr = P->field_stride;
+        ti.x0 = x0;
+        ti.y0 = y0;
+        ti.nx = P->nx;
+        ti.ny = P->ny;
+        ti.pitch = P->pitch;
+        ti.pml = P->pml;
+        ti.fs = P->fs;
+        ti.src_i = P->src_i;
+        ti.src_j = P->src_j;
+        ti.shot = P->shot;
+        ti.btab = P->btab;
+        ti.nbtab = P->nbtab;
+        ti.beta0 = P->fbeta0;
+        ti.inv_pml = P->finv_pml;
+        ti.idx1 = P->finv_dx;
+        ti.idx2 = P->finv_dx2;
+        ti.sig = (a.src_slot >= 0 && P->has_src) ? (float)P->sigma[a.src_slot] : 0.f;
+        ti.xs = a.x_scale_slot >= 0 ? (float)P->kry[a.x_scale_slot] : 1.f;
+        float* st = smem + (size_t)s * L::FLOATS;
+        // the arrive below releases the tile info together with the copies
+        mbar_expect_tx(&full[s], bytes);
+        const int kx = a.x, cx = a.x == 0 ? 0 : a.x - 1;
+        tma_load_4d(st + L::U_OFF, map_of(maps, kx, 0), x0 - TX, y0 - R, 0, cx, &full[s]);
+        tma_load_4d(st + L::WX_OFF, map_of(maps, kx, 1), x0 - TX, y0, 2, cx, &full[s]);
+        tma_load_4d(st + L::WY_OFF, map_of(maps, kx, 2), x0, y0 - R, 3, cx, &full[s]);
+        if (EPI < 2) tma_load_4d(st + L::V_OFF, map_of(maps, kx, 3), x0, y0, 1, cx, &full[s]);
+        if (EPI != 3) tma_load_2d(st + L::C2_OFF, maps + 10, x0, y0, &full[s]);
+        if (has_u)
+            tma_load_4d(st + L::PU_OFF, map_of(maps, a.u, 4), x0, y0, 0, a.u == 0 ? 0 : a.u - 1, &full[s]);
+        if (has_a)
+            tma_load_4d(st + L::PA_OFF, map_of(maps, a.a, 4), x0, y0, 0, a.a == 0 ? 0 : a.a - 1, &full[s]);
+        issued = it + 1;
+    }
+    return issued;
+}
+
+// Byte count one stage receives (the "full" barrier's transaction count).
+template <int R, int BYv, int EPI, bool HASU>
+__device__ __forceinline__ uint32_t tma_stage_bytes(const StageArgs& a) {
+    using L = StageLayout<R, BYv, HASU>;
+    const bool has_u = HASU && a.u >= 0, has_a = a.a >= 0;
+    // (the leap-frog step, EPI 2, does not read v; the gradient pass, EPI 3, neither v nor c^2)
+    return (uint32_t)((L::BOX_FLOATS - (EPI >= 2 ? BYv * BX : 0) - (EPI == 3 ? BYv * BX : 0) +
+                       (has_u ? 4 * BYv * BX : 0)) * 4) +
+           (has_a ? 4 * BYv * BX * 4 : 0);
+}
+
+// After a pipeline wait gave up: the producer waits (bounded) for the last copy issued into
+// every stage, so that no TMA write lands after the CTA exits, and the error word is set.
+template <int NSTv>
+__device__ __forceinline__ void tma_finish(int s_err, int issued, uint64_t* full, int* err) {
+    const int tid = threadIdx.x;
+    if (s_err) {
+        if (issued > 0) {
+            for (int it = issued - 1; it >= 0 && it >= issued - NSTv; --it)
+                (void)mbar_wait(&full[it % NSTv], (uint32_t)(it / NSTv) & 1u, kDrainLimitNs);
+        }
+        if (tid == 0) atomicOr(err, 1);
+    }
+}
+
 // EPI 0: the general epilogue.  EPI 1: the steady-state form of the Faber and HORK passes,
 // ck = 1 and cau = cak = cax = 0:  Y = cu U + cx X + ch (H X + sigma),  ACC = ca A + cay Y.
 template <int R, int BYv, int NW, int NSTv, int EPI, bool HASU>
@@ -304,73 +398,14 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
     __syncthreads();
 
     const bool has_u = HASU && a.u >= 0, has_a = a.a >= 0;
-    // (the leap-frog step, EPI 2, does not read v; the gradient pass, EPI 3, neither v nor c^2)
-    const uint32_t bytes = (uint32_t)((L::BOX_FLOATS - (EPI >= 2 ? BYv * BX : 0) - (EPI == 3 ? BYv * BX : 0) +
-                                       (has_u ? 4 * BYv * BX : 0)) * 4) +
-                           (has_a ? 4 * BYv * BX * 4 : 0);
+    const uint32_t bytes = tma_stage_bytes<R, BYv, EPI, HASU>(a);
     int issued = 0;
 
     if (warp == NW) {
         // ------------------------------------------------------------ producer
-        if (lane == 0) {
-            int it = 0;
-            for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
-                const int s = it % NSTv;
-                const uint32_t ph = (uint32_t)(it / NSTv) & 1u;
-                if (!mbar_wait(&empty[s], ph ^ 1u, wait_lim)) {
-                    s_err = 1;
-                    break;
-                }
-                const int pid = find_problem(tbase, nprob, tile);
-                const ProblemDev* P = probs + pid;
-                const CUtensorMap* maps = reinterpret_cast<const CUtensorMap*>(P->tmaps) + mapset * NMAP;
-                const int tiles_x = (P->nx + BX - 1) / BX;
-                const int lt = tile - __ldg(tbase + pid);
-                const int x0 = (lt % tiles_x) * BX, y0 = (lt / tiles_x) * BYv;
-                TileInfo& ti = info[s];
-                ti.Y = a.y_out >= 0 ? (a.y_out == 0 ? (float*)P->state
-                                                    : (float*)P->work + (long long)(a.y_out - 1) * P->vec_stride)
-                                    : nullptr;
-                ti.A = a.acc_out >= 0 ? (a.acc_out == 0 ? (float*)P->state
-                                                        : (float*)P->work + (long long)(a.acc_out - 1) * P->vec_stride)
-                                      : nullptr;
-                ti.fstr = P->field_stride;
-                ti.x0 = x0;
-                ti.y0 = y0;
-                ti.nx = P->nx;
-                ti.ny = P->ny;
-                ti.pitch = P->pitch;
-                ti.pml = P->pml;
-                ti.fs = P->fs;
-                ti.src_i = P->src_i;
-                ti.src_j = P->src_j;
-                ti.shot = P->shot;
-                ti.btab = P->btab;
-                ti.nbtab = P->nbtab;
-                ti.beta0 = P->fbeta0;
-                ti.inv_pml = P->finv_pml;
-                ti.idx1 = P->finv_dx;
-                ti.idx2 = P->finv_dx2;
-                ti.sig = (a.src_slot >= 0 && P->has_src) ? (float)P->sigma[a.src_slot] : 0.f;
-                ti.xs = a.x_scale_slot >= 0 ? (float)P->kry[a.x_scale_slot] : 1.f;
-                float* st = smem + (size_t)s * L::FLOATS;
-                // the arrive below releases the tile info together with the copies
-                mbar_expect_tx(&full[s], bytes);
-                const int kx = a.x, cx = a.x == 0 ? 0 : a.x - 1;
-                tma_load_4d(st + L::U_OFF, map_of(maps, kx, 0), x0 - TX, y0 - R, 0, cx, &full[s]);
-                tma_load_4d(st + L::WX_OFF, map_of(maps, kx, 1), x0 - TX, y0, 2, cx, &full[s]);
-                tma_load_4d(st + L::WY_OFF, map_of(maps, kx, 2), x0, y0 - R, 3, cx, &full[s]);
-                if (EPI < 2) tma_load_4d(st + L::V_OFF, map_of(maps, kx, 3), x0, y0, 1, cx, &full[s]);
-                if (EPI != 3) tma_load_2d(st + L::C2_OFF, maps + 10, x0, y0, &full[s]);
-                if (has_u)
-                    tma_load_4d(st + L::PU_OFF, map_of(maps, a.u, 4), x0, y0, 0, a.u == 0 ? 0 : a.u - 1,
-                                &full[s]);
-                if (has_a)
-                    tma_load_4d(st + L::PA_OFF, map_of(maps, a.a, 4), x0, y0, 0, a.a == 0 ? 0 : a.a - 1,
-                                &full[s]);
-                issued = it + 1;
-            }
-        }
+        if (lane == 0)
+            issued = tma_produce<R, BYv, NSTv, EPI, HASU>(probs, tbase, nprob, ntiles, mapset, a, smem, full,
+                                                          empty, info, &s_err, bytes, wait_lim);
     } else {
         // ------------------------------------------------------------ consumers
         const int tx = tid & (BX - 1);    // x inside the tile
@@ -661,14 +696,8 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
         }
     }
     __syncthreads();
-    if (s_err) {
-        // drain: wait (bounded) for the last copy issued into every stage
-        if (warp == NW && lane == 0) {
-            for (int it = issued - 1; it >= 0 && it >= issued - NSTv; --it)
-                (void)mbar_wait(&full[it % NSTv], (uint32_t)(it / NSTv) & 1u, kDrainLimitNs);
-        }
-        if (tid == 0) atomicOr(err, 1);
-    }
+    // (issued is non-zero on the producer lane only)
+    tma_finish<NSTv>(s_err, issued, full, err);
 }
 
 #undef cxf
@@ -680,6 +709,307 @@ stage_tma_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ t
 #undef cakf
 #undef cayf
 #undef caxf
+
+// ---------------------------------------------------------------- column-pair consumers
+// The same pass with every consumer thread on two adjacent columns (x, x + 1) of NR
+// consecutive rows: the column pair of a staged row is one 8-byte shared load, and the
+// arithmetic runs on packed FP32 pairs (one instruction for both columns).  The y taps of
+// both columns slide in registers as pairs; the x taps of a row are the five pairs from
+// x - 4 to x + 5, and the taps that straddle two pairs (odd offsets) are formed with scalar
+// operations.  Per grid point this issues about a third of the shared loads of the
+// one-column form and shares each tile's setup over twice the points.  Rows of the
+// free-surface band (Appendix A stencils, top tile only) take a scalar path per point.
+__device__ __forceinline__ float2 lds2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+__device__ __forceinline__ void st2(float* p, float2 v, bool both) {
+    if (both)
+        *reinterpret_cast<float2*>(p) = v;
+    else
+        p[0] = v.x;
+}
+
+// One point (tile column tc, tile row lr) from shared memory with the scalar formulas of the
+// one-column form, free-surface rows included, and its epilogue.
+template <int R, int BYv, int EPI, bool HASU>
+__device__ __forceinline__ void tma_point_scalar(const float* st, const TileInfo& ti, const StageArgs& a, int tc,
+                                             int lr, bool has_u, bool has_a) {
+    using L = StageLayout<R, BYv, HASU>;
+    const int nx = ti.nx, ny = ti.ny;
+    const int i = ti.x0 + tc, j = ti.y0 + lr;
+    if (i >= nx || j >= ny) return;
+    const bool fs = ti.fs != 0;
+    const int cs = tc + TX;
+    const float* su = st + L::U_OFF;
+    const float* swy = st + L::WY_OFF;
+    const float* urow = su + (lr + R) * L::SW + cs;
+    const float* wxrow = st + L::WX_OFF + lr * L::SW + cs;
+    auto ucolv = [&](int q) { return su[(lr + q) * L::SW + cs]; };   // staged row lr + q
+    auto wcolv = [&](int q) { return swy[(lr + q) * BX + tc]; };
+    float px[R], dx[R], dw[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        px[k] = urow[k + 1] + urow[-k - 1];
+        dx[k] = urow[1 + k] - urow[-k];
+        dw[k] = wxrow[k] - wxrow[-1 - k];
+    }
+    const float uc = urow[0];
+    const float uxx = cent_tree<R>(uc, px);
+    const float dux = stag_tree<R>(dx);
+    const float dwx = stag_tree<R>(dw);
+    float uyy, duy, dwy;
+    if (fs && j < 4) {
+        uyy = 0.f;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) uyy += g_tma_fs[TFS_UYY + j * 9 + q] * su[(q + R) * L::SW + cs];
+        dwy = 0.f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) dwy += g_tma_fs[TFS_DWY + j * 8 + q] * swy[(q + R) * BX + tc];
+    } else {
+        float py[R], dwv[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            py[k] = ucolv(R + k + 1) + ucolv(R - k - 1);
+            dwv[k] = wcolv(R - 1 - k) - wcolv(R + k);
+        }
+        uyy = cent_tree<R>(uc, py);
+        dwy = stag_tree<R>(dwv);
+    }
+    if (fs && j < 3) {
+        duy = 0.f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) duy += g_tma_fs[TFS_UY + j * 8 + q] * su[(q + R) * L::SW + cs];
+    } else {
+        float dy[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) dy[k] = ucolv(R - k) - ucolv(R + 1 + k);
+        duy = stag_tree<R>(dy);
+    }
+    const float* btab = ti.btab;
+    const int nbt = ti.nbtab;
+    const float bxn = btab_at(btab, nbt, 2 * min(i + 1, nx - i));
+    const float bxh = btab_at(btab, nbt, min(2 * i + 3, 2 * (nx - i) - 1));
+    const float byn = btab_at(btab, nbt, 2 * (fs ? ny - j : min(j + 1, ny - j)));
+    const float byh = btab_at(btab, nbt, fs ? 2 * (ny - j) - 1 : min(2 * j + 3, 2 * (ny - j) - 1));
+    const int pt = lr * BX + tc;
+    const float* sv = st + L::V_OFF;
+    const float* sc2 = st + L::C2_OFF;
+    const float* spu = st + L::PU_OFF;
+    const float* spa = st + L::PA_OFF;
+    const float idx1 = ti.idx1, idx2 = ti.idx2;
+    const float xu = uc, xv = sv[pt], xwx = wxrow[0], xwy = wcolv(R);
+    float hv = -bxn * byn * xu + sc2[pt] * ((uxx + uyy) * idx2 + (dwx + dwy) * idx1) - (bxn + byn) * xv;
+    if (i == ti.src_i && j == ti.src_j) hv += ti.sig;
+    const float hwx = (i < nx - 1) ? (byn - bxh) * dux * idx1 - bxh * xwx : 0.f;
+    const float hwy = (j < ny - 1) ? (bxn - byh) * duy * idx1 - byh * xwy : 0.f;
+    const float xf[4] = {xu, xv, xwx, xwy};
+    const float hf[4] = {xv, hv, hwx, hwy};
+    const float chx = a.fch * ti.xs;
+    const long long o = (long long)j * ti.pitch + i;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        const bool pad = (f == 2 && i >= nx - 1) || (f == 3 && j >= ny - 1);
+        const float uval = has_u ? spu[f * BYv * BX + pt] : 0.f;
+        const float aval = has_a ? spa[f * BYv * BX + pt] : 0.f;
+        const float kf = fmaf(a.fcx, xf[f], chx * hf[f]);
+        if constexpr (EPI == 1) {
+            const float yf = pad ? 0.f : (has_u ? fmaf(a.fcu, uval, kf) : kf);
+            if (ti.Y) ti.Y[f * ti.fstr + o] = yf;
+            if (ti.A) ti.A[f * ti.fstr + o] = has_a ? fmaf(a.fcay, yf, a.fca * aval) : a.fcay * yf;
+        } else {
+            const float yf = pad ? 0.f : (a.fcu * uval + a.fck * kf);
+            if (ti.Y) ti.Y[f * ti.fstr + o] = yf;
+            if (ti.A)
+                ti.A[f * ti.fstr + o] =
+                    pad ? 0.f : (a.fca * aval + a.fcau * uval + a.fcak * kf + a.fcay * yf + a.fcax * xf[f]);
+        }
+    }
+}
+
+template <int R, int BYv, int NW, int NSTv, int EPI, bool HASU>
+__global__ void __launch_bounds__(NW * 32 + 32, 1)
+stage_tma_x2_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ tbase, int nprob,
+                    int ntiles, int mapset, StageArgs a, int* err) {
+    static_assert(EPI <= 1, "the column-pair consumers serve the integrator passes");
+    using L = StageLayout<R, BYv, HASU>;
+    constexpr int CPR = BX / 2;                 // consumer threads per tile row
+    constexpr int TPR = NW * 32 / CPR;          // thread rows
+    constexpr int NR = BYv / TPR;               // consecutive rows per consumer thread
+    static_assert(NR * TPR == BYv && NR >= 1, "tile rows must split evenly over threads");
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    float* smem = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ __align__(8) uint64_t full[NSTv];
+    __shared__ __align__(8) uint64_t empty[NSTv];
+    __shared__ TileInfo info[NSTv];
+    __shared__ int s_err;
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const uint64_t wait_lim = g_tma_wait_limit_ns;
+    if (tid == 0) {
+        for (int s = 0; s < NSTv; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], NW);
+        }
+        s_err = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const bool has_u = HASU && a.u >= 0, has_a = a.a >= 0;
+    int issued = 0;
+    if (warp == NW) {
+        if (lane == 0)
+            issued = tma_produce<R, BYv, NSTv, EPI, HASU>(probs, tbase, nprob, ntiles, mapset, a, smem, full,
+                                                          empty, info, &s_err, tma_stage_bytes<R, BYv, EPI, HASU>(a),
+                                                          wait_lim);
+    } else {
+        const int tx2 = tid % CPR, ty = tid / CPR;
+        const int c0 = 2 * tx2;                 // first of the two tile columns
+        const int cs = c0 + TX;                 // its staged column (even: 8-byte aligned)
+        const int r0 = NR * ty;                 // first tile row of this thread
+        const float2 cx2 = f2s(a.fcx), cu2 = f2s(a.fcu), ck2 = f2s(a.fck), ca2 = f2s(a.fca);
+        const float2 cay2 = f2s(a.fcay), cau2 = f2s(a.fcau), cak2 = f2s(a.fcak), cax2 = f2s(a.fcax);
+        int it = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+            const int s = it % NSTv;
+            const uint32_t ph = (uint32_t)(it / NSTv) & 1u;
+            if (!mbar_wait(&full[s], ph, wait_lim)) {
+                s_err = 1;
+                break;
+            }
+            const TileInfo ti = load_info(&info[s]);
+            const float* st = smem + (size_t)s * L::FLOATS;
+            const int nx = ti.nx, ny = ti.ny;
+            const int i0 = ti.x0 + c0;
+            const int jt = ti.y0 + r0;
+            if (i0 < nx && jt < ny) {
+                if (ti.fs != 0 && jt < 4) {
+                    // free-surface band: one point at a time
+#pragma unroll 1
+                    for (int r = 0; r < NR; ++r) {
+                        tma_point_scalar<R, BYv, EPI, HASU>(st, ti, a, c0, r0 + r, has_u, has_a);
+                        tma_point_scalar<R, BYv, EPI, HASU>(st, ti, a, c0 + 1, r0 + r, has_u, has_a);
+                    }
+                } else {
+                    const float* su = st + L::U_OFF;
+                    const float* swx = st + L::WX_OFF;
+                    const float* swy = st + L::WY_OFF;
+                    const float* sv = st + L::V_OFF;
+                    const float* sc2 = st + L::C2_OFF;
+                    const float* spu = st + L::PU_OFF;
+                    const float* spa = st + L::PA_OFF;
+                    const bool fs = ti.fs != 0;
+                    const bool in1 = i0 + 1 < nx;
+                    float2 ucol[NR + 2 * R], wcol[NR + 2 * R - 1];
+#pragma unroll
+                    for (int q = 0; q < NR + 2 * R; ++q) ucol[q] = lds2(su + (r0 + q) * L::SW + cs);
+#pragma unroll
+                    for (int q = 0; q < NR + 2 * R - 1; ++q) wcol[q] = lds2(swy + (r0 + q) * BX + c0);
+                    const float* btab = ti.btab;
+                    const int nbt = ti.nbtab;
+                    const float2 bxn = f2(btab_at(btab, nbt, 2 * min(i0 + 1, nx - i0)),
+                                          btab_at(btab, nbt, 2 * min(i0 + 2, nx - i0 - 1)));
+                    const float2 bxh = f2(btab_at(btab, nbt, min(2 * i0 + 3, 2 * (nx - i0) - 1)),
+                                          btab_at(btab, nbt, min(2 * i0 + 5, 2 * (nx - i0) - 3)));
+                    const float2 nbxh = f2(-bxh.x, -bxh.y);
+                    const bool wx0in = i0 < nx - 1, wx1in = i0 + 1 < nx - 1;
+                    const float2 idx1 = f2s(ti.idx1), idx2 = f2s(ti.idx2);
+                    const float chx = a.fch * ti.xs;
+                    const float2 chx2 = f2s(chx);
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        const int lr = r0 + r, j = jt + r;
+                        if (j >= ny) break;
+                        // x taps: u and w_x at tile columns c0 - 4 .. c0 + 5 of this row
+                        const float* urow = su + (lr + R) * L::SW + cs;
+                        const float* wxr = swx + lr * L::SW + cs;
+                        const float2 up[5] = {lds2(urow - 4), lds2(urow - 2), ucol[r + R], lds2(urow + 2),
+                                              lds2(urow + 4)};
+                        const float2 wp[5] = {lds2(wxr - 4), lds2(wxr - 2), lds2(wxr), lds2(wxr + 2),
+                                              lds2(wxr + 4)};
+                        // scalar tap at column offset d (-4 .. 5) from the first column
+                        auto uo = [&](int d) { return ((d + 4) & 1) ? up[(d + 4) >> 1].y : up[(d + 4) >> 1].x; };
+                        auto wo = [&](int d) { return ((d + 4) & 1) ? wp[(d + 4) >> 1].y : wp[(d + 4) >> 1].x; };
+                        const float2 uc = ucol[r + R];
+                        float2 lap = mul2(f2s(2.f * cent<R>(0)), uc);
+                        float2 dux = f2s(0.f), duy = f2s(0.f), dw = f2s(0.f);
+#pragma unroll
+                        for (int k = 0; k < R; ++k) {
+                            // Laplacian: x and y pair sums at distance k + 1
+                            const int kk = k + 1;
+                            const float2 sx = (kk & 1) ? f2(uo(kk) + uo(-kk), uo(kk + 1) + uo(1 - kk))
+                                                       : add2(up[(kk + 4) >> 1], up[(4 - kk) >> 1]);
+                            const float2 sy = add2(ucol[r + R + kk], ucol[r + R - kk]);
+                            lap = fma2(f2s(cent<R>(kk)), add2(sx, sy), lap);
+                            // staggered differences: d_x u at x + 1/2, d_y u at y + 1/2,
+                            // the divergence of w at the node
+                            const float2 dxu = f2(uo(1 + k) - uo(-k), uo(2 + k) - uo(1 - k));
+                            dux = fma2(f2s(stag<R>(k)), dxu, dux);
+                            duy = fma2(f2s(stag<R>(k)), sub2(ucol[r + R - k], ucol[r + R + 1 + k]), duy);
+                            const float2 dxw = f2(wo(k) - wo(-1 - k), wo(1 + k) - wo(-k));
+                            const float2 dyw = sub2(wcol[r + R - 1 - k], wcol[r + R + k]);
+                            dw = fma2(f2s(stag<R>(k)), add2(dxw, dyw), dw);
+                        }
+                        const float byn = btab_at(btab, nbt, 2 * (fs ? ny - j : min(j + 1, ny - j)));
+                        const float byh =
+                            btab_at(btab, nbt, fs ? 2 * (ny - j) - 1 : min(2 * j + 3, 2 * (ny - j) - 1));
+                        const int pt = lr * BX + c0;
+                        const float2 xv = lds2(sv + pt), c2 = lds2(sc2 + pt);
+                        const float2 xwx = wp[2], xwy = wcol[r + R];
+                        // H v = -bx by u + c^2 (lap u / dx^2 + div w / dx) - (bx + by) v
+                        const float2 t = fma2(mul2(bxn, f2s(-byn)), uc, mul2(sub2(f2s(-byn), bxn), xv));
+                        float2 hv = fma2(c2, fma2(lap, idx2, mul2(dw, idx1)), t);
+                        if (j == ti.src_j) {
+                            if (i0 == ti.src_i) hv.x += ti.sig;
+                            if (i0 + 1 == ti.src_i) hv.y += ti.sig;
+                        }
+                        float2 hwx = fma2(nbxh, xwx, mul2(mul2(sub2(f2s(byn), bxh), dux), idx1));
+                        if (!wx0in) hwx.x = 0.f;
+                        if (!wx1in) hwx.y = 0.f;
+                        const bool wyin = j < ny - 1;
+                        const float2 hwy =
+                            wyin ? fma2(f2s(-byh), xwy, mul2(mul2(sub2(bxn, f2s(byh)), duy), idx1)) : f2s(0.f);
+                        const float2 xf[4] = {uc, xv, xwx, xwy};
+                        const float2 hf[4] = {xv, hv, hwx, hwy};
+                        const long long o = (long long)j * ti.pitch + i0;
+#pragma unroll
+                        for (int f = 0; f < 4; ++f) {
+                            const float2 uval = has_u ? lds2(spu + f * BYv * BX + pt) : f2s(0.f);
+                            const float2 aval = has_a ? lds2(spa + f * BYv * BX + pt) : f2s(0.f);
+                            const float2 kf = fma2(cx2, xf[f], mul2(chx2, hf[f]));
+                            float2 yf, af;
+                            if constexpr (EPI == 1) {
+                                yf = has_u ? fma2(cu2, uval, kf) : kf;
+                            } else {
+                                yf = fma2(cu2, uval, mul2(ck2, kf));
+                            }
+                            if (f == 2) {
+                                if (!wx0in) yf.x = 0.f;
+                                if (!wx1in) yf.y = 0.f;
+                            }
+                            if (f == 3 && !wyin) yf = f2s(0.f);
+                            if constexpr (EPI == 1) {
+                                af = has_a ? fma2(cay2, yf, mul2(ca2, aval)) : mul2(cay2, yf);
+                            } else {
+                                af = fma2(cax2, xf[f],
+                                          fma2(cay2, yf, fma2(cak2, kf, fma2(cau2, uval, mul2(ca2, aval)))));
+                                if (f == 2) {
+                                    if (!wx0in) af.x = 0.f;
+                                    if (!wx1in) af.y = 0.f;
+                                }
+                                if (f == 3 && !wyin) af = f2s(0.f);
+                            }
+                            if (ti.Y) st2(ti.Y + f * ti.fstr + o, yf, in1);
+                            if (ti.A) st2(ti.A + f * ti.fstr + o, af, in1);
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+        }
+    }
+    __syncthreads();
+    tma_finish<NSTv>(s_err, issued, full, err);
+}
 
 // ---------------------------------------------------------------- host side
 static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -776,11 +1106,14 @@ int build_tensor_maps(std::vector<ProblemDev>& probs, int R, const std::vector<i
 // Variant 5 keeps two rows per consumer thread with 20 warps (64 x 20 tiles): 21 warps per
 // SM, which caps a thread at 80 registers (six warps share one scheduler's register file).
 // Variant 6 uses 18 warps (64 x 18 tiles): 19 warps per SM, still 96 registers a thread.
+// Variants 7 to 9 run the column-pair consumers (two columns per thread): 7 = 64 x 18 tiles
+// with 9 warps (two rows a thread), 8 = 64 x 16 with 8 warps (two rows), 9 = 64 x 18 with
+// 18 warps (one row).
 struct TmaVariant {
     int by, nw, nst;
 };
-constexpr TmaVariant kVariants[TMA_NUM_VARIANTS] = {{16, 16, 3}, {16, 8, 3}, {8, 8, 5}, {8, 16, 5},
-                                                    {16, 16, 4}, {20, 20, 3}, {18, 18, 3}};
+constexpr TmaVariant kVariants[TMA_NUM_VARIANTS] = {{16, 16, 3}, {16, 8, 3}, {8, 8, 5},  {8, 16, 5}, {16, 16, 4},
+                                                    {20, 20, 3}, {18, 18, 3}, {18, 9, 3}, {16, 8, 3}, {18, 18, 3}};
 
 int tma_variant_tile_height(int v) { return kVariants[v].by; }
 void tma_variant_describe(int v, int* by, int* nw, int* nst) {
@@ -807,6 +1140,25 @@ static int launch_variant(const ProblemDev* probs, const int* tbase, int nprob, 
     }
     const int grid = ntiles < g_num_sms ? ntiles : g_num_sms;
     stage_tma_kernel<R, BYv, NW, NSTv, EPI, HASU><<<grid, NW * 32 + 32, smem, s>>>(
+        probs, tbase, nprob, ntiles, map_set_of(BYv), a, err);
+    return 0;
+}
+
+template <int R, int BYv, int NW, int NSTv, int EPI, bool HASU = true>
+static int launch_x2(const ProblemDev* probs, const int* tbase, int nprob, int ntiles, const StageArgs& a,
+                     int* err, cudaStream_t s) {
+    const size_t smem = (size_t)NSTv * StageLayout<R, BYv, HASU>::BYTES + 1024;
+    static unsigned long long configured = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return -1;
+    if (!(configured >> dev & 1ull)) {
+        if (cudaFuncSetAttribute(stage_tma_x2_kernel<R, BYv, NW, NSTv, EPI, HASU>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return -1;
+        configured |= 1ull << dev;
+    }
+    const int grid = ntiles < g_num_sms ? ntiles : g_num_sms;
+    stage_tma_x2_kernel<R, BYv, NW, NSTv, EPI, HASU><<<grid, NW * 32 + 32, smem, s>>>(
         probs, tbase, nprob, ntiles, map_set_of(BYv), a, err);
     return 0;
 }
@@ -890,6 +1242,17 @@ int launch_stage_tma(int variant, int R, const ProblemDev* probs, const int* tba
     EWV_TMA_CASE(3, 4, 8, 16, 5)
     EWV_TMA_CASE(5, 4, 20, 20, 3)
     EWV_TMA_CASE(6, 4, 18, 18, 3)
+#define EWV_TMA_X2_CASE(V, RR, BYV, NWV, NSTV) \
+    if (variant == V && R == RR)                                                             \
+        return epi ? launch_x2<RR, BYV, NWV, NSTV, 1>(probs, tbase, nprob, ntiles, a, err, s) \
+                   : launch_x2<RR, BYV, NWV, NSTV, 0>(probs, tbase, nprob, ntiles, a, err, s);
+    EWV_TMA_X2_CASE(7, 4, 18, 9, 3)
+    EWV_TMA_X2_CASE(8, 4, 16, 8, 3)
+    EWV_TMA_X2_CASE(9, 4, 18, 18, 3)
+    EWV_TMA_X2_CASE(7, 2, 18, 9, 3)
+    EWV_TMA_X2_CASE(8, 2, 16, 8, 3)
+    EWV_TMA_X2_CASE(9, 2, 18, 18, 3)
+#undef EWV_TMA_X2_CASE
     if (variant == 4) {   // no U buffer; a pass with a U operand runs variant 0
         if (a.u >= 0) variant = 0;
         else if (R == 4)

@@ -165,9 +165,13 @@ def load_library(path=LIB_PATH):
     return lib
 
 
+# persistent-pass variants the autotuner times (EWV_NUM_KERNEL_VARIANTS)
+NUM_KERNEL_VARIANTS = 10
+
+
 def _variant(fn, h, check):
     v, by, nw, nst = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    us = (ctypes.c_double * 7)()
+    us = (ctypes.c_double * NUM_KERNEL_VARIANTS)()
     check(fn(h, ctypes.byref(v), ctypes.byref(by), ctypes.byref(nw), ctypes.byref(nst), us))
     return {"variant": v.value, "tile": [64, by.value], "consumer_warps": nw.value,
             "stages": nst.value, "probe_us": list(us)}
