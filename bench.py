@@ -43,7 +43,7 @@ PICKS = [(0, 32), (1, 0), (5, 0)]
 CHECK_PROBLEMS = [(q, 0) for q in range(1, 9)] + [(0, k) for k in (0, 9, 18, 27, 32, 36, 45, 54, 63)]
 # Cheapest candidate found by the in-run search on GB300 (used by the CPU reference arm; the
 # GPU arm re-runs the search and reports what it finds).
-DEFAULT_SELECTION = ("hork-horner", 24, 5)     # method, m, dt in units of the leap-frog step
+DEFAULT_SELECTION = ("hork-horner", 20, 4)     # method, m, dt in units of the leap-frog step
 WORKLOAD_NAME = ("batched: 64 shots on 1001x501 + 8 models 201x101..801x401, layered "
                  "1500-4500 m/s, 8th order, free surface, 40-pt PML, Ricker 10 Hz, T=2 s")
 
@@ -320,8 +320,12 @@ def fp64_single_shot_estimate(wl, method, m, dt, nsteps, c_max, steps_sample=3):
 
 def fwi_gradient_step(method, m, dt_over_cfl):
     """FWI gradient (forward + adjoint) on the 401 x 201, 16-shot, 200-receiver workload,
-    FP32, with the given integrator (exact discrete adjoints of the computed steps, Krylov
-    included) at its m and step ratio; every state checkpointed."""
+    FP32, with the given integrator at its m and step ratio; every state checkpointed.  The
+    polynomial steps take their exact discrete adjoints; Krylov takes the adjoint of the
+    step's exponential, because the exact adjoint of a Krylov step of dimension 20 at 8 x
+    the leap-frog step is ill-conditioned over this run (its cotangent grows without bound
+    while the source is still silent); tests/test_gpu_fwi.py checks both against central
+    differences on this workload."""
     import numpy as np
     import torch
     from paper_2401_16322_gb300.fwi import FaberFWI
@@ -335,6 +339,8 @@ def fwi_gradient_step(method, m, dt_over_cfl):
     nsteps = int(round(w.T / dt))
     md = build_models([w], "f32", p=12, c_max=c_max)[0]
     common_ellipse([md], c_max)
+    if method == "krylov":
+        md.set_krylov_adjoint("exponential")
     fwi = FaberFWI(md, dt, m, nsteps, len(w.shots[0].rec), method=base_method([md], method))
     d_obs = fwi.forward(w.c ** 2)
     c_init = smooth_gradient_with_anomalies(w.nx, w.ny, 0, dx=w.dx, amps=())
@@ -352,8 +358,8 @@ def fwi_gradient_step(method, m, dt_over_cfl):
     md.close()
     return {"seconds": e0.elapsed_time(e1) * 1e-3, "forward_s": e0.elapsed_time(em) * 1e-3,
             "backward_s": em.elapsed_time(e1) * 1e-3, "method": method, "nsteps": nsteps,
-            "adjoint": ("exact discrete adjoint of the computed Krylov steps (reverse mode through "
-                        "Arnoldi)" if method == "krylov" else "exact discrete adjoint"),
+            "adjoint": ("adjoint of the step's exponential (FD-checked to 2e-3 on this workload)"
+                        if method == "krylov" else "exact discrete adjoint"),
             "dt_ms": dt * 1e3, "m": m,
             "shots": len(w.shots), "grid": f"{w.nx}x{w.ny}", "checkpoint_bytes": mem,
             "gradient_finite": ok}

@@ -233,7 +233,9 @@ int ewv_apply_operator(ewv_model_t model, int transpose, const void* x, void* y)
 int ewv_step_faber(ewv_model_t model, double t, double dt, int degree, int nsteps);
 
 /* Sec. 3.2 Krylov: Arnoldi (MGS) on dt H~ with m matrix-vector products, exp of the m x m
- * Hessenberg by [13/13] Pade with scaling and squaring.  *info (may be NULL) receives the
+ * Hessenberg by [13/13] Pade with scaling and squaring.  The start vector is [U^n; eta e_p]
+ * with the source column scaled by 1/eta, eta = |U^n| (1 if U^n = 0), which leaves the
+ * exponential unchanged and keeps the wavefield and the tail on one scale.  *info (may be NULL) receives the
  * smallest effective dimension over shots and steps (< m after a happy breakdown); with a
  * non-NULL info the call waits for the GPU to read it and returns EWV_ERR_NONFINITE itself
  * when the Arnoldi process met a non-finite value.  With info NULL it returns after
@@ -426,8 +428,12 @@ int ewv_batch_enable_graphs(ewv_batch_t batch, int enable);
 /* Tile-shape autotuner of the FP32 persistent TMA pass.  Variants (tile height, consumer
  * warps, pipeline stages): 0 = (16, 16, 3), 1 = (16, 8, 3), 2 = (8, 8, 5), 3 = (8, 16, 5),
  * 5 = (20, 20, 3), 6 = (18, 18, 3), each consumer thread on one column; 7 = (18, 9, 3),
- * 8 = (16, 8, 3), 9 = (18, 18, 3), each consumer thread on two adjacent columns (8-byte
- * shared loads, packed FP32 pair arithmetic); the leap-frog step and the gradient pass
+ * 8 = (16, 8, 3), 9 = (18, 18, 3), 10 = (24, 12, 2), each consumer thread on two adjacent
+ * columns (8-byte shared loads, packed FP32 pair arithmetic); 11 = (24, 12, 3) and
+ * 12 = (36, 9, 2) are composite: passes without an A operand (Horner HORK passes, Krylov
+ * products) run these column-pair shapes without the A stage buffer, passes with one run
+ * variant 7 (the reported shape is the no-A one).  The autotuner's score is the sum of a
+ * probe pass with and one without an A operand.  The leap-frog step and the gradient pass
  * always run the one-column form (18, 18);
  * tiles are 64 columns wide with a 4-column / R-row halo.  With v = -1 (default) the first
  * FP32 step call times every variant on a probe pass over the engine's own problems and
@@ -436,7 +442,7 @@ int ewv_batch_enable_graphs(ewv_batch_t batch, int enable);
  * 4) without the U stage buffer: passes that read a U vector run variant 0 under it.
  * 3D models: 0 (default) = TMA pipeline with 16 consumer warps, 2 = 8 warps, 1 = plain
  * z-marching kernel. */
-#define EWV_NUM_KERNEL_VARIANTS 10
+#define EWV_NUM_KERNEL_VARIANTS 13
 int ewv_set_kernel_variant(ewv_model_t model, int variant);
 int ewv_kernel_variant(ewv_model_t model, int* variant, int* tile_height, int* warps,
                        int* stages, double* probe_us);

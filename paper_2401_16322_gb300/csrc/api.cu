@@ -645,7 +645,7 @@ struct Ctx {
             if (E->tma_variant < 0) {
                 launch_failed = 1;
             } else {
-                const int set = tma_map_set(tma_variant_tile_height(E->tma_variant));
+                const int set = tma_map_set(tma_variant_tile_height_for(E->tma_variant, a.a >= 0));
                 if (launch_stage_tma(E->tma_variant, E->R, E->d_probs, E->d_tbase + (size_t)set * (E->nprob + 1),
                                      E->nprob, E->ntiles_by[set], a, E->d_err, s) != 0)
                     launch_failed = 1;
@@ -662,9 +662,11 @@ struct Ctx {
             launch_point(E->precision, E->ntiles, E->d_probs, E->d_tile_prob, pa, s);
         ++*launches;
     }
-    // Tile-shape autotuner: time every persistent-kernel variant on an idempotent probe pass
-    // (reads the state, writes workspace vectors 1 and 2, which every FP32 method overwrites
-    // before reading) and keep the fastest.  Runs once per engine, outside graph capture.
+    // Tile-shape autotuner: time every persistent-kernel variant on two idempotent probe
+    // passes (read the state, write workspace vectors 1 and 2, which every FP32 method
+    // overwrites before reading): one with a U and an A operand (the Faber and low-storage
+    // HORK form) and one with U only (the Horner HORK form); keep the variant with the
+    // smallest sum.  Runs once per engine, outside graph capture.
     void autotune() {
         StageArgs p = stage_defaults();
         p.x = 0;
@@ -678,15 +680,23 @@ struct Ctx {
         p.ck = 1.0;
         p.ca = 1.0;
         p.cay = 1.0;
+        StageArgs pn = p;           // no A operand, no accumulator
+        pn.a = -1;
+        pn.acc_out = -1;
+        pn.ca = 0.0;
+        pn.cay = 0.0;
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         int best = -1;
         double best_us = 1e300;
         for (int v = 0; v < TMA_NUM_VARIANTS; ++v) {
-            const int set = tma_map_set(tma_variant_tile_height(v));
+            const int set = tma_map_set(tma_variant_tile_height_for(v, true));
+            const int setn = tma_map_set(tma_variant_tile_height_for(v, false));
             const int* tb = E->d_tbase + (size_t)set * (E->nprob + 1);
+            const int* tbn = E->d_tbase + (size_t)setn * (E->nprob + 1);
             if (launch_stage_tma(v, E->R, E->d_probs, tb, E->nprob, E->ntiles_by[set], p, E->d_err, s) != 0 ||
+                launch_stage_tma(v, E->R, E->d_probs, tbn, E->nprob, E->ntiles_by[setn], pn, E->d_err, s) != 0 ||
                 cudaGetLastError() != cudaSuccess) {
                 E->tma_variant_us[v] = -1.0;
                 continue;
@@ -695,6 +705,7 @@ struct Ctx {
             for (int rep = 0; rep < 3; ++rep) {
                 cudaEventRecord(e0, s);
                 launch_stage_tma(v, E->R, E->d_probs, tb, E->nprob, E->ntiles_by[set], p, E->d_err, s);
+                launch_stage_tma(v, E->R, E->d_probs, tbn, E->nprob, E->ntiles_by[setn], pn, E->d_err, s);
                 cudaEventRecord(e1, s);
                 cudaEventSynchronize(e1);
                 float ms = 0.f;
@@ -718,7 +729,7 @@ struct Ctx {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         E->tma_variant = best;
-        *launches += 4 * TMA_NUM_VARIANTS;
+        *launches += 8 * TMA_NUM_VARIANTS;
     }
     void copy(int src, int dst, int fmask, bool swap) {
         PointArgs pa{};
@@ -2718,7 +2729,9 @@ int ewv_adjoint_step(ewv_model_t m, int method, double t, double dt, int deg,
         CUDA_OR_FAIL(m->err, cudaMemcpyAsync(E->d_adj, probs.data(), sizeof(ProblemDev) * ns,
                                              cudaMemcpyHostToDevice, s));
     }
-    const int tset = tma_adj ? tma_map_set(tma_variant_tile_height(E->tma_variant)) : 0;
+    auto tset_of = [&](const StageArgs& sa) {
+        return tma_map_set(tma_variant_tile_height_for(E->tma_variant, sa.a >= 0));
+    };
     const int gset = tma_map_set(18);
     auto stage = [&](const StageArgs& sa) {
         if (tma_adj && !sa.transpose && sa.grad && sa.fin_mode == FIN_NONE && sa.d < 0 &&
@@ -2728,8 +2741,8 @@ int ewv_adjoint_step(ewv_model_t m, int method, double t, double dt, int deg,
             return;
         }
         if (tma_adj && !sa.transpose && !sa.grad && sa.fin_mode == FIN_NONE && sa.d < 0 &&
-            launch_stage_tma(E->tma_variant, R, E->d_adj, E->d_tbase + (size_t)tset * (E->nprob + 1), ns,
-                             E->ntiles_by[tset], sa, E->d_err, s) == 0) {
+            launch_stage_tma(E->tma_variant, R, E->d_adj, E->d_tbase + (size_t)tset_of(sa) * (E->nprob + 1), ns,
+                             E->ntiles_by[tset_of(sa)], sa, E->d_err, s) == 0) {
             ++m->launches;
             return;
         }

@@ -185,7 +185,7 @@ int launch_leapfrog_tma3d(int R, int warps, const ProblemDev* probs, const int* 
 int upload_tma_tables(const double* fs_uyy, const double* fs_uy, const double* fs_dwy);
 int build_tensor_maps(std::vector<ProblemDev>& probs, int R, const std::vector<int>& work_vecs,
                       void** d_maps_inout);
-constexpr int TMA_NUM_VARIANTS = 10;
+constexpr int TMA_NUM_VARIANTS = 13;
 // One 2D FP32 leap-frog step through the persistent TMA pass (64 x 18 tiles); tbase and
 // ntiles are those of the 18-row map set.
 int launch_leapfrog_tma(int R, const ProblemDev* probs, const int* tbase, int nprob, int ntiles, int cur,
@@ -196,9 +196,12 @@ int launch_grad_tma(int R, const ProblemDev* probs, const int* tbase, int nprob,
 int launch_stage_tma(int variant, int R, const ProblemDev* probs, const int* tbase, int nprob,
                      int ntiles, const StageArgs& a, int* err, cudaStream_t s);
 int tma_variant_tile_height(int v);
+// Tile height of variant v for a pass that does (reads_a) or does not read an A operand
+// (composite variants pick their tile by it).
+int tma_variant_tile_height_for(int v, bool reads_a);
 // Tile heights of the 2D TMA map sets (set k has tile height TMA_SET_HEIGHTS[k]).
-constexpr int TMA_NUM_SETS = 4;
-constexpr int TMA_SET_HEIGHTS[TMA_NUM_SETS] = {16, 8, 20, 18};
+constexpr int TMA_NUM_SETS = 6;
+constexpr int TMA_SET_HEIGHTS[TMA_NUM_SETS] = {16, 8, 20, 18, 24, 36};
 int tma_map_set(int tile_height);
 void tma_variant_describe(int v, int* by, int* nw, int* nst);
 

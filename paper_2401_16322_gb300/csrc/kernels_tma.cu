@@ -31,8 +31,9 @@ constexpr int MAX_NST = 5;
 
 // Shared-memory layout of one stage (floats) for tile height BYv; every buffer starts on a
 // 128-byte boundary.  HASU = false drops the U buffer (passes without a U operand, e.g. the
-// HORK stages), so that more stages fit in shared memory.
-template <int R, int BYv, bool HASU = true>
+// HORK stages) and HASA = false the A buffer (passes without an A operand: the Horner HORK
+// passes, the Krylov products), so that more stages or taller tiles fit in shared memory.
+template <int R, int BYv, bool HASU = true, bool HASA = true>
 struct StageLayout {
     static constexpr int up32(int v) { return (v + 31) / 32 * 32; }   // 128-byte boundary
     static constexpr int SH = BYv + 2 * R;
@@ -44,7 +45,7 @@ struct StageLayout {
     static constexpr int C2_OFF = V_OFF + BYv * BX;                // c^2    BYv x BX
     static constexpr int PU_OFF = C2_OFF + BYv * BX;               // U      4 x BYv x BX
     static constexpr int PA_OFF = PU_OFF + (HASU ? 4 * BYv * BX : 0);   // A  4 x BYv x BX
-    static constexpr int FLOATS = PA_OFF + 4 * BYv * BX;
+    static constexpr int FLOATS = PA_OFF + (HASA ? 4 * BYv * BX : 0);
     // floats the five field boxes deliver (the padding between buffers is not written)
     static constexpr int BOX_FLOATS = SH * SW + BYv * SW + SH * BX + 2 * BYv * BX;
     static constexpr int BYTES = FLOATS * 4;
@@ -273,13 +274,13 @@ __device__ __forceinline__ int find_problem(const int* __restrict__ base, int np
 // The producer (one elected lane of the last warp): for each tile of this CTA, wait until
 // its stage is free, resolve the tile's problem and descriptor, arm the stage's "full"
 // barrier with the byte count and issue the TMA loads.  Returns the number of tiles issued.
-template <int R, int BYv, int NSTv, int EPI, bool HASU>
+template <int R, int BYv, int NSTv, int EPI, bool HASU, bool HASA = true>
 __device__ __forceinline__ int tma_produce(const ProblemDev* __restrict__ probs, const int* __restrict__ tbase,
                                            int nprob, int ntiles, int mapset, const StageArgs& a, float* smem,
                                            uint64_t* full, uint64_t* empty, TileInfo* info, int* s_err,
                                            uint32_t bytes, uint64_t wait_lim) {
-    using L = StageLayout<R, BYv, HASU>;
-    const bool has_u = HASU && a.u >= 0, has_a = a.a >= 0;
+    using L = StageLayout<R, BYv, HASU, HASA>;
+    const bool has_u = HASU && a.u >= 0, has_a = HASA && a.a >= 0;
     int issued = 0;
     int it = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
@@ -340,10 +341,10 @@ __device__ __forceinline__ int tma_produce(const ProblemDev* __restrict__ probs,
 }
 
 // Byte count one stage receives (the "full" barrier's transaction count).
-template <int R, int BYv, int EPI, bool HASU>
+template <int R, int BYv, int EPI, bool HASU, bool HASA = true>
 __device__ __forceinline__ uint32_t tma_stage_bytes(const StageArgs& a) {
-    using L = StageLayout<R, BYv, HASU>;
-    const bool has_u = HASU && a.u >= 0, has_a = a.a >= 0;
+    using L = StageLayout<R, BYv, HASU, HASA>;
+    const bool has_u = HASU && a.u >= 0, has_a = HASA && a.a >= 0;
     // (the leap-frog step, EPI 2, does not read v; the gradient pass, EPI 3, neither v nor c^2)
     return (uint32_t)((L::BOX_FLOATS - (EPI >= 2 ? BYv * BX : 0) - (EPI == 3 ? BYv * BX : 0) +
                        (has_u ? 4 * BYv * BX : 0)) * 4) +
@@ -729,10 +730,10 @@ __device__ __forceinline__ void st2(float* p, float2 v, bool both) {
 
 // One point (tile column tc, tile row lr) from shared memory with the scalar formulas of the
 // one-column form, free-surface rows included, and its epilogue.
-template <int R, int BYv, int EPI, bool HASU>
+template <int R, int BYv, int EPI, bool HASU, bool HASA>
 __device__ __forceinline__ void tma_point_scalar(const float* st, const TileInfo& ti, const StageArgs& a, int tc,
                                              int lr, bool has_u, bool has_a) {
-    using L = StageLayout<R, BYv, HASU>;
+    using L = StageLayout<R, BYv, HASU, HASA>;
     const int nx = ti.nx, ny = ti.ny;
     const int i = ti.x0 + tc, j = ti.y0 + lr;
     if (i >= nx || j >= ny) return;
@@ -824,12 +825,12 @@ __device__ __forceinline__ void tma_point_scalar(const float* st, const TileInfo
     }
 }
 
-template <int R, int BYv, int NW, int NSTv, int EPI, bool HASU>
+template <int R, int BYv, int NW, int NSTv, int EPI, bool HASU, bool HASA>
 __global__ void __launch_bounds__(NW * 32 + 32, 1)
 stage_tma_x2_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ tbase, int nprob,
                     int ntiles, int mapset, StageArgs a, int* err) {
     static_assert(EPI <= 1, "the column-pair consumers serve the integrator passes");
-    using L = StageLayout<R, BYv, HASU>;
+    using L = StageLayout<R, BYv, HASU, HASA>;
     constexpr int CPR = BX / 2;                 // consumer threads per tile row
     constexpr int TPR = NW * 32 / CPR;          // thread rows
     constexpr int NR = BYv / TPR;               // consecutive rows per consumer thread
@@ -853,13 +854,13 @@ stage_tma_x2_kernel(const ProblemDev* __restrict__ probs, const int* __restrict_
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    const bool has_u = HASU && a.u >= 0, has_a = a.a >= 0;
+    const bool has_u = HASU && a.u >= 0, has_a = HASA && a.a >= 0;
     int issued = 0;
     if (warp == NW) {
         if (lane == 0)
-            issued = tma_produce<R, BYv, NSTv, EPI, HASU>(probs, tbase, nprob, ntiles, mapset, a, smem, full,
-                                                          empty, info, &s_err, tma_stage_bytes<R, BYv, EPI, HASU>(a),
-                                                          wait_lim);
+            issued = tma_produce<R, BYv, NSTv, EPI, HASU, HASA>(
+                probs, tbase, nprob, ntiles, mapset, a, smem, full, empty, info, &s_err,
+                tma_stage_bytes<R, BYv, EPI, HASU, HASA>(a), wait_lim);
     } else {
         const int tx2 = tid % CPR, ty = tid / CPR;
         const int c0 = 2 * tx2;                 // first of the two tile columns
@@ -885,8 +886,8 @@ stage_tma_x2_kernel(const ProblemDev* __restrict__ probs, const int* __restrict_
                     // free-surface band: one point at a time
 #pragma unroll 1
                     for (int r = 0; r < NR; ++r) {
-                        tma_point_scalar<R, BYv, EPI, HASU>(st, ti, a, c0, r0 + r, has_u, has_a);
-                        tma_point_scalar<R, BYv, EPI, HASU>(st, ti, a, c0 + 1, r0 + r, has_u, has_a);
+                        tma_point_scalar<R, BYv, EPI, HASU, HASA>(st, ti, a, c0, r0 + r, has_u, has_a);
+                        tma_point_scalar<R, BYv, EPI, HASU, HASA>(st, ti, a, c0 + 1, r0 + r, has_u, has_a);
                     }
                 } else {
                     const float* su = st + L::U_OFF;
@@ -1054,9 +1055,13 @@ int tma_map_set(int tile_height) {
         if (TMA_SET_HEIGHTS[k] == tile_height) return k;
     return -1;
 }
-constexpr int map_set_of(int by) { return by == 16 ? 0 : (by == 8 ? 1 : (by == 20 ? 2 : 3)); }
+constexpr int map_set_of(int by) {
+    return by == 16 ? 0 : by == 8 ? 1 : by == 20 ? 2 : by == 18 ? 3 : by == 24 ? 4 : 5;
+}
 static_assert(map_set_of(16) == 0 && map_set_of(8) == 1 && map_set_of(20) == 2 && map_set_of(18) == 3 &&
-                  TMA_SET_HEIGHTS[2] == 20 && TMA_SET_HEIGHTS[3] == 18,
+                  map_set_of(24) == 4 && map_set_of(36) == 5 && TMA_SET_HEIGHTS[0] == 16 &&
+                  TMA_SET_HEIGHTS[1] == 8 && TMA_SET_HEIGHTS[2] == 20 && TMA_SET_HEIGHTS[3] == 18 &&
+                  TMA_SET_HEIGHTS[4] == 24 && TMA_SET_HEIGHTS[5] == 36,
               "map sets and tile heights must agree");
 
 // Build NMAP maps per problem and tile height (one map set per entry of TMA_SET_HEIGHTS)
@@ -1108,12 +1113,22 @@ int build_tensor_maps(std::vector<ProblemDev>& probs, int R, const std::vector<i
 // Variant 6 uses 18 warps (64 x 18 tiles): 19 warps per SM, still 96 registers a thread.
 // Variants 7 to 9 run the column-pair consumers (two columns per thread): 7 = 64 x 18 tiles
 // with 9 warps (two rows a thread), 8 = 64 x 16 with 8 warps (two rows), 9 = 64 x 18 with
-// 18 warps (one row).
+// 18 warps (one row), 10 = 64 x 24 with 12 warps and 2 stages (two rows).  11 and 12 are
+// composite: passes that read an A operand run variant 7, the others (Horner HORK passes,
+// Krylov products, leap-frog-free RK stages without an accumulator) drop the A buffer and
+// take taller tiles: 11 = 64 x 24 with 12 warps and 3 stages, 12 = 64 x 36 with 9 warps, four
+// rows a thread and 2 stages.  The shape reported for a composite is its no-A shape.
 struct TmaVariant {
     int by, nw, nst;
 };
-constexpr TmaVariant kVariants[TMA_NUM_VARIANTS] = {{16, 16, 3}, {16, 8, 3}, {8, 8, 5},  {8, 16, 5}, {16, 16, 4},
-                                                    {20, 20, 3}, {18, 18, 3}, {18, 9, 3}, {16, 8, 3}, {18, 18, 3}};
+constexpr TmaVariant kVariants[TMA_NUM_VARIANTS] = {
+    {16, 16, 3}, {16, 8, 3}, {8, 8, 5},  {8, 16, 5},  {16, 16, 4}, {20, 20, 3}, {18, 18, 3},
+    {18, 9, 3},  {16, 8, 3}, {18, 18, 3}, {24, 12, 2}, {24, 12, 3}, {36, 9, 2}};
+
+int tma_variant_tile_height_for(int v, bool reads_a) {
+    if ((v == 11 || v == 12) && reads_a) return kVariants[7].by;
+    return kVariants[v].by;
+}
 
 int tma_variant_tile_height(int v) { return kVariants[v].by; }
 void tma_variant_describe(int v, int* by, int* nw, int* nst) {
@@ -1144,21 +1159,22 @@ static int launch_variant(const ProblemDev* probs, const int* tbase, int nprob, 
     return 0;
 }
 
-template <int R, int BYv, int NW, int NSTv, int EPI, bool HASU = true>
+template <int R, int BYv, int NW, int NSTv, int EPI, bool HASA = true>
 static int launch_x2(const ProblemDev* probs, const int* tbase, int nprob, int ntiles, const StageArgs& a,
                      int* err, cudaStream_t s) {
-    const size_t smem = (size_t)NSTv * StageLayout<R, BYv, HASU>::BYTES + 1024;
+    if (!HASA && a.a >= 0) return -1;    // a pass with an A operand needs the A buffer
+    const size_t smem = (size_t)NSTv * StageLayout<R, BYv, true, HASA>::BYTES + 1024;
     static unsigned long long configured = 0;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return -1;
     if (!(configured >> dev & 1ull)) {
-        if (cudaFuncSetAttribute(stage_tma_x2_kernel<R, BYv, NW, NSTv, EPI, HASU>,
+        if (cudaFuncSetAttribute(stage_tma_x2_kernel<R, BYv, NW, NSTv, EPI, true, HASA>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return -1;
         configured |= 1ull << dev;
     }
     const int grid = ntiles < g_num_sms ? ntiles : g_num_sms;
-    stage_tma_x2_kernel<R, BYv, NW, NSTv, EPI, HASU><<<grid, NW * 32 + 32, smem, s>>>(
+    stage_tma_x2_kernel<R, BYv, NW, NSTv, EPI, true, HASA><<<grid, NW * 32 + 32, smem, s>>>(
         probs, tbase, nprob, ntiles, map_set_of(BYv), a, err);
     return 0;
 }
@@ -1246,12 +1262,24 @@ int launch_stage_tma(int variant, int R, const ProblemDev* probs, const int* tba
     if (variant == V && R == RR)                                                             \
         return epi ? launch_x2<RR, BYV, NWV, NSTV, 1>(probs, tbase, nprob, ntiles, a, err, s) \
                    : launch_x2<RR, BYV, NWV, NSTV, 0>(probs, tbase, nprob, ntiles, a, err, s);
+    if ((variant == 11 || variant == 12) && a.a >= 0) variant = 7;   // composite, pass with A
+#define EWV_TMA_X2_NOA_CASE(V, RR, BYV, NWV, NSTV) \
+    if (variant == V && R == RR)                                                                    \
+        return epi ? launch_x2<RR, BYV, NWV, NSTV, 1, false>(probs, tbase, nprob, ntiles, a, err, s) \
+                   : launch_x2<RR, BYV, NWV, NSTV, 0, false>(probs, tbase, nprob, ntiles, a, err, s);
     EWV_TMA_X2_CASE(7, 4, 18, 9, 3)
     EWV_TMA_X2_CASE(8, 4, 16, 8, 3)
     EWV_TMA_X2_CASE(9, 4, 18, 18, 3)
+    EWV_TMA_X2_CASE(10, 4, 24, 12, 2)
+    EWV_TMA_X2_NOA_CASE(11, 4, 24, 12, 3)
+    EWV_TMA_X2_NOA_CASE(12, 4, 36, 9, 2)
     EWV_TMA_X2_CASE(7, 2, 18, 9, 3)
     EWV_TMA_X2_CASE(8, 2, 16, 8, 3)
     EWV_TMA_X2_CASE(9, 2, 18, 18, 3)
+    EWV_TMA_X2_CASE(10, 2, 24, 12, 2)
+    EWV_TMA_X2_NOA_CASE(11, 2, 24, 12, 3)
+    EWV_TMA_X2_NOA_CASE(12, 2, 36, 9, 2)
+#undef EWV_TMA_X2_NOA_CASE
 #undef EWV_TMA_X2_CASE
     if (variant == 4) {   // no U buffer; a pass with a U operand runs variant 0
         if (a.u >= 0) variant = 0;

@@ -378,39 +378,63 @@ def test_krylov_exact_gradient_at_the_benchmark_setting(budget):
     assert abs(fd - float(np.sum(grad * dm))) <= 1e-3 * abs(fd)
 
 
-def test_krylov_gradient_central_differences_on_the_fwi_workload():
-    """The 16-shot FWI workload itself (401 x 201, 200 receivers, T = 1.5 s) with Krylov steps
-    of dimension 20 at 8 x the leap-frog step: in FP64 the exact discrete adjoint gradient
-    agrees with central differences of the misfit to 1e-3; the FP32 gradient is within 1e-2
-    of the FP64 one and agrees with FP32 central differences to 2e-2 (FP32 rounding of the
-    misfit limits that check)."""
+def _fwi_workload_fd(method, m, k, prec, eps, adjoint=None):
+    """(relative FD mismatch, gradient) of the FWI gradient on the 16-shot FWI workload
+    (401 x 201, 200 receivers, T = 1.5 s) at step k x the leap-frog step."""
     import torch
     from paper_2401_16322_gb300.fwi import FaberFWI
     from paper_2401_16322_gb300.tts import build_models, common_ellipse, leapfrog_step
     from paper_2401_16322_gb300.workloads import config_fwi, smooth_gradient_with_anomalies
     w = config_fwi()
     c_max = float(w.c.max()) * 1.05
-    dt = 8.0 * leapfrog_step(c_max, w.dx, w.order)
+    dt = k * leapfrog_step(c_max, w.dx, w.order)
     nsteps = int(round(w.T / dt))
     c_init = smooth_gradient_with_anomalies(w.nx, w.ny, 0, dx=w.dx, amps=())
     dm = smooth_random_state([(w.ny, w.nx)], 5, sigma_cells=8.0)[0] * 0.01 * c_init ** 2
-    grads, checks = {}, {}
-    for prec, eps in (("f64", 1e-3), ("f32", 1e-1)):
-        md = build_models([w], prec, p=12, c_max=c_max)[0]
-        common_ellipse([md], c_max)
-        fwi = FaberFWI(md, dt, 20, nsteps, len(w.shots[0].rec), method="krylov")
-        d_obs = fwi.forward(w.c ** 2).double()
-        seis = fwi.forward(c_init ** 2).double()
-        grad = fwi.backward(seis - d_obs).double().cpu().numpy()
+    md = build_models([w], prec, p=12, c_max=c_max)[0]
+    common_ellipse([md], c_max)
+    if adjoint:
+        md.set_krylov_adjoint(adjoint)
+    fwi = FaberFWI(md, dt, m, nsteps, len(w.shots[0].rec), method=method)
+    d_obs = fwi.forward(w.c ** 2).double()
+    seis = fwi.forward(c_init ** 2).double()
+    grad = fwi.backward(seis - d_obs).double().cpu().numpy()
 
-        def J(c2):
-            return 0.5 * float(((fwi.forward(c2).double() - d_obs) ** 2).sum())
+    def J(c2):
+        return 0.5 * float(((fwi.forward(c2).double() - d_obs) ** 2).sum())
 
-        fd = (J(c_init ** 2 + eps * dm) - J(c_init ** 2 - eps * dm)) / (2 * eps)
-        grads[prec] = grad
-        checks[prec] = abs(fd - float(np.sum(grad * dm))) / abs(fd)
-        md.close()
-        torch.cuda.empty_cache()
-    assert checks["f64"] <= 1e-3, checks
-    assert rel_l2(grads["f32"], grads["f64"]) < 1e-2, rel_l2(grads["f32"], grads["f64"])
-    assert checks["f32"] <= 2e-2, checks
+    fd = (J(c_init ** 2 + eps * dm) - J(c_init ** 2 - eps * dm)) / (2 * eps)
+    md.close()
+    torch.cuda.empty_cache()
+    return abs(fd - float(np.sum(grad * dm))) / abs(fd), grad
+
+
+def test_krylov_gradient_central_differences_on_the_fwi_workload():
+    """The 16-shot FWI workload itself: central differences of the GPU misfit against the
+    adjoint gradient.
+    - Krylov 20 at 4 x the leap-frog step, exact discrete adjoint, FP64: 1e-3 (measured
+      2.0e-5, the O(eps^2) term of the difference).
+    - Krylov 20 at 8 x (the benchmark setting), FP64: the exact adjoint of that step is
+      ill-conditioned over 148 steps (its cotangent grows by ~1e85 while the source is still
+      silent), so the FWI runs take the adjoint of the step's exponential, which agrees with
+      the differences of the computed Krylov misfit to the step's own accuracy: 2e-3
+      (measured 8.9e-4).
+    - FP32 at 8 x: the gradient is within 1e-3 of the FP64 one (measured 2.7e-4) and agrees
+      with FP32 differences to 1e-2 (measured 2.1e-3; FP32 rounding of the misfit)."""
+    err4, _ = _fwi_workload_fd("krylov", 20, 4.0, "f64", 1e-3)
+    assert err4 <= 1e-3, err4
+    err8, g64 = _fwi_workload_fd("krylov", 20, 8.0, "f64", 1e-3, adjoint="exponential")
+    assert err8 <= 2e-3, err8
+    err32, g32 = _fwi_workload_fd("krylov", 20, 8.0, "f32", 1e-2, adjoint="exponential")
+    assert rel_l2(g32, g64) < 1e-3, rel_l2(g32, g64)
+    assert err32 <= 1e-2, err32
+
+
+def test_hork_gradient_central_differences_on_the_fwi_workload():
+    """The same workload with Horner HORK 20 at 4 x (the FWI gradient bench.py times): the exact
+    discrete adjoint of the linear step agrees with FP64 central differences to 1e-4 (measured
+    2.0e-5), and the FP32 gradient is within 1e-3 of the FP64 one (measured 1.5e-4)."""
+    err, g64 = _fwi_workload_fd("hork", 20, 4.0, "f64", 1e-3)
+    assert err <= 1e-4, err
+    _, g32 = _fwi_workload_fd("hork", 20, 4.0, "f32", 1e-2)
+    assert rel_l2(g32, g64) < 1e-3, rel_l2(g32, g64)
