@@ -171,13 +171,19 @@ def measured_peaks():
 TMA_SOURCE = os.path.join(ROOT, "paper_2401_16322_gb300", "csrc", "kernels_tma.cu")
 
 
-def ncu_traffic_per_point(method):
+def tma_kernel_name(variant):
+    """The 2D TMA kernel a variant runs: variants 7 and up use the column-pair consumers."""
+    return "stage_tma_x2_kernel" if variant >= 7 else "stage_tma_kernel"
+
+
+def ncu_traffic_per_point(method, variant):
     """DRAM bytes per grid point of one steady-state stencil pass of ``method`` (a Faber
-    degree j >= 2 or a HORK pass after the first) from the committed ncu summary, or None
-    when there is none or the TMA kernel source changed since the capture."""
+    degree j >= 2 or a HORK pass after the first) from the committed ncu summary of the
+    kernel the variant runs, or None when there is none or the TMA kernel source changed
+    since the capture."""
     import hashlib
     name = {"hork": "hork_low_storage", "hork-horner": "hork_horner"}.get(method, method)
-    summary = os.path.join(ROOT, "profiles", f"stage_tma_kernel_{name}_1001x501x16.md")
+    summary = os.path.join(ROOT, "profiles", f"{tma_kernel_name(variant)}_{name}_1001x501x16.md")
     try:
         with open(TMA_SOURCE, "rb") as f:
             sha = hashlib.sha256(f.read()).hexdigest()
@@ -956,6 +962,7 @@ def run_ours(args):
         f1 = extras.get("config1_fp64") or {}
         fp = extras.get("fwi_gradient") or {}
         fk = extras.get("fwi_gradient_krylov") or {}
+        kvar = {k_: v_ for k_, v_ in batch.kernel_variant().items() if k_ != "probe_us"}
         result = {
             "metric": METRIC, "value": ms_per_step / 1e3, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -981,10 +988,10 @@ def run_ours(args):
             "grid_point_updates_per_s": pts * nsteps / (ms_per_step / 1e3),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
-                         "traffic": (tpp * pts if (tpp := ncu_traffic_per_point(method)) else None),
+                         "traffic": (tpp * pts if (tpp := ncu_traffic_per_point(method, kvar["variant"])) else None),
                          "peak_kind": peak_kind,
-                         "kernel": "stage_tma_kernel (persistent TMA fused stencil pass, FP32)",
-                         "variant": {k_: v_ for k_, v_ in batch.kernel_variant().items() if k_ != "probe_us"},
+                         "kernel": f"{tma_kernel_name(kvar['variant'])} (persistent TMA fused stencil pass, FP32)",
+                         "variant": kvar,
                          "avg_launch_us": avg_launch_ms * 1e3, "launches": kern_n,
                          "alg_bytes_per_launch": per_launch_bytes,
                          "timing": "CUDA events around every pass of one extra simulation after the timed region"},

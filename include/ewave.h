@@ -429,8 +429,8 @@ int ewv_batch_enable_graphs(ewv_batch_t batch, int enable);
  * warps, pipeline stages): 0 = (16, 16, 3), 1 = (16, 8, 3), 2 = (8, 8, 5), 3 = (8, 16, 5),
  * 5 = (20, 20, 3), 6 = (18, 18, 3), each consumer thread on one column; 7 = (18, 9, 3),
  * 8 = (16, 8, 3), 9 = (18, 18, 3), 10 = (24, 12, 2), each consumer thread on two adjacent
- * columns (8-byte shared loads, packed FP32 pair arithmetic); 11 = (24, 12, 3) and
- * 12 = (36, 9, 2) are composite: passes without an A operand (Horner HORK passes, Krylov
+ * columns (8-byte shared loads, packed FP32 pair arithmetic); 11 = (24, 12, 3),
+ * 12 = (36, 9, 2), 13 = (28, 14, 3) and 14 = (30, 15, 3) are composite: passes without an A operand (Horner HORK passes, Krylov
  * products) run these column-pair shapes without the A stage buffer, passes with one run
  * variant 7 (the reported shape is the no-A one).  The autotuner's score is the sum of a
  * probe pass with and one without an A operand.  The leap-frog step and the gradient pass
@@ -442,7 +442,7 @@ int ewv_batch_enable_graphs(ewv_batch_t batch, int enable);
  * 4) without the U stage buffer: passes that read a U vector run variant 0 under it.
  * 3D models: 0 (default) = TMA pipeline with 16 consumer warps, 2 = 8 warps, 1 = plain
  * z-marching kernel. */
-#define EWV_NUM_KERNEL_VARIANTS 13
+#define EWV_NUM_KERNEL_VARIANTS 15
 int ewv_set_kernel_variant(ewv_model_t model, int variant);
 int ewv_kernel_variant(ewv_model_t model, int* variant, int* tile_height, int* warps,
                        int* stages, double* probe_us);

@@ -639,6 +639,12 @@ struct Ctx {
             } else {
                 launch_stage3d(E->precision, E->R, E->ntiles, E->d_probs, E->d_tile_prob, a, s);
             }
+        } else if (E->precision == EWV_F32 && a.transpose && a.fin_mode == FIN_NONE && a.d < 0 && !a.grad &&
+                   !a.store_bf16 && E->d_tbase) {
+            const int set = tma_map_set(18);
+            if (launch_transpose_tma(E->R, E->d_probs, E->d_tbase + (size_t)set * (E->nprob + 1), E->nprob,
+                                     E->ntiles_by[set], a, E->d_err, s) != 0)
+                launch_failed = 1;
         } else if (E->precision == EWV_F32 && !a.transpose && a.fin_mode == FIN_NONE && a.d < 0 && !a.grad &&
                    !a.store_bf16) {
             if (E->tma_variant < 0) autotune();
@@ -2737,6 +2743,12 @@ int ewv_adjoint_step(ewv_model_t m, int method, double t, double dt, int deg,
         if (tma_adj && !sa.transpose && sa.grad && sa.fin_mode == FIN_NONE && sa.d < 0 &&
             launch_grad_tma(R, E->d_adj, E->d_tbase + (size_t)gset * (E->nprob + 1), ns, E->ntiles_by[gset], sa,
                             E->d_err, s) == 0) {
+            ++m->launches;
+            return;
+        }
+        if (tma_adj && sa.transpose && !sa.grad && sa.fin_mode == FIN_NONE && sa.d < 0 &&
+            launch_transpose_tma(R, E->d_adj, E->d_tbase + (size_t)gset * (E->nprob + 1), ns, E->ntiles_by[gset],
+                                 sa, E->d_err, s) == 0) {
             ++m->launches;
             return;
         }

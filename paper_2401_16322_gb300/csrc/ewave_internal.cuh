@@ -185,7 +185,7 @@ int launch_leapfrog_tma3d(int R, int warps, const ProblemDev* probs, const int* 
 int upload_tma_tables(const double* fs_uyy, const double* fs_uy, const double* fs_dwy);
 int build_tensor_maps(std::vector<ProblemDev>& probs, int R, const std::vector<int>& work_vecs,
                       void** d_maps_inout);
-constexpr int TMA_NUM_VARIANTS = 13;
+constexpr int TMA_NUM_VARIANTS = 15;
 // One 2D FP32 leap-frog step through the persistent TMA pass (64 x 18 tiles); tbase and
 // ntiles are those of the 18-row map set.
 int launch_leapfrog_tma(int R, const ProblemDev* probs, const int* tbase, int nprob, int ntiles, int cur,
@@ -193,6 +193,10 @@ int launch_leapfrog_tma(int R, const ProblemDev* probs, const int* tbase, int np
 // The FWI gradient pass through the persistent TMA pass (64 x 18 tiles, 18-row map set).
 int launch_grad_tma(int R, const ProblemDev* probs, const int* tbase, int nprob, int ntiles,
                     const StageArgs& a, int* err, cudaStream_t s);
+// The transposed pass H^T through the persistent TMA pipeline (FP32, no dot partner, no
+// gradient; 64 x 18 tiles, the 18-row map set).
+int launch_transpose_tma(int R, const ProblemDev* probs, const int* tbase, int nprob, int ntiles,
+                         const StageArgs& a, int* err, cudaStream_t s);
 int launch_stage_tma(int variant, int R, const ProblemDev* probs, const int* tbase, int nprob,
                      int ntiles, const StageArgs& a, int* err, cudaStream_t s);
 int tma_variant_tile_height(int v);
@@ -200,8 +204,8 @@ int tma_variant_tile_height(int v);
 // (composite variants pick their tile by it).
 int tma_variant_tile_height_for(int v, bool reads_a);
 // Tile heights of the 2D TMA map sets (set k has tile height TMA_SET_HEIGHTS[k]).
-constexpr int TMA_NUM_SETS = 6;
-constexpr int TMA_SET_HEIGHTS[TMA_NUM_SETS] = {16, 8, 20, 18, 24, 36};
+constexpr int TMA_NUM_SETS = 8;
+constexpr int TMA_SET_HEIGHTS[TMA_NUM_SETS] = {16, 8, 20, 18, 24, 36, 28, 30};
 int tma_map_set(int tile_height);
 void tma_variant_describe(int v, int* by, int* nw, int* nst);
 

@@ -26,7 +26,7 @@
 namespace ewv {
 
 constexpr int TX = 4;                 // staged x halo (>= R, keeps the box start 16-B aligned)
-constexpr int NMAP = 11;              // tensor maps per problem and tile height
+constexpr int NMAP = 12;              // tensor maps per problem and tile height
 constexpr int MAX_NST = 5;
 
 // Shared-memory layout of one stage (floats) for tile height BYv; every buffer starts on a
@@ -271,6 +271,36 @@ __device__ __forceinline__ int find_problem(const int* __restrict__ base, int np
     return lo;
 }
 
+// The tile descriptor the producer hands to the consumers with a stage.
+__device__ __forceinline__ void fill_tile_info(TileInfo& ti, const ProblemDev* P, const StageArgs& a, int x0,
+                                               int y0) {
+    ti.Y = a.y_out >= 0 ? (a.y_out == 0 ? (float*)P->state
+                                        : (float*)P->work + (long long)(a.y_out - 1) * P->vec_stride)
+                        : nullptr;
+    ti.A = a.acc_out >= 0 ? (a.acc_out == 0 ? (float*)P->state
+                                            : (float*)P->work + (long long)(a.acc_out - 1) * P->vec_stride)
+                          : nullptr;
+    ti.fstr = P->field_stride;
+    ti.x0 = x0;
+    ti.y0 = y0;
+    ti.nx = P->nx;
+    ti.ny = P->ny;
+    ti.pitch = P->pitch;
+    ti.pml = P->pml;
+    ti.fs = P->fs;
+    ti.src_i = P->src_i;
+    ti.src_j = P->src_j;
+    ti.shot = P->shot;
+    ti.btab = P->btab;
+    ti.nbtab = P->nbtab;
+    ti.beta0 = P->fbeta0;
+    ti.inv_pml = P->finv_pml;
+    ti.idx1 = P->finv_dx;
+    ti.idx2 = P->finv_dx2;
+    ti.sig = (a.src_slot >= 0 && P->has_src) ? (float)P->sigma[a.src_slot] : 0.f;
+    ti.xs = a.x_scale_slot >= 0 ? (float)P->kry[a.x_scale_slot] : 1.f;
+}
+
 // The producer (one elected lane of the last warp): for each tile of this CTA, wait until
 // its stage is free, resolve the tile's problem and descriptor, arm the stage's "full"
 // barrier with the byte count and issue the TMA loads.  Returns the number of tiles issued.
@@ -296,32 +326,7 @@ __device__ __forceinline__ int tma_produce(const ProblemDev* __restrict__ probs,
         const int tiles_x = (P->nx + BX - 1) / BX;
         const int lt = tile - __ldg(tbase + pid);
         const int x0 = (lt % tiles_x) * BX, y0 = (lt / tiles_x) * BYv;
-        TileInfo& ti = info[s];
-        ti.Y = a.y_out >= 0 ? (a.y_out == 0 ? (float*)P->state
-                                            : (float*)P->work + (long long)(a.y_out - 1) * P->vec_stride)
-                            : nullptr;
-        ti.A = a.acc_out >= 0 ? (a.acc_out == 0 ? (float*)P->state
-                                                : (float*)P->work + (long long)(a.acc_out - 1) * P->vec_stride)
-                              : nullptr;
-        ti.fstr = P->field_stride;
-        ti.x0 = x0;
-        ti.y0 = y0;
-        ti.nx = P->nx;
-        ti.ny = P->ny;
-        ti.pitch = P->pitch;
-        ti.pml = P->pml;
-        ti.fs = P->fs;
-        ti.src_i = P->src_i;
-        ti.src_j = P->src_j;
-        ti.shot = P->shot;
-        ti.btab = P->btab;
-        ti.nbtab = P->nbtab;
-        ti.beta0 = P->fbeta0;
-        ti.inv_pml = P->finv_pml;
-        ti.idx1 = P->finv_dx;
-        ti.idx2 = P->finv_dx2;
-        ti.sig = (a.src_slot >= 0 && P->has_src) ? (float)P->sigma[a.src_slot] : 0.f;
-        ti.xs = a.x_scale_slot >= 0 ? (float)P->kry[a.x_scale_slot] : 1.f;
+        fill_tile_info(info[s], P, a, x0, y0);
         float* st = smem + (size_t)s * L::FLOATS;
         // the arrive below releases the tile info together with the copies
         mbar_expect_tx(&full[s], bytes);
@@ -1012,6 +1017,378 @@ stage_tma_x2_kernel(const ProblemDev* __restrict__ probs, const int* __restrict_
     tma_finish<NSTv>(s_err, issued, full, err);
 }
 
+// ---------------------------------------------------------------- transposed pass
+// H^T y (the adjoint's passes) with the column-pair consumers.  For y = (y_u, y_v, y_wx,
+// y_wy):
+//   (H^T y)_u  = -bx by y_v + L (c^2 y_v) - D_x(z_x) - D_y(z_y)      (L symmetric in the interior)
+//   (H^T y)_v  = y_u - (bx + by) y_v
+//   (H^T y)_wx = -d_x^+(c^2 y_v) - bx^h y_wx                          at (i+1/2, j)
+//   (H^T y)_wy = -d_y^+(c^2 y_v) - by^h y_wy                          at (i, j+1/2)
+// with z_x = (by - bx^h) y_wx at the half columns and z_y = (bx - by^h) y_wy at the half rows:
+// the transposes of the forward's staggered derivatives are the negated staggered
+// derivatives of the other grid (zero extension keeps that exact at the edges).  The stage
+// carries y_v and c^2 with the 2D halo (their product is formed from shared memory), y_wx
+// with the x halo, y_wy with the y halo, y_u and the U / A operands.  The rows whose
+// transposed stencils meet the free-surface rows of Appendix A (rows 0..8: the columns of
+// those rows) take a scalar path per point that adds the tables' columns.
+template <int R, int BYv, bool HASU, bool HASA>
+struct TLayout {
+    static constexpr int up32(int v) { return (v + 31) / 32 * 32; }
+    static constexpr int SH = BYv + 2 * R;
+    static constexpr int SW = BX + 2 * TX;
+    static constexpr int ZV_OFF = 0;                                 // y_v    SH x SW
+    static constexpr int C2_OFF = up32(ZV_OFF + SH * SW);            // c^2    SH x SW
+    static constexpr int WX_OFF = up32(C2_OFF + SH * SW);            // y_wx   BYv x SW
+    static constexpr int WY_OFF = up32(WX_OFF + BYv * SW);           // y_wy   SH x BX
+    static constexpr int YU_OFF = WY_OFF + SH * BX;                  // y_u    BYv x BX
+    static constexpr int PU_OFF = YU_OFF + BYv * BX;                 // U      4 x BYv x BX
+    static constexpr int PA_OFF = PU_OFF + (HASU ? 4 * BYv * BX : 0);   // A   4 x BYv x BX
+    static constexpr int FLOATS = PA_OFF + (HASA ? 4 * BYv * BX : 0);
+    static constexpr int BOX_FLOATS = 2 * SH * SW + BYv * SW + SH * BX + BYv * BX;
+    static constexpr int BYTES = FLOATS * 4;
+    static_assert((C2_OFF * 4) % 128 == 0 && (WX_OFF * 4) % 128 == 0 && (WY_OFF * 4) % 128 == 0 &&
+                      (YU_OFF * 4) % 128 == 0 && (PU_OFF * 4) % 128 == 0 && (PA_OFF * 4) % 128 == 0 &&
+                      BYTES % 128 == 0,
+                  "TMA destinations must be 128-byte aligned");
+};
+
+template <int R, int BYv, int NSTv, bool HASU, bool HASA>
+__device__ __forceinline__ int tma_produce_t(const ProblemDev* __restrict__ probs, const int* __restrict__ tbase,
+                                             int nprob, int ntiles, int mapset, const StageArgs& a, float* smem,
+                                             uint64_t* full, uint64_t* empty, TileInfo* info, int* s_err,
+                                             uint64_t wait_lim) {
+    using L = TLayout<R, BYv, HASU, HASA>;
+    const bool has_u = HASU && a.u >= 0, has_a = HASA && a.a >= 0;
+    const uint32_t bytes = (uint32_t)(L::BOX_FLOATS + (has_u ? 4 * BYv * BX : 0) + (has_a ? 4 * BYv * BX : 0)) * 4u;
+    int issued = 0;
+    int it = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const int s = it % NSTv;
+        const uint32_t ph = (uint32_t)(it / NSTv) & 1u;
+        if (!mbar_wait(&empty[s], ph ^ 1u, wait_lim)) {
+            *s_err = 1;
+            break;
+        }
+        const int pid = find_problem(tbase, nprob, tile);
+        const ProblemDev* P = probs + pid;
+        const CUtensorMap* maps = reinterpret_cast<const CUtensorMap*>(P->tmaps) + mapset * NMAP;
+        const int tiles_x = (P->nx + BX - 1) / BX;
+        const int lt = tile - __ldg(tbase + pid);
+        const int x0 = (lt % tiles_x) * BX, y0 = (lt / tiles_x) * BYv;
+        fill_tile_info(info[s], P, a, x0, y0);
+        float* st = smem + (size_t)s * L::FLOATS;
+        mbar_expect_tx(&full[s], bytes);
+        const int kx = a.x, cx = a.x == 0 ? 0 : a.x - 1;
+        tma_load_4d(st + L::ZV_OFF, map_of(maps, kx, 0), x0 - TX, y0 - R, 1, cx, &full[s]);   // y_v, 2D halo
+        tma_load_2d(st + L::C2_OFF, maps + 11, x0 - TX, y0 - R, &full[s]);                   // c^2, 2D halo
+        tma_load_4d(st + L::WX_OFF, map_of(maps, kx, 1), x0 - TX, y0, 2, cx, &full[s]);
+        tma_load_4d(st + L::WY_OFF, map_of(maps, kx, 2), x0, y0 - R, 3, cx, &full[s]);
+        tma_load_4d(st + L::YU_OFF, map_of(maps, kx, 3), x0, y0, 0, cx, &full[s]);           // y_u
+        if (has_u)
+            tma_load_4d(st + L::PU_OFF, map_of(maps, a.u, 4), x0, y0, 0, a.u == 0 ? 0 : a.u - 1, &full[s]);
+        if (has_a)
+            tma_load_4d(st + L::PA_OFF, map_of(maps, a.a, 4), x0, y0, 0, a.a == 0 ? 0 : a.a - 1, &full[s]);
+        issued = it + 1;
+    }
+    return issued;
+}
+
+// The general epilogue (StageArgs) of one point: K = cx X + ch xs HX, Y = cu U + ck K,
+// ACC = ca A + cau U + cak K + cay Y + cax X, pads of w_x / w_y zero.
+__device__ __forceinline__ void tma_epilogue_point(const TileInfo& ti, const StageArgs& a, long long o, const float* xf,
+                                                   const float* hf, const float* uv, const float* av, bool padx,
+                                                   bool pady) {
+    const float chx = a.fch * ti.xs;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        const bool pad = (f == 2 && padx) || (f == 3 && pady);
+        const float kf = fmaf(a.fcx, xf[f], chx * hf[f]);
+        const float yf = pad ? 0.f : (a.fcu * uv[f] + a.fck * kf);
+        if (ti.Y) ti.Y[f * ti.fstr + o] = yf;
+        if (ti.A)
+            ti.A[f * ti.fstr + o] =
+                pad ? 0.f : (a.fca * av[f] + a.fcau * uv[f] + a.fcak * kf + a.fcay * yf + a.fcax * xf[f]);
+    }
+}
+
+// One transposed point from shared memory with the free-surface columns (rows 0..8 of the
+// top tile), following the row structure of the forward operator.
+template <int R, int BYv, bool HASU, bool HASA>
+__device__ __forceinline__ void tma_point_scalar_t(const float* st, const TileInfo& ti, const StageArgs& a, int tc,
+                                                   int lr, bool has_u, bool has_a) {
+    using L = TLayout<R, BYv, HASU, HASA>;
+    const int nx = ti.nx, ny = ti.ny;
+    const int i = ti.x0 + tc, j = ti.y0 + lr;
+    if (i >= nx || j >= ny) return;
+    const bool fs = ti.fs != 0;
+    const int cs = tc + TX;
+    const float* btab = ti.btab;
+    const int nbt = ti.nbtab;
+    const float* zv_ = st + L::ZV_OFF;
+    const float* c2_ = st + L::C2_OFF;
+    const float* wx_ = st + L::WX_OFF;
+    const float* wy_ = st + L::WY_OFF;
+    // z_v at staged row q (grid row y0 + q - R), tile column tc + d
+    auto zv = [&](int q, int d) { return zv_[q * L::SW + cs + d] * c2_[q * L::SW + cs + d]; };
+    const float byn = btab_at(btab, nbt, 2 * (fs ? ny - j : min(j + 1, ny - j)));
+    const float bxn = btab_at(btab, nbt, 2 * min(i + 1, nx - i));
+    const float bxh = btab_at(btab, nbt, min(2 * i + 3, 2 * (nx - i) - 1));
+    const float byh = btab_at(btab, nbt, fs ? 2 * (ny - j) - 1 : min(2 * j + 3, 2 * (ny - j) - 1));
+    // z_x at half column i + d + 1/2 of this row, z_y at half row h of this column
+    auto zx = [&](int d) {
+        const int p = i + d;
+        const float bh = btab_at(btab, nbt, min(2 * p + 3, 2 * (nx - p) - 1));
+        return (byn - bh) * wx_[lr * L::SW + cs + d];
+    };
+    auto zy = [&](int h) {
+        const float bh = btab_at(btab, nbt, fs ? 2 * (ny - h) - 1 : min(2 * h + 3, 2 * (ny - h) - 1));
+        return (bxn - bh) * wy_[(h - ti.y0 + R) * BX + tc];
+    };
+    const int q0 = lr + R;   // staged row of j
+    float lxx = cent<R>(0) * zv(q0, 0);
+#pragma unroll
+    for (int k = 1; k <= R; ++k) lxx += cent<R>(k) * (zv(q0, k) + zv(q0, -k));
+    float lyy = 0.f;
+    const int rfs = fs ? 4 : 0;
+#pragma unroll
+    for (int k = -R; k <= R; ++k) {
+        const int r = j + k;
+        if (r >= rfs && r < ny) lyy += cent<R>(k < 0 ? -k : k) * zv(q0 + k, 0);
+    }
+    if (fs && j <= 8) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+            if (r < ny) lyy += g_tma_fs[TFS_UYY + r * 9 + j] * zv(r - ti.y0 + R, 0);
+    }
+    float gxt = 0.f;
+#pragma unroll
+    for (int k = 0; k < R; ++k) gxt += stag<R>(k) * (zx(-1 - k) - zx(k));
+    float gyt = 0.f;
+    const int hfs = fs ? 3 : 0;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const int h1 = j + k, h2 = j - 1 - k;
+        if (h1 >= hfs && h1 < ny - 1) gyt += stag<R>(k) * zy(h1);
+        if (h2 >= hfs && h2 >= 0) gyt -= stag<R>(k) * zy(h2);
+    }
+    if (fs && j <= 7) {
+#pragma unroll
+        for (int h = 0; h < 3; ++h)
+            if (h < ny - 1) gyt += g_tma_fs[TFS_UY + h * 8 + j] * zy(h);
+    }
+    float dxt = 0.f;
+#pragma unroll
+    for (int k = 0; k < R; ++k) dxt += stag<R>(k) * (zv(q0, -k) - zv(q0, 1 + k));
+    float dyt = 0.f;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const int r1 = j + 1 + k, r2 = j - k;
+        if (r1 >= rfs && r1 < ny) dyt += stag<R>(k) * zv(q0 + 1 + k, 0);
+        if (r2 >= rfs && r2 >= 0) dyt -= stag<R>(k) * zv(q0 - k, 0);
+    }
+    if (fs && j <= 7) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+            if (r < ny) dyt += g_tma_fs[TFS_DWY + r * 8 + j] * zv(r - ti.y0 + R, 0);
+    }
+    const int pt = lr * BX + tc;
+    const float yu = st[L::YU_OFF + pt], yv = zv_[q0 * L::SW + cs];
+    const float ywx = (i < nx - 1) ? wx_[lr * L::SW + cs] : 0.f;
+    const float ywy = (j < ny - 1) ? wy_[q0 * BX + tc] : 0.f;
+    const float idx1 = ti.idx1, idx2 = ti.idx2;
+    const float xf[4] = {yu, yv, ywx, ywy};
+    const float hf[4] = {-bxn * byn * yv + (lxx + lyy) * idx2 + (gxt + gyt) * idx1, yu - (bxn + byn) * yv,
+                         (i < nx - 1) ? dxt * idx1 - bxh * ywx : 0.f, (j < ny - 1) ? dyt * idx1 - byh * ywy : 0.f};
+    float uv[4], av[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        uv[f] = has_u ? st[L::PU_OFF + f * BYv * BX + pt] : 0.f;
+        av[f] = has_a ? st[L::PA_OFF + f * BYv * BX + pt] : 0.f;
+    }
+    tma_epilogue_point(ti, a, (long long)j * ti.pitch + i, xf, hf, uv, av, i >= nx - 1, j >= ny - 1);
+}
+
+template <int R, int BYv, int NW, int NSTv, bool HASU, bool HASA>
+__global__ void __launch_bounds__(NW * 32 + 32, 1)
+stage_tma_t_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ tbase, int nprob, int ntiles,
+                   int mapset, StageArgs a, int* err) {
+    using L = TLayout<R, BYv, HASU, HASA>;
+    constexpr int CPR = BX / 2;
+    constexpr int TPR = NW * 32 / CPR;
+    constexpr int NR = BYv / TPR;
+    static_assert(NR * TPR == BYv && NR >= 1, "tile rows must split evenly over threads");
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    float* smem = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    __shared__ __align__(8) uint64_t full[NSTv];
+    __shared__ __align__(8) uint64_t empty[NSTv];
+    __shared__ TileInfo info[NSTv];
+    __shared__ int s_err;
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const uint64_t wait_lim = g_tma_wait_limit_ns;
+    if (tid == 0) {
+        for (int s = 0; s < NSTv; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], NW);
+        }
+        s_err = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const bool has_u = HASU && a.u >= 0, has_a = HASA && a.a >= 0;
+    int issued = 0;
+    if (warp == NW) {
+        if (lane == 0)
+            issued = tma_produce_t<R, BYv, NSTv, HASU, HASA>(probs, tbase, nprob, ntiles, mapset, a, smem, full,
+                                                             empty, info, &s_err, wait_lim);
+    } else {
+        const int tx2 = tid % CPR, ty = tid / CPR;
+        const int c0 = 2 * tx2, cs = c0 + TX, r0 = NR * ty;
+        const float2 cx2 = f2s(a.fcx), cu2 = f2s(a.fcu), ck2 = f2s(a.fck), ca2 = f2s(a.fca);
+        const float2 cay2 = f2s(a.fcay), cau2 = f2s(a.fcau), cak2 = f2s(a.fcak), cax2 = f2s(a.fcax);
+        int it = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+            const int s = it % NSTv;
+            const uint32_t ph = (uint32_t)(it / NSTv) & 1u;
+            if (!mbar_wait(&full[s], ph, wait_lim)) {
+                s_err = 1;
+                break;
+            }
+            const TileInfo ti = load_info(&info[s]);
+            const float* st = smem + (size_t)s * L::FLOATS;
+            const int nx = ti.nx, ny = ti.ny;
+            const int i0 = ti.x0 + c0;
+            const int jt = ti.y0 + r0;
+            if (i0 < nx && jt < ny) {
+                if (ti.fs != 0 && jt < 9) {
+#pragma unroll 1
+                    for (int r = 0; r < NR; ++r) {
+                        tma_point_scalar_t<R, BYv, HASU, HASA>(st, ti, a, c0, r0 + r, has_u, has_a);
+                        tma_point_scalar_t<R, BYv, HASU, HASA>(st, ti, a, c0 + 1, r0 + r, has_u, has_a);
+                    }
+                } else {
+                    const float* zvp = st + L::ZV_OFF;
+                    const float* c2p = st + L::C2_OFF;
+                    const float* wxp = st + L::WX_OFF;
+                    const float* wyp = st + L::WY_OFF;
+                    const float* yup = st + L::YU_OFF;
+                    const float* spu = st + L::PU_OFF;
+                    const float* spa = st + L::PA_OFF;
+                    const bool fs = ti.fs != 0;
+                    const bool in1 = i0 + 1 < nx;
+                    const float* btab = ti.btab;
+                    const int nbt = ti.nbtab;
+                    const float2 bxn = f2(btab_at(btab, nbt, 2 * min(i0 + 1, nx - i0)),
+                                          btab_at(btab, nbt, 2 * min(i0 + 2, nx - i0 - 1)));
+                    // bx at the half columns i0 + d + 1/2, d = -4 .. 5 (the z_x taps)
+                    float bxh[10];
+#pragma unroll
+                    for (int d = -4; d <= 5; ++d) {
+                        const int p = i0 + d;
+                        bxh[d + 4] = btab_at(btab, nbt, min(2 * p + 3, 2 * (nx - p) - 1));
+                    }
+                    const float2 bxhp = f2(bxh[4], bxh[5]);   // at this thread's two columns
+                    unsigned xin = 0u;                           // half columns 0 .. nx - 2
+#pragma unroll
+                    for (int d = -4; d <= 5; ++d)
+                        if (i0 + d >= 0 && i0 + d < nx - 1) xin |= 1u << (d + 4);
+                    // z_v = c^2 y_v and z_y = (bx - by^h) y_wy down this column pair
+                    float2 zq[NR + 2 * R], zyq[NR + 2 * R - 1];
+#pragma unroll
+                    for (int q = 0; q < NR + 2 * R; ++q)
+                        zq[q] = mul2(lds2(zvp + (r0 + q) * L::SW + cs), lds2(c2p + (r0 + q) * L::SW + cs));
+#pragma unroll
+                    for (int q = 0; q < NR + 2 * R - 1; ++q) {
+                        const int h = ti.y0 + r0 + q - R;
+                        const float bh = btab_at(btab, nbt, fs ? 2 * (ny - h) - 1 : min(2 * h + 3, 2 * (ny - h) - 1));
+                        zyq[q] = (h >= 0 && h < ny - 1) ? mul2(sub2(bxn, f2s(bh)), lds2(wyp + (r0 + q) * BX + c0))
+                                                        : f2s(0.f);
+                    }
+                    const bool wx0in = i0 < nx - 1, wx1in = i0 + 1 < nx - 1;
+                    const float2 idx1 = f2s(ti.idx1), idx2 = f2s(ti.idx2);
+                    const float2 chx2 = f2s(a.fch * ti.xs);
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        const int lr = r0 + r, j = jt + r;
+                        if (j >= ny) break;
+                        const float byn = btab_at(btab, nbt, 2 * (fs ? ny - j : min(j + 1, ny - j)));
+                        const float byh =
+                            btab_at(btab, nbt, fs ? 2 * (ny - j) - 1 : min(2 * j + 3, 2 * (ny - j) - 1));
+                        // x taps of z_v (pairs at column offsets -4 .. 5) and y_wx
+                        const float* zr = zvp + (lr + R) * L::SW + cs;
+                        const float* cr = c2p + (lr + R) * L::SW + cs;
+                        const float2 zp[5] = {mul2(lds2(zr - 4), lds2(cr - 4)), mul2(lds2(zr - 2), lds2(cr - 2)),
+                                              zq[r + R], mul2(lds2(zr + 2), lds2(cr + 2)),
+                                              mul2(lds2(zr + 4), lds2(cr + 4))};
+                        const float* wr = wxp + lr * L::SW + cs;
+                        const float2 wp[5] = {lds2(wr - 4), lds2(wr - 2), lds2(wr), lds2(wr + 2), lds2(wr + 4)};
+                        auto zo = [&](int d) { return ((d + 4) & 1) ? zp[(d + 4) >> 1].y : zp[(d + 4) >> 1].x; };
+                        // z_x at half column offset d: (by - bx^h) y_wx (zero off the w_x grid)
+                        auto xo = [&](int d) {
+                            const float wv = ((d + 4) & 1) ? wp[(d + 4) >> 1].y : wp[(d + 4) >> 1].x;
+                            return ((xin >> (d + 4)) & 1u) ? (byn - bxh[d + 4]) * wv : 0.f;
+                        };
+                        const float2 zc = zq[r + R];
+                        float2 lap = mul2(f2s(2.f * cent<R>(0)), zc);
+                        float2 gxt = f2s(0.f), gyt = f2s(0.f), dxt = f2s(0.f), dyt = f2s(0.f);
+#pragma unroll
+                        for (int k = 0; k < R; ++k) {
+                            const int kk = k + 1;
+                            const float2 sx = (kk & 1) ? f2(zo(kk) + zo(-kk), zo(kk + 1) + zo(1 - kk))
+                                                       : add2(zp[(kk + 4) >> 1], zp[(4 - kk) >> 1]);
+                            const float2 sy = add2(zq[r + R + kk], zq[r + R - kk]);
+                            lap = fma2(f2s(cent<R>(kk)), add2(sx, sy), lap);
+                            gxt = fma2(f2s(stag<R>(k)), f2(xo(-1 - k) - xo(k), xo(-k) - xo(1 + k)), gxt);
+                            gyt = fma2(f2s(stag<R>(k)), sub2(zyq[r + R + k], zyq[r + R - 1 - k]), gyt);
+                            dxt = fma2(f2s(stag<R>(k)), f2(zo(-k) - zo(1 + k), zo(1 - k) - zo(2 + k)), dxt);
+                            dyt = fma2(f2s(stag<R>(k)), sub2(zq[r + R + 1 + k], zq[r + R - k]), dyt);
+                        }
+                        const int pt = lr * BX + c0;
+                        const float2 yv = lds2(zvp + (lr + R) * L::SW + cs);
+                        const float2 yu = lds2(yup + pt);
+                        const bool wyin = j < ny - 1;
+                        float2 ywx = wp[2];
+                        if (!wx0in) ywx.x = 0.f;
+                        if (!wx1in) ywx.y = 0.f;
+                        const float2 ywy = wyin ? lds2(wyp + (lr + R) * BX + c0) : f2s(0.f);
+                        // (H^T y)_u, _v, _wx, _wy
+                        const float2 hu = fma2(mul2(bxn, f2s(-byn)), yv,
+                                               fma2(lap, idx2, mul2(add2(gxt, gyt), idx1)));
+                        const float2 hv = fma2(sub2(f2s(-byn), bxn), yv, yu);
+                        float2 hwx = fma2(dxt, idx1, mul2(f2(-bxhp.x, -bxhp.y), ywx));
+                        if (!wx0in) hwx.x = 0.f;
+                        if (!wx1in) hwx.y = 0.f;
+                        const float2 hwy = wyin ? fma2(dyt, idx1, mul2(f2s(-byh), ywy)) : f2s(0.f);
+                        const float2 xf[4] = {yu, yv, ywx, ywy};
+                        const float2 hf[4] = {hu, hv, hwx, hwy};
+                        const long long o = (long long)j * ti.pitch + i0;
+#pragma unroll
+                        for (int f = 0; f < 4; ++f) {
+                            const float2 uval = has_u ? lds2(spu + f * BYv * BX + pt) : f2s(0.f);
+                            const float2 aval = has_a ? lds2(spa + f * BYv * BX + pt) : f2s(0.f);
+                            const float2 kf = fma2(cx2, xf[f], mul2(chx2, hf[f]));
+                            float2 yf = fma2(cu2, uval, mul2(ck2, kf));
+                            float2 af = fma2(cax2, xf[f],
+                                             fma2(cay2, yf, fma2(cak2, kf, fma2(cau2, uval, mul2(ca2, aval)))));
+                            if (f == 2) {
+                                if (!wx0in) yf.x = af.x = 0.f;
+                                if (!wx1in) yf.y = af.y = 0.f;
+                            }
+                            if (f == 3 && !wyin) yf = af = f2s(0.f);
+                            if (ti.Y) st2(ti.Y + f * ti.fstr + o, yf, in1);
+                            if (ti.A) st2(ti.A + f * ti.fstr + o, af, in1);
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+        }
+    }
+    __syncthreads();
+    tma_finish<NSTv>(s_err, issued, full, err);
+}
+
 // ---------------------------------------------------------------- host side
 static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
@@ -1056,13 +1433,13 @@ int tma_map_set(int tile_height) {
     return -1;
 }
 constexpr int map_set_of(int by) {
-    return by == 16 ? 0 : by == 8 ? 1 : by == 20 ? 2 : by == 18 ? 3 : by == 24 ? 4 : 5;
+    for (int k = 0; k < TMA_NUM_SETS; ++k)
+        if (TMA_SET_HEIGHTS[k] == by) return k;
+    return -1;
 }
-static_assert(map_set_of(16) == 0 && map_set_of(8) == 1 && map_set_of(20) == 2 && map_set_of(18) == 3 &&
-                  map_set_of(24) == 4 && map_set_of(36) == 5 && TMA_SET_HEIGHTS[0] == 16 &&
-                  TMA_SET_HEIGHTS[1] == 8 && TMA_SET_HEIGHTS[2] == 20 && TMA_SET_HEIGHTS[3] == 18 &&
-                  TMA_SET_HEIGHTS[4] == 24 && TMA_SET_HEIGHTS[5] == 36,
-              "map sets and tile heights must agree");
+static_assert(map_set_of(16) == 0 && map_set_of(18) == 3 && map_set_of(24) >= 0 && map_set_of(28) >= 0 &&
+                  map_set_of(30) >= 0 && map_set_of(36) >= 0,
+              "every tile height in use has a map set");
 
 // Build NMAP maps per problem and tile height (one map set per entry of TMA_SET_HEIGHTS)
 // into a device array (FP32 only); sets P.tmaps to the problem's first map.
@@ -1093,6 +1470,8 @@ int build_tensor_maps(std::vector<ProblemDev>& probs, int R, const std::vector<i
                     return -1;
             }
             if (encode2(m + 10, const_cast<void*>(P.c2), P.nx, P.ny, P.pitch, BX, by) != 0) return -1;
+            // c^2 with the 2D halo of u (the transposed pass stages c^2 y_v)
+            if (encode2(m + 11, const_cast<void*>(P.c2), P.nx, P.ny, P.pitch, SW, SH) != 0) return -1;
         }
     }
     cudaFree(*d_maps_inout);
@@ -1117,16 +1496,20 @@ int build_tensor_maps(std::vector<ProblemDev>& probs, int R, const std::vector<i
 // composite: passes that read an A operand run variant 7, the others (Horner HORK passes,
 // Krylov products, leap-frog-free RK stages without an accumulator) drop the A buffer and
 // take taller tiles: 11 = 64 x 24 with 12 warps and 3 stages, 12 = 64 x 36 with 9 warps, four
-// rows a thread and 2 stages.  The shape reported for a composite is its no-A shape.
+// rows a thread and 2 stages; 13 = 64 x 28 with 14 warps and 3 stages; 14 = 64 x 30 with 15
+// warps and 3 stages (512 threads at 128 registers: the whole register file).  The shape
+// reported for a composite is its no-A shape.
 struct TmaVariant {
     int by, nw, nst;
 };
 constexpr TmaVariant kVariants[TMA_NUM_VARIANTS] = {
     {16, 16, 3}, {16, 8, 3}, {8, 8, 5},  {8, 16, 5},  {16, 16, 4}, {20, 20, 3}, {18, 18, 3},
-    {18, 9, 3},  {16, 8, 3}, {18, 18, 3}, {24, 12, 2}, {24, 12, 3}, {36, 9, 2}};
+    {18, 9, 3},  {16, 8, 3}, {18, 18, 3}, {24, 12, 2}, {24, 12, 3}, {36, 9, 2}, {28, 14, 3}, {30, 15, 3}};
+
+static bool composite(int v) { return v >= 11 && v <= 14; }
 
 int tma_variant_tile_height_for(int v, bool reads_a) {
-    if ((v == 11 || v == 12) && reads_a) return kVariants[7].by;
+    if (composite(v) && reads_a) return kVariants[7].by;
     return kVariants[v].by;
 }
 
@@ -1162,6 +1545,7 @@ static int launch_variant(const ProblemDev* probs, const int* tbase, int nprob, 
 template <int R, int BYv, int NW, int NSTv, int EPI, bool HASA = true>
 static int launch_x2(const ProblemDev* probs, const int* tbase, int nprob, int ntiles, const StageArgs& a,
                      int* err, cudaStream_t s) {
+    static_assert(map_set_of(BYv) >= 0, "tile height without a map set");
     if (!HASA && a.a >= 0) return -1;    // a pass with an A operand needs the A buffer
     const size_t smem = (size_t)NSTv * StageLayout<R, BYv, true, HASA>::BYTES + 1024;
     static unsigned long long configured = 0;
@@ -1227,6 +1611,61 @@ int launch_grad_tma(int R, const ProblemDev* probs, const int* tbase, int nprob,
     return -1;
 }
 
+template <int R, bool HASU, bool HASA>
+static int launch_t(const ProblemDev* probs, const int* tbase, int nprob, int ntiles, const StageArgs& a, int* err,
+                    cudaStream_t s) {
+    constexpr int BYv = 18, NW = 9, NSTv = 3;
+    const size_t smem = (size_t)NSTv * TLayout<R, BYv, HASU, HASA>::BYTES + 1024;
+    static unsigned long long configured = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return -1;
+    if (!(configured >> dev & 1ull)) {
+        if (cudaFuncSetAttribute(stage_tma_t_kernel<R, BYv, NW, NSTv, HASU, HASA>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return -1;
+        configured |= 1ull << dev;
+    }
+    const int grid = ntiles < g_num_sms ? ntiles : g_num_sms;
+    stage_tma_t_kernel<R, BYv, NW, NSTv, HASU, HASA><<<grid, NW * 32 + 32, smem, s>>>(
+        probs, tbase, nprob, ntiles, map_set_of(BYv), a, err);
+    return 0;
+}
+
+// The transposed pass H^T (FP32, no dot partner, no gradient) on 64 x 18 tiles with 9
+// column-pair consumer warps; tbase and ntiles are those of the 18-row map set.
+int launch_transpose_tma(int R, const ProblemDev* probs, const int* tbase, int nprob, int ntiles,
+                         const StageArgs& a_in, int* err, cudaStream_t s) {
+    if (ntiles <= 0) return nprob > 0 ? -1 : 0;
+    if (!g_num_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 1;
+    }
+    StageArgs a = a_in;
+    a.fcx = (float)a.cx;
+    a.fch = (float)a.ch;
+    a.fcu = (float)a.cu;
+    a.fck = (float)a.ck;
+    a.fca = (float)a.ca;
+    a.fcau = (float)a.cau;
+    a.fcak = (float)a.cak;
+    a.fcay = (float)a.cay;
+    a.fcax = (float)a.cax;
+    const bool hu = a.u >= 0, ha = a.a >= 0;
+    if (R == 4)
+        return hu ? (ha ? launch_t<4, true, true>(probs, tbase, nprob, ntiles, a, err, s)
+                        : launch_t<4, true, false>(probs, tbase, nprob, ntiles, a, err, s))
+                  : (ha ? launch_t<4, false, true>(probs, tbase, nprob, ntiles, a, err, s)
+                        : launch_t<4, false, false>(probs, tbase, nprob, ntiles, a, err, s));
+    if (R == 2)
+        return hu ? (ha ? launch_t<2, true, true>(probs, tbase, nprob, ntiles, a, err, s)
+                        : launch_t<2, true, false>(probs, tbase, nprob, ntiles, a, err, s))
+                  : (ha ? launch_t<2, false, true>(probs, tbase, nprob, ntiles, a, err, s)
+                        : launch_t<2, false, false>(probs, tbase, nprob, ntiles, a, err, s));
+    return -1;
+}
+
 int launch_stage_tma(int variant, int R, const ProblemDev* probs, const int* tbase, int nprob,
                      int ntiles, const StageArgs& a_in, int* err, cudaStream_t s) {
     StageArgs a = a_in;
@@ -1262,7 +1701,7 @@ int launch_stage_tma(int variant, int R, const ProblemDev* probs, const int* tba
     if (variant == V && R == RR)                                                             \
         return epi ? launch_x2<RR, BYV, NWV, NSTV, 1>(probs, tbase, nprob, ntiles, a, err, s) \
                    : launch_x2<RR, BYV, NWV, NSTV, 0>(probs, tbase, nprob, ntiles, a, err, s);
-    if ((variant == 11 || variant == 12) && a.a >= 0) variant = 7;   // composite, pass with A
+    if (composite(variant) && a.a >= 0) variant = 7;   // composite, pass with A
 #define EWV_TMA_X2_NOA_CASE(V, RR, BYV, NWV, NSTV) \
     if (variant == V && R == RR)                                                                    \
         return epi ? launch_x2<RR, BYV, NWV, NSTV, 1, false>(probs, tbase, nprob, ntiles, a, err, s) \
@@ -1273,12 +1712,16 @@ int launch_stage_tma(int variant, int R, const ProblemDev* probs, const int* tba
     EWV_TMA_X2_CASE(10, 4, 24, 12, 2)
     EWV_TMA_X2_NOA_CASE(11, 4, 24, 12, 3)
     EWV_TMA_X2_NOA_CASE(12, 4, 36, 9, 2)
+    EWV_TMA_X2_NOA_CASE(13, 4, 28, 14, 3)
+    EWV_TMA_X2_NOA_CASE(14, 4, 30, 15, 3)
     EWV_TMA_X2_CASE(7, 2, 18, 9, 3)
     EWV_TMA_X2_CASE(8, 2, 16, 8, 3)
     EWV_TMA_X2_CASE(9, 2, 18, 18, 3)
     EWV_TMA_X2_CASE(10, 2, 24, 12, 2)
     EWV_TMA_X2_NOA_CASE(11, 2, 24, 12, 3)
     EWV_TMA_X2_NOA_CASE(12, 2, 36, 9, 2)
+    EWV_TMA_X2_NOA_CASE(13, 2, 28, 14, 3)
+    EWV_TMA_X2_NOA_CASE(14, 2, 30, 15, 3)
 #undef EWV_TMA_X2_NOA_CASE
 #undef EWV_TMA_X2_CASE
     if (variant == 4) {   // no U buffer; a pass with a U operand runs variant 0

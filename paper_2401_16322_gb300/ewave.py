@@ -166,7 +166,7 @@ def load_library(path=LIB_PATH):
 
 
 # persistent-pass variants the autotuner times (EWV_NUM_KERNEL_VARIANTS)
-NUM_KERNEL_VARIANTS = 13
+NUM_KERNEL_VARIANTS = 15
 
 
 def _variant(fn, h, check):

@@ -98,7 +98,7 @@ def test_batch_bitwise_equals_single_models():
             assert np.array_equal(batched[q][s], g.get_state(s))
 
 
-@pytest.mark.parametrize("variant", list(range(13)))
+@pytest.mark.parametrize("variant", list(range(15)))
 def test_every_kernel_variant_matches_oracle(variant):
     """Each persistent-kernel variant the autotuner may pick (tile height 16, 8, 18 or 20;
     8 to 20 consumer warps; 3 to 5 stages; one or two columns per thread) gives the oracle's
@@ -133,7 +133,7 @@ def test_autotuner_picks_a_timed_variant():
     B.step("faber", 0.04, 1.1e-3, 8, 1)
     info = B.kernel_variant()
     times = info["probe_us"]
-    assert len(times) == 13 and 0 <= info["variant"] < len(times)
+    assert len(times) == 15 and 0 <= info["variant"] < len(times)
     assert all(t > 0 for t in times)
     assert times[info["variant"]] == min(times)
 
