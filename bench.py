@@ -65,12 +65,13 @@ def parse(argv=None):
                          "rk32, rk44, leapfrog, leapfrog-difference), m and step in leap-frog steps "
                          f"(default {','.join(map(str, DEFAULT_SELECTION))})")
     ap.add_argument("--variant", type=int, default=-1,
-                    help="FP32 stencil-pass variant (0..6; -1: autotune at first use)")
-    ap.add_argument("--case", default="full", choices=["full", "small", "medium", "cube", "signal", "oracle"],
+                    help="FP32 stencil-pass variant (0..14; -1: autotune at first use)")
+    ap.add_argument("--case", default="full", choices=["full", "small", "medium", "cube", "signal", "oracle", "fwi"],
                     help="small / medium: the 1001x501 model with 4 / 16 shots (profiling); "
                          "cube: only the 3D side run (--n3d, --check3d); signal: only the "
                          "single-signal experiment of Sec. 4 (FP64, 10 m against 2.5 m); oracle: "
-                         "the FP64 oracle run in full on the host cores (no GPU)")
+                         "the FP64 oracle run in full on the host cores (no GPU); fwi: only the FWI "
+                         "gradient side runs (HORK and Krylov on the 16-shot FWI workload)")
     ap.add_argument("--check3d", type=int, default=0,
                     help="edge of the 3D accuracy cube of a Delta-t_max search (0: time the "
                          "settings found by that search on a 96^3 cube, and check their error "
@@ -1066,6 +1067,12 @@ def main(argv=None):
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         print(json_line({"config5_3d": config5_3d(args.n3d, args.check3d)}), flush=True)
+        return 0
+    if args.case == "fwi":
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        print(json_line({"fwi_gradient": fwi_gradient_step(*DEFAULT_SELECTION),
+                         "fwi_gradient_krylov": fwi_gradient_step("krylov", 20, 8.0)}), flush=True)
         return 0
     if args.case == "signal":
         import torch
