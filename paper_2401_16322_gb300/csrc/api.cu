@@ -1495,7 +1495,7 @@ int run_leapfrog(Ctx& C, std::vector<ewv_model*>& models, double t, double dt, i
             launch_leapfrog3d(C.E->precision, C.E->R, C.E->ntiles, C.E->d_probs, C.E->d_tile_prob,
                               cur, prev, variant, dt, C.s);
         } else if (C.E->precision == EWV_F32) {
-            const int set = tma_map_set(18);
+            const int set = tma_map_set(30);
             if (launch_leapfrog_tma(C.E->R, C.E->d_probs, C.E->d_tbase + (size_t)set * (C.E->nprob + 1),
                                     C.E->nprob, C.E->ntiles_by[set], cur, prev, variant, dt, C.E->d_err,
                                     C.s) != 0)

@@ -186,8 +186,8 @@ int upload_tma_tables(const double* fs_uyy, const double* fs_uy, const double* f
 int build_tensor_maps(std::vector<ProblemDev>& probs, int R, const std::vector<int>& work_vecs,
                       void** d_maps_inout);
 constexpr int TMA_NUM_VARIANTS = 15;
-// One 2D FP32 leap-frog step through the persistent TMA pass (64 x 18 tiles); tbase and
-// ntiles are those of the 18-row map set.
+// One 2D FP32 leap-frog step through the persistent TMA pass (column-pair consumers on
+// 64 x 30 tiles); tbase and ntiles are those of the 30-row map set.
 int launch_leapfrog_tma(int R, const ProblemDev* probs, const int* tbase, int nprob, int ntiles, int cur,
                         int prev, int variant, double dt, int* err, cudaStream_t s);
 // The FWI gradient pass through the persistent TMA pass (64 x 18 tiles, 18-row map set).

@@ -733,6 +733,47 @@ __device__ __forceinline__ void st2(float* p, float2 v, bool both) {
         p[0] = v.x;
 }
 
+// One leap-frog step (Sec. 3.1) at a point of the column-pair form: level n in registers,
+// level n - 1 (u^{n-1}, or d^n in field 1 in difference form, and w^{n-1}) from the A stage
+// box at pa (fields plane floats apart); level n + 1 (u, w_x, w_y) goes to Y and, in
+// difference form, d^{n+1} to field 1 of A.  Same arithmetic as the one-column form.
+__device__ __forceinline__ void lf_point(const TileInfo& ti, const StageArgs& a, const float* pa, int plane, int ii,
+                                         int jj, float uu, float c2v, float lap, float dws, float dux, float duy,
+                                         float bxnv, float bxhv, float bynv, float byhv, float xwxv, float xwyv) {
+    const float idx1 = ti.idx1, idx2 = ti.idx2;
+    const float dt = (float)a.dt, bsum = bxnv + bynv;
+    float rhs = -bxnv * bynv * uu + c2v * (lap * idx2 + dws * idx1);
+    if (ii == ti.src_i && jj == ti.src_j) rhs += ti.sig;
+    const long long o = (long long)jj * ti.pitch + ii;
+    const long long fstr = ti.fstr;
+    // fast (2-ulp) divisions, as in the one-column form
+    float up;
+    if (a.m == 2) {
+        const float hb = 0.5f * bsum * dt;
+        const float dn = __fdividef(pa[plane] * (1.f - hb) + dt * dt * rhs, 1.f + hb);
+        ti.A[fstr + o] = dn;
+        up = uu + dn;
+    } else {
+        const float um = pa[0];
+        const float inv_dt2 = 1.f / (dt * dt), inv_2dt = 1.f / (2.f * dt);
+        up = __fdividef((2.f * uu - um) * inv_dt2 + bsum * um * inv_2dt + rhs, inv_dt2 + bsum * inv_2dt);
+    }
+    float wxp = 0.f, wyp = 0.f;
+    if (ii < ti.nx - 1) {
+        const float gx = (bynv - bxhv) * dux * idx1, wm = pa[2 * plane];
+        wxp = a.m != 1 ? __fdividef((1.f - bxhv * dt) * wm + 2.f * dt * gx, 1.f + bxhv * dt)
+                       : wm + 2.f * dt * (-bxhv * xwxv + gx);
+    }
+    if (jj < ti.ny - 1) {
+        const float gy = (bxnv - byhv) * duy * idx1, wm = pa[3 * plane];
+        wyp = a.m != 1 ? __fdividef((1.f - byhv * dt) * wm + 2.f * dt * gy, 1.f + byhv * dt)
+                       : wm + 2.f * dt * (-byhv * xwyv + gy);
+    }
+    ti.Y[o] = up;
+    ti.Y[2 * fstr + o] = wxp;
+    ti.Y[3 * fstr + o] = wyp;
+}
+
 // One point (tile column tc, tile row lr) from shared memory with the scalar formulas of the
 // one-column form, free-surface rows included, and its epilogue.
 template <int R, int BYv, int EPI, bool HASU, bool HASA>
@@ -800,6 +841,11 @@ __device__ __forceinline__ void tma_point_scalar(const float* st, const TileInfo
     const float* sc2 = st + L::C2_OFF;
     const float* spu = st + L::PU_OFF;
     const float* spa = st + L::PA_OFF;
+    if constexpr (EPI == 2) {
+        lf_point(ti, a, spa + pt, BYv * BX, i, j, uc, sc2[pt], uxx + uyy, dwx + dwy, dux, duy, bxn, bxh, byn,
+                 byh, wxrow[0], wcolv(R));
+        return;
+    }
     const float idx1 = ti.idx1, idx2 = ti.idx2;
     const float xu = uc, xv = sv[pt], xwx = wxrow[0], xwy = wcolv(R);
     float hv = -bxn * byn * xu + sc2[pt] * ((uxx + uyy) * idx2 + (dwx + dwy) * idx1) - (bxn + byn) * xv;
@@ -834,7 +880,7 @@ template <int R, int BYv, int NW, int NSTv, int EPI, bool HASU, bool HASA>
 __global__ void __launch_bounds__(NW * 32 + 32, 1)
 stage_tma_x2_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ tbase, int nprob,
                     int ntiles, int mapset, StageArgs a, int* err) {
-    static_assert(EPI <= 1, "the column-pair consumers serve the integrator passes");
+    static_assert(EPI <= 2, "the column-pair consumers serve the integrator passes and the leap-frog step");
     using L = StageLayout<R, BYv, HASU, HASA>;
     constexpr int CPR = BX / 2;                 // consumer threads per tile row
     constexpr int TPR = NW * 32 / CPR;          // thread rows
@@ -958,6 +1004,16 @@ stage_tma_x2_kernel(const ProblemDev* __restrict__ probs, const int* __restrict_
                         const float byh =
                             btab_at(btab, nbt, fs ? 2 * (ny - j) - 1 : min(2 * j + 3, 2 * (ny - j) - 1));
                         const int pt = lr * BX + c0;
+                        if constexpr (EPI == 2) {
+                            // one leap-frog step per column of the pair
+                            const float2 c2l = lds2(sc2 + pt);
+                            lf_point(ti, a, spa + pt, BYv * BX, i0, j, uc.x, c2l.x, lap.x, dw.x, dux.x, duy.x,
+                                     bxn.x, bxh.x, byn, byh, wp[2].x, wcol[r + R].x);
+                            if (in1)
+                                lf_point(ti, a, spa + pt + 1, BYv * BX, i0 + 1, j, uc.y, c2l.y, lap.y, dw.y, dux.y,
+                                         duy.y, bxn.y, bxh.y, byn, byh, wp[2].y, wcol[r + R].y);
+                            continue;
+                        }
                         const float2 xv = lds2(sv + pt), c2 = lds2(sc2 + pt);
                         const float2 xwx = wp[2], xwy = wcol[r + R];
                         // H v = -bx by u + c^2 (lap u / dx^2 + div w / dx) - (bx + by) v
@@ -1542,29 +1598,30 @@ static int launch_variant(const ProblemDev* probs, const int* tbase, int nprob, 
     return 0;
 }
 
-template <int R, int BYv, int NW, int NSTv, int EPI, bool HASA = true>
+template <int R, int BYv, int NW, int NSTv, int EPI, bool HASA = true, bool HASU = true>
 static int launch_x2(const ProblemDev* probs, const int* tbase, int nprob, int ntiles, const StageArgs& a,
                      int* err, cudaStream_t s) {
     static_assert(map_set_of(BYv) >= 0, "tile height without a map set");
     if (!HASA && a.a >= 0) return -1;    // a pass with an A operand needs the A buffer
-    const size_t smem = (size_t)NSTv * StageLayout<R, BYv, true, HASA>::BYTES + 1024;
+    if (!HASU && a.u >= 0) return -1;    // and one with a U operand the U buffer
+    const size_t smem = (size_t)NSTv * StageLayout<R, BYv, HASU, HASA>::BYTES + 1024;
     static unsigned long long configured = 0;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return -1;
     if (!(configured >> dev & 1ull)) {
-        if (cudaFuncSetAttribute(stage_tma_x2_kernel<R, BYv, NW, NSTv, EPI, true, HASA>,
+        if (cudaFuncSetAttribute(stage_tma_x2_kernel<R, BYv, NW, NSTv, EPI, HASU, HASA>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return -1;
         configured |= 1ull << dev;
     }
     const int grid = ntiles < g_num_sms ? ntiles : g_num_sms;
-    stage_tma_x2_kernel<R, BYv, NW, NSTv, EPI, true, HASA><<<grid, NW * 32 + 32, smem, s>>>(
+    stage_tma_x2_kernel<R, BYv, NW, NSTv, EPI, HASU, HASA><<<grid, NW * 32 + 32, smem, s>>>(
         probs, tbase, nprob, ntiles, map_set_of(BYv), a, err);
     return 0;
 }
 
-// One leap-frog step (EPI 2) on 64 x 18 tiles with 18 consumer warps and no U buffer
-// (4 stages); tbase is the tile list of the 18-row map set.
+// One leap-frog step (EPI 2) on the column-pair consumers (64 x 30 tiles, 15 warps, 3
+// stages, no U buffer); tbase and ntiles are those of the 30-row map set.
 int launch_leapfrog_tma(int R, const ProblemDev* probs, const int* tbase, int nprob, int ntiles, int cur,
                         int prev, int variant, double dt, int* err, cudaStream_t s) {
     if (ntiles <= 0) return nprob > 0 ? -1 : 0;
@@ -1585,8 +1642,8 @@ int launch_leapfrog_tma(int R, const ProblemDev* probs, const int* tbase, int np
     a.x_scale_slot = -1;
     a.m = variant;
     a.dt = dt;
-    if (R == 4) return launch_variant<4, 18, 18, 4, 2, false>(probs, tbase, nprob, ntiles, a, err, s);
-    if (R == 2) return launch_variant<2, 18, 18, 4, 2, false>(probs, tbase, nprob, ntiles, a, err, s);
+    if (R == 4) return launch_x2<4, 30, 15, 3, 2, true, false>(probs, tbase, nprob, ntiles, a, err, s);
+    if (R == 2) return launch_x2<2, 30, 15, 3, 2, true, false>(probs, tbase, nprob, ntiles, a, err, s);
     return -1;
 }
 
