@@ -2738,7 +2738,7 @@ int ewv_adjoint_step(ewv_model_t m, int method, double t, double dt, int deg,
     auto tset_of = [&](const StageArgs& sa) {
         return tma_map_set(tma_variant_tile_height_for(E->tma_variant, sa.a >= 0));
     };
-    const int gset = tma_map_set(18);
+    const int gset = tma_map_set(30), trset = tma_map_set(18);
     auto stage = [&](const StageArgs& sa) {
         if (tma_adj && !sa.transpose && sa.grad && sa.fin_mode == FIN_NONE && sa.d < 0 &&
             launch_grad_tma(R, E->d_adj, E->d_tbase + (size_t)gset * (E->nprob + 1), ns, E->ntiles_by[gset], sa,
@@ -2747,7 +2747,7 @@ int ewv_adjoint_step(ewv_model_t m, int method, double t, double dt, int deg,
             return;
         }
         if (tma_adj && sa.transpose && !sa.grad && sa.fin_mode == FIN_NONE && sa.d < 0 &&
-            launch_transpose_tma(R, E->d_adj, E->d_tbase + (size_t)gset * (E->nprob + 1), ns, E->ntiles_by[gset],
+            launch_transpose_tma(R, E->d_adj, E->d_tbase + (size_t)trset * (E->nprob + 1), ns, E->ntiles_by[trset],
                                  sa, E->d_err, s) == 0) {
             ++m->launches;
             return;

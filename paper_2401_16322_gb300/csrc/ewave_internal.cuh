@@ -190,7 +190,8 @@ constexpr int TMA_NUM_VARIANTS = 15;
 // 64 x 30 tiles); tbase and ntiles are those of the 30-row map set.
 int launch_leapfrog_tma(int R, const ProblemDev* probs, const int* tbase, int nprob, int ntiles, int cur,
                         int prev, int variant, double dt, int* err, cudaStream_t s);
-// The FWI gradient pass through the persistent TMA pass (64 x 18 tiles, 18-row map set).
+// The FWI gradient pass through the persistent TMA pass (column-pair consumers on 64 x 30
+// tiles, the 30-row map set).
 int launch_grad_tma(int R, const ProblemDev* probs, const int* tbase, int nprob, int ntiles,
                     const StageArgs& a, int* err, cudaStream_t s);
 // The transposed pass H^T through the persistent TMA pipeline (FP32, no dot partner, no

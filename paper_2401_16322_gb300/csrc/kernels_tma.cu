@@ -841,6 +841,12 @@ __device__ __forceinline__ void tma_point_scalar(const float* st, const TileInfo
     const float* sc2 = st + L::C2_OFF;
     const float* spu = st + L::PU_OFF;
     const float* spa = st + L::PA_OFF;
+    if constexpr (EPI == 3) {
+        float* G = (float*)a.grad + (long long)ti.shot * ti.fstr;
+        G[(long long)j * ti.pitch + i] +=
+            (float)a.gscale * spa[BYv * BX + pt] * ((uxx + uyy) * ti.idx2 + (dwx + dwy) * ti.idx1);
+        return;
+    }
     if constexpr (EPI == 2) {
         lf_point(ti, a, spa + pt, BYv * BX, i, j, uc, sc2[pt], uxx + uyy, dwx + dwy, dux, duy, bxn, bxh, byn,
                  byh, wxrow[0], wcolv(R));
@@ -880,7 +886,7 @@ template <int R, int BYv, int NW, int NSTv, int EPI, bool HASU, bool HASA>
 __global__ void __launch_bounds__(NW * 32 + 32, 1)
 stage_tma_x2_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ tbase, int nprob,
                     int ntiles, int mapset, StageArgs a, int* err) {
-    static_assert(EPI <= 2, "the column-pair consumers serve the integrator passes and the leap-frog step");
+    static_assert(EPI <= 3, "EPI 0 / 1: integrator passes, 2: leap-frog step, 3: gradient pass");
     using L = StageLayout<R, BYv, HASU, HASA>;
     constexpr int CPR = BX / 2;                 // consumer threads per tile row
     constexpr int TPR = NW * 32 / CPR;          // thread rows
@@ -1004,6 +1010,22 @@ stage_tma_x2_kernel(const ProblemDev* __restrict__ probs, const int* __restrict_
                         const float byh =
                             btab_at(btab, nbt, fs ? 2 * (ny - j) - 1 : min(2 * j + 3, 2 * (ny - j) - 1));
                         const int pt = lr * BX + c0;
+                        if constexpr (EPI == 3) {
+                            // FWI gradient pass: grad += gscale q_v (L u + D w) of X (m = c^2);
+                            // q's fields ride in the A box
+                            float* G = (float*)a.grad + (long long)ti.shot * ti.fstr +
+                                       (long long)j * ti.pitch + i0;
+                            const float2 qv = lds2(spa + BYv * BX + pt);
+                            const float2 gv = mul2(mul2(f2s((float)a.gscale), qv),
+                                                   fma2(lap, f2s(ti.idx2), mul2(dw, f2s(ti.idx1))));
+                            if (in1) {
+                                float2 g0 = *reinterpret_cast<float2*>(G);
+                                *reinterpret_cast<float2*>(G) = add2(g0, gv);
+                            } else {
+                                G[0] += gv.x;
+                            }
+                            continue;
+                        }
                         if constexpr (EPI == 2) {
                             // one leap-frog step per column of the pair
                             const float2 c2l = lds2(sc2 + pt);
@@ -1648,7 +1670,8 @@ int launch_leapfrog_tma(int R, const ProblemDev* probs, const int* tbase, int np
 }
 
 // The FWI gradient pass (EPI 3): grad += gscale q_v (L u + D w) of vector a.x, q = a.gq (its
-// four fields ride in the A box); same tiles as the leap-frog step.
+// four fields ride in the A box); column-pair consumers on the leap-frog step's tiles
+// (64 x 30, 15 warps, 3 stages; the 30-row map set).
 int launch_grad_tma(int R, const ProblemDev* probs, const int* tbase, int nprob, int ntiles,
                     const StageArgs& a_in, int* err, cudaStream_t s) {
     if (ntiles <= 0) return nprob > 0 ? -1 : 0;
@@ -1663,8 +1686,8 @@ int launch_grad_tma(int R, const ProblemDev* probs, const int* tbase, int nprob,
     a.a = a.gq;
     a.y_out = -1;
     a.acc_out = -1;
-    if (R == 4) return launch_variant<4, 18, 18, 4, 3, false>(probs, tbase, nprob, ntiles, a, err, s);
-    if (R == 2) return launch_variant<2, 18, 18, 4, 3, false>(probs, tbase, nprob, ntiles, a, err, s);
+    if (R == 4) return launch_x2<4, 30, 15, 3, 3, true, false>(probs, tbase, nprob, ntiles, a, err, s);
+    if (R == 2) return launch_x2<2, 30, 15, 3, 3, true, false>(probs, tbase, nprob, ntiles, a, err, s);
     return -1;
 }
 
