@@ -273,18 +273,6 @@ int ewv_step_krylov_adaptive(ewv_model_t model, double t, double dt, double tol,
  * Gram-Schmidt.  A batch uses the window of its first model. */
 int ewv_set_krylov_window(ewv_model_t model, int window);
 
-/* Gram-Schmidt order of the FP32 Krylov step (the FP64 step always runs the modified order of
- * Sec. 3.2's listing).  EWV_KRYLOV_GS_MODIFIED: one pass per basis vector, as the listing.
- * EWV_KRYLOV_GS_PAIRED (default): each pass subtracts two basis vectors at once; the second
- * coefficient is the modified Gram-Schmidt value <w - h_{k,j} v_k, v_{k+1}>, formed as
- * <w, v_{k+1}> - h_{k,j} <v_k, v_{k+1}> from dot products the previous pass took, so the
- * Hessenberg matrix equals the modified order's in exact arithmetic and the passes read a
- * quarter fewer bytes.  Applies to ewv_step_krylov and the batch step; the adaptive step and
- * the adjoints keep the modified order. */
-#define EWV_KRYLOV_GS_MODIFIED 0
-#define EWV_KRYLOV_GS_PAIRED 1
-int ewv_set_krylov_gram_schmidt(ewv_model_t model, int mode);
-
 /* Sec. 3.2 HORK (scheme EWV_METHOD_HORK, `stages` = m) or Sec. 3.1 RK3-2 / RK4-4
  * (EWV_METHOD_RK32 / EWV_METHOD_RK44; stages ignored). */
 int ewv_step_rk(ewv_model_t model, double t, double dt, int scheme, int stages, int nsteps);

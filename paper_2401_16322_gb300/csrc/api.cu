@@ -161,7 +161,6 @@ struct ewv_model {
     int lf_variant = EWV_LEAPFROG_AVERAGED;
     int store_bf16 = 0;         // storage-precision experiment (ewv_set_storage_rounding)
     int kry_window = 0;         // Krylov orthogonalisation window (0 = full Gram-Schmidt)
-    int kry_gs = EWV_KRYLOV_GS_PAIRED;   // FP32 Gram-Schmidt order (ewv_set_krylov_gram_schmidt)
     int hork_form = EWV_HORK_LOW_STORAGE;   // evaluation order of the HORK polynomial
     int kry_adjoint = EWV_KRYLOV_ADJOINT_EXACT;   // which Krylov adjoint ewv_adjoint_step runs
     bool lf_history_valid = false;
@@ -522,8 +521,7 @@ int build_engine(Engine* E, std::string& err) {
     E->d_counters = nullptr;
     CUDA_OR_FAIL(err, cudaMalloc(&E->d_probs, sizeof(ProblemDev) * E->nprob));
     CUDA_OR_FAIL(err, cudaMalloc(&E->d_tile_prob, sizeof(int) * (size_t)tb));
-    // (three partials per chunk for the paired Gram-Schmidt passes)
-    CUDA_OR_FAIL(err, cudaMalloc(&E->d_partials, sizeof(double) * (size_t)std::max(tb, 3 * E->nchunks)));
+    CUDA_OR_FAIL(err, cudaMalloc(&E->d_partials, sizeof(double) * (size_t)std::max(tb, E->nchunks)));
     CUDA_OR_FAIL(err, cudaMalloc(&E->d_counters, sizeof(unsigned int) * E->nprob));
     CUDA_OR_FAIL(err, cudaMemcpy(E->d_probs, E->probs.data(), sizeof(ProblemDev) * E->nprob,
                                  cudaMemcpyHostToDevice));
@@ -664,7 +662,7 @@ struct Ctx {
         ++*launches;
     }
     void point(const PointArgs& pa) {
-        if (pa.mode <= 2 || pa.mode == 5 || pa.mode >= 7)   // norm, MGS, combine, dots: flat
+        if (pa.mode <= 2 || pa.mode == 5 || pa.mode == 7)   // norm, MGS, combine, dots: flat
             launch_point_flat(E->precision, E->nchunks, E->d_probs, E->d_pbase, E->nprob, pa, s);
         else
             launch_point(E->precision, E->ntiles, E->d_probs, E->d_tile_prob, pa, s);
@@ -1066,7 +1064,6 @@ int run_krylov(Ctx& C, double t, double dt, int m, int nsteps, int* info) {
     // a flat pass then forms <q_{j+1}, q_k0> with the same finalisation (FP64 keeps the fused
     // dot of the plain stencil kernel)
     const bool split_dot = C.E->precision == EWV_F32;
-    const bool paired = split_dot && !C.E->models.empty() && C.E->models[0]->kry_gs == EWV_KRYLOV_GS_PAIRED;
     int rc0 = C.step_loop(nsteps, EWV_METHOD_KRYLOV, m, dt, tol, (double)window, 0, 1, [&](int) {
         C.prologue(PRO_KRYLOV, m);
         PointArgs pn{};
@@ -1099,35 +1096,6 @@ int run_krylov(Ctx& C, double t, double dt, int m, int nsteps, int* info) {
                 a.fin_mode = FIN_NONE;
             }
             C.stage(a);
-            if (paired) {
-                // paired Gram-Schmidt (krylov_finalize_pair): the dots of the first pair after
-                // the product, then passes that subtract one pair and form the next pair's
-                // dots; the last one forms |q_{j+1}|^2 (none at j = m, whose h_{m+1,m} the
-                // result does not use, and whose last pair needs no subtraction)
-                std::vector<std::pair<int, int>> grp;
-                for (int k = k0; k <= j; k += 2) grp.emplace_back(k, k + 1 <= j ? k + 1 : 0);
-                PointArgs pd{};
-                pd.mode = 8;
-                pd.j = j;
-                pd.m = m;
-                pd.tol = tol;
-                pd.n1 = grp[0].first;
-                pd.n2 = grp[0].second;
-                pd.partials = C.E->d_partials;
-                pd.counters = C.E->d_counters;
-                C.point(pd);
-                const int ng = (int)grp.size();
-                for (int g = 0; g < (j == m ? ng - 1 : ng); ++g) {
-                    PointArgs pp = pd;
-                    pp.mode = 9;
-                    pp.k = grp[g].first;
-                    pp.k2 = grp[g].second;
-                    pp.n1 = g + 1 < ng ? grp[g + 1].first : 0;
-                    pp.n2 = g + 1 < ng ? grp[g + 1].second : 0;
-                    C.point(pp);
-                }
-                continue;
-            }
             if (split_dot) {
                 PointArgs pd{};
                 pd.mode = 5;
@@ -2131,15 +2099,6 @@ int ewv_set_krylov_window(ewv_model_t m, int window) {
     if (!m || window < 0) return EWV_ERR_INVALID_ARG;
     if (m->kry_window != window) {
         m->kry_window = window;
-        ++m->version;   // drops the captured step graphs
-    }
-    return EWV_OK;
-}
-
-int ewv_set_krylov_gram_schmidt(ewv_model_t m, int mode) {
-    if (!m || (mode != EWV_KRYLOV_GS_MODIFIED && mode != EWV_KRYLOV_GS_PAIRED)) return EWV_ERR_INVALID_ARG;
-    if (m->kry_gs != mode) {
-        m->kry_gs = mode;
         ++m->version;   // drops the captured step graphs
     }
     return EWV_OK;

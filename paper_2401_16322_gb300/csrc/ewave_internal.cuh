@@ -138,18 +138,12 @@ struct StageArgs {
 struct PointArgs {
     int mode;        // 0: |q1|^2 (norm); 1: MGS pass; 2: Krylov combine; 3: copy; 4: swap;
                      // 5: <q_{j+1}, q_k> after a matrix-vector product (flat); 6: zero the
-                     // fields fmask of vector dst; 7: |slot j+1|^2 into kry[KRY_AN] (flat);
-                     // 8, 9: paired Gram-Schmidt (below)
+                     // fields fmask of vector dst; 7: |slot j+1|^2 into kry[KRY_AN] (flat)
     int j, k, m;
     int src, dst;    // copy / swap vectors; combine: destination vector (mode 2)
     int notail;      // mode 0: 1 = start an Arnoldi process without the augmented tail;
                      // 2 = start from the tail already in slot 1 (adaptive substeps)
     int fmask;       // fields for copy / swap (bit f)
-    // modes 8 and 9 (paired Gram-Schmidt, FP32 Krylov): k and k2 = the pair whose update a
-    // mode-9 pass applies (k2 = 0: a single vector), n1 and n2 = the pair whose dot products
-    // it forms next (n1 = 0: the norm of the result instead; n2 = 0: a single vector).  Mode 8
-    // forms the dots of the pair (n1, n2) after a matrix-vector product.
-    int k2, n1, n2;
     double tol;
     double* partials;
     unsigned int* counters;

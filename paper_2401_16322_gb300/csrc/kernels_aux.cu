@@ -388,7 +388,7 @@ point_flat_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ 
     const int pid = flat_problem(pbase, nprob, blockIdx.x);
     const ProblemDev* P = probs + pid;
     double* kry = P->kry;
-    if ((pa.mode == 1 || pa.mode == 5 || pa.mode == 8 || pa.mode == 9) && kry[KRY_ACTIVE] == 0.0) return;
+    if ((pa.mode == 1 || pa.mode == 5) && kry[KRY_ACTIVE] == 0.0) return;
     if (pa.mode == 2 && (kry[KRY_NONFINITE] != 0.0 || kry[KRY_SKIP] != 0.0)) return;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int nf = P->nfields;   // 4 (2D) or 6 (3D: w_z and psi added)
@@ -408,46 +408,6 @@ point_flat_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ 
             for (int k = 1; k <= meff; ++k) fma16(acc, s_coef[k - 1], reinterpret_cast<const V*>(vptr<T>(P, k - 1))[q]);
             St[q] = acc;
         }
-        return;
-    }
-    if (pa.mode == 8 || pa.mode == 9) {
-        // paired Gram-Schmidt: mode 9 subtracts the pair (k, k2) from w, both modes form the
-        // dot products with the pair (n1, n2) (or |w|^2 when n1 = 0); krylov_finalize_pair
-        V* W = reinterpret_cast<V*>(vptr<T>(P, pa.j));                                 // slot j+1
-        const bool apply = pa.mode == 9;
-        const V* Qa = apply ? reinterpret_cast<const V*>(vptr<T>(P, pa.k - 1)) : nullptr;
-        const V* Qb = apply && pa.k2 > 0 ? reinterpret_cast<const V*>(vptr<T>(P, pa.k2 - 1)) : nullptr;
-        const V* Na = pa.n1 > 0 ? reinterpret_cast<const V*>(vptr<T>(P, pa.n1 - 1)) : nullptr;
-        const V* Nb = pa.n2 > 0 ? reinterpret_cast<const V*>(vptr<T>(P, pa.n2 - 1)) : nullptr;
-        const T ca = apply ? (T)(kry[KRY_H + (pa.k - 1) * MAX_M + (pa.j - 1)] * kry[KRY_S + pa.k]) : T(0);
-        const T cb = Qb ? (T)(kry[KRY_H + (pa.k2 - 1) * MAX_M + (pa.j - 1)] * kry[KRY_S + pa.k2]) : T(0);
-        double da = 0.0, db = 0.0, dc = 0.0;
-        for (long long q = q0 + tid; q < q1; q += NTHREADS) {
-            V w = W[q];
-            if (apply) {
-                w = axpy16(w, ca, Qa[q]);
-                if (Qb) w = axpy16(w, cb, Qb[q]);
-                W[q] = w;
-            }
-            if (Na) {
-                const V na = Na[q];
-                da += dotv(w, na);
-                if (Nb) {
-                    const V nb = Nb[q];
-                    db += dotv(w, nb);
-                    dc += dotv(na, nb);
-                }
-            } else {
-                da += dotv(w, w);
-            }
-        }
-        // the last column of a full-dimension step needs no norm (h_{m+1,m} is unused)
-        if (apply && pa.n1 == 0 && pa.j == pa.m) return;
-        double bs[3];
-        bs[0] = block_sum_fixed(da, red);
-        bs[1] = block_sum_fixed(db, red);
-        bs[2] = block_sum_fixed(dc, red);
-        partial3_and_finalize_pair(P, pid, pa, bs, red, &s_last, blockIdx.x, __ldg(pbase + pid), P->pchunks);
         return;
     }
     double accd = 0.0;

@@ -141,77 +141,6 @@ __device__ inline void krylov_finalize(const ProblemDev* P, int mode, int j, int
     }
 }
 
-// Paired Gram-Schmidt (FP32 Krylov step; the same h_{k,j} as modified Gram-Schmidt in exact
-// arithmetic).  A pass that subtracts the pair (ka, kb) from w also forms the dot products
-// with the next pair (na, nb): a = <w', q_na>, b = <w', q_nb>, c = <q_na, q_nb> on the grid, w'
-// the updated vector.  With the tails, h_{na,j} = s_na <w', q_na>, and the second one is the
-// modified Gram-Schmidt value <w' - h_{na,j} v_na, v_nb> = s_nb <w', q_nb> - h_{na,j} <v_na, v_nb>,
-// so the next pass can subtract both at once.  kb = 0 / nb = 0: a single vector; na = 0: the
-// pass forms |w'|^2 instead (h_{j+1,j}, as FIN_MGS at k = j); ka = 0: the first pair after the
-// matrix-vector product (the tail of w is set as FIN_MATVEC does).
-__device__ inline void krylov_finalize_pair(const ProblemDev* P, int j, int ka, int kb, int na, int nb, int m,
-                                            double tol, const double* tot) {
-    double* kry = P->kry;
-    const int p = P->p;
-    if (!isfinite(tot[0]) || !isfinite(tot[1]) || !isfinite(tot[2])) {
-        kry[KRY_NONFINITE] = 1.0;
-        kry[KRY_ACTIVE] = 0.0;
-        return;
-    }
-    double* tw = kry_tail(kry, j + 1);
-    auto hh = [&](int k) -> double& { return kry[KRY_H + (k - 1) * MAX_M + (j - 1)]; };
-    if (ka == 0) {
-        const double sj = kry[KRY_S + j];
-        const double* tj = kry_tail(kry, j);
-        for (int q = 0; q < p - 1; ++q) tw[q] = sj * tj[q + 1];   // J (s_j tail_j)
-        tw[p - 1] = 0.0;
-    } else {
-        const double* ta = kry_tail(kry, ka);
-        const double ca = hh(ka) * kry[KRY_S + ka];
-        for (int q = 0; q < p; ++q) tw[q] -= ca * ta[q];
-        if (kb > 0) {
-            const double* tb = kry_tail(kry, kb);
-            const double cb = hh(kb) * kry[KRY_S + kb];
-            for (int q = 0; q < p; ++q) tw[q] -= cb * tb[q];
-        }
-    }
-    if (na > 0) {
-        const double* ta = kry_tail(kry, na);
-        double da = 0.0;
-        for (int q = 0; q < p; ++q) da += tw[q] * ta[q];
-        const double sa = kry[KRY_S + na];
-        const double ha = sa * (tot[0] + da);
-        hh(na) = ha;
-        if (nb > 0) {
-            const double* tb = kry_tail(kry, nb);
-            double db = 0.0, dc = 0.0;
-            for (int q = 0; q < p; ++q) {
-                db += tw[q] * tb[q];
-                dc += ta[q] * tb[q];
-            }
-            const double sb = kry[KRY_S + nb];
-            hh(nb) = sb * (tot[1] + db) - ha * sa * sb * (tot[2] + dc);
-        }
-        return;
-    }
-    // |w'|^2 -> h_{j+1,j}, the next scale and the breakdown test (as FIN_MGS at k = j)
-    double d = 0.0;
-    for (int q = 0; q < p; ++q) d += tw[q] * tw[q];
-    const double h = sqrt(tot[0] + d);
-    if (j < m) {
-        kry[KRY_H + j * MAX_M + (j - 1)] = h;
-        if (!(h > tol)) {
-            kry[KRY_ACTIVE] = 0.0;
-            kry[KRY_MEFF] = (double)j;
-        } else {
-            kry[KRY_S + j + 1] = 1.0 / h;
-            double sg = 0.0;
-            for (int q = 0; q < p; ++q) sg += kry[KRY_W + q] * tw[q];
-            P->sigma[j + 1] = P->has_src ? sg : 0.0;
-        }
-    }
-}
-
 // Block-wide fixed-order sum of one double per thread (blockDim.x * blockDim.y == NTHREADS).
 __device__ __forceinline__ double block_sum_fixed(double v, double* red) {
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
@@ -248,35 +177,6 @@ __device__ inline void partial_and_finalize_at(const ProblemDev* P, int pid, con
     if (tid == 0) {
         krylov_finalize(P, a.fin_mode, a.fin_j, a.fin_k, a.m, a.tol, tot);
         a.counters[pid] = 0u;
-        __threadfence();
-    }
-}
-
-// Three partial sums per block (slots 3 slot .. 3 slot + 2) for the paired Gram-Schmidt
-// passes; the problem's last block sums each in a fixed order and runs krylov_finalize_pair.
-__device__ inline void partial3_and_finalize_pair(const ProblemDev* P, int pid, const PointArgs& pa,
-                                                  const double* bp_on_t0, double* red, int* s_last, int slot,
-                                                  int base, int count) {
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    if (tid == 0) {
-        for (int i = 0; i < 3; ++i) pa.partials[3 * (long long)slot + i] = bp_on_t0[i];
-        __threadfence();
-        const unsigned int prev = atomicAdd(pa.counters + pid, 1u);
-        *s_last = (prev == (unsigned int)(count - 1));
-    }
-    __syncthreads();
-    if (!*s_last) return;
-    __threadfence();
-    double tot[3];
-    for (int i = 0; i < 3; ++i) {
-        double v = 0.0;
-        for (int t = tid; t < count; t += NTHREADS) v += __ldcg(pa.partials + 3 * (long long)(base + t) + i);
-        tot[i] = block_sum_fixed(v, red);
-    }
-    if (tid == 0) {
-        const int ka = pa.mode == 8 ? 0 : pa.k;
-        krylov_finalize_pair(P, pa.j, ka, pa.mode == 8 ? 0 : pa.k2, pa.n1, pa.n2, pa.m, pa.tol, tot);
-        pa.counters[pid] = 0u;
         __threadfence();
     }
 }

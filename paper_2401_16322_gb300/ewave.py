@@ -42,7 +42,6 @@ EXPORTS = [
     "ewv_set_kernel_variant", "ewv_kernel_variant", "ewv_batch_set_kernel_variant",
     "ewv_batch_kernel_variant", "ewv_set_source_receivers3d", "ewv_set_storage_rounding",
     "ewv_set_krylov_window",
-    "ewv_set_krylov_gram_schmidt",
     "ewv_set_hork_form",
 ]
 
@@ -109,7 +108,6 @@ def load_library(path=LIB_PATH):
         "ewv_set_source_receivers3d": ([vp, i, d, d, d, d, d, d, i, dp, ip32, ip32], i),
         "ewv_set_storage_rounding": ([vp, i], i),
         "ewv_set_krylov_window": ([vp, i], i),
-        "ewv_set_krylov_gram_schmidt": ([vp, i], i),
         "ewv_set_hork_form": ([vp, i], i),
         "ewv_set_faber_ellipse": ([vp, d, d, d], i),
         "ewv_get_faber_ellipse": ([vp, dp, dp, dp], i),
@@ -293,12 +291,6 @@ class Model:
     def set_krylov_window(self, q):
         """Orthogonalise each Krylov vector against the q most recent ones only (0: all)."""
         self._check(self.lib.ewv_set_krylov_window(self.h, int(q)), "krylov_window")
-
-    def set_krylov_gram_schmidt(self, mode):
-        """FP32 Krylov Gram-Schmidt order: 'paired' (default: two basis vectors per pass,
-        the modified order's coefficients) or 'modified' (one per pass, Sec. 3.2's listing)."""
-        self._check(self.lib.ewv_set_krylov_gram_schmidt(self.h, {"modified": 0, "paired": 1}[mode]),
-                    "krylov_gram_schmidt")
 
     def set_storage_rounding(self, bf16):
         """Round every stored integrator vector to bfloat16 (storage-precision experiment)."""
