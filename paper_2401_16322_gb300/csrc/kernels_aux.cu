@@ -433,10 +433,15 @@ point_flat_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ 
         const V* Qk = reinterpret_cast<const V*>(vptr<T>(P, pa.k - 1));   // slot k
         const V* Qn = pa.k < pa.j ? reinterpret_cast<const V*>(vptr<T>(P, pa.k)) : nullptr;
         const T coef = (T)(kry[KRY_H + (pa.k - 1) * MAX_M + (pa.j - 1)] * kry[KRY_S + pa.k]);
+#pragma unroll 2
         for (long long q = q0 + tid; q < q1; q += NTHREADS) {
-            const V w = axpy16(W[q], coef, Qk[q]);
+            const V wq = W[q], qk = Qk[q];
+            // every operand is loaded before the store: the loads may not move past a store
+            // the compiler cannot prove disjoint, which would cost a second memory round trip
+            const V qn = Qn ? Qn[q] : V{};
+            const V w = axpy16(wq, coef, qk);
             W[q] = w;
-            accd += dotv(w, Qn ? Qn[q] : w);
+            accd += dotv(w, Qn ? qn : w);
         }
     }
     if (pa.mode == 1 && pa.k == pa.j && pa.j == pa.m) return;   // h_{m+1,m} unused
