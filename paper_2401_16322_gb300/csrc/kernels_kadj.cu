@@ -223,12 +223,15 @@ kadj_flat_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ p
             const V* Qn = reinterpret_cast<const V*>(kvec<T>(P, j + 1));
             const V* Vb = reinterpret_cast<const V*>(kvec<T>(P, m + 2 + j));
             const V* Qd = ka.dot >= 0 && j <= me ? reinterpret_cast<const V*>(kvec<T>(P, ka.dot)) : nullptr;
+            // every operand is loaded before the stores (one memory round trip per element)
             for (long long q = q0 + tid; q < q1; q += NTHREADS) {
                 const V qn = Qn[q];
-                const V wb = live ? Ops::fma(cq, qn, Ops::scale(hinv, Vb[q])) : Ops::zero();
+                const V vbq = Vb[q];
+                const V qd = Qd ? Qd[q] : Ops::zero();
+                const V wb = live ? Ops::fma(cq, qn, Ops::scale(hinv, vbq)) : Ops::zero();
                 Wb[q] = wb;
                 Wc[q] = qn;
-                if (Qd) acc += Ops::dot(wb, Qd[q]);
+                if (Qd) acc += Ops::dot(wb, qd);
             }
             break;
         }
@@ -247,6 +250,7 @@ kadj_flat_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ p
                 const V wb = Wb[q];
                 V wc = Wc[q];
                 V vb = Vb[q];
+                const V qd = Qd ? Qd[q] : Ops::zero();   // before the stores, as above
                 if (!only) {
                     wc = Ops::fma(hs, qk, wc);                 // w_before(k)
                     Wc[q] = wc;
@@ -255,7 +259,7 @@ kadj_flat_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ p
                 Vb[q] = Ops::fma(hbar, wc, vb);
                 const V wn = Ops::fma(hbs, qk, wb);
                 Wb[q] = wn;
-                if (Qd) acc += Ops::dot(wn, Qd[q]);
+                if (Qd) acc += Ops::dot(wn, qd);
             }
             break;
         }
