@@ -679,17 +679,20 @@ leapfrog_adjoint_kernel(const ProblemDev* __restrict__ probs, const int* __restr
                 Q[3 * fstr + o] = hy ? T(2) * dt * lwy / (T(1) + byh * dt) : T(0);
             } else {
                 const T* Y = vec_ptr<T>(P, yv);
-                const T lum = L0[fstr + o];
-                L0[o] = Y[o] + T(2) * inv_dt2 * sn * lu + lum;
+                // every operand is loaded before the first store (one memory round trip)
+                const T lum = L0[fstr + o], yu = Y[o];
+                const T ywx = hx ? Y[2 * fstr + o] : T(0), l1x = hx ? L1[2 * fstr + o] : T(0);
+                const T ywy = hy ? Y[3 * fstr + o] : T(0), l1y = hy ? L1[3 * fstr + o] : T(0);
+                L0[o] = yu + T(2) * inv_dt2 * sn * lu + lum;
                 L0[fstr + o] = sn * (bsum * inv_2dt - inv_dt2) * lu;
                 if (hx) {
                     const T qx = T(2) * dt * lwx / (T(1) + bxh * dt);
-                    L0[2 * fstr + o] = Y[2 * fstr + o] + bxh * qx + L1[2 * fstr + o];
+                    L0[2 * fstr + o] = ywx + bxh * qx + l1x;
                     L1[2 * fstr + o] = (T(1) - bxh * dt) / (T(1) + bxh * dt) * lwx;
                 }
                 if (hy) {
                     const T qy = T(2) * dt * lwy / (T(1) + byh * dt);
-                    L0[3 * fstr + o] = Y[3 * fstr + o] + byh * qy + L1[3 * fstr + o];
+                    L0[3 * fstr + o] = ywy + byh * qy + l1y;
                     L1[3 * fstr + o] = (T(1) - byh * dt) / (T(1) + byh * dt) * lwy;
                 }
             }
