@@ -430,14 +430,15 @@ int ewv_batch_enable_graphs(ewv_batch_t batch, int enable);
  * 5 = (20, 20, 3), 6 = (18, 18, 3), each consumer thread on one column; 7 = (18, 9, 3),
  * 8 = (16, 8, 3), 9 = (18, 18, 3), 10 = (24, 12, 2), each consumer thread on two adjacent
  * columns (8-byte shared loads, packed FP32 pair arithmetic); 11 = (24, 12, 3),
- * 12 = (36, 9, 2), 13 = (28, 14, 3) and 14 = (30, 15, 3) are composite: passes without an A operand (Horner HORK passes, Krylov
- * products) run these column-pair shapes without the A stage buffer, passes with one run
+ * 12 = (36, 9, 2), 13 = (28, 14, 3) and 14 = (30, 15, 3) are composite: passes without an A
+ * operand (Horner HORK passes, Krylov products) run these column-pair shapes without the A
+ * stage buffer, passes with one run
  * variant 7 (the reported shape is the no-A one).  The autotuner's score is the sum of a
  * probe pass with and one without an A operand.  The leap-frog step and the FWI gradient
  * pass always run the column-pair form on 64 x 30 tiles with 15 warps, the transposed pass
  * on 64 x 18 tiles with 9 warps;
  * tiles are 64 columns wide with a 4-column / R-row halo.  With v = -1 (default) the first
- * FP32 step call times every variant on a probe pass over the engine's own problems and
+ * FP32 step call times every variant on the probe passes over the engine's own problems and
  * keeps the fastest; ewv_*kernel_variant reports the choice, its shape and the probe times
  * (us[EWV_NUM_KERNEL_VARIANTS], -1 where a variant could not launch).  Variant 4 = (16, 16,
  * 4) without the U stage buffer: passes that read a U vector run variant 0 under it.
