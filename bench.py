@@ -332,7 +332,9 @@ def fwi_gradient_step(method, m, dt_over_cfl):
     step's exponential, because the exact adjoint of a Krylov step of dimension 20 at 8 x
     the leap-frog step is ill-conditioned over this run (its cotangent grows without bound
     while the source is still silent); tests/test_gpu_fwi.py checks both against central
-    differences on this workload."""
+    differences on this workload.  The Krylov forward keeps every step's four dense states
+    (ewv_step_krylov_dense), so its adjoint runs no forward Arnoldi; the recomputing form is
+    timed beside it."""
     import numpy as np
     import torch
     from paper_2401_16322_gb300.fwi import FaberFWI
@@ -348,28 +350,37 @@ def fwi_gradient_step(method, m, dt_over_cfl):
     common_ellipse([md], c_max)
     if method == "krylov":
         md.set_krylov_adjoint("exponential")
-    fwi = FaberFWI(md, dt, m, nsteps, len(w.shots[0].rec), method=base_method([md], method))
-    d_obs = fwi.forward(w.c ** 2)
     c_init = smooth_gradient_with_anomalies(w.nx, w.ny, 0, dx=w.dx, amps=())
-    fwi.backward(fwi.forward(c_init ** 2) - d_obs)     # warm-up: workspaces, graphs, tuning
-    torch.cuda.synchronize()
-    e0, em, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-    e0.record()
-    seis = fwi.forward(c_init ** 2)
-    em.record()
-    grad = fwi.backward(seis - d_obs)
-    e1.record()
-    torch.cuda.synchronize()
-    ok = bool(torch.isfinite(grad).all())
-    mem = fwi.ckpt.numel() * fwi.ckpt.element_size()
+
+    def timed(dense):
+        fwi = FaberFWI(md, dt, m, nsteps, len(w.shots[0].rec), method=base_method([md], method),
+                       dense_states=dense)
+        d_obs = fwi.forward(w.c ** 2)
+        fwi.backward(fwi.forward(c_init ** 2) - d_obs)     # warm-up: workspaces, graphs, tuning
+        torch.cuda.synchronize()
+        e0, em, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record()
+        seis = fwi.forward(c_init ** 2)
+        em.record()
+        grad = fwi.backward(seis - d_obs)
+        e1.record()
+        torch.cuda.synchronize()
+        out = {"seconds": e0.elapsed_time(e1) * 1e-3, "forward_s": e0.elapsed_time(em) * 1e-3,
+               "backward_s": em.elapsed_time(e1) * 1e-3, "stored_bytes": fwi.stored_bytes(),
+               "gradient_finite": bool(torch.isfinite(grad).all())}
+        del fwi
+        return out
+
+    res = timed(method == "krylov")
+    res.update({"method": method, "nsteps": nsteps,
+                "adjoint": ("adjoint of the step's exponential from the forward's dense states "
+                            "(FD-checked to 2e-3 on this workload)"
+                            if method == "krylov" else "exact discrete adjoint"),
+                "dt_ms": dt * 1e3, "m": m, "shots": len(w.shots), "grid": f"{w.nx}x{w.ny}"})
+    if method == "krylov":
+        res["recomputing_forward_arnoldi"] = timed(False)
     md.close()
-    return {"seconds": e0.elapsed_time(e1) * 1e-3, "forward_s": e0.elapsed_time(em) * 1e-3,
-            "backward_s": em.elapsed_time(e1) * 1e-3, "method": method, "nsteps": nsteps,
-            "adjoint": ("adjoint of the step's exponential (FD-checked to 2e-3 on this workload)"
-                        if method == "krylov" else "exact discrete adjoint"),
-            "dt_ms": dt * 1e3, "m": m,
-            "shots": len(w.shots), "grid": f"{w.nx}x{w.ny}", "checkpoint_bytes": mem,
-            "gradient_finite": ok}
+    return res
 
 
 # Delta-t_max scan of the 3D side run: (method, m values, step multiples, largest first)
@@ -1013,8 +1024,10 @@ def run_ours(args):
             "fwi_gradient": ({k_: fp.get(k_) for k_ in ("method", "m", "dt_ms", "nsteps", "seconds",
                                                         "forward_s", "backward_s", "gradient_finite")}
                              if fp else None),
-            "fwi_gradient_krylov": ({k_: fk.get(k_) for k_ in ("m", "dt_ms", "nsteps", "seconds",
-                                                               "forward_s", "backward_s", "adjoint")}
+            "fwi_gradient_krylov": ({**{k_: fk.get(k_) for k_ in ("m", "dt_ms", "nsteps", "seconds",
+                                                                  "forward_s", "backward_s", "stored_bytes",
+                                                                  "adjoint")},
+                                     "recomputing_s": (fk.get("recomputing_forward_arnoldi") or {}).get("seconds")}
                                     if fk else None),
             "config5_3d": ({"selected": {k_: (x3.get("selected") or {}).get(k_) for k_ in
                                          ("method", "m", "dt_over_leapfrog_step", "time_to_T_s",

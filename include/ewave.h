@@ -242,6 +242,18 @@ int ewv_step_faber(ewv_model_t model, double t, double dt, int degree, int nstep
  * enqueueing, like the other step calls. */
 int ewv_step_krylov(ewv_model_t model, double t, double dt, int m, int nsteps, int* info);
 
+/* One ewv_step_krylov step (nsteps = 1, no info) that also writes the step's dense states
+ *   x_q = [I 0] beta V_m exp(tau_q H_m) e_1 ~ [I 0] exp(tau_q dt H~) [U^n; e_p],  q = 0..3,
+ * tau_q the 4-point Gauss-Legendre nodes on [0, 1], from the step's own Arnoldi basis and
+ * Hessenberg matrix (Sec. 3.2) into dense: 4 x nshots padded state vectors of the model's
+ * precision, device memory, caller-owned, 256-B aligned, laid out [q][shot].  These are the
+ * forward states the adjoint of the step's exponential integrates against (see
+ * ewv_adjoint_step_krylov_dense): storing them trades 4 vectors per step of memory (Sec. 3.3,
+ * N_mem) for the forward Arnoldi the adjoint would otherwise recompute.  The call runs
+ * without step graphs.  Errors as ewv_step_krylov; BAD_SIZE_OR_ALIGNMENT for a misaligned
+ * buffer. */
+int ewv_step_krylov_dense(ewv_model_t model, double t, double dt, int m, void* dense);
+
 /* Adaptive Krylov step (KIOPS-style; the paper names adaptive dimensions and substeps as the
  * improvement it leaves out, Secs. 3.2 and 6): advance every shot by nsteps steps of dt of
  * U^{n+1} = [I 0] exp(dt H~) [U^n; eta e_p] (the balanced start vector of ewv_step_krylov),
@@ -334,7 +346,10 @@ int ewv_set_leapfrog_variant(ewv_model_t model, int variant);
  * level n-1.  One H^T pass and two pointwise passes; workspace
  * ewv_workspace_bytes(EWV_METHOD_ADJOINT_LEAPFROG, 0) (3 vectors).  UNSUPPORTED for the
  * literal damping variant.
- * 2D models only.  Buffers 256-B aligned, caller-owned.
+ * 2D models only.  Buffers 256-B aligned, caller-owned.  In FP32 the stencil passes run on
+ * the persistent TMA kernels (Faber, HORK, leap-frog: forward recompute, H^T and gradient;
+ * Krylov's exponential form: both Arnoldi processes and the gradient), and the call then
+ * synchronises the stream once to read their pipeline-timeout flag (EWV_ERR_TIMEOUT).
  *
  * ewv_adjoint_inject: lambda_u += R^T values at the receivers, values [nshots][max_receivers]
  * of the model's precision (the seismogram cotangent of one sample).
@@ -347,6 +362,14 @@ int ewv_adjoint_step(ewv_model_t model, int method, double t, double dt, int m,
 #define EWV_KRYLOV_ADJOINT_EXACT 0        /* reverse mode through the computed Krylov step */
 #define EWV_KRYLOV_ADJOINT_EXPONENTIAL 1  /* adjoint of exp(dt H~), the step's limit          */
 int ewv_set_krylov_adjoint(ewv_model_t model, int mode);
+/* The adjoint of one Krylov step's exponential (as EWV_KRYLOV_ADJOINT_EXPONENTIAL, whatever
+ * mode ewv_set_krylov_adjoint holds) from the forward step's dense states instead of its
+ * checkpoint: dense is the buffer ewv_step_krylov_dense wrote for that step (4 x nshots
+ * padded vectors, [q][shot]); t, dt, m as in that call; adj_state and grad as in
+ * ewv_adjoint_step.  Only the adjoint Arnoldi on dt H^T runs (m products, none of the forward
+ * process).  Workspace: ewv_workspace_bytes(EWV_METHOD_ADJOINT_KRYLOV, m). */
+int ewv_adjoint_step_krylov_dense(ewv_model_t model, double t, double dt, int m, const void* dense,
+                                  void* adj_state, void* grad);
 int ewv_adjoint_inject(ewv_model_t model, void* adj_state, const void* values);
 int ewv_checkpoint_stride(int nsteps, int budget, int* stride);
 /* out[o] = sum over shots of per_shot[shot][o] (fields [ny][pitch]), shots summed in order:

@@ -30,7 +30,8 @@ dense output of the forward and adjoint Arnoldi bases (exp(tau A) x ~ |x| V exp(
 
 This route is independent of the CUDA path: B^T uses the transposed sparse matrix of
 ``oracle.operator.assemble_H``.  Pins: tests/test_oracle_adjoint.py (dot-product identity
-of one adjoint step; central finite differences of J along seeded directions).
+of one adjoint step; central finite differences of J along seeded directions; the Krylov
+dense states against dense expm of the augmented matrix at the Gauss nodes).
 """
 import math
 
@@ -162,15 +163,13 @@ def gauss_legendre4():
     return (1.0 + x) / 2.0, w / 2.0
 
 
-def krylov_adjoint_step(model, U_prev_flat, ybar, src, t_n, dt, m, HT=None):
-    """Cotangent of U^{n-1} and the m-gradient of one Krylov step (linearised, see the module
-    header).  Returns (exp(dt H)^T ybar by Arnoldi, grad [ny*nx])."""
+def krylov_dense_states(model, U_prev_flat, src, t_n, dt, m, taus=None):
+    """Dense output of one Krylov step (Sec. 3.2): x(tau dt) = [I 0] beta V_m exp(tau H_m) e_1,
+    the grid part of the Arnoldi approximation of exp(tau dt H~)[U; e_p] from the step's own
+    basis (start vector [U; eta e_p], W / eta, as krylov_step), at the 4-point Gauss-Legendre
+    nodes on [0, 1] unless taus is given.  Returns a list of flat state vectors."""
     from .krylov import arnoldi, expm
     nU = model.n
-    nu = model.nx * model.ny
-    if HT is None:
-        HT = assemble_H(model).T.tocsr()
-    # forward Arnoldi on dt H~ from [U; eta e_p], W / eta (as krylov_step)
     p = src.p if src is not None else 1
     w = src.W(t_n, dt) if src is not None else np.zeros(p)
     eta = float(np.linalg.norm(U_prev_flat))
@@ -186,19 +185,31 @@ def krylov_adjoint_step(model, U_prev_flat, ybar, src, t_n, dt, m, HT=None):
     y0 = np.zeros(p)
     y0[-1] = eta
     beta, V, Hm, _ = arnoldi(matvec, np.concatenate([U_prev_flat, y0]), m)
+    if taus is None:
+        taus = gauss_legendre4()[0]
+    return [beta * (V[:nU] @ expm(tau * Hm)[:, 0]) if beta > 0.0 else np.zeros(nU) for tau in taus]
+
+
+def krylov_adjoint_step(model, U_prev_flat, ybar, src, t_n, dt, m, HT=None):
+    """Cotangent of U^{n-1} and the m-gradient of one Krylov step (linearised, see the module
+    header).  Returns (exp(dt H)^T ybar by Arnoldi, grad [ny*nx])."""
+    from .krylov import arnoldi, expm
+    nU = model.n
+    nu = model.nx * model.ny
+    if HT is None:
+        HT = assemble_H(model).T.tocsr()
+    taus, wts = gauss_legendre4()
+    # forward states x(tau_q dt): dense output of the step's own Arnoldi basis
+    xs = krylov_dense_states(model, U_prev_flat, src, t_n, dt, m, taus)
     # adjoint Arnoldi on dt H^T from ybar
     beta_t, Vt, Ht, _ = arnoldi(lambda y: dt * (HT @ y), ybar, m)
-
-    def fwd(tau):
-        return beta * (V[:nU] @ expm(tau * Hm)[:, 0]) if beta > 0.0 else np.zeros(nU)
 
     def adj(sig):
         return beta_t * (Vt @ expm(sig * Ht)[:, 0]) if beta_t > 0.0 else np.zeros(nU)
 
-    taus, wts = gauss_legendre4()
     grad = np.zeros(nu)
-    for tau, wq in zip(taus, wts):
-        grad += dt * wq * adj(1.0 - tau)[nu:2 * nu] * G_of(model, fwd(tau))
+    for x, tau, wq in zip(xs, taus, wts):
+        grad += dt * wq * adj(1.0 - tau)[nu:2 * nu] * G_of(model, x)
     return adj(1.0), grad
 
 

@@ -207,8 +207,17 @@ struct Engine {
     size_t d_adj_bytes = 0;
     ProblemDev* d_kadj = nullptr; // Krylov adjoint: three descriptor views of the workspace
     size_t d_kadj_bytes = 0;
+    void* d_kexp_maps = nullptr;  // FP32 exponential Krylov adjoint: tensor maps of the
+    const void* kexp_key_state = nullptr;    // forward and adjoint Arnoldi views, valid for
+    const void* kexp_key_work = nullptr;     // this cotangent buffer, workspace,
+    size_t kexp_key_bytes = 0;               // workspace size
+    int kexp_key_m = 0;                      // and Krylov dimension
+    std::vector<const void*> kexp_tmaps;     // per-view map pointers (2 nshots)
     double* d_kbar = nullptr;     // exact Krylov adjoint: per-shot reverse-sweep scalars
     size_t d_kbar_n = 0;
+    // Krylov step with dense output (ewv_step_krylov_dense): the caller's buffer of the
+    // four Gauss-Legendre states, set for the duration of that call only
+    void* kry_dense = nullptr;
     // adaptive Krylov step: tolerance, dimension range and statistics of the current call
     double ad_tol = 0.0;
     int ad_mmin = 1, ad_mmax = 1;
@@ -276,6 +285,7 @@ struct Engine {
         cudaFree(d_adj);
         cudaFree(d_adj_maps);
         cudaFree(d_kadj);
+        cudaFree(d_kexp_maps);
         cudaFree(d_kbar);
     }
 };
@@ -1064,7 +1074,15 @@ int run_krylov(Ctx& C, double t, double dt, int m, int nsteps, int* info) {
     // a flat pass then forms <q_{j+1}, q_k0> with the same finalisation (FP64 keeps the fused
     // dot of the plain stencil kernel)
     const bool split_dot = C.E->precision == EWV_F32;
-    int rc0 = C.step_loop(nsteps, EWV_METHOD_KRYLOV, m, dt, tol, (double)window, 0, 1, [&](int) {
+    // dense output: before the step's own combine (which overwrites q_1 = U^{n-1}), the states
+    // x(tau_q dt) = beta V exp(tau_q H_m) e_1 at the 4-point Gauss-Legendre nodes go to the
+    // caller's buffer [q][shot]; a key of its own keeps such a call out of the step graphs
+    void* const dense = C.E->kry_dense;
+    static const double kTauGL[4] = {0.069431844202973712, 0.33000947820757187,
+                                     0.66999052179242813, 0.93056815579702629};
+    const long long vel = C.E->nprob > 0 ? (long long)C.E->models[0]->vec_elems : 0;
+    const int key_method = dense ? -EWV_METHOD_KRYLOV : EWV_METHOD_KRYLOV;
+    int rc0 = C.step_loop(nsteps, key_method, m, dt, tol, (double)window, 0, 1, [&](int) {
         C.prologue(PRO_KRYLOV, m);
         PointArgs pn{};
         pn.mode = 0;
@@ -1119,6 +1137,18 @@ int run_krylov(Ctx& C, double t, double dt, int m, int nsteps, int* info) {
                 pm.partials = C.E->d_partials;
                 pm.counters = C.E->d_counters;
                 C.point(pm);
+            }
+        }
+        if (dense) {
+            for (int q = 0; q < 4; ++q) {
+                if (launch_expm(C.E->d_probs, C.E->nprob, m, C.s, kTauGL[q]) != 0) expm_ok = false;
+                ++*C.launches;
+                PointArgs pq{};
+                pq.mode = 2;
+                pq.m = m;
+                pq.out = static_cast<char*>(dense) + (size_t)q * C.E->nprob * vel * C.E->models[0]->elem;
+                pq.out_stride = vel;
+                C.point(pq);
             }
         }
         if (launch_expm(C.E->d_probs, C.E->nprob, m, C.s) != 0) expm_ok = false;
@@ -2306,7 +2336,8 @@ int ewv_batch_kernel_timing(ewv_batch_t b, double* total_ms, long long* launches
 //     y(1 - tau_q) -> W_{2m+4+q}; finally y(1) -> the cotangent
 //   G (state = cotangent, work W_0): gradient passes, x(tau_q) = G vector m+q+1, y = 2m+5+q.
 static int adjoint_krylov(ewv_model* m, Engine* E, double t, double dt, int mm, void* adj_state,
-                          void* grad, const std::vector<ProblemDev>& base, const int* d_tp, int tb) {
+                          void* grad, const std::vector<ProblemDev>& base, const int* d_tp, int tb,
+                          const void* xdense) {
     cudaStream_t s = m->stream;
     const int ns = m->d.nshots, prec = m->d.precision, R = m->R;
     const size_t vb = m->vec_elems * m->elem;
@@ -2328,6 +2359,37 @@ static int adjoint_krylov(ewv_model* m, Engine* E, double t, double dt, int mm, 
         views[ns + sh] = A;
         views[2 * ns + sh] = G;
     }
+    // FP32: the products of both Arnoldi processes take the persistent TMA passes (the forward
+    // one the autotuned variant, the transposed one 64 x 18 tiles), each followed by a flat
+    // pass forming <q_{j+1}, q_1> with the finalisation of the plain kernel's fused dot; the
+    // tensor maps describe the F and A views and are rebuilt when the buffers change.  The
+    // gradient passes take the TMA gradient pass when the caller built maps of the G view
+    // (the cotangent and the workspace from vector 0).
+    bool tma = prec == EWV_F32 && E->tma_variant >= 0 && E->d_tbase && E->nprob == ns &&
+               per_shot >= (size_t)(2 * mm + 9);
+    if (tma && (E->kexp_key_state != adj_state || E->kexp_key_work != m->work ||
+                E->kexp_key_bytes != m->work_bytes || E->kexp_key_m != mm)) {
+        std::vector<ProblemDev> fa(views.begin(), views.begin() + 2 * (size_t)ns);
+        std::vector<int> wv(2 * (size_t)ns);
+        for (int sh = 0; sh < ns; ++sh) {
+            wv[sh] = (int)per_shot - 1;
+            wv[ns + sh] = (int)per_shot - (mm + 5);
+        }
+        E->kexp_key_state = nullptr;
+        if (build_tensor_maps(fa, R, wv, &E->d_kexp_maps) == 0) {
+            E->kexp_key_state = adj_state;
+            E->kexp_key_work = m->work;
+            E->kexp_key_bytes = m->work_bytes;
+            E->kexp_key_m = mm;
+            E->kexp_tmaps.assign(2 * (size_t)ns, nullptr);
+            for (int i = 0; i < 2 * ns; ++i) E->kexp_tmaps[i] = fa[i].tmaps;
+        } else {
+            tma = false;
+        }
+    }
+    if (tma)
+        for (int i = 0; i < 2 * ns; ++i) views[i].tmaps = E->kexp_tmaps[i];
+    const bool tma_grad = prec == EWV_F32 && E->d_tbase && E->nprob == ns && base[0].tmaps != nullptr;
     const size_t bytes = sizeof(ProblemDev) * views.size();
     if (!E->d_kadj || E->d_kadj_bytes < bytes) {
         cudaFree(E->d_kadj);
@@ -2344,6 +2406,8 @@ static int adjoint_krylov(ewv_model* m, Engine* E, double t, double dt, int mm, 
                                    0.66999052179242813, 0.93056815579702629};
     static const double kW[4] = {0.17392742256872693, 0.32607257743127307,
                                  0.32607257743127307, 0.17392742256872693};
+    const int fset = tma ? tma_map_set(tma_variant_tile_height_for(E->tma_variant, false)) : 0;
+    const int trset = tma_map_set(18), gset = tma_map_set(30);
     auto arnoldi = [&](const ProblemDev* v, bool transpose) {
         PointArgs pn{};
         pn.mode = 0;
@@ -2370,8 +2434,34 @@ static int adjoint_krylov(ewv_model* m, Engine* E, double t, double dt, int mm, 
             a.tol = tol;
             a.partials = E->d_partials;
             a.counters = E->d_counters;
-            launch_stage(prec, R, tb, v, d_tp, a, s);
-            ++m->launches;
+            bool fused = true;
+            if (tma) {
+                StageArgs b = a;
+                b.d = -1;
+                b.fin_mode = FIN_NONE;
+                const int set = transpose ? trset : fset;
+                const int* tbs = E->d_tbase + (size_t)set * (E->nprob + 1);
+                const int rc = transpose
+                                   ? launch_transpose_tma(R, v, tbs, ns, E->ntiles_by[set], b, E->d_err, s)
+                                   : launch_stage_tma(E->tma_variant, R, v, tbs, ns, E->ntiles_by[set], b, E->d_err, s);
+                if (rc == 0) {
+                    PointArgs pd{};
+                    pd.mode = 5;
+                    pd.j = j;
+                    pd.k = 1;
+                    pd.m = mm;
+                    pd.tol = tol;
+                    pd.partials = E->d_partials;
+                    pd.counters = E->d_counters;
+                    launch_point_flat(prec, E->nchunks, v, E->d_pbase, ns, pd, s);
+                    m->launches += 2;
+                    fused = false;
+                }
+            }
+            if (fused) {
+                launch_stage(prec, R, tb, v, d_tp, a, s);
+                ++m->launches;
+            }
             const int kmax = (j == mm) ? j - 1 : j;
             for (int k = 1; k <= kmax; ++k) {
                 PointArgs pm{};
@@ -2397,13 +2487,22 @@ static int adjoint_krylov(ewv_model* m, Engine* E, double t, double dt, int mm, 
         m->launches += 2;
         return true;
     };
-    // forward Arnoldi from the checkpoint (W_0 holds U^{n-1}), with the source of step n
-    launch_set_clock(vF, ns, t, dt, s);
-    launch_prologue(vF, ns, PRO_KRYLOV, mm, 0.0, 0.0, 0.0, s);
-    m->launches += 2;
-    arnoldi(vF, false);
-    for (int q = 0; q < 4; ++q)
-        if (!dense(vF, kTau[q], mm + 1 + q)) return fail(m->err, EWV_ERR_CUDA, "expm configuration failed");
+    if (xdense) {
+        // the forward step's dense states, x(tau_q) [q][shot], into the slots where the
+        // forward Arnoldi below would leave them
+        for (int q = 0; q < 4; ++q)
+            CUDA_OR_FAIL(m->err, cudaMemcpy2DAsync(wvec(0, mm + 1 + q), per_shot * vb,
+                                                   static_cast<const char*>(xdense) + (size_t)q * ns * vb, vb, vb,
+                                                   ns, cudaMemcpyDeviceToDevice, s));
+    } else {
+        // forward Arnoldi from the checkpoint (W_0 holds U^{n-1}), with the source of step n
+        launch_set_clock(vF, ns, t, dt, s);
+        launch_prologue(vF, ns, PRO_KRYLOV, mm, 0.0, 0.0, 0.0, s);
+        m->launches += 2;
+        arnoldi(vF, false);
+        for (int q = 0; q < 4; ++q)
+            if (!dense(vF, kTau[q], mm + 1 + q)) return fail(m->err, EWV_ERR_CUDA, "expm configuration failed");
+    }
     // adjoint Arnoldi on dt H^T from the cotangent (no tail, no source)
     arnoldi(vA, true);
     for (int q = 0; q < 4; ++q)
@@ -2415,12 +2514,24 @@ static int adjoint_krylov(ewv_model* m, Engine* E, double t, double dt, int mm, 
         gr.grad = grad;
         gr.gq = 2 * mm + 6 + q;
         gr.gscale = dt * kW[q];
-        launch_stage(prec, R, tb, vG, d_tp, gr, s);
+        if (!tma_grad || launch_grad_tma(R, vG, E->d_tbase + (size_t)gset * (E->nprob + 1), ns, E->ntiles_by[gset],
+                                         gr, E->d_err, s) != 0)
+            launch_stage(prec, R, tb, vG, d_tp, gr, s);
         ++m->launches;
     }
     // new cotangent y(1) into the cotangent buffer
     if (!dense(vA, 1.0, 0)) return fail(m->err, EWV_ERR_CUDA, "expm configuration failed");
-    return check_launch(m->err);
+    int rc = check_launch(m->err);
+    if (rc != EWV_OK || !(tma || tma_grad)) return rc;
+    // the TMA pipeline's timeout flag
+    int herr = 0;
+    CUDA_OR_FAIL(m->err, cudaMemcpyAsync(&herr, E->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_OR_FAIL(m->err, cudaStreamSynchronize(s));
+    if (herr) {
+        CUDA_OR_FAIL(m->err, cudaMemset(E->d_err, 0, sizeof(int)));
+        return fail(m->err, EWV_ERR_TIMEOUT, "a pipeline wait in the TMA stencil kernel timed out");
+    }
+    return EWV_OK;
 }
 
 // ---------------------------------------------------------------- exact Krylov adjoint
@@ -2654,9 +2765,15 @@ int ewv_set_krylov_adjoint(ewv_model_t m, int mode) {
     return EWV_OK;
 }
 
-int ewv_adjoint_step(ewv_model_t m, int method, double t, double dt, int deg,
-                     const void* checkpoint, void* adj_state, void* grad) {
-    if (!m || !checkpoint || !adj_state || !grad) return EWV_ERR_INVALID_ARG;
+// One adjoint step; for the Krylov step, xdense (when set) holds the forward step's dense
+// states and replaces the checkpoint (the adjoint of the step's exponential without the
+// forward Arnoldi).
+static int adjoint_step_impl(ewv_model_t m, int method, double t, double dt, int deg, const void* checkpoint,
+                             const void* xdense, void* adj_state, void* grad) {
+    if (!m || !(checkpoint || xdense) || !adj_state || !grad) return EWV_ERR_INVALID_ARG;
+    if (xdense && method != EWV_METHOD_KRYLOV)
+        return fail(m->err, EWV_ERR_INVALID_ARG, "dense states belong to the Krylov step");
+    if (xdense) checkpoint = xdense;   // validated below like a checkpoint, never read as one
     if (m->d.dims == 3) return fail(m->err, EWV_ERR_UNSUPPORTED, "the adjoint is two-dimensional");
     if (method != EWV_METHOD_FABER && method != EWV_METHOD_HORK && method != EWV_METHOD_KRYLOV &&
         method != EWV_METHOD_LEAPFROG)
@@ -2709,8 +2826,9 @@ int ewv_adjoint_step(ewv_model_t m, int method, double t, double dt, int deg,
     CUDA_OR_FAIL(m->err, cudaMemcpyAsync(d_tp, tp.data(), sizeof(int) * (size_t)tb,
                                          cudaMemcpyHostToDevice, s));
     // checkpoint U^{n-1} -> tape slot T_0 (workspace vector 1) of every shot
-    CUDA_OR_FAIL(m->err, cudaMemcpy2DAsync(m->work, per_shot * vb, checkpoint, vb, vb, ns,
-                                           cudaMemcpyDeviceToDevice, s));
+    if (!xdense)
+        CUDA_OR_FAIL(m->err, cudaMemcpy2DAsync(m->work, per_shot * vb, checkpoint, vb, vb, ns,
+                                               cudaMemcpyDeviceToDevice, s));
     const int R = m->R, prec = m->d.precision;
     // FP32: the forward-recompute passes (no transpose, no gradient) take the persistent TMA
     // pass, with tensor maps of the adjoint's buffers (rebuilt when the buffers change)
@@ -2775,9 +2893,9 @@ int ewv_adjoint_step(ewv_model_t m, int method, double t, double dt, int deg,
         return EWV_OK;
     };
     if (method == EWV_METHOD_KRYLOV)
-        return m->kry_adjoint == EWV_KRYLOV_ADJOINT_EXACT
-                   ? adjoint_krylov_exact(m, E, t, dt, deg, adj_state, grad, probs, d_tp, tb)
-                   : adjoint_krylov(m, E, t, dt, deg, adj_state, grad, probs, d_tp, tb);
+        return xdense || m->kry_adjoint == EWV_KRYLOV_ADJOINT_EXPONENTIAL
+                   ? adjoint_krylov(m, E, t, dt, deg, adj_state, grad, probs, d_tp, tb, xdense)
+                   : adjoint_krylov_exact(m, E, t, dt, deg, adj_state, grad, probs, d_tp, tb);
     if (lf) {
         // tape (vector 1) = level n; q in vector 2, H^T q in vector 3; the cotangents of
         // w^{n-1} live in the second nshots vectors of adj_state
@@ -2928,6 +3046,27 @@ int ewv_adjoint_step(ewv_model_t m, int method, double t, double dt, int deg,
         ++m->launches;
     }
     return adj_finish();
+}
+
+int ewv_adjoint_step(ewv_model_t m, int method, double t, double dt, int deg,
+                     const void* checkpoint, void* adj_state, void* grad) {
+    return adjoint_step_impl(m, method, t, dt, deg, checkpoint, nullptr, adj_state, grad);
+}
+
+int ewv_adjoint_step_krylov_dense(ewv_model_t m, double t, double dt, int mdim, const void* dense,
+                                  void* adj_state, void* grad) {
+    if (!m || !dense) return EWV_ERR_INVALID_ARG;
+    return adjoint_step_impl(m, EWV_METHOD_KRYLOV, t, dt, mdim, nullptr, dense, adj_state, grad);
+}
+
+int ewv_step_krylov_dense(ewv_model_t m, double t, double dt, int mdim, void* dense) {
+    if (!m || !dense) return EWV_ERR_INVALID_ARG;
+    if (!aligned(dense)) return fail(m->err, EWV_ERR_BAD_SIZE_OR_ALIGNMENT, "dense buffer must be 256-B aligned");
+    Engine* E = ensure_model_engine(m);
+    E->kry_dense = dense;
+    const int rc = step_model(m, EWV_METHOD_KRYLOV, t, dt, mdim, 1, nullptr);
+    E->kry_dense = nullptr;
+    return rc;
 }
 
 int ewv_adjoint_inject(ewv_model_t m, void* adj_state, const void* values) {

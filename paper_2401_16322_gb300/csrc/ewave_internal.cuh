@@ -147,6 +147,8 @@ struct PointArgs {
     double tol;
     double* partials;
     unsigned int* counters;
+    void* out;             // combine (mode 2): when set, problem p's result goes to the
+    long long out_stride;  // caller's buffer at out + p * out_stride elements, not vector dst
 };
 
 // Host-side launchers (defined in kernels_stencil.cu / kernels_aux.cu).

@@ -402,7 +402,8 @@ point_flat_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ 
         const double beta = kry[KRY_BETA];
         for (int k = tid; k < meff; k += NTHREADS) s_coef[k] = (T)(beta * kry[KRY_E + k] * kry[KRY_S + k + 1]);
         __syncthreads();
-        V* St = reinterpret_cast<V*>(vptr<T>(P, pa.dst));
+        V* St = pa.out ? reinterpret_cast<V*>(static_cast<T*>(pa.out) + (long long)pid * pa.out_stride)
+                       : reinterpret_cast<V*>(vptr<T>(P, pa.dst));
         for (long long q = q0 + tid; q < q1; q += NTHREADS) {
             V acc = {};
             for (int k = 1; k <= meff; ++k) fma16(acc, s_coef[k - 1], reinterpret_cast<const V*>(vptr<T>(P, k - 1))[q]);

@@ -38,6 +38,7 @@ EXPORTS = [
     "ewv_batch_last_error", "ewv_version", "ewv_launch_count", "ewv_enable_kernel_timing",
     "ewv_kernel_timing", "ewv_batch_enable_kernel_timing", "ewv_batch_kernel_timing", "ewv_reset_state",
     "ewv_faber_step_noalloc", "ewv_adjoint_step", "ewv_adjoint_inject", "ewv_checkpoint_stride",
+    "ewv_step_krylov_dense", "ewv_adjoint_step_krylov_dense",
     "ewv_sum_shot_fields", "ewv_enable_graphs", "ewv_batch_enable_graphs",
     "ewv_set_kernel_variant", "ewv_kernel_variant", "ewv_batch_set_kernel_variant",
     "ewv_batch_kernel_variant", "ewv_set_source_receivers3d", "ewv_set_storage_rounding",
@@ -134,6 +135,8 @@ def load_library(path=LIB_PATH):
         "ewv_launch_count": ([vp, ctypes.POINTER(ctypes.c_longlong)], i),
         "ewv_reset_state": ([vp], i),
         "ewv_adjoint_step": ([vp, i, d, d, i, vp, vp, vp], i),
+        "ewv_step_krylov_dense": ([vp, d, d, i, vp], i),
+        "ewv_adjoint_step_krylov_dense": ([vp, d, d, i, vp, vp, vp], i),
         "ewv_adjoint_inject": ([vp, vp, vp], i),
         "ewv_checkpoint_stride": ([i, i, ctypes.POINTER(i)], i),
         "ewv_sum_shot_fields": ([vp, vp, vp], i),
@@ -374,6 +377,15 @@ class Model:
         self._check(self.lib.ewv_step_krylov(self.h, t, dt, m, nsteps, ctypes.byref(info)), "step_krylov")
         return info.value
 
+    def step_krylov_dense(self, t, dt, m, dense):
+        """One Krylov step that also writes its four dense states x(tau_q dt) (4-point
+        Gauss-Legendre nodes tau_q on [0, 1]) into ``dense``: 4 nshots padded vectors, [q][shot]
+        (the input of adjoint_step_krylov_dense)."""
+        self._need("dense", dense, 4 * self.nshots * self.vector_elems)
+        self.ensure_workspace("krylov", m)
+        self._check(self.lib.ewv_step_krylov_dense(self.h, t, dt, m, ctypes.c_void_p(dense.data_ptr())),
+                    "step_krylov_dense")
+
     def step_krylov_adaptive(self, t, dt, tol, m_min=1, m_max=30, nsteps=1):
         """Adaptive Krylov steps (dimension and substeps chosen per shot to meet ``tol``);
         returns {"substeps", "matvecs", "max_dim"} summed over shots and steps."""
@@ -421,21 +433,37 @@ class Model:
     # ---------------------------------------------------------------- adjoint
     def adjoint_step(self, t, dt, degree, checkpoint, adj, grad, method="faber"):
         """lambda <- (dPhi/dU)^T lambda, grad += (dPhi/dm)^T lambda for one Faber / HORK /
-        leap-frog step (Krylov: the adjoint of the step's exponential).  Leap-frog: ``adj``
+        Krylov / leap-frog step (Krylov: the exact discrete adjoint, or the adjoint of the
+        step's exponential after set_krylov_adjoint('exponential')).  Leap-frog: ``adj``
         holds 2 nshots vectors (cotangents of level n, then of w at level n-1)."""
         ns, nv, fe = self.nshots, self.vector_elems, self.layout.field_elems
         levels = 2 if method == "leapfrog" else 1
         for name, buf, need in (("checkpoint", checkpoint, ns * nv), ("adj", adj, levels * ns * nv),
                                 ("grad", grad, ns * fe)):
-            if buf.numel() < need or buf.dtype != self.dtype or not buf.is_cuda:
-                raise ValueError(f"adjoint_step: {name} must be a CUDA tensor of at least {need} "
-                                 f"{self.dtype} elements (got {buf.numel()} {buf.dtype} on {buf.device})")
+            self._need(name, buf, need)
         self.ensure_workspace({"krylov": "adjoint_krylov", "leapfrog": "adjoint_leapfrog"}.get(
             method, "adjoint_faber"), degree)
         self._check(self.lib.ewv_adjoint_step(self.h, METHOD[method], t, dt, degree,
                                               ctypes.c_void_p(checkpoint.data_ptr()),
                                               ctypes.c_void_p(adj.data_ptr()),
                                               ctypes.c_void_p(grad.data_ptr())), "adjoint_step")
+
+    def adjoint_step_krylov_dense(self, t, dt, m, dense, adj, grad):
+        """The adjoint of one Krylov step's exponential from the forward step's dense states
+        (step_krylov_dense) instead of a checkpoint: no forward Arnoldi is recomputed."""
+        ns, nv, fe = self.nshots, self.vector_elems, self.layout.field_elems
+        for name, buf, need in (("dense", dense, 4 * ns * nv), ("adj", adj, ns * nv), ("grad", grad, ns * fe)):
+            self._need(name, buf, need)
+        self.ensure_workspace("adjoint_krylov", m)
+        self._check(self.lib.ewv_adjoint_step_krylov_dense(self.h, t, dt, m, ctypes.c_void_p(dense.data_ptr()),
+                                                           ctypes.c_void_p(adj.data_ptr()),
+                                                           ctypes.c_void_p(grad.data_ptr())),
+                    "adjoint_step_krylov_dense")
+
+    def _need(self, name, buf, need):
+        if buf.numel() < need or buf.dtype != self.dtype or not buf.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor of at least {need} {self.dtype} elements "
+                             f"(got {buf.numel()} {buf.dtype} on {buf.device})")
 
     def adjoint_inject(self, adj, values):
         self._check(self.lib.ewv_adjoint_inject(self.h, ctypes.c_void_p(adj.data_ptr()),

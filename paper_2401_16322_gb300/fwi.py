@@ -18,16 +18,27 @@ from .ewave import Model, checkpoint_stride
 
 class FaberFWI:
     """Forward simulation with checkpoints and the adjoint gradient for one model
-    (``method`` "faber": degree m; "hork": m stages; "krylov": dimension m, adjoint of the
-    step's exponential; "leapfrog": the two-step scheme with averaged damping, m ignored).
+    (``method`` "faber": degree m; "hork": m stages; "krylov": dimension m, the adjoint the
+    model's Krylov adjoint mode selects; "leapfrog": the two-step scheme with averaged
+    damping, m ignored).
 
     Leap-frog carries two time levels: a checkpoint stores the state (level n) and the
     library's history vector (level n-1, workspace vector 1 of each shot), and the adjoint
-    state has two vectors per shot (``ewv_adjoint_step``)."""
+    state has two vectors per shot (``ewv_adjoint_step``).
 
-    def __init__(self, model: Model, dt, degree, nsteps, nrec, budget=None, t0=0.0, method="faber"):
+    ``dense_states`` (Krylov only): the adjoint of each step's exponential runs from the four
+    dense states the forward step writes (``ewv_step_krylov_dense``) instead of recomputing
+    the forward Arnoldi from a checkpoint.  With every step stored (no budget) the forward
+    pass keeps them, 4 vectors per step in place of 1; with a budget a segment's dense states
+    are recomputed from its checkpoint in the backward pass."""
+
+    def __init__(self, model: Model, dt, degree, nsteps, nrec, budget=None, t0=0.0, method="faber",
+                 dense_states=False):
         if method not in ("faber", "hork", "krylov", "leapfrog"):
             raise ValueError("the adjoint exists for the Faber, HORK, Krylov and leap-frog steps")
+        if dense_states and method != "krylov":
+            raise ValueError("dense states belong to the Krylov step")
+        self.dense = bool(dense_states)
         self.method = method
         self.model = model
         self.dt, self.degree, self.nsteps, self.nrec, self.t0 = dt, degree, nsteps, nrec, t0
@@ -40,9 +51,19 @@ class FaberFWI:
             # so the history vector survives
             model.ensure_workspace("adjoint_leapfrog", 0)
         self.nck = (nsteps + self.stride - 1) // self.stride
-        self.ckpt = torch.zeros(self.nck, self.levels, model.nshots * nv, dtype=model.dtype,
-                                device=model.device)
-        self.seg = torch.zeros(self.stride, model.nshots * nv, dtype=model.dtype, device=model.device)
+        ns = model.nshots
+        # with dense states and every step stored, no checkpoint is read back
+        nck = 0 if (self.dense and self.stride == 1) else self.nck
+        self.ckpt = torch.zeros(nck, self.levels, ns * nv, dtype=model.dtype, device=model.device)
+        self.seg = torch.zeros(0 if self.dense else self.stride, ns * nv, dtype=model.dtype,
+                               device=model.device)
+        # dense states [step, q, shot vectors]: every step's (no budget) or one segment's
+        nxd = (nsteps if self.stride == 1 else self.stride) if self.dense else 0
+        self.xd = torch.zeros(nxd, 4, ns * nv, dtype=model.dtype, device=model.device)
+
+    def stored_bytes(self):
+        """Device bytes of the stored forward states (checkpoints, segment and dense states)."""
+        return sum(b.numel() * b.element_size() for b in (self.ckpt, self.seg, self.xd))
 
     def _history(self):
         """Leap-frog: the level n-1 vector of every shot (workspace vector 1), as a view."""
@@ -82,9 +103,12 @@ class FaberFWI:
         md.reset_state()
         md.ensure_workspace(self.method, self.degree)
         for n in range(self.nsteps):
-            if n % self.stride == 0:
+            if n % self.stride == 0 and self.ckpt.shape[0] > 0:
                 self._save(n // self.stride)
-            md.step(self.method, self.t0 + n * self.dt, self.dt, self.degree, 1)
+            if self.dense and self.stride == 1:
+                md.step_krylov_dense(self.t0 + n * self.dt, self.dt, self.degree, self.xd[n])
+            else:
+                md.step(self.method, self.t0 + n * self.dt, self.dt, self.degree, 1)
         md.sync()           # raises if the forward run produced a non-finite state
         s = md.seismo.view(md.nshots, md.capacity, md.max_receivers)[:, :self.nsteps, :self.nrec]
         return s.clone()
@@ -106,6 +130,21 @@ class FaberFWI:
         for k in range(self.nck - 1, -1, -1):
             n0 = k * self.stride
             n1 = min(n0 + self.stride, self.nsteps)
+            if self.dense and self.stride > 1:
+                # recompute the segment's steps n0+1 .. n1 from its checkpoint, keeping the
+                # dense states of each
+                md.ensure_workspace(self.method, self.degree)
+                self._restore(k)
+                for n in range(n0, n1):
+                    md.step_krylov_dense(self.t0 + n * self.dt, self.dt, self.degree, self.xd[n - n0])
+                md.ensure_workspace(adj_ws, self.degree)
+            if self.dense:
+                for n in range(n1, n0, -1):      # adjoint of step n from its dense states
+                    xd = self.xd[n - 1] if self.stride == 1 else self.xd[n - 1 - n0]
+                    md.adjoint_step_krylov_dense(self.t0 + (n - 1) * self.dt, self.dt, self.degree, xd, lam, grad)
+                    if n - 1 >= 1:
+                        md.adjoint_inject(lam, g[:, n - 2, :].contiguous())
+                continue
             # recompute the states U^{n0} .. U^{n1-1} of this segment from its checkpoint
             if self.stride > 1:
                 md.ensure_workspace(self.method, self.degree)

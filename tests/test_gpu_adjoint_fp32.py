@@ -1,12 +1,14 @@
 """FP32 adjoint steps through the persistent TMA passes (forward recompute, gradient and the
-transposed pass H^T on the column-pair consumers) against the oracle's adjoint steps, on
+transposed pass H^T on the column-pair consumers; for Krylov, the adjoint of the step's
+exponential with both Arnoldi processes on the TMA passes and split dots) against the
+oracle's adjoint steps, on
 grids that span several 64 x 18 tiles with ragged tails, with and without the free surface
 (whose transposed rows, 0..8, take the kernel's scalar path) and at both orders."""
 import numpy as np
 import pytest
 
 from _helpers import flatten, rel_l2
-from oracle.adjoint import faber_adjoint_step, hork_adjoint_step
+from oracle.adjoint import faber_adjoint_step, hork_adjoint_step, krylov_adjoint_step
 from oracle.faber import ellipse_params
 from oracle.model import Model as OModel
 from oracle.model import default_beta0
@@ -25,7 +27,7 @@ CASES = [
 DX = 10.0
 
 
-@pytest.mark.parametrize("method,m", [("faber", 6), ("hork", 5)])
+@pytest.mark.parametrize("method,m", [("faber", 6), ("hork", 5), ("krylov", 8)])
 @pytest.mark.parametrize("nx,ny,order,fs,pml", CASES)
 def test_fp32_adjoint_step_matches_oracle(method, m, nx, ny, order, fs, pml):
     import torch
@@ -51,12 +53,16 @@ def test_fp32_adjoint_step_matches_oracle(method, m, nx, ny, order, fs, pml):
         g.pack(Us[k], ck[k * nv:(k + 1) * nv])
         g.pack(ybars[k], lam[k * nv:(k + 1) * nv])
     grad = torch.zeros(2 * fe, dtype=torch.float32, device="cuda")
+    if method == "krylov":
+        g.set_krylov_adjoint("exponential")
     g.adjoint_step(t, dt, m, ck, lam, grad, method=method)
     g.sync()
     for k, sx in enumerate(sxs):
         src = PointSource(om, sx, 2 * DX, 30.0, 0.04, amp=1e3, p=8)
         if method == "faber":
             Ub, gr = faber_adjoint_step(om, Us[k], ybars[k], src, t, dt, m, ell)
+        elif method == "krylov":
+            Ub, gr = krylov_adjoint_step(om, Us[k], ybars[k], src, t, dt, m)
         else:
             Ub, gr = hork_adjoint_step(om, Us[k], ybars[k], src, t, dt, m)
         got = g.unpack(lam[k * nv:(k + 1) * nv])

@@ -210,6 +210,93 @@ def test_krylov_gradient_matches_oracle_and_differences(budget):
     assert abs(fd - float(np.sum(grad * dm))) <= 1e-3 * abs(fd)
 
 
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-12), ("f32", 2e-5)])
+def test_krylov_dense_step_and_adjoint(prec, tol):
+    """ewv_step_krylov_dense leaves the state ewv_step_krylov leaves (bit for bit: the same
+    passes) and writes the oracle's four dense states (Sec. 3.2 dense output at the
+    Gauss-Legendre nodes); the adjoint from those states equals the exponential adjoint that
+    recomputes the forward Arnoldi from the checkpoint, and the oracle's.  In FP64 the adjoint
+    is held to 1e-10, not 1e-12: the Arnoldi process on dt H^T amplifies rounding-order
+    differences about a thousandfold here (perturbing the oracle's cotangent by one part in
+    1e16 moves its result by up to 3e-13)."""
+    import torch
+    from oracle.adjoint import krylov_adjoint_step, krylov_dense_states
+    c_true, c0, beta0, ell = _setup()
+    om = OModel(NX, NY, DX, 8, PML, beta0, True, c_true)
+    g = _gpu(c_true, beta0, ell, prec)
+    g.bind_seismogram(4)
+    dtype = torch.float64 if prec == "f64" else torch.float32
+    ns, nv, fe = 2, g.vector_elems, g.layout.field_elems
+    t, dt, m = 0.02, 2e-3, 12
+    Us = [flatten(smooth_random_state([f.shape for f in om.zeros_state()], 70 + k)) for k in range(ns)]
+    ybars = [random_state([(om.n,)], 80 + k)[0] for k in range(ns)]
+    u0 = torch.zeros(ns * nv, dtype=dtype, device="cuda")
+    y0 = torch.zeros(ns * nv, dtype=dtype, device="cuda")
+    for k in range(ns):
+        g.pack(Us[k], u0[k * nv:(k + 1) * nv])
+        g.pack(ybars[k], y0[k * nv:(k + 1) * nv])
+    g.step_krylov(t, dt, m)                  # tunes the passes before the comparison
+    g.state.copy_(u0)
+    g.step_krylov(t, dt, m)
+    ref = g.state.clone()
+    xd = torch.zeros(4 * ns * nv, dtype=dtype, device="cuda")
+    g.state.copy_(u0)
+    g.step_krylov_dense(t, dt, m, xd)
+    g.sync()
+    assert torch.equal(g.state[:ns * nv], ref[:ns * nv])
+    lam_r, lam_d = y0.clone(), y0.clone()
+    grad_r = torch.zeros(ns * fe, dtype=dtype, device="cuda")
+    grad_d = torch.zeros(ns * fe, dtype=dtype, device="cuda")
+    g.set_krylov_adjoint("exponential")
+    g.adjoint_step(t, dt, m, u0, lam_r, grad_r, method="krylov")
+    g.adjoint_step_krylov_dense(t, dt, m, xd, lam_d, grad_d)
+    g.sync()
+    assert float((lam_d - lam_r).norm() / lam_r.norm()) < 1e-6 * (1e-6 if prec == "f64" else 1.0)
+    assert float((grad_d - grad_r).norm() / grad_r.norm()) < 1e-6 * (1e-6 if prec == "f64" else 1.0)
+    for k, sx in enumerate(SX):
+        src = PointSource(om, sx, 2 * DX, 30.0, 0.04, amp=1e3, p=10)
+        want = krylov_dense_states(om, Us[k], src, t, dt, m)
+        for q in range(4):
+            got = g.unpack(xd[(q * ns + k) * nv:(q * ns + k + 1) * nv])
+            assert rel_l2(got, want[q]) < tol, (k, q, rel_l2(got, want[q]))
+        Ub, gr = krylov_adjoint_step(om, Us[k], ybars[k], src, t, dt, m)
+        tol_adj = 1e-10 if prec == "f64" else tol
+        e_lam = rel_l2(g.unpack(lam_d[k * nv:(k + 1) * nv]), Ub)
+        g_got = grad_d[k * fe:(k + 1) * fe].view(NY, g.layout.pitch)[:, :NX].double().cpu().numpy()
+        e_grad = rel_l2(g_got, gr.reshape(NY, NX))
+        assert e_lam < tol_adj and e_grad < tol_adj, (k, e_lam, e_grad)
+    g.close()
+
+
+@pytest.mark.parametrize("budget", [None, 4])
+def test_krylov_dense_state_gradient_matches_oracle(budget):
+    """FWI gradient with the forward's dense states (no forward Arnoldi in the adjoint):
+    every step's states stored, or a segment's recomputed from its checkpoint; equals the
+    oracle's exponential-adjoint gradient (FP64) and the recomputing path's."""
+    import torch
+    from paper_2401_16322_gb300.fwi import FaberFWI
+    c_true, c0, beta0, ell = _setup()
+    dt, m, nsteps = 1e-3, 12, 10
+    om_t = OModel(NX, NY, DX, 8, PML, beta0, True, c_true)
+    d_obs = faber_forward(om_t, _oshots(om_t), dt, nsteps, m, ell, method="krylov")[1]
+    om = OModel(NX, NY, DX, 8, PML, beta0, True, c0)
+    J_o, g_o = fwi_gradient(om, _oshots(om), d_obs, dt, nsteps, m, ell, method="krylov")
+    g = _gpu(c0, beta0, ell, "f64")
+    g.set_krylov_adjoint("exponential")
+    d = torch.tensor(np.array(d_obs), dtype=torch.float64, device="cuda")
+    fwi = FaberFWI(g, dt, m, nsteps, len(REC), budget=budget, method="krylov", dense_states=True)
+    seis = fwi.forward(c0 ** 2)
+    assert abs(0.5 * float(((seis - d) ** 2).sum()) - J_o) <= 1e-9 * J_o
+    grad = fwi.backward(seis - d).double().cpu().numpy()
+    assert rel_l2(grad, g_o) < 1e-9
+    ref = FaberFWI(g, dt, m, nsteps, len(REC), budget=budget, method="krylov")
+    grad_r = ref.backward(ref.forward(c0 ** 2) - d).double().cpu().numpy()
+    assert rel_l2(grad, grad_r) < 1e-12
+    if budget is None:
+        assert fwi.ckpt.numel() == 0 and fwi.xd.shape[0] == nsteps
+    g.close()
+
+
 # ---------------------------------------------------------------- leap-frog adjoint
 LF_DT, LF_NSTEPS = 1e-3, 30
 

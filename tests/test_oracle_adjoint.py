@@ -147,6 +147,38 @@ def test_krylov_gradient_is_the_frechet_derivative():
     assert abs(got - exact) <= 1e-6 * abs(exact), (got, exact)
 
 
+def test_krylov_dense_states_are_the_exponential_at_the_gauss_nodes():
+    """With a full-dimension basis the step's dense states are [I 0] exp(tau_q dt H~)[U; e_p]
+    at the 4-point Gauss-Legendre nodes (dense expm of the augmented matrix, Eq.
+    matrix_ampli); with a short basis the state at tau = 1 is the Krylov step's own result."""
+    import scipy.linalg as sl
+    from oracle.adjoint import gauss_legendre4, krylov_dense_states
+    from oracle.krylov import krylov_step
+    from oracle.model import unflatten
+    from oracle.operator import assemble_H
+    m, c = _tiny_krylov_model()
+    src = PointSource(m, 4 * DX, 2 * DX, 40.0, 0.02, amp=1e3, p=6)
+    U = flatten(smooth_random_state([f.shape for f in m.zeros_state()], 21))
+    dt, t = 3e-4, 0.01
+    n, p = m.n, src.p
+    A = np.zeros((n + p, n + p))
+    A[:n, :n] = assemble_H(m).toarray()
+    A[m.nx * m.ny + src.j * m.nx + src.i, n:] = src.W(t, dt)
+    for k in range(p - 1):
+        A[n + k, n + k + 1] = 1.0 / dt
+    x = np.concatenate([U, np.eye(p)[-1]])
+    taus = gauss_legendre4()[0]
+    got = krylov_dense_states(m, U, src, t, dt, n + p)
+    for tau, g in zip(taus, got):
+        want = (sl.expm(tau * dt * A) @ x)[:n]
+        assert np.linalg.norm(g - want) <= 1e-10 * np.linalg.norm(want), tau
+    one = krylov_dense_states(m, U, src, t, dt, 6, taus=[1.0])[0]
+    step = flatten(krylov_step(m, unflatten(m, U), src, t, dt, 6))
+    assert np.linalg.norm(one - step) <= 1e-13 * np.linalg.norm(step)
+    # the dense states are not the endpoint: x(tau) moves with tau
+    assert np.linalg.norm(got[0] - got[3]) > 1e-3 * np.linalg.norm(got[3])
+
+
 def test_krylov_fwi_gradient_matches_central_differences():
     """The linearised Krylov gradient agrees with central differences of the Krylov
     forward to the step's time accuracy (the acceptance level of the FWI gradient)."""
