@@ -470,6 +470,13 @@ int build_engine(Engine* E, std::string& err) {
         }
         pb[E->nprob] = acc;
         E->nchunks = acc;
+        // per-block (problem, chunk) pairs: a block finds its problem with one load
+        pb.resize((size_t)flat_block_table(E->nprob) + 2 * (size_t)acc, 0);
+        for (int p = 0, b = 0; p < E->nprob; ++p)
+            for (int c = 0; c < E->probs[p].pchunks; ++c, ++b) {
+                pb[(size_t)flat_block_table(E->nprob) + 2 * (size_t)b] = p;
+                pb[(size_t)flat_block_table(E->nprob) + 2 * (size_t)b + 1] = c;
+            }
         cudaFree(E->d_pbase);
         E->d_pbase = nullptr;
         CUDA_OR_FAIL(err, cudaMalloc(&E->d_pbase, sizeof(int) * pb.size()));

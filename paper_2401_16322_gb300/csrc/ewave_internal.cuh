@@ -220,7 +220,9 @@ void launch_record(int precision, const ProblemDev* probs, int nprob, int vec, c
 void launch_point(int precision, int nblocks, const ProblemDev* probs, const int* tile_prob,
                   const PointArgs& pa, cudaStream_t s);
 // Flat pointwise passes (modes 0, 1, 2 of PointArgs) over whole padded vectors, PCHUNK
-// elements per block; pbase: nprob + 1 prefix sums of the problems' chunk counts.
+// elements per block; pbase: nprob + 1 prefix sums of the problems' chunk counts, then, from
+// int offset flat_block_table(nprob), one (problem, chunk within the problem) pair per block.
+__host__ __device__ constexpr int flat_block_table(int nprob) { return (nprob + 2) & ~1; }
 void launch_point_flat(int precision, int nchunks, const ProblemDev* probs, const int* pbase,
                        int nprob, const PointArgs& pa, cudaStream_t s);
 // Non-finite check of every problem's state vector (and its Arnoldi flag): sets bit 2 of *err.

@@ -322,7 +322,8 @@ point_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ tile_
 // ---------------------------------------------------------------- flat pointwise passes
 // Modes 0 (|q_1|^2), 1 (MGS pass) and 2 (Krylov combine) over whole padded vectors: every
 // pad element is zero in every vector, so the flat sums and updates equal the masked ones.
-// Block b handles elements [c PCHUNK, (c + 1) PCHUNK) of problem p, c = b - pbase[p], with
+// Block b handles elements [c PCHUNK, (c + 1) PCHUNK) of problem p ((p, c) from the block
+// table after the prefix sums), with
 // 16-byte vector loads; its partial dot product goes to slot b, and the problem's last block
 // sums the partials in a fixed order (deterministic, no waiting).
 template <typename T>
@@ -385,7 +386,8 @@ point_flat_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ 
     __shared__ double red[NTHREADS / 32];
     __shared__ int s_last;
     __shared__ T s_coef[MAX_M];
-    const int pid = flat_problem(pbase, nprob, blockIdx.x);
+    const int2 pc = __ldg(reinterpret_cast<const int2*>(pbase + flat_block_table(nprob)) + blockIdx.x);
+    const int pid = pc.x;
     const ProblemDev* P = probs + pid;
     double* kry = P->kry;
     if ((pa.mode == 1 || pa.mode == 5) && kry[KRY_ACTIVE] == 0.0) return;
@@ -393,7 +395,7 @@ point_flat_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ 
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int nf = P->nfields;   // 4 (2D) or 6 (3D: w_z and psi added)
     const long long nelem = (long long)nf * P->field_stride;
-    const long long e0 = (long long)(blockIdx.x - __ldg(pbase + pid)) * PCHUNK;
+    const long long e0 = (long long)pc.y * PCHUNK;
     const long long e1 = e0 + PCHUNK < nelem ? e0 + PCHUNK : nelem;
     const long long q0 = e0 / NV, q1 = e1 / NV;
     if (pa.mode == 2) {
@@ -457,7 +459,7 @@ point_flat_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ 
     a.tol = pa.tol;
     a.partials = pa.partials;
     a.counters = pa.counters;
-    partial_and_finalize_at(P, pid, a, bsum, red, &s_last, blockIdx.x, __ldg(pbase + pid), P->pchunks);
+    partial_and_finalize_at(P, pid, a, bsum, red, &s_last, blockIdx.x, blockIdx.x - pc.y, P->pchunks);
 }
 
 // ---------------------------------------------------------------- Hessenberg exponential

@@ -35,6 +35,7 @@ __device__ __forceinline__ double* kry_tail(double* kry, int k) {  // k = 1..MAX
 
 __device__ inline void krylov_finalize(const ProblemDev* P, int mode, int j, int k, int m,
                                        double tol, double tot) {
+    __shared__ double fin_buf[3][MAX_P];   // one thread per block runs this
     double* kry = P->kry;
     const int p = P->p;
     if (!isfinite(tot)) {
@@ -48,8 +49,8 @@ __device__ inline void krylov_finalize(const ProblemDev* P, int mode, int j, int
     }
     if (mode == FIN_NORM0_TAIL) {
         // a later substep of the adaptive step: the tail of slot 1 is the previous substep's
-        // (uploaded by the host) and W is already scaled by this step's eta
-        for (int r = 0; r < (MAX_M + 1) * MAX_M; ++r) kry[KRY_H + r] = 0.0;
+        // (uploaded by the host) and W is already scaled by this step's eta; H was zeroed by
+        // the finalising block (zero_krylov_start)
         if (kry[KRY_SKIP] != 0.0) {
             kry[KRY_ACTIVE] = 0.0;
             return;
@@ -68,19 +69,13 @@ __device__ inline void krylov_finalize(const ProblemDev* P, int mode, int j, int
         return;
     }
     if (mode == FIN_NORM0_NOTAIL) {
-        // Arnoldi on a plain (non-augmented) operator, e.g. dt H^T: zero tail, no source
+        // Arnoldi on a plain (non-augmented) operator, e.g. dt H^T: zero tail, no source (the
+        // tails, W, sigma and H were zeroed by the finalising block: zero_krylov_start)
         const double beta = sqrt(tot);
-        for (int k = 1; k <= MAX_M + 1; ++k) {
-            double* tk = kry_tail(kry, k);
-            for (int q = 0; q < MAX_P; ++q) tk[q] = 0.0;
-        }
-        for (int q = 0; q < MAX_P; ++q) kry[KRY_W + q] = 0.0;
         kry[KRY_BETA] = beta;
         kry[KRY_S + 1] = beta > 0.0 ? 1.0 / beta : 0.0;
         kry[KRY_ACTIVE] = beta > 0.0 ? 1.0 : 0.0;
         kry[KRY_MEFF] = beta > 0.0 ? (double)m : 0.0;
-        for (int j2 = 0; j2 <= MAX_M; ++j2) P->sigma[j2] = 0.0;
-        for (int r = 0; r < (MAX_M + 1) * MAX_M; ++r) kry[KRY_H + r] = 0.0;
     } else if (mode == FIN_NORM0) {
         double* t1 = kry_tail(kry, 1);
         kry[KRY_SKIP] = 0.0;
@@ -96,34 +91,53 @@ __device__ inline void krylov_finalize(const ProblemDev* P, int mode, int j, int
         double sg = 0.0;
         for (int q = 0; q < p; ++q) sg += kry[KRY_W + q] * t1[q];
         P->sigma[1] = P->has_src ? sg : 0.0;
-        for (int r = 0; r < (MAX_M + 1) * MAX_M; ++r) kry[KRY_H + r] = 0.0;
     } else if (mode == FIN_MATVEC) {
         // tot = <q_{j+1}, q_{k0}>, k0 = k (the first vector this step orthogonalises against:
         // 1 for full Gram-Schmidt, j - q + 1 with an orthogonalisation window of q)
+        // (the tails are copied to shared memory before any store to them: a load after a
+        // store to the same array could not be issued ahead of it, one memory latency per
+        // entry; the copies in shared memory cannot alias the global rows)
         const int k0 = k >= 1 ? k : 1;
         const double sj = kry[KRY_S + j];
         const double* tj = kry_tail(kry, j);
         double* tw = kry_tail(kry, j + 1);
-        for (int q = 0; q < p - 1; ++q) tw[q] = sj * tj[q + 1];   // J (s_j tail_j)
-        tw[p - 1] = 0.0;
         const double* tk0 = kry_tail(kry, k0);
+        double* a = fin_buf[0];
+        double* b = fin_buf[1];
+        for (int q = 0; q < p; ++q) {
+            a[q] = tj[q];
+            b[q] = tk0[q];
+        }
+        for (int q = 0; q < p - 1; ++q) a[q] = sj * a[q + 1];   // J (s_j tail_j)
+        a[p - 1] = 0.0;
         double d = 0.0;
-        for (int q = 0; q < p; ++q) d += tw[q] * tk0[q];
+        for (int q = 0; q < p; ++q) d += a[q] * b[q];
+        for (int q = 0; q < p; ++q) tw[q] = a[q];
         kry[KRY_H + (k0 - 1) * MAX_M + (j - 1)] = kry[KRY_S + k0] * (tot + d);
     } else if (mode == FIN_MGS) {
+        // loads first, as in FIN_MATVEC; c holds tail_{k+1} (k < j) or W (k = j)
         const double hkj = kry[KRY_H + (k - 1) * MAX_M + (j - 1)];
         const double sk = kry[KRY_S + k];
         const double* tk = kry_tail(kry, k);
         double* tw = kry_tail(kry, j + 1);
-        for (int q = 0; q < p; ++q) tw[q] -= hkj * sk * tk[q];
+        const double* tc = k < j ? kry_tail(kry, k + 1) : kry + KRY_W;
+        double* a = fin_buf[0];
+        double* w = fin_buf[1];
+        double* c = fin_buf[2];
+        for (int q = 0; q < p; ++q) {
+            a[q] = tk[q];
+            w[q] = tw[q];
+            c[q] = tc[q];
+        }
+        for (int q = 0; q < p; ++q) w[q] -= hkj * sk * a[q];
+        for (int q = 0; q < p; ++q) tw[q] = w[q];
         if (k < j) {
-            const double* tn = kry_tail(kry, k + 1);
             double d = 0.0;
-            for (int q = 0; q < p; ++q) d += tw[q] * tn[q];
+            for (int q = 0; q < p; ++q) d += w[q] * c[q];
             kry[KRY_H + k * MAX_M + (j - 1)] = kry[KRY_S + k + 1] * (tot + d);
         } else {
             double d = 0.0;
-            for (int q = 0; q < p; ++q) d += tw[q] * tw[q];
+            for (int q = 0; q < p; ++q) d += w[q] * w[q];
             const double h = sqrt(tot + d);
             if (j < m) {
                 kry[KRY_H + j * MAX_M + (j - 1)] = h;
@@ -133,7 +147,7 @@ __device__ inline void krylov_finalize(const ProblemDev* P, int mode, int j, int
                 } else {
                     kry[KRY_S + j + 1] = 1.0 / h;
                     double sg = 0.0;
-                    for (int q = 0; q < p; ++q) sg += kry[KRY_W + q] * tw[q];
+                    for (int q = 0; q < p; ++q) sg += c[q] * w[q];
                     P->sigma[j + 1] = P->has_src ? sg : 0.0;
                 }
             }
@@ -155,6 +169,21 @@ __device__ __forceinline__ double block_sum_fixed(double v, double* red) {
     return s;   // valid on thread 0
 }
 
+// The zeroing that starts an Arnoldi process (modes FIN_NORM0*), spread over the finalising
+// block: the Hessenberg block, and for FIN_NORM0_NOTAIL every tail, W and sigma.  Called by
+// all threads; ends with a barrier.
+__device__ inline void zero_krylov_start(const ProblemDev* P, int mode, int tid) {
+    if (mode != FIN_NORM0 && mode != FIN_NORM0_NOTAIL && mode != FIN_NORM0_TAIL) return;
+    double* kry = P->kry;
+    for (int r = tid; r < (MAX_M + 1) * MAX_M; r += NTHREADS) kry[KRY_H + r] = 0.0;
+    if (mode == FIN_NORM0_NOTAIL) {
+        for (int r = tid; r < (MAX_M + 1) * MAX_P; r += NTHREADS) kry[KRY_T + r] = 0.0;
+        for (int r = tid; r < MAX_P; r += NTHREADS) kry[KRY_W + r] = 0.0;
+        for (int r = tid; r <= MAX_M; r += NTHREADS) P->sigma[r] = 0.0;
+    }
+    __syncthreads();
+}
+
 // Write this block's partial into slot `slot`; if it is the last of the problem's `count`
 // blocks (slots base .. base + count - 1), sum all partials in a fixed order and finalise.
 // Must be called by all threads of the block.
@@ -174,6 +203,7 @@ __device__ inline void partial_and_finalize_at(const ProblemDev* P, int pid, con
     double v = 0.0;
     for (int t = tid; t < count; t += NTHREADS) v += __ldcg(a.partials + base + t);
     const double tot = block_sum_fixed(v, red);
+    zero_krylov_start(P, a.fin_mode, tid);
     if (tid == 0) {
         krylov_finalize(P, a.fin_mode, a.fin_j, a.fin_k, a.m, a.tol, tot);
         a.counters[pid] = 0u;
