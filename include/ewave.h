@@ -494,12 +494,22 @@ int ewv_sync(ewv_model_t model);
 int ewv_batch_sync(ewv_batch_t batch);
 
 /* Testing aid: the limit, in ns (at most 1e9, the default), after which a pipeline wait of
- * the 2D FP32 TMA pass on the current device gives up.  The kernel then waits (up to 1 s)
- * for its copies in flight, sets the timeout bit of the error word and returns, so that a
- * test can check the EWV_ERR_TIMEOUT path on a healthy GPU with a limit a normal pass
- * outruns (e.g. 0).  Waits for the device to be idle first; applies to later launches,
- * graph replays included.  Restore 1000000000 afterwards.  INVALID_ARG above 1e9. */
+ * the 2D FP32 TMA pass, or a grid-barrier wait of the Gram-Schmidt column kernel, on the
+ * current device gives up.  The TMA kernel then waits (up to 1 s) for its copies in flight;
+ * either sets the timeout bit of the error word and returns, so that a test can check the
+ * EWV_ERR_TIMEOUT path on a healthy GPU with a limit a normal pass outruns (e.g. 0).  Waits
+ * for the device to be idle first; applies to later launches, graph replays included.
+ * Restore 1000000000 afterwards.  INVALID_ARG above 1e9. */
 int ewv_debug_set_wait_limit(unsigned long long ns);
+
+/* Testing aid: whether Krylov steps (and the exponential Krylov adjoint) run each Arnoldi
+ * column's modified Gram-Schmidt steps on the column kernel -- one cooperative launch per
+ * column with q_{j+1} in shared memory and a bounded grid barrier per step, taken when every
+ * flat chunk of the engine fits one co-resident grid -- (1, the default) or on one flat
+ * pass per step (0).  In FP32 both give the same values bit for bit; in FP64 the flat form
+ * fuses the first dot of a column into the stencil pass, so they agree to rounding.
+ * Process-wide; waits for the device to be idle first. */
+int ewv_debug_set_column_kernel(int enable);
 
 #ifdef __cplusplus
 }

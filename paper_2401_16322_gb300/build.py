@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libewave.so")
 BUILD_DIR = os.path.join(ROOT, "_build")
 SOURCES = ["kernels_stencil.cu", "kernels_aux.cu", "kernels_tma.cu", "kernels_3d.cu",
-           "kernels_tma3d.cu", "kernels_kadj.cu", "api.cu", "noalloc.cu"]
+           "kernels_tma3d.cu", "kernels_kadj.cu", "kernels_mgs.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

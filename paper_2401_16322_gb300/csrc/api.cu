@@ -218,11 +218,17 @@ struct Engine {
     // Krylov step with dense output (ewv_step_krylov_dense): the caller's buffer of the
     // four Gauss-Legendre states, set for the duration of that call only
     void* kry_dense = nullptr;
+    // Gram-Schmidt column kernel: chunks per block for a co-resident grid (0: flat passes
+    // only), double-buffered partials and the grid-barrier words
+    int mgs_cpb = 0;
+    double* d_mgs_partials = nullptr;
+    unsigned int* d_mgs_bar = nullptr;
     // adaptive Krylov step: tolerance, dimension range and statistics of the current call
     double ad_tol = 0.0;
     int ad_mmin = 1, ad_mmax = 1;
     int ad_stats[3] = {0, 0, 0};
-    int* d_err = nullptr;       // error word: 1 = a TMA pipeline wait timed out, 2 = non-finite
+    int* d_err = nullptr;       // error word: 1 = a bounded wait timed out (TMA pipeline or the
+                                // Gram-Schmidt grid barrier), 2 = non-finite
     int* h_err = nullptr;       // pinned host copy, written by an async copy at the end of a call
     cudaEvent_t err_ev = nullptr;   // recorded after that copy
     std::map<std::tuple<double, int, double, double, double>, std::vector<double>> faber_cache;
@@ -286,6 +292,8 @@ struct Engine {
         cudaFree(d_adj_maps);
         cudaFree(d_kadj);
         cudaFree(d_kexp_maps);
+        cudaFree(d_mgs_partials);
+        cudaFree(d_mgs_bar);
         cudaFree(d_kbar);
     }
 };
@@ -299,6 +307,16 @@ struct ewv_batch {
 };
 
 namespace {
+
+// Krylov steps run each Arnoldi column's Gram-Schmidt steps on the column kernel when the
+// engine's chunks fit one co-resident grid (ewv_debug_set_column_kernel(0) keeps the flat
+// passes, for comparisons)
+bool g_mgs_enabled = true;
+
+// One column's Gram-Schmidt steps (first dot, then k = k0 .. kmax) on the column kernel over
+// nprob problems laid out like the engine's (its chunk table); false if it cannot run.
+bool mgs_column(Engine* E, int precision, const ProblemDev* probs, int nprob, int j, int k0, int kmax, int m,
+                double tol, cudaStream_t s);
 
 int fail(std::string& err, int code, const char* fmt, ...) {
     char buf[512];
@@ -481,6 +499,17 @@ int build_engine(Engine* E, std::string& err) {
         E->d_pbase = nullptr;
         CUDA_OR_FAIL(err, cudaMalloc(&E->d_pbase, sizeof(int) * pb.size()));
         CUDA_OR_FAIL(err, cudaMemcpy(E->d_pbase, pb.data(), sizeof(int) * pb.size(), cudaMemcpyHostToDevice));
+        // the Gram-Schmidt column kernel, where every chunk fits one co-resident grid
+        cudaFree(E->d_mgs_partials);
+        cudaFree(E->d_mgs_bar);
+        E->d_mgs_partials = nullptr;
+        E->d_mgs_bar = nullptr;
+        E->mgs_cpb = mgs_column_chunks_per_block(E->precision, E->nchunks);
+        if (E->mgs_cpb > 0) {
+            CUDA_OR_FAIL(err, cudaMalloc(&E->d_mgs_partials, sizeof(double) * 2 * (size_t)E->nchunks));
+            CUDA_OR_FAIL(err, cudaMalloc(&E->d_mgs_bar, sizeof(unsigned int) * 2));
+            CUDA_OR_FAIL(err, cudaMemset(E->d_mgs_bar, 0, sizeof(unsigned int) * 2));
+        }
     }
     if (E->precision == EWV_F32 && E->dims == 2) {
         if (build_tensor_maps(E->probs, E->R, work_vecs, &E->d_maps) != 0)
@@ -1069,6 +1098,21 @@ int run_rk(Ctx& C, double t, double dt, int scheme, int nsteps) {
     return check_launch(*C.err);
 }
 
+bool mgs_column(Engine* E, int precision, const ProblemDev* probs, int nprob, int j, int k0, int kmax, int m,
+                double tol, cudaStream_t s) {
+    if (E->mgs_cpb <= 0 || nprob != E->nprob || !E->d_mgs_partials || !E->d_mgs_bar) return false;
+    MgsArgs ma{};
+    ma.j = j;
+    ma.k0 = k0;
+    ma.kmax = kmax;
+    ma.m = m;
+    ma.tol = tol;
+    ma.partials = E->d_mgs_partials;
+    ma.bar = E->d_mgs_bar;
+    ma.err = E->d_err;
+    return launch_mgs_column(precision, E->nchunks, E->mgs_cpb, probs, E->d_pbase, nprob, ma, s) == 0;
+}
+
 int run_krylov(Ctx& C, double t, double dt, int m, int nsteps, int* info) {
     std::string& err = *C.err;
     if (m < 1 || m > MAX_M) return fail(err, EWV_ERR_INVALID_ARG, "Krylov m must be 1..%d", MAX_M);
@@ -1098,6 +1142,7 @@ int run_krylov(Ctx& C, double t, double dt, int m, int nsteps, int* info) {
         pn.partials = C.E->d_partials;
         pn.counters = C.E->d_counters;
         C.point(pn);
+        const bool col = g_mgs_enabled && C.E->mgs_cpb > 0;
         for (int j = 1; j <= m; ++j) {
             // orthogonalise q_{j+1} against q_{k0} .. q_j (all of them without a window)
             const int k0 = window > 0 ? std::max(1, j - window + 1) : 1;
@@ -1116,12 +1161,17 @@ int run_krylov(Ctx& C, double t, double dt, int m, int nsteps, int* info) {
             a.tol = tol;
             a.partials = C.E->d_partials;
             a.counters = C.E->d_counters;
-            if (split_dot) {
+            if (split_dot || col) {
                 a.d = -1;
                 a.fin_mode = FIN_NONE;
             }
             C.stage(a);
-            if (split_dot) {
+            if (col && mgs_column(C.E, C.E->precision, C.E->d_probs, C.E->nprob, j, k0, (j == m) ? j - 1 : j, m,
+                                  tol, C.s)) {
+                ++*C.launches;
+                continue;
+            }
+            if (split_dot || col) {        // (col: the column kernel could not be launched)
                 PointArgs pd{};
                 pd.mode = 5;
                 pd.j = j;
@@ -1630,7 +1680,7 @@ int take_pending_error(Engine* E, cudaStream_t s, std::string& err) {
     const int w = *(volatile int*)E->h_err;
     CUDA_OR_FAIL(err, cudaMemset(E->d_err, 0, sizeof(int)));
     *(volatile int*)E->h_err = 0;
-    if (w & 1) return fail(err, EWV_ERR_TIMEOUT, "a pipeline wait in the TMA stencil kernel timed out "
+    if (w & 1) return fail(err, EWV_ERR_TIMEOUT, "a bounded wait in a TMA pass or a Gram-Schmidt barrier timed out "
                                                  "during an earlier call");
     return fail(err, EWV_ERR_NONFINITE, "a non-finite value appeared in the state during an earlier call");
 }
@@ -2415,6 +2465,7 @@ static int adjoint_krylov(ewv_model* m, Engine* E, double t, double dt, int mm, 
                                  0.32607257743127307, 0.17392742256872693};
     const int fset = tma ? tma_map_set(tma_variant_tile_height_for(E->tma_variant, false)) : 0;
     const int trset = tma_map_set(18), gset = tma_map_set(30);
+    const bool col = g_mgs_enabled && E->mgs_cpb > 0 && E->nprob == ns;
     auto arnoldi = [&](const ProblemDev* v, bool transpose) {
         PointArgs pn{};
         pn.mode = 0;
@@ -2442,7 +2493,37 @@ static int adjoint_krylov(ewv_model* m, Engine* E, double t, double dt, int mm, 
             a.partials = E->d_partials;
             a.counters = E->d_counters;
             bool fused = true;
-            if (tma) {
+            if (col) {
+                // the product without a dot (TMA pass in FP32), then the column kernel
+                StageArgs b = a;
+                b.d = -1;
+                b.fin_mode = FIN_NONE;
+                const int set = transpose ? trset : fset;
+                const int* tbs = tma ? E->d_tbase + (size_t)set * (E->nprob + 1) : nullptr;
+                int rc = 1;
+                if (tma)
+                    rc = transpose ? launch_transpose_tma(R, v, tbs, ns, E->ntiles_by[set], b, E->d_err, s)
+                                   : launch_stage_tma(E->tma_variant, R, v, tbs, ns, E->ntiles_by[set], b, E->d_err, s);
+                if (rc != 0) launch_stage(prec, R, tb, v, d_tp, b, s);
+                ++m->launches;
+                const int kmax = (j == mm) ? j - 1 : j;
+                if (mgs_column(E, prec, v, ns, j, 1, kmax, mm, tol, s)) {
+                    ++m->launches;
+                    continue;
+                }
+                // the column kernel could not be launched: the flat dot, then the flat passes
+                PointArgs pd{};
+                pd.mode = 5;
+                pd.j = j;
+                pd.k = 1;
+                pd.m = mm;
+                pd.tol = tol;
+                pd.partials = E->d_partials;
+                pd.counters = E->d_counters;
+                launch_point_flat(prec, E->nchunks, v, E->d_pbase, ns, pd, s);
+                ++m->launches;
+                fused = false;
+            } else if (tma) {
                 StageArgs b = a;
                 b.d = -1;
                 b.fin_mode = FIN_NONE;
@@ -2536,7 +2617,7 @@ static int adjoint_krylov(ewv_model* m, Engine* E, double t, double dt, int mm, 
     CUDA_OR_FAIL(m->err, cudaStreamSynchronize(s));
     if (herr) {
         CUDA_OR_FAIL(m->err, cudaMemset(E->d_err, 0, sizeof(int)));
-        return fail(m->err, EWV_ERR_TIMEOUT, "a pipeline wait in the TMA stencil kernel timed out");
+        return fail(m->err, EWV_ERR_TIMEOUT, "a bounded wait in a TMA pass or a Gram-Schmidt barrier timed out");
     }
     return EWV_OK;
 }
@@ -2895,7 +2976,7 @@ static int adjoint_step_impl(ewv_model_t m, int method, double t, double dt, int
         CUDA_OR_FAIL(m->err, cudaStreamSynchronize(s));
         if (herr) {
             CUDA_OR_FAIL(m->err, cudaMemset(E->d_err, 0, sizeof(int)));
-            return fail(m->err, EWV_ERR_TIMEOUT, "a pipeline wait in the TMA stencil kernel timed out");
+            return fail(m->err, EWV_ERR_TIMEOUT, "a bounded wait in a TMA pass or a Gram-Schmidt barrier timed out");
         }
         return EWV_OK;
     };
@@ -3124,7 +3205,13 @@ int ewv_batch_sync(ewv_batch_t b) {
 int ewv_debug_set_wait_limit(unsigned long long ns) {
     if (ns > 1000000000ull) return EWV_ERR_INVALID_ARG;
     if (cudaDeviceSynchronize() != cudaSuccess) return EWV_ERR_CUDA;
-    return set_tma_wait_limit_ns(ns) == 0 ? EWV_OK : EWV_ERR_CUDA;
+    return set_tma_wait_limit_ns(ns) == 0 && set_mgs_wait_limit_ns(ns) == 0 ? EWV_OK : EWV_ERR_CUDA;
+}
+
+int ewv_debug_set_column_kernel(int enable) {
+    if (cudaDeviceSynchronize() != cudaSuccess) return EWV_ERR_CUDA;
+    g_mgs_enabled = enable != 0;
+    return EWV_OK;
 }
 
 }  // extern "C"

@@ -235,6 +235,22 @@ void launch_inject(int precision, void* adj, long long vec_elems, const void* va
 void launch_sum_shots(int precision, const void* in, void* out, long long n, int nshots,
                       cudaStream_t s);
 int launch_expm(const ProblemDev* probs, int nprob, int mmax, cudaStream_t s, double hscale = 1.0);
+
+// kernels_mgs.cu: the modified Gram-Schmidt steps of one Arnoldi column (first dot, then
+// k = k0 .. kmax) in one cooperative launch over the flat chunks, q_{j+1} in shared memory.
+constexpr int MGS_MAX_CPB = 4;   // chunks per block at most
+struct MgsArgs {
+    int j, k0, kmax, m, cpb;
+    double tol;
+    double* partials;     // 2 x nchunks
+    unsigned int* bar;    // [2]: grid-barrier arrivals and generation
+    int* err;             // error word (bit 0: a barrier wait gave up)
+};
+// Chunks per block for which the grid is co-resident (smallest), or 0 if none is.
+int mgs_column_chunks_per_block(int precision, int nchunks);
+int launch_mgs_column(int precision, int nchunks, int cpb, const ProblemDev* probs, const int* pbase, int nprob,
+                      const MgsArgs& ma, cudaStream_t s);
+int set_mgs_wait_limit_ns(unsigned long long ns);
 void launch_faber_coeffs(double dt, double gamma, double c0, double c1, int m, double* out,
                          cudaStream_t s);
 

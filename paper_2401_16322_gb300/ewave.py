@@ -38,7 +38,7 @@ EXPORTS = [
     "ewv_batch_last_error", "ewv_version", "ewv_launch_count", "ewv_enable_kernel_timing",
     "ewv_kernel_timing", "ewv_batch_enable_kernel_timing", "ewv_batch_kernel_timing", "ewv_reset_state",
     "ewv_faber_step_noalloc", "ewv_adjoint_step", "ewv_adjoint_inject", "ewv_checkpoint_stride",
-    "ewv_step_krylov_dense", "ewv_adjoint_step_krylov_dense",
+    "ewv_step_krylov_dense", "ewv_adjoint_step_krylov_dense", "ewv_debug_set_column_kernel",
     "ewv_sum_shot_fields", "ewv_enable_graphs", "ewv_batch_enable_graphs",
     "ewv_set_kernel_variant", "ewv_kernel_variant", "ewv_batch_set_kernel_variant",
     "ewv_batch_kernel_variant", "ewv_set_source_receivers3d", "ewv_set_storage_rounding",
@@ -156,6 +156,7 @@ def load_library(path=LIB_PATH):
         "ewv_sync": ([vp], i),
         "ewv_batch_sync": ([vp], i),
         "ewv_debug_set_wait_limit": ([ctypes.c_ulonglong], i),
+        "ewv_debug_set_column_kernel": ([i], i),
         "ewv_set_krylov_adjoint": ([vp, i], i),
         "ewv_step_krylov_adaptive": ([vp, d, d, d, i, i, i, ctypes.POINTER(i)], i),
         "ewv_batch_step_krylov_adaptive": ([vp, d, d, d, i, i, i, ctypes.POINTER(i)], i),
@@ -502,10 +503,19 @@ def checkpoint_stride(nsteps, budget):
 
 
 def debug_set_wait_limit(ns):
-    """Testing aid: pipeline-wait limit of the 2D FP32 TMA pass (ns, default 1e9)."""
+    """Testing aid: wait limit (ns, default 1e9) of the 2D FP32 TMA pass's pipeline waits and
+    of the Gram-Schmidt column kernel's grid barriers."""
     rc = load_library().ewv_debug_set_wait_limit(int(ns))
     if rc != EWV_OK:
         raise EwaveError(f"debug_set_wait_limit: {ERRORS.get(rc, rc)}")
+
+
+def debug_set_column_kernel(enable):
+    """Testing aid: run the Krylov Gram-Schmidt steps on the column kernel (True, default,
+    where the engine's chunks fit one co-resident grid) or on the flat passes (False)."""
+    rc = load_library().ewv_debug_set_column_kernel(1 if enable else 0)
+    if rc != EWV_OK:
+        raise EwaveError(f"debug_set_column_kernel: {ERRORS.get(rc, rc)}")
 
 
 def faber_step_noalloc(args, state, c2, t, dt, degree, nsteps=1, stream=None):
