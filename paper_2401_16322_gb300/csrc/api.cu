@@ -223,6 +223,7 @@ struct Engine {
     int mgs_cpb = 0;
     double* d_mgs_partials = nullptr;
     unsigned int* d_mgs_bar = nullptr;
+    double* d_ecoef = nullptr;    // [nprob][MAX_TAU][MAX_M]: exp(tau H) e_1 of a multi-output combine
     // adaptive Krylov step: tolerance, dimension range and statistics of the current call
     double ad_tol = 0.0;
     int ad_mmin = 1, ad_mmax = 1;
@@ -294,6 +295,7 @@ struct Engine {
         cudaFree(d_kexp_maps);
         cudaFree(d_mgs_partials);
         cudaFree(d_mgs_bar);
+        cudaFree(d_ecoef);
         cudaFree(d_kbar);
     }
 };
@@ -505,6 +507,9 @@ int build_engine(Engine* E, std::string& err) {
         E->d_mgs_partials = nullptr;
         E->d_mgs_bar = nullptr;
         E->mgs_cpb = mgs_column_chunks_per_block(E->precision, E->nchunks);
+        cudaFree(E->d_ecoef);
+        E->d_ecoef = nullptr;
+        CUDA_OR_FAIL(err, cudaMalloc(&E->d_ecoef, sizeof(double) * (size_t)E->nprob * MAX_TAU * MAX_M));
         if (E->mgs_cpb > 0) {
             CUDA_OR_FAIL(err, cudaMalloc(&E->d_mgs_partials, sizeof(double) * 2 * (size_t)E->nchunks));
             CUDA_OR_FAIL(err, cudaMalloc(&E->d_mgs_bar, sizeof(unsigned int) * 2));
@@ -708,7 +713,7 @@ struct Ctx {
         ++*launches;
     }
     void point(const PointArgs& pa) {
-        if (pa.mode <= 2 || pa.mode == 5 || pa.mode == 7)   // norm, MGS, combine, dots: flat
+        if (pa.mode <= 2 || pa.mode == 5 || pa.mode == 7 || pa.mode == 8)   // norm, MGS, combines, dots: flat
             launch_point_flat(E->precision, E->nchunks, E->d_probs, E->d_pbase, E->nprob, pa, s);
         else
             launch_point(E->precision, E->ntiles, E->d_probs, E->d_tile_prob, pa, s);
@@ -1197,23 +1202,28 @@ int run_krylov(Ctx& C, double t, double dt, int m, int nsteps, int* info) {
             }
         }
         if (dense) {
-            for (int q = 0; q < 4; ++q) {
-                if (launch_expm(C.E->d_probs, C.E->nprob, m, C.s, kTauGL[q]) != 0) expm_ok = false;
-                ++*C.launches;
-                PointArgs pq{};
-                pq.mode = 2;
-                pq.m = m;
-                pq.out = static_cast<char*>(dense) + (size_t)q * C.E->nprob * vel * C.E->models[0]->elem;
-                pq.out_stride = vel;
-                C.point(pq);
-            }
+            // the four dense states and the step's result from one read of the basis
+            const double taus[5] = {kTauGL[0], kTauGL[1], kTauGL[2], kTauGL[3], 1.0};
+            if (launch_expm_multi(C.E->d_probs, C.E->nprob, m, C.s, taus, 5, C.E->d_ecoef) != 0) expm_ok = false;
+            ++*C.launches;
+            PointArgs pq{};
+            pq.mode = 8;
+            pq.m = m;
+            pq.nout = 4;
+            pq.final_out = 1;
+            pq.ecoef = C.E->d_ecoef;
+            pq.out = dense;
+            pq.out_stride = vel;
+            pq.out_qstride = (long long)C.E->nprob * vel;
+            C.point(pq);
+        } else {
+            if (launch_expm(C.E->d_probs, C.E->nprob, m, C.s) != 0) expm_ok = false;
+            ++*C.launches;
+            PointArgs pc{};
+            pc.mode = 2;
+            pc.m = m;
+            C.point(pc);
         }
-        if (launch_expm(C.E->d_probs, C.E->nprob, m, C.s) != 0) expm_ok = false;
-        ++*C.launches;
-        PointArgs pc{};
-        pc.mode = 2;
-        pc.m = m;
-        C.point(pc);
         C.record();
     });
     if (rc0 != EWV_OK) return rc0;
@@ -2565,11 +2575,16 @@ static int adjoint_krylov(ewv_model* m, Engine* E, double t, double dt, int mm, 
             }
         }
     };
-    auto dense = [&](const ProblemDev* v, double tau, int dst) {
-        if (launch_expm(v, ns, mm, s, tau) != 0) return false;
+    // dense output of a basis at ntau values of tau from one read of it: vectors dst .. dst + 3
+    // (and, with final, the last tau into vector 0)
+    auto dense = [&](const ProblemDev* v, const double* taus, int ntau, int dst, int final) {
+        if (launch_expm_multi(v, ns, mm, s, taus, ntau, E->d_ecoef) != 0) return false;
         PointArgs pc{};
-        pc.mode = 2;
+        pc.mode = 8;
         pc.m = mm;
+        pc.nout = ntau - final;
+        pc.final_out = final;
+        pc.ecoef = E->d_ecoef;
         pc.dst = dst;
         launch_point_flat(prec, E->nchunks, v, E->d_pbase, ns, pc, s);
         m->launches += 2;
@@ -2588,13 +2603,14 @@ static int adjoint_krylov(ewv_model* m, Engine* E, double t, double dt, int mm, 
         launch_prologue(vF, ns, PRO_KRYLOV, mm, 0.0, 0.0, 0.0, s);
         m->launches += 2;
         arnoldi(vF, false);
-        for (int q = 0; q < 4; ++q)
-            if (!dense(vF, kTau[q], mm + 1 + q)) return fail(m->err, EWV_ERR_CUDA, "expm configuration failed");
+        if (!dense(vF, kTau, 4, mm + 1, 0)) return fail(m->err, EWV_ERR_CUDA, "expm configuration failed");
     }
     // adjoint Arnoldi on dt H^T from the cotangent (no tail, no source)
     arnoldi(vA, true);
-    for (int q = 0; q < 4; ++q)
-        if (!dense(vA, 1.0 - kTau[q], mm + 1 + q)) return fail(m->err, EWV_ERR_CUDA, "expm configuration failed");
+    // y(1 - tau_q) into vectors m+1 .. m+4 of A, and the new cotangent y(1) into the cotangent
+    // buffer (the gradient passes below do not read it)
+    const double taus_a[5] = {1.0 - kTau[0], 1.0 - kTau[1], 1.0 - kTau[2], 1.0 - kTau[3], 1.0};
+    if (!dense(vA, taus_a, 5, mm + 1, 1)) return fail(m->err, EWV_ERR_CUDA, "expm configuration failed");
     // gradient: dt w_q y_v(1 - tau_q) G(x(tau_q))
     for (int q = 0; q < 4; ++q) {
         StageArgs gr = stage_defaults();
@@ -2607,8 +2623,6 @@ static int adjoint_krylov(ewv_model* m, Engine* E, double t, double dt, int mm, 
             launch_stage(prec, R, tb, vG, d_tp, gr, s);
         ++m->launches;
     }
-    // new cotangent y(1) into the cotangent buffer
-    if (!dense(vA, 1.0, 0)) return fail(m->err, EWV_ERR_CUDA, "expm configuration failed");
     int rc = check_launch(m->err);
     if (rc != EWV_OK || !(tma || tma_grad)) return rc;
     // the TMA pipeline's timeout flag

@@ -138,7 +138,8 @@ struct StageArgs {
 struct PointArgs {
     int mode;        // 0: |q1|^2 (norm); 1: MGS pass; 2: Krylov combine; 3: copy; 4: swap;
                      // 5: <q_{j+1}, q_k> after a matrix-vector product (flat); 6: zero the
-                     // fields fmask of vector dst; 7: |slot j+1|^2 into kry[KRY_AN] (flat)
+                     // fields fmask of vector dst; 7: |slot j+1|^2 into kry[KRY_AN] (flat);
+                     // 8: multi-output Krylov combine (flat)
     int j, k, m;
     int src, dst;    // copy / swap vectors; combine: destination vector (mode 2)
     int notail;      // mode 0: 1 = start an Arnoldi process without the augmented tail;
@@ -149,6 +150,13 @@ struct PointArgs {
     unsigned int* counters;
     void* out;             // combine (mode 2): when set, problem p's result goes to the
     long long out_stride;  // caller's buffer at out + p * out_stride elements, not vector dst
+    // multi-output combine (mode 8): nout outputs from one read of the basis, output q with the
+    // coefficients ecoef[(p (nout + final) + q) MAX_M ..] going to out + q out_qstride +
+    // p out_stride (out set) or to vector dst + q; with final = 1 one more output, the last
+    // coefficient row, goes to vector 0 (the state; every element is read before it is written)
+    int nout, final_out;
+    const double* ecoef;
+    long long out_qstride;
 };
 
 // Host-side launchers (defined in kernels_stencil.cu / kernels_aux.cu).
@@ -235,6 +243,16 @@ void launch_inject(int precision, void* adj, long long vec_elems, const void* va
 void launch_sum_shots(int precision, const void* in, void* out, long long n, int nshots,
                       cudaStream_t s);
 int launch_expm(const ProblemDev* probs, int nprob, int mmax, cudaStream_t s, double hscale = 1.0);
+// exp(tau_q H_meff) e_1 for ntau (<= MAX_TAU) values of tau in one launch, into
+// out[(p ntau + q) MAX_M ..] (the coefficients of a multi-output Krylov combine, mode 8)
+constexpr int MAX_TAU = 5;
+struct ExpmTaus {
+    int n;
+    double tau[MAX_TAU];
+    double* out;
+};
+int launch_expm_multi(const ProblemDev* probs, int nprob, int mmax, cudaStream_t s, const double* taus, int ntau,
+                      double* out);
 
 // kernels_mgs.cu: the modified Gram-Schmidt steps of one Arnoldi column (first dot, then
 // k = k0 .. kmax) in one cooperative launch over the flat chunks, q_{j+1} in shared memory.

@@ -417,6 +417,62 @@ point_flat_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ 
     partial_and_finalize_at(P, pid, a, bsum, red, &s_last, blockIdx.x, blockIdx.x - pc.y, P->pchunks);
 }
 
+// Multi-output Krylov combine (PointArgs mode 8): output q = beta sum_{k=1}^{meff} e_{q,k} s_k q_k
+// for every q from one read of the basis (each output's arithmetic is that of mode 2, so an
+// output equals the single combine with the same coefficients bit for bit).  A kernel of its
+// own keeps the accumulators out of the flat passes' register budget.
+template <typename T>
+__global__ void __launch_bounds__(NTHREADS)
+combine_multi_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__ pbase, int nprob, PointArgs pa) {
+    using V = typename Vec16<T>::type;
+    constexpr int NV = Vec16<T>::N;
+    __shared__ T s_mc[MAX_TAU][MAX_M];
+    const int2 pc = __ldg(reinterpret_cast<const int2*>(pbase + flat_block_table(nprob)) + blockIdx.x);
+    const int pid = pc.x;
+    const ProblemDev* P = probs + pid;
+    const double* kry = P->kry;
+    if (kry[KRY_NONFINITE] != 0.0 || kry[KRY_SKIP] != 0.0) return;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int meff = (int)kry[KRY_MEFF];
+    const double beta = kry[KRY_BETA];
+    const int nt = pa.nout + pa.final_out;
+    const double* ec = pa.ecoef + (size_t)pid * nt * MAX_M;
+    for (int e = tid; e < nt * meff; e += NTHREADS) {
+        const int q = e / meff, k = e - q * meff;
+        s_mc[q][k] = (T)(beta * ec[q * MAX_M + k] * kry[KRY_S + k + 1]);
+    }
+    __syncthreads();
+    const long long nelem = (long long)P->nfields * P->field_stride;
+    const long long e0 = (long long)pc.y * PCHUNK;
+    const long long e1 = e0 + PCHUNK < nelem ? e0 + PCHUNK : nelem;
+    const long long q0 = e0 / NV, q1 = e1 / NV;
+    V* outs[MAX_TAU];
+#pragma unroll
+    for (int q = 0; q < MAX_TAU; ++q) {
+        outs[q] = nullptr;
+        if (q < pa.nout)
+            outs[q] = pa.out ? reinterpret_cast<V*>(static_cast<T*>(pa.out) + q * pa.out_qstride +
+                                                    (long long)pid * pa.out_stride)
+                             : reinterpret_cast<V*>(vptr<T>(P, pa.dst + q));
+        else if (q == pa.nout && pa.final_out)
+            outs[q] = reinterpret_cast<V*>(vptr<T>(P, 0));
+    }
+    for (long long i = q0 + tid; i < q1; i += NTHREADS) {
+        V acc[MAX_TAU];
+#pragma unroll
+        for (int q = 0; q < MAX_TAU; ++q) acc[q] = V{};
+        for (int k = 1; k <= meff; ++k) {
+            const V v = reinterpret_cast<const V*>(vptr<T>(P, k - 1))[i];
+#pragma unroll
+            for (int q = 0; q < MAX_TAU; ++q)
+                if (q < nt) fma16(acc[q], s_mc[q][k - 1], v);
+        }
+#pragma unroll
+        for (int q = 0; q < MAX_TAU; ++q)
+            if (q < nt) outs[q][i] = acc[q];
+    }
+}
+
 // ---------------------------------------------------------------- Hessenberg exponential
 // [13/13] Pade approximant with scaling and squaring (Higham 2005), FP64, one block per
 // problem; writes exp(H_meff) e_1 to kry[KRY_E..].  Shared memory: 7 matrices of meff^2.
@@ -430,13 +486,17 @@ __device__ void mat_mul(const double* A, const double* B, double* C, int n) {
     __syncthreads();
 }
 
-__global__ void expm_kernel(const ProblemDev* probs, int nprob, double hscale) {
+// Block (p, q) writes exp(tau_q H_meff) e_1 of problem p to kry[KRY_E..] (et.out null, one
+// tau) or to et.out[(p ntau + q) MAX_M ..] (several taus in one launch).
+__global__ void expm_kernel(const ProblemDev* probs, int nprob, ExpmTaus et) {
     extern __shared__ double sm[];
     __shared__ double b[14];
     __shared__ double colmax[MAX_M];
     __shared__ int s_scale, s_piv;
     const ProblemDev* P = probs + blockIdx.x;
     double* kry = P->kry;
+    const double hscale = et.tau[blockIdx.y];
+    double* eo = et.out ? et.out + ((size_t)blockIdx.x * et.n + blockIdx.y) * MAX_M : kry + KRY_E;
     const int n = (int)kry[KRY_MEFF];
     if (n <= 0 || kry[KRY_NONFINITE] != 0.0) return;
     const int nn = n * n;
@@ -570,7 +630,7 @@ __global__ void expm_kernel(const ProblemDev* probs, int nprob, double hscale) {
             for (int r = tid; r < n; r += blockDim.x) x[r] = y[r];
             __syncthreads();
         }
-        for (int r = tid; r < n; r += blockDim.x) kry[KRY_E + r] = x[r];
+        for (int r = tid; r < n; r += blockDim.x) eo[r] = x[r];
     } else {
         double* cur = Rm;
         double* nxt = Um;
@@ -580,7 +640,7 @@ __global__ void expm_kernel(const ProblemDev* probs, int nprob, double hscale) {
             cur = nxt;
             nxt = t;
         }
-        for (int r = tid; r < n; r += blockDim.x) kry[KRY_E + r] = cur[r * n + 0];
+        for (int r = tid; r < n; r += blockDim.x) eo[r] = cur[r * n + 0];
     }
 }
 
@@ -691,18 +751,40 @@ void launch_point_flat(int precision, int nchunks, const ProblemDev* probs, cons
                        int nprob, const PointArgs& pa, cudaStream_t s) {
     if (nchunks <= 0) return;
     const dim3 block(TPX, TPY);
+    if (pa.mode == 8) {
+        if (pa.nout + pa.final_out < 1 || pa.nout + pa.final_out > MAX_TAU || !pa.ecoef) return;
+        if (precision == 0) combine_multi_kernel<float><<<nchunks, block, 0, s>>>(probs, pbase, nprob, pa);
+        else combine_multi_kernel<double><<<nchunks, block, 0, s>>>(probs, pbase, nprob, pa);
+        return;
+    }
     if (precision == 0) point_flat_kernel<float><<<nchunks, block, 0, s>>>(probs, pbase, nprob, pa);
     else point_flat_kernel<double><<<nchunks, block, 0, s>>>(probs, pbase, nprob, pa);
 }
-int launch_expm(const ProblemDev* probs, int nprob, int mmax, cudaStream_t s, double hscale) {
+static int launch_expm_taus(const ProblemDev* probs, int nprob, int mmax, cudaStream_t s, const ExpmTaus& et) {
     const size_t smem = (size_t)7 * mmax * mmax * sizeof(double);
     if (smem > 48 * 1024) {
         if (cudaFuncSetAttribute(expm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem) != cudaSuccess)
             return -1;
     }
-    expm_kernel<<<nprob, 256, smem, s>>>(probs, nprob, hscale);
+    expm_kernel<<<dim3(nprob, et.n), 256, smem, s>>>(probs, nprob, et);
     return 0;
+}
+int launch_expm(const ProblemDev* probs, int nprob, int mmax, cudaStream_t s, double hscale) {
+    ExpmTaus et{};
+    et.n = 1;
+    et.tau[0] = hscale;
+    et.out = nullptr;
+    return launch_expm_taus(probs, nprob, mmax, s, et);
+}
+int launch_expm_multi(const ProblemDev* probs, int nprob, int mmax, cudaStream_t s, const double* taus, int ntau,
+                      double* out) {
+    if (ntau < 1 || ntau > MAX_TAU || !out) return -1;
+    ExpmTaus et{};
+    et.n = ntau;
+    for (int q = 0; q < ntau; ++q) et.tau[q] = taus[q];
+    et.out = out;
+    return launch_expm_taus(probs, nprob, mmax, s, et);
 }
 void launch_faber_coeffs(double dt, double gamma, double c0, double c1, int m, double* out,
                          cudaStream_t s) {
