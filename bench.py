@@ -553,6 +553,37 @@ def config5_3d(n=400, check_n=0, target=TARGET):
         out["candidates"].append(cand)
         log(f"3D {method} ({prec}) m={m} at {k:.3g} x: {step_ms:.2f} ms/step, {nsteps} steps, "
             f"{cand['time_to_T_s']:.2f} s, err {err:.3e}")
+    # the 3D pass of each fused integrator timed on its own, whether or not its step was
+    # selected: 4 steps of Faber 40 and of HORK 16 in Horner form at 2 x the 3D leap-frog step
+    if md is not None:
+        out["pass_rooflines"] = {}
+        for method, m in (("faber", 40), ("hork-horner", 16)):
+            try:
+                dt = 2.0 * dt3
+                bm = base_method([md], method)
+                md.ensure_workspace(bm, m)
+                md.reset_state()
+                md.step(bm, t_live - 2 * dt, dt, m, 2)
+                torch.cuda.synchronize()
+                md.enable_kernel_timing(True)
+                md.kernel_timing()
+                md.step(bm, t_live, dt, m, 4)
+                md.sync()
+                kms, kn = md.kernel_timing()
+                md.enable_kernel_timing(False)
+                words = pass_words3d(method, m)
+                per_launch = sum(words) * 4.0 * n ** 3 / len(words)
+                avg = kms / kn * 1e-3
+                out["pass_rooflines"][method] = {
+                    "m": m, "bound": "hbm", "kernel": "stage_tma3d_kernel (FP32)",
+                    "achieved": per_launch / avg / 1e9, "peak": peak, "unit": "GB/s",
+                    "frac": per_launch / avg / 1e9 / peak, "peak_kind": peak_kind,
+                    "avg_launch_us": avg * 1e6, "alg_bytes_per_launch": per_launch}
+                log(f"3D {method} pass: {avg * 1e6:.1f} us, "
+                    f"{per_launch / avg / 1e9 / peak:.3f} of the {peak_kind} copy peak")
+            except Exception as e:
+                md.enable_kernel_timing(False)
+                log(f"3D {method} pass timing failed: {e}")
     for d in (md, md64):
         if d is not None:
             d.close()
@@ -1035,6 +1066,8 @@ def run_ours(args):
                             "leapfrog_f32": {k_: (x3.get("leapfrog_best") or {}).get(k_) for k_ in
                                              ("dt_over_leapfrog_step", "time_to_T_s", "seismo_rel_err_vs_fp64")},
                             "roofline_frac": x3.get("roofline_frac"),
+                            "pass_roofline_frac": {k_: v_.get("frac") for k_, v_ in
+                                                   (x3.get("pass_rooflines") or {}).items()},
                             "pml": x3.get("pml")} if x3 else None),
             "config1_fp64": ({"selected": f1.get("selected"), "leapfrog": f1.get("leapfrog")}
                              if f1 else None),
