@@ -362,6 +362,19 @@ stage_tma3d_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__
             const int lt = task - __ldg(tbase + pid);
             const int k0 = ((lt / tiles_x) / tiles_y) * KC3;
             const int k1 = min(k0 + KC3, P->nz);
+            // the horizontal damping of this thread's column and rows is fixed for the task:
+            // looked up once, not per plane
+            const int ti_ = (lt % tiles_x) * BX + tx;
+            const int nxt = P->nx, nyt = P->ny;
+            const float bxn_t = bt3(btab, nbt, 2 * min(ti_ + 1, nxt - ti_));
+            const float bxh_t = bt3(btab, nbt, min(2 * ti_ + 3, 2 * (nxt - ti_) - 1));
+            float byn_t[NR], byh_t[NR];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const int tj_ = ((lt / tiles_x) % tiles_y) * BY3 + NR * ty + r;
+                byn_t[r] = bt3(btab, nbt, 2 * min(tj_ + 1, nyt - tj_));
+                byh_t[r] = bt3(btab, nbt, min(2 * tj_ + 3, 2 * (nyt - tj_) - 1));
+            }
             for (int f = k0 - R; f < k1 + R; ++f, ++it) {
                 const int s = it % NST;
                 const uint32_t ph = (uint32_t)(it / NST) & 1u;
@@ -392,8 +405,7 @@ stage_tma3d_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__
                     const float* su = st + L::U_OFF;
                     const float* swx = st + L::WX_OFF;
                     const float* swy = st + L::WY_OFF;
-                    const float bxn = bt3(btab, nbt, 2 * min(i + 1, nx - i));
-                    const float bxh = bt3(btab, nbt, min(2 * i + 3, 2 * (nx - i) - 1));
+                    const float bxn = bxn_t, bxh = bxh_t;
                     const float bzn = bt3(btab, nbt, 2 * (fs ? nz - c : min(c + 1, nz - c)));
                     const float bzh = bt3(btab, nbt, fs ? 2 * (nz - c) - 1 : min(2 * c + 3, 2 * (nz - c) - 1));
 #pragma unroll
@@ -452,8 +464,7 @@ stage_tma3d_kernel(const ProblemDev* __restrict__ probs, const int* __restrict__
                             for (int q = 0; q < R; ++q) dz[q] = uq[r][R - q] - uq[r][R + 1 + q];
                             duz = st_tree<R>(dz);
                         }
-                        const float byn = bt3(btab, nbt, 2 * min(j + 1, ny - j));
-                        const float byh = bt3(btab, nbt, min(2 * j + 3, 2 * (ny - j) - 1));
+                        const float byn = byn_t[r], byh = byh_t[r];
                         const int pt = ly * BX + tx;
                         const float xwx = wxrow[0];
                         const float xwy = swy[(ly + R) * BX + tx];
