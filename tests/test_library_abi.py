@@ -45,6 +45,9 @@ def test_null_handle_errors_without_gpu(lib):
     assert lib.ewv_set_stream(None, None) == -1
     assert lib.ewv_last_error(None) == b"null handle"
     assert lib.ewv_create_model(None, None) == -1
+    assert lib.ewv_step_krylov_dense(None, 0.0, 1e-3, 8, None) == -1
+    assert lib.ewv_adjoint_step_krylov_dense(None, 0.0, 1e-3, 8, None, None, None) == -1
+    assert lib.ewv_adjoint_step(None, 0, 0.0, 1e-3, 8, None, None, None) == -1
 
 
 def test_checkpoint_stride_host_logic_matches_oracle(lib):
